@@ -1,0 +1,403 @@
+/*
+ * masw_oracle.c -- plain CPU FP64 oracle for the theoretical Rayleigh-wave
+ * dispersion curve C_t of layered models (Kump & Martin, MASWAccelerated).
+ *
+ * TEST INFRASTRUCTURE. Only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg call this file. The product (the CUDA library)
+ * shares no code, header or table with it and never calls it.
+ *
+ * What it computes, in the paper's order:
+ *   Algorithm 1 (Section 2.1): for every wavelength w of a model, take test
+ *   velocities V[0] < V[1] < ... in increasing order, evaluate the determinant
+ *   of the stiffness matrix K(k = 2*pi/w, c = V[n]) and stop at the first n
+ *   whose determinant sign differs from that of V[n-1]; C_t[w] = V[n].
+ *   Section 2.1: K is the 2(N+1) x 2(N+1) global stiffness matrix of the
+ *   stiffness matrix method (N finite layers over a half-space).
+ *   Algorithm 2 (Section 2.1): misfit = (1/l) * sum |C_t - C_e| / C_e.
+ *
+ * Deliberately plain: K is assembled as a DENSE matrix and its determinant is
+ * taken by dense LU with partial pivoting (sign = parity of row swaps times
+ * the signs of U's diagonal, magnitude kept as sum of log|u_ii|). No banded
+ * structure, no recurrence, no reuse between test velocities.
+ *
+ * Stiffness entries. The paper only names the stiffness matrix method; the
+ * entries below are derived from textbook P-SV elastodynamics. With fields
+ * ~ exp(i(omega t - k x)) and the real motion-stress vector
+ *   y = (u_x, u_z / i, tau_xz / (k mu), tau_zz / (i k mu)),
+ * dy/d(kz) = A y with eigenvalues +-r, +-s, where
+ *   r^2 = 1 - c^2/alpha^2,  s^2 = 1 - c^2/beta^2.
+ * The layer stiffness maps nodal displacements (top, bottom) to the nodal
+ * forces (-tau(top), +tau(bottom)); eliminating the layer's internal state
+ * from its transfer matrix gives, in units of k*mu and with
+ *   C_x = cosh(k h x),  Sd_x = sinh(k h x)/x,  Sm_x = x sinh(k h x)
+ * (even in x, so imaginary r or s turn into cos/sin with no complex numbers),
+ *   D = 2 (1 - C_r C_s) + Sd_r Sd_s + Sm_r Sm_s
+ *   a = q (C_r Sd_s - C_s Sm_r) / D          q = c^2 / beta^2
+ *   d = q (C_s Sd_r - C_r Sm_s) / D
+ *   b = ((s^2 + 3)(C_r C_s - 1) - 2 Sm_r Sm_s - Sd_r Sm_s - Sd_r Sd_s) / D
+ *   e = q (Sm_r - Sd_s) / D
+ *   f = -q (C_r - C_s) / D
+ *   g = q (Sm_s - Sd_r) / D
+ *   K11 = [[a, b], [b, d]]   K22 = [[a, -b], [-b, d]]
+ *   K12 = [[e, f], [-f, g]]  K21 = K12^T
+ * and for the half-space (decaying waves only, c < beta), in units of k*mu,
+ *   Khs = [[r q, 2 r s - 1 - s^2], [2 r s - 1 - s^2, s q]] / (1 - r s).
+ * det Khs is proportional to the Rayleigh function (2 - q)^2 - 4 r s, so a
+ * bare half-space gives the textbook Rayleigh speed at every wavelength.
+ * The tests pin these closed forms against a high-precision matrix
+ * exponential of A (independent route) and against the Rayleigh cubic.
+ *
+ * Readings of the paper where it is silent (all shared with the CUDA path's
+ * documentation, none with its code):
+ *   - V[n] = c0 + n*dc, rounded once (fma), n = 0..n_c-1.
+ *   - Only test velocities strictly below the half-space shear speed are
+ *     scanned (above it the half-space stiffness is complex); no sign change
+ *     there -> status NO_ROOT, C_t = NaN, index -1.
+ *   - sgn(x) = (x > 0) - (x < 0); an exact zero (or NaN) counts as a change.
+ *   - C_t is the upper end V[n] of the first sign-changing pair.
+ *   - Domain: k h <= ORACLE_MAX_KH for every layer (the unscaled cosh/sinh
+ *     products would overflow beyond it); outside it calls return EINVAL.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "masw_oracle.h"
+
+static int sgn(double x) { return (x > 0.0) - (x < 0.0); }
+
+/* V[n] of the test-velocity grid, rounded once. */
+double oracle_grid_velocity(double c0, double dc, int n) {
+    return fma((double)n, dc, c0);
+}
+
+/* cosh(kh w), sinh(kh w)/w, w sinh(kh w) for w = sqrt(w2); w2 may be < 0. */
+static void even_funcs(double kh, double w2, double* C, double* Sd, double* Sm) {
+    if (w2 > 0.0) {
+        double w = sqrt(w2), x = kh * w, sh = sinh(x);
+        *C = cosh(x);
+        *Sd = sh / w;
+        *Sm = w * sh;
+    } else if (w2 < 0.0) {
+        double w = sqrt(-w2), y = kh * w, sn = sin(y);
+        *C = cos(y);
+        *Sd = sn / w;
+        *Sm = -w * sn;
+    } else {
+        *C = 1.0;
+        *Sd = kh;
+        *Sm = 0.0;
+    }
+}
+
+/* 4x4 layer stiffness, row-major, DOFs (ux_top, uz_top, ux_bot, uz_bot). */
+void oracle_layer_stiffness(double k, double c, double h, double alpha,
+                            double beta, double rho, double* Ke) {
+    double mu = rho * beta * beta;
+    double q = (c * c) / (beta * beta);
+    double r2 = 1.0 - (c * c) / (alpha * alpha);
+    double s2 = 1.0 - q;
+    double Cr, Sdr, Smr, Cs, Sds, Sms;
+    even_funcs(k * h, r2, &Cr, &Sdr, &Smr);
+    even_funcs(k * h, s2, &Cs, &Sds, &Sms);
+    double D = 2.0 * (1.0 - Cr * Cs) + Sdr * Sds + Smr * Sms;
+    double a = q * (Cr * Sds - Cs * Smr) / D;
+    double d = q * (Cs * Sdr - Cr * Sms) / D;
+    double b = ((s2 + 3.0) * (Cr * Cs - 1.0) - 2.0 * Smr * Sms - Sdr * Sms - Sdr * Sds) / D;
+    double e = q * (Smr - Sds) / D;
+    double f = -q * (Cr - Cs) / D;
+    double g = q * (Sms - Sdr) / D;
+    double km = k * mu;
+    double M[16] = {
+        a,  b,  e,  f,
+        b,  d, -f,  g,
+        e, -f,  a, -b,
+        f,  g, -b,  d,
+    };
+    for (int i = 0; i < 16; ++i) Ke[i] = km * M[i];
+}
+
+/* 2x2 half-space stiffness (c < beta), row-major, DOFs (ux, uz). */
+void oracle_halfspace_stiffness(double k, double c, double alpha, double beta,
+                                double rho, double* Kh) {
+    double mu = rho * beta * beta;
+    double q = (c * c) / (beta * beta);
+    double r = sqrt(1.0 - (c * c) / (alpha * alpha));
+    double s = sqrt(1.0 - q);
+    double den = 1.0 - r * s;
+    double km = k * mu;
+    double off = (2.0 * r * s - 1.0 - s * s) / den;
+    Kh[0] = km * r * q / den;
+    Kh[1] = km * off;
+    Kh[2] = km * off;
+    Kh[3] = km * s * q / den;
+}
+
+/* Dense global stiffness, n = 2(N+1), row-major. Layer i (1..N) couples
+ * interface nodes i-1 and i; the half-space sits under node N. */
+void oracle_assemble(int N, const double* h, const double* alpha,
+                     const double* beta, const double* rho, double k, double c,
+                     double* K) {
+    int n = 2 * (N + 1);
+    memset(K, 0, sizeof(double) * (size_t)n * (size_t)n);
+    double Ke[16];
+    for (int i = 0; i < N; ++i) {
+        oracle_layer_stiffness(k, c, h[i], alpha[i], beta[i], rho[i], Ke);
+        int base = 2 * i; /* top node DOFs base, base+1; bottom base+2, base+3 */
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b)
+                K[(size_t)(base + a) * n + (base + b)] += Ke[a * 4 + b];
+    }
+    double Kh[4];
+    oracle_halfspace_stiffness(k, c, alpha[N], beta[N], rho[N], Kh);
+    int base = 2 * N;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            K[(size_t)(base + a) * n + (base + b)] += Kh[a * 2 + b];
+}
+
+/* Determinant of a dense n x n matrix by LU with partial pivoting. A is
+ * overwritten. sign in {-1, 0, +1}; log_abs = ln|det| (-inf when singular). */
+void oracle_lu_det(int n, double* A, int* sign, double* log_abs) {
+    int sg = 1;
+    double la = 0.0;
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        double best = fabs(A[(size_t)col * n + col]);
+        for (int row = col + 1; row < n; ++row) {
+            double v = fabs(A[(size_t)row * n + col]);
+            if (v > best) { best = v; piv = row; }
+        }
+        if (!(best > 0.0)) { /* exact zero column (or NaN) */
+            *sign = 0;
+            *log_abs = -INFINITY;
+            return;
+        }
+        if (piv != col) {
+            for (int j = 0; j < n; ++j) {
+                double t = A[(size_t)col * n + j];
+                A[(size_t)col * n + j] = A[(size_t)piv * n + j];
+                A[(size_t)piv * n + j] = t;
+            }
+            sg = -sg;
+        }
+        double p = A[(size_t)col * n + col];
+        sg *= sgn(p);
+        la += log(fabs(p));
+        for (int row = col + 1; row < n; ++row) {
+            double m = A[(size_t)row * n + col] / p;
+            if (m == 0.0) continue;
+            for (int j = col + 1; j < n; ++j)
+                A[(size_t)row * n + j] -= m * A[(size_t)col * n + j];
+        }
+    }
+    *sign = sg;
+    *log_abs = la;
+}
+
+/* Domain of the plain (unscaled) hyperbolic functions: products of two
+ * cosh(k h x) stay finite while k h <= ORACLE_MAX_KH for every layer. */
+static int in_domain(int N, const double* h, double k) {
+    for (int i = 0; i < N; ++i)
+        if (!(k * h[i] <= ORACLE_MAX_KH)) return 0;
+    return 1;
+}
+
+int oracle_det(int N, const double* h, const double* alpha, const double* beta,
+               const double* rho, double k, double c, int* sign, double* log_abs) {
+    if (!in_domain(N, h, k)) return ORACLE_EINVAL;
+    int n = 2 * (N + 1);
+    double* K = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    if (!K) return ORACLE_ENOMEM;
+    oracle_assemble(N, h, alpha, beta, rho, k, c, K);
+    oracle_lu_det(n, K, sign, log_abs);
+    free(K);
+    return ORACLE_OK;
+}
+
+/* Number of grid points the scan may visit: V[n] < beta of the half-space. */
+int oracle_scan_limit(double beta_hs, double c0, double dc, int n_c) {
+    int n = 0;
+    while (n < n_c && oracle_grid_velocity(c0, dc, n) < beta_hs) ++n;
+    return n;
+}
+
+/* Algorithm 1 for one wavelength. Returns ORACLE_OK or ORACLE_NO_ROOT. */
+int oracle_scan(int N, const double* h, const double* alpha, const double* beta,
+                const double* rho, double lambda, double c0, double dc, int n_c,
+                double* ct, int* idx) {
+    double k = 2.0 * M_PI / lambda;
+    *ct = NAN;
+    *idx = -1;
+    if (!in_domain(N, h, k)) return ORACLE_EINVAL;
+    int n_lim = oracle_scan_limit(beta[N], c0, dc, n_c);
+    int n = 2 * (N + 1);
+    double* K = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    if (!K) return ORACLE_ENOMEM;
+    int status = ORACLE_NO_ROOT;
+    if (n_lim >= 2) {
+        int s_old, s_new;
+        double la;
+        oracle_assemble(N, h, alpha, beta, rho, k, oracle_grid_velocity(c0, dc, 0), K);
+        oracle_lu_det(n, K, &s_old, &la);
+        for (int j = 1; j < n_lim; ++j) {
+            double c = oracle_grid_velocity(c0, dc, j);
+            oracle_assemble(N, h, alpha, beta, rho, k, c, K);
+            oracle_lu_det(n, K, &s_new, &la);
+            if (s_new != s_old) {
+                *ct = c;
+                *idx = j;
+                status = ORACLE_OK;
+                break;
+            }
+            s_old = s_new;
+        }
+    }
+    free(K);
+    return status;
+}
+
+/* Ragged batch: models are concatenated; model m has n_layers[m] finite
+ * layers (h has N_m entries, alpha/beta/rho have N_m+1) and n_lambda[m]
+ * wavelengths. Items (model, wavelength) are independent; OpenMP spreads
+ * them over n_threads host threads (0 = runtime default). */
+int oracle_dispersion(int n_models, const int* n_layers, const double* h,
+                      const double* alpha, const double* beta, const double* rho,
+                      const int* n_lambda, const double* lambda, double c0,
+                      double dc, int n_c, double* ct, int* idx, int* status,
+                      int n_threads) {
+    int64_t* hoff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_models + 1));
+    int64_t* loff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_models + 1));
+    int64_t* woff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_models + 1));
+    if (!hoff || !loff || !woff) { free(hoff); free(loff); free(woff); return ORACLE_ENOMEM; }
+    hoff[0] = loff[0] = woff[0] = 0;
+    for (int m = 0; m < n_models; ++m) {
+        hoff[m + 1] = hoff[m] + n_layers[m];
+        loff[m + 1] = loff[m] + n_layers[m] + 1;
+        woff[m + 1] = woff[m] + n_lambda[m];
+    }
+    int64_t n_items = woff[n_models];
+    int* item_model = (int*)malloc(sizeof(int) * (size_t)(n_items > 0 ? n_items : 1));
+    if (!item_model) { free(hoff); free(loff); free(woff); return ORACLE_ENOMEM; }
+    for (int m = 0; m < n_models; ++m)
+        for (int64_t j = woff[m]; j < woff[m + 1]; ++j) item_model[j] = m;
+    int err = ORACLE_OK;
+#ifdef _OPENMP
+    int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+    for (int64_t it = 0; it < n_items; ++it) {
+        int m = item_model[it];
+        int st = oracle_scan(n_layers[m], h + hoff[m], alpha + loff[m], beta + loff[m],
+                             rho + loff[m], lambda[it], c0, dc, n_c, &ct[it], &idx[it]);
+        if (st < 0) err = st;
+        status[it] = st;
+    }
+    free(item_model);
+    free(hoff);
+    free(loff);
+    free(woff);
+    return err;
+}
+
+/* Continuous root inside [c_lo, c_hi] by bisection on sgn det K, until the
+ * bracket is narrower than rel_tol * c_hi. Requires a sign change at the
+ * ends; returns ORACLE_NO_ROOT otherwise. The root is the bracket midpoint. */
+int oracle_refine(int N, const double* h, const double* alpha, const double* beta,
+                  const double* rho, double lambda, double c_lo, double c_hi,
+                  double rel_tol, double* root) {
+    double k = 2.0 * M_PI / lambda;
+    int s_lo, s_hi, s_mid;
+    double la;
+    int st = oracle_det(N, h, alpha, beta, rho, k, c_lo, &s_lo, &la);
+    if (st) { *root = NAN; return st; }
+    oracle_det(N, h, alpha, beta, rho, k, c_hi, &s_hi, &la);
+    if (s_lo == s_hi) { *root = NAN; return ORACLE_NO_ROOT; }
+    if (s_lo == 0) { *root = c_lo; return ORACLE_OK; }
+    for (int it = 0; it < 200 && (c_hi - c_lo) > rel_tol * c_hi; ++it) {
+        double mid = 0.5 * (c_lo + c_hi);
+        oracle_det(N, h, alpha, beta, rho, k, mid, &s_mid, &la);
+        if (s_mid == 0) { c_lo = c_hi = mid; break; }
+        if (s_mid == s_lo) c_lo = mid; else c_hi = mid;
+    }
+    *root = 0.5 * (c_lo + c_hi);
+    return ORACLE_OK;
+}
+
+/* Refined root for one item given its Algorithm-1 index: bisection inside
+ * the window [V[idx-2], V[idx+1]] (clamped to the scanned range), which
+ * contains the first sign change [V[idx-1], V[idx]] and tolerates the small
+ * root shifts of finite-difference perturbations. */
+static int window_root(int N, const double* h, const double* alpha, const double* beta,
+                       const double* rho, double lambda, double c0, double dc, int n_c,
+                       int idx, double rel_tol, double* root) {
+    int n_lim = oracle_scan_limit(beta[N], c0, dc, n_c);
+    int lo = idx - 2 < 0 ? 0 : idx - 2;
+    int hi = idx + 1 > n_lim - 1 ? n_lim - 1 : idx + 1;
+    return oracle_refine(N, h, alpha, beta, rho, lambda, oracle_grid_velocity(c0, dc, lo),
+                         oracle_grid_velocity(c0, dc, hi), rel_tol, root);
+}
+
+int oracle_root(int N, const double* h, const double* alpha, const double* beta,
+                const double* rho, double lambda, double c0, double dc, int n_c,
+                int idx, double rel_tol, double* root) {
+    (void)n_c;
+    if (idx < 1) { *root = NAN; return ORACLE_NO_ROOT; }
+    double lo = oracle_grid_velocity(c0, dc, idx - 1);
+    double hi = oracle_grid_velocity(c0, dc, idx);
+    return oracle_refine(N, h, alpha, beta, rho, lambda, lo, hi, rel_tol, root);
+}
+
+/* Central finite differences of the refined root of one item with respect to
+ * beta_1..beta_{N+1} (Poisson ratio held: alpha_i scales with beta_i) and
+ * h_1..h_N, relative step rel_step. dC_dbeta has N+1 entries, dC_dh N. */
+int oracle_root_grad_fd(int N, const double* h, const double* alpha, const double* beta,
+                        const double* rho, double lambda, double c0, double dc, int n_c,
+                        int idx, double rel_step, double rel_tol, double* dC_dbeta,
+                        double* dC_dh) {
+    double hp[ORACLE_MAX_LAYERS], ap[ORACLE_MAX_LAYERS + 1], bp[ORACLE_MAX_LAYERS + 1];
+    if (N > ORACLE_MAX_LAYERS || idx < 1) return ORACLE_EINVAL;
+    for (int p = 0; p <= N; ++p) {
+        double cp, cm;
+        memcpy(hp, h, sizeof(double) * (size_t)N);
+        memcpy(ap, alpha, sizeof(double) * (size_t)(N + 1));
+        memcpy(bp, beta, sizeof(double) * (size_t)(N + 1));
+        double del = rel_step * beta[p];
+        bp[p] = beta[p] + del;
+        ap[p] = alpha[p] * (bp[p] / beta[p]);
+        int s1 = window_root(N, hp, ap, bp, rho, lambda, c0, dc, n_c, idx, rel_tol, &cp);
+        bp[p] = beta[p] - del;
+        ap[p] = alpha[p] * (bp[p] / beta[p]);
+        int s2 = window_root(N, hp, ap, bp, rho, lambda, c0, dc, n_c, idx, rel_tol, &cm);
+        dC_dbeta[p] = (s1 || s2) ? NAN : (cp - cm) / (2.0 * del);
+    }
+    for (int p = 0; p < N; ++p) {
+        double cp, cm;
+        memcpy(hp, h, sizeof(double) * (size_t)N);
+        double del = rel_step * h[p];
+        hp[p] = h[p] + del;
+        int s1 = window_root(N, hp, alpha, beta, rho, lambda, c0, dc, n_c, idx, rel_tol, &cp);
+        hp[p] = h[p] - del;
+        int s2 = window_root(N, hp, alpha, beta, rho, lambda, c0, dc, n_c, idx, rel_tol, &cm);
+        dC_dh[p] = (s1 || s2) ? NAN : (cp - cm) / (2.0 * del);
+    }
+    return ORACLE_OK;
+}
+
+/* Algorithm 2: mean relative error (e starts at 0). */
+double oracle_misfit_paper(int L, const double* ct, const double* ce) {
+    double e = 0.0;
+    for (int i = 0; i < L; ++i) e += fabs(ct[i] - ce[i]) / ce[i];
+    return e / (double)L;
+}
+
+/* Least-squares misfit 1/(2 sigma^2) * sum (C - C_e)^2. */
+double oracle_misfit_lsq(int L, const double* ct, const double* ce, double sigma) {
+    double e = 0.0;
+    for (int i = 0; i < L; ++i) e += (ct[i] - ce[i]) * (ct[i] - ce[i]);
+    return e / (2.0 * sigma * sigma);
+}
