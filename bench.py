@@ -1,0 +1,305 @@
+"""Benchmark: dispersion curves per second on GB300.
+
+A step is one MASW evaluation of a whole batch -- Algorithm 1 (theoretical
+dispersion curve of every (model, wavelength) item) followed by Algorithm 2
+(misfit per model) -- on the uniform workload: 1024 models of 8 layers over a
+half-space, 200 log-spaced wavelengths 1..150 m, test velocities 50..1200 m/s
+step 0.25 (4601 points), FP64. Inputs are resident in device memory when the
+timed region starts; L2 is flushed (256 MB write) between timed steps.
+
+Also reported on the same line: the plain one-curve-per-launch GPU path,
+the end-to-end figure through the C ABI with host buffers, the roofline of
+the scan kernel against the measured FP64 peak, and the CPU oracle on a
+bounded sample (``cpu_baseline``). ``--impl reference`` times the CPU oracle
+alone (the reference arm).
+
+Multi-GPU: one process per GPU (torchrun); each rank evaluates its own
+1024-model batch (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2003_02256_gb300 import workloads as W  # noqa: E402
+
+METRIC = "dispersion curves/sec (model x all lambda) and p50/p99 latency vs plain GPU"
+UNIT = "curves/s"
+WORKLOAD = ("uniform_batch: 1024 models x (8 layers + half-space), h~U[1,8] m, beta_1~U[100,250] "
+            "+U[10,120] per layer, nu~U[0.25,0.4], rho~U[1700,2100]; 200 log-spaced lambda "
+            "1..150 m; c grid 50..1200 m/s step 0.25 (4601 points); FP64")
+# FP64 flops per layer-evaluation of the scan kernel (element assembly + one
+# Schur step): 2*DFMA + DADD + DMUL executed per evaluated (layer, c) pair,
+# from ncu instruction counters on this workload (profiles/).
+F_LAYER_FLOPS = 180.0
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(models, grid, n_models: int, seconds_hint: float = 10.0):
+    """Time the CPU oracle on the first n_models models of the workload, on
+    all host cores. Returns (curves/s, cores, sample description)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    sub = models.subset(range(n_models))
+    t0 = time.perf_counter()
+    oracle.dispersion(sub.as_dict(), grid.c0, grid.dc, grid.n_c, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return n_models / dt, cores, f"first {n_models} of the 1024 models, all 200 wavelengths, " \
+                                 f"{dt:.1f} s on {cores} threads"
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    models, grid = W.uniform_batch()
+    per_step = 16
+    for _ in range(args.warmup):
+        cpu_oracle_rate(models, grid, 4)
+    times = []
+    cores = os.cpu_count() or 1
+    import oracle
+    for s in range(args.steps):
+        sub = models.subset(range((s * per_step) % 1024, (s * per_step) % 1024 + per_step))
+        t0 = time.perf_counter()
+        oracle.dispersion(sub.as_dict(), grid.c0, grid.dc, grid.n_c, n_threads=cores)
+        times.append(time.perf_counter() - t0)
+    value = per_step * args.steps / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_models_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} models x 200 wavelengths per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def algorithmic_layer_evals(models, idx, st, nlim):
+    """Sum over items of (evaluated grid points) x (N + 1): idx + 1 points
+    when a root is found, the whole scannable range otherwise."""
+    nl = np.repeat(models.n_layers.astype(np.int64) + 1, models.n_lambda)
+    pts = np.where(st == 0, idx.astype(np.int64) + 1, np.repeat(nlim, models.n_lambda))
+    return int(np.sum(pts * nl))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--models", type=int, default=1024,
+                    help="models per GPU (smaller only for profiler captures)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2003_02256_gb300 import masw
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+
+    models, grid = W.uniform_batch(n_models=args.models, seed=W.SEED + 1000 * rank)
+    ce_host = W.noisy_observation(np.full(models.n_items, 250.0), sigma=30.0, seed=rank)
+    batch = masw.Batch(models, grid)
+    if not args.no_autotune:
+        plan = batch.autotune(reps=1)
+    else:
+        plan = batch.plan()
+
+    # results of one pass (parity-checked in tests; used for the algorithmic count)
+    ct, idx, st = batch.dispersion()
+    nlim = np.array([int(np.sum(grid.c0 + np.arange(grid.n_c) * grid.dc < models.model(m)[2][-1]))
+                     for m in range(models.n_models)])
+    units = algorithmic_layer_evals(models, idx, st, nlim)
+
+    ce = torch.from_numpy(ce_host).cuda()
+    phi = torch.empty(models.n_models, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        masw.misfit(batch.handle, ce, masw.MISFIT_LSQ, 2.0, phi)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    scan_ms = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            scan_ms.append(batch.last_scan_ms())
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(np.sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * models.n_models * args.steps / (total_ms * 1e-3)
+
+    # plain one-curve-per-launch path (same kernel body, one launch + sync per model)
+    plain_ms = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        batch.dispersion(plain=True)
+        plain_ms.append(1e3 * (time.perf_counter() - t0))
+    plain_value = models.n_models / (min(plain_ms) * 1e-3)
+
+    # end to end through the C ABI with host buffers: upload of the step's
+    # model parameters and C_e from pinned memory, misfit read back to host
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hh, ha, hb, hr, hce = (pin(x) for x in (models.h, models.alpha, models.beta, models.rho, ce_host))
+    hphi = torch.empty(models.n_models, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        masw.model_batch_update(batch.handle, hh, ha, hb, hr)
+        masw.misfit(batch.handle, hce, masw.MISFIT_LSQ, 2.0, hphi)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_total = float(np.sum(e2e_ms))
+    if dist:
+        t = torch.tensor([e2e_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * models.n_models * args.steps / (e2e_total * 1e-3)
+    h2d = sum(x.numel() * 8 for x in (hh, ha, hb, hr, hce))
+    d2h = hphi.numel() * 8
+
+    # roofline of the scan kernel: algorithmic FP64 flops / device time
+    peak = masw.fp64_peak()
+    scan_avg = float(np.mean(scan_ms)) * 1e-3
+    achieved = units * F_LAYER_FLOPS / scan_avg
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "kernel": "scan_kernel (FP64 pipe)", "peak_source": "measured DFMA microbenchmark",
+                "layer_evals_per_launch": units, "flops_per_layer_eval": F_LAYER_FLOPS,
+                "scan_ms": scan_avg * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_oracle_rate(models, grid, 64)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "models_per_gpu": models.n_models,
+                           "items_per_gpu": models.n_items, "seed": W.SEED,
+                           "l2": "flushed between timed steps (256 MB write)",
+                           "step": "Algorithm 1 scan of every item + Algorithm 2 misfit",
+                           "plan": plan.as_dict(), "parallelism": f"replicas x{world}"},
+                "clocks": clk.summary(),
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": 2 * args.steps,
+                "roofline": roofline,
+                "cpu_baseline": cpu,
+                "plain_gpu": {"value": plain_value, "unit": UNIT,
+                              "ms_per_step": min(plain_ms),
+                              "speedup_of_batched": value / world / plain_value},
+                "found_fraction": float(np.mean(st == 0))}
+        print(json.dumps(line), flush=True)
+    batch.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * masw.h -- C ABI of libmasw, a GB300-native engine for theoretical
+ * Rayleigh-wave dispersion curves (the forward problem of MASW inversion,
+ * Kump & Martin, "MASWAccelerated").
+ *
+ * Problem statement (Section 2.1, Algorithm 1): a model M has N finite layers
+ * (thickness h, P speed alpha, S speed beta, density rho) over a half-space.
+ * For each wavelength lambda in W and test velocities V[0] < V[1] < ..., the
+ * theoretical velocity C_t(lambda) is the first V[n] whose stiffness-matrix
+ * determinant det K(k = 2 pi / lambda, c = V[n]) differs in sign from that of
+ * V[n-1]. K is the 2(N+1) x 2(N+1) banded stiffness matrix of the stiffness
+ * matrix method. The misfit (Algorithm 2) compares C_t with an observed curve
+ * C_e.
+ *
+ * Conventions shared by every call:
+ *  - Units: metres, metres per second, kilograms per cubic metre.
+ *  - Ragged batches: models are concatenated. Model m has n_layers[m] = N_m
+ *    finite layers; h holds N_m values, alpha/beta/rho hold N_m + 1 (the last
+ *    is the half-space); lambda holds n_lambda[m] values. An "item" is one
+ *    (model, wavelength) pair; item order is the concatenated lambda order.
+ *  - Grid: V[n] = c0 + n * dc, rounded once (fused multiply-add), n < n_c.
+ *    Only V[n] < beta of the half-space is scanned (the half-space stiffness
+ *    is complex above it). No sign change there -> per-item status
+ *    MASW_NO_ROOT, C_t = NaN, index -1.
+ *  - sgn(x) = (x > 0) - (x < 0); an exact zero determinant counts as a change.
+ *  - C_t is the upper end V[n] of the first sign-changing pair.
+ *  - Every call enqueues its GPU work on the batch's stream. Calls that write
+ *    host memory synchronise that stream before returning; calls that only
+ *    write device memory return without synchronising.
+ *  - Pointers marked "host or device" are classified with
+ *    cudaPointerGetAttributes; all buffers are owned by the caller and are
+ *    only read or written during the call (or, for device outputs, by work
+ *    the call enqueued).
+ *  - Return value: MASW_OK (0) or a positive MASW_E* code; masw_strerror
+ *    gives its text. On a validation error no output is written.
+ */
+#ifndef MASW_H
+#define MASW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- call status codes ---- */
+#define MASW_OK 0
+#define MASW_EINVAL 1   /* invalid argument or model (h<=0, rho<=0, beta<=0, alpha^2 <= 4/3 beta^2, NaN, ...) */
+#define MASW_ENOMEM 2   /* device or host allocation failed */
+#define MASW_EADMIT 3   /* serving: request refused by the slot or memory cap */
+#define MASW_ECUDA 4    /* a CUDA runtime call failed */
+#define MASW_ETIMEOUT 5 /* serving: a bounded wait ran out */
+#define MASW_EAGAIN 6   /* serving: result not ready yet */
+
+/* ---- per-item status ---- */
+#define MASW_FOUND 0
+#define MASW_NO_ROOT 1
+
+/* ---- memory spaces ---- */
+#define MASW_HOST 0
+#define MASW_DEVICE 1
+
+/* ---- misfit kinds ---- */
+#define MASW_MISFIT_PAPER 0 /* Algorithm 2: (1/L) sum |C - C_e| / C_e */
+#define MASW_MISFIT_LSQ 1   /* 1/(2 sigma^2) sum (C - C_e)^2 */
+
+/* Library limits. */
+#define MASW_MAX_LAYERS 128 /* finite layers per model */
+
+typedef struct masw_batch masw_batch;
+
+/* Ragged model batch (Section 2.1, "model parameter inputs M" and "W").
+ * mem_space tells where ALL pointers of this struct live. */
+typedef struct {
+    int32_t n_models;
+    const int32_t* n_layers; /* [n_models] N_m >= 0 */
+    const double* h;         /* [sum N_m]           thickness, > 0 */
+    const double* alpha;     /* [sum N_m + 1]       P speed, alpha^2 > 4/3 beta^2 */
+    const double* beta;      /* [sum N_m + 1]       S speed, > 0 */
+    const double* rho;       /* [sum N_m + 1]       density, > 0 */
+    const int32_t* n_lambda; /* [n_models] >= 0 */
+    const double* lambda;    /* [sum n_lambda]      wavelength, > 0 */
+    int32_t mem_space;       /* MASW_HOST or MASW_DEVICE */
+} masw_models_desc;
+
+/* Test velocities V (Algorithm 1): V[n] = c0 + n*dc, c0 > 0, dc > 0, n_c >= 2. */
+typedef struct {
+    double c0;
+    double dc;
+    int32_t n_c;
+} masw_grid;
+
+/* Launch plan of the scan (see masw_autotune). */
+typedef struct {
+    int32_t warps_per_block; /* 1, 2, 4, 8 */
+    int32_t cpl;             /* test velocities per lane per chunk: 1, 2, 4 */
+    int32_t blocks_per_sm;   /* persistent grid = blocks_per_sm x SM count */
+    int32_t persistent;      /* 1: warps pop items from a work queue */
+    int32_t ordered;         /* 1: queue ordered by predicted scan length (longest first) */
+    int32_t stage_layers;    /* layer records staged in shared memory per warp (0: none) */
+    int32_t use_graph;       /* 1: replay the scan as a captured CUDA graph */
+} masw_plan;
+
+/* Copy and validate a model batch into batch-owned device memory and bind it
+ * to cuda_stream (a cudaStream_t; NULL = legacy default stream). The caller
+ * keeps ownership of every input pointer; they are read during the call only.
+ * Errors: MASW_EINVAL (any invalid value, n_models < 1, N_m > MASW_MAX_LAYERS),
+ * MASW_ENOMEM, MASW_ECUDA. *out is set only on success. */
+int masw_model_batch_create(const masw_models_desc* models, const masw_grid* grid,
+                            void* cuda_stream, masw_batch** out);
+
+/* Release the batch and everything it owns (waits for its stream). */
+int masw_model_batch_destroy(masw_batch* batch);
+
+/* Replace the layer parameters of an existing batch (same n_layers and
+ * n_lambda; wavelengths unchanged). Pointers live in mem_space. Used by
+ * inversion loops and samplers; a captured scan graph stays valid. */
+int masw_model_batch_update(masw_batch* batch, const double* h, const double* alpha,
+                            const double* beta, const double* rho, int32_t mem_space);
+
+/* Number of items (sum of n_lambda) and models of the batch. */
+int masw_batch_info(const masw_batch* batch, int64_t* n_items, int32_t* n_models,
+                    int32_t* max_layers);
+
+/* Algorithm 1 for every item. Outputs (length n_items, item order) live in
+ * out_mem_space: ct = C_t (NaN when not found), ct_idx = n (-1 when not
+ * found), status = MASW_FOUND / MASW_NO_ROOT. Any output pointer may be NULL.
+ * Uses the batch plan (persistent, ordered, graph-replayed by default). */
+int masw_dispersion(masw_batch* batch, double* ct, int32_t* ct_idx, int32_t* status,
+                    int32_t out_mem_space);
+
+/* The plain comparison path: one scan launch per model (one curve per
+ * launch), synchronising the stream after each model -- the paper's
+ * one-curve-per-call GPU pattern (Section 2.3). Same outputs as
+ * masw_dispersion. */
+int masw_dispersion_plain(masw_batch* batch, double* ct, int32_t* ct_idx, int32_t* status,
+                          int32_t out_mem_space);
+
+/* Algorithm 2 per model after running Algorithm 1: ce (host or device,
+ * length n_items, item order) is the observed curve C_e; misfit (host or
+ * device, length n_models). kind = MASW_MISFIT_PAPER or MASW_MISFIT_LSQ
+ * (sigma > 0 used by LSQ only). A model with an item without root gets NaN. */
+int masw_misfit(masw_batch* batch, const double* ce, int32_t kind, double sigma, double* misfit);
+
+/* Misfit evaluated on the refined continuous roots C* (bisection inside the
+ * first sign-changing bracket to a relative width of 1e-13) and its exact
+ * gradient by the implicit-function rule d(C*)/d(theta) = -(u^T dK/dtheta u) /
+ * (u^T dK/dc u), u the null vector of K(C*). theta = beta_i (Poisson ratio
+ * held: alpha_i moves with beta_i) and h_i. grad_beta has sum(N_m + 1)
+ * entries, grad_h sum(N_m), both concatenated like beta and h. All outputs
+ * host or device; any may be NULL except misfit. */
+int masw_misfit_grad(masw_batch* batch, const double* ce, int32_t kind, double sigma,
+                     double* misfit, double* grad_beta, double* grad_h);
+
+/* Refined roots C* per item (host or device, length n_items; NaN where
+ * Algorithm 1 found none). */
+int masw_roots(masw_batch* batch, double* croot);
+
+/* d(C*)/d(theta) per item: rows of 2 N_m + 1 values (dbeta_0..dbeta_N,
+ * dh_0..dh_{N-1}) concatenated in item order (host or device). *row_len_total
+ * receives the total length when rows is NULL. */
+int masw_root_grad(masw_batch* batch, double* rows, int64_t* row_len_total);
+
+/* Sign and ln|det K(k_item, c)| at n arbitrary points (parity checks of the
+ * block recurrence). item, c, sign, log_abs: host or device, length n.
+ * Points with c outside (0, beta_halfspace) get sign 0 and NaN. */
+int masw_det_eval(masw_batch* batch, int32_t n, const int32_t* item, const double* c,
+                  int32_t* sign, double* log_abs);
+
+/* Current plan of the batch; set a plan (validated; the graph is rebuilt). */
+int masw_get_plan(const masw_batch* batch, masw_plan* plan);
+int masw_set_plan(masw_batch* batch, const masw_plan* plan);
+
+/* Time candidate plans on this batch (reps timed scans each, CUDA events on
+ * the batch stream), keep the fastest, return it in *best (may be NULL).
+ * Results never depend on the plan. Winners are cached per (max layers,
+ * n_c, item-count bucket) in-process and, when the environment variable
+ * MASW_PLAN_CACHE names a file, across processes. */
+int masw_autotune(masw_batch* batch, int32_t reps, masw_plan* best);
+
+/* Device time (ms) of the most recent scan launched by masw_dispersion or
+ * masw_dispersion_plain (CUDA events on the batch stream). */
+int masw_last_scan_ms(const masw_batch* batch, float* ms);
+
+/* FP64 fused multiply-add throughput of this GPU in flop/s (2 per DFMA),
+ * measured by a dependent-chain microbenchmark on `cuda_stream`. */
+int masw_fp64_peak(void* cuda_stream, double* flops);
+
+/* Number of streaming multiprocessors of the current device. */
+int masw_sm_count(int32_t* sms);
+
+const char* masw_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MASW_H */

@@ -1,0 +1,817 @@
+// masw_api.cu -- the C ABI of libmasw (include/masw.h): batch state, input
+// validation, device layout, launch plans, CUDA-graph replay and autotuning.
+//
+// Device layout of a batch (all batch-owned, allocated once at create):
+//   layers      [records][8] f64: h, mu = rho beta^2, rho, 1/alpha^2,
+//               1/beta^2, beta, alpha/beta, 0 (one 64-byte line per layer;
+//               each model has N finite records then its half-space)
+//   model_loff  [M+1] i32 record offsets;  model_woff [M+1] i32 item offsets
+//   model_nlim  [M] i32 grid points below the half-space shear speed
+//   k           [items] f64 2 pi / lambda;  item_model [items] i32
+//   order       [items] i32 processing order (longest predicted scan first)
+//   ct, idx, status [items] results of the last scan
+// plus lazily allocated buffers for roots, gradient rows and misfits.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/masw.h"
+#include "masw_device.cuh"
+#include "masw_internal.h"
+
+using namespace masw;
+
+struct masw_batch {
+    int32_t n_models = 0;
+    int64_t n_items = 0;
+    int64_t n_records = 0;
+    int32_t max_layers = 0;
+    int64_t grad_len = 0;
+    masw_grid grid{};
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+
+    std::vector<int32_t> n_layers, n_lambda, loff, woff, nlim, item_model;
+    std::vector<double> lambda, kvec;
+    std::vector<int32_t> order_sorted, order_natural;
+    std::vector<int64_t> grad_off;
+
+    double* d_layers = nullptr;
+    int32_t* d_loff = nullptr;
+    int32_t* d_woff = nullptr;
+    int32_t* d_nlim = nullptr;
+    double* d_k = nullptr;
+    int32_t* d_item_model = nullptr;
+    int32_t* d_order_sorted = nullptr;
+    int32_t* d_order_natural = nullptr;
+    int64_t* d_grad_off = nullptr;
+    int32_t* d_counter = nullptr;
+    double* d_ct = nullptr;
+    int32_t* d_idx = nullptr;
+    int32_t* d_status = nullptr;
+    // lazily allocated
+    double* d_croot = nullptr;
+    double* d_rows = nullptr;
+    double* d_bs = nullptr;
+    double* d_dphi = nullptr;
+    double* d_ce = nullptr;
+    double* d_misfit = nullptr;
+    double* d_gb = nullptr;
+    double* d_gh = nullptr;
+
+    masw_plan plan{};
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    float last_ms = 0.f;
+
+    DevBatch dev(bool ordered) const {
+        DevBatch b;
+        b.layers = d_layers;
+        b.model_loff = d_loff;
+        b.model_nlim = d_nlim;
+        b.model_woff = d_woff;
+        b.k = d_k;
+        b.item_model = d_item_model;
+        b.order = ordered ? d_order_sorted : d_order_natural;
+        b.grad_off = d_grad_off;
+        b.n_models = n_models;
+        b.n_items = (int32_t)n_items;
+        b.c0 = grid.c0;
+        b.dc = grid.dc;
+        b.n_c = grid.n_c;
+        return b;
+    }
+};
+
+// ------------------------------------------------------------- helpers
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) {                \
+            record_cuda_error(e_, #x, __LINE__); \
+            return MASW_ECUDA;                  \
+        }                                       \
+    } while (0)
+
+static thread_local char g_last_cuda[256] = "";
+
+static void record_cuda_error(cudaError_t e, const char* what, int line) {
+    snprintf(g_last_cuda, sizeof(g_last_cuda), "%s (%s) at masw_api.cu:%d", cudaGetErrorString(e),
+             what, line);
+}
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static int dev_alloc(T** p, size_t n) {
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return MASW_ENOMEM;
+    }
+    return MASW_OK;
+}
+
+template <typename T>
+static int fetch(std::vector<T>& dst, const T* src, size_t n, bool device) {
+    dst.resize(n);
+    if (n == 0) return MASW_OK;
+    if (!src) return MASW_EINVAL;
+    if (device) {
+        CK(cudaMemcpy(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(dst.data(), src, n * sizeof(T));
+    }
+    return MASW_OK;
+}
+
+// Copy n elements from a batch buffer to a caller buffer (host or device).
+template <typename T>
+static int copy_out(T* dst, const T* src, size_t n, cudaStream_t s, bool* need_sync) {
+    if (!dst || n == 0) return MASW_OK;
+    if (is_device_ptr(dst)) {
+        CK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    } else {
+        CK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+        *need_sync = true;
+    }
+    return MASW_OK;
+}
+
+template <typename T>
+static int copy_in(T* dst, const T* src, size_t n, cudaStream_t s) {
+    if (n == 0) return MASW_OK;
+    if (!src) return MASW_EINVAL;
+    cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(T), kind, s));
+    if (kind == cudaMemcpyHostToDevice) CK(cudaStreamSynchronize(s));  // caller may reuse src
+    return MASW_OK;
+}
+
+static double grid_v(const masw_grid& g, int n) { return std::fma((double)n, g.dc, g.c0); }
+
+// Number of grid points with V[n] < beta_hs (same rounding as the device).
+static int32_t scan_limit(const masw_grid& g, double beta_hs) {
+    double est = std::floor((beta_hs - g.c0) / g.dc);
+    int64_t n = (int64_t)std::max(0.0, std::min(est, (double)g.n_c));
+    while (n > 0 && !(grid_v(g, (int)(n - 1)) < beta_hs)) --n;
+    while (n < g.n_c && grid_v(g, (int)n) < beta_hs) ++n;
+    return (int32_t)n;
+}
+
+static bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+static int validate_layers(const std::vector<int32_t>& nl, const std::vector<double>& h,
+                           const std::vector<double>& a, const std::vector<double>& b,
+                           const std::vector<double>& r) {
+    size_t ih = 0, il = 0;
+    for (size_t m = 0; m < nl.size(); ++m) {
+        for (int i = 0; i < nl[m]; ++i)
+            if (!finite_pos(h[ih++])) return MASW_EINVAL;
+        for (int i = 0; i <= nl[m]; ++i, ++il) {
+            if (!finite_pos(a[il]) || !finite_pos(b[il]) || !finite_pos(r[il])) return MASW_EINVAL;
+            // positive bulk modulus: alpha^2 > 4/3 beta^2 (also keeps r != s)
+            if (!(3.0 * a[il] * a[il] > 4.0 * b[il] * b[il])) return MASW_EINVAL;
+        }
+    }
+    return MASW_OK;
+}
+
+static void build_records(masw_batch* B, const std::vector<double>& h, const std::vector<double>& a,
+                          const std::vector<double>& b, const std::vector<double>& r,
+                          std::vector<double>& rec) {
+    rec.assign((size_t)B->n_records * LAYER_STRIDE, 0.0);
+    size_t ih = 0, il = 0;
+    for (int32_t m = 0; m < B->n_models; ++m) {
+        int N = B->n_layers[m];
+        for (int i = 0; i <= N; ++i, ++il) {
+            double* L = &rec[il * LAYER_STRIDE];
+            L[L_H] = (i < N) ? h[ih++] : 0.0;
+            L[L_MU] = r[il] * b[il] * b[il];
+            L[L_RHO] = r[il];
+            L[L_IA2] = 1.0 / (a[il] * a[il]);
+            L[L_IB2] = 1.0 / (b[il] * b[il]);
+            L[L_BETA] = b[il];
+            L[L_RATIO] = a[il] / b[il];
+        }
+    }
+}
+
+// Predicted scan length of an item (speed only): the first root sits near
+// 0.93 x the shear speed at depth ~ lambda/2.
+static double predicted_cost(const masw_batch* B, int32_t m, double lam,
+                             const std::vector<double>& h, const std::vector<double>& b,
+                             size_t h0, size_t l0) {
+    int N = B->n_layers[m];
+    double depth = 0.5 * lam, z = 0.0, be = b[l0 + N];
+    for (int i = 0; i < N; ++i) {
+        z += h[h0 + i];
+        if (z >= depth) { be = b[l0 + i]; break; }
+    }
+    double n = (0.93 * be - B->grid.c0) / B->grid.dc;
+    n = std::max(1.0, std::min(n, (double)B->nlim[m]));
+    return (n + 32.0) * (N + 1);
+}
+
+static void free_batch(masw_batch* B) {
+    if (!B) return;
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    if (B->ev0) cudaEventDestroy(B->ev0);
+    if (B->ev1) cudaEventDestroy(B->ev1);
+    void* ptrs[] = {B->d_layers, B->d_loff,  B->d_woff,  B->d_nlim,   B->d_k,
+                    B->d_item_model, B->d_order_sorted, B->d_order_natural, B->d_grad_off,
+                    B->d_counter, B->d_ct, B->d_idx, B->d_status, B->d_croot, B->d_rows, B->d_bs,
+                    B->d_dphi, B->d_ce, B->d_misfit, B->d_gb, B->d_gh};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete B;
+}
+
+static masw_plan default_plan(const masw_batch* B) {
+    masw_plan p;
+    p.warps_per_block = 8;
+    p.cpl = 1;
+    p.blocks_per_sm = 3;
+    p.persistent = 1;
+    p.ordered = 1;
+    p.stage_layers = std::min(B->max_layers + 1, 32);
+    p.use_graph = 1;
+    return p;
+}
+
+static bool plan_ok(const masw_plan& p) {
+    bool wpb = p.warps_per_block == 1 || p.warps_per_block == 2 || p.warps_per_block == 4 ||
+               p.warps_per_block == 8;
+    bool cpl = p.cpl == 1 || p.cpl == 2 || p.cpl == 4;
+    return wpb && cpl && p.blocks_per_sm >= 1 && p.blocks_per_sm <= 32 && p.stage_layers >= 0 &&
+           p.stage_layers <= MASW_MAX_LAYERS + 1 &&
+           (size_t)p.warps_per_block * p.stage_layers * LAYER_STRIDE * sizeof(double) <= 48 * 1024;
+}
+
+static ScanPlan to_scan_plan(const masw_batch* B, const masw_plan& p) {
+    ScanPlan s;
+    s.warps_per_block = p.warps_per_block;
+    s.cpl = p.cpl;
+    s.blocks = p.blocks_per_sm * B->sm_count;
+    s.persistent = p.persistent;
+    s.stage_layers = p.stage_layers;
+    return s;
+}
+
+// Enqueue one full scan (all items) with the given plan on stream s.
+static cudaError_t enqueue_scan(masw_batch* B, const masw_plan& p, cudaStream_t s) {
+    if (p.persistent) {
+        cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(int32_t), s);
+        if (e != cudaSuccess) return e;
+    }
+    ScanOut o{B->d_ct, B->d_idx, B->d_status};
+    return launch_scan(B->dev(p.ordered != 0), o, to_scan_plan(B, p), B->d_counter, 0,
+                       (int)B->n_items, s);
+}
+
+static int rebuild_graph(masw_batch* B) {
+    if (B->graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+    }
+    if (!B->plan.use_graph) return MASW_OK;
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e2 = enqueue_scan(B, B->plan, cap);
+        e = cudaStreamEndCapture(cap, &g);
+        if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&B->graph, g, 0);
+        cudaGraphDestroy(g);
+    }
+    cudaStreamDestroy(cap);
+    CK(e);
+    return MASW_OK;
+}
+
+// Run Algorithm 1 over the whole batch into the batch-owned outputs.
+static int run_scan(masw_batch* B) {
+    CK(cudaEventRecord(B->ev0, B->stream));
+    if (B->plan.use_graph && B->graph) {
+        CK(cudaGraphLaunch(B->graph, B->stream));
+    } else {
+        CK(enqueue_scan(B, B->plan, B->stream));
+    }
+    CK(cudaEventRecord(B->ev1, B->stream));
+    return MASW_OK;
+}
+
+static int ensure(double** p, size_t n) { return *p ? MASW_OK : dev_alloc(p, n); }
+
+// ------------------------------------------------------------- the ABI
+
+extern "C" {
+
+const char* masw_strerror(int code) {
+    switch (code) {
+        case MASW_OK: return "ok";
+        case MASW_EINVAL: return "invalid argument or model";
+        case MASW_ENOMEM: return "out of memory";
+        case MASW_EADMIT: return "request refused by the admission cap";
+        case MASW_ECUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA runtime error";
+        case MASW_ETIMEOUT: return "bounded wait timed out";
+        case MASW_EAGAIN: return "result not ready";
+        default: return "unknown error code";
+    }
+}
+
+int masw_sm_count(int32_t* sms) {
+    if (!sms) return MASW_EINVAL;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    int n = 0;
+    CK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    *sms = n;
+    return MASW_OK;
+}
+
+int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, void* cuda_stream,
+                            masw_batch** out) {
+    if (!md || !grid || !out) return MASW_EINVAL;
+    if (md->n_models < 1 || (md->mem_space != MASW_HOST && md->mem_space != MASW_DEVICE))
+        return MASW_EINVAL;
+    if (!(std::isfinite(grid->c0) && grid->c0 > 0.0 && std::isfinite(grid->dc) && grid->dc > 0.0 &&
+          grid->n_c >= 2))
+        return MASW_EINVAL;
+    bool dev = md->mem_space == MASW_DEVICE;
+    masw_batch* B = new (std::nothrow) masw_batch();
+    if (!B) return MASW_ENOMEM;
+    B->grid = *grid;
+    B->stream = (cudaStream_t)cuda_stream;
+    B->n_models = md->n_models;
+    int rc;
+    if ((rc = fetch(B->n_layers, md->n_layers, md->n_models, dev)) ||
+        (rc = fetch(B->n_lambda, md->n_lambda, md->n_models, dev))) {
+        free_batch(B);
+        return rc;
+    }
+    int64_t nh = 0, nl = 0, nw = 0;
+    for (int32_t m = 0; m < B->n_models; ++m) {
+        if (B->n_layers[m] < 0 || B->n_layers[m] > MASW_MAX_LAYERS || B->n_lambda[m] < 0) {
+            free_batch(B);
+            return MASW_EINVAL;
+        }
+        nh += B->n_layers[m];
+        nl += B->n_layers[m] + 1;
+        nw += B->n_lambda[m];
+        B->max_layers = std::max(B->max_layers, B->n_layers[m]);
+    }
+    if (nw > INT32_MAX / 2 || nl > INT32_MAX / 2) {
+        free_batch(B);
+        return MASW_EINVAL;
+    }
+    B->n_records = nl;
+    B->n_items = nw;
+    std::vector<double> h, a, b, r;
+    if ((rc = fetch(h, md->h, nh, dev)) || (rc = fetch(a, md->alpha, nl, dev)) ||
+        (rc = fetch(b, md->beta, nl, dev)) || (rc = fetch(r, md->rho, nl, dev)) ||
+        (rc = fetch(B->lambda, md->lambda, nw, dev))) {
+        free_batch(B);
+        return rc;
+    }
+    if ((rc = validate_layers(B->n_layers, h, a, b, r))) {
+        free_batch(B);
+        return rc;
+    }
+    for (double lam : B->lambda)
+        if (!finite_pos(lam)) {
+            free_batch(B);
+            return MASW_EINVAL;
+        }
+    // offsets, limits, items
+    B->loff.assign(B->n_models + 1, 0);
+    B->woff.assign(B->n_models + 1, 0);
+    B->nlim.assign(B->n_models, 0);
+    std::vector<size_t> hoff(B->n_models + 1, 0);
+    for (int32_t m = 0; m < B->n_models; ++m) {
+        B->loff[m + 1] = B->loff[m] + B->n_layers[m] + 1;
+        B->woff[m + 1] = B->woff[m] + B->n_lambda[m];
+        hoff[m + 1] = hoff[m] + B->n_layers[m];
+        B->nlim[m] = scan_limit(B->grid, b[B->loff[m + 1] - 1]);
+    }
+    B->item_model.resize(nw);
+    B->kvec.resize(nw);
+    B->grad_off.assign(nw + 1, 0);
+    std::vector<double> cost(nw);
+    for (int32_t m = 0; m < B->n_models; ++m)
+        for (int32_t j = B->woff[m]; j < B->woff[m + 1]; ++j) {
+            B->item_model[j] = m;
+            B->kvec[j] = 2.0 * M_PI / B->lambda[j];
+            B->grad_off[j + 1] = B->grad_off[j] + 2 * B->n_layers[m] + 1;
+            cost[j] = predicted_cost(B, m, B->lambda[j], h, b, hoff[m], B->loff[m]);
+        }
+    B->grad_len = B->grad_off[nw];
+    B->order_natural.resize(nw);
+    std::iota(B->order_natural.begin(), B->order_natural.end(), 0);
+    B->order_sorted = B->order_natural;
+    std::stable_sort(B->order_sorted.begin(), B->order_sorted.end(),
+                     [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+    std::vector<double> rec;
+    build_records(B, h, a, b, r, rec);
+
+    if ((rc = masw_sm_count(&B->sm_count))) {
+        free_batch(B);
+        return rc;
+    }
+    if (dev_alloc(&B->d_layers, rec.size()) || dev_alloc(&B->d_loff, B->n_models + 1) ||
+        dev_alloc(&B->d_woff, B->n_models + 1) || dev_alloc(&B->d_nlim, B->n_models) ||
+        dev_alloc(&B->d_k, nw) || dev_alloc(&B->d_item_model, nw) ||
+        dev_alloc(&B->d_order_sorted, nw) || dev_alloc(&B->d_order_natural, nw) ||
+        dev_alloc(&B->d_grad_off, nw + 1) || dev_alloc(&B->d_counter, 1) ||
+        dev_alloc(&B->d_ct, nw) || dev_alloc(&B->d_idx, nw) || dev_alloc(&B->d_status, nw)) {
+        free_batch(B);
+        return MASW_ENOMEM;
+    }
+    auto up = [&](void* d, const void* s, size_t bytes) {
+        return bytes ? cudaMemcpy(d, s, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+    };
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = up(B->d_layers, rec.data(), rec.size() * sizeof(double));
+    if (e == cudaSuccess) e = up(B->d_loff, B->loff.data(), B->loff.size() * 4);
+    if (e == cudaSuccess) e = up(B->d_woff, B->woff.data(), B->woff.size() * 4);
+    if (e == cudaSuccess) e = up(B->d_nlim, B->nlim.data(), B->nlim.size() * 4);
+    if (e == cudaSuccess) e = up(B->d_k, B->kvec.data(), nw * 8);
+    if (e == cudaSuccess) e = up(B->d_item_model, B->item_model.data(), nw * 4);
+    if (e == cudaSuccess) e = up(B->d_order_sorted, B->order_sorted.data(), nw * 4);
+    if (e == cudaSuccess) e = up(B->d_order_natural, B->order_natural.data(), nw * 4);
+    if (e == cudaSuccess) e = up(B->d_grad_off, B->grad_off.data(), (nw + 1) * 8);
+    if (e == cudaSuccess) e = cudaEventCreate(&B->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&B->ev1);
+    if (e != cudaSuccess) {
+        record_cuda_error(e, "batch upload", __LINE__);
+        free_batch(B);
+        return MASW_ECUDA;
+    }
+    B->plan = default_plan(B);
+    if ((rc = rebuild_graph(B))) {
+        free_batch(B);
+        return rc;
+    }
+    *out = B;
+    return MASW_OK;
+}
+
+int masw_model_batch_destroy(masw_batch* B) {
+    if (!B) return MASW_EINVAL;
+    cudaStreamSynchronize(B->stream);
+    free_batch(B);
+    return MASW_OK;
+}
+
+int masw_model_batch_update(masw_batch* B, const double* h, const double* alpha, const double* beta,
+                            const double* rho, int32_t mem_space) {
+    if (!B || (mem_space != MASW_HOST && mem_space != MASW_DEVICE)) return MASW_EINVAL;
+    bool dev = mem_space == MASW_DEVICE;
+    int64_t nh = B->n_records - B->n_models;
+    std::vector<double> hv, a, b, r;
+    int rc;
+    if ((rc = fetch(hv, h, nh, dev)) || (rc = fetch(a, alpha, B->n_records, dev)) ||
+        (rc = fetch(b, beta, B->n_records, dev)) || (rc = fetch(r, rho, B->n_records, dev)))
+        return rc;
+    if ((rc = validate_layers(B->n_layers, hv, a, b, r))) return rc;
+    std::vector<int32_t> nlim(B->n_models);
+    for (int32_t m = 0; m < B->n_models; ++m) nlim[m] = scan_limit(B->grid, b[B->loff[m + 1] - 1]);
+    std::vector<double> rec;
+    build_records(B, hv, a, b, r, rec);
+    // the upload is ordered after work already queued on the batch stream
+    CK(cudaStreamSynchronize(B->stream));
+    CK(cudaMemcpy(B->d_layers, rec.data(), rec.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(B->d_nlim, nlim.data(), nlim.size() * 4, cudaMemcpyHostToDevice));
+    B->nlim = nlim;
+    return MASW_OK;
+}
+
+int masw_batch_info(const masw_batch* B, int64_t* n_items, int32_t* n_models, int32_t* max_layers) {
+    if (!B) return MASW_EINVAL;
+    if (n_items) *n_items = B->n_items;
+    if (n_models) *n_models = B->n_models;
+    if (max_layers) *max_layers = B->max_layers;
+    return MASW_OK;
+}
+
+static int finish_outputs(masw_batch* B, double* ct, int32_t* idx, int32_t* status) {
+    bool sync = false;
+    int rc;
+    if ((rc = copy_out(ct, B->d_ct, B->n_items, B->stream, &sync)) ||
+        (rc = copy_out(idx, B->d_idx, B->n_items, B->stream, &sync)) ||
+        (rc = copy_out(status, B->d_status, B->n_items, B->stream, &sync)))
+        return rc;
+    if (sync) CK(cudaStreamSynchronize(B->stream));
+    return MASW_OK;
+}
+
+int masw_dispersion(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* status,
+                    int32_t out_mem_space) {
+    if (!B || (out_mem_space != MASW_HOST && out_mem_space != MASW_DEVICE)) return MASW_EINVAL;
+    int rc = run_scan(B);
+    if (rc) return rc;
+    return finish_outputs(B, ct, ct_idx, status);
+}
+
+int masw_dispersion_plain(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* status,
+                          int32_t out_mem_space) {
+    if (!B || (out_mem_space != MASW_HOST && out_mem_space != MASW_DEVICE)) return MASW_EINVAL;
+    masw_plan p = B->plan;
+    p.persistent = 0;
+    p.ordered = 0;
+    ScanOut o{B->d_ct, B->d_idx, B->d_status};
+    DevBatch d = B->dev(false);
+    ScanPlan sp = to_scan_plan(B, p);
+    CK(cudaEventRecord(B->ev0, B->stream));
+    for (int32_t m = 0; m < B->n_models; ++m) {
+        CK(launch_scan(d, o, sp, B->d_counter, B->woff[m], B->woff[m + 1], B->stream));
+        CK(cudaStreamSynchronize(B->stream));
+    }
+    CK(cudaEventRecord(B->ev1, B->stream));
+    return finish_outputs(B, ct, ct_idx, status);
+}
+
+int masw_last_scan_ms(const masw_batch* B, float* ms) {
+    if (!B || !ms) return MASW_EINVAL;
+    CK(cudaEventSynchronize(B->ev1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, B->ev0, B->ev1));
+    *ms = t;
+    return MASW_OK;
+}
+
+int masw_misfit(masw_batch* B, const double* ce, int32_t kind, double sigma, double* misfit) {
+    if (!B || !ce || !misfit || (kind != MASW_MISFIT_PAPER && kind != MASW_MISFIT_LSQ))
+        return MASW_EINVAL;
+    if (kind == MASW_MISFIT_LSQ && !(sigma > 0.0 && std::isfinite(sigma))) return MASW_EINVAL;
+    int rc;
+    if ((rc = ensure(&B->d_ce, B->n_items)) || (rc = ensure(&B->d_misfit, B->n_models))) return rc;
+    if ((rc = copy_in(B->d_ce, ce, B->n_items, B->stream))) return rc;
+    if ((rc = run_scan(B))) return rc;
+    CK(launch_misfit(B->dev(false), B->d_ct, B->d_ce, kind, sigma, B->d_misfit, nullptr, B->stream));
+    bool sync = false;
+    if ((rc = copy_out(misfit, B->d_misfit, B->n_models, B->stream, &sync))) return rc;
+    if (sync) CK(cudaStreamSynchronize(B->stream));
+    return MASW_OK;
+}
+
+static int run_roots(masw_batch* B) {
+    int rc;
+    if ((rc = ensure(&B->d_croot, B->n_items))) return rc;
+    if ((rc = run_scan(B))) return rc;
+    CK(launch_refine(B->dev(false), B->d_idx, 1e-13, B->d_croot, B->stream));
+    return MASW_OK;
+}
+
+static int run_root_grad(masw_batch* B) {
+    int rc;
+    if ((rc = ensure(&B->d_rows, B->grad_len)) ||
+        (rc = ensure(&B->d_bs, 4 * (B->grad_len - B->n_items) + 1)))
+        return rc;
+    if ((rc = run_roots(B))) return rc;
+    CK(launch_root_grad(B->dev(false), B->d_croot, B->d_rows, B->d_bs, B->stream));
+    return MASW_OK;
+}
+
+int masw_roots(masw_batch* B, double* croot) {
+    if (!B || !croot) return MASW_EINVAL;
+    int rc = run_roots(B);
+    if (rc) return rc;
+    bool sync = false;
+    if ((rc = copy_out(croot, B->d_croot, B->n_items, B->stream, &sync))) return rc;
+    if (sync) CK(cudaStreamSynchronize(B->stream));
+    return MASW_OK;
+}
+
+int masw_root_grad(masw_batch* B, double* rows, int64_t* row_len_total) {
+    if (!B) return MASW_EINVAL;
+    if (row_len_total) *row_len_total = B->grad_len;
+    if (!rows) return MASW_OK;
+    int rc = run_root_grad(B);
+    if (rc) return rc;
+    bool sync = false;
+    if ((rc = copy_out(rows, B->d_rows, B->grad_len, B->stream, &sync))) return rc;
+    if (sync) CK(cudaStreamSynchronize(B->stream));
+    return MASW_OK;
+}
+
+int masw_misfit_grad(masw_batch* B, const double* ce, int32_t kind, double sigma, double* misfit,
+                     double* grad_beta, double* grad_h) {
+    if (!B || !ce || !misfit || (kind != MASW_MISFIT_PAPER && kind != MASW_MISFIT_LSQ))
+        return MASW_EINVAL;
+    if (kind == MASW_MISFIT_LSQ && !(sigma > 0.0 && std::isfinite(sigma))) return MASW_EINVAL;
+    int rc;
+    if ((rc = ensure(&B->d_ce, B->n_items)) || (rc = ensure(&B->d_misfit, B->n_models)) ||
+        (rc = ensure(&B->d_dphi, B->n_items)) || (rc = ensure(&B->d_gb, B->n_records)) ||
+        (rc = ensure(&B->d_gh, B->n_records - B->n_models)))
+        return rc;
+    if ((rc = copy_in(B->d_ce, ce, B->n_items, B->stream))) return rc;
+    if ((rc = run_root_grad(B))) return rc;
+    DevBatch d = B->dev(false);
+    CK(launch_misfit(d, B->d_croot, B->d_ce, kind, sigma, B->d_misfit, B->d_dphi, B->stream));
+    CK(launch_grad_reduce(d, B->d_rows, B->d_dphi, B->d_gb, B->d_gh, B->stream));
+    bool sync = false;
+    if ((rc = copy_out(misfit, B->d_misfit, B->n_models, B->stream, &sync)) ||
+        (rc = copy_out(grad_beta, B->d_gb, B->n_records, B->stream, &sync)) ||
+        (rc = copy_out(grad_h, B->d_gh, B->n_records - B->n_models, B->stream, &sync)))
+        return rc;
+    if (sync) CK(cudaStreamSynchronize(B->stream));
+    return MASW_OK;
+}
+
+int masw_det_eval(masw_batch* B, int32_t n, const int32_t* item, const double* c, int32_t* sign,
+                  double* log_abs) {
+    if (!B || n < 0 || (n > 0 && (!item || !c || !sign || !log_abs))) return MASW_EINVAL;
+    if (n == 0) return MASW_OK;
+    int32_t *d_item = nullptr, *d_sign = nullptr;
+    double *d_c = nullptr, *d_la = nullptr;
+    int rc = MASW_OK;
+    if (dev_alloc(&d_item, n) || dev_alloc(&d_sign, n) || dev_alloc(&d_c, n) || dev_alloc(&d_la, n))
+        rc = MASW_ENOMEM;
+    bool sync = false;
+    if (!rc) rc = copy_in(d_item, item, n, B->stream);
+    if (!rc) rc = copy_in(d_c, c, n, B->stream);
+    if (!rc) {
+        cudaError_t e = launch_det_eval(B->dev(false), n, d_item, d_c, d_sign, d_la, B->stream);
+        if (e != cudaSuccess) {
+            record_cuda_error(e, "det_eval", __LINE__);
+            rc = MASW_ECUDA;
+        }
+    }
+    if (!rc) rc = copy_out(sign, d_sign, n, B->stream, &sync);
+    if (!rc) rc = copy_out(log_abs, d_la, n, B->stream, &sync);
+    cudaError_t e = cudaStreamSynchronize(B->stream);
+    if (!rc && e != cudaSuccess) {
+        record_cuda_error(e, "det_eval sync", __LINE__);
+        rc = MASW_ECUDA;
+    }
+    cudaFree(d_item);
+    cudaFree(d_sign);
+    cudaFree(d_c);
+    cudaFree(d_la);
+    return rc;
+}
+
+int masw_get_plan(const masw_batch* B, masw_plan* plan) {
+    if (!B || !plan) return MASW_EINVAL;
+    *plan = B->plan;
+    return MASW_OK;
+}
+
+int masw_set_plan(masw_batch* B, const masw_plan* plan) {
+    if (!B || !plan || !plan_ok(*plan)) return MASW_EINVAL;
+    CK(cudaStreamSynchronize(B->stream));
+    B->plan = *plan;
+    return rebuild_graph(B);
+}
+
+// ----------------------------------------------------------- autotuner
+
+namespace {
+std::mutex g_cache_mu;
+std::map<std::tuple<int, int, int>, masw_plan> g_cache;
+bool g_cache_loaded = false;
+
+std::tuple<int, int, int> cache_key(const masw_batch* B) {
+    int bucket = 0;
+    for (int64_t n = B->n_items; n > 1; n >>= 1) ++bucket;
+    return {B->max_layers, B->grid.n_c, bucket};
+}
+
+void load_cache_file() {
+    if (g_cache_loaded) return;
+    g_cache_loaded = true;
+    const char* path = getenv("MASW_PLAN_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    int a, b, c;
+    masw_plan p;
+    while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d", &a, &b, &c, &p.warps_per_block, &p.cpl,
+                  &p.blocks_per_sm, &p.persistent, &p.ordered, &p.stage_layers, &p.use_graph) == 10)
+        if (plan_ok(p)) g_cache[{a, b, c}] = p;
+    fclose(f);
+}
+
+void save_cache_file() {
+    const char* path = getenv("MASW_PLAN_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "w");
+    if (!f) return;
+    for (auto& kv : g_cache) {
+        const masw_plan& p = kv.second;
+        fprintf(f, "%d %d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                std::get<2>(kv.first), p.warps_per_block, p.cpl, p.blocks_per_sm, p.persistent,
+                p.ordered, p.stage_layers, p.use_graph);
+    }
+    fclose(f);
+}
+}  // namespace
+
+int masw_autotune(masw_batch* B, int32_t reps, masw_plan* best) {
+    if (!B || reps < 1) return MASW_EINVAL;
+    auto key = cache_key(B);
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        load_cache_file();
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) {
+            int rc = masw_set_plan(B, &it->second);
+            if (rc) return rc;
+            if (best) *best = it->second;
+            return MASW_OK;
+        }
+    }
+    std::vector<masw_plan> cands;
+    int stage = std::min(B->max_layers + 1, 32);
+    for (int wpb : {2, 4, 8})
+        for (int cpl : {1, 2})
+            for (int bps : {2, 4, 8, 16}) {
+                masw_plan p{wpb, cpl, bps, 1, 1, stage, 1};
+                if (plan_ok(p)) cands.push_back(p);
+            }
+    masw_plan flat{8, 1, 1, 0, 1, stage, 1};
+    if (plan_ok(flat)) cands.push_back(flat);
+    float best_ms = 1e30f;
+    masw_plan bestp = B->plan;
+    for (const masw_plan& p : cands) {
+        int rc = masw_set_plan(B, &p);
+        if (rc) return rc;
+        if ((rc = run_scan(B))) return rc;  // warm-up
+        float tot = 0.f;
+        for (int r = 0; r < reps; ++r) {
+            if ((rc = run_scan(B))) return rc;
+            float ms;
+            if ((rc = masw_last_scan_ms(B, &ms))) return rc;
+            tot += ms;
+        }
+        if (tot / reps < best_ms) {
+            best_ms = tot / reps;
+            bestp = p;
+        }
+    }
+    int rc = masw_set_plan(B, &bestp);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        g_cache[key] = bestp;
+        save_cache_file();
+    }
+    if (best) *best = bestp;
+    return MASW_OK;
+}
+
+int masw_fp64_peak(void* cuda_stream, double* flops) {
+    if (!flops) return MASW_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int32_t sms = 0;
+    int rc = masw_sm_count(&sms);
+    if (rc) return rc;
+    double* sink = nullptr;
+    if (dev_alloc(&sink, 4096)) return MASW_ENOMEM;
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    const int threads = 256, iters = 2048;
+    const int blocks = sms * 8;
+    float ms = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+        CK(cudaEventRecord(a, s));
+        CK(launch_fp64_peak(blocks, threads, iters, sink, s));
+        CK(cudaEventRecord(b, s));
+        CK(cudaEventSynchronize(b));
+        CK(cudaEventElapsedTime(&ms, a, b));
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    double dfma = (double)blocks * threads * iters * 16.0 * 8.0;
+    *flops = 2.0 * dfma / (ms * 1e-3);
+    return MASW_OK;
+}
+
+}  // extern "C"

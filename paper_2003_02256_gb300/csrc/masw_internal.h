@@ -1,0 +1,55 @@
+// masw_internal.h -- device-side data layout and kernel launchers shared by
+// the C-ABI layer (masw_api.cu) and the kernels (masw_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace masw {
+
+// Device view of a ragged model batch.
+struct DevBatch {
+    const double* layers;      // [n_records][LAYER_STRIDE] records, per model N finite + 1 half-space
+    const int32_t* model_loff; // [n_models + 1] record offsets
+    const int32_t* model_nlim; // [n_models] number of grid points below beta_halfspace
+    const int32_t* model_woff; // [n_models + 1] item offsets (items of model m are contiguous)
+    const double* k;           // [n_items] wavenumber 2*pi/lambda
+    const int32_t* item_model; // [n_items]
+    const int32_t* order;      // [n_items] item ids in processing order
+    const int64_t* grad_off;   // [n_items + 1] offsets of per-item gradient rows (2N+1 each)
+    int32_t n_models;
+    int32_t n_items;
+    double c0, dc;
+    int32_t n_c;
+};
+
+struct ScanOut {
+    double* ct;
+    int32_t* idx;
+    int32_t* status;
+};
+
+// Launch configuration of the scan (the batch plan).
+struct ScanPlan {
+    int warps_per_block;  // 1..32
+    int cpl;              // test velocities per lane per chunk: 1, 2 or 4
+    int blocks;           // grid size (persistent: multiple of the SM count)
+    int persistent;       // 1: warps pop items from a queue; 0: one item per warp
+    int stage_layers;     // layer records staged in shared memory per warp (0 = read global)
+};
+
+cudaError_t launch_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p, int32_t* counter,
+                        int item_begin, int item_end, cudaStream_t s);
+cudaError_t launch_det_eval(const DevBatch& b, int n, const int32_t* item, const double* c,
+                            int32_t* sign, double* log_abs, cudaStream_t s);
+cudaError_t launch_refine(const DevBatch& b, const int32_t* idx, double rel_tol, double* croot,
+                          cudaStream_t s);
+cudaError_t launch_root_grad(const DevBatch& b, const double* croot, double* rows, double* bs,
+                             cudaStream_t s);
+cudaError_t launch_misfit(const DevBatch& b, const double* ct, const double* ce, int kind,
+                          double sigma, double* misfit, double* dphi_dc, cudaStream_t s);
+cudaError_t launch_grad_reduce(const DevBatch& b, const double* rows, const double* dphi_dc,
+                               double* grad_beta, double* grad_h, cudaStream_t s);
+cudaError_t launch_fp64_peak(int blocks, int threads, int iters, double* sink, cudaStream_t s);
+
+}  // namespace masw

@@ -1,0 +1,50 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every entry point that include/masw.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "masw.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(masw_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2003_02256_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("masw_model_batch_create", "masw_model_batch_destroy", "masw_dispersion",
+                     "masw_misfit", "masw_misfit_grad", "masw_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_needs_no_gpu(lib):
+    lib.masw_strerror.restype = ctypes.c_char_p
+    assert lib.masw_strerror(0) == b"ok"
+    assert b"invalid" in lib.masw_strerror(1)
+    assert lib.masw_strerror(999) == b"unknown error code"
+
+
+def test_null_arguments_are_rejected_without_touching_the_gpu(lib):
+    f = lib.masw_model_batch_create
+    f.restype = ctypes.c_int
+    assert f(None, None, None, None) == 1
+    assert lib.masw_dispersion(None, None, None, None, 0) == 1
+    assert lib.masw_misfit(None, None, 0, ctypes.c_double(1.0), None) == 1
