@@ -192,10 +192,54 @@ cudaError_t launch_refine(const DevBatch& b, const int32_t* idx, double rel_tol,
 
 // ------------------------------------------------------------- root grad
 
+// 2x2 helpers for the (cold) adjoint path: general matrices m = {a, b, c, d}
+// = [[a, b], [c, d]].
+struct M2 { double a, b, c, d; };
+__device__ __forceinline__ M2 mmul(M2 x, M2 y) {
+    return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
+}
+__device__ __forceinline__ M2 madd(M2 x, M2 y) { return {x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d}; }
+__device__ __forceinline__ M2 msub(M2 x, M2 y) { return {x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d}; }
+__device__ __forceinline__ double mdet(M2 x) { return x.a * x.d - x.b * x.c; }
+// x^-1 y
+__device__ __forceinline__ M2 msolve(M2 x, M2 y) {
+    double id = 1.0 / mdet(x);
+    M2 adj = {x.d * id, -x.b * id, -x.c * id, x.a * id};
+    return mmul(adj, y);
+}
+__device__ __forceinline__ void mvsolve(M2 x, double v0, double v1, double* o0, double* o1) {
+    double id = 1.0 / mdet(x);
+    *o0 = (x.d * v0 - x.b * v1) * id;
+    *o1 = (-x.c * v0 + x.a * v1) * id;
+}
+__device__ __forceinline__ void ld(const double* p, M2* m) { *m = {p[0], p[1], p[2], p[3]}; }
+__device__ __forceinline__ void st(double* p, M2 m) { p[0] = m.a; p[1] = m.b; p[2] = m.c; p[3] = m.d; }
+
+// Element blocks of layer j at (k, c), k dropped: K11, K12 (K22 and K21 follow
+// from the layer's symmetry: K22 = [[A, -B], [-B, Dd]], K21 = K12^T).
+__device__ __forceinline__ void elem_blocks(const double* L, double k, double c2, M2* K11, M2* K12,
+                                            M2* K21, M2* K22) {
+    LayerNum n = layer_numerators(L, k, c2);
+    double id = 1.0 / n.Dh;
+    double A = n.n00 * id, B = n.n01 * id, Dd = n.n11 * id;
+    double E = n.ce * id, F = n.cf * id, G = n.cg * id;
+    *K11 = {A, B, B, Dd};
+    *K22 = {A, -B, -B, Dd};
+    *K12 = {E, F, -F, G};
+    *K21 = {E, -F, F, G};
+}
+
 // One thread per item. Row layout: dC/dbeta_0..beta_N, dC/dh_0..h_{N-1}.
-// `bs` holds 8 doubles per finite layer of the item (the Schur block, the
-// coupling numerators, the back-substitution factor and the scale exponent);
-// the item's slice starts at 4 * (grad_off[item] - item) = 8 * sum of N.
+// The null vector u of K(C*) comes from a twisted block factorization: a
+// top-down Schur sweep (S_j = P_j + K11_j) and a bottom-up one (B_j, the
+// stiffness of everything below node j condensed onto it); at every node the
+// condensed block G_j = P_j + B_j is singular at the root, and the node
+// where it is most singular (relative to its size) carries the largest
+// amplitude. u starts there and is propagated upward with the top-down
+// factors and downward with the bottom-up ones, so it only ever decays and
+// neither a thick top layer (mode confined to the surface) nor a deep one
+// breaks it. `bs` holds 16 doubles per node of the item, starting at
+// 8 * grad_off[item] + 8 * item = 16 * (sum of (N+1) of earlier items).
 __global__ void __launch_bounds__(64) root_grad_kernel(DevBatch b, const double* __restrict__ croot,
                                                        double* rows, double* bs) {
     int it = blockIdx.x * blockDim.x + threadIdx.x;
@@ -204,7 +248,7 @@ __global__ void __launch_bounds__(64) root_grad_kernel(DevBatch b, const double*
     int lo_rec = b.model_loff[m];
     int N = b.model_loff[m + 1] - lo_rec - 1;
     double* row = rows + b.grad_off[it];
-    double* sc8 = bs + 4 * (b.grad_off[it] - it);
+    double* ws = bs + 8 * b.grad_off[it] + 8 * (int64_t)it;
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
     double c = croot[it];
     if (!(c == c)) {
@@ -214,73 +258,93 @@ __global__ void __launch_bounds__(64) root_grad_kernel(DevBatch b, const double*
     const double* lay = b.layers + (size_t)lo_rec * LAYER_STRIDE;
     double k = b.k[it];
     double c2 = c * c;
-
-    // Forward block elimination at C*, keeping what back-substitution needs.
-    HState st{0.0, 0.0, 0.0, 1.0};
+    // node j slot: [0..3] S_j (top-down), [4..7] M_j = B_{j+1} + K22_j,
+    //              [8..11] B_j (bottom-up), [12..15] P_j
+    M2 P = {0.0, 0.0, 0.0, 0.0};
     for (int j = 0; j < N; ++j) {
-        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2);
-        double w = st.w;
-        bool ok;
-        double* r8 = sc8 + 8 * j;
-        double det = schur_layer(st, n, &ok, r8);
-        r8[3] = n.ce; r8[4] = n.cf; r8[5] = n.cg;
-        r8[6] = w / det;
-        if (!ok) {
-            for (int p = 0; p < 2 * N + 1; ++p) row[p] = nan;
-            return;
-        }
+        M2 K11, K12, K21, K22;
+        elem_blocks(lay + j * LAYER_STRIDE, k, c2, &K11, &K12, &K21, &K22);
+        M2 S = madd(P, K11);
+        st(ws + 16 * j, S);
+        st(ws + 16 * j + 12, P);
+        P = msub(K22, mmul(K21, msolve(S, K12)));
     }
+    st(ws + 16 * N + 12, P);
     HalfNum hn = halfspace_numerators(lay + N * LAYER_STRIDE, c2);
-    double s00 = fma(hn.den, st.p00, st.w * hn.m00);
-    double s01 = fma(hn.den, st.p01, st.w * hn.m01);
-    double s11 = fma(hn.den, st.p11, st.w * hn.m11);
-    // null vector of the (nearly singular) last Schur block: a row of adj
-    double ux, uz;
-    if (fabs(s00) >= fabs(s11)) { ux = -s01; uz = s00; }
-    else { ux = s11; uz = -s01; }
-    double nrm = fmax(fabs(ux), fabs(uz));
-    ux /= nrm; uz /= nrm;
-
-    // half-space contribution, at scale exponent 0
-    HalfD H = halfspace_d(lay + N * LAYER_STRIDE, c);
-    D4 qh = half_quad(H, ux, uz);
-    double den = qh.d0;  // sum of u^T dK/dc u, stored at scale 2^(2 ecur)
-    row[N] = qh.d1;
-    int ecur = 0;
+    double iden = 1.0 / hn.den;
+    M2 Bv = {hn.m00 * iden, hn.m01 * iden, hn.m01 * iden, hn.m11 * iden};
+    st(ws + 16 * N + 8, Bv);
     for (int j = N - 1; j >= 0; --j) {
-        const double* r8 = sc8 + 8 * j;
-        // u_j = -fac_j adj(Shat_j) Nc_j u_{j+1}
-        double y0 = r8[3] * ux + r8[4] * uz;
-        double y1 = -r8[4] * ux + r8[5] * uz;
-        double vx = -r8[6] * (r8[2] * y0 - r8[1] * y1);
-        double vz = -r8[6] * (-r8[1] * y0 + r8[0] * y1);
+        M2 K11, K12, K21, K22;
+        elem_blocks(lay + j * LAYER_STRIDE, k, c2, &K11, &K12, &K21, &K22);
+        M2 Mj = madd(Bv, K22);
+        st(ws + 16 * j + 4, Mj);
+        Bv = msub(K11, mmul(K12, msolve(Mj, K21)));
+        st(ws + 16 * j + 8, Bv);
+    }
+    // twist node: most singular condensed block
+    int js = N;
+    double best = 1e300;
+    for (int j = 0; j <= N; ++j) {
+        M2 Pj, Bj;
+        ld(ws + 16 * j + 12, &Pj);
+        ld(ws + 16 * j + 8, &Bj);
+        M2 G = madd(Pj, Bj);
+        double nrm = G.a * G.a + G.b * G.b + G.c * G.c + G.d * G.d;
+        double sng = fabs(mdet(G)) / nrm;
+        if (sng < best) { best = sng; js = j; }
+    }
+    M2 G;
+    {
+        M2 Pj, Bj;
+        ld(ws + 16 * js + 12, &Pj);
+        ld(ws + 16 * js + 8, &Bj);
+        G = madd(Pj, Bj);
+    }
+    // null vector of the 2x2 G from its larger row
+    double nx, nz;
+    if (G.a * G.a + G.b * G.b >= G.c * G.c + G.d * G.d) { nx = -G.b; nz = G.a; }
+    else { nx = -G.d; nz = G.c; }
+    double nn = fmax(fabs(nx), fabs(nz));
+    nx /= nn; nz /= nn;
+    // store u_j in the P slot (no longer needed): [12], [13]
+    ws[16 * js + 12] = nx;
+    ws[16 * js + 13] = nz;
+    for (int j = js - 1; j >= 0; --j) {  // upward: u_j = -S_j^-1 K12_j u_{j+1}
+        M2 K11, K12, K21, K22, S;
+        elem_blocks(lay + j * LAYER_STRIDE, k, c2, &K11, &K12, &K21, &K22);
+        ld(ws + 16 * j, &S);
+        double x = ws[16 * (j + 1) + 12], z = ws[16 * (j + 1) + 13];
+        double v0 = K12.a * x + K12.b * z, v1 = K12.c * x + K12.d * z, o0, o1;
+        mvsolve(S, v0, v1, &o0, &o1);
+        ws[16 * j + 12] = -o0;
+        ws[16 * j + 13] = -o1;
+    }
+    for (int j = js + 1; j <= N; ++j) {  // downward: u_j = -M_{j-1}^-1 K21_{j-1} u_{j-1}
+        M2 K11, K12, K21, K22, Mj;
+        elem_blocks(lay + (j - 1) * LAYER_STRIDE, k, c2, &K11, &K12, &K21, &K22);
+        ld(ws + 16 * (j - 1) + 4, &Mj);
+        double x = ws[16 * (j - 1) + 12], z = ws[16 * (j - 1) + 13];
+        double v0 = K21.a * x + K21.b * z, v1 = K21.c * x + K21.d * z, o0, o1;
+        mvsolve(Mj, v0, v1, &o0, &o1);
+        ws[16 * j + 12] = -o0;
+        ws[16 * j + 13] = -o1;
+    }
+    // implicit-function rule with dual-number element derivatives
+    HalfD H = halfspace_d(lay + N * LAYER_STRIDE, c);
+    D4 qh = half_quad(H, ws[16 * N + 12], ws[16 * N + 13]);
+    double den = qh.d0;
+    row[N] = qh.d1;
+    for (int j = 0; j < N; ++j) {
         ElemD K = layer_element_d(lay + j * LAYER_STRIDE, k, c);
-        D4 q = elem_quad(K, vx, vz, ux, uz);
+        D4 q = elem_quad(K, ws[16 * j + 12], ws[16 * j + 13], ws[16 * (j + 1) + 12],
+                         ws[16 * (j + 1) + 13]);
         den += q.d0;
         row[j] = q.d1;
         row[N + 1 + j] = q.d2;
-        sc8[8 * j + 7] = (double)ecur;
-        // renormalise u_j to a largest component in [1, 2)
-        double mx = fmax(fabs(vx), fabs(vz));
-        double sc;
-        if (pow2_normaliser(mx, &sc)) {
-            long long bits = __double_as_longlong(mx);
-            ecur += (int)((bits >> 52) & 0x7ff) - 1023;
-            den *= sc * sc;
-            vx *= sc;
-            vz *= sc;
-        }
-        ux = vx;
-        uz = vz;
     }
-    // true contribution = stored * 2^(2 e_j); den is stored at 2^(2 ecur).
     double inv = -1.0 / den;
-    row[N] *= inv * exp2(-2.0 * ecur);
-    for (int j = 0; j < N; ++j) {
-        double f = inv * exp2(2.0 * (sc8[8 * j + 7] - ecur));
-        row[j] *= f;
-        row[N + 1 + j] *= f;
-    }
+    for (int p = 0; p < 2 * N + 1; ++p) row[p] *= inv;
 }
 
 cudaError_t launch_root_grad(const DevBatch& b, const double* croot, double* rows, double* bs,
