@@ -41,7 +41,15 @@ WORKLOAD = ("uniform_batch: 1024 models x (8 layers + half-space), h~U[1,8] m, b
 # FP64 flops per layer-evaluation of the scan kernel (element assembly + one
 # Schur step): 2*DFMA + DADD + DMUL executed per evaluated (layer, c) pair,
 # from ncu instruction counters on this workload (profiles/).
-F_LAYER_FLOPS = 180.0
+F_LAYER_FLOPS = 162.3
+# FP64 pipe of GB300: DFMA issue rate per SM per clock (ncu peak_sustained) and
+# the maximum SM clock.
+FP64_DFMA_PER_CLK_SM = 2.0
+SM_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) of one scan launch per model, from the ncu capture
+# of the 64-model case (281.6 KB read, 0 written), scaled by the models of a
+# launch; traffic grows with the number of items.
+SCAN_DRAM_BYTES_PER_MODEL = 281.6e3 / 64
 
 
 def dist_env():
@@ -273,13 +281,20 @@ def main():
     h2d = sum(x.numel() * 8 for x in (hh, ha, hb, hr, hce))
     d2h = hphi.numel() * 8
 
-    # roofline of the scan kernel: algorithmic FP64 flops / device time
-    peak = masw.fp64_peak()
+    # roofline of the scan kernel: algorithmic FP64 flops / device time, against
+    # the FP64 peak derived from unit counts and the maximum SM clock
+    # (2 DFMA per clock per SM x 2 flops x SMs x 2070 MHz); the live DFMA
+    # microbenchmark is reported beside it
+    micro = masw.fp64_peak()
+    peak = FP64_DFMA_PER_CLK_SM * 2.0 * masw.sm_count() * SM_MAX_MHZ * 1e6
     scan_avg = float(np.mean(scan_ms)) * 1e-3
     achieved = units * F_LAYER_FLOPS / scan_avg
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "kernel": "scan_kernel (FP64 pipe)", "peak_source": "measured DFMA microbenchmark",
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": SCAN_DRAM_BYTES_PER_MODEL * models.n_models,
+                "kernel": "scan_kernel (FP64 pipe)",
+                "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
+                "peak_microbenchmark": micro / 1e12,
                 "layer_evals_per_launch": units, "flops_per_layer_eval": F_LAYER_FLOPS,
                 "executed_layer_evals_per_launch": executed,
                 "scan_ms": scan_avg * 1e3}
