@@ -51,6 +51,7 @@ extern "C" {
 #define MASW_ECUDA 4    /* a CUDA runtime call failed */
 #define MASW_ETIMEOUT 5 /* serving: a bounded wait ran out */
 #define MASW_EAGAIN 6   /* serving: result not ready yet */
+#define MASW_ETOOBIG 7  /* batch exceeds the fixed scratch of masw_dispersion_noalloc */
 
 /* ---- per-item status ---- */
 #define MASW_FOUND 0
@@ -188,6 +189,37 @@ int masw_fp64_peak(void* cuda_stream, double* flops);
 
 /* Number of streaming multiprocessors of the current device. */
 int masw_sm_count(int32_t* sms);
+
+/* Algorithm 1 for callers that cannot allocate memory. The paper has no
+ * counterpart: this exists for embedders whose GPU memory is handed out by
+ * someone else (a framework allocator, a fixed budget, a service that forbids
+ * allocation after start-up), so masw_model_batch_create, which allocates a
+ * device copy of the batch, is not open to them. This call allocates nothing,
+ * neither on the device nor on the host: everything derived from the inputs
+ * (layer records, offsets, scan limits, wavenumbers, item order and the
+ * work-queue counter) goes to one fixed array of MASW_NOALLOC_SCRATCH_BYTES
+ * in device memory that every GPU loading the library holds until exit.
+ *  - models: like masw_model_batch_create (host or device arrays, mem_space);
+ *    grid as there. ct, ct_idx, status: DEVICE buffers of sum(n_lambda)
+ *    entries, same meaning as masw_dispersion; results equal its results.
+ *  - Limits: n_models <= MASW_NOALLOC_MAX_MODELS, sum(N_m + 1) <=
+ *    MASW_NOALLOC_MAX_RECORDS, sum(n_lambda) <= MASW_NOALLOC_MAX_ITEMS;
+ *    beyond them the call returns MASW_ETOOBIG and touches nothing.
+ *  - The first call on a device looks up the array's device address (once,
+ *    with that device current); make that first call before any stream
+ *    capture on that device.
+ *  - It validates on the GPU and waits for that check (it synchronises
+ *    cuda_stream once before launching the scan), then enqueues the scan and
+ *    returns; the outputs are complete when cuda_stream reaches that point.
+ *  - All calls share the one array and every call overwrites it: calls that
+ *    may run at the same time on the GPU (other streams, other threads) race
+ *    and give wrong results. Calls on one stream are ordered and safe. */
+#define MASW_NOALLOC_MAX_MODELS 1024
+#define MASW_NOALLOC_MAX_RECORDS 16384
+#define MASW_NOALLOC_MAX_ITEMS 65536
+#define MASW_NOALLOC_SCRATCH_BYTES 3159040
+int masw_dispersion_noalloc(const masw_models_desc* models, const masw_grid* grid,
+                            void* cuda_stream, double* ct, int32_t* ct_idx, int32_t* status);
 
 const char* masw_strerror(int code);
 

@@ -340,6 +340,8 @@ const char* masw_strerror(int code) {
         case MASW_ECUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA runtime error";
         case MASW_ETIMEOUT: return "bounded wait timed out";
         case MASW_EAGAIN: return "result not ready";
+        case MASW_ETOOBIG:
+            return "batch exceeds the fixed scratch of masw_dispersion_noalloc (see MASW_NOALLOC_MAX_*)";
         default: return "unknown error code";
     }
 }

@@ -346,3 +346,28 @@ class Batch:
 
     def last_scan_ms(self) -> float:
         return last_scan_ms(self.handle)
+
+
+# ------------------------------------------------------------ no allocation
+
+ETOOBIG = 7
+NOALLOC_MAX_MODELS, NOALLOC_MAX_RECORDS, NOALLOC_MAX_ITEMS = 1024, 16384, 65536
+
+
+def dispersion_noalloc(n_layers, h, alpha, beta, rho, n_lambda, lam, grid, ct, ct_idx, status,
+                       stream=None):
+    """masw_dispersion_noalloc: Algorithm 1 without any allocation by the
+    library, for callers whose GPU memory comes from someone else. Model
+    arrays host or device (all in the same space); ct, ct_idx, status must be
+    device tensors. Raises MaswError (code ETOOBIG beyond the fixed limits)."""
+    lib = load()
+    f = lib.masw_dispersion_noalloc
+    f.argtypes = [ctypes.POINTER(ModelsDesc), ctypes.POINTER(GridDesc), ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    space = _space(beta)
+    desc = ModelsDesc(int(len(n_layers)), _ptr(n_layers), _ptr(h), _ptr(alpha), _ptr(beta),
+                      _ptr(rho), _ptr(n_lambda), _ptr(lam), space)
+    g = GridDesc(float(grid[0]), float(grid[1]), int(grid[2]))
+    _check(f(ctypes.byref(desc), ctypes.byref(g), _stream_handle(stream), _ptr(ct), _ptr(ct_idx),
+             _ptr(status)), "masw_dispersion_noalloc")
