@@ -119,6 +119,14 @@ int masw_model_batch_destroy(masw_batch* batch);
 int masw_model_batch_update(masw_batch* batch, const double* h, const double* alpha,
                             const double* beta, const double* rho, int32_t mem_space);
 
+/* Set beta_i (sum(N_m + 1) values) and h_i (sum(N_m)) of every layer with
+ * each layer's Poisson ratio and density held, i.e. alpha_i = beta_i *
+ * (alpha_i/beta_i as created): the parameters of masw_misfit_grad. Runs on
+ * the GPU (host or device pointers); synchronises the batch stream to
+ * report MASW_EINVAL for a non-positive or non-finite value. Used by
+ * gradient-based inversion loops; the processing order is kept. */
+int masw_model_batch_update_beta_h(masw_batch* batch, const double* h, const double* beta);
+
 /* Number of items (sum of n_lambda) and models of the batch. */
 int masw_batch_info(const masw_batch* batch, int64_t* n_items, int32_t* n_models,
                     int32_t* max_layers);

@@ -512,6 +512,29 @@ int masw_model_batch_update(masw_batch* B, const double* h, const double* alpha,
     return MASW_OK;
 }
 
+int masw_model_batch_update_beta_h(masw_batch* B, const double* h, const double* beta) {
+    if (!B || !beta || (B->n_records > B->n_models && !h)) return MASW_EINVAL;
+    int rc;
+    double *dh = nullptr, *db = nullptr;
+    int64_t nh = B->n_records - B->n_models;
+    bool hdev = h ? is_device_ptr(h) : true, bdev = is_device_ptr(beta);
+    if (!hdev || !bdev) {  // stage host arrays in the (lazily allocated) gradient buffers
+        if ((rc = ensure(&B->d_gb, B->n_records)) || (rc = ensure(&B->d_gh, nh))) return rc;
+        if ((rc = copy_in(B->d_gb, beta, B->n_records, B->stream))) return rc;
+        if (nh && (rc = copy_in(B->d_gh, h, nh, B->stream))) return rc;
+        db = B->d_gb;
+        dh = B->d_gh;
+    }
+    if (bdev) db = const_cast<double*>(beta);
+    if (hdev) dh = const_cast<double*>(h);
+    int32_t herr = 0;
+    CK(cudaMemsetAsync(B->d_counter, 0, sizeof(int32_t), B->stream));
+    CK(launch_update_beta_h(B->dev(false), dh, db, B->d_layers, B->d_nlim, B->d_counter, B->stream));
+    CK(cudaMemcpyAsync(&herr, B->d_counter, sizeof(int32_t), cudaMemcpyDeviceToHost, B->stream));
+    CK(cudaStreamSynchronize(B->stream));
+    return herr ? MASW_EINVAL : MASW_OK;
+}
+
 int masw_batch_info(const masw_batch* B, int64_t* n_items, int32_t* n_models, int32_t* max_layers) {
     if (!B) return MASW_EINVAL;
     if (n_items) *n_items = B->n_items;

@@ -50,6 +50,8 @@ cudaError_t launch_misfit(const DevBatch& b, const double* ct, const double* ce,
                           double sigma, double* misfit, double* dphi_dc, cudaStream_t s);
 cudaError_t launch_grad_reduce(const DevBatch& b, const double* rows, const double* dphi_dc,
                                double* grad_beta, double* grad_h, cudaStream_t s);
+cudaError_t launch_update_beta_h(const DevBatch& b, const double* h, const double* beta,
+                                 double* layers, int32_t* nlim, int32_t* err, cudaStream_t s);
 cudaError_t launch_fp64_peak(int blocks, int threads, int iters, double* sink, cudaStream_t s);
 
 }  // namespace masw

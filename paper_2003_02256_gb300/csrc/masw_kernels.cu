@@ -420,6 +420,47 @@ cudaError_t launch_grad_reduce(const DevBatch& b, const double* rows, const doub
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------- in-place update
+
+// New beta and h for every layer of the batch with each layer's Poisson ratio
+// and density held (alpha_i = beta_i * (alpha/beta)_i): the parameterisation
+// of the gradient. One thread per model; recomputes the records and the scan
+// limit; any invalid value sets *err (records are then unspecified).
+__global__ void update_beta_h_kernel(DevBatch b, const double* __restrict__ h,
+                                     const double* __restrict__ beta, double* layers,
+                                     int32_t* nlim, int32_t* err) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= b.n_models) return;
+    int lo = b.model_loff[m];
+    int N = b.model_loff[m + 1] - lo - 1;
+    int h0 = lo - m;
+    for (int i = 0; i <= N; ++i) {
+        double* L = layers + (size_t)(lo + i) * LAYER_STRIDE;
+        double be = beta[lo + i];
+        double hh = (i < N) ? h[h0 + i] : 0.0;
+        if (!(isfinite(be) && be > 0.0) || (i < N && !(isfinite(hh) && hh > 0.0))) atomicOr(err, 1);
+        double a = be * L[L_RATIO];
+        L[L_H] = hh;
+        L[L_MU] = L[L_RHO] * be * be;
+        L[L_IA2] = 1.0 / (a * a);
+        L[L_IB2] = 1.0 / (be * be);
+        L[L_BETA] = be;
+    }
+    double bhs = beta[lo + N];
+    double est = floor((bhs - b.c0) / b.dc);
+    long long n = (long long)fmax(0.0, fmin(est, (double)b.n_c));
+    while (n > 0 && !(grid_c(b.c0, b.dc, (int)(n - 1)) < bhs)) --n;
+    while (n < b.n_c && grid_c(b.c0, b.dc, (int)n) < bhs) ++n;
+    nlim[m] = (int32_t)n;
+}
+
+cudaError_t launch_update_beta_h(const DevBatch& b, const double* h, const double* beta,
+                                 double* layers, int32_t* nlim, int32_t* err, cudaStream_t s) {
+    if (b.n_models <= 0) return cudaSuccess;
+    update_beta_h_kernel<<<(b.n_models + 127) / 128, 128, 0, s>>>(b, h, beta, layers, nlim, err);
+    return cudaGetLastError();
+}
+
 // ----------------------------------------------------------- FP64 peak
 
 // Eight independent DFMA chains per thread; the result is written so the

@@ -165,6 +165,15 @@ def model_batch_update(handle, h, alpha, beta, rho):
            "masw_model_batch_update")
 
 
+def model_batch_update_beta_h(handle, h, beta):
+    """masw_model_batch_update_beta_h: new beta and h, Poisson ratio and
+    density held."""
+    f = load().masw_model_batch_update_beta_h
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    _check(f(ctypes.c_void_p(handle), _ptr(h), _ptr(beta)), "masw_model_batch_update_beta_h")
+
+
 def batch_info(handle):
     n_items, n_models, max_layers = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().masw_batch_info(ctypes.c_void_p(handle), ctypes.byref(n_items),
