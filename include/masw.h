@@ -198,6 +198,75 @@ int masw_fp64_peak(void* cuda_stream, double* flops);
 /* Number of streaming multiprocessors of the current device. */
 int masw_sm_count(int32_t* sms);
 
+/* ---------------------------------------------------------------------
+ * Serving: continuous batching of model evaluations. No paper counterpart
+ * beyond its motivation (repeated evaluation inside an optimisation or
+ * uncertainty loop, Section 1 and Section 2.1): requests, each one model
+ * with its own layer count and wavelengths, arrive at any time; each
+ * admitted request holds a slot with its data resident on the device; every
+ * tick advances every running (request, wavelength) item by at most
+ * chunks_per_tick 32-point chunks of Algorithm 1 and compacts the rest, so
+ * requests admitted between ticks overlap with those in flight. A result is
+ * identical to masw_dispersion's for the same model. The host waits for a
+ * tick on an event; nothing waits on the device.
+ * --------------------------------------------------------------------- */
+typedef struct masw_server masw_server;
+
+typedef struct {
+    int32_t max_slots;       /* requests in flight at most */
+    int32_t max_layers;      /* finite layers per request (<= MASW_MAX_LAYERS) */
+    int32_t max_lambda;      /* wavelengths per request */
+    int64_t mem_cap_bytes;   /* admission cap on the device bytes held by requests in flight */
+    int32_t chunks_per_tick; /* chunks of 32 test velocities an item advances per tick */
+    int32_t warps_per_block; /* 1, 2, 4 or 8 */
+} masw_server_config;
+
+typedef struct {
+    int32_t in_flight;       /* slots held */
+    int32_t active_items;    /* items still scanning */
+    int64_t bytes_in_flight; /* bytes charged against mem_cap_bytes */
+    int64_t ticks;
+    int64_t completed;
+} masw_server_stats;
+
+/* Allocate the slot table (device) and its pinned staging/result buffers for
+ * the given grid; all later work runs on cuda_stream. MASW_EINVAL on a bad
+ * config, MASW_ENOMEM when the buffers do not fit. */
+int masw_server_create(const masw_grid* grid, const masw_server_config* cfg, void* cuda_stream,
+                       masw_server** out);
+int masw_server_destroy(masw_server* server);
+
+/* Admit one request (host arrays as in masw_models_desc for one model).
+ * MASW_EADMIT when no slot is free or its bytes would exceed the cap (the
+ * server is unchanged; retry after a tick); MASW_EINVAL on invalid values.
+ * The request joins the next tick. */
+int masw_server_submit(masw_server* server, int32_t n_layers, const double* h,
+                       const double* alpha, const double* beta, const double* rho,
+                       int32_t n_lambda, const double* lambda, int64_t* request_id);
+
+/* Run one tick and wait for it; *n_completed = requests that finished. */
+int masw_server_tick(masw_server* server, int32_t* n_completed);
+
+/* Copy a finished request's results (host arrays of its n_lambda entries,
+ * any may be NULL) and free its slot; MASW_EAGAIN if not finished yet. */
+int masw_server_poll(masw_server* server, int64_t request_id, double* ct, int32_t* ct_idx,
+                     int32_t* status);
+
+int masw_server_get_stats(const masw_server* server, masw_server_stats* stats);
+
+/* Replay a request trace natively: request i (concatenated host arrays as in
+ * masw_models_desc) arrives arrival_s[i] seconds (non-decreasing) after the
+ * call starts; the loop admits arrived requests while slots and bytes allow,
+ * ticks, and retires finished ones. latency_s[i] = completion - arrival.
+ * ct, ct_idx, status (sum of n_lambda, may be NULL) receive the results;
+ * stats (3 values, may be NULL): ticks, refused admissions, max in flight.
+ * The server must be idle. MASW_ETIMEOUT after timeout_s seconds. */
+int masw_server_run_trace(masw_server* server, int32_t n_requests, const int32_t* n_layers,
+                          const double* h, const double* alpha, const double* beta,
+                          const double* rho, const int32_t* n_lambda, const double* lambda,
+                          const double* arrival_s, double timeout_s, double* latency_s,
+                          double* ct, int32_t* ct_idx, int32_t* status, int64_t* stats);
+
 /* Algorithm 1 for callers that cannot allocate memory. The paper has no
  * counterpart: this exists for embedders whose GPU memory is handed out by
  * someone else (a framework allocator, a fixed budget, a service that forbids

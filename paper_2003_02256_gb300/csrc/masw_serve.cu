@@ -1,0 +1,493 @@
+// masw_serve.cu -- continuous-batching request loop for model evaluations.
+//
+// Repeated evaluation of candidate models is what an inversion or an
+// uncertainty sampler does (Section 1; Section 2.1, "exhaustive quantity of
+// plausible model parameters"); the paper evaluates one model per call. Here
+// requests (one model with its own layer count and wavelengths each) arrive
+// at any time and share the GPU:
+//  * each admitted request owns a slot: its layer records, wavenumbers, scan
+//    state and results stay resident until the request is polled;
+//  * admission needs a free slot and room under the byte cap;
+//  * every tick launches one kernel that advances every active item (one
+//    (request, wavelength) pair) by at most `chunks_per_tick` 32-point chunks
+//    of Algorithm 1's scan and compacts the items still running; requests
+//    admitted between ticks join the next tick, so their work overlaps with
+//    the requests already in flight;
+//  * an item's chunks are exactly those of the batch scan (32 consecutive
+//    grid points from V[0], sign carried across chunks), so a result does not
+//    depend on what else is in flight.
+// There are no device-side waits: the host waits for each tick on an event.
+//
+// Slot layout (one pinned host staging region and one device region per
+// slot, copied with a single transfer at admission):
+//   [meta: 4 x i32 (nrec, nlim, n_lambda, 0)] [records: rmax x 8 f64]
+//   [k: imax f64] [scan state: imax x (base i32, carry i32)]
+// Results are written by the kernel into mapped pinned host memory, so
+// retiring a request is a host memcpy.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "../../include/masw.h"
+#include "masw_device.cuh"
+#include "masw_internal.h"
+
+using namespace masw;
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+struct SlotView {
+    double* region;      // [slots][stride] doubles
+    int64_t stride;      // doubles per slot
+    int rmax, imax;
+    double* ct;          // mapped host [slots * imax]
+    int32_t* idx;
+    int32_t* status;
+    int32_t* remaining;  // [slots] items still running
+    int32_t* done;       // [slots] slots finished during the tick
+    int32_t* counters;   // [0] survivors, [1] done count
+};
+
+__device__ __forceinline__ const int32_t* slot_meta(const SlotView& v, int s) {
+    return (const int32_t*)(v.region + (size_t)s * v.stride);
+}
+__device__ __forceinline__ double* slot_records(const SlotView& v, int s) {
+    return v.region + (size_t)s * v.stride + 2;
+}
+__device__ __forceinline__ double* slot_k(const SlotView& v, int s) {
+    return v.region + (size_t)s * v.stride + 2 + (size_t)v.rmax * LAYER_STRIDE;
+}
+__device__ __forceinline__ int32_t* slot_state(const SlotView& v, int s) {
+    return (int32_t*)(v.region + (size_t)s * v.stride + 2 + (size_t)v.rmax * LAYER_STRIDE + v.imax);
+}
+
+__global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
+                                                         const int32_t* __restrict__ active_in,
+                                                         int n_active, int32_t* active_out,
+                                                         int chunks, double c0, double dc) {
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int a = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (a >= n_active) return;
+    const int item = active_in[a];
+    const int slot = item / v.imax;
+    const int j = item - slot * v.imax;
+    const int32_t* meta = slot_meta(v, slot);
+    const int nrec = meta[0];
+    const int nlim = meta[1];
+    const int N = nrec - 1;
+    double* my = smem + (size_t)wib * v.rmax * LAYER_STRIDE;
+    const double* src = slot_records(v, slot);
+    for (int t = lane; t < nrec * LAYER_STRIDE; t += 32) my[t] = src[t];
+    __syncwarp();
+    const double k = slot_k(v, slot)[j];
+    int32_t* stt = slot_state(v, slot) + 2 * j;
+    int base = stt[0];
+    int carry = stt[1];
+    int res = -1;
+    bool finished = base >= nlim;
+    for (int c = 0; c < chunks && !finished; ++c) {
+        int n = base + lane;
+        int sg = (n < nlim) ? det_sign(my, N, k, grid_c(c0, dc, n)) : 0;
+        int prev = __shfl_up_sync(FULL, sg, 1);
+        if (lane == 0) prev = carry;
+        unsigned msk = __ballot_sync(FULL, n >= 1 && n < nlim && sg != prev);
+        if (msk) {
+            res = base + __ffs(msk) - 1;
+            finished = true;
+        } else {
+            carry = __shfl_sync(FULL, sg, 31);
+            base += 32;
+            finished = base >= nlim;
+        }
+    }
+    if (lane == 0) {
+        if (finished) {
+            if (res >= 0) {
+                v.ct[item] = grid_c(c0, dc, res);
+                v.idx[item] = res;
+                v.status[item] = MASW_FOUND;
+            } else {
+                v.ct[item] = __longlong_as_double(0x7ff8000000000000LL);
+                v.idx[item] = -1;
+                v.status[item] = MASW_NO_ROOT;
+            }
+            __threadfence_system();
+            if (atomicSub(&v.remaining[slot], 1) == 1) v.done[atomicAdd(&v.counters[1], 1)] = slot;
+        } else {
+            stt[0] = base;
+            stt[1] = carry;
+            active_out[atomicAdd(&v.counters[0], 1)] = item;
+        }
+    }
+}
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+int64_t request_bytes(int32_t n_layers, int32_t n_lambda) {
+    // records + per-item k, scan state and results
+    return (int64_t)(n_layers + 1) * LAYER_STRIDE * 8 + (int64_t)n_lambda * (8 + 8 + 16);
+}
+
+int32_t scan_limit_host(const masw_grid& g, double beta_hs) {
+    double est = std::floor((beta_hs - g.c0) / g.dc);
+    int64_t n = (int64_t)std::max(0.0, std::min(est, (double)g.n_c));
+    while (n > 0 && !(std::fma((double)(n - 1), g.dc, g.c0) < beta_hs)) --n;
+    while (n < g.n_c && std::fma((double)n, g.dc, g.c0) < beta_hs) ++n;
+    return (int32_t)n;
+}
+
+}  // namespace
+
+struct masw_server {
+    masw_grid grid{};
+    masw_server_config cfg{};
+    cudaStream_t stream = nullptr;
+    SlotView v{};
+    double* h_region = nullptr;  // pinned staging, same layout as v.region
+    double* h_ct = nullptr;      // mapped pinned results
+    int32_t* h_idx = nullptr;
+    int32_t* h_status = nullptr;
+    int32_t* active[2] = {nullptr, nullptr};
+    int32_t* h_new_items = nullptr;
+    int32_t* h_counters = nullptr;
+    int32_t* h_done = nullptr;
+    cudaEvent_t ev = nullptr;
+    int cur = 0;
+    int n_active = 0;
+    std::vector<int32_t> free_slots;
+    std::vector<int64_t> slot_req;  // request id held by a slot (-1 free)
+    std::vector<int32_t> slot_nlambda;
+    std::vector<int64_t> slot_bytes;
+    std::vector<char> slot_done;
+    std::vector<int32_t> id_slot;   // request id -> slot (-1 after poll)
+    std::vector<int32_t> pending;   // items admitted since the last tick
+    std::vector<int32_t> just_done; // slots finished by the last tick
+    int64_t bytes_in_flight = 0;
+    int64_t ticks = 0;
+    int64_t completed = 0;
+};
+
+namespace {
+
+void server_free(masw_server* S) {
+    if (!S) return;
+    void* dev[] = {S->v.region, S->v.remaining, S->v.done, S->v.counters, S->active[0],
+                   S->active[1]};
+    for (void* p : dev)
+        if (p) cudaFree(p);
+    void* host[] = {S->h_region, S->h_ct, S->h_idx, S->h_status, S->h_new_items, S->h_counters,
+                    S->h_done};
+    for (void* p : host)
+        if (p) cudaFreeHost(p);
+    if (S->ev) cudaEventDestroy(S->ev);
+    delete S;
+}
+
+template <typename T>
+bool dalloc(T** p, size_t n) {
+    return cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T)) == cudaSuccess;
+}
+template <typename T>
+bool halloc(T** p, size_t n, unsigned flags = cudaHostAllocDefault) {
+    return cudaHostAlloc((void**)p, std::max<size_t>(n, 1) * sizeof(T), flags) == cudaSuccess;
+}
+
+// Launch one tick and wait for it; the finished slots land in just_done.
+int run_tick(masw_server* S) {
+    S->just_done.clear();
+    int n_new = (int)S->pending.size();
+    if (n_new) {
+        std::memcpy(S->h_new_items, S->pending.data(), n_new * sizeof(int32_t));
+        if (cudaMemcpyAsync(S->active[S->cur] + S->n_active, S->h_new_items, n_new * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, S->stream) != cudaSuccess)
+            return MASW_ECUDA;
+        S->n_active += n_new;
+        S->pending.clear();
+    }
+    if (S->n_active == 0) return MASW_OK;
+    if (cudaMemsetAsync(S->v.counters, 0, 2 * sizeof(int32_t), S->stream) != cudaSuccess)
+        return MASW_ECUDA;
+    int wpb = S->cfg.warps_per_block;
+    int blocks = (S->n_active + wpb - 1) / wpb;
+    size_t shm = (size_t)wpb * S->v.rmax * LAYER_STRIDE * sizeof(double);
+    serve_tick_kernel<<<blocks, 32 * wpb, shm, S->stream>>>(S->v, S->active[S->cur], S->n_active,
+                                                            S->active[1 - S->cur],
+                                                            S->cfg.chunks_per_tick, S->grid.c0,
+                                                            S->grid.dc);
+    if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
+    if (cudaMemcpyAsync(S->h_counters, S->v.counters, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                        S->stream) != cudaSuccess ||
+        cudaEventRecord(S->ev, S->stream) != cudaSuccess ||
+        cudaEventSynchronize(S->ev) != cudaSuccess)
+        return MASW_ECUDA;
+    int survivors = S->h_counters[0], n_done = S->h_counters[1];
+    if (n_done > 0) {
+        if (cudaMemcpy(S->h_done, S->v.done, n_done * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return MASW_ECUDA;
+        for (int i = 0; i < n_done; ++i) {
+            S->slot_done[S->h_done[i]] = 1;
+            S->just_done.push_back(S->h_done[i]);
+        }
+    }
+    S->cur = 1 - S->cur;
+    S->n_active = survivors;
+    S->ticks++;
+    S->completed += n_done;
+    return MASW_OK;
+}
+
+int slot_of(const masw_server* S, int64_t id) {
+    if (id < 0 || id >= (int64_t)S->id_slot.size()) return -1;
+    return S->id_slot[id];
+}
+
+// Copy a finished slot's results out and free the slot.
+void retire_slot(masw_server* S, int slot, double* ct, int32_t* idx, int32_t* status) {
+    int n = S->slot_nlambda[slot];
+    size_t i0 = (size_t)slot * S->v.imax;
+    if (ct) std::memcpy(ct, S->h_ct + i0, n * sizeof(double));
+    if (idx) std::memcpy(idx, S->h_idx + i0, n * sizeof(int32_t));
+    if (status) std::memcpy(status, S->h_status + i0, n * sizeof(int32_t));
+    S->id_slot[S->slot_req[slot]] = -1;
+    S->slot_req[slot] = -1;
+    S->slot_done[slot] = 0;
+    S->bytes_in_flight -= S->slot_bytes[slot];
+    S->free_slots.push_back(slot);
+}
+
+}  // namespace
+
+extern "C" {
+
+int masw_server_create(const masw_grid* grid, const masw_server_config* cfg, void* cuda_stream,
+                       masw_server** out) {
+    if (!grid || !cfg || !out) return MASW_EINVAL;
+    if (!(std::isfinite(grid->c0) && grid->c0 > 0 && std::isfinite(grid->dc) && grid->dc > 0 &&
+          grid->n_c >= 2))
+        return MASW_EINVAL;
+    if (cfg->max_slots < 1 || cfg->max_layers < 0 || cfg->max_layers > MASW_MAX_LAYERS ||
+        cfg->max_lambda < 1 || cfg->mem_cap_bytes <= 0 || cfg->chunks_per_tick < 1 ||
+        !(cfg->warps_per_block == 1 || cfg->warps_per_block == 2 || cfg->warps_per_block == 4 ||
+          cfg->warps_per_block == 8))
+        return MASW_EINVAL;
+    int64_t cap_items = (int64_t)cfg->max_slots * cfg->max_lambda;
+    if (cap_items > INT32_MAX / 2) return MASW_EINVAL;
+    size_t shm = (size_t)cfg->warps_per_block * (cfg->max_layers + 1) * LAYER_STRIDE * 8;
+    if (shm > 48 * 1024) return MASW_EINVAL;
+    masw_server* S = new (std::nothrow) masw_server();
+    if (!S) return MASW_ENOMEM;
+    S->grid = *grid;
+    S->cfg = *cfg;
+    S->stream = (cudaStream_t)cuda_stream;
+    S->v.rmax = cfg->max_layers + 1;
+    S->v.imax = cfg->max_lambda;
+    S->v.stride = 2 + (int64_t)S->v.rmax * LAYER_STRIDE + 2 * (int64_t)S->v.imax;
+    S->v.stride = (S->v.stride + 31) / 32 * 32;  // 256-byte aligned slots
+    size_t slots = cfg->max_slots, items = (size_t)cap_items;
+    bool ok = dalloc(&S->v.region, slots * S->v.stride) && dalloc(&S->v.remaining, slots) &&
+              dalloc(&S->v.done, slots) && dalloc(&S->v.counters, 2) &&
+              dalloc(&S->active[0], items) && dalloc(&S->active[1], items) &&
+              halloc(&S->h_region, slots * S->v.stride) &&
+              halloc(&S->h_ct, items, cudaHostAllocMapped) &&
+              halloc(&S->h_idx, items, cudaHostAllocMapped) &&
+              halloc(&S->h_status, items, cudaHostAllocMapped) && halloc(&S->h_new_items, items) &&
+              halloc(&S->h_counters, 2) && halloc(&S->h_done, slots) &&
+              cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaHostGetDevicePointer((void**)&S->v.ct, S->h_ct, 0) == cudaSuccess &&
+              cudaHostGetDevicePointer((void**)&S->v.idx, S->h_idx, 0) == cudaSuccess &&
+              cudaHostGetDevicePointer((void**)&S->v.status, S->h_status, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        server_free(S);
+        return MASW_ENOMEM;
+    }
+    S->free_slots.resize(slots);
+    for (size_t s = 0; s < slots; ++s) S->free_slots[s] = (int32_t)(slots - 1 - s);
+    S->slot_req.assign(slots, -1);
+    S->slot_nlambda.assign(slots, 0);
+    S->slot_bytes.assign(slots, 0);
+    S->slot_done.assign(slots, 0);
+    *out = S;
+    return MASW_OK;
+}
+
+int masw_server_destroy(masw_server* S) {
+    if (!S) return MASW_EINVAL;
+    cudaStreamSynchronize(S->stream);
+    server_free(S);
+    return MASW_OK;
+}
+
+int masw_server_submit(masw_server* S, int32_t n_layers, const double* h, const double* alpha,
+                       const double* beta, const double* rho, int32_t n_lambda,
+                       const double* lambda, int64_t* request_id) {
+    if (!S || !alpha || !beta || !rho || !lambda || !request_id || (n_layers > 0 && !h))
+        return MASW_EINVAL;
+    if (n_layers < 0 || n_layers > S->cfg.max_layers || n_lambda < 1 || n_lambda > S->v.imax)
+        return MASW_EINVAL;
+    for (int i = 0; i < n_layers; ++i)
+        if (!(std::isfinite(h[i]) && h[i] > 0)) return MASW_EINVAL;
+    for (int i = 0; i <= n_layers; ++i) {
+        double a = alpha[i], b = beta[i], r = rho[i];
+        if (!(std::isfinite(a) && a > 0 && std::isfinite(b) && b > 0 && std::isfinite(r) && r > 0 &&
+              3.0 * a * a > 4.0 * b * b))
+            return MASW_EINVAL;
+    }
+    for (int j = 0; j < n_lambda; ++j)
+        if (!(std::isfinite(lambda[j]) && lambda[j] > 0)) return MASW_EINVAL;
+    int64_t need = request_bytes(n_layers, n_lambda);
+    if (S->free_slots.empty() || S->bytes_in_flight + need > S->cfg.mem_cap_bytes) return MASW_EADMIT;
+    int slot = S->free_slots.back();
+    // stage meta, records (as masw_model_batch_create builds them), k and a
+    // zero scan state in the slot's pinned region, then one transfer
+    double* reg = S->h_region + (size_t)slot * S->v.stride;
+    int32_t* meta = (int32_t*)reg;
+    meta[0] = n_layers + 1;
+    meta[1] = scan_limit_host(S->grid, beta[n_layers]);
+    meta[2] = n_lambda;
+    meta[3] = 0;
+    double* rec = reg + 2;
+    for (int i = 0; i <= n_layers; ++i) {
+        double* L = rec + (size_t)i * LAYER_STRIDE;
+        double a = alpha[i], b = beta[i], r = rho[i];
+        L[L_H] = (i < n_layers) ? h[i] : 0.0;
+        L[L_MU] = r * b * b;
+        L[L_RHO] = r;
+        L[L_IA2] = 1.0 / (a * a);
+        L[L_IB2] = 1.0 / (b * b);
+        L[L_BETA] = b;
+        L[L_RATIO] = a / b;
+        L[7] = 0.0;
+    }
+    double* kk = rec + (size_t)S->v.rmax * LAYER_STRIDE;
+    for (int j = 0; j < n_lambda; ++j) kk[j] = 2.0 * M_PI / lambda[j];
+    int32_t* stt = (int32_t*)(kk + S->v.imax);
+    std::memset(stt, 0, (size_t)n_lambda * 2 * sizeof(int32_t));
+    size_t bytes = (size_t)((char*)(stt + 2 * n_lambda) - (char*)reg);
+    cudaError_t e = cudaMemcpyAsync(S->v.region + (size_t)slot * S->v.stride, reg, bytes,
+                                    cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->v.remaining + slot, &meta[2], sizeof(int32_t), cudaMemcpyHostToDevice,
+                            S->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MASW_ECUDA;
+    }
+    S->free_slots.pop_back();
+    int64_t id = (int64_t)S->id_slot.size();
+    S->id_slot.push_back(slot);
+    int64_t i0 = (int64_t)slot * S->v.imax;
+    for (int j = 0; j < n_lambda; ++j) S->pending.push_back((int32_t)(i0 + j));
+    S->slot_req[slot] = id;
+    S->slot_nlambda[slot] = n_lambda;
+    S->slot_bytes[slot] = need;
+    S->slot_done[slot] = 0;
+    S->bytes_in_flight += need;
+    *request_id = id;
+    return MASW_OK;
+}
+
+int masw_server_tick(masw_server* S, int32_t* n_completed) {
+    if (!S) return MASW_EINVAL;
+    int rc = run_tick(S);
+    if (rc) return rc;
+    if (n_completed) *n_completed = (int32_t)S->just_done.size();
+    return MASW_OK;
+}
+
+int masw_server_poll(masw_server* S, int64_t request_id, double* ct, int32_t* ct_idx,
+                     int32_t* status) {
+    if (!S) return MASW_EINVAL;
+    int slot = slot_of(S, request_id);
+    if (slot < 0) return MASW_EINVAL;
+    if (!S->slot_done[slot]) return MASW_EAGAIN;
+    retire_slot(S, slot, ct, ct_idx, status);
+    return MASW_OK;
+}
+
+int masw_server_get_stats(const masw_server* S, masw_server_stats* st) {
+    if (!S || !st) return MASW_EINVAL;
+    st->in_flight = (int32_t)(S->cfg.max_slots - (int32_t)S->free_slots.size());
+    st->active_items = S->n_active + (int32_t)S->pending.size();
+    st->bytes_in_flight = S->bytes_in_flight;
+    st->ticks = S->ticks;
+    st->completed = S->completed;
+    return MASW_OK;
+}
+
+int masw_server_run_trace(masw_server* S, int32_t n_requests, const int32_t* n_layers,
+                          const double* h, const double* alpha, const double* beta,
+                          const double* rho, const int32_t* n_lambda, const double* lambda,
+                          const double* arrival_s, double timeout_s, double* latency_s,
+                          double* ct, int32_t* ct_idx, int32_t* status, int64_t* stats) {
+    if (!S || n_requests < 1 || !n_layers || !alpha || !beta || !rho || !n_lambda || !lambda ||
+        !arrival_s || !latency_s)
+        return MASW_EINVAL;
+    if (S->free_slots.size() != (size_t)S->cfg.max_slots) return MASW_EINVAL;  // must start idle
+    std::vector<int64_t> hoff(n_requests + 1, 0), loff(n_requests + 1, 0), woff(n_requests + 1, 0);
+    for (int i = 0; i < n_requests; ++i) {
+        if (n_layers[i] < 0 || n_lambda[i] < 1) return MASW_EINVAL;
+        hoff[i + 1] = hoff[i] + n_layers[i];
+        loff[i + 1] = loff[i] + n_layers[i] + 1;
+        woff[i + 1] = woff[i] + n_lambda[i];
+        if (i && arrival_s[i] < arrival_s[i - 1]) return MASW_EINVAL;
+    }
+    std::vector<int32_t> slot_q(S->cfg.max_slots, -1);
+    int next = 0, done = 0;
+    int64_t refused = 0, max_in_flight = 0;
+    const double t0 = now_s();
+    while (done < n_requests) {
+        double t = now_s() - t0;
+        if (t > timeout_s) return MASW_ETIMEOUT;
+        while (next < n_requests && arrival_s[next] <= t) {
+            int64_t id;
+            int rc = masw_server_submit(S, n_layers[next], h + hoff[next], alpha + loff[next],
+                                        beta + loff[next], rho + loff[next], n_lambda[next],
+                                        lambda + woff[next], &id);
+            if (rc == MASW_EADMIT) {  // wait for slots or bytes to free up
+                ++refused;
+                break;
+            }
+            if (rc) return rc;
+            slot_q[S->id_slot[id]] = next;
+            ++next;
+        }
+        max_in_flight = std::max<int64_t>(max_in_flight, S->cfg.max_slots - (int64_t)S->free_slots.size());
+        if (S->n_active + (int)S->pending.size() > 0) {
+            int rc = run_tick(S);
+            if (rc) return rc;
+            double tc = now_s() - t0;
+            for (int slot : S->just_done) {
+                int q = slot_q[slot];
+                slot_q[slot] = -1;
+                retire_slot(S, slot, ct ? ct + woff[q] : nullptr, ct_idx ? ct_idx + woff[q] : nullptr,
+                            status ? status + woff[q] : nullptr);
+                latency_s[q] = tc - arrival_s[q];
+                ++done;
+            }
+        } else if (next < n_requests) {
+            double wait = arrival_s[next] - (now_s() - t0);
+            if (wait > 0)
+                std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 1e-3)));
+        }
+    }
+    if (stats) {
+        stats[0] = S->ticks;
+        stats[1] = refused;
+        stats[2] = max_in_flight;
+    }
+    return MASW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+"""Continuous-batching server: each result is identical alone and in the mix
+(and equal to the batch entry point and to the oracle), admission by slots
+and bytes refuses with a status instead of failing, and the trace replay
+returns sane latencies."""
+import numpy as np
+import pytest
+
+from paper_2003_02256_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_02256_gb300 import masw, serving
+    masw.load()
+    return masw, serving
+
+
+def requests(n, seed=5):
+    s = W.RandomWalkSampler(seed=seed, chain_len=8)
+    return W.concat([s.next() for _ in range(n)])
+
+
+def test_results_identical_alone_in_the_mix_and_batched(env, oracle_lib):
+    masw, serving = env
+    reqs = requests(60)
+    grid = W.Grid(50.0, 0.25, 4601)
+    with masw.Batch(reqs, grid) as b:
+        ref_ct, ref_idx, ref_st = b.dispersion()
+    # in the mix: fast Poisson arrivals, several ticks per request
+    arr = W.poisson_arrivals(reqs.n_models, rate=2e4, seed=1)
+    with serving.Server(grid, max_slots=32, chunks_per_tick=3) as srv:
+        lat, ct, idx, st, stats = srv.run_trace(reqs, arr)
+    assert np.array_equal(idx, ref_idx) and np.array_equal(st, ref_st)
+    assert np.array_equal(ct, ref_ct, equal_nan=True)
+    assert stats["ticks"] > 3 and stats["max_in_flight"] > 1
+    assert (lat >= 0).all()
+    # alone: one request at a time, ticked to completion
+    hoff, loff, woff = reqs.layer_offsets()
+    with serving.Server(grid, max_slots=1, chunks_per_tick=1) as srv:
+        for q in range(0, reqs.n_models, 7):
+            h, a, bb, r, lam = reqs.model(q)
+            rid = srv.submit(h, a, bb, r, lam)
+            out = None
+            while out is None:
+                srv.tick()
+                out = srv.poll(rid, lam.size)
+            assert np.array_equal(out[1], ref_idx[woff[q]:woff[q + 1]])
+            assert np.array_equal(out[2], ref_st[woff[q]:woff[q + 1]])
+    # a few requests against the oracle
+    for q in (0, 13, 41):
+        h, a, bb, r, lam = reqs.model(q)
+        o_ct, o_idx, o_st = oracle_lib.dispersion(reqs.subset([q]).as_dict(), grid.c0, grid.dc,
+                                                  grid.n_c)
+        sl = slice(woff[q], woff[q + 1])
+        assert np.array_equal(o_st, st[sl])
+        d = np.abs(o_idx - idx[sl])
+        assert d.max() <= 1 and (d == 0).mean() >= 0.99
+
+
+def test_admission_refuses_past_the_caps_with_a_status(env):
+    masw, serving = env
+    reqs = requests(6, seed=9)
+    grid = W.Grid(50.0, 0.25, 4601)
+    h, a, b, r, lam = reqs.model(0)
+    one = (len(a) * 64) + lam.size * 32
+    with serving.Server(grid, max_slots=4, mem_cap_bytes=int(one * 1.5)) as srv:
+        rid = srv.submit(h, a, b, r, lam)
+        h1, a1, b1, r1, l1 = reqs.model(1)
+        with pytest.raises(masw.MaswError) as ei:
+            srv.submit(h1, a1, b1, r1, l1)
+        assert ei.value.code == masw.EADMIT
+        while srv.poll(rid, lam.size) is None:
+            srv.tick()
+        srv.submit(h1, a1, b1, r1, l1)  # room again after the poll
+    with serving.Server(grid, max_slots=2) as srv:
+        srv.submit(*reqs.model(0))
+        srv.submit(*reqs.model(1))
+        with pytest.raises(masw.MaswError) as ei:
+            srv.submit(*reqs.model(2))
+        assert ei.value.code == masw.EADMIT
+        st = srv.stats()
+        assert st["in_flight"] == 2 and st["bytes_in_flight"] > 0
+
+
+def test_invalid_requests_are_rejected(env):
+    masw, serving = env
+    grid = W.Grid(50.0, 0.25, 4601)
+    with serving.Server(grid, max_slots=2, max_layers=4, max_lambda=10) as srv:
+        ok = (np.ones(2), np.array([500.0, 600, 900]), np.array([200.0, 250, 400]),
+              np.full(3, 1900.0), np.array([5.0, 10.0]))
+        for bad in ((np.ones(5), np.full(6, 900.0), np.full(6, 300.0), np.full(6, 1900.0), ok[4]),
+                    (ok[0], ok[1], ok[2], ok[3], np.arange(1.0, 12.0)),
+                    (-ok[0], ok[1], ok[2], ok[3], ok[4])):
+            with pytest.raises(masw.MaswError) as ei:
+                srv.submit(*bad)
+            assert ei.value.code == masw.EINVAL
+        srv.submit(*ok)
+
+
+def test_plain_per_request_mode_matches(env):
+    masw, serving = env
+    reqs = requests(12, seed=3)
+    grid = W.Grid(50.0, 0.25, 4601)
+    arr = W.poisson_arrivals(reqs.n_models, rate=1e4, seed=2)
+    with serving.Server(grid, max_slots=32, chunks_per_tick=4) as a:
+        la, ct_a, idx_a, st_a, _ = a.run_trace(reqs, arr)
+    with serving.Server(grid, max_slots=1, chunks_per_tick=1 << 20) as p:
+        lp, ct_p, idx_p, st_p, sp = p.run_trace(reqs, arr)
+    assert np.array_equal(idx_a, idx_p) and np.array_equal(st_a, st_p)
+    assert sp["max_in_flight"] == 1
+    s = serving.latency_summary(la, arr, reqs.n_models)
+    assert s["p99_ms"] >= s["p50_ms"] > 0
