@@ -175,6 +175,67 @@ def executed_layer_evals(models, idx, st, nlim, cpl):
     return int(np.sum(pts * nl))
 
 
+def run_extras(args, masw, torch):
+    """Secondary workloads on the same line: the ragged batch (autotuned
+    persistent graph vs one launch per model), the differentiation batch
+    (misfit + adjoint gradient per second) and the serving trace (p50/p99
+    latency and curves/s of the continuous-batching server vs the plain
+    one-request-at-a-time path, per arrival rate)."""
+    from paper_2003_02256_gb300 import serving
+    out = {}
+    # ragged batch
+    m3, g3 = W.ragged_batch(n_models=args.ragged_models)
+    with masw.Batch(m3, g3) as b:
+        plan = b.autotune(reps=1)
+        b.dispersion()
+        times = []
+        for _ in range(2):
+            b.dispersion()
+            times.append(b.last_scan_ms())
+        t0 = time.perf_counter()
+        b.dispersion(plain=True)
+        plain_s = time.perf_counter() - t0
+    out["ragged_batch"] = {
+        "workload": f"{m3.n_models} models, N~U{{3..30}}, n_lambda~U{{30..400}} log-spaced to "
+                    "2x total depth, 10% low-velocity layer; c grid 50..1200 step 0.25",
+        "items": m3.n_items, "batched_curves_per_s": m3.n_models / (min(times) * 1e-3),
+        "plain_curves_per_s": m3.n_models / plain_s, "plan": plan.as_dict()}
+    # differentiation batch
+    m4, g4, true = W.differentiation_batch()
+    gold = np.loadtxt(os.path.join(ROOT, "tests", "golden", "differentiation_true_roots.txt"))
+    ce = np.tile(W.noisy_observation(gold[:, 2], sigma=2.0), m4.n_models)
+    with masw.Batch(m4, g4) as b:
+        b.misfit_grad(ce)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 2
+        for _ in range(reps):
+            b.misfit_grad(ce)
+        dt = (time.perf_counter() - t0) / reps
+    out["differentiation"] = {"workload": "512 models x 12 layers, 150 wavelengths, LSQ misfit "
+                                          "+ adjoint gradient (beta, h)",
+                              "gradients_per_s": m4.n_models / dt, "ms_per_batch": 1e3 * dt}
+    # serving
+    sampler = W.RandomWalkSampler()
+    reqs = W.concat([sampler.next() for _ in range(args.serving_requests)])
+    grid = W.Grid(50.0, 0.25, 4601)
+    rates = {}
+    for rate in (1e3, 1e4, 1e5):
+        arr = W.poisson_arrivals(reqs.n_models, rate=rate)
+        with serving.Server(grid, max_slots=2048, chunks_per_tick=8,
+                            mem_cap_bytes=16 << 30) as srv:
+            lat, _, _, _, st = srv.run_trace(reqs, arr)
+        with serving.Server(grid, max_slots=1, chunks_per_tick=1 << 20) as plain:
+            lat_p, _, _, _, _ = plain.run_trace(reqs, arr)
+        rates[f"{rate:g}"] = {"served": serving.latency_summary(lat, arr, reqs.n_models),
+                              "plain": serving.latency_summary(lat_p, arr, reqs.n_models),
+                              "ticks": st["ticks"], "max_in_flight": st["max_in_flight"]}
+    out["serving"] = {"workload": f"{reqs.n_models} random-walk model evaluations per rate "
+                                  "(layers 3..30, wavelengths 30..400), Poisson arrivals, "
+                                  "16 GB admission cap", "rates_per_s": rates}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,6 +245,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--ragged-models", type=int, default=8192)
+    ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--models", type=int, default=1024,
                     help="models per GPU (smaller only for profiler captures)")
     args = ap.parse_args()
@@ -299,6 +363,10 @@ def main():
                 "executed_layer_evals_per_launch": executed,
                 "scan_ms": scan_avg * 1e3}
 
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = run_extras(args, masw, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_oracle_rate(models, grid, 64)
@@ -323,7 +391,8 @@ def main():
                 "plain_gpu": None if plain_value is None else {
                     "value": plain_value, "unit": UNIT, "ms_per_step": min(plain_ms),
                     "speedup_of_batched": value / world / plain_value},
-                "found_fraction": float(np.mean(st == 0))}
+                "found_fraction": float(np.mean(st == 0)),
+                "extras": extras}
         print(json.dumps(line), flush=True)
     batch.close()
     if dist:
