@@ -100,6 +100,9 @@ typedef struct {
     int32_t ordered;         /* 1: queue ordered by predicted scan length (longest first) */
     int32_t stage_layers;    /* layer records staged in shared memory per warp (0: none) */
     int32_t use_graph;       /* 1: replay the scan as a captured CUDA graph */
+    int32_t precision;       /* 0: FP64 scan of every test velocity; 1: FP32 screen locates the
+                                first change, FP64 decides it (V[0], V[n-1], V[n], then an FP64
+                                window or full re-scan when they disagree) */
 } masw_plan;
 
 /* Copy and validate a model batch into batch-owned device memory and bind it
@@ -190,6 +193,11 @@ int masw_autotune(masw_batch* batch, int32_t reps, masw_plan* best);
 /* Device time (ms) of the most recent scan launched by masw_dispersion or
  * masw_dispersion_plain (CUDA events on the batch stream). */
 int masw_last_scan_ms(const masw_batch* batch, float* ms);
+
+/* Items of the most recent two-precision scan (plan precision 1) whose FP32
+ * screen disagreed with the FP64 check and were re-scanned in FP64 (-1 for a
+ * precision-0 plan). Synchronises the batch stream. */
+int masw_last_scan_unresolved(const masw_batch* batch, int32_t* n);
 
 /* FP64 fused multiply-add throughput of this GPU in flop/s (2 per DFMA),
  * measured by a dependent-chain microbenchmark on `cuda_stream`. */

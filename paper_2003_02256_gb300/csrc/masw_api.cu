@@ -26,6 +26,7 @@
 #include "../../include/masw.h"
 #include "masw_device.cuh"
 #include "masw_internal.h"
+#include "masw_screen.cuh"
 
 using namespace masw;
 
@@ -66,6 +67,12 @@ struct masw_batch {
     double* d_misfit = nullptr;
     double* d_gb = nullptr;
     double* d_gh = nullptr;
+    // two-precision scan
+    float* d_layers32 = nullptr;
+    int32_t* d_n32 = nullptr;
+    int32_t* d_ref = nullptr;
+    int32_t* d_unres = nullptr;
+    int32_t* d_counters3 = nullptr;
 
     masw_plan plan{};
     cudaGraphExec_t graph = nullptr;
@@ -217,6 +224,26 @@ static void build_records(masw_batch* B, const std::vector<double>& h, const std
     }
 }
 
+// FP32 records of the screen: stiffnesses divided by the half-space shear
+// modulus of the model (a positive common factor).
+static void build_records32(const masw_batch* B, const std::vector<double>& rec,
+                            std::vector<float>& rec32) {
+    rec32.assign((size_t)B->n_records * LAYER_STRIDE32, 0.0f);
+    for (int32_t m = 0; m < B->n_models; ++m) {
+        int lo = B->loff[m], N = B->n_layers[m];
+        double mref = rec[(size_t)(lo + N) * LAYER_STRIDE + L_MU];
+        for (int i = 0; i <= N; ++i) {
+            const double* L = &rec[(size_t)(lo + i) * LAYER_STRIDE];
+            float* F = &rec32[(size_t)(lo + i) * LAYER_STRIDE32];
+            F[F_H] = (float)L[L_H];
+            F[F_MU] = (float)(L[L_MU] / mref);
+            F[F_RHO] = (float)(L[L_RHO] / mref);
+            F[F_IA2] = (float)L[L_IA2];
+            F[F_IB2] = (float)L[L_IB2];
+        }
+    }
+}
+
 // Predicted scan length of an item (speed only): the first root sits near
 // 0.93 x the shear speed at depth ~ lambda/2.
 static double predicted_cost(const masw_batch* B, int32_t m, double lam,
@@ -241,7 +268,8 @@ static void free_batch(masw_batch* B) {
     void* ptrs[] = {B->d_layers, B->d_loff,  B->d_woff,  B->d_nlim,   B->d_k,
                     B->d_item_model, B->d_order_sorted, B->d_order_natural, B->d_grad_off,
                     B->d_counter, B->d_ct, B->d_idx, B->d_status, B->d_croot, B->d_rows, B->d_bs,
-                    B->d_dphi, B->d_ce, B->d_misfit, B->d_gb, B->d_gh};
+                    B->d_dphi, B->d_ce, B->d_misfit, B->d_gb, B->d_gh, B->d_layers32,
+                    B->d_n32, B->d_ref, B->d_unres, B->d_counters3};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete B;
@@ -256,6 +284,7 @@ static masw_plan default_plan(const masw_batch* B) {
     p.ordered = 1;
     p.stage_layers = std::min(B->max_layers + 1, 32);
     p.use_graph = 1;
+    p.precision = 1;
     return p;
 }
 
@@ -263,7 +292,8 @@ static bool plan_ok(const masw_plan& p) {
     bool wpb = p.warps_per_block == 1 || p.warps_per_block == 2 || p.warps_per_block == 4 ||
                p.warps_per_block == 8;
     bool cpl = p.cpl == 1 || p.cpl == 2 || p.cpl == 4;
-    return wpb && cpl && p.blocks_per_sm >= 1 && p.blocks_per_sm <= 32 && p.stage_layers >= 0 &&
+    return wpb && cpl && (p.precision == 0 || p.precision == 1) && p.blocks_per_sm >= 1 &&
+           p.blocks_per_sm <= 32 && p.stage_layers >= 0 &&
            p.stage_layers <= MASW_MAX_LAYERS + 1 &&
            (size_t)p.warps_per_block * p.stage_layers * LAYER_STRIDE * sizeof(double) <= 48 * 1024;
 }
@@ -280,6 +310,12 @@ static ScanPlan to_scan_plan(const masw_batch* B, const masw_plan& p) {
 
 // Enqueue one full scan (all items) with the given plan on stream s.
 static cudaError_t enqueue_scan(masw_batch* B, const masw_plan& p, cudaStream_t s) {
+    if (p.precision == 1) {
+        ScanOut o{B->d_ct, B->d_idx, B->d_status};
+        return launch_screen_scan(B->dev(p.ordered != 0), o, to_scan_plan(B, p), B->d_layers32,
+                                  B->d_n32, B->d_ref, B->d_unres, B->d_counters3, 0,
+                                  (int)B->n_items, s);
+    }
     if (p.persistent) {
         cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(int32_t), s);
         if (e != cudaSuccess) return e;
@@ -439,6 +475,8 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
                      [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
     std::vector<double> rec;
     build_records(B, h, a, b, r, rec);
+    std::vector<float> rec32;
+    build_records32(B, rec, rec32);
 
     if ((rc = masw_sm_count(&B->sm_count))) {
         free_batch(B);
@@ -449,7 +487,9 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
         dev_alloc(&B->d_k, nw) || dev_alloc(&B->d_item_model, nw) ||
         dev_alloc(&B->d_order_sorted, nw) || dev_alloc(&B->d_order_natural, nw) ||
         dev_alloc(&B->d_grad_off, nw + 1) || dev_alloc(&B->d_counter, 1) ||
-        dev_alloc(&B->d_ct, nw) || dev_alloc(&B->d_idx, nw) || dev_alloc(&B->d_status, nw)) {
+        dev_alloc(&B->d_ct, nw) || dev_alloc(&B->d_idx, nw) || dev_alloc(&B->d_status, nw) ||
+        dev_alloc(&B->d_layers32, rec32.size()) || dev_alloc(&B->d_n32, nw) ||
+        dev_alloc(&B->d_ref, nw) || dev_alloc(&B->d_unres, nw) || dev_alloc(&B->d_counters3, 3)) {
         free_batch(B);
         return MASW_ENOMEM;
     }
@@ -458,6 +498,7 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
     };
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = up(B->d_layers, rec.data(), rec.size() * sizeof(double));
+    if (e == cudaSuccess) e = up(B->d_layers32, rec32.data(), rec32.size() * sizeof(float));
     if (e == cudaSuccess) e = up(B->d_loff, B->loff.data(), B->loff.size() * 4);
     if (e == cudaSuccess) e = up(B->d_woff, B->woff.data(), B->woff.size() * 4);
     if (e == cudaSuccess) e = up(B->d_nlim, B->nlim.data(), B->nlim.size() * 4);
@@ -504,9 +545,12 @@ int masw_model_batch_update(masw_batch* B, const double* h, const double* alpha,
     for (int32_t m = 0; m < B->n_models; ++m) nlim[m] = scan_limit(B->grid, b[B->loff[m + 1] - 1]);
     std::vector<double> rec;
     build_records(B, hv, a, b, r, rec);
+    std::vector<float> rec32;
+    build_records32(B, rec, rec32);
     // the upload is ordered after work already queued on the batch stream
     CK(cudaStreamSynchronize(B->stream));
     CK(cudaMemcpy(B->d_layers, rec.data(), rec.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(B->d_layers32, rec32.data(), rec32.size() * sizeof(float), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(B->d_nlim, nlim.data(), nlim.size() * 4, cudaMemcpyHostToDevice));
     B->nlim = nlim;
     return MASW_OK;
@@ -529,7 +573,8 @@ int masw_model_batch_update_beta_h(masw_batch* B, const double* h, const double*
     if (hdev) dh = const_cast<double*>(h);
     int32_t herr = 0;
     CK(cudaMemsetAsync(B->d_counter, 0, sizeof(int32_t), B->stream));
-    CK(launch_update_beta_h(B->dev(false), dh, db, B->d_layers, B->d_nlim, B->d_counter, B->stream));
+    CK(launch_update_beta_h(B->dev(false), dh, db, B->d_layers, B->d_layers32, B->d_nlim,
+                            B->d_counter, B->stream));
     CK(cudaMemcpyAsync(&herr, B->d_counter, sizeof(int32_t), cudaMemcpyDeviceToHost, B->stream));
     CK(cudaStreamSynchronize(B->stream));
     return herr ? MASW_EINVAL : MASW_OK;
@@ -573,11 +618,28 @@ int masw_dispersion_plain(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* s
     ScanPlan sp = to_scan_plan(B, p);
     CK(cudaEventRecord(B->ev0, B->stream));
     for (int32_t m = 0; m < B->n_models; ++m) {
-        CK(launch_scan(d, o, sp, B->d_counter, B->woff[m], B->woff[m + 1], B->stream));
+        if (p.precision == 1)
+            CK(launch_screen_scan(d, o, sp, B->d_layers32, B->d_n32, B->d_ref, B->d_unres,
+                                  B->d_counters3, B->woff[m], B->woff[m + 1], B->stream));
+        else
+            CK(launch_scan(d, o, sp, B->d_counter, B->woff[m], B->woff[m + 1], B->stream));
         CK(cudaStreamSynchronize(B->stream));
     }
     CK(cudaEventRecord(B->ev1, B->stream));
     return finish_outputs(B, ct, ct_idx, status);
+}
+
+int masw_last_scan_unresolved(const masw_batch* B, int32_t* n) {
+    if (!B || !n) return MASW_EINVAL;
+    if (B->plan.precision != 1) {
+        *n = -1;
+        return MASW_OK;
+    }
+    int32_t v = 0;
+    CK(cudaStreamSynchronize(B->stream));
+    CK(cudaMemcpy(&v, B->d_counters3 + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    *n = v;
+    return MASW_OK;
 }
 
 int masw_last_scan_ms(const masw_batch* B, float* ms) {
@@ -724,7 +786,7 @@ bool g_cache_loaded = false;
 std::tuple<int, int, int> cache_key(const masw_batch* B) {
     int bucket = 0;
     for (int64_t n = B->n_items; n > 1; n >>= 1) ++bucket;
-    return {B->max_layers, B->grid.n_c, bucket};
+    return {B->max_layers * 2 + B->plan.precision, B->grid.n_c, bucket};
 }
 
 void load_cache_file() {
@@ -736,8 +798,9 @@ void load_cache_file() {
     if (!f) return;
     int a, b, c;
     masw_plan p;
-    while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d", &a, &b, &c, &p.warps_per_block, &p.cpl,
-                  &p.blocks_per_sm, &p.persistent, &p.ordered, &p.stage_layers, &p.use_graph) == 10)
+    while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d", &a, &b, &c, &p.warps_per_block, &p.cpl,
+                  &p.blocks_per_sm, &p.persistent, &p.ordered, &p.stage_layers, &p.use_graph,
+                  &p.precision) == 11)
         if (plan_ok(p)) g_cache[{a, b, c}] = p;
     fclose(f);
 }
@@ -749,9 +812,9 @@ void save_cache_file() {
     if (!f) return;
     for (auto& kv : g_cache) {
         const masw_plan& p = kv.second;
-        fprintf(f, "%d %d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
-                std::get<2>(kv.first), p.warps_per_block, p.cpl, p.blocks_per_sm, p.persistent,
-                p.ordered, p.stage_layers, p.use_graph);
+        fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first),
+                std::get<1>(kv.first), std::get<2>(kv.first), p.warps_per_block, p.cpl,
+                p.blocks_per_sm, p.persistent, p.ordered, p.stage_layers, p.use_graph, p.precision);
     }
     fclose(f);
 }
@@ -776,10 +839,10 @@ int masw_autotune(masw_batch* B, int32_t reps, masw_plan* best) {
     for (int wpb : {2, 4, 8})
         for (int cpl : {1, 2})
             for (int bps : {2, 4, 8, 16}) {
-                masw_plan p{wpb, cpl, bps, 1, 1, stage, 1};
+                masw_plan p{wpb, cpl, bps, 1, 1, stage, 1, B->plan.precision};
                 if (plan_ok(p)) cands.push_back(p);
             }
-    masw_plan flat{8, 1, 1, 0, 1, stage, 1};
+    masw_plan flat{8, 1, 1, 0, 1, stage, 1, B->plan.precision};
     if (plan_ok(flat)) cands.push_back(flat);
     float best_ms = 1e30f;
     masw_plan bestp = B->plan;

@@ -38,6 +38,12 @@ struct ScanPlan {
     int stage_layers;     // layer records staged in shared memory per warp (0 = read global)
 };
 
+// FP32 screen + FP64 decision (masw_screen.cuh, masw_kernels.cu).
+cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p,
+                               const float* layers32, int32_t* n32, int32_t* ref_sign,
+                               int32_t* unresolved, int32_t* counters, int item_begin,
+                               int item_end, cudaStream_t s);
+
 cudaError_t launch_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p, int32_t* counter,
                         int item_begin, int item_end, cudaStream_t s);
 cudaError_t launch_det_eval(const DevBatch& b, int n, const int32_t* item, const double* c,
@@ -51,7 +57,8 @@ cudaError_t launch_misfit(const DevBatch& b, const double* ct, const double* ce,
 cudaError_t launch_grad_reduce(const DevBatch& b, const double* rows, const double* dphi_dc,
                                double* grad_beta, double* grad_h, cudaStream_t s);
 cudaError_t launch_update_beta_h(const DevBatch& b, const double* h, const double* beta,
-                                 double* layers, int32_t* nlim, int32_t* err, cudaStream_t s);
+                                 double* layers, float* layers32, int32_t* nlim, int32_t* err,
+                                 cudaStream_t s);
 cudaError_t launch_fp64_peak(int blocks, int threads, int iters, double* sink, cudaStream_t s);
 
 }  // namespace masw

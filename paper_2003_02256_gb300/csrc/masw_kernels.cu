@@ -16,9 +16,12 @@
 //                   dPhi/dC per item; deterministic warp reductions.
 //  grad_reduce      dPhi/dtheta = sum_j dPhi/dC_j dC_j/dtheta per model.
 //  fp64_peak_kernel DFMA throughput microbenchmark (roofline denominator).
+#include <algorithm>
+
 #include "masw_adjoint.cuh"
 #include "masw_device.cuh"
 #include "masw_internal.h"
+#include "masw_screen.cuh"
 
 namespace masw {
 
@@ -126,6 +129,229 @@ cudaError_t launch_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p, 
         default:
             return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- two-precision scan
+//
+// 1. screen32_kernel: the scan of scan_kernel in FP32 (det_sign_f), giving
+//    the FP32 first sign change n32 per item (-1 if none below the limit).
+// 2. verify64_kernel: one thread per item, FP64 signs (det_sign) at V[0],
+//    V[n32-1], V[n32]; the item is resolved to n32 when V[0] and V[n32-1]
+//    agree and V[n32] differs (or, for n32 = -1, to "no root" when V[0] and
+//    the last scanned point agree); otherwise it goes to the unresolved list.
+// 3. resolve64_kernel: one warp per unresolved item, FP64 chunked scan
+//    starting 16 points below n32 (its first point must carry V[0]'s sign,
+//    else from V[0]), continuing until the first FP64 change.
+// Every reported index is a sign change of the FP64 recurrence whose lower
+// point carries the FP64 sign of V[0].
+
+template <int CPL>
+__global__ void __launch_bounds__(256) screen32_kernel(DevBatch b, const float* __restrict__ layers32,
+                                                       int32_t* n32out, int persistent,
+                                                       int stage_layers, int32_t* counter,
+                                                       int item_begin, int item_end) {
+    extern __shared__ float smemf[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    float* my = smemf + (size_t)wib * stage_layers * LAYER_STRIDE32;
+    int pos;
+    if (persistent) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1);
+        pos = item_begin + __shfl_sync(FULL, t, 0);
+    } else {
+        pos = item_begin + blockIdx.x * wpb + wib;
+    }
+    const float c0 = (float)b.c0, dc = (float)b.dc;
+    while (pos < item_end) {
+        const int item = b.order[pos];
+        const int m = b.item_model[item];
+        const int lo = b.model_loff[m];
+        const int nrec = b.model_loff[m + 1] - lo;
+        const int N = nrec - 1;
+        const float* lay = layers32 + (size_t)lo * LAYER_STRIDE32;
+        if (nrec <= stage_layers) {
+            for (int t = lane; t < nrec * LAYER_STRIDE32; t += 32) my[t] = lay[t];
+            __syncwarp();
+            lay = my;
+        }
+        const float k = (float)b.k[item];
+        const int nlim = b.model_nlim[m];
+        int res = -1;
+        if (nlim >= 2) {
+            int carry = 0;
+            for (int base = 0; base < nlim && res < 0; base += 32 * CPL) {
+                int sg[CPL];
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) {
+                    int n = base + j * 32 + lane;
+                    sg[j] = (n < nlim) ? det_sign_f(lay, N, k, fmaf((float)n, dc, c0)) : 0;
+                }
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) {
+                    if (res < 0) {
+                        int n = base + j * 32 + lane;
+                        int prev = __shfl_up_sync(FULL, sg[j], 1);
+                        if (lane == 0) prev = carry;
+                        unsigned msk = __ballot_sync(FULL, n >= 1 && n < nlim && sg[j] != prev);
+                        if (msk) res = base + j * 32 + __ffs(msk) - 1;
+                        carry = __shfl_sync(FULL, sg[j], 31);
+                    }
+                }
+            }
+        }
+        if (lane == 0) n32out[item] = res;
+        __syncwarp();
+        if (persistent) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(counter, 1);
+            pos = item_begin + __shfl_sync(FULL, t, 0);
+        } else {
+            pos = item_end;
+        }
+    }
+}
+
+__device__ __forceinline__ void write_result(const DevBatch& b, const ScanOut& o, int item, int res) {
+    if (res >= 0) {
+        o.ct[item] = grid_c(b.c0, b.dc, res);
+        o.idx[item] = res;
+        o.status[item] = 0;
+    } else {
+        o.ct[item] = __longlong_as_double(0x7ff8000000000000LL);
+        o.idx[item] = -1;
+        o.status[item] = 1;
+    }
+}
+
+__global__ void verify64_kernel(DevBatch b, ScanOut o, const int32_t* __restrict__ n32,
+                                int32_t* ref_sign, int32_t* unresolved, int32_t* n_unresolved,
+                                int item_begin, int item_end) {
+    int pos = item_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= item_end) return;
+    const int item = b.order[pos];
+    const int m = b.item_model[item];
+    const int lo = b.model_loff[m];
+    const int N = b.model_loff[m + 1] - lo - 1;
+    const double* lay = b.layers + (size_t)lo * LAYER_STRIDE;
+    const double k = b.k[item];
+    const int nlim = b.model_nlim[m];
+    if (nlim < 2) {
+        write_result(b, o, item, -1);
+        return;
+    }
+    const int n = n32[item];
+    int s0 = det_sign(lay, N, k, grid_c(b.c0, b.dc, 0));
+    bool ok;
+    if (n >= 1) {
+        int sa = (n == 1) ? s0 : det_sign(lay, N, k, grid_c(b.c0, b.dc, n - 1));
+        int sb = det_sign(lay, N, k, grid_c(b.c0, b.dc, n));
+        ok = (sa == s0) && (sb != sa);
+    } else {
+        int sz = det_sign(lay, N, k, grid_c(b.c0, b.dc, nlim - 1));
+        ok = (sz == s0);
+    }
+    if (ok) {
+        write_result(b, o, item, n >= 1 ? n : -1);
+    } else {
+        ref_sign[item] = s0;
+        unresolved[atomicAdd(n_unresolved, 1)] = item;
+    }
+}
+
+__global__ void __launch_bounds__(256) resolve64_kernel(DevBatch b, ScanOut o,
+                                                        const int32_t* __restrict__ n32,
+                                                        const int32_t* __restrict__ ref_sign,
+                                                        const int32_t* __restrict__ unresolved,
+                                                        const int32_t* __restrict__ n_unresolved,
+                                                        int32_t* counter) {
+    const int lane = threadIdx.x & 31;
+    const int total = *n_unresolved;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= total) return;
+        const int item = unresolved[t];
+        const int m = b.item_model[item];
+        const int lo = b.model_loff[m];
+        const int N = b.model_loff[m + 1] - lo - 1;
+        const double* lay = b.layers + (size_t)lo * LAYER_STRIDE;
+        const double k = b.k[item];
+        const int nlim = b.model_nlim[m];
+        const int ref = ref_sign[item];
+        const int n = n32[item];
+        int base = 0, carry = 0, res = -1;
+        if (n >= 18) {
+            // window from n - 17: its first point must carry V[0]'s sign
+            base = n - 17;
+            int nn = base + lane;
+            int sg = (nn < nlim) ? det_sign(lay, N, k, grid_c(b.c0, b.dc, nn)) : 0;
+            int first = __shfl_sync(FULL, sg, 0);
+            if (first != ref) {
+                base = 0;  // an FP64 change below the window: scan from V[0]
+            } else {
+                int prev = __shfl_up_sync(FULL, sg, 1);
+                unsigned msk = __ballot_sync(FULL, lane >= 1 && nn < nlim && sg != prev);
+                if (msk) res = base + __ffs(msk) - 1;
+                carry = __shfl_sync(FULL, sg, 31);
+                base += 32;
+            }
+        }
+        for (; base < nlim && res < 0; base += 32) {
+            int nn = base + lane;
+            int sg = (nn < nlim) ? det_sign(lay, N, k, grid_c(b.c0, b.dc, nn)) : 0;
+            int prev = __shfl_up_sync(FULL, sg, 1);
+            if (lane == 0) prev = carry;
+            unsigned msk = __ballot_sync(FULL, nn >= 1 && nn < nlim && sg != prev);
+            if (msk) res = base + __ffs(msk) - 1;
+            carry = __shfl_sync(FULL, sg, 31);
+        }
+        if (lane == 0) write_result(b, o, item, res);
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p,
+                               const float* layers32, int32_t* n32, int32_t* ref_sign,
+                               int32_t* unresolved, int32_t* counters, int item_begin,
+                               int item_end, cudaStream_t s) {
+    if (item_end <= item_begin) return cudaSuccess;
+    // counters: [0] screen queue, [1] unresolved count, [2] resolve queue
+    cudaError_t e = cudaMemsetAsync(counters, 0, 3 * sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    int wpb = p.warps_per_block;
+    int blocks = p.persistent ? p.blocks : (item_end - item_begin + wpb - 1) / wpb;
+    size_t shm = (size_t)wpb * p.stage_layers * LAYER_STRIDE32 * sizeof(float);
+    switch (p.cpl) {
+        case 1:
+            screen32_kernel<1><<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,
+                                                            p.stage_layers, counters, item_begin,
+                                                            item_end);
+            break;
+        case 2:
+            screen32_kernel<2><<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,
+                                                            p.stage_layers, counters, item_begin,
+                                                            item_end);
+            break;
+        case 4:
+            screen32_kernel<4><<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,
+                                                            p.stage_layers, counters, item_begin,
+                                                            item_end);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int n = item_end - item_begin;
+    verify64_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, o, n32, ref_sign, unresolved, counters + 1,
+                                                    item_begin, item_end);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int rblocks = std::max(1, std::min(p.blocks, (n + wpb - 1) / wpb));
+    resolve64_kernel<<<rblocks, 32 * wpb, 0, s>>>(b, o, n32, ref_sign, unresolved, counters + 1,
+                                                  counters + 2);
     return cudaGetLastError();
 }
 
@@ -428,7 +654,7 @@ cudaError_t launch_grad_reduce(const DevBatch& b, const double* rows, const doub
 // limit; any invalid value sets *err (records are then unspecified).
 __global__ void update_beta_h_kernel(DevBatch b, const double* __restrict__ h,
                                      const double* __restrict__ beta, double* layers,
-                                     int32_t* nlim, int32_t* err) {
+                                     float* layers32, int32_t* nlim, int32_t* err) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= b.n_models) return;
     int lo = b.model_loff[m];
@@ -445,6 +671,16 @@ __global__ void update_beta_h_kernel(DevBatch b, const double* __restrict__ h,
         L[L_IA2] = 1.0 / (a * a);
         L[L_IB2] = 1.0 / (be * be);
         L[L_BETA] = be;
+        if (layers32) {
+            double mref = layers[(size_t)(lo + N) * LAYER_STRIDE + L_RHO] * beta[lo + N] *
+                          beta[lo + N];
+            float* F = layers32 + (size_t)(lo + i) * LAYER_STRIDE32;
+            F[F_H] = (float)hh;
+            F[F_MU] = (float)(L[L_MU] / mref);
+            F[F_RHO] = (float)(L[L_RHO] / mref);
+            F[F_IA2] = (float)L[L_IA2];
+            F[F_IB2] = (float)L[L_IB2];
+        }
     }
     double bhs = beta[lo + N];
     double est = floor((bhs - b.c0) / b.dc);
@@ -455,9 +691,11 @@ __global__ void update_beta_h_kernel(DevBatch b, const double* __restrict__ h,
 }
 
 cudaError_t launch_update_beta_h(const DevBatch& b, const double* h, const double* beta,
-                                 double* layers, int32_t* nlim, int32_t* err, cudaStream_t s) {
+                                 double* layers, float* layers32, int32_t* nlim, int32_t* err,
+                                 cudaStream_t s) {
     if (b.n_models <= 0) return cudaSuccess;
-    update_beta_h_kernel<<<(b.n_models + 127) / 128, 128, 0, s>>>(b, h, beta, layers, nlim, err);
+    update_beta_h_kernel<<<(b.n_models + 127) / 128, 128, 0, s>>>(b, h, beta, layers, layers32,
+                                                                  nlim, err);
     return cudaGetLastError();
 }
 

@@ -46,7 +46,7 @@ class Plan(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_int32), ("cpl", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("ordered", ctypes.c_int32), ("stage_layers", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -243,6 +243,15 @@ def last_scan_ms(handle) -> float:
     return ms.value
 
 
+def last_scan_unresolved(handle) -> int:
+    f = load().masw_last_scan_unresolved
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
+    f.restype = ctypes.c_int
+    n = ctypes.c_int32()
+    _check(f(ctypes.c_void_p(handle), ctypes.byref(n)), "masw_last_scan_unresolved")
+    return n.value
+
+
 def fp64_peak(stream=None) -> float:
     f = ctypes.c_double()
     _check(load().masw_fp64_peak(_stream_handle(stream), ctypes.byref(f)), "masw_fp64_peak")
@@ -355,6 +364,9 @@ class Batch:
 
     def last_scan_ms(self) -> float:
         return last_scan_ms(self.handle)
+
+    def last_scan_unresolved(self) -> int:
+        return last_scan_unresolved(self.handle)
 
 
 # ------------------------------------------------------------ no allocation

@@ -86,10 +86,11 @@ def test_coarse_grid_with_ragged_tail(masw, oracle_lib):
     g = W.Grid(61.3, 0.77, 1013)
     o_ct, o_idx, o_st = oracle_lib.dispersion(m.as_dict(), g.c0, g.dc, g.n_c)
     with masw.Batch(m, g) as b:
-        for cpl in (1, 2, 4):
-            b.set_plan(cpl=cpl)
-            ct, idx, st = b.dispersion()
-            assert_index_parity(idx, st, o_idx, o_st)
+        for precision in (0, 1):
+            for cpl in (1, 2, 4):
+                b.set_plan(cpl=cpl, precision=precision)
+                ct, idx, st = b.dispersion()
+                assert_index_parity(idx, st, o_idx, o_st)
 
 
 # ---------------------------------------------------- full-size, sampled
@@ -203,6 +204,22 @@ def test_invalid_inputs_are_rejected(masw):
 
 # ------------------------------------------------------- plans and paths
 
+@pytest.mark.parametrize("which", ["uniform", "ragged"])
+def test_two_precision_scan_equals_the_fp64_scan_at_full_size(masw, which):
+    """The FP32 screen only locates the change; every reported index is an
+    FP64 decision, so the two plans agree item for item."""
+    m, g = W.uniform_batch() if which == "uniform" else W.ragged_batch()
+    with masw.Batch(m, g) as b:
+        b.set_plan(precision=1)
+        ct1, idx1, st1 = b.dispersion()
+        unresolved = b.last_scan_unresolved()
+        b.set_plan(precision=0)
+        ct0, idx0, st0 = b.dispersion()
+    assert np.array_equal(idx1, idx0) and np.array_equal(st1, st0)
+    assert np.array_equal(ct1, ct0, equal_nan=True)
+    assert 0 <= unresolved < 0.5 * m.n_items
+
+
 def test_every_plan_and_the_plain_path_give_identical_indices(masw):
     m, g = W.ragged_batch(n_models=64, seed=77)
     with masw.Batch(m, g) as b:
@@ -212,7 +229,8 @@ def test_every_plan_and_the_plain_path_give_identical_indices(masw):
         assert np.array_equal(ref[1], plain[1]) and np.array_equal(ref[2], plain[2])
         for plan in (dict(persistent=0), dict(ordered=0), dict(use_graph=0),
                      dict(stage_layers=0), dict(warps_per_block=2, blocks_per_sm=1),
-                     dict(cpl=2), dict(cpl=4)):
+                     dict(cpl=2), dict(cpl=4), dict(precision=0), dict(precision=0, cpl=2),
+                     dict(precision=1, persistent=0)):
             b.set_plan(**plan)
             got = b.dispersion()
             assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2]), plan
