@@ -42,6 +42,11 @@ WORKLOAD = ("uniform_batch: 1024 models x (8 layers + half-space), h~U[1,8] m, b
 # Schur step): 2*DFMA + DADD + DMUL executed per evaluated (layer, c) pair,
 # from ncu instruction counters on this workload (profiles/).
 F_LAYER_FLOPS = 162.3
+# FP32 flops per layer-evaluation of the screen kernel (2*FFMA + FMUL + FADD
+# per evaluated (layer, c) pair, ncu instruction counters; profiles/).
+F_LAYER_FLOPS_FP32 = 150.0
+# FP32 pipe: FFMA issue rate per SM per clock.
+FP32_FFMA_PER_CLK_SM = 128.0
 # FP64 pipe of GB300: DFMA issue rate per SM per clock (ncu peak_sustained) and
 # the maximum SM clock.
 FP64_DFMA_PER_CLK_SM = 2.0
@@ -248,6 +253,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--ragged-models", type=int, default=8192)
     ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--precision", type=int, default=None, choices=[0, 1],
+                    help="scan plan: 0 FP64 scan, 1 FP32 screen + FP64 decision (default: library)")
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "ragged"],
+                    help="main workload (ragged only for profiling the ragged batch)")
     ap.add_argument("--models", type=int, default=1024,
                     help="models per GPU (smaller only for profiler captures)")
     args = ap.parse_args()
@@ -265,9 +274,14 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
 
-    models, grid = W.uniform_batch(n_models=args.models, seed=W.SEED + 1000 * rank)
+    if args.workload == "uniform":
+        models, grid = W.uniform_batch(n_models=args.models, seed=W.SEED + 1000 * rank)
+    else:
+        models, grid = W.ragged_batch(n_models=args.models, seed=W.SEED + 3 + 1000 * rank)
     ce_host = W.noisy_observation(np.full(models.n_items, 250.0), sigma=30.0, seed=rank)
     batch = masw.Batch(models, grid)
+    if args.precision is not None:
+        batch.set_plan(precision=args.precision)
     if not args.no_autotune:
         plan = batch.autotune(reps=1)
     else:
@@ -345,6 +359,21 @@ def main():
     h2d = sum(x.numel() * 8 for x in (hh, ha, hb, hr, hce))
     d2h = hphi.numel() * 8
 
+    # per-kernel device times of the two-precision scan (same kernels, launched
+    # without the graph so events can sit between them)
+    phases = None
+    unresolved = None
+    if plan.precision == 1:
+        batch.set_plan(use_graph=0)
+        ph = []
+        for _ in range(3):
+            flush.zero_()
+            batch.dispersion()
+            ph.append(masw.last_scan_phases(batch.handle))
+        unresolved = batch.last_scan_unresolved()
+        batch.set_plan(use_graph=plan.use_graph)
+        phases = [float(np.mean([p[i] for p in ph])) for i in range(3)]
+
     # roofline of the scan kernel: algorithmic FP64 flops / device time, against
     # the FP64 peak derived from unit counts and the maximum SM clock
     # (2 DFMA per clock per SM x 2 flops x SMs x 2070 MHz); the live DFMA
@@ -352,16 +381,33 @@ def main():
     micro = masw.fp64_peak()
     peak = FP64_DFMA_PER_CLK_SM * 2.0 * masw.sm_count() * SM_MAX_MHZ * 1e6
     scan_avg = float(np.mean(scan_ms)) * 1e-3
-    achieved = units * F_LAYER_FLOPS / scan_avg
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": SCAN_DRAM_BYTES_PER_MODEL * models.n_models,
-                "kernel": "scan_kernel (FP64 pipe)",
-                "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
-                "peak_microbenchmark": micro / 1e12,
-                "layer_evals_per_launch": units, "flops_per_layer_eval": F_LAYER_FLOPS,
-                "executed_layer_evals_per_launch": executed,
-                "scan_ms": scan_avg * 1e3}
+    if phases is None:
+        achieved = units * F_LAYER_FLOPS / scan_avg
+        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": SCAN_DRAM_BYTES_PER_MODEL * models.n_models,
+                    "kernel": "scan_kernel (FP64 pipe)",
+                    "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
+                    "peak_microbenchmark": micro / 1e12,
+                    "layer_evals_per_launch": units, "flops_per_layer_eval": F_LAYER_FLOPS,
+                    "executed_layer_evals_per_launch": executed,
+                    "scan_ms": scan_avg * 1e3}
+    else:
+        peak32 = FP32_FFMA_PER_CLK_SM * 2.0 * masw.sm_count() * SM_MAX_MHZ * 1e6
+        t_screen = phases[0] * 1e-3
+        achieved = units * F_LAYER_FLOPS_FP32 / t_screen
+        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak32 / 1e12,
+                    "unit": "TFLOP/s", "frac": achieved / peak32, "traffic": None,
+                    "kernel": "screen32_kernel (FP32 pipe)",
+                    "peak_source": "derived: 128 FFMA/clk/SM x 2 flop x SMs x 2070 MHz",
+                    "layer_evals_per_launch": units,
+                    "flops_per_layer_eval": F_LAYER_FLOPS_FP32,
+                    "executed_layer_evals_per_launch": executed,
+                    "scan_ms": scan_avg * 1e3,
+                    "phases_ms": {"screen32": phases[0], "verify64": phases[1],
+                                  "resolve64": phases[2]},
+                    "fp64_peak_derived": peak / 1e12, "fp64_peak_microbenchmark": micro / 1e12,
+                    "unresolved_items": unresolved}
 
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
@@ -385,7 +431,7 @@ def main():
                 "clocks": clk.summary(),
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": 2 * args.steps,
+                "gpu_launches": (4 if plan.precision == 1 else 2) * args.steps,
                 "roofline": roofline,
                 "cpu_baseline": cpu,
                 "plain_gpu": None if plain_value is None else {

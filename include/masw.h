@@ -194,6 +194,12 @@ int masw_autotune(masw_batch* batch, int32_t reps, masw_plan* best);
  * masw_dispersion_plain (CUDA events on the batch stream). */
 int masw_last_scan_ms(const masw_batch* batch, float* ms);
 
+/* Device time (ms) of the three kernels of the most recent two-precision
+ * scan launched without a graph (plan use_graph 0): ms[0] FP32 screen, ms[1]
+ * FP64 check, ms[2] FP64 re-scan (CUDA events between the launches on the
+ * batch stream). MASW_EINVAL when that scan was graph-replayed. */
+int masw_last_scan_phases(const masw_batch* batch, float* ms);
+
 /* Items of the most recent two-precision scan (plan precision 1) whose FP32
  * screen disagreed with the FP64 check and were re-scanned in FP64 (-1 for a
  * precision-0 plan). Synchronises the batch stream. */

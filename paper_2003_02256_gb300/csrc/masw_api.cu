@@ -77,6 +77,8 @@ struct masw_batch {
     masw_plan plan{};
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t phase_ev[2] = {nullptr, nullptr};
+    bool phases_valid = false;
     float last_ms = 0.f;
 
     DevBatch dev(bool ordered) const {
@@ -265,6 +267,8 @@ static void free_batch(masw_batch* B) {
     if (B->graph) cudaGraphExecDestroy(B->graph);
     if (B->ev0) cudaEventDestroy(B->ev0);
     if (B->ev1) cudaEventDestroy(B->ev1);
+    for (cudaEvent_t e : B->phase_ev)
+        if (e) cudaEventDestroy(e);
     void* ptrs[] = {B->d_layers, B->d_loff,  B->d_woff,  B->d_nlim,   B->d_k,
                     B->d_item_model, B->d_order_sorted, B->d_order_natural, B->d_grad_off,
                     B->d_counter, B->d_ct, B->d_idx, B->d_status, B->d_croot, B->d_rows, B->d_bs,
@@ -309,12 +313,13 @@ static ScanPlan to_scan_plan(const masw_batch* B, const masw_plan& p) {
 }
 
 // Enqueue one full scan (all items) with the given plan on stream s.
-static cudaError_t enqueue_scan(masw_batch* B, const masw_plan& p, cudaStream_t s) {
+static cudaError_t enqueue_scan(masw_batch* B, const masw_plan& p, cudaStream_t s,
+                                bool phase_events = false) {
     if (p.precision == 1) {
         ScanOut o{B->d_ct, B->d_idx, B->d_status};
         return launch_screen_scan(B->dev(p.ordered != 0), o, to_scan_plan(B, p), B->d_layers32,
                                   B->d_n32, B->d_ref, B->d_unres, B->d_counters3, 0,
-                                  (int)B->n_items, s);
+                                  (int)B->n_items, s, phase_events ? B->phase_ev : nullptr);
     }
     if (p.persistent) {
         cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(int32_t), s);
@@ -354,8 +359,11 @@ static int run_scan(masw_batch* B) {
     CK(cudaEventRecord(B->ev0, B->stream));
     if (B->plan.use_graph && B->graph) {
         CK(cudaGraphLaunch(B->graph, B->stream));
+        B->phases_valid = false;
     } else {
-        CK(enqueue_scan(B, B->plan, B->stream));
+        bool ph = B->plan.precision == 1;
+        CK(enqueue_scan(B, B->plan, B->stream, ph));
+        B->phases_valid = ph;
     }
     CK(cudaEventRecord(B->ev1, B->stream));
     return MASW_OK;
@@ -509,6 +517,8 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
     if (e == cudaSuccess) e = up(B->d_grad_off, B->grad_off.data(), (nw + 1) * 8);
     if (e == cudaSuccess) e = cudaEventCreate(&B->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&B->ev1);
+    if (e == cudaSuccess) e = cudaEventCreate(&B->phase_ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&B->phase_ev[1]);
     if (e != cudaSuccess) {
         record_cuda_error(e, "batch upload", __LINE__);
         free_batch(B);
@@ -620,13 +630,23 @@ int masw_dispersion_plain(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* s
     for (int32_t m = 0; m < B->n_models; ++m) {
         if (p.precision == 1)
             CK(launch_screen_scan(d, o, sp, B->d_layers32, B->d_n32, B->d_ref, B->d_unres,
-                                  B->d_counters3, B->woff[m], B->woff[m + 1], B->stream));
+                                  B->d_counters3, B->woff[m], B->woff[m + 1], B->stream, nullptr));
         else
             CK(launch_scan(d, o, sp, B->d_counter, B->woff[m], B->woff[m + 1], B->stream));
         CK(cudaStreamSynchronize(B->stream));
     }
     CK(cudaEventRecord(B->ev1, B->stream));
     return finish_outputs(B, ct, ct_idx, status);
+}
+
+int masw_last_scan_phases(const masw_batch* B, float* ms) {
+    if (!B || !ms) return MASW_EINVAL;
+    if (!B->phases_valid) return MASW_EINVAL;
+    CK(cudaEventSynchronize(B->ev1));
+    CK(cudaEventElapsedTime(&ms[0], B->ev0, B->phase_ev[0]));
+    CK(cudaEventElapsedTime(&ms[1], B->phase_ev[0], B->phase_ev[1]));
+    CK(cudaEventElapsedTime(&ms[2], B->phase_ev[1], B->ev1));
+    return MASW_OK;
 }
 
 int masw_last_scan_unresolved(const masw_batch* B, int32_t* n) {

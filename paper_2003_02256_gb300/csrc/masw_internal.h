@@ -42,7 +42,7 @@ struct ScanPlan {
 cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p,
                                const float* layers32, int32_t* n32, int32_t* ref_sign,
                                int32_t* unresolved, int32_t* counters, int item_begin,
-                               int item_end, cudaStream_t s);
+                               int item_end, cudaStream_t s, cudaEvent_t* phase_ev);
 
 cudaError_t launch_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p, int32_t* counter,
                         int item_begin, int item_end, cudaStream_t s);

@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256) resolve64_kernel(DevBatch b, ScanOut o,
 cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p,
                                const float* layers32, int32_t* n32, int32_t* ref_sign,
                                int32_t* unresolved, int32_t* counters, int item_begin,
-                               int item_end, cudaStream_t s) {
+                               int item_end, cudaStream_t s, cudaEvent_t* phase_ev) {
     if (item_end <= item_begin) return cudaSuccess;
     // counters: [0] screen queue, [1] unresolved count, [2] resolve queue
     cudaError_t e = cudaMemsetAsync(counters, 0, 3 * sizeof(int32_t), s);
@@ -345,10 +345,12 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
             return cudaErrorInvalidValue;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (phase_ev && (e = cudaEventRecord(phase_ev[0], s)) != cudaSuccess) return e;
     int n = item_end - item_begin;
     verify64_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, o, n32, ref_sign, unresolved, counters + 1,
                                                     item_begin, item_end);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (phase_ev && (e = cudaEventRecord(phase_ev[1], s)) != cudaSuccess) return e;
     int rblocks = std::max(1, std::min(p.blocks, (n + wpb - 1) / wpb));
     resolve64_kernel<<<rblocks, 32 * wpb, 0, s>>>(b, o, n32, ref_sign, unresolved, counters + 1,
                                                   counters + 2);

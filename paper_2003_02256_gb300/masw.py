@@ -243,6 +243,15 @@ def last_scan_ms(handle) -> float:
     return ms.value
 
 
+def last_scan_phases(handle):
+    f = load().masw_last_scan_phases
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]
+    f.restype = ctypes.c_int
+    ms = (ctypes.c_float * 3)()
+    _check(f(ctypes.c_void_p(handle), ms), "masw_last_scan_phases")
+    return [ms[0], ms[1], ms[2]]
+
+
 def last_scan_unresolved(handle) -> int:
     f = load().masw_last_scan_unresolved
     f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
