@@ -200,6 +200,11 @@ int masw_last_scan_ms(const masw_batch* batch, float* ms);
  * batch stream). MASW_EINVAL when that scan was graph-replayed. */
 int masw_last_scan_phases(const masw_batch* batch, float* ms);
 
+/* The FP32 screen's first-change index per item (item order, -1 when the
+ * screen saw none) from the most recent two-precision scan, host or device
+ * buffer of n_items; a diagnostic of how well the screen locates roots. */
+int masw_last_scan_screen(masw_batch* batch, int32_t* n32);
+
 /* Items of the most recent two-precision scan (plan precision 1) whose FP32
  * screen disagreed with the FP64 check and were re-scanned in FP64 (-1 for a
  * precision-0 plan). Synchronises the batch stream. */

@@ -242,6 +242,7 @@ static void build_records32(const masw_batch* B, const std::vector<double>& rec,
             F[F_RHO] = (float)(L[L_RHO] / mref);
             F[F_IA2] = (float)L[L_IA2];
             F[F_IB2] = (float)L[L_IB2];
+            F[F_DIB] = (float)(L[L_IB2] - L[L_IA2]);
         }
     }
 }
@@ -646,6 +647,15 @@ int masw_last_scan_phases(const masw_batch* B, float* ms) {
     CK(cudaEventElapsedTime(&ms[0], B->ev0, B->phase_ev[0]));
     CK(cudaEventElapsedTime(&ms[1], B->phase_ev[0], B->phase_ev[1]));
     CK(cudaEventElapsedTime(&ms[2], B->phase_ev[1], B->ev1));
+    return MASW_OK;
+}
+
+int masw_last_scan_screen(masw_batch* B, int32_t* n32) {
+    if (!B || !n32 || B->plan.precision != 1) return MASW_EINVAL;
+    bool sync = false;
+    int rc = copy_out(n32, B->d_n32, B->n_items, B->stream, &sync);
+    if (rc) return rc;
+    if (sync) CK(cudaStreamSynchronize(B->stream));
     return MASW_OK;
 }
 

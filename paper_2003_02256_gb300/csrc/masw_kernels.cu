@@ -682,6 +682,7 @@ __global__ void update_beta_h_kernel(DevBatch b, const double* __restrict__ h,
             F[F_RHO] = (float)(L[L_RHO] / mref);
             F[F_IA2] = (float)L[L_IA2];
             F[F_IB2] = (float)L[L_IB2];
+            F[F_DIB] = (float)(L[L_IB2] - L[L_IA2]);
         }
     }
     double bhs = beta[lo + N];

@@ -13,7 +13,18 @@
 // modulus (a positive common factor, so no sign changes) to keep the
 // recurrence far from FP32 overflow; the Taylor series is cut where its
 // remainder falls below FP32 rounding; exponentials and reciprocal square
-// roots use the SFU; the power-of-two rescaling works on FP32 exponent bits.
+// roots use the SFU; the power-of-two rescaling works on FP32 exponent bits,
+// both for the recurrence weight and for each layer's numerators and
+// denominator (a common factor of K_e's numerator and denominator).
+//
+// Below a layer's shear speed (r, s real) the plain denominator
+// D = 2(1 - C_r C_s) + Sd_r Sd_s + Sm_r Sm_s cancels to O(q^2) of its terms
+// (q = c^2/beta^2 small for stiff layers at low c), which in FP32 gives the
+// wrong sign. There the screen uses the exact rearrangement
+//   D = (1 - rs)^2 Sd_r Sd_s - 4 sinh^2(k h (r - s) / 2),
+//   1 - rs = (p + q - pq) / (1 + rs),  r - s = (q - p) / (r + s),
+// and C_r - C_s = 2 sinh((x_r + x_s)/2) sinh((x_r - x_s)/2), whose terms
+// carry no cancellation (scaled by exp(-x_r - x_s) like every other term).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,8 +32,9 @@
 
 namespace masw {
 
-// FP32 layer record: h, mu/mu_ref, rho/mu_ref, 1/alpha^2, 1/beta^2, pad x3.
-enum LayerField32 { F_H = 0, F_MU = 1, F_RHO = 2, F_IA2 = 3, F_IB2 = 4 };
+// FP32 layer record: h, mu/mu_ref, rho/mu_ref, 1/alpha^2, 1/beta^2,
+// 1/beta^2 - 1/alpha^2 (rounded once from FP64), pad x2.
+enum LayerField32 { F_H = 0, F_MU = 1, F_RHO = 2, F_IA2 = 3, F_IB2 = 4, F_DIB = 5 };
 constexpr int LAYER_STRIDE32 = 8;
 
 __device__ __forceinline__ int sgnf(float x) { return (x > 0.0f) - (x < 0.0f); }
@@ -89,19 +101,60 @@ __device__ __forceinline__ int det_sign_f(const float* __restrict__ lay, int N, 
         const float* L = lay + j * LAYER_STRIDE32;
         float kh = k * L[F_H];
         float q = c2 * L[F_IB2];
-        float r2 = fmaf(-c2, L[F_IA2], 1.0f);
+        float pp = c2 * L[F_IA2];
+        float r2 = 1.0f - pp;
         float s2 = 1.0f - q;
-        WaveF R = wave_fns_f(kh, r2);
-        WaveF S = wave_fns_f(kh, s2);
-        float ErEs = R.E * S.E;
-        float CrCs = R.C * S.C;
-        float Dh = fmaf(2.0f, ErEs - CrCs, fmaf(R.Sd, S.Sd, R.Sm * S.Sm));
-        float A1 = fmaf(R.C, S.Sd, -S.C * R.Sm);
-        float D1 = fmaf(S.C, R.Sd, -R.C * S.Sm);
-        float B1 = fmaf(s2 + 3.0f, CrCs - ErEs, -fmaf(S.Sm, fmaf(2.0f, R.Sm, R.Sd), R.Sd * S.Sd));
-        float E1 = fmaf(R.Sm, S.E, -R.E * S.Sd);
-        float F1 = fmaf(R.E, S.C, -R.C * S.E);
-        float G1 = fmaf(S.Sm, R.E, -S.E * R.Sd);
+        float Dh, A1, D1, B1, E1, F1, G1;
+        if (s2 > 0.0f) {
+            // r, s real (c below the layer's shear speed): every term scaled
+            // by exp(-x_r - x_s) and written without cancellation
+            float rwr = rsqrtf(r2), rws = rsqrtf(s2);
+            float r = r2 * rwr, s = s2 * rws;
+            float xr = kh * r, xs = kh * s;
+            float emr = expm1f(-2.0f * xr), ems = expm1f(-2.0f * xs);
+            float hr = -0.5f * emr, hs = -0.5f * ems;             // exp(-x) sinh(x)
+            float cr = fmaf(0.5f, emr, 1.0f), cs = fmaf(0.5f, ems, 1.0f);  // exp(-x) cosh(x)
+            float Er = __expf(-xr), Es = __expf(-xs);
+            float dlt = __fdividef(kh * c2 * L[F_DIB], r + s);  // x_r - x_s >= 0
+            float dE = -Es * expm1f(-dlt);                    // E_s - E_r
+            float sE = Es + Er;
+            float omP = fmaf(-Er, Es, 1.0f);                  // 1 - E_r E_s
+            float rs = r * s;
+            float om = __fdividef(fmaf(-pp, q, pp + q), 1.0f + rs);  // 1 - rs
+            float shd = 0.5f * dE * sE;                       // exp(-x_r-x_s) sinh(x_r-x_s)
+            Dh = fmaf(om * om * (hr * rwr), hs * rws, -dE * dE);
+            A1 = fmaf(om * cs, hr, -shd) * rws;
+            D1 = fmaf(om * cr, hs, shd) * rwr;
+            float K2 = fmaf(4.0f - q, rs, fmaf(2.0f * rs, rs, s2 + 1.0f));
+            B1 = 0.25f * fmaf(omP * omP, om * fmaf(-2.0f, om, q), dE * dE * K2) * (rwr * rws);
+            F1 = -0.5f * dE * omP;
+            E1 = fmaf(hr * r, Es, -Er * (hs * rws));
+            G1 = fmaf(hs * s, Er, -Es * (hr * rwr));
+        } else {
+            WaveF R = wave_fns_f(kh, r2);
+            WaveF S = wave_fns_f(kh, s2);
+            float ErEs = R.E * S.E;
+            float CrCs = R.C * S.C;
+            Dh = fmaf(2.0f, ErEs - CrCs, fmaf(R.Sd, S.Sd, R.Sm * S.Sm));
+            A1 = fmaf(R.C, S.Sd, -S.C * R.Sm);
+            D1 = fmaf(S.C, R.Sd, -R.C * S.Sm);
+            B1 = fmaf(s2 + 3.0f, CrCs - ErEs, -fmaf(S.Sm, fmaf(2.0f, R.Sm, R.Sd), R.Sd * S.Sd));
+            E1 = fmaf(R.Sm, S.E, -R.E * S.Sd);
+            F1 = fmaf(R.E, S.C, -R.C * S.E);
+            G1 = fmaf(S.Sm, R.E, -S.E * R.Sd);
+        }
+        // K_e = numerators / Dh is unchanged by a common factor: bring Dh to
+        // [0.5, 1) so that long wavelengths (Dh ~ (kh)^2 p q) cannot drive the
+        // recurrence into FP32 underflow
+        float nrm;
+        if (!pow2_normaliser_f(Dh, &nrm)) return 0;
+        Dh *= nrm;
+        A1 *= nrm;
+        B1 *= nrm;
+        D1 *= nrm;
+        E1 *= nrm;
+        F1 *= nrm;
+        G1 *= nrm;
         float rc2 = L[F_RHO] * c2, mu = L[F_MU];
         float n00 = rc2 * A1, n01 = mu * B1, n11 = rc2 * D1;
         float ce = rc2 * E1, cf = rc2 * F1, cg = rc2 * G1;

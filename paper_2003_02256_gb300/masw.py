@@ -252,6 +252,13 @@ def last_scan_phases(handle):
     return [ms[0], ms[1], ms[2]]
 
 
+def last_scan_screen(handle, n32):
+    f = load().masw_last_scan_screen
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    _check(f(ctypes.c_void_p(handle), _ptr(n32)), "masw_last_scan_screen")
+
+
 def last_scan_unresolved(handle) -> int:
     f = load().masw_last_scan_unresolved
     f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
