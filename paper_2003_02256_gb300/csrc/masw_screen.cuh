@@ -13,9 +13,7 @@
 // modulus (a positive common factor, so no sign changes) to keep the
 // recurrence far from FP32 overflow; the Taylor series is cut where its
 // remainder falls below FP32 rounding; exponentials and reciprocal square
-// roots use the SFU; the power-of-two rescaling works on FP32 exponent bits,
-// both for the recurrence weight and for each layer's numerators and
-// denominator (a common factor of K_e's numerator and denominator).
+// roots and reciprocals use the SFU.
 //
 // Below a layer's shear speed (r, s real) the plain denominator
 // D = 2(1 - C_r C_s) + Sd_r Sd_s + Sm_r Sm_s cancels to O(q^2) of its terms
@@ -23,8 +21,14 @@
 // wrong sign. There the screen uses the exact rearrangement
 //   D = (1 - rs)^2 Sd_r Sd_s - 4 sinh^2(k h (r - s) / 2),
 //   1 - rs = (p + q - pq) / (1 + rs),  r - s = (q - p) / (r + s),
-// and C_r - C_s = 2 sinh((x_r + x_s)/2) sinh((x_r - x_s)/2), whose terms
-// carry no cancellation (scaled by exp(-x_r - x_s) like every other term).
+// and C_r - C_s = 2 sinh((x_r + x_s)/2) sinh((x_r - x_s)/2); the K11 and
+// coupling numerators are rearranged the same way,
+//   A1 s = (1 - rs) C_s S_r - sinh(x_r - x_s),
+//   D1 r = (1 - rs) C_r S_s + sinh(x_r - x_s),
+//   B1 rs = sinh^2((x_r + x_s)/2) (1 - rs)(q - 2(1 - rs))
+//         + sinh^2((x_r - x_s)/2) ((4 - q) rs + 2 r^2 s^2 + s^2 + 1),
+// whose terms carry no cancellation (scaled by exp(-x_r - x_s) like every
+// other term).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,14 +42,6 @@ enum LayerField32 { F_H = 0, F_MU = 1, F_RHO = 2, F_IA2 = 3, F_IB2 = 4, F_DIB = 
 constexpr int LAYER_STRIDE32 = 8;
 
 __device__ __forceinline__ int sgnf(float x) { return (x > 0.0f) - (x < 0.0f); }
-
-__device__ __forceinline__ bool pow2_normaliser_f(float x, float* scale) {
-    int bits = __float_as_int(x);
-    int be = (bits >> 23) & 0xff;
-    if (be == 0 || be >= 253) return false;
-    *scale = __int_as_float((253 - be) << 23);  // 2^-(be - 126): |x * scale| in [0.5, 1)
-    return true;
-}
 
 struct WaveF { float E, C, Sd, Sm; };
 
@@ -92,16 +88,43 @@ __device__ __forceinline__ WaveF wave_fns_f(float kh, float w2) {
     return o;
 }
 
-// Sign of det K at (k, c) in FP32 (same recurrence as det_sign).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// exp(y) - 1 for y <= 0: Taylor polynomial near 0 (remainder < 2e-8
+// relative for y > -0.35), exp(y) - 1 from the SFU otherwise.
+__device__ __forceinline__ float expm1_neg(float y) {
+    if (y > -0.35f) {
+        float p = fmaf(y, 1.0f / 5040.0f, 1.0f / 720.0f);
+        p = fmaf(p, y, 1.0f / 120.0f);
+        p = fmaf(p, y, 1.0f / 24.0f);
+        p = fmaf(p, y, 1.0f / 6.0f);
+        p = fmaf(p, y, 0.5f);
+        p = fmaf(p, y, 1.0f);
+        return p * y;
+    }
+    return __expf(y) - 1.0f;
+}
+
+// Sign of det K at (k, c) in FP32. Same element stiffness as det_sign (in
+// units of the half-space shear modulus) but the plain Schur recurrence
+// S = P + K11, P' = K22 - K21 S^-1 K12 with SFU reciprocals: on the FP32
+// pipe a reciprocal is cheaper than the homogeneous bookkeeping the FP64
+// path uses to avoid divisions.
 __device__ __forceinline__ int det_sign_f(const float* __restrict__ lay, int N, float k, float c) {
     float c2 = c * c;
-    float p00 = 0.0f, p01 = 0.0f, p11 = 0.0f, w = 1.0f;
+    float p00 = 0.0f, p01 = 0.0f, p11 = 0.0f;
     int sg = 1;
     for (int j = 0; j < N; ++j) {
-        const float* L = lay + j * LAYER_STRIDE32;
-        float kh = k * L[F_H];
-        float q = c2 * L[F_IB2];
-        float pp = c2 * L[F_IA2];
+        const float4 LA = *reinterpret_cast<const float4*>(lay + j * LAYER_STRIDE32);
+        const float2 LB = *reinterpret_cast<const float2*>(lay + j * LAYER_STRIDE32 + 4);
+        // LA = (h, mu, rho, 1/alpha^2), LB = (1/beta^2, 1/beta^2 - 1/alpha^2)
+        float kh = k * LA.x;
+        float q = c2 * LB.x;
+        float pp = c2 * LA.w;
         float r2 = 1.0f - pp;
         float s2 = 1.0f - q;
         float Dh, A1, D1, B1, E1, F1, G1;
@@ -110,26 +133,25 @@ __device__ __forceinline__ int det_sign_f(const float* __restrict__ lay, int N, 
             // by exp(-x_r - x_s) and written without cancellation
             float rwr = rsqrtf(r2), rws = rsqrtf(s2);
             float r = r2 * rwr, s = s2 * rws;
-            float xr = kh * r, xs = kh * s;
-            float emr = expm1f(-2.0f * xr), ems = expm1f(-2.0f * xs);
-            float hr = -0.5f * emr, hs = -0.5f * ems;             // exp(-x) sinh(x)
-            float cr = fmaf(0.5f, emr, 1.0f), cs = fmaf(0.5f, ems, 1.0f);  // exp(-x) cosh(x)
-            float Er = __expf(-xr), Es = __expf(-xs);
-            float dlt = __fdividef(kh * c2 * L[F_DIB], r + s);  // x_r - x_s >= 0
-            float dE = -Es * expm1f(-dlt);                    // E_s - E_r
-            float sE = Es + Er;
-            float omP = fmaf(-Er, Es, 1.0f);                  // 1 - E_r E_s
+            float emr1 = expm1_neg(-kh * r), ems1 = expm1_neg(-kh * s);  // exp(-x) - 1
+            float Er = 1.0f + emr1, Es = 1.0f + ems1;
+            float hr = -0.5f * emr1 * (1.0f + Er), hs = -0.5f * ems1 * (1.0f + Es);  // exp(-x) sinh x
+            float cr = 1.0f - hr, cs = 1.0f - hs;                                  // exp(-x) cosh x
             float rs = r * s;
-            float om = __fdividef(fmaf(-pp, q, pp + q), 1.0f + rs);  // 1 - rs
-            float shd = 0.5f * dE * sE;                       // exp(-x_r-x_s) sinh(x_r-x_s)
-            Dh = fmaf(om * om * (hr * rwr), hs * rws, -dE * dE);
+            float irs = rcp_approx(r + s);
+            float dE = -Es * expm1_neg(-kh * c2 * LB.y * irs);  // E_s - E_r, x_r - x_s >= 0
+            float omP = fmaf(-Er, Es, 1.0f);                     // 1 - E_r E_s
+            float om = fmaf(-pp, q, pp + q) * rcp_approx(1.0f + rs);  // 1 - rs
+            float shd = 0.5f * dE * (Es + Er);                   // exp(-x_r-x_s) sinh(x_r-x_s)
+            float sdr = hr * rwr, sds = hs * rws;
+            Dh = fmaf(om * om * sdr, sds, -dE * dE);
             A1 = fmaf(om * cs, hr, -shd) * rws;
             D1 = fmaf(om * cr, hs, shd) * rwr;
             float K2 = fmaf(4.0f - q, rs, fmaf(2.0f * rs, rs, s2 + 1.0f));
             B1 = 0.25f * fmaf(omP * omP, om * fmaf(-2.0f, om, q), dE * dE * K2) * (rwr * rws);
             F1 = -0.5f * dE * omP;
-            E1 = fmaf(hr * r, Es, -Er * (hs * rws));
-            G1 = fmaf(hs * s, Er, -Es * (hr * rwr));
+            E1 = fmaf(hr * r, Es, -Er * sds);
+            G1 = fmaf(hs * s, Er, -Es * sdr);
         } else {
             WaveF R = wave_fns_f(kh, r2);
             WaveF S = wave_fns_f(kh, s2);
@@ -143,26 +165,16 @@ __device__ __forceinline__ int det_sign_f(const float* __restrict__ lay, int N, 
             F1 = fmaf(R.E, S.C, -R.C * S.E);
             G1 = fmaf(S.Sm, R.E, -S.E * R.Sd);
         }
-        // K_e = numerators / Dh is unchanged by a common factor: bring Dh to
-        // [0.5, 1) so that long wavelengths (Dh ~ (kh)^2 p q) cannot drive the
-        // recurrence into FP32 underflow
-        float nrm;
-        if (!pow2_normaliser_f(Dh, &nrm)) return 0;
-        Dh *= nrm;
-        A1 *= nrm;
-        B1 *= nrm;
-        D1 *= nrm;
-        E1 *= nrm;
-        F1 *= nrm;
-        G1 *= nrm;
-        float rc2 = L[F_RHO] * c2, mu = L[F_MU];
-        float n00 = rc2 * A1, n01 = mu * B1, n11 = rc2 * D1;
-        float ce = rc2 * E1, cf = rc2 * F1, cg = rc2 * G1;
-        float s00 = fmaf(Dh, p00, w * n00);
-        float s01 = fmaf(Dh, p01, w * n01);
-        float s11 = fmaf(Dh, p11, w * n11);
+        // element blocks K = numerators / Dh (k and mu_ref dropped)
+        float iD = rcp_approx(Dh);
+        float fr = LA.z * c2 * iD, fm = LA.y * iD;
+        float n00 = fr * A1, n01 = fm * B1, n11 = fr * D1;
+        float ce = fr * E1, cf = fr * F1, cg = fr * G1;
+        float s00 = p00 + n00, s01 = p01 + n01, s11 = p11 + n11;
         float det = fmaf(s00, s11, -s01 * s01);
         sg *= sgnf(det);
+        float idet = rcp_approx(det);
+        // P' = K22 - K21 adj(S) K12 / det,  K12 = [[ce, cf], [-cf, cg]]
         float t00 = fmaf(s11, ce, s01 * cf);
         float t01 = fmaf(s11, cf, -s01 * cg);
         float t10 = -fmaf(s01, ce, s00 * cf);
@@ -170,29 +182,22 @@ __device__ __forceinline__ int det_sign_f(const float* __restrict__ lay, int N, 
         float q00 = fmaf(ce, t00, -cf * t10);
         float q01 = fmaf(ce, t01, -cf * t11);
         float q11 = fmaf(cf, t01, cg * t11);
-        p00 = fmaf(n00, det, -w * q00);
-        p01 = fmaf(-n01, det, -w * q01);
-        p11 = fmaf(n11, det, -w * q11);
-        float wn = Dh * det;
-        float sc;
-        if (!pow2_normaliser_f(wn, &sc)) return 0;
-        p00 *= sc;
-        p01 *= sc;
-        p11 *= sc;
-        w = wn * sc;
+        p00 = fmaf(-idet, q00, n00);
+        p01 = fmaf(-idet, q01, -n01);
+        p11 = fmaf(-idet, q11, n11);
     }
-    const float* L = lay + N * LAYER_STRIDE32;
-    float q = c2 * L[F_IB2];
-    float p = c2 * L[F_IA2];
+    const float4 LA = *reinterpret_cast<const float4*>(lay + N * LAYER_STRIDE32);
+    const float LBx = lay[N * LAYER_STRIDE32 + 4];
+    float q = c2 * LBx;
+    float p = c2 * LA.w;
     float r = sqrtf(1.0f - p);
     float s = sqrtf(1.0f - q);
     float g = fmaf(r, s, 1.0f);
-    float den = fmaf(-p, q, p + q);
-    float rc2g = L[F_RHO] * c2 * g;
-    float m00 = rc2g * r, m01 = L[F_MU] * fmaf(g, q, -2.0f * den), m11 = rc2g * s;
-    float s00 = fmaf(den, p00, w * m00);
-    float s01 = fmaf(den, p01, w * m01);
-    float s11 = fmaf(den, p11, w * m11);
+    float iden = rcp_approx(fmaf(-p, q, p + q));
+    float rc2g = LA.z * c2 * g * iden;
+    float s00 = fmaf(rc2g, r, p00);
+    float s01 = fmaf(LA.y * iden, fmaf(g, q, -2.0f * fmaf(-p, q, p + q)), p01);
+    float s11 = fmaf(rc2g, s, p11);
     return sg * sgnf(fmaf(s00, s11, -s01 * s01));
 }
 
