@@ -21,7 +21,13 @@
 // Slot layout (one pinned host staging region and one device region per
 // slot, copied with a single transfer at admission):
 //   [meta: 4 x i32 (nrec, nlim, n_lambda, 0)] [records: rmax x 8 f64]
-//   [k: imax f64] [scan state: imax x (base i32, carry i32)]
+//   [FP32 records: rmax x 8 f32] [k: imax f64]
+//   [scan state: imax x (base, carry, phase, ref) i32]
+// Each item runs the two-precision scan of the batch path: FP32 chunks
+// locate the first sign change; a single FP64 warp pass over V[0] and a
+// 31-point window around the located index decides it; when that pass does
+// not confirm, the item continues with FP64 chunks (one per tick) from the
+// window's end or from V[0].
 // Results are written by the kernel into mapped pinned host memory, so
 // retiring a request is a host memcpy.
 #include <algorithm>
@@ -34,6 +40,7 @@
 #include "../../include/masw.h"
 #include "masw_device.cuh"
 #include "masw_internal.h"
+#include "masw_screen.cuh"
 
 using namespace masw;
 
@@ -59,18 +66,24 @@ __device__ __forceinline__ const int32_t* slot_meta(const SlotView& v, int s) {
 __device__ __forceinline__ double* slot_records(const SlotView& v, int s) {
     return v.region + (size_t)s * v.stride + 2;
 }
+__device__ __forceinline__ float* slot_records32(const SlotView& v, int s) {
+    return (float*)(v.region + (size_t)s * v.stride + 2 + (size_t)v.rmax * LAYER_STRIDE);
+}
 __device__ __forceinline__ double* slot_k(const SlotView& v, int s) {
-    return v.region + (size_t)s * v.stride + 2 + (size_t)v.rmax * LAYER_STRIDE;
+    return v.region + (size_t)s * v.stride + 2 + (size_t)v.rmax * (LAYER_STRIDE + 4);
 }
 __device__ __forceinline__ int32_t* slot_state(const SlotView& v, int s) {
-    return (int32_t*)(v.region + (size_t)s * v.stride + 2 + (size_t)v.rmax * LAYER_STRIDE + v.imax);
+    return (int32_t*)(v.region + (size_t)s * v.stride + 2 + (size_t)v.rmax * (LAYER_STRIDE + 4) +
+                      v.imax);
 }
+
+enum { PH_SCREEN = 0, PH_FP64 = 1 };
 
 __global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
                                                          const int32_t* __restrict__ active_in,
                                                          int n_active, int32_t* active_out,
                                                          int chunks, double c0, double dc) {
-    extern __shared__ double smem[];
+    extern __shared__ float smemf[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int a = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -82,19 +95,59 @@ __global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
     const int nrec = meta[0];
     const int nlim = meta[1];
     const int N = nrec - 1;
-    double* my = smem + (size_t)wib * v.rmax * LAYER_STRIDE;
-    const double* src = slot_records(v, slot);
-    for (int t = lane; t < nrec * LAYER_STRIDE; t += 32) my[t] = src[t];
+    float* my = smemf + (size_t)wib * v.rmax * LAYER_STRIDE32;
+    const float* src = slot_records32(v, slot);
+    for (int t = lane; t < nrec * LAYER_STRIDE32; t += 32) my[t] = src[t];
     __syncwarp();
+    const double* lay = slot_records(v, slot);
     const double k = slot_k(v, slot)[j];
-    int32_t* stt = slot_state(v, slot) + 2 * j;
-    int base = stt[0];
-    int carry = stt[1];
+    const float kf = (float)k, c0f = (float)c0, dcf = (float)dc;
+    int32_t* stt = slot_state(v, slot) + 4 * j;
+    int base = stt[0], carry = stt[1], phase = stt[2], ref = stt[3];
     int res = -1;
-    bool finished = base >= nlim;
-    for (int c = 0; c < chunks && !finished; ++c) {
+    bool finished = false;
+    if (phase == PH_SCREEN) {
+        for (int c = 0; c < chunks && !finished && phase == PH_SCREEN; ++c) {
+            int n = base + lane;
+            int sg = (n < nlim) ? det_sign_f(my, N, kf, fmaf((float)n, dcf, c0f)) : 0;
+            int prev = __shfl_up_sync(FULL, sg, 1);
+            if (lane == 0) prev = carry;
+            unsigned msk = __ballot_sync(FULL, n >= 1 && n < nlim && sg != prev);
+            int n32 = -1;
+            if (msk) {
+                n32 = base + __ffs(msk) - 1;
+            } else {
+                carry = __shfl_sync(FULL, sg, 31);
+                base += 32;
+                if (base >= nlim) n32 = -2;  // the screen saw no change
+            }
+            if (n32 == -1) continue;
+            // FP64 decision: lane 0 -> V[0]; lanes 1..31 -> V[w0 .. w0 + 30]
+            int w0 = n32 >= 0 ? max(0, n32 - 16) : max(0, nlim - 31);
+            int pt = lane == 0 ? 0 : w0 + lane - 1;
+            int s64 = (pt < nlim) ? det_sign(lay, N, k, grid_c(c0, dc, pt)) : 0;
+            int r0 = __shfl_sync(FULL, s64, 0);
+            int first = __shfl_sync(FULL, s64, 1);
+            int prv = __shfl_up_sync(FULL, s64, 1);
+            unsigned m64 = __ballot_sync(FULL, lane >= 2 && pt < nlim && s64 != prv);
+            int last = min(w0 + 30, nlim - 1);
+            int s_last = __shfl_sync(FULL, s64, last - w0 + 1);
+            if (first != r0) {  // an FP64 change below the window: FP64 from V[0]
+                phase = PH_FP64; base = 0; carry = 0; ref = r0;
+            } else if (m64) {
+                res = w0 + __ffs(m64) - 2;
+                finished = true;
+            } else if (last >= nlim - 1) {
+                finished = (s_last == r0);  // no change up to the last scanned point
+                if (!finished) { phase = PH_FP64; base = 0; carry = 0; ref = r0; }
+            } else {  // the screen's change was not confirmed: FP64 from the window's end
+                phase = PH_FP64; base = last + 1; carry = s_last; ref = r0;
+            }
+        }
+    } else if (base < nlim) {
+        // one FP64 chunk per tick
         int n = base + lane;
-        int sg = (n < nlim) ? det_sign(my, N, k, grid_c(c0, dc, n)) : 0;
+        int sg = (n < nlim) ? det_sign(lay, N, k, grid_c(c0, dc, n)) : 0;
         int prev = __shfl_up_sync(FULL, sg, 1);
         if (lane == 0) prev = carry;
         unsigned msk = __ballot_sync(FULL, n >= 1 && n < nlim && sg != prev);
@@ -106,6 +159,8 @@ __global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
             base += 32;
             finished = base >= nlim;
         }
+    } else {
+        finished = true;
     }
     if (lane == 0) {
         if (finished) {
@@ -123,6 +178,8 @@ __global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
         } else {
             stt[0] = base;
             stt[1] = carry;
+            stt[2] = phase;
+            stt[3] = ref;
             active_out[atomicAdd(&v.counters[0], 1)] = item;
         }
     }
@@ -135,7 +192,8 @@ double now_s() {
 
 int64_t request_bytes(int32_t n_layers, int32_t n_lambda) {
     // records + per-item k, scan state and results
-    return (int64_t)(n_layers + 1) * LAYER_STRIDE * 8 + (int64_t)n_lambda * (8 + 8 + 16);
+    return (int64_t)(n_layers + 1) * (LAYER_STRIDE * 8 + LAYER_STRIDE32 * 4) +
+           (int64_t)n_lambda * (8 + 16 + 16);
 }
 
 int32_t scan_limit_host(const masw_grid& g, double beta_hs) {
@@ -219,7 +277,7 @@ int run_tick(masw_server* S) {
         return MASW_ECUDA;
     int wpb = S->cfg.warps_per_block;
     int blocks = (S->n_active + wpb - 1) / wpb;
-    size_t shm = (size_t)wpb * S->v.rmax * LAYER_STRIDE * sizeof(double);
+    size_t shm = (size_t)wpb * S->v.rmax * LAYER_STRIDE32 * sizeof(float);
     serve_tick_kernel<<<blocks, 32 * wpb, shm, S->stream>>>(S->v, S->active[S->cur], S->n_active,
                                                             S->active[1 - S->cur],
                                                             S->cfg.chunks_per_tick, S->grid.c0,
@@ -283,7 +341,7 @@ int masw_server_create(const masw_grid* grid, const masw_server_config* cfg, voi
         return MASW_EINVAL;
     int64_t cap_items = (int64_t)cfg->max_slots * cfg->max_lambda;
     if (cap_items > INT32_MAX / 2) return MASW_EINVAL;
-    size_t shm = (size_t)cfg->warps_per_block * (cfg->max_layers + 1) * LAYER_STRIDE * 8;
+    size_t shm = (size_t)cfg->warps_per_block * (cfg->max_layers + 1) * LAYER_STRIDE32 * 4;
     if (shm > 48 * 1024) return MASW_EINVAL;
     masw_server* S = new (std::nothrow) masw_server();
     if (!S) return MASW_ENOMEM;
@@ -292,7 +350,7 @@ int masw_server_create(const masw_grid* grid, const masw_server_config* cfg, voi
     S->stream = (cudaStream_t)cuda_stream;
     S->v.rmax = cfg->max_layers + 1;
     S->v.imax = cfg->max_lambda;
-    S->v.stride = 2 + (int64_t)S->v.rmax * LAYER_STRIDE + 2 * (int64_t)S->v.imax;
+    S->v.stride = 2 + (int64_t)S->v.rmax * (LAYER_STRIDE + 4) + 3 * (int64_t)S->v.imax;
     S->v.stride = (S->v.stride + 31) / 32 * 32;  // 256-byte aligned slots
     size_t slots = cfg->max_slots, items = (size_t)cap_items;
     bool ok = dalloc(&S->v.region, slots * S->v.stride) && dalloc(&S->v.remaining, slots) &&
@@ -370,11 +428,25 @@ int masw_server_submit(masw_server* S, int32_t n_layers, const double* h, const 
         L[L_RATIO] = a / b;
         L[7] = 0.0;
     }
-    double* kk = rec + (size_t)S->v.rmax * LAYER_STRIDE;
+    // FP32 records of the screen (stiffnesses over the half-space shear modulus)
+    float* rec32 = (float*)(rec + (size_t)S->v.rmax * LAYER_STRIDE);
+    double mref = rec[(size_t)n_layers * LAYER_STRIDE + L_MU];
+    for (int i = 0; i <= n_layers; ++i) {
+        const double* L = rec + (size_t)i * LAYER_STRIDE;
+        float* F = rec32 + (size_t)i * LAYER_STRIDE32;
+        F[F_H] = (float)L[L_H];
+        F[F_MU] = (float)(L[L_MU] / mref);
+        F[F_RHO] = (float)(L[L_RHO] / mref);
+        F[F_IA2] = (float)L[L_IA2];
+        F[F_IB2] = (float)L[L_IB2];
+        F[F_DIB] = (float)(L[L_IB2] - L[L_IA2]);
+        F[6] = F[7] = 0.0f;
+    }
+    double* kk = rec + (size_t)S->v.rmax * (LAYER_STRIDE + 4);
     for (int j = 0; j < n_lambda; ++j) kk[j] = 2.0 * M_PI / lambda[j];
     int32_t* stt = (int32_t*)(kk + S->v.imax);
-    std::memset(stt, 0, (size_t)n_lambda * 2 * sizeof(int32_t));
-    size_t bytes = (size_t)((char*)(stt + 2 * n_lambda) - (char*)reg);
+    std::memset(stt, 0, (size_t)n_lambda * 4 * sizeof(int32_t));
+    size_t bytes = (size_t)((char*)(stt + 4 * n_lambda) - (char*)reg);
     cudaError_t e = cudaMemcpyAsync(S->v.region + (size_t)slot * S->v.stride, reg, bytes,
                                     cudaMemcpyHostToDevice, S->stream);
     if (e == cudaSuccess)

@@ -67,7 +67,7 @@ def test_admission_refuses_past_the_caps_with_a_status(env):
     reqs = requests(6, seed=9)
     grid = W.Grid(50.0, 0.25, 4601)
     h, a, b, r, lam = reqs.model(0)
-    one = (len(a) * 64) + lam.size * 32
+    one = (len(a) * (64 + 32)) + lam.size * 40
     with serving.Server(grid, max_slots=4, mem_cap_bytes=int(one * 1.5)) as srv:
         rid = srv.submit(h, a, b, r, lam)
         h1, a1, b1, r1, l1 = reqs.model(1)
