@@ -43,8 +43,12 @@ WORKLOAD = ("uniform_batch: 1024 models x (8 layers + half-space), h~U[1,8] m, b
 # from ncu instruction counters on this workload (profiles/).
 F_LAYER_FLOPS = 162.3
 # FP32 flops per layer-evaluation of the screen kernel (2*FFMA + FMUL + FADD
-# per evaluated (layer, c) pair, ncu instruction counters; profiles/).
-F_LAYER_FLOPS_FP32 = 150.0
+# per executed (layer, c) pair: 29.6 FFMA, 54.2 FMUL, 16.4 FADD; ncu
+# instruction counters of the 64-model case, profiles/).
+F_LAYER_FLOPS_FP32 = 129.8
+# DRAM bytes (read + write) of one screen launch per model (ncu, 64-model case:
+# 239.6 KB read, 0 written), scaled by the models of a launch.
+SCREEN_DRAM_BYTES_PER_MODEL = 239.6e3 / 64
 # FP32 pipe: FFMA issue rate per SM per clock.
 FP32_FFMA_PER_CLK_SM = 128.0
 # FP64 pipe of GB300: DFMA issue rate per SM per clock (ncu peak_sustained) and
@@ -397,7 +401,8 @@ def main():
         t_screen = phases[0] * 1e-3
         achieved = units * F_LAYER_FLOPS_FP32 / t_screen
         roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak32 / 1e12,
-                    "unit": "TFLOP/s", "frac": achieved / peak32, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / peak32,
+                    "traffic": SCREEN_DRAM_BYTES_PER_MODEL * models.n_models,
                     "kernel": "screen32_kernel (FP32 pipe)",
                     "peak_source": "derived: 128 FFMA/clk/SM x 2 flop x SMs x 2070 MHz",
                     "layer_evals_per_launch": units,
