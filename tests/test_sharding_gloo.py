@@ -1,0 +1,65 @@
+"""The multi-rank path on CPU: world_size-2 gloo groups split the items of a
+ragged batch (modular and contiguous partitions), each rank runs the CPU
+oracle on its shard, results gather on rank 0 and equal a one-process run;
+the timing reduction takes the max over ranks."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+from paper_2003_02256_gb300 import sharding
+from paper_2003_02256_gb300 import workloads as W
+
+
+def _port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, mode, out_path):
+    import torch.distributed as dist
+
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    m, g = W.ragged_batch(n_models=6, layers=(3, 6), lambdas=(5, 12), grid=W.Grid(60.0, 1.0, 900))
+    item_model = np.repeat(np.arange(m.n_models), m.n_lambda)
+    mine = sharding.shard(m.n_items, rank, world, mode)
+    ct = np.empty(mine.size)
+    for t, it in enumerate(mine):
+        h, a, b, r, _ = m.model(item_model[it])
+        ct[t] = oracle.scan(h, a, b, r, m.lam[it], g.c0, g.dc, g.n_c)[1]
+    full = sharding.gather(ct, mine, m.n_items)
+    tmax = sharding.max_over_ranks(float(rank + 1))
+    if rank == 0:
+        np.save(out_path, np.r_[full, tmax])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("mode", ["modular", "contiguous"])
+def test_two_rank_gloo_shards_gather_to_the_single_process_result(tmp_path, oracle_lib, mode):
+    out = str(tmp_path / "res.npy")
+    mp.spawn(_worker, args=(2, _port(), mode, out), nprocs=2, join=True)
+    res = np.load(out)
+    full, tmax = res[:-1], res[-1]
+    m, g = W.ragged_batch(n_models=6, layers=(3, 6), lambdas=(5, 12), grid=W.Grid(60.0, 1.0, 900))
+    ref, _, _ = oracle_lib.dispersion(m.as_dict(), g.c0, g.dc, g.n_c)
+    assert np.array_equal(full, ref, equal_nan=True)
+    assert tmax == 2.0
+
+
+def test_partitions_cover_every_unit_once():
+    for n in (0, 1, 7, 40, 41):
+        for world in (1, 2, 3, 8):
+            for mode in ("modular", "contiguous"):
+                parts = [sharding.shard(n, r, world, mode) for r in range(world)]
+                allidx = np.sort(np.concatenate(parts)) if parts else np.zeros(0)
+                assert np.array_equal(allidx, np.arange(n))
+    with pytest.raises(ValueError):
+        sharding.shard(4, 2, 2)
