@@ -94,7 +94,8 @@ typedef struct {
 /* Launch plan of the scan (see masw_autotune). */
 typedef struct {
     int32_t warps_per_block; /* 1, 2, 4, 8 */
-    int32_t cpl;             /* test velocities per lane per chunk: 1, 2, 4 */
+    int32_t cpl;             /* test velocities per lane per chunk: 1, 2, 4 (precision 1 with
+                                2: two adjacent points per lane in packed FP32x2 arithmetic) */
     int32_t blocks_per_sm;   /* persistent grid = blocks_per_sm x SM count */
     int32_t persistent;      /* 1: warps pop items from a work queue */
     int32_t ordered;         /* 1: queue ordered by predicted scan length (longest first) */

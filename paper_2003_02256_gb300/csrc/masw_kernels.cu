@@ -214,6 +214,76 @@ __global__ void __launch_bounds__(256) screen32_kernel(DevBatch b, const float* 
     }
 }
 
+// Paired variant of the screen: lane l evaluates the adjacent points
+// base + 2l and base + 2l + 1 with packed FP32x2 arithmetic (64 points per
+// chunk); the first change is the first set bit of the interleaved masks.
+__global__ void __launch_bounds__(256) screen32p_kernel(DevBatch b, const float* __restrict__ layers32,
+                                                        int32_t* n32out, int persistent,
+                                                        int stage_layers, int32_t* counter,
+                                                        int item_begin, int item_end) {
+    extern __shared__ float smemf[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    float* my = smemf + (size_t)wib * stage_layers * LAYER_STRIDE32;
+    int pos;
+    if (persistent) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1);
+        pos = item_begin + __shfl_sync(FULL, t, 0);
+    } else {
+        pos = item_begin + blockIdx.x * wpb + wib;
+    }
+    const float c0 = (float)b.c0, dc = (float)b.dc;
+    while (pos < item_end) {
+        const int item = b.order[pos];
+        const int m = b.item_model[item];
+        const int lo = b.model_loff[m];
+        const int nrec = b.model_loff[m + 1] - lo;
+        const int N = nrec - 1;
+        const float* lay = layers32 + (size_t)lo * LAYER_STRIDE32;
+        if (nrec <= stage_layers) {
+            for (int t = lane; t < nrec * LAYER_STRIDE32; t += 32) my[t] = lay[t];
+            __syncwarp();
+            lay = my;
+        }
+        const float k = (float)b.k[item];
+        const int nlim = b.model_nlim[m];
+        int res = -1;
+        if (nlim >= 2) {
+            int carry = 0;
+            for (int base = 0; base < nlim && res < 0; base += 64) {
+                const int n0 = base + 2 * lane, n1 = n0 + 1;
+                int s0 = 0, s1 = 0;
+                if (n1 < nlim) {
+                    det_sign_f2(lay, N, k, fmaf((float)n0, dc, c0), fmaf((float)n1, dc, c0), &s0, &s1);
+                } else if (n0 < nlim) {
+                    s0 = det_sign_f(lay, N, k, fmaf((float)n0, dc, c0));
+                }
+                int prev = __shfl_up_sync(FULL, s1, 1);
+                if (lane == 0) prev = carry;
+                unsigned m0 = __ballot_sync(FULL, n0 >= 1 && n0 < nlim && s0 != prev);
+                unsigned m1 = __ballot_sync(FULL, n1 < nlim && s1 != s0);
+                unsigned mm = m0 | m1;
+                if (mm) {
+                    int l = __ffs(mm) - 1;
+                    res = base + 2 * l + (((m0 >> l) & 1u) ? 0 : 1);
+                }
+                carry = __shfl_sync(FULL, s1, 31);
+            }
+        }
+        if (lane == 0) n32out[item] = res;
+        __syncwarp();
+        if (persistent) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(counter, 1);
+            pos = item_begin + __shfl_sync(FULL, t, 0);
+        } else {
+            pos = item_end;
+        }
+    }
+}
+
 __device__ __forceinline__ void write_result(const DevBatch& b, const ScanOut& o, int item, int res) {
     if (res >= 0) {
         o.ct[item] = grid_c(b.c0, b.dc, res);
@@ -331,10 +401,10 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
                                                             p.stage_layers, counters, item_begin,
                                                             item_end);
             break;
-        case 2:
-            screen32_kernel<2><<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,
-                                                            p.stage_layers, counters, item_begin,
-                                                            item_end);
+        case 2:  // paired points, packed FP32x2
+            screen32p_kernel<<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,
+                                                          p.stage_layers, counters, item_begin,
+                                                          item_end);
             break;
         case 4:
             screen32_kernel<4><<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,

@@ -202,3 +202,216 @@ __device__ __forceinline__ int det_sign_f(const float* __restrict__ lay, int N, 
 }
 
 }  // namespace masw
+
+// ---------------------------------------------------------------------
+// Paired evaluation: two test velocities per thread in packed FP32x2
+// arithmetic (fma/mul/add.rn.f32x2). The FP32 pipe runs the same number of
+// lane operations either way, but one packed instruction issues two of them,
+// and the screen is issue-bound. SFU operations stay per element. When the
+// two points of a layer take different branches the layer is evaluated per
+// element with the scalar code.
+namespace masw {
+
+struct f2 { unsigned long long v; };
+
+__device__ __forceinline__ f2 P2(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ f2 B2(float a) { return P2(a, a); }
+__device__ __forceinline__ float X(f2 a) {
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
+    return x;
+}
+__device__ __forceinline__ float Y(f2 a) {
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
+    return y;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+// a * b - c
+__device__ __forceinline__ f2 fms2(f2 a, f2 b, f2 c) { return fma2(a, b, mul2(c, B2(-1.0f))); }
+
+__device__ __forceinline__ f2 expm1_neg2(f2 y) {
+    float yx = X(y), yy = Y(y);
+    if (yx > -0.35f && yy > -0.35f) {
+        f2 p = fma2(y, B2(1.0f / 5040.0f), B2(1.0f / 720.0f));
+        p = fma2(p, y, B2(1.0f / 120.0f));
+        p = fma2(p, y, B2(1.0f / 24.0f));
+        p = fma2(p, y, B2(1.0f / 6.0f));
+        p = fma2(p, y, B2(0.5f));
+        p = fma2(p, y, B2(1.0f));
+        return mul2(p, y);
+    }
+    return P2(expm1_neg(yx), expm1_neg(yy));
+}
+
+// One layer's element numerators (scalar, any branch), for the mixed case.
+__device__ __forceinline__ void layer_nums_f(float kh, float c2, float pp, float q, float dib,
+                                             float* Dh, float* A1, float* B1, float* D1, float* E1,
+                                             float* F1, float* G1) {
+    float r2 = 1.0f - pp, s2 = 1.0f - q;
+    if (s2 > 0.0f) {
+        float rwr = rsqrtf(r2), rws = rsqrtf(s2);
+        float r = r2 * rwr, s = s2 * rws;
+        float emr1 = expm1_neg(-kh * r), ems1 = expm1_neg(-kh * s);
+        float Er = 1.0f + emr1, Es = 1.0f + ems1;
+        float hr = -0.5f * emr1 * (1.0f + Er), hs = -0.5f * ems1 * (1.0f + Es);
+        float cr = 1.0f - hr, cs = 1.0f - hs;
+        float rs = r * s;
+        float dE = -Es * expm1_neg(-kh * c2 * dib * rcp_approx(r + s));
+        float omP = fmaf(-Er, Es, 1.0f);
+        float om = fmaf(-pp, q, pp + q) * rcp_approx(1.0f + rs);
+        float shd = 0.5f * dE * (Es + Er);
+        float sdr = hr * rwr, sds = hs * rws;
+        *Dh = fmaf(om * om * sdr, sds, -dE * dE);
+        *A1 = fmaf(om * cs, hr, -shd) * rws;
+        *D1 = fmaf(om * cr, hs, shd) * rwr;
+        float K2 = fmaf(4.0f - q, rs, fmaf(2.0f * rs, rs, s2 + 1.0f));
+        *B1 = 0.25f * fmaf(omP * omP, om * fmaf(-2.0f, om, q), dE * dE * K2) * (rwr * rws);
+        *F1 = -0.5f * dE * omP;
+        *E1 = fmaf(hr * r, Es, -Er * sds);
+        *G1 = fmaf(hs * s, Er, -Es * sdr);
+    } else {
+        WaveF R = wave_fns_f(kh, r2);
+        WaveF S = wave_fns_f(kh, s2);
+        float ErEs = R.E * S.E;
+        float CrCs = R.C * S.C;
+        *Dh = fmaf(2.0f, ErEs - CrCs, fmaf(R.Sd, S.Sd, R.Sm * S.Sm));
+        *A1 = fmaf(R.C, S.Sd, -S.C * R.Sm);
+        *D1 = fmaf(S.C, R.Sd, -R.C * S.Sm);
+        *B1 = fmaf(s2 + 3.0f, CrCs - ErEs, -fmaf(S.Sm, fmaf(2.0f, R.Sm, R.Sd), R.Sd * S.Sd));
+        *E1 = fmaf(R.Sm, S.E, -R.E * S.Sd);
+        *F1 = fmaf(R.E, S.C, -R.C * S.E);
+        *G1 = fmaf(S.Sm, R.E, -S.E * R.Sd);
+    }
+}
+
+// Signs of det K at two test velocities (ca, cb) in packed FP32.
+__device__ __forceinline__ void det_sign_f2(const float* __restrict__ lay, int N, float k, float ca,
+                                            float cb, int* sa, int* sb) {
+    const f2 one = B2(1.0f);
+    f2 c2 = P2(ca * ca, cb * cb);
+    f2 p00 = B2(0.0f), p01 = B2(0.0f), p11 = B2(0.0f);
+    unsigned neg_a = 0, neg_b = 0, zero = 0;
+    for (int j = 0; j < N; ++j) {
+        const float4 LA = *reinterpret_cast<const float4*>(lay + j * LAYER_STRIDE32);
+        const float2 LB = *reinterpret_cast<const float2*>(lay + j * LAYER_STRIDE32 + 4);
+        float kh = k * LA.x;
+        f2 q = mul2(c2, B2(LB.x));
+        f2 pp = mul2(c2, B2(LA.w));
+        f2 s2 = sub2(one, q);
+        f2 Dh, A1, B1, D1, E1, F1, G1;
+        bool ra = X(s2) > 0.0f, rb = Y(s2) > 0.0f;
+        if (ra && rb) {
+            f2 r2 = sub2(one, pp);
+            f2 rwr = P2(rsqrtf(X(r2)), rsqrtf(Y(r2)));
+            f2 rws = P2(rsqrtf(X(s2)), rsqrtf(Y(s2)));
+            f2 r = mul2(r2, rwr), s = mul2(s2, rws);
+            f2 nkh = B2(-kh);
+            f2 emr1 = expm1_neg2(mul2(nkh, r)), ems1 = expm1_neg2(mul2(nkh, s));
+            f2 Er = add2(one, emr1), Es = add2(one, ems1);
+            f2 hr = mul2(emr1, fma2(B2(-0.5f), emr1, B2(-1.0f)));  // exp(-x) sinh x
+            f2 hs = mul2(ems1, fma2(B2(-0.5f), ems1, B2(-1.0f)));
+            f2 cr = sub2(one, hr), cs = sub2(one, hs);
+            f2 rs = mul2(r, s);
+            f2 rps = add2(r, s);
+            f2 irs = P2(rcp_approx(X(rps)), rcp_approx(Y(rps)));
+            f2 dlt = mul2(mul2(B2(-kh * LB.y), c2), irs);  // -(x_r - x_s)
+            f2 dE = mul2(mul2(Es, expm1_neg2(dlt)), B2(-1.0f));  // E_s - E_r
+            f2 omP = fms2(B2(-1.0f), mul2(Er, Es), B2(-1.0f));     // 1 - Er Es
+            f2 ops = add2(one, rs);
+            f2 num = fms2(add2(pp, q), one, mul2(pp, q));
+            f2 om = mul2(num, P2(rcp_approx(X(ops)), rcp_approx(Y(ops))));  // 1 - rs
+            f2 shd = mul2(mul2(B2(0.5f), dE), add2(Es, Er));
+            f2 sdr = mul2(hr, rwr), sds = mul2(hs, rws);
+            f2 dE2 = mul2(dE, dE);
+            Dh = fms2(mul2(mul2(om, om), sdr), sds, dE2);
+            A1 = mul2(fms2(mul2(om, cs), hr, shd), rws);
+            D1 = mul2(fma2(mul2(om, cr), hs, shd), rwr);
+            f2 K2 = fma2(sub2(B2(4.0f), q), rs, fma2(add2(rs, rs), rs, sub2(B2(2.0f), q)));
+            f2 t1 = mul2(mul2(omP, omP), mul2(om, fma2(B2(-2.0f), om, q)));
+            B1 = mul2(mul2(B2(0.25f), fma2(dE2, K2, t1)), mul2(rwr, rws));
+            F1 = mul2(mul2(B2(-0.5f), dE), omP);
+            E1 = fms2(mul2(hr, r), Es, mul2(Er, sds));
+            G1 = fms2(mul2(hs, s), Er, mul2(Es, sdr));
+        } else {
+            float da, aa, ba, dda, ea, fa, ga, db, ab, bb, ddb, eb, fb, gb;
+            layer_nums_f(kh, X(c2), X(pp), X(q), LB.y, &da, &aa, &ba, &dda, &ea, &fa, &ga);
+            layer_nums_f(kh, Y(c2), Y(pp), Y(q), LB.y, &db, &ab, &bb, &ddb, &eb, &fb, &gb);
+            Dh = P2(da, db);
+            A1 = P2(aa, ab);
+            B1 = P2(ba, bb);
+            D1 = P2(dda, ddb);
+            E1 = P2(ea, eb);
+            F1 = P2(fa, fb);
+            G1 = P2(ga, gb);
+        }
+        f2 iD = P2(rcp_approx(X(Dh)), rcp_approx(Y(Dh)));
+        f2 fr = mul2(mul2(B2(LA.z), c2), iD), fm = mul2(B2(LA.y), iD);
+        f2 n00 = mul2(fr, A1), n01 = mul2(fm, B1), n11 = mul2(fr, D1);
+        f2 ce = mul2(fr, E1), cf = mul2(fr, F1), cg = mul2(fr, G1);
+        f2 s00 = add2(p00, n00), s01 = add2(p01, n01), s11 = add2(p11, n11);
+        f2 det = fms2(s00, s11, mul2(s01, s01));
+        float dx = X(det), dy = Y(det);
+        neg_a ^= __float_as_uint(dx);
+        neg_b ^= __float_as_uint(dy);
+        zero |= (dx == 0.0f) | ((dy == 0.0f) << 1);
+        f2 idet = P2(rcp_approx(dx), rcp_approx(dy));
+        f2 t00 = fma2(s11, ce, mul2(s01, cf));
+        f2 t01 = fms2(s11, cf, mul2(s01, cg));
+        f2 t10 = mul2(fma2(s01, ce, mul2(s00, cf)), B2(-1.0f));
+        f2 t11 = fms2(s00, cg, mul2(s01, cf));
+        f2 q00 = fms2(ce, t00, mul2(cf, t10));
+        f2 q01 = fms2(ce, t01, mul2(cf, t11));
+        f2 q11 = fma2(cf, t01, mul2(cg, t11));
+        f2 nid = mul2(idet, B2(-1.0f));
+        p00 = fma2(nid, q00, n00);
+        p01 = fms2(nid, q01, n01);
+        p11 = fma2(nid, q11, n11);
+    }
+    const float4 LA = *reinterpret_cast<const float4*>(lay + N * LAYER_STRIDE32);
+    const float LBx = lay[N * LAYER_STRIDE32 + 4];
+    int out[2];
+    for (int e = 0; e < 2; ++e) {
+        float c2e = e ? Y(c2) : X(c2);
+        float q = c2e * LBx, p = c2e * LA.w;
+        float r = sqrtf(1.0f - p), s = sqrtf(1.0f - q);
+        float g = fmaf(r, s, 1.0f);
+        float den = fmaf(-p, q, p + q);
+        float iden = rcp_approx(den);
+        float rc2g = LA.z * c2e * g * iden;
+        float s00 = fmaf(rc2g, r, e ? Y(p00) : X(p00));
+        float s01 = fmaf(LA.y * iden, fmaf(g, q, -2.0f * den), e ? Y(p01) : X(p01));
+        float s11 = fmaf(rc2g, s, e ? Y(p11) : X(p11));
+        float dl = fmaf(s00, s11, -s01 * s01);
+        unsigned nb = (e ? neg_b : neg_a) ^ __float_as_uint(dl);
+        bool z = (dl == 0.0f) || ((zero >> e) & 1);
+        out[e] = z ? 0 : ((nb >> 31) ? -1 : 1);
+    }
+    *sa = out[0];
+    *sb = out[1];
+}
+
+}  // namespace masw
