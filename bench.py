@@ -260,6 +260,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--precision", type=int, default=None, choices=[0, 1],
                     help="scan plan: 0 FP64 scan, 1 FP32 screen + FP64 decision (default: library)")
+    ap.add_argument("--cpl", type=int, default=None, choices=[1, 2, 4],
+                    help="scan plan test velocities per lane (2: paired FP32x2 screen)")
     ap.add_argument("--workload", default="uniform", choices=["uniform", "ragged"],
                     help="main workload (ragged only for profiling the ragged batch)")
     ap.add_argument("--models", type=int, default=1024,
@@ -289,6 +291,8 @@ def main():
     batch = masw.Batch(models, grid)
     if args.precision is not None:
         batch.set_plan(precision=args.precision)
+    if args.cpl is not None:
+        batch.set_plan(cpl=args.cpl)
     if not args.no_autotune:
         plan = batch.autotune(reps=1)
     else:
