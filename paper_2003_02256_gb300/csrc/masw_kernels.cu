@@ -299,9 +299,10 @@ __device__ __forceinline__ void write_result(const DevBatch& b, const ScanOut& o
 __global__ void verify64_kernel(DevBatch b, ScanOut o, const int32_t* __restrict__ n32,
                                 int32_t* ref_sign, int32_t* unresolved, int32_t* n_unresolved,
                                 int item_begin, int item_end) {
-    int pos = item_begin + blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= item_end) return;
-    const int item = b.order[pos];
+    // natural item order: a warp's threads share a model and have adjacent
+    // wavelengths, so their FP64 branches (series / exp / sincos) agree
+    const int item = item_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= item_end) return;
     const int m = b.item_model[item];
     const int lo = b.model_loff[m];
     const int N = b.model_loff[m + 1] - lo - 1;
