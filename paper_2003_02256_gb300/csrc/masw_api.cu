@@ -283,8 +283,8 @@ static void free_batch(masw_batch* B) {
 static masw_plan default_plan(const masw_batch* B) {
     masw_plan p;
     p.warps_per_block = 8;
-    p.cpl = 1;
-    p.blocks_per_sm = 3;
+    p.cpl = 2;
+    p.blocks_per_sm = 4;
     p.persistent = 1;
     p.ordered = 1;
     p.stage_layers = std::min(B->max_layers + 1, 32);
