@@ -225,6 +225,24 @@ def run_extras(args, masw, torch):
     out["differentiation"] = {"workload": "512 models x 12 layers, 150 wavelengths, LSQ misfit "
                                           "+ adjoint gradient (beta, h)",
                               "gradients_per_s": m4.n_models / dt, "ms_per_batch": 1e3 * dt}
+    # partition study (Section 3.2): per-wavelength work of Algorithm 1 on a
+    # 40-wavelength decreasing curve, split over P ranks contiguously or modularly
+    m1, g1 = W.single_curve()
+    lam = sharding.variable_curve_wavelengths(40)
+    var = W.Models(m1.n_layers, m1.h, m1.alpha, m1.beta, m1.rho,
+                   np.array([lam.size], np.int32), lam)
+    with masw.Batch(var, g1) as b:
+        _, vidx, vst = b.dispersion()
+    work = vidx.astype(np.float64) + 1.0
+    out["partition_study"] = {
+        "workload": "single-curve model, 40 log-spaced decreasing wavelengths 60..1 m, "
+                    "work = determinants evaluated by Algorithm 1 (idx + 1)",
+        "speedup": {str(P): {"modular": sharding.partition_speedup(work, P, "modular"),
+                             "contiguous": sharding.partition_speedup(work, P, "contiguous")}
+                    for P in (1, 2, 3, 4, 8, 16, 20, 24)},
+        "paper_section_3_2": {"3": {"modular": 2.8, "contiguous": 1.9},
+                              "8": {"modular": 7.0, "contiguous": 4.2}}}
+
     # serving
     sampler = W.RandomWalkSampler()
     reqs = W.concat([sampler.next() for _ in range(args.serving_requests)])

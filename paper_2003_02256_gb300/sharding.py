@@ -50,3 +50,20 @@ def gather(local: np.ndarray, indices: np.ndarray, n_total: int, dst: int = 0):
     for idx, vals in parts:
         out[idx] = vals
     return out
+
+
+def partition_speedup(work, ranks: int, mode: str = "modular") -> float:
+    """Strong-scaling speedup of splitting per-unit ``work`` over ``ranks``
+    with the given partition: total work / work of the busiest rank (the
+    cost model of Section 3.2, where a wavelength's cost is the number of
+    determinants Algorithm 1 evaluates for it)."""
+    work = np.asarray(work, dtype=np.float64)
+    loads = [work[shard(work.size, r, ranks, mode)].sum() for r in range(ranks)]
+    return float(work.sum() / max(loads))
+
+
+def variable_curve_wavelengths(n: int = 40, lam_max: float = 60.0, lam_min: float = 1.0):
+    """A 'variable' dispersion-curve layout: n wavelengths in decreasing
+    order (long to short), log-spaced -- the typical shape the paper's
+    variable dataset follows (decreasing wavelengths and velocities)."""
+    return np.geomspace(lam_max, lam_min, n)

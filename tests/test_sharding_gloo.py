@@ -63,3 +63,25 @@ def test_partitions_cover_every_unit_once():
                 assert np.array_equal(allidx, np.arange(n))
     with pytest.raises(ValueError):
         sharding.shard(4, 2, 2)
+
+
+def test_modular_partition_balances_a_variable_curve_better(oracle_lib):
+    """Section 3.2: on a curve with decreasing wavelengths the per-wavelength
+    work (determinants evaluated by Algorithm 1) trends with the index, so the
+    modular partition beats the contiguous one at 3 and 8 ranks."""
+    m, g = W.single_curve()
+    h, a, b, r, _ = m.model(0)
+    lam = sharding.variable_curve_wavelengths(40)
+    work = []
+    for l in lam:
+        st, ct, idx = oracle_lib.scan(h, a, b, r, l, g.c0, g.dc, g.n_c)
+        assert st == 0
+        work.append(idx + 1)
+    work = np.array(work)
+    assert work[0] > work[-1]  # long wavelengths scan further
+    for P in (3, 8):
+        mod = sharding.partition_speedup(work, P, "modular")
+        con = sharding.partition_speedup(work, P, "contiguous")
+        assert mod > con
+        assert mod <= P + 1e-12 and con <= P + 1e-12
+    assert sharding.partition_speedup(work, 1) == 1.0
