@@ -225,6 +225,27 @@ def run_extras(args, masw, torch):
     out["differentiation"] = {"workload": "512 models x 12 layers, 150 wavelengths, LSQ misfit "
                                           "+ adjoint gradient (beta, h)",
                               "gradients_per_s": m4.n_models / dt, "ms_per_batch": 1e3 * dt}
+    # inversion loops (one inversion per model of the differentiation batch)
+    from paper_2003_02256_gb300 import inversion
+    with masw.Batch(m4, g4) as b:
+        ce_true = np.tile(gold[:, 2], m4.n_models)
+        inversion.gradient_inversion(b, ce_true, iters=2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, hist = inversion.gradient_inversion(b, ce_true, iters=10)
+        torch.cuda.synchronize()
+        t_grad = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, _, _, acc = inversion.metropolis(b, ce_true, steps=20, step_frac=0.01)
+        torch.cuda.synchronize()
+        t_mc = time.perf_counter() - t0
+    out["inversion"] = {"workload": "512 models x 12 layers, 150 wavelengths, observed curve = "
+                                    "true-model roots (tests/golden)",
+                        "descent_model_steps_per_s": m4.n_models * 10 / t_grad,
+                        "misfit_ratio_after_10_steps": float(np.median(hist[-1] / hist[0])),
+                        "metropolis_chain_steps_per_s": m4.n_models * 20 / t_mc,
+                        "metropolis_acceptance": float(np.mean(acc))}
+
     # partition study (Section 3.2): per-wavelength work of Algorithm 1 on a
     # 40-wavelength decreasing curve, split over P ranks contiguously or modularly
     m1, g1 = W.single_curve()
