@@ -23,11 +23,11 @@
 //   [meta: 4 x i32 (nrec, nlim, n_lambda, 0)] [records: rmax x 8 f64]
 //   [FP32 records: rmax x 8 f32] [k: imax f64]
 //   [scan state: imax x (base, carry, phase, ref) i32]
-// Each item runs the two-precision scan of the batch path: FP32 chunks
-// locate the first sign change; a single FP64 warp pass over V[0] and a
-// 31-point window around the located index decides it; when that pass does
-// not confirm, the item continues with FP64 chunks (one per tick) from the
-// window's end or from V[0].
+// Each item runs the two-precision scan of the batch path: paired FP32
+// chunks locate the first sign change; a thread-per-item FP64 check at V[0],
+// V[n-1], V[n] (a second kernel of the same tick) decides it; when the check
+// does not confirm, the item continues with FP64 chunks from V[0], one per
+// tick.
 // Results are written by the kernel into mapped pinned host memory, so
 // retiring a request is a host memcpy.
 #include <algorithm>
@@ -57,7 +57,7 @@ struct SlotView {
     int32_t* status;
     int32_t* remaining;  // [slots] items still running
     int32_t* done;       // [slots] slots finished during the tick
-    int32_t* counters;   // [0] survivors, [1] done count
+    int32_t* counters;   // [0] survivors, [1] done count, [2] check-list count
 };
 
 __device__ __forceinline__ const int32_t* slot_meta(const SlotView& v, int s) {
@@ -79,10 +79,15 @@ __device__ __forceinline__ int32_t* slot_state(const SlotView& v, int s) {
 
 enum { PH_SCREEN = 0, PH_FP64 = 1 };
 
+// Tick, part 1 (one warp per active item). PH_SCREEN: up to `chunks` paired
+// FP32 chunks (64 test velocities each); when the screen sees a change (or
+// reaches the scan limit) the item goes to the check list with its index.
+// PH_FP64: one FP64 chunk (32 test velocities) of the plain scan.
 __global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
                                                          const int32_t* __restrict__ active_in,
                                                          int n_active, int32_t* active_out,
-                                                         int chunks, double c0, double dc) {
+                                                         int32_t* check_list, int chunks,
+                                                         double c0, double dc) {
     extern __shared__ float smemf[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -95,57 +100,42 @@ __global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
     const int nrec = meta[0];
     const int nlim = meta[1];
     const int N = nrec - 1;
-    float* my = smemf + (size_t)wib * v.rmax * LAYER_STRIDE32;
-    const float* src = slot_records32(v, slot);
-    for (int t = lane; t < nrec * LAYER_STRIDE32; t += 32) my[t] = src[t];
-    __syncwarp();
-    const double* lay = slot_records(v, slot);
-    const double k = slot_k(v, slot)[j];
-    const float kf = (float)k, c0f = (float)c0, dcf = (float)dc;
     int32_t* stt = slot_state(v, slot) + 4 * j;
-    int base = stt[0], carry = stt[1], phase = stt[2], ref = stt[3];
+    int base = stt[0], carry = stt[1], phase = stt[2];
+    const double k = slot_k(v, slot)[j];
     int res = -1;
-    bool finished = false;
+    bool finished = false, to_check = false;
     if (phase == PH_SCREEN) {
-        for (int c = 0; c < chunks && !finished && phase == PH_SCREEN; ++c) {
-            int n = base + lane;
-            int sg = (n < nlim) ? det_sign_f(my, N, kf, fmaf((float)n, dcf, c0f)) : 0;
-            int prev = __shfl_up_sync(FULL, sg, 1);
-            if (lane == 0) prev = carry;
-            unsigned msk = __ballot_sync(FULL, n >= 1 && n < nlim && sg != prev);
-            int n32 = -1;
-            if (msk) {
-                n32 = base + __ffs(msk) - 1;
-            } else {
-                carry = __shfl_sync(FULL, sg, 31);
-                base += 32;
-                if (base >= nlim) n32 = -2;  // the screen saw no change
+        float* my = smemf + (size_t)wib * v.rmax * LAYER_STRIDE32;
+        const float* src = slot_records32(v, slot);
+        for (int t = lane; t < nrec * LAYER_STRIDE32; t += 32) my[t] = src[t];
+        __syncwarp();
+        const float kf = (float)k, c0f = (float)c0, dcf = (float)dc;
+        for (int c = 0; c < chunks && !to_check; ++c) {
+            const int n0 = base + 2 * lane, n1 = n0 + 1;
+            int s0 = 0, s1 = 0;
+            if (n1 < nlim) {
+                det_sign_f2(my, N, kf, fmaf((float)n0, dcf, c0f), fmaf((float)n1, dcf, c0f), &s0, &s1);
+            } else if (n0 < nlim) {
+                s0 = det_sign_f(my, N, kf, fmaf((float)n0, dcf, c0f));
             }
-            if (n32 == -1) continue;
-            // FP64 decision: lane 0 -> V[0]; lanes 1..31 -> V[w0 .. w0 + 30]
-            int w0 = n32 >= 0 ? max(0, n32 - 16) : max(0, nlim - 31);
-            int pt = lane == 0 ? 0 : w0 + lane - 1;
-            int s64 = (pt < nlim) ? det_sign(lay, N, k, grid_c(c0, dc, pt)) : 0;
-            int r0 = __shfl_sync(FULL, s64, 0);
-            int first = __shfl_sync(FULL, s64, 1);
-            int prv = __shfl_up_sync(FULL, s64, 1);
-            unsigned m64 = __ballot_sync(FULL, lane >= 2 && pt < nlim && s64 != prv);
-            int last = min(w0 + 30, nlim - 1);
-            int s_last = __shfl_sync(FULL, s64, last - w0 + 1);
-            if (first != r0) {  // an FP64 change below the window: FP64 from V[0]
-                phase = PH_FP64; base = 0; carry = 0; ref = r0;
-            } else if (m64) {
-                res = w0 + __ffs(m64) - 2;
-                finished = true;
-            } else if (last >= nlim - 1) {
-                finished = (s_last == r0);  // no change up to the last scanned point
-                if (!finished) { phase = PH_FP64; base = 0; carry = 0; ref = r0; }
-            } else {  // the screen's change was not confirmed: FP64 from the window's end
-                phase = PH_FP64; base = last + 1; carry = s_last; ref = r0;
+            int prev = __shfl_up_sync(FULL, s1, 1);
+            if (lane == 0) prev = carry;
+            unsigned m0 = __ballot_sync(FULL, n0 >= 1 && n0 < nlim && s0 != prev);
+            unsigned m1 = __ballot_sync(FULL, n1 < nlim && s1 != s0);
+            unsigned mm = m0 | m1;
+            if (mm) {
+                int l = __ffs(mm) - 1;
+                res = base + 2 * l + (((m0 >> l) & 1u) ? 0 : 1);
+                to_check = true;
+            } else {
+                carry = __shfl_sync(FULL, s1, 31);
+                base += 64;
+                if (base >= nlim) { res = -2; to_check = true; }
             }
         }
     } else if (base < nlim) {
-        // one FP64 chunk per tick
+        const double* lay = slot_records(v, slot);
         int n = base + lane;
         int sg = (n < nlim) ? det_sign(lay, N, k, grid_c(c0, dc, n)) : 0;
         int prev = __shfl_up_sync(FULL, sg, 1);
@@ -179,9 +169,66 @@ __global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
             stt[0] = base;
             stt[1] = carry;
             stt[2] = phase;
-            stt[3] = ref;
-            active_out[atomicAdd(&v.counters[0], 1)] = item;
+            if (to_check) {
+                stt[3] = res;  // screen index (-2: none below the limit)
+                check_list[atomicAdd(&v.counters[2], 1)] = item;
+            } else {
+                active_out[atomicAdd(&v.counters[0], 1)] = item;
+            }
         }
+    }
+}
+
+// Tick, part 2 (one thread per item on the check list): FP64 signs at V[0],
+// V[n32-1], V[n32] (or V[0] and the last scanned point) accept the screen's
+// index; otherwise the item continues with the FP64 scan from V[0].
+__global__ void serve_check_kernel(SlotView v, const int32_t* __restrict__ check_list,
+                                   const int32_t* __restrict__ n_check, int32_t* active_out,
+                                   double c0, double dc) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *n_check) return;
+    const int item = check_list[t];
+    const int slot = item / v.imax;
+    const int j = item - slot * v.imax;
+    const int32_t* meta = slot_meta(v, slot);
+    const int N = meta[0] - 1;
+    const int nlim = meta[1];
+    const double* lay = slot_records(v, slot);
+    const double k = slot_k(v, slot)[j];
+    int32_t* stt = slot_state(v, slot) + 4 * j;
+    const int n = stt[3];
+    int res = -1;
+    bool ok;
+    if (nlim < 2) {
+        ok = true;
+    } else {
+        int s0 = det_sign(lay, N, k, grid_c(c0, dc, 0));
+        if (n >= 1) {
+            int sa = (n == 1) ? s0 : det_sign(lay, N, k, grid_c(c0, dc, n - 1));
+            int sb = det_sign(lay, N, k, grid_c(c0, dc, n));
+            ok = (sa == s0) && (sb != sa);
+            res = n;
+        } else {
+            ok = det_sign(lay, N, k, grid_c(c0, dc, nlim - 1)) == s0;
+        }
+    }
+    if (ok) {
+        if (res >= 0) {
+            v.ct[item] = grid_c(c0, dc, res);
+            v.idx[item] = res;
+            v.status[item] = MASW_FOUND;
+        } else {
+            v.ct[item] = __longlong_as_double(0x7ff8000000000000LL);
+            v.idx[item] = -1;
+            v.status[item] = MASW_NO_ROOT;
+        }
+        __threadfence_system();
+        if (atomicSub(&v.remaining[slot], 1) == 1) v.done[atomicAdd(&v.counters[1], 1)] = slot;
+    } else {
+        stt[0] = 0;
+        stt[1] = 0;
+        stt[2] = PH_FP64;
+        active_out[atomicAdd(&v.counters[0], 1)] = item;
     }
 }
 
@@ -216,6 +263,7 @@ struct masw_server {
     int32_t* h_idx = nullptr;
     int32_t* h_status = nullptr;
     int32_t* active[2] = {nullptr, nullptr};
+    int32_t* check = nullptr;
     int32_t* h_new_items = nullptr;
     int32_t* h_counters = nullptr;
     int32_t* h_done = nullptr;
@@ -240,7 +288,7 @@ namespace {
 void server_free(masw_server* S) {
     if (!S) return;
     void* dev[] = {S->v.region, S->v.remaining, S->v.done, S->v.counters, S->active[0],
-                   S->active[1]};
+                   S->active[1], S->check};
     for (void* p : dev)
         if (p) cudaFree(p);
     void* host[] = {S->h_region, S->h_ct, S->h_idx, S->h_status, S->h_new_items, S->h_counters,
@@ -273,17 +321,21 @@ int run_tick(masw_server* S) {
         S->pending.clear();
     }
     if (S->n_active == 0) return MASW_OK;
-    if (cudaMemsetAsync(S->v.counters, 0, 2 * sizeof(int32_t), S->stream) != cudaSuccess)
+    if (cudaMemsetAsync(S->v.counters, 0, 3 * sizeof(int32_t), S->stream) != cudaSuccess)
         return MASW_ECUDA;
     int wpb = S->cfg.warps_per_block;
     int blocks = (S->n_active + wpb - 1) / wpb;
     size_t shm = (size_t)wpb * S->v.rmax * LAYER_STRIDE32 * sizeof(float);
     serve_tick_kernel<<<blocks, 32 * wpb, shm, S->stream>>>(S->v, S->active[S->cur], S->n_active,
-                                                            S->active[1 - S->cur],
+                                                            S->active[1 - S->cur], S->check,
                                                             S->cfg.chunks_per_tick, S->grid.c0,
                                                             S->grid.dc);
     if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
-    if (cudaMemcpyAsync(S->h_counters, S->v.counters, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost,
+    // every item that entered the check list this tick (at most n_active)
+    serve_check_kernel<<<(S->n_active + 127) / 128, 128, 0, S->stream>>>(
+        S->v, S->check, S->v.counters + 2, S->active[1 - S->cur], S->grid.c0, S->grid.dc);
+    if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
+    if (cudaMemcpyAsync(S->h_counters, S->v.counters, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost,
                         S->stream) != cudaSuccess ||
         cudaEventRecord(S->ev, S->stream) != cudaSuccess ||
         cudaEventSynchronize(S->ev) != cudaSuccess)
@@ -354,8 +406,9 @@ int masw_server_create(const masw_grid* grid, const masw_server_config* cfg, voi
     S->v.stride = (S->v.stride + 31) / 32 * 32;  // 256-byte aligned slots
     size_t slots = cfg->max_slots, items = (size_t)cap_items;
     bool ok = dalloc(&S->v.region, slots * S->v.stride) && dalloc(&S->v.remaining, slots) &&
-              dalloc(&S->v.done, slots) && dalloc(&S->v.counters, 2) &&
+              dalloc(&S->v.done, slots) && dalloc(&S->v.counters, 3) &&
               dalloc(&S->active[0], items) && dalloc(&S->active[1], items) &&
+              dalloc(&S->check, items) &&
               halloc(&S->h_region, slots * S->v.stride) &&
               halloc(&S->h_ct, items, cudaHostAllocMapped) &&
               halloc(&S->h_idx, items, cudaHostAllocMapped) &&
