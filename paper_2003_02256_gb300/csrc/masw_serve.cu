@@ -309,7 +309,13 @@ bool halloc(T** p, size_t n, unsigned flags = cudaHostAllocDefault) {
 }
 
 // Launch one tick and wait for it; the finished slots land in just_done.
+int run_tick_impl(masw_server* S);
 int run_tick(masw_server* S) {
+    int rc = run_tick_impl(S);
+    if (rc != MASW_OK) cudaGetLastError();  // leave no pending error behind
+    return rc;
+}
+int run_tick_impl(masw_server* S) {
     S->just_done.clear();
     int n_new = (int)S->pending.size();
     if (n_new) {
@@ -413,7 +419,7 @@ int masw_server_create(const masw_grid* grid, const masw_server_config* cfg, voi
               halloc(&S->h_ct, items, cudaHostAllocMapped) &&
               halloc(&S->h_idx, items, cudaHostAllocMapped) &&
               halloc(&S->h_status, items, cudaHostAllocMapped) && halloc(&S->h_new_items, items) &&
-              halloc(&S->h_counters, 2) && halloc(&S->h_done, slots) &&
+              halloc(&S->h_counters, 3) && halloc(&S->h_done, slots) &&
               cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming) == cudaSuccess &&
               cudaHostGetDevicePointer((void**)&S->v.ct, S->h_ct, 0) == cudaSuccess &&
               cudaHostGetDevicePointer((void**)&S->v.idx, S->h_idx, 0) == cudaSuccess &&
