@@ -77,7 +77,7 @@ __device__ __forceinline__ int32_t* slot_state(const SlotView& v, int s) {
                       v.imax);
 }
 
-enum { PH_SCREEN = 0, PH_FP64 = 1 };
+enum { PH_SCREEN = 0, PH_FP64 = 1, PH_FP64_WINDOW = 2 };
 
 // Tick, part 1 (one warp per active item). PH_SCREEN: up to `chunks` paired
 // FP32 chunks (64 test velocities each); when the screen sees a change (or
@@ -135,19 +135,29 @@ __global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
             }
         }
     } else if (base < nlim) {
+        // one FP64 chunk per tick; a PH_FP64_WINDOW chunk starts below the
+        // screen's index and its first point must carry V[0]'s sign (carry)
         const double* lay = slot_records(v, slot);
         int n = base + lane;
         int sg = (n < nlim) ? det_sign(lay, N, k, grid_c(c0, dc, n)) : 0;
         int prev = __shfl_up_sync(FULL, sg, 1);
+        bool window = phase == PH_FP64_WINDOW;
         if (lane == 0) prev = carry;
-        unsigned msk = __ballot_sync(FULL, n >= 1 && n < nlim && sg != prev);
-        if (msk) {
-            res = base + __ffs(msk) - 1;
-            finished = true;
+        if (window && __shfl_sync(FULL, sg, 0) != carry) {
+            base = 0;  // an FP64 change below the window: scan from V[0]
+            carry = 0;
+            phase = PH_FP64;
         } else {
-            carry = __shfl_sync(FULL, sg, 31);
-            base += 32;
-            finished = base >= nlim;
+            unsigned msk = __ballot_sync(FULL, n >= 1 && n < nlim && sg != prev);
+            if (msk) {
+                res = base + __ffs(msk) - 1;
+                finished = true;
+            } else {
+                carry = __shfl_sync(FULL, sg, 31);
+                base += 32;
+                phase = PH_FP64;
+                finished = base >= nlim;
+            }
         }
     } else {
         finished = true;
@@ -225,9 +235,12 @@ __global__ void serve_check_kernel(SlotView v, const int32_t* __restrict__ check
         __threadfence_system();
         if (atomicSub(&v.remaining[slot], 1) == 1) v.done[atomicAdd(&v.counters[1], 1)] = slot;
     } else {
-        stt[0] = 0;
-        stt[1] = 0;
-        stt[2] = PH_FP64;
+        // FP64 from 17 points below the screen's index (first point checked
+        // against V[0]'s sign), or from V[0] when the index is that small
+        bool win = n >= 18;
+        stt[0] = win ? n - 17 : 0;
+        stt[1] = win ? det_sign(lay, N, k, grid_c(c0, dc, 0)) : 0;
+        stt[2] = win ? PH_FP64_WINDOW : PH_FP64;
         active_out[atomicAdd(&v.counters[0], 1)] = item;
     }
 }
