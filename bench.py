@@ -185,6 +185,66 @@ def executed_layer_evals(models, idx, st, nlim, cpl):
     return int(np.sum(pts * nl))
 
 
+def counting_evals(models, grid, idx, st, nlim, n32):
+    """Per-item evaluations of the counting-search scan (plan precision 2):
+    FP32 layer evaluations of the search (1 + ceil(log2 npf) inertia counts
+    for a located item, npf = grid points below the pole-free bound
+    min_i beta_i sqrt(1 + (pi/(k h_i))^2)) and of the linear fallback (points
+    from its start up to the change), and FP64 layer evaluations of the
+    check (2 for a certified item, V[0], V[n-1], V[n] otherwise)."""
+    counted = (n32 >= 0) & ((n32 & (1 << 30)) != 0)
+    hoff, loff, _ = models.layer_offsets()
+    item_model = np.repeat(np.arange(models.n_models), models.n_lambda)
+    nl = (models.n_layers.astype(np.int64) + 1)[item_model]
+    k = 2.0 * np.pi / models.lam
+    cb = np.full(models.n_items, np.inf)
+    for m in range(models.n_models):
+        h, _, b, _, _ = models.model(m)
+        sl = slice(int(np.sum(models.n_lambda[:m])), int(np.sum(models.n_lambda[:m + 1])))
+        kk = k[sl][:, None]
+        cb[sl] = np.min(b[None, :-1] * np.sqrt(1.0 + (np.pi / (kk * h[None, :])) ** 2), axis=1)
+    lim = nlim[item_model].astype(np.int64)
+    npf = np.clip(np.ceil((cb * (1.0 - 1e-4) - grid.c0) / grid.dc), 0, lim).astype(np.int64)
+    search = np.where(npf >= 1, 1 + np.ceil(np.log2(np.maximum(npf, 1))), 0)
+    root = np.where(st == 0, idx.astype(np.int64), lim - 1)
+    start = np.where(root >= npf, npf, 0)
+    linear = np.where(counted, 0, np.maximum(root - start + 1, 0))
+    fp64 = np.where(counted, 2, np.where(st == 0, 3, 2))
+    fp64 = np.where(lim >= 2, fp64, 0)
+    return (int(np.sum((search + linear) * nl)), int(np.sum(fp64 * nl)),
+            float(np.mean(counted)))
+
+
+def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, sms):
+    """Roofline of the dominant kernel of a counting-search scan: the FP32
+    search (+ fallback) against the FP32 pipe or the FP64 check against the
+    FP64 pipe, both from algorithmic layer evaluations / device time."""
+    e32, e64, frac_counted = counting_evals(models, grid, idx, st, nlim, n32)
+    peak32 = FP32_FFMA_PER_CLK_SM * 2.0 * sms * SM_MAX_MHZ * 1e6
+    common = {"bound": "alu", "unit": "TFLOP/s",
+              "phases_ms": {"search32": phases[0], "verify64": phases[1],
+                            "resolve64": phases[2]},
+              "counted_fraction": frac_counted,
+              "search_layer_evals_fp32": e32, "check_layer_evals_fp64": e64,
+              "fp64_peak_microbenchmark": micro / 1e12}
+    if phases[1] >= phases[0]:
+        achieved = e64 * F_LAYER_FLOPS / (phases[1] * 1e-3)
+        common.update({"achieved": achieved / 1e12, "peak": peak64 / 1e12,
+                       "frac": achieved / peak64, "traffic": None,
+                       "kernel": "verify64_kernel (FP64 pipe, certificate)",
+                       "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
+                       "layer_evals_per_launch": e64, "flops_per_layer_eval": F_LAYER_FLOPS})
+    else:
+        achieved = e32 * F_LAYER_FLOPS_FP32 / (phases[0] * 1e-3)
+        common.update({"achieved": achieved / 1e12, "peak": peak32 / 1e12,
+                       "frac": achieved / peak32, "traffic": None,
+                       "kernel": "search32_kernel + fallback32p_kernel (FP32 pipe)",
+                       "peak_source": "derived: 128 FFMA/clk/SM x 2 flop x SMs x 2070 MHz",
+                       "layer_evals_per_launch": e32,
+                       "flops_per_layer_eval": F_LAYER_FLOPS_FP32})
+    return common
+
+
 def run_extras(args, masw, torch):
     """Secondary workloads on the same line: the ragged batch (autotuned
     persistent graph vs one launch per model), the differentiation batch
@@ -297,8 +357,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--ragged-models", type=int, default=8192)
     ap.add_argument("--serving-requests", type=int, default=2000)
-    ap.add_argument("--precision", type=int, default=None, choices=[0, 1],
-                    help="scan plan: 0 FP64 scan, 1 FP32 screen + FP64 decision (default: library)")
+    ap.add_argument("--precision", type=int, default=None, choices=[0, 1, 2],
+                    help="scan plan: 0 FP64 scan, 1 FP32 screen + FP64 decision, 2 counting "
+                         "search + FP64 certificate (default: library)")
     ap.add_argument("--cpl", type=int, default=None, choices=[1, 2, 4],
                     help="scan plan test velocities per lane (2: paired FP32x2 screen)")
     ap.add_argument("--workload", default="uniform", choices=["uniform", "ragged"],
@@ -407,7 +468,9 @@ def main():
     # without the graph so events can sit between them)
     phases = None
     unresolved = None
-    if plan.precision == 1:
+    fallback = None
+    n32 = None
+    if plan.precision >= 1:
         batch.set_plan(use_graph=0)
         ph = []
         for _ in range(3):
@@ -415,6 +478,9 @@ def main():
             batch.dispersion()
             ph.append(masw.last_scan_phases(batch.handle))
         unresolved = batch.last_scan_unresolved()
+        fallback = batch.last_scan_fallback()
+        n32 = np.empty(models.n_items, dtype=np.int32)
+        masw.last_scan_screen(batch.handle, n32)
         batch.set_plan(use_graph=plan.use_graph)
         phases = [float(np.mean([p[i] for p in ph])) for i in range(3)]
 
@@ -436,6 +502,11 @@ def main():
                     "layer_evals_per_launch": units, "flops_per_layer_eval": F_LAYER_FLOPS,
                     "executed_layer_evals_per_launch": executed,
                     "scan_ms": scan_avg * 1e3}
+    elif plan.precision == 2:
+        roofline = counting_roofline(models, grid, idx, st, nlim, n32, phases, peak, micro,
+                                     masw.sm_count())
+        roofline.update({"scan_ms": scan_avg * 1e3, "unresolved_items": unresolved,
+                         "fallback_items": fallback})
     else:
         peak32 = FP32_FFMA_PER_CLK_SM * 2.0 * masw.sm_count() * SM_MAX_MHZ * 1e6
         t_screen = phases[0] * 1e-3
@@ -476,7 +547,7 @@ def main():
                 "clocks": clk.summary(),
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": (4 if plan.precision == 1 else 2) * args.steps,
+                "gpu_launches": {0: 2, 1: 4, 2: 5}[plan.precision] * args.steps,
                 "roofline": roofline,
                 "cpu_baseline": cpu,
                 "plain_gpu": None if plain_value is None else {

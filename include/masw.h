@@ -103,7 +103,12 @@ typedef struct {
     int32_t use_graph;       /* 1: replay the scan as a captured CUDA graph */
     int32_t precision;       /* 0: FP64 scan of every test velocity; 1: FP32 screen locates the
                                 first change, FP64 decides it (V[0], V[n-1], V[n], then an FP64
-                                window or full re-scan when they disagree) */
+                                window or full re-scan when they disagree); 2: as 1, but the
+                                FP32 change is located by a Wittrick-Williams counting search
+                                (bisection on the number of negative eigenvalues of K below
+                                the pole-free bound min_i beta_i sqrt(1 + (pi/(k h_i))^2)),
+                                certified in FP64 by count 0 at V[n-1] and odd at V[n]; items
+                                outside the bound take the linear screen of 1 */
 } masw_plan;
 
 /* Copy and validate a model batch into batch-owned device memory and bind it
@@ -203,13 +208,21 @@ int masw_last_scan_phases(const masw_batch* batch, float* ms);
 
 /* The FP32 screen's first-change index per item (item order, -1 when the
  * screen saw none) from the most recent two-precision scan, host or device
- * buffer of n_items; a diagnostic of how well the screen locates roots. */
+ * buffer of n_items; a diagnostic of how well the screen locates roots.
+ * Under plan precision 2, bit 30 (MASW_SCREEN_COUNTED) is set on items whose
+ * index the counting search located and the FP64 count certified. */
+#define MASW_SCREEN_COUNTED (1 << 30)
 int masw_last_scan_screen(masw_batch* batch, int32_t* n32);
 
-/* Items of the most recent two-precision scan (plan precision 1) whose FP32
+/* Items of the most recent two-precision scan (plan precision 1 or 2) whose FP32
  * screen disagreed with the FP64 check and were re-scanned in FP64 (-1 for a
  * precision-0 plan). Synchronises the batch stream. */
 int masw_last_scan_unresolved(const masw_batch* batch, int32_t* n);
+
+/* Items of the most recent counting-search scan (plan precision 2) that fell
+ * back to the linear FP32 screen (change above the pole-free bound, at V[0],
+ * or an even count jump); -1 for other plans. Synchronises the batch stream. */
+int masw_last_scan_fallback(const masw_batch* batch, int32_t* n);
 
 /* FP64 fused multiply-add throughput of this GPU in flop/s (2 per DFMA),
  * measured by a dependent-chain microbenchmark on `cuda_stream`. */

@@ -72,7 +72,8 @@ struct masw_batch {
     int32_t* d_n32 = nullptr;
     int32_t* d_ref = nullptr;
     int32_t* d_unres = nullptr;
-    int32_t* d_counters3 = nullptr;
+    int32_t* d_fallback = nullptr;
+    int32_t* d_counters = nullptr;  // SCAN_COUNTERS
 
     masw_plan plan{};
     cudaGraphExec_t graph = nullptr;
@@ -274,11 +275,13 @@ static void free_batch(masw_batch* B) {
                     B->d_item_model, B->d_order_sorted, B->d_order_natural, B->d_grad_off,
                     B->d_counter, B->d_ct, B->d_idx, B->d_status, B->d_croot, B->d_rows, B->d_bs,
                     B->d_dphi, B->d_ce, B->d_misfit, B->d_gb, B->d_gh, B->d_layers32,
-                    B->d_n32, B->d_ref, B->d_unres, B->d_counters3};
+                    B->d_n32, B->d_ref, B->d_unres, B->d_fallback, B->d_counters};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete B;
 }
+
+static_assert(MASW_SCREEN_COUNTED == SCREEN_COUNTED, "n32 flag of the counting search");
 
 static masw_plan default_plan(const masw_batch* B) {
     masw_plan p;
@@ -297,7 +300,7 @@ static bool plan_ok(const masw_plan& p) {
     bool wpb = p.warps_per_block == 1 || p.warps_per_block == 2 || p.warps_per_block == 4 ||
                p.warps_per_block == 8;
     bool cpl = p.cpl == 1 || p.cpl == 2 || p.cpl == 4;
-    return wpb && cpl && (p.precision == 0 || p.precision == 1) && p.blocks_per_sm >= 1 &&
+    return wpb && cpl && p.precision >= 0 && p.precision <= 2 && p.blocks_per_sm >= 1 &&
            p.blocks_per_sm <= 32 && p.stage_layers >= 0 &&
            p.stage_layers <= MASW_MAX_LAYERS + 1 &&
            (size_t)p.warps_per_block * p.stage_layers * LAYER_STRIDE * sizeof(double) <= 48 * 1024;
@@ -316,11 +319,12 @@ static ScanPlan to_scan_plan(const masw_batch* B, const masw_plan& p) {
 // Enqueue one full scan (all items) with the given plan on stream s.
 static cudaError_t enqueue_scan(masw_batch* B, const masw_plan& p, cudaStream_t s,
                                 bool phase_events = false) {
-    if (p.precision == 1) {
+    if (p.precision >= 1) {
         ScanOut o{B->d_ct, B->d_idx, B->d_status};
         return launch_screen_scan(B->dev(p.ordered != 0), o, to_scan_plan(B, p), B->d_layers32,
-                                  B->d_n32, B->d_ref, B->d_unres, B->d_counters3, 0,
-                                  (int)B->n_items, s, phase_events ? B->phase_ev : nullptr);
+                                  B->d_n32, B->d_ref, B->d_unres, B->d_fallback, B->d_counters,
+                                  p.precision == 2, 0, (int)B->n_items, s,
+                                  phase_events ? B->phase_ev : nullptr);
     }
     if (p.persistent) {
         cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(int32_t), s);
@@ -362,7 +366,7 @@ static int run_scan(masw_batch* B) {
         CK(cudaGraphLaunch(B->graph, B->stream));
         B->phases_valid = false;
     } else {
-        bool ph = B->plan.precision == 1;
+        bool ph = B->plan.precision >= 1;
         CK(enqueue_scan(B, B->plan, B->stream, ph));
         B->phases_valid = ph;
     }
@@ -498,7 +502,8 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
         dev_alloc(&B->d_grad_off, nw + 1) || dev_alloc(&B->d_counter, 1) ||
         dev_alloc(&B->d_ct, nw) || dev_alloc(&B->d_idx, nw) || dev_alloc(&B->d_status, nw) ||
         dev_alloc(&B->d_layers32, rec32.size()) || dev_alloc(&B->d_n32, nw) ||
-        dev_alloc(&B->d_ref, nw) || dev_alloc(&B->d_unres, nw) || dev_alloc(&B->d_counters3, 3)) {
+        dev_alloc(&B->d_ref, nw) || dev_alloc(&B->d_unres, nw) || dev_alloc(&B->d_fallback, nw) ||
+        dev_alloc(&B->d_counters, SCAN_COUNTERS)) {
         free_batch(B);
         return MASW_ENOMEM;
     }
@@ -629,9 +634,10 @@ int masw_dispersion_plain(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* s
     ScanPlan sp = to_scan_plan(B, p);
     CK(cudaEventRecord(B->ev0, B->stream));
     for (int32_t m = 0; m < B->n_models; ++m) {
-        if (p.precision == 1)
+        if (p.precision >= 1)
             CK(launch_screen_scan(d, o, sp, B->d_layers32, B->d_n32, B->d_ref, B->d_unres,
-                                  B->d_counters3, B->woff[m], B->woff[m + 1], B->stream, nullptr));
+                                  B->d_fallback, B->d_counters, p.precision == 2, B->woff[m],
+                                  B->woff[m + 1], B->stream, nullptr));
         else
             CK(launch_scan(d, o, sp, B->d_counter, B->woff[m], B->woff[m + 1], B->stream));
         CK(cudaStreamSynchronize(B->stream));
@@ -651,7 +657,7 @@ int masw_last_scan_phases(const masw_batch* B, float* ms) {
 }
 
 int masw_last_scan_screen(masw_batch* B, int32_t* n32) {
-    if (!B || !n32 || B->plan.precision != 1) return MASW_EINVAL;
+    if (!B || !n32 || B->plan.precision < 1) return MASW_EINVAL;
     bool sync = false;
     int rc = copy_out(n32, B->d_n32, B->n_items, B->stream, &sync);
     if (rc) return rc;
@@ -661,13 +667,26 @@ int masw_last_scan_screen(masw_batch* B, int32_t* n32) {
 
 int masw_last_scan_unresolved(const masw_batch* B, int32_t* n) {
     if (!B || !n) return MASW_EINVAL;
-    if (B->plan.precision != 1) {
+    if (B->plan.precision < 1) {
         *n = -1;
         return MASW_OK;
     }
     int32_t v = 0;
     CK(cudaStreamSynchronize(B->stream));
-    CK(cudaMemcpy(&v, B->d_counters3 + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&v, B->d_counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    *n = v;
+    return MASW_OK;
+}
+
+int masw_last_scan_fallback(const masw_batch* B, int32_t* n) {
+    if (!B || !n) return MASW_EINVAL;
+    if (B->plan.precision != 2) {
+        *n = -1;
+        return MASW_OK;
+    }
+    int32_t v = 0;
+    CK(cudaStreamSynchronize(B->stream));
+    CK(cudaMemcpy(&v, B->d_counters + 3, sizeof(int32_t), cudaMemcpyDeviceToHost));
     *n = v;
     return MASW_OK;
 }

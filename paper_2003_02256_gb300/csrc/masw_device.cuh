@@ -230,6 +230,34 @@ __device__ __forceinline__ int det_sign(const double* __restrict__ lay, int N, d
     return sg * sgn(fma(s00, s11, -s01 * s01));
 }
 
+// Number of negative eigenvalues of K(k, c) (Sylvester's law of inertia over
+// the 2x2 Schur pivots S_j = Shat_j / (w Dh)): a pivot with det < 0 has one,
+// one with det > 0 has two when its diagonal is negative. A zero determinant
+// counts as one; -1 when the rescaling failed. The parity equals the sign
+// det_sign reports (same arithmetic). Requires c < beta_halfspace.
+__device__ inline int det_inertia(const double* __restrict__ lay, int N, double k, double c) {
+    double c2 = c * c;
+    HState st{0.0, 0.0, 0.0, 1.0};
+    int cnt = 0;
+    double sv[3];
+    for (int j = 0; j < N; ++j) {
+        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2);
+        double f = st.w * n.Dh;
+        bool ok;
+        double det = schur_layer(st, n, &ok, sv);
+        cnt += det < 0.0 ? 1 : (det > 0.0 ? (((sv[0] < 0.0) != (f < 0.0)) ? 2 : 0) : 1);
+        if (!ok) return -1;
+    }
+    HalfNum hn = halfspace_numerators(lay + N * LAYER_STRIDE, c2);
+    double f = st.w * hn.den;
+    double s00 = fma(hn.den, st.p00, st.w * hn.m00);
+    double s01 = fma(hn.den, st.p01, st.w * hn.m01);
+    double s11 = fma(hn.den, st.p11, st.w * hn.m11);
+    double det = fma(s00, s11, -s01 * s01);
+    cnt += det < 0.0 ? 1 : (det > 0.0 ? (((s00 < 0.0) != (f < 0.0)) ? 2 : 0) : 1);
+    return cnt;
+}
+
 // Sign and ln|det K| including the dropped factor k^(2(N+1)) (parity checks).
 __device__ inline int det_sign_log(const double* __restrict__ lay, int N, double k, double c,
                                    double* log_abs) {

@@ -38,11 +38,17 @@ struct ScanPlan {
     int stage_layers;     // layer records staged in shared memory per warp (0 = read global)
 };
 
-// FP32 screen + FP64 decision (masw_screen.cuh, masw_kernels.cu).
+// FP32 screen + FP64 decision (masw_screen.cuh, masw_kernels.cu). search 0:
+// linear FP32 screen; 1: counting search with the linear screen as fallback.
+// n32, ref_sign, unresolved, fallback: n_items each; counters: SCAN_COUNTERS.
+constexpr int SCAN_COUNTERS = 5;
+// n32 flag of an index located by the counting search (MASW_SCREEN_COUNTED)
+constexpr int32_t SCREEN_COUNTED = 1 << 30;
 cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p,
                                const float* layers32, int32_t* n32, int32_t* ref_sign,
-                               int32_t* unresolved, int32_t* counters, int item_begin,
-                               int item_end, cudaStream_t s, cudaEvent_t* phase_ev);
+                               int32_t* unresolved, int32_t* fallback, int32_t* counters,
+                               int search, int item_begin, int item_end, cudaStream_t s,
+                               cudaEvent_t* phase_ev);
 
 cudaError_t launch_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p, int32_t* counter,
                         int item_begin, int item_end, cudaStream_t s);

@@ -214,9 +214,38 @@ __global__ void __launch_bounds__(256) screen32_kernel(DevBatch b, const float* 
     }
 }
 
-// Paired variant of the screen: lane l evaluates the adjacent points
-// base + 2l and base + 2l + 1 with packed FP32x2 arithmetic (64 points per
-// chunk); the first change is the first set bit of the interleaved masks.
+// Paired linear FP32 scan of one item by one warp from grid index `start`
+// (`carry`: the FP32 sign assumed at V[start - 1]; unused for start 0): lane
+// l evaluates the adjacent points base + 2l and base + 2l + 1 with packed
+// FP32x2 arithmetic (64 points per chunk); the first change is the first set
+// bit of the interleaved masks. Returns the index (warp-uniform) or -1.
+__device__ __forceinline__ int screen_paired_item(const float* __restrict__ lay, int N, float k,
+                                                  float c0, float dc, int nlim, int start,
+                                                  int carry, int lane) {
+    int res = -1;
+    for (int base = start; base < nlim && res < 0; base += 64) {
+        const int n0 = base + 2 * lane, n1 = n0 + 1;
+        int s0 = 0, s1 = 0;
+        if (n1 < nlim) {
+            det_sign_f2(lay, N, k, fmaf((float)n0, dc, c0), fmaf((float)n1, dc, c0), &s0, &s1);
+        } else if (n0 < nlim) {
+            s0 = det_sign_f(lay, N, k, fmaf((float)n0, dc, c0));
+        }
+        int prev = __shfl_up_sync(FULL, s1, 1);
+        if (lane == 0) prev = carry;
+        unsigned m0 = __ballot_sync(FULL, n0 >= 1 && n0 < nlim && s0 != prev);
+        unsigned m1 = __ballot_sync(FULL, n1 < nlim && s1 != s0);
+        unsigned mm = m0 | m1;
+        if (mm) {
+            int l = __ffs(mm) - 1;
+            res = base + 2 * l + (((m0 >> l) & 1u) ? 0 : 1);
+        }
+        carry = __shfl_sync(FULL, s1, 31);
+    }
+    return res;
+}
+
+// Paired variant of the screen (screen_paired_item from V[0]).
 __global__ void __launch_bounds__(256) screen32p_kernel(DevBatch b, const float* __restrict__ layers32,
                                                         int32_t* n32out, int persistent,
                                                         int stage_layers, int32_t* counter,
@@ -249,29 +278,7 @@ __global__ void __launch_bounds__(256) screen32p_kernel(DevBatch b, const float*
         }
         const float k = (float)b.k[item];
         const int nlim = b.model_nlim[m];
-        int res = -1;
-        if (nlim >= 2) {
-            int carry = 0;
-            for (int base = 0; base < nlim && res < 0; base += 64) {
-                const int n0 = base + 2 * lane, n1 = n0 + 1;
-                int s0 = 0, s1 = 0;
-                if (n1 < nlim) {
-                    det_sign_f2(lay, N, k, fmaf((float)n0, dc, c0), fmaf((float)n1, dc, c0), &s0, &s1);
-                } else if (n0 < nlim) {
-                    s0 = det_sign_f(lay, N, k, fmaf((float)n0, dc, c0));
-                }
-                int prev = __shfl_up_sync(FULL, s1, 1);
-                if (lane == 0) prev = carry;
-                unsigned m0 = __ballot_sync(FULL, n0 >= 1 && n0 < nlim && s0 != prev);
-                unsigned m1 = __ballot_sync(FULL, n1 < nlim && s1 != s0);
-                unsigned mm = m0 | m1;
-                if (mm) {
-                    int l = __ffs(mm) - 1;
-                    res = base + 2 * l + (((m0 >> l) & 1u) ? 0 : 1);
-                }
-                carry = __shfl_sync(FULL, s1, 31);
-            }
-        }
+        int res = nlim >= 2 ? screen_paired_item(lay, N, k, c0, dc, nlim, 0, 0, lane) : -1;
         if (lane == 0) n32out[item] = res;
         __syncwarp();
         if (persistent) {
@@ -281,6 +288,101 @@ __global__ void __launch_bounds__(256) screen32p_kernel(DevBatch b, const float*
         } else {
             pos = item_end;
         }
+    }
+}
+
+// Counting search: one thread per item (natural item order, so a warp's
+// threads share a model and have adjacent wavelengths). Inside the pole-free
+// range [0, npf) of pole_free_points_f the FP32 negative-eigenvalue count
+// (inertia_f) is a non-decreasing step function of the grid index that is 0
+// at c = 0, so the first index with a nonzero count is found by bisection in
+// ceil(log2(npf + 1)) evaluations instead of a linear walk. An odd count
+// there is Algorithm 1's first sign change; the index is stored with
+// SCREEN_COUNTED for the FP64 certificate of verify64_kernel. Items whose change
+// lies above the range (count 0 at its last point), at V[0], or where the
+// count jumps by an even number, go to the fallback list for the linear
+// FP32 scan, with the grid index to start from in n32.
+__global__ void __launch_bounds__(128) search32_kernel(DevBatch b, const float* __restrict__ layers32,
+                                                       int32_t* n32out, int32_t* fallback,
+                                                       int32_t* n_fallback, int item_begin,
+                                                       int item_end) {
+    const int item = item_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= item_end) return;
+    const int m = b.item_model[item];
+    const int lo_rec = b.model_loff[m];
+    const int N = b.model_loff[m + 1] - lo_rec - 1;
+    const float* lay = layers32 + (size_t)lo_rec * LAYER_STRIDE32;
+    const int nlim = b.model_nlim[m];
+    if (nlim < 2) {
+        n32out[item] = -1;
+        return;
+    }
+    const float k = (float)b.k[item];
+    const float c0 = (float)b.c0, dc = (float)b.dc;
+    const int npf = pole_free_points_f(lay, N, k, c0, dc, nlim);
+    int start = 0, res = -1;
+    if (npf >= 1) {
+        int hi = npf - 1;
+        int chi = inertia_f(lay, N, k, fmaf((float)hi, dc, c0));
+        if (chi == 0) {
+            start = npf;  // no mode below the bound: scan linearly above it
+        } else {
+            int lo = -1;  // count 0 at c = 0
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                const int cm = inertia_f(lay, N, k, fmaf((float)mid, dc, c0));
+                if (cm >= 1) {
+                    hi = mid;
+                    chi = cm;
+                } else {
+                    lo = mid;
+                }
+            }
+            if (hi >= 1 && (chi & 1)) res = hi;
+        }
+    }
+    if (res >= 1) {
+        n32out[item] = res | SCREEN_COUNTED;
+    } else {
+        n32out[item] = start;
+        fallback[atomicAdd(n_fallback, 1)] = item;
+    }
+}
+
+// Linear paired FP32 scan of the fallback items of search32_kernel: one warp
+// per listed item, from the start index in n32 (the points below it carry
+// count 0, i.e. a positive FP32 sign).
+__global__ void __launch_bounds__(256) fallback32p_kernel(DevBatch b, const float* __restrict__ layers32,
+                                                          int32_t* n32, const int32_t* __restrict__ fallback,
+                                                          const int32_t* __restrict__ n_fallback,
+                                                          int32_t* counter, int stage_layers) {
+    extern __shared__ float smemf[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    float* my = smemf + (size_t)wib * stage_layers * LAYER_STRIDE32;
+    const int total = *n_fallback;
+    const float c0 = (float)b.c0, dc = (float)b.dc;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= total) return;
+        const int item = fallback[t];
+        const int m = b.item_model[item];
+        const int lo = b.model_loff[m];
+        const int nrec = b.model_loff[m + 1] - lo;
+        const int N = nrec - 1;
+        const float* lay = layers32 + (size_t)lo * LAYER_STRIDE32;
+        if (nrec <= stage_layers) {
+            for (int q = lane; q < nrec * LAYER_STRIDE32; q += 32) my[q] = lay[q];
+            __syncwarp();
+            lay = my;
+        }
+        const int start = n32[item];
+        int res = screen_paired_item(lay, N, (float)b.k[item], c0, dc, b.model_nlim[m], start,
+                                     1, lane);
+        if (lane == 0) n32[item] = res;
+        __syncwarp();
     }
 }
 
@@ -296,7 +398,7 @@ __device__ __forceinline__ void write_result(const DevBatch& b, const ScanOut& o
     }
 }
 
-__global__ void verify64_kernel(DevBatch b, ScanOut o, const int32_t* __restrict__ n32,
+__global__ void verify64_kernel(DevBatch b, ScanOut o, int32_t* __restrict__ n32,
                                 int32_t* ref_sign, int32_t* unresolved, int32_t* n_unresolved,
                                 int item_begin, int item_end) {
     // natural item order: a warp's threads share a model and have adjacent
@@ -313,7 +415,26 @@ __global__ void verify64_kernel(DevBatch b, ScanOut o, const int32_t* __restrict
         write_result(b, o, item, -1);
         return;
     }
-    const int n = n32[item];
+    int n = n32[item];
+    if (n >= 0 && (n & SCREEN_COUNTED)) {
+        // counting-search index inside the pole-free range: FP64 count 0 at
+        // V[n-1] (so 0, and the sign of V[0], at every point below it) and odd
+        // at V[n] (the sign differs) is Algorithm 1's first change
+        // (n32 keeps the flag for certified items; a re-scan needs it clear)
+        n &= ~SCREEN_COUNTED;
+        const int ia = det_inertia(lay, N, k, grid_c(b.c0, b.dc, n - 1));
+        if (ia == 0) {
+            const int ib = det_inertia(lay, N, k, grid_c(b.c0, b.dc, n));
+            if (ib > 0 && (ib & 1)) {
+                write_result(b, o, item, n);
+                return;
+            }
+        }
+        n32[item] = n;
+        ref_sign[item] = det_sign(lay, N, k, grid_c(b.c0, b.dc, 0));
+        unresolved[atomicAdd(n_unresolved, 1)] = item;
+        return;
+    }
     int s0 = det_sign(lay, N, k, grid_c(b.c0, b.dc, 0));
     bool ok;
     if (n >= 1) {
@@ -387,16 +508,26 @@ __global__ void __launch_bounds__(256) resolve64_kernel(DevBatch b, ScanOut o,
 
 cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p,
                                const float* layers32, int32_t* n32, int32_t* ref_sign,
-                               int32_t* unresolved, int32_t* counters, int item_begin,
-                               int item_end, cudaStream_t s, cudaEvent_t* phase_ev) {
+                               int32_t* unresolved, int32_t* fallback, int32_t* counters,
+                               int search, int item_begin, int item_end, cudaStream_t s,
+                               cudaEvent_t* phase_ev) {
     if (item_end <= item_begin) return cudaSuccess;
-    // counters: [0] screen queue, [1] unresolved count, [2] resolve queue
-    cudaError_t e = cudaMemsetAsync(counters, 0, 3 * sizeof(int32_t), s);
+    // counters: [0] screen queue, [1] unresolved count, [2] resolve queue,
+    // [3] fallback count, [4] fallback queue
+    cudaError_t e = cudaMemsetAsync(counters, 0, SCAN_COUNTERS * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     int wpb = p.warps_per_block;
     int blocks = p.persistent ? p.blocks : (item_end - item_begin + wpb - 1) / wpb;
     size_t shm = (size_t)wpb * p.stage_layers * LAYER_STRIDE32 * sizeof(float);
-    switch (p.cpl) {
+    int n = item_end - item_begin;
+    if (search) {
+        search32_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, layers32, n32, fallback, counters + 3,
+                                                        item_begin, item_end);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        int fblocks = std::max(1, std::min(p.blocks, (n + wpb - 1) / wpb));
+        fallback32p_kernel<<<fblocks, 32 * wpb, shm, s>>>(b, layers32, n32, fallback, counters + 3,
+                                                          counters + 4, p.stage_layers);
+    } else switch (p.cpl) {
         case 1:
             screen32_kernel<1><<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,
                                                             p.stage_layers, counters, item_begin,
@@ -417,7 +548,6 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (phase_ev && (e = cudaEventRecord(phase_ev[0], s)) != cudaSuccess) return e;
-    int n = item_end - item_begin;
     verify64_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, o, n32, ref_sign, unresolved, counters + 1,
                                                     item_begin, item_end);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -109,15 +109,24 @@ __device__ __forceinline__ float expm1_neg(float y) {
     return __expf(y) - 1.0f;
 }
 
-// Sign of det K at (k, c) in FP32. Same element stiffness as det_sign (in
-// units of the half-space shear modulus) but the plain Schur recurrence
-// S = P + K11, P' = K22 - K21 S^-1 K12 with SFU reciprocals: on the FP32
-// pipe a reciprocal is cheaper than the homogeneous bookkeeping the FP64
-// path uses to avoid divisions.
-__device__ __forceinline__ int det_sign_f(const float* __restrict__ lay, int N, float k, float c) {
+// Number of negative eigenvalues of a symmetric 2x2 block from its det and
+// first diagonal entry (a zero determinant counts as one).
+__device__ __forceinline__ int neg_eigs_2x2(float det, float s00) {
+    return det < 0.0f ? 1 : (det > 0.0f ? (s00 < 0.0f ? 2 : 0) : 1);
+}
+
+// Sign of det K at (k, c) in FP32 (MODE 0), or the number of its negative
+// eigenvalues by Sylvester's law of inertia over the 2x2 Schur pivots
+// (MODE 1). Same element stiffness as det_sign (in units of the half-space
+// shear modulus) but the plain Schur recurrence S = P + K11,
+// P' = K22 - K21 S^-1 K12 with SFU reciprocals: on the FP32 pipe a
+// reciprocal is cheaper than the homogeneous bookkeeping the FP64 path uses
+// to avoid divisions.
+template <int MODE>
+__device__ __forceinline__ int det_core_f(const float* __restrict__ lay, int N, float k, float c) {
     float c2 = c * c;
     float p00 = 0.0f, p01 = 0.0f, p11 = 0.0f;
-    int sg = 1;
+    int sg = MODE == 0 ? 1 : 0;
     for (int j = 0; j < N; ++j) {
         const float4 LA = *reinterpret_cast<const float4*>(lay + j * LAYER_STRIDE32);
         const float2 LB = *reinterpret_cast<const float2*>(lay + j * LAYER_STRIDE32 + 4);
@@ -172,7 +181,8 @@ __device__ __forceinline__ int det_sign_f(const float* __restrict__ lay, int N, 
         float ce = fr * E1, cf = fr * F1, cg = fr * G1;
         float s00 = p00 + n00, s01 = p01 + n01, s11 = p11 + n11;
         float det = fmaf(s00, s11, -s01 * s01);
-        sg *= sgnf(det);
+        if (MODE == 0) sg *= sgnf(det);
+        else sg += neg_eigs_2x2(det, s00);
         float idet = rcp_approx(det);
         // P' = K22 - K21 adj(S) K12 / det,  K12 = [[ce, cf], [-cf, cg]]
         float t00 = fmaf(s11, ce, s01 * cf);
@@ -198,7 +208,16 @@ __device__ __forceinline__ int det_sign_f(const float* __restrict__ lay, int N, 
     float s00 = fmaf(rc2g, r, p00);
     float s01 = fmaf(LA.y * iden, fmaf(g, q, -2.0f * fmaf(-p, q, p + q)), p01);
     float s11 = fmaf(rc2g, s, p11);
-    return sg * sgnf(fmaf(s00, s11, -s01 * s01));
+    float dl = fmaf(s00, s11, -s01 * s01);
+    if (MODE == 0) return sg * sgnf(dl);
+    return sg + neg_eigs_2x2(dl, s00);
+}
+
+__device__ __forceinline__ int det_sign_f(const float* __restrict__ lay, int N, float k, float c) {
+    return det_core_f<0>(lay, N, k, c);
+}
+__device__ __forceinline__ int inertia_f(const float* __restrict__ lay, int N, float k, float c) {
+    return det_core_f<1>(lay, N, k, c);
 }
 
 }  // namespace masw
@@ -412,6 +431,29 @@ __device__ __forceinline__ void det_sign_f2(const float* __restrict__ lay, int N
     }
     *sa = out[0];
     *sb = out[1];
+}
+
+// Counting search (Wittrick-Williams). With both faces of layer i clamped,
+// its energy is mu |grad u|^2 + (lambda + mu) |div u|^2 >= mu |grad u|^2
+// (lambda + mu = rho (alpha^2 - beta^2) > 0), and Poincare's inequality in
+// depth bounds |grad u|^2 >= (k^2 + (pi/h_i)^2) |u|^2; so no clamped-layer
+// mode lies below c_i = beta_i sqrt(1 + (pi / (k h_i))^2). Below
+// min_i c_i the element stiffnesses have no pole, the number of negative
+// eigenvalues of K(k, c) equals the number of modes below omega = k c, and
+// it is non-decreasing in c from 0 at c = 0 (static stiffness positive
+// definite). Returns the number of grid points V[n] < (1 - 1e-4) min_i c_i,
+// at most nlim (the margin covers the FP32 rounding of the bound).
+__device__ __forceinline__ int pole_free_points_f(const float* __restrict__ lay, int N, float k,
+                                                  float c0, float dc, int nlim) {
+    float cb2 = 3.0e38f;
+    for (int j = 0; j < N; ++j) {
+        float t = 3.14159265f / (k * lay[j * LAYER_STRIDE32 + F_H]);
+        cb2 = fminf(cb2, fmaf(t, t, 1.0f) / lay[j * LAYER_STRIDE32 + F_IB2]);
+    }
+    float x = (sqrtf(cb2) * (1.0f - 1.0e-4f) - c0) / dc;  // V[n] below the bound: n < x
+    if (!(x > 0.0f)) return 0;
+    if (x >= (float)nlim) return nlim;
+    return min((int)ceilf(x), nlim);
 }
 
 }  // namespace masw

@@ -268,6 +268,15 @@ def last_scan_unresolved(handle) -> int:
     return n.value
 
 
+def last_scan_fallback(handle) -> int:
+    f = load().masw_last_scan_fallback
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
+    f.restype = ctypes.c_int
+    n = ctypes.c_int32()
+    _check(f(ctypes.c_void_p(handle), ctypes.byref(n)), "masw_last_scan_fallback")
+    return n.value
+
+
 def fp64_peak(stream=None) -> float:
     f = ctypes.c_double()
     _check(load().masw_fp64_peak(_stream_handle(stream), ctypes.byref(f)), "masw_fp64_peak")
@@ -383,6 +392,9 @@ class Batch:
 
     def last_scan_unresolved(self) -> int:
         return last_scan_unresolved(self.handle)
+
+    def last_scan_fallback(self) -> int:
+        return last_scan_fallback(self.handle)
 
 
 # ------------------------------------------------------------ no allocation

@@ -86,7 +86,7 @@ def test_coarse_grid_with_ragged_tail(masw, oracle_lib):
     g = W.Grid(61.3, 0.77, 1013)
     o_ct, o_idx, o_st = oracle_lib.dispersion(m.as_dict(), g.c0, g.dc, g.n_c)
     with masw.Batch(m, g) as b:
-        for precision in (0, 1):
+        for precision in (0, 1, 2):
             for cpl in (1, 2, 4):
                 b.set_plan(cpl=cpl, precision=precision)
                 ct, idx, st = b.dispersion()
@@ -161,10 +161,34 @@ def test_no_root_and_empty_models(masw, oracle_lib):
     g = W.Grid(50.0, 1.0, 150)
     o_ct, o_idx, o_st = oracle_lib.dispersion(m.as_dict(), g.c0, g.dc, g.n_c)
     with masw.Batch(m, g) as b:
-        ct, idx, st = b.dispersion()
-    assert (st == o_st).all() and (idx == o_idx).all()
+        for precision in (0, 1, 2):
+            b.set_plan(precision=precision)
+            ct, idx, st = b.dispersion()
+            assert (st == o_st).all() and (idx == o_idx).all(), precision
+            assert np.isnan(ct[st == 1]).all()
     assert (o_st == 1).any() and (o_st == 0).any()
-    assert np.isnan(ct[st == 1]).all()
+
+
+def test_grid_starting_above_the_fundamental_root(masw, oracle_lib):
+    """V[0] above the fundamental mode: det K already carries one negative
+    eigenvalue there, and Algorithm 1 reports the next change (a higher
+    mode) or none; the counting search hands such items to the linear
+    screen."""
+    m = W.Models(np.array([1, 2], np.int32), np.array([6.0, 3.0, 5.0]),
+                 np.array([400.0, 1700.0, 450.0, 700.0, 1800.0]),
+                 np.array([150.0, 600.0, 170.0, 260.0, 650.0]),
+                 np.full(5, 1900.0), np.array([6, 5], np.int32),
+                 np.array([2.0, 4.0, 8.0, 12.0, 20.0, 30.0, 3.0, 6.0, 10.0, 18.0, 25.0]))
+    g = W.Grid(165.0, 0.5, 1000)
+    o_ct, o_idx, o_st = oracle_lib.dispersion(m.as_dict(), g.c0, g.dc, g.n_c)
+    with masw.Batch(m, g) as b:
+        for precision in (0, 1, 2):
+            b.set_plan(precision=precision)
+            ct, idx, st = b.dispersion()
+            assert (st == o_st).all() and (idx == o_idx).all(), precision
+        b.set_plan(precision=2)
+        b.dispersion()
+        assert b.last_scan_fallback() >= 1
 
 
 def test_max_layers_model(masw, oracle_lib):
@@ -204,20 +228,27 @@ def test_invalid_inputs_are_rejected(masw):
 
 # ------------------------------------------------------- plans and paths
 
+@pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("which", ["uniform", "ragged"])
-def test_two_precision_scan_equals_the_fp64_scan_at_full_size(masw, which):
-    """The FP32 screen only locates the change; every reported index is an
-    FP64 decision, so the two plans agree item for item."""
+def test_two_precision_scan_equals_the_fp64_scan_at_full_size(masw, which, precision):
+    """The FP32 screen (linear, or the counting search) only locates the
+    change; every reported index is an FP64 decision, so the plans agree
+    with the FP64 scan item for item."""
     m, g = W.uniform_batch() if which == "uniform" else W.ragged_batch()
     with masw.Batch(m, g) as b:
-        b.set_plan(precision=1)
+        b.set_plan(precision=precision)
         ct1, idx1, st1 = b.dispersion()
         unresolved = b.last_scan_unresolved()
+        fallback = b.last_scan_fallback()
         b.set_plan(precision=0)
         ct0, idx0, st0 = b.dispersion()
     assert np.array_equal(idx1, idx0) and np.array_equal(st1, st0)
     assert np.array_equal(ct1, ct0, equal_nan=True)
     assert 0 <= unresolved < 0.5 * m.n_items
+    if precision == 2:
+        assert 0 <= fallback < 0.5 * m.n_items
+    else:
+        assert fallback == -1
 
 
 def test_every_plan_and_the_plain_path_give_identical_indices(masw):
@@ -230,7 +261,9 @@ def test_every_plan_and_the_plain_path_give_identical_indices(masw):
         for plan in (dict(persistent=0), dict(ordered=0), dict(use_graph=0),
                      dict(stage_layers=0), dict(warps_per_block=2, blocks_per_sm=1),
                      dict(cpl=2), dict(cpl=4), dict(precision=0), dict(precision=0, cpl=2),
-                     dict(precision=1, persistent=0)):
+                     dict(precision=1, persistent=0), dict(precision=2),
+                     dict(precision=2, use_graph=0), dict(precision=2, stage_layers=0),
+                     dict(precision=2, warps_per_block=1, blocks_per_sm=1)):
             b.set_plan(**plan)
             got = b.dispersion()
             assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2]), plan
