@@ -222,7 +222,7 @@ def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, s
     e32, e64, frac_counted = counting_evals(models, grid, idx, st, nlim, n32)
     peak32 = FP32_FFMA_PER_CLK_SM * 2.0 * sms * SM_MAX_MHZ * 1e6
     common = {"bound": "alu", "unit": "TFLOP/s",
-              "phases_ms": {"search32": phases[0], "verify64": phases[1],
+              "phases_ms": {"search32": phases[0], "certify64": phases[1],
                             "resolve64": phases[2]},
               "counted_fraction": frac_counted,
               "search_layer_evals_fp32": e32, "check_layer_evals_fp64": e64,
@@ -231,14 +231,14 @@ def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, s
         achieved = e64 * F_LAYER_FLOPS / (phases[1] * 1e-3)
         common.update({"achieved": achieved / 1e12, "peak": peak64 / 1e12,
                        "frac": achieved / peak64, "traffic": None,
-                       "kernel": "verify64_kernel (FP64 pipe, certificate)",
+                       "kernel": "certify64_kernel (FP64 pipe)",
                        "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
                        "layer_evals_per_launch": e64, "flops_per_layer_eval": F_LAYER_FLOPS})
     else:
         achieved = e32 * F_LAYER_FLOPS_FP32 / (phases[0] * 1e-3)
         common.update({"achieved": achieved / 1e12, "peak": peak32 / 1e12,
                        "frac": achieved / peak32, "traffic": None,
-                       "kernel": "search32_kernel + fallback32p_kernel (FP32 pipe)",
+                       "kernel": "search32_kernel + fallback32_kernel (FP32 pipe)",
                        "peak_source": "derived: 128 FFMA/clk/SM x 2 flop x SMs x 2070 MHz",
                        "layer_evals_per_launch": e32,
                        "flops_per_layer_eval": F_LAYER_FLOPS_FP32})

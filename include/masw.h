@@ -108,7 +108,7 @@ typedef struct {
                                 (bisection on the number of negative eigenvalues of K below
                                 the pole-free bound min_i beta_i sqrt(1 + (pi/(k h_i))^2)),
                                 certified in FP64 by count 0 at V[n-1] and odd at V[n]; items
-                                outside the bound take the linear screen of 1 */
+                                outside the bound take the linear screen of 1. Default: 2 */
 } masw_plan;
 
 /* Copy and validate a model batch into batch-owned device memory and bind it

@@ -292,7 +292,7 @@ static masw_plan default_plan(const masw_batch* B) {
     p.ordered = 1;
     p.stage_layers = std::min(B->max_layers + 1, 32);
     p.use_graph = 1;
-    p.precision = 1;
+    p.precision = 2;
     return p;
 }
 

@@ -349,43 +349,6 @@ __global__ void __launch_bounds__(128) search32_kernel(DevBatch b, const float* 
     }
 }
 
-// Linear paired FP32 scan of the fallback items of search32_kernel: one warp
-// per listed item, from the start index in n32 (the points below it carry
-// count 0, i.e. a positive FP32 sign).
-__global__ void __launch_bounds__(256) fallback32p_kernel(DevBatch b, const float* __restrict__ layers32,
-                                                          int32_t* n32, const int32_t* __restrict__ fallback,
-                                                          const int32_t* __restrict__ n_fallback,
-                                                          int32_t* counter, int stage_layers) {
-    extern __shared__ float smemf[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    float* my = smemf + (size_t)wib * stage_layers * LAYER_STRIDE32;
-    const int total = *n_fallback;
-    const float c0 = (float)b.c0, dc = (float)b.dc;
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(counter, 1);
-        t = __shfl_sync(FULL, t, 0);
-        if (t >= total) return;
-        const int item = fallback[t];
-        const int m = b.item_model[item];
-        const int lo = b.model_loff[m];
-        const int nrec = b.model_loff[m + 1] - lo;
-        const int N = nrec - 1;
-        const float* lay = layers32 + (size_t)lo * LAYER_STRIDE32;
-        if (nrec <= stage_layers) {
-            for (int q = lane; q < nrec * LAYER_STRIDE32; q += 32) my[q] = lay[q];
-            __syncwarp();
-            lay = my;
-        }
-        const int start = n32[item];
-        int res = screen_paired_item(lay, N, (float)b.k[item], c0, dc, b.model_nlim[m], start,
-                                     1, lane);
-        if (lane == 0) n32[item] = res;
-        __syncwarp();
-    }
-}
-
 __device__ __forceinline__ void write_result(const DevBatch& b, const ScanOut& o, int item, int res) {
     if (res >= 0) {
         o.ct[item] = grid_c(b.c0, b.dc, res);
@@ -398,7 +361,7 @@ __device__ __forceinline__ void write_result(const DevBatch& b, const ScanOut& o
     }
 }
 
-__global__ void verify64_kernel(DevBatch b, ScanOut o, int32_t* __restrict__ n32,
+__global__ void verify64_kernel(DevBatch b, ScanOut o, const int32_t* __restrict__ n32,
                                 int32_t* ref_sign, int32_t* unresolved, int32_t* n_unresolved,
                                 int item_begin, int item_end) {
     // natural item order: a warp's threads share a model and have adjacent
@@ -415,26 +378,7 @@ __global__ void verify64_kernel(DevBatch b, ScanOut o, int32_t* __restrict__ n32
         write_result(b, o, item, -1);
         return;
     }
-    int n = n32[item];
-    if (n >= 0 && (n & SCREEN_COUNTED)) {
-        // counting-search index inside the pole-free range: FP64 count 0 at
-        // V[n-1] (so 0, and the sign of V[0], at every point below it) and odd
-        // at V[n] (the sign differs) is Algorithm 1's first change
-        // (n32 keeps the flag for certified items; a re-scan needs it clear)
-        n &= ~SCREEN_COUNTED;
-        const int ia = det_inertia(lay, N, k, grid_c(b.c0, b.dc, n - 1));
-        if (ia == 0) {
-            const int ib = det_inertia(lay, N, k, grid_c(b.c0, b.dc, n));
-            if (ib > 0 && (ib & 1)) {
-                write_result(b, o, item, n);
-                return;
-            }
-        }
-        n32[item] = n;
-        ref_sign[item] = det_sign(lay, N, k, grid_c(b.c0, b.dc, 0));
-        unresolved[atomicAdd(n_unresolved, 1)] = item;
-        return;
-    }
+    const int n = n32[item];
     int s0 = det_sign(lay, N, k, grid_c(b.c0, b.dc, 0));
     bool ok;
     if (n >= 1) {
@@ -448,6 +392,186 @@ __global__ void verify64_kernel(DevBatch b, ScanOut o, int32_t* __restrict__ n32
     if (ok) {
         write_result(b, o, item, n >= 1 ? n : -1);
     } else {
+        ref_sign[item] = s0;
+        unresolved[atomicAdd(n_unresolved, 1)] = item;
+    }
+}
+
+// Linear paired FP32 scan of the fallback items of search32_kernel, one
+// block per listed item (few items, each a long walk: the block's warps take
+// consecutive 64-point sub-chunks, 64 x warps points per round), from the
+// start index in n32 (the points below it carry count 0, i.e. a positive
+// FP32 sign). The first change of a round is the smallest index any warp
+// found; warp w's first point compares with warp w-1's last.
+__global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float* __restrict__ layers32,
+                                                         int32_t* n32, const int32_t* __restrict__ fallback,
+                                                         const int32_t* __restrict__ n_fallback,
+                                                         int32_t* counter, int stage_layers) {
+    extern __shared__ float smemf[];
+    __shared__ int s_item, s_res, s_last[32];
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int total = *n_fallback;
+    const float c0 = (float)b.c0, dc = (float)b.dc;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(counter, 1);
+            s_res = 0x7fffffff;
+        }
+        __syncthreads();
+        const int t = s_item;
+        if (t >= total) return;
+        const int item = fallback[t];
+        const int m = b.item_model[item];
+        const int lo = b.model_loff[m];
+        const int nrec = b.model_loff[m + 1] - lo;
+        const int N = nrec - 1;
+        const float* lay = layers32 + (size_t)lo * LAYER_STRIDE32;
+        if (nrec <= stage_layers) {
+            for (int q = threadIdx.x; q < nrec * LAYER_STRIDE32; q += blockDim.x) smemf[q] = lay[q];
+            __syncthreads();
+            lay = smemf;
+        }
+        const float k = (float)b.k[item];
+        const int nlim = b.model_nlim[m];
+        int carry = 1, res = -1;
+        for (int base = n32[item]; base < nlim; base += 64 * nw) {
+            const int n0 = base + 64 * w + 2 * lane, n1 = n0 + 1;
+            int s0 = 0, s1 = 0;
+            if (n1 < nlim) {
+                det_sign_f2(lay, N, k, fmaf((float)n0, dc, c0), fmaf((float)n1, dc, c0), &s0, &s1);
+            } else if (n0 < nlim) {
+                s0 = det_sign_f(lay, N, k, fmaf((float)n0, dc, c0));
+            }
+            const int last = __shfl_sync(FULL, s1, 31);
+            if (lane == 0) s_last[w] = last;
+            __syncthreads();
+            int prev = __shfl_up_sync(FULL, s1, 1);
+            if (lane == 0) prev = (w == 0) ? carry : s_last[w - 1];
+            const unsigned m0 = __ballot_sync(FULL, n0 >= 1 && n0 < nlim && s0 != prev);
+            const unsigned m1 = __ballot_sync(FULL, n1 < nlim && s1 != s0);
+            const unsigned mm = m0 | m1;
+            if (mm && lane == 0) {
+                const int l = __ffs(mm) - 1;
+                atomicMin(&s_res, base + 64 * w + 2 * l + (((m0 >> l) & 1u) ? 0 : 1));
+            }
+            __syncthreads();
+            const int r = s_res;
+            carry = s_last[nw - 1];
+            __syncthreads();
+            if (r != 0x7fffffff) {
+                res = r;
+                break;
+            }
+        }
+        if (threadIdx.x == 0) n32[item] = res;
+        __syncthreads();
+    }
+}
+
+// FP64 decision of a counting-search scan, two lanes per item (natural item
+// order, so a warp's lanes share a model and take the same FP64 branches):
+// for an index n located by the search, lane 2i counts the negative
+// eigenvalues of K at V[n-1] and lane 2i+1 at V[n]; count 0 below (so 0, and
+// V[0]'s sign, at every point below, the count being monotone in the
+// pole-free range) and odd at n (the sign differs) is Algorithm 1's first
+// change. Items the linear fallback located get the sign check of
+// verify64_kernel (V[0], V[n-1], V[n]; V[0] and the last point when it saw
+// no change). When the FP32 count was off by one next to the change (count
+// 0 at both points: the change is higher; nonzero at V[n-1]: lower), the
+// pair takes one FP64 step of two points in that direction, staying inside
+// the pole-free range. Failures go to the FP64 re-scan with V[0]'s sign;
+// n32 keeps the SCREEN_COUNTED flag on certified items.
+__global__ void __launch_bounds__(128) certify64_kernel(DevBatch b, const float* __restrict__ layers32,
+                                                        ScanOut o, int32_t* __restrict__ n32,
+                                                        int32_t* ref_sign, int32_t* unresolved,
+                                                        int32_t* n_unresolved, int item_begin,
+                                                        int item_end) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int item = item_begin + (t >> 1);
+    const int half = t & 1;
+    int kind = 0, n = -1, nlim = 0, N = 0;
+    const double* lay = nullptr;
+    double k = 0.0;
+    if (item < item_end) {
+        const int m = b.item_model[item];
+        const int lo = b.model_loff[m];
+        N = b.model_loff[m + 1] - lo - 1;
+        lay = b.layers + (size_t)lo * LAYER_STRIDE;
+        k = b.k[item];
+        nlim = b.model_nlim[m];
+        n = n32[item];
+        if (nlim < 2) kind = 4;                            // nothing to scan
+        else if (n >= 0 && (n & SCREEN_COUNTED)) kind = 1; // counting search
+        else if (n >= 1) kind = 2;                         // linear fallback, change
+        else kind = 3;                                     // linear fallback, none
+        n &= ~SCREEN_COUNTED;
+    }
+    int v = 0;
+    if (kind == 1) v = det_inertia(lay, N, k, grid_c(b.c0, b.dc, n - 1 + half));
+    else if (kind == 2) v = det_sign(lay, N, k, grid_c(b.c0, b.dc, n - 1 + half));
+    else if (kind == 3) v = det_sign(lay, N, k, grid_c(b.c0, b.dc, half ? nlim - 1 : 0));
+    const int vo = __shfl_xor_sync(FULL, v, 1);
+    if (item >= item_end) return;
+    const int va = half ? vo : v;  // lower point
+    const int vb = half ? v : vo;  // upper point
+    int walked = -1;
+    if (kind == 1 && !(va == 0 && vb > 0 && (vb & 1)) && va >= 0 && vb >= 0) {
+        // both lanes of the pair take this branch (same item, same counts)
+        const bool up = va == 0 && vb == 0;
+        const bool down = va > 0 && n >= 3;
+        if (up || down) {
+            const int p0 = up ? n + 1 : n - 3;
+            const int nlim_pf = up ? pole_free_points_f(layers32 + (size_t)b.model_loff[b.item_model[item]] *
+                                                            LAYER_STRIDE32,
+                                                        N, (float)k, (float)b.c0, (float)b.dc, nlim)
+                                   : nlim;
+            const int pt = p0 + half;
+            const int w = pt < nlim ? det_inertia(lay, N, k, grid_c(b.c0, b.dc, pt)) : -1;
+            const int wo = __shfl_xor_sync(3u << ((threadIdx.x & 31) & 30), w, 1);
+            const int c_lo = half ? wo : w, c_hi = half ? w : wo;
+            if (up) {
+                // counts 0 at n; first nonzero at n+1 or n+2 (n+1 inside the range)
+                if (c_lo > 0) {
+                    if (c_lo & 1) walked = n + 1;
+                } else if (c_lo == 0 && c_hi > 0 && (c_hi & 1) && n + 1 < nlim_pf) {
+                    walked = n + 2;
+                }
+            } else {
+                // count nonzero at n-1; first nonzero at n-1 or n-2
+                if (c_hi == 0) {
+                    if (va & 1) walked = n - 1;
+                } else if (c_hi > 0 && c_lo == 0 && (c_hi & 1)) {
+                    walked = n - 2;
+                }
+            }
+        }
+    }
+    if (half) return;
+    bool ok;
+    int s0 = 0;
+    if (kind == 4) {
+        write_result(b, o, item, -1);
+        return;
+    } else if (kind == 1) {
+        ok = va == 0 && vb > 0 && (vb & 1);
+        if (!ok && walked >= 1) {
+            n = walked;
+            ok = true;
+        }
+        if (!ok) s0 = det_sign(lay, N, k, grid_c(b.c0, b.dc, 0));
+    } else if (kind == 2) {
+        s0 = (n == 1) ? va : det_sign(lay, N, k, grid_c(b.c0, b.dc, 0));
+        ok = va == s0 && vb != va;
+    } else {
+        s0 = va;
+        ok = vb == va;
+    }
+    if (ok) {
+        write_result(b, o, item, kind == 3 ? -1 : n);
+    } else {
+        n32[item] = kind == 3 ? -1 : n;
         ref_sign[item] = s0;
         unresolved[atomicAdd(n_unresolved, 1)] = item;
     }
@@ -524,9 +648,9 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
         search32_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, layers32, n32, fallback, counters + 3,
                                                         item_begin, item_end);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        int fblocks = std::max(1, std::min(p.blocks, (n + wpb - 1) / wpb));
-        fallback32p_kernel<<<fblocks, 32 * wpb, shm, s>>>(b, layers32, n32, fallback, counters + 3,
-                                                          counters + 4, p.stage_layers);
+        fallback32_kernel<<<std::max(1, std::min(p.blocks, n)), 256,
+                            (size_t)p.stage_layers * LAYER_STRIDE32 * sizeof(float), s>>>(
+            b, layers32, n32, fallback, counters + 3, counters + 4, p.stage_layers);
     } else switch (p.cpl) {
         case 1:
             screen32_kernel<1><<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,
@@ -548,8 +672,13 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (phase_ev && (e = cudaEventRecord(phase_ev[0], s)) != cudaSuccess) return e;
-    verify64_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, o, n32, ref_sign, unresolved, counters + 1,
-                                                    item_begin, item_end);
+    if (search)
+        certify64_kernel<<<(2 * n + 127) / 128, 128, 0, s>>>(b, layers32, o, n32, ref_sign,
+                                                             unresolved, counters + 1, item_begin,
+                                                             item_end);
+    else
+        verify64_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, o, n32, ref_sign, unresolved,
+                                                        counters + 1, item_begin, item_end);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (phase_ev && (e = cudaEventRecord(phase_ev[1], s)) != cudaSuccess) return e;
     int rblocks = std::max(1, std::min(p.blocks, (n + wpb - 1) / wpb));
