@@ -56,6 +56,9 @@ FP32_FFMA_PER_CLK_SM = 128.0
 # the maximum SM clock.
 FP64_DFMA_PER_CLK_SM = 2.0
 SM_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) of one certify64 launch per model (ncu, 128-model
+# case: 585.0 KB read, 0 written), scaled by the models of a launch.
+CERTIFY_DRAM_BYTES_PER_MODEL = 584.96e3 / 128
 # DRAM bytes (read + write) of one scan launch per model, from the ncu capture
 # of the 64-model case (281.6 KB read, 0 written), scaled by the models of a
 # launch; traffic grows with the number of items.
@@ -230,7 +233,8 @@ def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, s
     if phases[1] >= phases[0]:
         achieved = e64 * F_LAYER_FLOPS / (phases[1] * 1e-3)
         common.update({"achieved": achieved / 1e12, "peak": peak64 / 1e12,
-                       "frac": achieved / peak64, "traffic": None,
+                       "frac": achieved / peak64,
+                       "traffic": CERTIFY_DRAM_BYTES_PER_MODEL * models.n_models,
                        "kernel": "certify64_kernel (FP64 pipe)",
                        "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
                        "layer_evals_per_launch": e64, "flops_per_layer_eval": F_LAYER_FLOPS})
