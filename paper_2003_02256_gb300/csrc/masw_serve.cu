@@ -8,14 +8,15 @@
 //  * each admitted request owns a slot: its layer records, wavenumbers, scan
 //    state and results stay resident until the request is polled;
 //  * admission needs a free slot and room under the byte cap;
-//  * every tick launches one kernel that advances every active item (one
-//    (request, wavelength) pair) by at most `chunks_per_tick` 32-point chunks
-//    of Algorithm 1's scan and compacts the items still running; requests
-//    admitted between ticks join the next tick, so their work overlaps with
-//    the requests already in flight;
-//  * an item's chunks are exactly those of the batch scan (32 consecutive
-//    grid points from V[0], sign carried across chunks), so a result does not
-//    depend on what else is in flight.
+//  * every tick runs the counting search over the items (one (request,
+//    wavelength) pair each) admitted since the last tick, advances every
+//    item still scanning linearly by at most `chunks_per_tick` chunks of
+//    Algorithm 1's scan, checks in FP64 what the two located, and compacts
+//    the items still running; requests admitted between ticks join the next
+//    tick, so their work overlaps with the requests already in flight;
+//  * an item's evaluations are exactly those of the batch path (the same
+//    search, the same chunks from the same start, sign carried across
+//    chunks), so a result does not depend on what else is in flight.
 // There are no device-side waits: the host waits for each tick on an event.
 //
 // Slot layout (one pinned host staging region and one device region per
@@ -23,11 +24,15 @@
 //   [meta: 4 x i32 (nrec, nlim, n_lambda, 0)] [records: rmax x 8 f64]
 //   [FP32 records: rmax x 8 f32] [k: imax f64]
 //   [scan state: imax x (base, carry, phase, ref) i32]
-// Each item runs the two-precision scan of the batch path: paired FP32
-// chunks locate the first sign change; a thread-per-item FP64 check at V[0],
-// V[n-1], V[n] (a second kernel of the same tick) decides it; when the check
-// does not confirm, the item continues with FP64 chunks from V[0], one per
-// tick.
+// Each item runs the default scan of the batch path: in the tick after its
+// admission, a thread-per-item counting search (the FP32 negative-eigenvalue
+// count bisected below the pole-free bound) locates the first sign change,
+// and the tick's FP64 check (count 0 at V[n-1], odd at V[n]) decides it, so
+// most requests finish in one tick. Items whose change lies above the bound
+// continue with paired FP32 chunks from the bound, up to `chunks_per_tick`
+// per tick, and get the FP64 sign check at V[0], V[n-1], V[n]; when a check
+// does not confirm, the item continues with FP64 chunks, one per tick, from a
+// window below the located index (or from V[0]).
 // Results are written by the kernel into mapped pinned host memory, so
 // retiring a request is a host memcpy.
 #include <algorithm>
@@ -78,6 +83,64 @@ __device__ __forceinline__ int32_t* slot_state(const SlotView& v, int s) {
 }
 
 enum { PH_SCREEN = 0, PH_FP64 = 1, PH_FP64_WINDOW = 2 };
+
+// Tick, part 0 (one thread per item admitted since the last tick): the
+// counting search of the batch path (search32_kernel). A located index goes
+// to the check list flagged SCREEN_COUNTED; otherwise the item enters the
+// linear FP32 screen at the next tick, from the end of the pole-free range
+// (carrying the positive sign of count 0) or from V[0].
+__global__ void __launch_bounds__(128) serve_search_kernel(SlotView v, const int32_t* __restrict__ items,
+                                                           int n_items, int32_t* active_out,
+                                                           int32_t* check_list, double c0, double dc) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_items) return;
+    const int item = items[t];
+    const int slot = item / v.imax;
+    const int j = item - slot * v.imax;
+    const int32_t* meta = slot_meta(v, slot);
+    const int N = meta[0] - 1;
+    const int nlim = meta[1];
+    int32_t* stt = slot_state(v, slot) + 4 * j;
+    if (nlim < 2) {
+        stt[3] = -2;
+        check_list[atomicAdd(&v.counters[2], 1)] = item;
+        return;
+    }
+    const float* lay = slot_records32(v, slot);
+    const float k = (float)slot_k(v, slot)[j];
+    const float c0f = (float)c0, dcf = (float)dc;
+    const int npf = pole_free_points_f(lay, N, k, c0f, dcf, nlim);
+    int start = 0, res = -1;
+    if (npf >= 1) {
+        int hi = npf - 1;
+        int chi = inertia_f(lay, N, k, fmaf((float)hi, dcf, c0f));
+        if (chi == 0) {
+            start = npf;
+        } else {
+            int lo = -1;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                const int cm = inertia_f(lay, N, k, fmaf((float)mid, dcf, c0f));
+                if (cm >= 1) {
+                    hi = mid;
+                    chi = cm;
+                } else {
+                    lo = mid;
+                }
+            }
+            if (hi >= 1 && (chi & 1)) res = hi;
+        }
+    }
+    if (res >= 1) {
+        stt[3] = res | SCREEN_COUNTED;
+        check_list[atomicAdd(&v.counters[2], 1)] = item;
+    } else {
+        stt[0] = start;
+        stt[1] = start > 0 ? 1 : 0;
+        stt[2] = PH_SCREEN;
+        active_out[atomicAdd(&v.counters[0], 1)] = item;
+    }
+}
 
 // Tick, part 1 (one warp per active item). PH_SCREEN: up to `chunks` paired
 // FP32 chunks (64 test velocities each); when the screen sees a change (or
@@ -189,9 +252,11 @@ __global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
     }
 }
 
-// Tick, part 2 (one thread per item on the check list): FP64 signs at V[0],
-// V[n32-1], V[n32] (or V[0] and the last scanned point) accept the screen's
-// index; otherwise the item continues with the FP64 scan from V[0].
+// Tick, part 2 (one thread per item on the check list): an index of the
+// counting search is accepted when the FP64 count is 0 at V[n-1] and odd at
+// V[n]; a linear screen's index when the FP64 signs at V[0], V[n-1], V[n]
+// (or V[0] and the last scanned point) agree with it; otherwise the item
+// continues with the FP64 scan.
 __global__ void serve_check_kernel(SlotView v, const int32_t* __restrict__ check_list,
                                    const int32_t* __restrict__ n_check, int32_t* active_out,
                                    double c0, double dc) {
@@ -206,11 +271,20 @@ __global__ void serve_check_kernel(SlotView v, const int32_t* __restrict__ check
     const double* lay = slot_records(v, slot);
     const double k = slot_k(v, slot)[j];
     int32_t* stt = slot_state(v, slot) + 4 * j;
-    const int n = stt[3];
+    int n = stt[3];
     int res = -1;
     bool ok;
     if (nlim < 2) {
         ok = true;
+    } else if (n >= 0 && (n & SCREEN_COUNTED)) {
+        n &= ~SCREEN_COUNTED;
+        const int ia = det_inertia(lay, N, k, grid_c(c0, dc, n - 1));
+        ok = ia == 0;
+        if (ok) {
+            const int ib = det_inertia(lay, N, k, grid_c(c0, dc, n));
+            ok = ib > 0 && (ib & 1);
+        }
+        res = n;
     } else {
         int s0 = det_sign(lay, N, k, grid_c(c0, dc, 0));
         if (n >= 1) {
@@ -277,6 +351,7 @@ struct masw_server {
     int32_t* h_status = nullptr;
     int32_t* active[2] = {nullptr, nullptr};
     int32_t* check = nullptr;
+    int32_t* new_items = nullptr;  // device copy of the items admitted since the last tick
     int32_t* h_new_items = nullptr;
     int32_t* h_counters = nullptr;
     int32_t* h_done = nullptr;
@@ -301,7 +376,7 @@ namespace {
 void server_free(masw_server* S) {
     if (!S) return;
     void* dev[] = {S->v.region, S->v.remaining, S->v.done, S->v.counters, S->active[0],
-                   S->active[1], S->check};
+                   S->active[1], S->check, S->new_items};
     for (void* p : dev)
         if (p) cudaFree(p);
     void* host[] = {S->h_region, S->h_ct, S->h_idx, S->h_status, S->h_new_items, S->h_counters,
@@ -333,25 +408,31 @@ int run_tick_impl(masw_server* S) {
     int n_new = (int)S->pending.size();
     if (n_new) {
         std::memcpy(S->h_new_items, S->pending.data(), n_new * sizeof(int32_t));
-        if (cudaMemcpyAsync(S->active[S->cur] + S->n_active, S->h_new_items, n_new * sizeof(int32_t),
+        if (cudaMemcpyAsync(S->new_items, S->h_new_items, n_new * sizeof(int32_t),
                             cudaMemcpyHostToDevice, S->stream) != cudaSuccess)
             return MASW_ECUDA;
-        S->n_active += n_new;
         S->pending.clear();
     }
-    if (S->n_active == 0) return MASW_OK;
+    if (S->n_active + n_new == 0) return MASW_OK;
     if (cudaMemsetAsync(S->v.counters, 0, 3 * sizeof(int32_t), S->stream) != cudaSuccess)
         return MASW_ECUDA;
-    int wpb = S->cfg.warps_per_block;
-    int blocks = (S->n_active + wpb - 1) / wpb;
-    size_t shm = (size_t)wpb * S->v.rmax * LAYER_STRIDE32 * sizeof(float);
-    serve_tick_kernel<<<blocks, 32 * wpb, shm, S->stream>>>(S->v, S->active[S->cur], S->n_active,
-                                                            S->active[1 - S->cur], S->check,
-                                                            S->cfg.chunks_per_tick, S->grid.c0,
-                                                            S->grid.dc);
-    if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
-    // every item that entered the check list this tick (at most n_active)
-    serve_check_kernel<<<(S->n_active + 127) / 128, 128, 0, S->stream>>>(
+    if (n_new) {
+        serve_search_kernel<<<(n_new + 127) / 128, 128, 0, S->stream>>>(
+            S->v, S->new_items, n_new, S->active[1 - S->cur], S->check, S->grid.c0, S->grid.dc);
+        if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
+    }
+    if (S->n_active) {
+        int wpb = S->cfg.warps_per_block;
+        int blocks = (S->n_active + wpb - 1) / wpb;
+        size_t shm = (size_t)wpb * S->v.rmax * LAYER_STRIDE32 * sizeof(float);
+        serve_tick_kernel<<<blocks, 32 * wpb, shm, S->stream>>>(S->v, S->active[S->cur], S->n_active,
+                                                                S->active[1 - S->cur], S->check,
+                                                                S->cfg.chunks_per_tick, S->grid.c0,
+                                                                S->grid.dc);
+        if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
+    }
+    // every item that entered the check list this tick (at most n_active + n_new)
+    serve_check_kernel<<<(S->n_active + n_new + 127) / 128, 128, 0, S->stream>>>(
         S->v, S->check, S->v.counters + 2, S->active[1 - S->cur], S->grid.c0, S->grid.dc);
     if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
     if (cudaMemcpyAsync(S->h_counters, S->v.counters, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost,
@@ -427,7 +508,7 @@ int masw_server_create(const masw_grid* grid, const masw_server_config* cfg, voi
     bool ok = dalloc(&S->v.region, slots * S->v.stride) && dalloc(&S->v.remaining, slots) &&
               dalloc(&S->v.done, slots) && dalloc(&S->v.counters, 3) &&
               dalloc(&S->active[0], items) && dalloc(&S->active[1], items) &&
-              dalloc(&S->check, items) &&
+              dalloc(&S->check, items) && dalloc(&S->new_items, items) &&
               halloc(&S->h_region, slots * S->v.stride) &&
               halloc(&S->h_ct, items, cudaHostAllocMapped) &&
               halloc(&S->h_idx, items, cudaHostAllocMapped) &&

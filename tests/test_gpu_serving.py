@@ -115,3 +115,38 @@ def test_plain_per_request_mode_matches(env):
     assert sp["max_in_flight"] == 1
     s = serving.latency_summary(la, arr, reqs.n_models)
     assert s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_fallback_items_match_the_batch_path(env):
+    """Items whose change lies above the pole-free bound or below V[0] leave
+    the counting search for the linear screen; served results still equal
+    the batch entry point's, with the linear plan and the FP64 plan."""
+    masw, serving = env
+    m = W.Models(np.array([1, 2], np.int32), np.array([6.0, 3.0, 5.0]),
+                 np.array([400.0, 1700.0, 450.0, 700.0, 1800.0]),
+                 np.array([150.0, 600.0, 170.0, 260.0, 650.0]),
+                 np.full(5, 1900.0), np.array([6, 5], np.int32),
+                 np.array([2.0, 4.0, 8.0, 12.0, 20.0, 30.0, 3.0, 6.0, 10.0, 18.0, 25.0]))
+    grid = W.Grid(165.0, 0.5, 1000)
+    with masw.Batch(m, grid) as b:
+        ref = b.dispersion()
+        b.set_plan(precision=0)
+        ref0 = b.dispersion()
+        b.set_plan(precision=2)
+        b.dispersion()
+        assert b.last_scan_fallback() >= 1
+    assert np.array_equal(ref[1], ref0[1]) and np.array_equal(ref[2], ref0[2])
+    hoff, loff, woff = m.layer_offsets()
+    with serving.Server(grid, max_slots=4, chunks_per_tick=1) as srv:
+        ids = [srv.submit(*m.model(q)) for q in range(m.n_models)]
+        outs = [None] * m.n_models
+        for _ in range(200):
+            srv.tick()
+            for q in range(m.n_models):
+                if outs[q] is None:
+                    outs[q] = srv.poll(ids[q], int(m.n_lambda[q]))
+            if all(o is not None for o in outs):
+                break
+    for q in range(m.n_models):
+        sl = slice(woff[q], woff[q + 1])
+        assert np.array_equal(outs[q][1], ref[1][sl]) and np.array_equal(outs[q][2], ref[2][sl])
