@@ -333,7 +333,7 @@ def run_extras(args, masw, torch):
     reqs = W.concat([sampler.next() for _ in range(args.serving_requests)])
     grid = W.Grid(50.0, 0.25, 4601)
     rates = {}
-    for rate in (1e3, 1e4, 1e5):
+    for rate in (1e3, 1e4, 1e5, 1e6):
         arr = W.poisson_arrivals(reqs.n_models, rate=rate)
         with serving.Server(grid, max_slots=2048, chunks_per_tick=8,
                             mem_cap_bytes=16 << 30) as srv:
