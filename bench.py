@@ -189,64 +189,60 @@ def executed_layer_evals(models, idx, st, nlim, cpl):
 
 
 def counting_evals(models, grid, idx, st, nlim, n32):
-    """Per-item evaluations of the counting-search scan (plan precision 2):
-    FP32 layer evaluations of the search (1 + ceil(log2 npf) inertia counts
-    for a located item, npf = grid points below the pole-free bound
-    min_i beta_i sqrt(1 + (pi/(k h_i))^2)) and of the linear fallback (points
-    from its start up to the change), and FP64 layer evaluations of the
-    check (2 for a certified item, V[0], V[n-1], V[n] otherwise)."""
+    """Per-item evaluations of the counting-search scan (plan precision 2).
+    FP32 layer evaluations of the search: 1 + ceil(log3 npf) steps of two
+    inertia counts for a located item, npf = grid points below the pole-free
+    bound min_i beta_i sqrt(1 + (pi/(k h_i))^2). FP64 layer evaluations of
+    the certificate: 2 per counted item. Fallback items: the linear FP32
+    scan from its start up to the change, and the three-point FP64 check."""
     counted = (n32 >= 0) & ((n32 & (1 << 30)) != 0)
-    hoff, loff, _ = models.layer_offsets()
     item_model = np.repeat(np.arange(models.n_models), models.n_lambda)
     nl = (models.n_layers.astype(np.int64) + 1)[item_model]
     k = 2.0 * np.pi / models.lam
     cb = np.full(models.n_items, np.inf)
+    woff = np.concatenate([[0], np.cumsum(models.n_lambda)])
     for m in range(models.n_models):
         h, _, b, _, _ = models.model(m)
-        sl = slice(int(np.sum(models.n_lambda[:m])), int(np.sum(models.n_lambda[:m + 1])))
+        sl = slice(int(woff[m]), int(woff[m + 1]))
         kk = k[sl][:, None]
         cb[sl] = np.min(b[None, :-1] * np.sqrt(1.0 + (np.pi / (kk * h[None, :])) ** 2), axis=1)
     lim = nlim[item_model].astype(np.int64)
     npf = np.clip(np.ceil((cb * (1.0 - 1e-4) - grid.c0) / grid.dc), 0, lim).astype(np.int64)
-    search = np.where(npf >= 1, 1 + np.ceil(np.log2(np.maximum(npf, 1))), 0)
+    steps = np.where(npf >= 2, 1 + np.ceil(np.log(np.maximum(npf, 2)) / np.log(3.0)), 1)
+    search = np.where(npf >= 1, 2 * steps, 0)
     root = np.where(st == 0, idx.astype(np.int64), lim - 1)
     start = np.where(root >= npf, npf, 0)
     linear = np.where(counted, 0, np.maximum(root - start + 1, 0))
-    fp64 = np.where(counted, 2, np.where(st == 0, 3, 2))
-    fp64 = np.where(lim >= 2, fp64, 0)
-    return (int(np.sum((search + linear) * nl)), int(np.sum(fp64 * nl)),
-            float(np.mean(counted)))
+    live = lim >= 2
+    e32 = int(np.sum(np.where(live, search + linear, 0) * nl))
+    e64_counted = int(np.sum(np.where(live & counted, 2, 0) * nl))
+    e64_fallback = int(np.sum(np.where(live & ~counted, 3, 0) * nl))
+    return e32, e64_counted, e64_fallback, float(np.mean(counted))
 
 
 def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, sms):
-    """Roofline of the dominant kernel of a counting-search scan: the FP32
-    search (+ fallback) against the FP32 pipe or the FP64 check against the
-    FP64 pipe, both from algorithmic layer evaluations / device time."""
-    e32, e64, frac_counted = counting_evals(models, grid, idx, st, nlim, n32)
+    """Roofline of the dominant kernel of a counting-search scan, the fused
+    search + FP64 certificate: its FP64 work (2 layer-evaluation chains per
+    counted item) against the FP64 pipe, from algorithmic layer evaluations /
+    device time. Its FP32 search work runs on the FP32 pipe beside it and is
+    reported separately."""
+    e32, e64, e64_fb, frac_counted = counting_evals(models, grid, idx, st, nlim, n32)
     peak32 = FP32_FFMA_PER_CLK_SM * 2.0 * sms * SM_MAX_MHZ * 1e6
-    common = {"bound": "alu", "unit": "TFLOP/s",
-              "phases_ms": {"search32": phases[0], "certify64": phases[1],
-                            "resolve64": phases[2]},
-              "counted_fraction": frac_counted,
-              "search_layer_evals_fp32": e32, "check_layer_evals_fp64": e64,
-              "fp64_peak_microbenchmark": micro / 1e12}
-    if phases[1] >= phases[0]:
-        achieved = e64 * F_LAYER_FLOPS / (phases[1] * 1e-3)
-        common.update({"achieved": achieved / 1e12, "peak": peak64 / 1e12,
-                       "frac": achieved / peak64,
-                       "traffic": CERTIFY_DRAM_BYTES_PER_MODEL * models.n_models,
-                       "kernel": "certify64_kernel (FP64 pipe)",
-                       "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
-                       "layer_evals_per_launch": e64, "flops_per_layer_eval": F_LAYER_FLOPS})
-    else:
-        achieved = e32 * F_LAYER_FLOPS_FP32 / (phases[0] * 1e-3)
-        common.update({"achieved": achieved / 1e12, "peak": peak32 / 1e12,
-                       "frac": achieved / peak32, "traffic": None,
-                       "kernel": "search32_kernel + fallback32_kernel (FP32 pipe)",
-                       "peak_source": "derived: 128 FFMA/clk/SM x 2 flop x SMs x 2070 MHz",
-                       "layer_evals_per_launch": e32,
-                       "flops_per_layer_eval": F_LAYER_FLOPS_FP32})
-    return common
+    t0 = phases[0] * 1e-3
+    achieved = e64 * F_LAYER_FLOPS / t0
+    return {"bound": "alu", "unit": "TFLOP/s",
+            "achieved": achieved / 1e12, "peak": peak64 / 1e12, "frac": achieved / peak64,
+            "traffic": CERTIFY_DRAM_BYTES_PER_MODEL * models.n_models,
+            "kernel": "count_certify_kernel (FP64 pipe; FP32 search alongside)",
+            "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
+            "layer_evals_per_launch": e64, "flops_per_layer_eval": F_LAYER_FLOPS,
+            "search_layer_evals_fp32": e32,
+            "search_fp32_frac_of_fp32_peak": e32 * F_LAYER_FLOPS_FP32 / t0 / peak32,
+            "fallback_check_layer_evals_fp64": e64_fb,
+            "phases_ms": {"count_certify": phases[0], "fallback": phases[1],
+                          "resolve64": phases[2]},
+            "counted_fraction": frac_counted,
+            "fp64_peak_microbenchmark": micro / 1e12}
 
 
 def run_extras(args, masw, torch):

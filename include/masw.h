@@ -200,10 +200,13 @@ int masw_autotune(masw_batch* batch, int32_t reps, masw_plan* best);
  * masw_dispersion_plain (CUDA events on the batch stream). */
 int masw_last_scan_ms(const masw_batch* batch, float* ms);
 
-/* Device time (ms) of the three kernels of the most recent two-precision
- * scan launched without a graph (plan use_graph 0): ms[0] FP32 screen, ms[1]
- * FP64 check, ms[2] FP64 re-scan (CUDA events between the launches on the
- * batch stream). MASW_EINVAL when that scan was graph-replayed. */
+/* Device time (ms) of the three phases of the most recent two-precision
+ * scan launched without a graph (plan use_graph 0), from CUDA events between
+ * the launches on the batch stream. Plan precision 1: ms[0] FP32 screen,
+ * ms[1] FP64 check, ms[2] FP64 re-scan. Plan precision 2: ms[0] counting
+ * search with its FP64 certificate (one fused kernel), ms[1] linear scan and
+ * FP64 check of the fallback items, ms[2] FP64 re-scan. MASW_EINVAL when that
+ * scan was graph-replayed. */
 int masw_last_scan_phases(const masw_batch* batch, float* ms);
 
 /* The FP32 screen's first-change index per item (item order, -1 when the

@@ -291,64 +291,6 @@ __global__ void __launch_bounds__(256) screen32p_kernel(DevBatch b, const float*
     }
 }
 
-// Counting search: one thread per item (natural item order, so a warp's
-// threads share a model and have adjacent wavelengths). Inside the pole-free
-// range [0, npf) of pole_free_points_f the FP32 negative-eigenvalue count
-// (inertia_f) is a non-decreasing step function of the grid index that is 0
-// at c = 0, so the first index with a nonzero count is found by bisection in
-// ceil(log2(npf + 1)) evaluations instead of a linear walk. An odd count
-// there is Algorithm 1's first sign change; the index is stored with
-// SCREEN_COUNTED for the FP64 certificate of verify64_kernel. Items whose change
-// lies above the range (count 0 at its last point), at V[0], or where the
-// count jumps by an even number, go to the fallback list for the linear
-// FP32 scan, with the grid index to start from in n32.
-__global__ void __launch_bounds__(128) search32_kernel(DevBatch b, const float* __restrict__ layers32,
-                                                       int32_t* n32out, int32_t* fallback,
-                                                       int32_t* n_fallback, int item_begin,
-                                                       int item_end) {
-    const int item = item_begin + blockIdx.x * blockDim.x + threadIdx.x;
-    if (item >= item_end) return;
-    const int m = b.item_model[item];
-    const int lo_rec = b.model_loff[m];
-    const int N = b.model_loff[m + 1] - lo_rec - 1;
-    const float* lay = layers32 + (size_t)lo_rec * LAYER_STRIDE32;
-    const int nlim = b.model_nlim[m];
-    if (nlim < 2) {
-        n32out[item] = -1;
-        return;
-    }
-    const float k = (float)b.k[item];
-    const float c0 = (float)b.c0, dc = (float)b.dc;
-    const int npf = pole_free_points_f(lay, N, k, c0, dc, nlim);
-    int start = 0, res = -1;
-    if (npf >= 1) {
-        int hi = npf - 1;
-        int chi = inertia_f(lay, N, k, fmaf((float)hi, dc, c0));
-        if (chi == 0) {
-            start = npf;  // no mode below the bound: scan linearly above it
-        } else {
-            int lo = -1;  // count 0 at c = 0
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                const int cm = inertia_f(lay, N, k, fmaf((float)mid, dc, c0));
-                if (cm >= 1) {
-                    hi = mid;
-                    chi = cm;
-                } else {
-                    lo = mid;
-                }
-            }
-            if (hi >= 1 && (chi & 1)) res = hi;
-        }
-    }
-    if (res >= 1) {
-        n32out[item] = res | SCREEN_COUNTED;
-    } else {
-        n32out[item] = start;
-        fallback[atomicAdd(n_fallback, 1)] = item;
-    }
-}
-
 __device__ __forceinline__ void write_result(const DevBatch& b, const ScanOut& o, int item, int res) {
     if (res >= 0) {
         o.ct[item] = grid_c(b.c0, b.dc, res);
@@ -361,13 +303,11 @@ __device__ __forceinline__ void write_result(const DevBatch& b, const ScanOut& o
     }
 }
 
-__global__ void verify64_kernel(DevBatch b, ScanOut o, const int32_t* __restrict__ n32,
-                                int32_t* ref_sign, int32_t* unresolved, int32_t* n_unresolved,
-                                int item_begin, int item_end) {
-    // natural item order: a warp's threads share a model and have adjacent
-    // wavelengths, so their FP64 branches (series / exp / sincos) agree
-    const int item = item_begin + blockIdx.x * blockDim.x + threadIdx.x;
-    if (item >= item_end) return;
+// Three-point FP64 check of a linear screen's index n (-1: no change seen):
+// FP64 signs at V[0], V[n-1], V[n] (or V[0] and the last scanned point).
+__device__ __forceinline__ void verify_item(const DevBatch& b, const ScanOut& o, int item, int n,
+                                            int32_t* ref_sign, int32_t* unresolved,
+                                            int32_t* n_unresolved) {
     const int m = b.item_model[item];
     const int lo = b.model_loff[m];
     const int N = b.model_loff[m + 1] - lo - 1;
@@ -378,7 +318,6 @@ __global__ void verify64_kernel(DevBatch b, ScanOut o, const int32_t* __restrict
         write_result(b, o, item, -1);
         return;
     }
-    const int n = n32[item];
     int s0 = det_sign(lay, N, k, grid_c(b.c0, b.dc, 0));
     bool ok;
     if (n >= 1) {
@@ -397,7 +336,63 @@ __global__ void verify64_kernel(DevBatch b, ScanOut o, const int32_t* __restrict
     }
 }
 
-// Linear paired FP32 scan of the fallback items of search32_kernel, one
+__global__ void verify64_kernel(DevBatch b, ScanOut o, const int32_t* __restrict__ n32,
+                                int32_t* ref_sign, int32_t* unresolved, int32_t* n_unresolved,
+                                int item_begin, int item_end) {
+    // natural item order: a warp's threads share a model and have adjacent
+    // wavelengths, so their FP64 branches (series / exp / sincos) agree
+    const int item = item_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= item_end) return;
+    verify_item(b, o, item, n32[item], ref_sign, unresolved, n_unresolved);
+}
+
+// The same check over a device-counted list (the fallback items of the
+// counting search), four lanes per item so that its three FP64 evaluations
+// run side by side (a lone evaluation is a long dependent FP64 chain; a few
+// listed items are latency-bound), grid-stride over the list.
+__global__ void __launch_bounds__(128) verify64_list_kernel(DevBatch b, ScanOut o,
+                                                            const int32_t* __restrict__ n32,
+                                                            const int32_t* __restrict__ list,
+                                                            const int32_t* __restrict__ n_list,
+                                                            int32_t* ref_sign, int32_t* unresolved,
+                                                            int32_t* n_unresolved) {
+    const int total = *n_list;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & 3;
+    const int q0 = lane & 28;
+    const unsigned quad = 0xFu << q0;
+    const int stride = (gridDim.x * blockDim.x) >> 2;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 2; t < total; t += stride) {
+        const int item = list[t];
+        const int m = b.item_model[item];
+        const int lo = b.model_loff[m];
+        const int N = b.model_loff[m + 1] - lo - 1;
+        const double* lay = b.layers + (size_t)lo * LAYER_STRIDE;
+        const double k = b.k[item];
+        const int nlim = b.model_nlim[m];
+        if (nlim < 2) {
+            if (sub == 0) write_result(b, o, item, -1);
+            continue;
+        }
+        const int n = n32[item];
+        // lane 0: V[0]; lane 1: V[n-1] (no change seen: the last point); lane 2: V[n]
+        const int pt = sub == 0 ? 0 : sub == 1 ? (n >= 1 ? n - 1 : nlim - 1) : sub == 2 ? (n >= 1 ? n : -1) : -1;
+        const int sg = pt >= 0 ? det_sign(lay, N, k, grid_c(b.c0, b.dc, pt)) : 0;
+        const int s0 = __shfl_sync(quad, sg, q0);
+        const int sa = __shfl_sync(quad, sg, q0 + 1);
+        const int sb = __shfl_sync(quad, sg, q0 + 2);
+        if (sub != 0) continue;
+        const bool ok = n >= 1 ? (sa == s0 && sb != sa) : (sa == s0);
+        if (ok) {
+            write_result(b, o, item, n >= 1 ? n : -1);
+        } else {
+            ref_sign[item] = s0;
+            unresolved[atomicAdd(n_unresolved, 1)] = item;
+        }
+    }
+}
+
+// Linear paired FP32 scan of the fallback items of count_certify_kernel, one
 // block per listed item (few items, each a long walk: the block's warps take
 // consecutive 64-point sub-chunks, 64 x warps points per round), from the
 // start index in n32 (the points below it carry count 0, i.e. a positive
@@ -470,109 +465,139 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
     }
 }
 
-// FP64 decision of a counting-search scan, two lanes per item (natural item
-// order, so a warp's lanes share a model and take the same FP64 branches):
-// for an index n located by the search, lane 2i counts the negative
-// eigenvalues of K at V[n-1] and lane 2i+1 at V[n]; count 0 below (so 0, and
-// V[0]'s sign, at every point below, the count being monotone in the
-// pole-free range) and odd at n (the sign differs) is Algorithm 1's first
-// change. Items the linear fallback located get the sign check of
-// verify64_kernel (V[0], V[n-1], V[n]; V[0] and the last point when it saw
-// no change). When the FP32 count was off by one next to the change (count
-// 0 at both points: the change is higher; nonzero at V[n-1]: lower), the
-// pair takes one FP64 step of two points in that direction, staying inside
-// the pole-free range. Failures go to the FP64 re-scan with V[0]'s sign;
-// n32 keeps the SCREEN_COUNTED flag on certified items.
-__global__ void __launch_bounds__(128) certify64_kernel(DevBatch b, const float* __restrict__ layers32,
-                                                        ScanOut o, int32_t* __restrict__ n32,
-                                                        int32_t* ref_sign, int32_t* unresolved,
-                                                        int32_t* n_unresolved, int item_begin,
-                                                        int item_end) {
+// Counting search and its FP64 certificate (plan precision 2), fused, two
+// lanes per item (natural item order: a warp's 16 items share a model and
+// have adjacent wavelengths, so their branches agree). Fusing lets warps in
+// the FP32 search and warps in the FP64 certificate share an SM: the two use
+// different pipes.
+//  * Search. Inside the pole-free range [0, npf) of pole_free_points_f the
+//    FP32 negative-eigenvalue count (inertia_f) is a non-decreasing step
+//    function of the grid index, 0 at c = 0. The pair evaluates the top of
+//    the range and its midpoint, then splits the bracket in three per step
+//    (one point per lane): about log3(npf) steps instead of a linear walk.
+//    An odd count at the first nonzero point is Algorithm 1's first change.
+//  * Certificate. The FP64 count (det_inertia) is 0 at V[n-1] (so 0, and
+//    V[0]'s sign, at every point below) and odd at V[n] (the sign differs).
+//    When the FP32 count was off by one next to the change (count 0 at both
+//    points: the change is higher; nonzero at V[n-1]: lower), the pair takes
+//    one FP64 step of two points in that direction, inside the range.
+// Items whose change lies above the range (count 0 at its top), at V[0], or
+// where the count jumps by an even number go to the fallback list, with the
+// grid index to scan from in n32; uncertified items go to the FP64 re-scan
+// with V[0]'s sign. Certified items keep SCREEN_COUNTED in n32.
+__global__ void __launch_bounds__(128) count_certify_kernel(DevBatch b, const float* __restrict__ layers32,
+                                                            ScanOut o, int32_t* __restrict__ n32,
+                                                            int32_t* ref_sign, int32_t* unresolved,
+                                                            int32_t* n_unresolved, int32_t* fallback,
+                                                            int32_t* n_fallback, int item_begin,
+                                                            int item_end) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int item = item_begin + (t >> 1);
+    if (item >= item_end) return;  // both lanes of a pair leave together
     const int half = t & 1;
-    int kind = 0, n = -1, nlim = 0, N = 0;
-    const double* lay = nullptr;
-    double k = 0.0;
-    if (item < item_end) {
-        const int m = b.item_model[item];
-        const int lo = b.model_loff[m];
-        N = b.model_loff[m + 1] - lo - 1;
-        lay = b.layers + (size_t)lo * LAYER_STRIDE;
-        k = b.k[item];
-        nlim = b.model_nlim[m];
-        n = n32[item];
-        if (nlim < 2) kind = 4;                            // nothing to scan
-        else if (n >= 0 && (n & SCREEN_COUNTED)) kind = 1; // counting search
-        else if (n >= 1) kind = 2;                         // linear fallback, change
-        else kind = 3;                                     // linear fallback, none
-        n &= ~SCREEN_COUNTED;
+    const unsigned pair = 3u << ((threadIdx.x & 31) & 30);
+    const int m = b.item_model[item];
+    const int lo_rec = b.model_loff[m];
+    const int N = b.model_loff[m + 1] - lo_rec - 1;
+    const int nlim = b.model_nlim[m];
+    if (nlim < 2) {
+        if (!half) {
+            n32[item] = -1;
+            write_result(b, o, item, -1);
+        }
+        return;
     }
-    int v = 0;
-    if (kind == 1) v = det_inertia(lay, N, k, grid_c(b.c0, b.dc, n - 1 + half));
-    else if (kind == 2) v = det_sign(lay, N, k, grid_c(b.c0, b.dc, n - 1 + half));
-    else if (kind == 3) v = det_sign(lay, N, k, grid_c(b.c0, b.dc, half ? nlim - 1 : 0));
-    const int vo = __shfl_xor_sync(FULL, v, 1);
-    if (item >= item_end) return;
-    const int va = half ? vo : v;  // lower point
-    const int vb = half ? v : vo;  // upper point
-    int walked = -1;
-    if (kind == 1 && !(va == 0 && vb > 0 && (vb & 1)) && va >= 0 && vb >= 0) {
-        // both lanes of the pair take this branch (same item, same counts)
+    const float* lay32 = layers32 + (size_t)lo_rec * LAYER_STRIDE32;
+    const float kf = (float)b.k[item];
+    const float c0f = (float)b.c0, dcf = (float)b.dc;
+    const int npf = pole_free_points_f(lay32, N, kf, c0f, dcf, nlim);
+    int n = -1, start = 0;
+    if (npf >= 1) {
+        int lo = -1, hi = npf - 1;
+        const int mid = (hi - 1) >> 1;  // midpoint of (lo, hi); -1 when hi == 0
+        const int pt = half ? mid : hi;
+        const int cnt = pt >= 0 ? inertia_f(lay32, N, kf, fmaf((float)pt, dcf, c0f)) : 0;
+        const int oth = __shfl_xor_sync(pair, cnt, 1);
+        const int c_top = half ? oth : cnt, c_mid = half ? cnt : oth;
+        if (c_top == 0) {
+            start = npf;  // no mode below the bound: scan linearly above it
+        } else {
+            int chi = c_top;
+            if (mid >= 0) {
+                if (c_mid >= 1) {
+                    hi = mid;
+                    chi = c_mid;
+                } else {
+                    lo = mid;
+                }
+            }
+            while (hi - lo > 1) {
+                const int len = hi - lo;
+                const int a = lo + (len + 1) / 3, bq = lo + (2 * len + 1) / 3;  // lo < a <= bq < hi
+                const int q = half ? bq : a;
+                const int c = inertia_f(lay32, N, kf, fmaf((float)q, dcf, c0f));
+                const int co = __shfl_xor_sync(pair, c, 1);
+                const int ca = half ? co : c, cb = half ? c : co;
+                if (ca >= 1) {
+                    hi = a;
+                    chi = ca;
+                } else if (cb >= 1) {
+                    lo = a;
+                    hi = bq;
+                    chi = cb;
+                } else {
+                    lo = bq;
+                }
+            }
+            if (hi >= 1 && (chi & 1)) n = hi;
+        }
+    }
+    if (n < 1) {
+        if (!half) {
+            n32[item] = start;
+            fallback[atomicAdd(n_fallback, 1)] = item;
+        }
+        return;
+    }
+    const double* lay = b.layers + (size_t)lo_rec * LAYER_STRIDE;
+    const double k = b.k[item];
+    const int v = det_inertia(lay, N, k, grid_c(b.c0, b.dc, n - 1 + half));
+    const int vo = __shfl_xor_sync(pair, v, 1);
+    const int va = half ? vo : v;  // V[n-1]
+    const int vb = half ? v : vo;  // V[n]
+    int cert = (va == 0 && vb > 0 && (vb & 1)) ? n : -1;
+    if (cert < 0 && va >= 0 && vb >= 0) {
         const bool up = va == 0 && vb == 0;
         const bool down = va > 0 && n >= 3;
         if (up || down) {
-            const int p0 = up ? n + 1 : n - 3;
-            const int nlim_pf = up ? pole_free_points_f(layers32 + (size_t)b.model_loff[b.item_model[item]] *
-                                                            LAYER_STRIDE32,
-                                                        N, (float)k, (float)b.c0, (float)b.dc, nlim)
-                                   : nlim;
-            const int pt = p0 + half;
-            const int w = pt < nlim ? det_inertia(lay, N, k, grid_c(b.c0, b.dc, pt)) : -1;
-            const int wo = __shfl_xor_sync(3u << ((threadIdx.x & 31) & 30), w, 1);
+            const int p = (up ? n + 1 : n - 3) + half;
+            const int w = p < nlim ? det_inertia(lay, N, k, grid_c(b.c0, b.dc, p)) : -1;
+            const int wo = __shfl_xor_sync(pair, w, 1);
             const int c_lo = half ? wo : w, c_hi = half ? w : wo;
             if (up) {
-                // counts 0 at n; first nonzero at n+1 or n+2 (n+1 inside the range)
+                // count 0 at n; first nonzero at n+1, or at n+2 with n+1 inside the range
                 if (c_lo > 0) {
-                    if (c_lo & 1) walked = n + 1;
-                } else if (c_lo == 0 && c_hi > 0 && (c_hi & 1) && n + 1 < nlim_pf) {
-                    walked = n + 2;
+                    if (c_lo & 1) cert = n + 1;
+                } else if (c_lo == 0 && c_hi > 0 && (c_hi & 1) && n + 1 < npf) {
+                    cert = n + 2;
                 }
             } else {
                 // count nonzero at n-1; first nonzero at n-1 or n-2
                 if (c_hi == 0) {
-                    if (va & 1) walked = n - 1;
+                    if (va & 1) cert = n - 1;
                 } else if (c_hi > 0 && c_lo == 0 && (c_hi & 1)) {
-                    walked = n - 2;
+                    cert = n - 2;
                 }
             }
         }
     }
     if (half) return;
-    bool ok;
-    int s0 = 0;
-    if (kind == 4) {
-        write_result(b, o, item, -1);
-        return;
-    } else if (kind == 1) {
-        ok = va == 0 && vb > 0 && (vb & 1);
-        if (!ok && walked >= 1) {
-            n = walked;
-            ok = true;
-        }
-        if (!ok) s0 = det_sign(lay, N, k, grid_c(b.c0, b.dc, 0));
-    } else if (kind == 2) {
-        s0 = (n == 1) ? va : det_sign(lay, N, k, grid_c(b.c0, b.dc, 0));
-        ok = va == s0 && vb != va;
+    if (cert >= 1) {
+        n32[item] = cert | SCREEN_COUNTED;
+        write_result(b, o, item, cert);
     } else {
-        s0 = va;
-        ok = vb == va;
-    }
-    if (ok) {
-        write_result(b, o, item, kind == 3 ? -1 : n);
-    } else {
-        n32[item] = kind == 3 ? -1 : n;
-        ref_sign[item] = s0;
+        n32[item] = n;
+        ref_sign[item] = det_sign(lay, N, k, grid_c(b.c0, b.dc, 0));
         unresolved[atomicAdd(n_unresolved, 1)] = item;
     }
 }
@@ -645,42 +670,46 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
     size_t shm = (size_t)wpb * p.stage_layers * LAYER_STRIDE32 * sizeof(float);
     int n = item_end - item_begin;
     if (search) {
-        search32_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, layers32, n32, fallback, counters + 3,
-                                                        item_begin, item_end);
+        count_certify_kernel<<<(2 * n + 127) / 128, 128, 0, s>>>(b, layers32, o, n32, ref_sign,
+                                                                 unresolved, counters + 1, fallback,
+                                                                 counters + 3, item_begin, item_end);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (phase_ev && (e = cudaEventRecord(phase_ev[0], s)) != cudaSuccess) return e;
         fallback32_kernel<<<std::max(1, std::min(p.blocks, n)), 256,
                             (size_t)p.stage_layers * LAYER_STRIDE32 * sizeof(float), s>>>(
             b, layers32, n32, fallback, counters + 3, counters + 4, p.stage_layers);
-    } else switch (p.cpl) {
-        case 1:
-            screen32_kernel<1><<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,
-                                                            p.stage_layers, counters, item_begin,
-                                                            item_end);
-            break;
-        case 2:  // paired points, packed FP32x2
-            screen32p_kernel<<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,
-                                                          p.stage_layers, counters, item_begin,
-                                                          item_end);
-            break;
-        case 4:
-            screen32_kernel<4><<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,
-                                                            p.stage_layers, counters, item_begin,
-                                                            item_end);
-            break;
-        default:
-            return cudaErrorInvalidValue;
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (phase_ev && (e = cudaEventRecord(phase_ev[0], s)) != cudaSuccess) return e;
-    if (search)
-        certify64_kernel<<<(2 * n + 127) / 128, 128, 0, s>>>(b, layers32, o, n32, ref_sign,
-                                                             unresolved, counters + 1, item_begin,
-                                                             item_end);
-    else
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        verify64_list_kernel<<<std::max(1, std::min(p.blocks, (4 * n + 127) / 128)), 128, 0, s>>>(
+            b, o, n32, fallback, counters + 3, ref_sign, unresolved, counters + 1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (phase_ev && (e = cudaEventRecord(phase_ev[1], s)) != cudaSuccess) return e;
+    } else {
+        switch (p.cpl) {
+            case 1:
+                screen32_kernel<1><<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,
+                                                                p.stage_layers, counters, item_begin,
+                                                                item_end);
+                break;
+            case 2:  // paired points, packed FP32x2
+                screen32p_kernel<<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,
+                                                              p.stage_layers, counters, item_begin,
+                                                              item_end);
+                break;
+            case 4:
+                screen32_kernel<4><<<blocks, 32 * wpb, shm, s>>>(b, layers32, n32, p.persistent,
+                                                                p.stage_layers, counters, item_begin,
+                                                                item_end);
+                break;
+            default:
+                return cudaErrorInvalidValue;
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (phase_ev && (e = cudaEventRecord(phase_ev[0], s)) != cudaSuccess) return e;
         verify64_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, o, n32, ref_sign, unresolved,
                                                         counters + 1, item_begin, item_end);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (phase_ev && (e = cudaEventRecord(phase_ev[1], s)) != cudaSuccess) return e;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (phase_ev && (e = cudaEventRecord(phase_ev[1], s)) != cudaSuccess) return e;
+    }
     int rblocks = std::max(1, std::min(p.blocks, (n + wpb - 1) / wpb));
     resolve64_kernel<<<rblocks, 32 * wpb, 0, s>>>(b, o, n32, ref_sign, unresolved, counters + 1,
                                                   counters + 2);
