@@ -126,12 +126,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(models, grid, n_models: int, seconds_hint: float = 10.0):
+def cpu_oracle_rate(models, grid, n_models: int, threads: int = 0):
     """Time the CPU oracle on the first n_models models of the workload, on
-    all host cores. Returns (curves/s, cores, sample description)."""
+    `threads` host threads (0: all cores). Returns (curves/s, threads,
+    sample description)."""
     import oracle
     oracle.build()
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     sub = models.subset(range(n_models))
     t0 = time.perf_counter()
     oracle.dispersion(sub.as_dict(), grid.c0, grid.dc, grid.n_c, n_threads=cores)
@@ -324,12 +325,51 @@ def run_extras(args, masw, torch):
         "paper_section_3_2": {"3": {"modular": 2.8, "contiguous": 1.9},
                               "8": {"modular": 7.0, "contiguous": 4.2}}}
 
+    # uniform-work stress curves: one wavelength repeated per curve, roots
+    # near 72 / 238 / 256 m/s
+    stress = {}
+    for target in W.STRESS_TARGETS:
+        row = {}
+        for rep in (50, 100, 200, 500):
+            sm, sg = W.uniform_stress(target, rep, n_models=256)
+            with masw.Batch(sm, sg) as b:
+                sct, _, _ = b.dispersion()
+                ms = []
+                for _ in range(10):
+                    b.dispersion()
+                    ms.append(b.last_scan_ms())
+            row[str(rep)] = {"curves_per_s": sm.n_models / (float(np.median(ms)) * 1e-3),
+                             "scan_ms": float(np.median(ms)), "ct": float(sct[0])}
+        stress[f"{target:g}"] = row
+    out["uniform_stress"] = {"workload": "256 identical curves per case, one wavelength repeated "
+                                         "50..500 times (0.5 m or 2000 m on 2-layer models); "
+                                         "c grid 50..1200 step 0.25", "targets_m_s": stress}
+
+    # first use: batch creation (upload, records, graph capture) and the first
+    # scan of a fresh batch vs the warm median (CUDA context and library
+    # already loaded in this process)
+    fm, fg = W.uniform_batch()
+    t0 = time.perf_counter()
+    fb = masw.Batch(fm, fg)
+    t1 = time.perf_counter()
+    fb.dispersion()
+    t2 = time.perf_counter()
+    warm = []
+    for _ in range(10):
+        t3 = time.perf_counter()
+        fb.dispersion()
+        warm.append(time.perf_counter() - t3)
+    fb.close()
+    out["first_call"] = {"workload": "uniform_batch (1024 models), default plan, host outputs",
+                         "create_ms": 1e3 * (t1 - t0), "first_dispersion_ms": 1e3 * (t2 - t1),
+                         "warm_median_ms": 1e3 * float(np.median(warm))}
+
     # serving
     sampler = W.RandomWalkSampler()
     reqs = W.concat([sampler.next() for _ in range(args.serving_requests)])
     grid = W.Grid(50.0, 0.25, 4601)
     rates = {}
-    for rate in (1e3, 1e4, 1e5, 1e6):
+    for rate in (1e3, 3e3, 1e4, 3e4, 1e5, 1e6):
         arr = W.poisson_arrivals(reqs.n_models, rate=rate)
         with serving.Server(grid, max_slots=2048, chunks_per_tick=8,
                             mem_cap_bytes=16 << 30) as srv:
@@ -532,7 +572,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_oracle_rate(models, grid, min(256, models.n_models))
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        v1, _, sample1 = cpu_oracle_rate(models, grid, min(8, models.n_models), threads=1)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread": {"value": v1, "unit": UNIT, "sample": sample1}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -177,6 +177,36 @@ def ragged_batch(n_models: int = 8192, layers=(3, 30), lambdas=(30, 400),
     return m, grid or Grid(50.0, 0.25, 4601)
 
 
+STRESS_TARGETS = (72.0, 238.0, 256.0)
+
+
+def uniform_stress(target: float, repeats: int, n_models: int = 256) -> tuple[Models, Grid]:
+    """Uniform-work stress curves (the paper's uniform runs: one wavelength
+    repeated many times per curve). Each of the n_models identical curves
+    holds `repeats` copies of one wavelength, chosen so that the root lies
+    near `target` m/s, from the textbook limits of the fundamental mode (the
+    Rayleigh speed of the top layer at short wavelengths, of the half-space
+    at long ones; 0.9194 beta for nu = 0.25):
+      72  -> model S (h = [4, 6] m, beta = [78.3, 180, 278.4] m/s), lambda 0.5 m;
+      238 -> model U (h = [4, 6] m, beta = [200, 230, 258.9] m/s), lambda 2000 m;
+      256 -> model S, lambda 2000 m.
+    nu = 0.25, rho = 1900 kg/m^3; c grid 50..1200 m/s step 0.25."""
+    models = {"S": np.array([78.3, 180.0, 278.4]), "U": np.array([200.0, 230.0, 258.9])}
+    case = {72.0: ("S", 0.5), 238.0: ("U", 2000.0), 256.0: ("S", 2000.0)}
+    if float(target) not in case:
+        raise ValueError(f"target must be one of {STRESS_TARGETS}")
+    name, lam = case[float(target)]
+    beta = models[name]
+    h = np.array([4.0, 6.0])
+    alpha = alpha_from_nu(beta, 0.25)
+    rho = np.full(3, 1900.0)
+    profiles = [(h, alpha, beta, rho)] * n_models
+    lams = [np.full(int(repeats), lam)] * n_models
+    m = _pack(profiles, lams, {"workload": f"uniform_stress target {target:g} m/s, "
+                                           f"lambda {lam:g} m x {repeats}"})
+    return m, Grid(50.0, 0.25, 4601)
+
+
 def differentiation_batch(n_models: int = 512, n_layers: int = 12, n_lambda: int = 150,
                           grid: Grid | None = None, seed: int = SEED + 4,
                           spread: float = 0.05) -> tuple[Models, Grid, Models]:

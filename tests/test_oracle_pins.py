@@ -435,3 +435,15 @@ def test_fd_gradient_of_layer_identical_to_half_space_thickness_is_zero(oracle_l
     gb, gh = oracle_lib.root_grad_fd(h, a, b, r, 8.0, 50.0, 0.25, 4601, idx)
     assert abs(gh[0]) < 1e-6
     assert float(gb.sum()) == pytest.approx(rayleigh_ratio(nu), rel=1e-7)
+
+
+def test_uniform_stress_roots_land_near_their_targets(oracle_lib):
+    """Input recipe of the uniform stress curves: the oracle's first change
+    lies within 1.5 m/s of the targeted fundamental-mode limits (top-layer
+    Rayleigh speed at 0.5 m, half-space Rayleigh speed at 2000 m), and every
+    repeat of the wavelength gives the same index."""
+    for target in workloads.STRESS_TARGETS:
+        m, g = workloads.uniform_stress(target, 4, n_models=2)
+        ct, idx, st = oracle_lib.dispersion(m.as_dict(), g.c0, g.dc, g.n_c)
+        assert (st == 0).all() and (idx == idx[0]).all()
+        assert abs(ct[0] - target) <= 1.5, (target, ct[0])
