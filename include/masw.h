@@ -239,12 +239,15 @@ int masw_sm_count(int32_t* sms);
  * beyond its motivation (repeated evaluation inside an optimisation or
  * uncertainty loop, Section 1 and Section 2.1): requests, each one model
  * with its own layer count and wavelengths, arrive at any time; each
- * admitted request holds a slot with its data resident on the device; every
- * tick advances every running (request, wavelength) item by at most
- * chunks_per_tick 32-point chunks of Algorithm 1 and compacts the rest, so
- * requests admitted between ticks overlap with those in flight. A result is
- * identical to masw_dispersion's for the same model. The host waits for a
- * tick on an event; nothing waits on the device.
+ * admitted request holds a slot with its data resident on the device. Every
+ * tick uploads the requests admitted since the last one (one copy), runs the
+ * counting search of plan precision 2 on their (request, wavelength) items,
+ * advances every item scanning linearly (its change above the pole-free
+ * bound) by at most chunks_per_tick chunks of Algorithm 1, checks in FP64
+ * what these located, and compacts the rest, so requests admitted between
+ * ticks overlap with those in flight. A result is identical to
+ * masw_dispersion's for the same model. The host waits for a tick on an
+ * event; nothing waits on the device.
  * --------------------------------------------------------------------- */
 typedef struct masw_server masw_server;
 
@@ -253,7 +256,8 @@ typedef struct {
     int32_t max_layers;      /* finite layers per request (<= MASW_MAX_LAYERS) */
     int32_t max_lambda;      /* wavelengths per request */
     int64_t mem_cap_bytes;   /* admission cap on the device bytes held by requests in flight */
-    int32_t chunks_per_tick; /* chunks of 32 test velocities an item advances per tick */
+    int32_t chunks_per_tick; /* chunks of 64 test velocities (paired FP32 screen) an item
+                                scanning linearly advances per tick */
     int32_t warps_per_block; /* 1, 2, 4 or 8 */
 } masw_server_config;
 
@@ -265,9 +269,11 @@ typedef struct {
     int64_t completed;
 } masw_server_stats;
 
-/* Allocate the slot table (device) and its pinned staging/result buffers for
- * the given grid; all later work runs on cuda_stream. MASW_EINVAL on a bad
- * config, MASW_ENOMEM when the buffers do not fit. */
+/* Allocate the slot table (device), its packed upload buffer (pinned host and
+ * device, one slot block per slot) and the mapped result buffers for the
+ * given grid; all later work runs on cuda_stream. MASW_EINVAL on a bad config
+ * (including an upload buffer above 2^31 bytes), MASW_ENOMEM when the
+ * buffers do not fit. */
 int masw_server_create(const masw_grid* grid, const masw_server_config* cfg, void* cuda_stream,
                        masw_server** out);
 int masw_server_destroy(masw_server* server);

@@ -19,8 +19,10 @@
 //    chunks), so a result does not depend on what else is in flight.
 // There are no device-side waits: the host waits for each tick on an event.
 //
-// Slot layout (one pinned host staging region and one device region per
-// slot, copied with a single transfer at admission):
+// Admission builds a request's slot block in one packed pinned upload
+// buffer; each tick sends everything admitted since the last tick (blocks,
+// their descriptors and the new item ids) with one host-to-device copy, and
+// a scatter kernel moves each block into its slot. Slot layout:
 //   [meta: 4 x i32 (nrec, nlim, n_lambda, 0)] [records: rmax x 8 f64]
 //   [FP32 records: rmax x 8 f32] [k: imax f64]
 //   [scan state: imax x (base, carry, phase, ref) i32]
@@ -83,6 +85,22 @@ __device__ __forceinline__ int32_t* slot_state(const SlotView& v, int s) {
 }
 
 enum { PH_SCREEN = 0, PH_FP64 = 1, PH_FP64_WINDOW = 2 };
+
+// Upload descriptor of one admitted request inside the packed upload buffer.
+struct UploadDesc { int32_t slot, offset, bytes, n_lambda; };
+
+// Tick, admission: one block per request copies its block (16-byte words;
+// offsets and slot strides are multiples of 256 bytes) from the upload
+// buffer into its slot and sets its running-item count.
+__global__ void __launch_bounds__(256) serve_scatter_kernel(SlotView v, const unsigned char* __restrict__ up,
+                                                            const UploadDesc* __restrict__ desc) {
+    const UploadDesc d = desc[blockIdx.x];
+    const uint4* src = reinterpret_cast<const uint4*>(up + d.offset);
+    uint4* dst = reinterpret_cast<uint4*>(v.region + (size_t)d.slot * v.stride);
+    const int words = (d.bytes + 15) / 16;
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0) v.remaining[d.slot] = d.n_lambda;
+}
 
 // Tick, part 0 (one thread per item admitted since the last tick): the
 // counting search of the batch path (search32_kernel). A located index goes
@@ -345,14 +363,17 @@ struct masw_server {
     masw_server_config cfg{};
     cudaStream_t stream = nullptr;
     SlotView v{};
-    double* h_region = nullptr;  // pinned staging, same layout as v.region
+    // packed upload: [request blocks, 256-byte aligned][descriptors][new item ids]
+    unsigned char* h_upload = nullptr;  // pinned
+    unsigned char* d_upload = nullptr;
+    size_t upload_cap = 0;   // bytes
+    size_t upload_used = 0;  // bytes of request blocks staged since the last tick
+    std::vector<UploadDesc> upload_desc;
     double* h_ct = nullptr;      // mapped pinned results
     int32_t* h_idx = nullptr;
     int32_t* h_status = nullptr;
     int32_t* active[2] = {nullptr, nullptr};
     int32_t* check = nullptr;
-    int32_t* new_items = nullptr;  // device copy of the items admitted since the last tick
-    int32_t* h_new_items = nullptr;
     int32_t* h_counters = nullptr;
     int32_t* h_done = nullptr;
     cudaEvent_t ev = nullptr;
@@ -376,10 +397,10 @@ namespace {
 void server_free(masw_server* S) {
     if (!S) return;
     void* dev[] = {S->v.region, S->v.remaining, S->v.done, S->v.counters, S->active[0],
-                   S->active[1], S->check, S->new_items};
+                   S->active[1], S->check, S->d_upload};
     for (void* p : dev)
         if (p) cudaFree(p);
-    void* host[] = {S->h_region, S->h_ct, S->h_idx, S->h_status, S->h_new_items, S->h_counters,
+    void* host[] = {S->h_upload, S->h_ct, S->h_idx, S->h_status, S->h_counters,
                     S->h_done};
     for (void* p : host)
         if (p) cudaFreeHost(p);
@@ -406,19 +427,32 @@ int run_tick(masw_server* S) {
 int run_tick_impl(masw_server* S) {
     S->just_done.clear();
     int n_new = (int)S->pending.size();
+    const int32_t* new_items = nullptr;
     if (n_new) {
-        std::memcpy(S->h_new_items, S->pending.data(), n_new * sizeof(int32_t));
-        if (cudaMemcpyAsync(S->new_items, S->h_new_items, n_new * sizeof(int32_t),
-                            cudaMemcpyHostToDevice, S->stream) != cudaSuccess)
+        // one transfer: staged blocks, then descriptors, then the new item ids
+        const int n_req = (int)S->upload_desc.size();
+        const size_t desc_off = S->upload_used;
+        const size_t items_off = desc_off + (size_t)n_req * sizeof(UploadDesc);
+        const size_t total = items_off + (size_t)n_new * sizeof(int32_t);
+        std::memcpy(S->h_upload + desc_off, S->upload_desc.data(), n_req * sizeof(UploadDesc));
+        std::memcpy(S->h_upload + items_off, S->pending.data(), n_new * sizeof(int32_t));
+        if (cudaMemcpyAsync(S->d_upload, S->h_upload, total, cudaMemcpyHostToDevice, S->stream) !=
+            cudaSuccess)
             return MASW_ECUDA;
+        serve_scatter_kernel<<<n_req, 256, 0, S->stream>>>(
+            S->v, S->d_upload, reinterpret_cast<const UploadDesc*>(S->d_upload + desc_off));
+        if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
+        new_items = reinterpret_cast<const int32_t*>(S->d_upload + items_off);
         S->pending.clear();
+        S->upload_desc.clear();
+        S->upload_used = 0;
     }
     if (S->n_active + n_new == 0) return MASW_OK;
     if (cudaMemsetAsync(S->v.counters, 0, 3 * sizeof(int32_t), S->stream) != cudaSuccess)
         return MASW_ECUDA;
     if (n_new) {
         serve_search_kernel<<<(n_new + 127) / 128, 128, 0, S->stream>>>(
-            S->v, S->new_items, n_new, S->active[1 - S->cur], S->check, S->grid.c0, S->grid.dc);
+            S->v, new_items, n_new, S->active[1 - S->cur], S->check, S->grid.c0, S->grid.dc);
         if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
     }
     if (S->n_active) {
@@ -505,14 +539,21 @@ int masw_server_create(const masw_grid* grid, const masw_server_config* cfg, voi
     S->v.stride = 2 + (int64_t)S->v.rmax * (LAYER_STRIDE + 4) + 3 * (int64_t)S->v.imax;
     S->v.stride = (S->v.stride + 31) / 32 * 32;  // 256-byte aligned slots
     size_t slots = cfg->max_slots, items = (size_t)cap_items;
+    // every slot's block at once, plus descriptors and item ids
+    S->upload_cap = slots * (size_t)S->v.stride * sizeof(double) + slots * sizeof(UploadDesc) +
+                    items * sizeof(int32_t) + 256;
+    if (S->upload_cap > (size_t)INT32_MAX) {  // upload offsets are 32-bit
+        server_free(S);
+        return MASW_EINVAL;
+    }
     bool ok = dalloc(&S->v.region, slots * S->v.stride) && dalloc(&S->v.remaining, slots) &&
               dalloc(&S->v.done, slots) && dalloc(&S->v.counters, 3) &&
               dalloc(&S->active[0], items) && dalloc(&S->active[1], items) &&
-              dalloc(&S->check, items) && dalloc(&S->new_items, items) &&
-              halloc(&S->h_region, slots * S->v.stride) &&
+              dalloc(&S->check, items) && dalloc(&S->d_upload, S->upload_cap) &&
+              halloc(&S->h_upload, S->upload_cap) &&
               halloc(&S->h_ct, items, cudaHostAllocMapped) &&
               halloc(&S->h_idx, items, cudaHostAllocMapped) &&
-              halloc(&S->h_status, items, cudaHostAllocMapped) && halloc(&S->h_new_items, items) &&
+              halloc(&S->h_status, items, cudaHostAllocMapped) &&
               halloc(&S->h_counters, 3) && halloc(&S->h_done, slots) &&
               cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming) == cudaSuccess &&
               cudaHostGetDevicePointer((void**)&S->v.ct, S->h_ct, 0) == cudaSuccess &&
@@ -560,9 +601,9 @@ int masw_server_submit(masw_server* S, int32_t n_layers, const double* h, const 
     int64_t need = request_bytes(n_layers, n_lambda);
     if (S->free_slots.empty() || S->bytes_in_flight + need > S->cfg.mem_cap_bytes) return MASW_EADMIT;
     int slot = S->free_slots.back();
-    // stage meta, records (as masw_model_batch_create builds them), k and a
-    // zero scan state in the slot's pinned region, then one transfer
-    double* reg = S->h_region + (size_t)slot * S->v.stride;
+    // build meta, records (as masw_model_batch_create builds them), k and a
+    // zero scan state in the packed upload buffer; the next tick sends it
+    double* reg = reinterpret_cast<double*>(S->h_upload + S->upload_used);
     int32_t* meta = (int32_t*)reg;
     meta[0] = n_layers + 1;
     meta[1] = scan_limit_host(S->grid, beta[n_layers]);
@@ -599,16 +640,9 @@ int masw_server_submit(masw_server* S, int32_t n_layers, const double* h, const 
     for (int j = 0; j < n_lambda; ++j) kk[j] = 2.0 * M_PI / lambda[j];
     int32_t* stt = (int32_t*)(kk + S->v.imax);
     std::memset(stt, 0, (size_t)n_lambda * 4 * sizeof(int32_t));
-    size_t bytes = (size_t)((char*)(stt + 4 * n_lambda) - (char*)reg);
-    cudaError_t e = cudaMemcpyAsync(S->v.region + (size_t)slot * S->v.stride, reg, bytes,
-                                    cudaMemcpyHostToDevice, S->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(S->v.remaining + slot, &meta[2], sizeof(int32_t), cudaMemcpyHostToDevice,
-                            S->stream);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return MASW_ECUDA;
-    }
+    const size_t bytes = (size_t)((char*)(stt + 4 * n_lambda) - (char*)reg);
+    S->upload_desc.push_back({slot, (int32_t)S->upload_used, (int32_t)bytes, n_lambda});
+    S->upload_used += (bytes + 255) / 256 * 256;
     S->free_slots.pop_back();
     int64_t id = (int64_t)S->id_slot.size();
     S->id_slot.push_back(slot);
