@@ -364,7 +364,9 @@ struct masw_server {
     cudaStream_t stream = nullptr;
     SlotView v{};
     // packed upload: [request blocks, 256-byte aligned][descriptors][new item ids]
-    unsigned char* h_upload = nullptr;  // pinned
+    unsigned char* h_upload[2] = {nullptr, nullptr};  // pinned, two halves: one staging while
+                                                      // the other may still be in a copy
+    int up_cur = 0;                                   // half that submit stages into
     unsigned char* d_upload = nullptr;
     size_t upload_cap = 0;   // bytes
     size_t upload_used = 0;  // bytes of request blocks staged since the last tick
@@ -388,6 +390,7 @@ struct masw_server {
     std::vector<int32_t> pending;   // items admitted since the last tick
     std::vector<int32_t> just_done; // slots finished by the last tick
     int64_t bytes_in_flight = 0;
+    int32_t pending_active = 0;  // new items of a launched, unfinished tick
     int64_t ticks = 0;
     int64_t completed = 0;
 };
@@ -396,12 +399,12 @@ namespace {
 
 void server_free(masw_server* S) {
     if (!S) return;
-    void* dev[] = {S->v.region, S->v.remaining, S->v.done, S->v.counters, S->active[0],
+    void* dev[] = {S->v.region, S->v.remaining, S->v.counters, S->active[0],
                    S->active[1], S->check, S->d_upload};
     for (void* p : dev)
         if (p) cudaFree(p);
-    void* host[] = {S->h_upload, S->h_ct, S->h_idx, S->h_status, S->h_counters,
-                    S->h_done};
+    void* host[] = {S->h_upload[0], S->h_upload[1], S->h_ct, S->h_idx, S->h_status,
+                    S->h_counters};
     for (void* p : host)
         if (p) cudaFreeHost(p);
     if (S->ev) cudaEventDestroy(S->ev);
@@ -417,26 +420,46 @@ bool halloc(T** p, size_t n, unsigned flags = cudaHostAllocDefault) {
     return cudaHostAlloc((void**)p, std::max<size_t>(n, 1) * sizeof(T), flags) == cudaSuccess;
 }
 
-// Launch one tick and wait for it; the finished slots land in just_done.
-int run_tick_impl(masw_server* S);
-int run_tick(masw_server* S) {
-    int rc = run_tick_impl(S);
+// A tick in two halves: tick_launch enqueues the upload of the requests
+// admitted since the last tick, the kernels and the copy back of the
+// counters and done list, and records the tick's event; tick_finish waits on
+// it and takes the finished slots into just_done. Between the two the host
+// may admit more requests: they stage into the other half of the upload
+// buffer and join the next tick.
+int tick_launch_impl(masw_server* S, bool* launched);
+int tick_finish_impl(masw_server* S);
+int tick_launch(masw_server* S, bool* launched) {
+    int rc = tick_launch_impl(S, launched);
     if (rc != MASW_OK) cudaGetLastError();  // leave no pending error behind
     return rc;
 }
-int run_tick_impl(masw_server* S) {
+int tick_finish(masw_server* S) {
+    int rc = tick_finish_impl(S);
+    if (rc != MASW_OK) cudaGetLastError();
+    return rc;
+}
+int run_tick(masw_server* S) {
+    bool launched = false;
+    int rc = tick_launch(S, &launched);
+    if (rc == MASW_OK && launched) rc = tick_finish(S);
+    return rc;
+}
+int tick_launch_impl(masw_server* S, bool* launched) {
+    *launched = false;
     S->just_done.clear();
     int n_new = (int)S->pending.size();
+    if (S->n_active + n_new == 0) return MASW_OK;
     const int32_t* new_items = nullptr;
     if (n_new) {
         // one transfer: staged blocks, then descriptors, then the new item ids
+        unsigned char* up = S->h_upload[S->up_cur];
         const int n_req = (int)S->upload_desc.size();
         const size_t desc_off = S->upload_used;
         const size_t items_off = desc_off + (size_t)n_req * sizeof(UploadDesc);
         const size_t total = items_off + (size_t)n_new * sizeof(int32_t);
-        std::memcpy(S->h_upload + desc_off, S->upload_desc.data(), n_req * sizeof(UploadDesc));
-        std::memcpy(S->h_upload + items_off, S->pending.data(), n_new * sizeof(int32_t));
-        if (cudaMemcpyAsync(S->d_upload, S->h_upload, total, cudaMemcpyHostToDevice, S->stream) !=
+        std::memcpy(up + desc_off, S->upload_desc.data(), n_req * sizeof(UploadDesc));
+        std::memcpy(up + items_off, S->pending.data(), n_new * sizeof(int32_t));
+        if (cudaMemcpyAsync(S->d_upload, up, total, cudaMemcpyHostToDevice, S->stream) !=
             cudaSuccess)
             return MASW_ECUDA;
         serve_scatter_kernel<<<n_req, 256, 0, S->stream>>>(
@@ -446,8 +469,8 @@ int run_tick_impl(masw_server* S) {
         S->pending.clear();
         S->upload_desc.clear();
         S->upload_used = 0;
+        S->up_cur = 1 - S->up_cur;  // later submits stage into the other half
     }
-    if (S->n_active + n_new == 0) return MASW_OK;
     if (cudaMemsetAsync(S->v.counters, 0, 3 * sizeof(int32_t), S->stream) != cudaSuccess)
         return MASW_ECUDA;
     if (n_new) {
@@ -469,23 +492,25 @@ int run_tick_impl(masw_server* S) {
     serve_check_kernel<<<(S->n_active + n_new + 127) / 128, 128, 0, S->stream>>>(
         S->v, S->check, S->v.counters + 2, S->active[1 - S->cur], S->grid.c0, S->grid.dc);
     if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
-    if (cudaMemcpyAsync(S->h_counters, S->v.counters, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                        S->stream) != cudaSuccess ||
-        cudaEventRecord(S->ev, S->stream) != cudaSuccess ||
-        cudaEventSynchronize(S->ev) != cudaSuccess)
+    // counters and the done list (first counters[1] entries) come back together
+    if (cudaMemcpyAsync(S->h_counters, S->v.counters, (4 + S->cfg.max_slots) * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost, S->stream) != cudaSuccess ||
+        cudaEventRecord(S->ev, S->stream) != cudaSuccess)
         return MASW_ECUDA;
+    S->pending_active = n_new;  // items of this tick (for the stats until it finishes)
+    *launched = true;
+    return MASW_OK;
+}
+int tick_finish_impl(masw_server* S) {
+    if (cudaEventSynchronize(S->ev) != cudaSuccess) return MASW_ECUDA;
     int survivors = S->h_counters[0], n_done = S->h_counters[1];
-    if (n_done > 0) {
-        if (cudaMemcpy(S->h_done, S->v.done, n_done * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
-            cudaSuccess)
-            return MASW_ECUDA;
-        for (int i = 0; i < n_done; ++i) {
-            S->slot_done[S->h_done[i]] = 1;
-            S->just_done.push_back(S->h_done[i]);
-        }
+    for (int i = 0; i < n_done; ++i) {
+        S->slot_done[S->h_done[i]] = 1;
+        S->just_done.push_back(S->h_done[i]);
     }
     S->cur = 1 - S->cur;
     S->n_active = survivors;
+    S->pending_active = 0;
     S->ticks++;
     S->completed += n_done;
     return MASW_OK;
@@ -546,19 +571,24 @@ int masw_server_create(const masw_grid* grid, const masw_server_config* cfg, voi
         server_free(S);
         return MASW_EINVAL;
     }
+    // counters (3, padded to 4) and the done list share one buffer: one copy back per tick
     bool ok = dalloc(&S->v.region, slots * S->v.stride) && dalloc(&S->v.remaining, slots) &&
-              dalloc(&S->v.done, slots) && dalloc(&S->v.counters, 3) &&
+              dalloc(&S->v.counters, 4 + slots) &&
               dalloc(&S->active[0], items) && dalloc(&S->active[1], items) &&
               dalloc(&S->check, items) && dalloc(&S->d_upload, S->upload_cap) &&
-              halloc(&S->h_upload, S->upload_cap) &&
+              halloc(&S->h_upload[0], S->upload_cap) && halloc(&S->h_upload[1], S->upload_cap) &&
               halloc(&S->h_ct, items, cudaHostAllocMapped) &&
               halloc(&S->h_idx, items, cudaHostAllocMapped) &&
               halloc(&S->h_status, items, cudaHostAllocMapped) &&
-              halloc(&S->h_counters, 3) && halloc(&S->h_done, slots) &&
+              halloc(&S->h_counters, 4 + slots) &&
               cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming) == cudaSuccess &&
               cudaHostGetDevicePointer((void**)&S->v.ct, S->h_ct, 0) == cudaSuccess &&
               cudaHostGetDevicePointer((void**)&S->v.idx, S->h_idx, 0) == cudaSuccess &&
               cudaHostGetDevicePointer((void**)&S->v.status, S->h_status, 0) == cudaSuccess;
+    if (ok) {
+        S->v.done = S->v.counters + 4;
+        S->h_done = S->h_counters + 4;
+    }
     if (!ok) {
         cudaGetLastError();
         server_free(S);
@@ -603,7 +633,7 @@ int masw_server_submit(masw_server* S, int32_t n_layers, const double* h, const 
     int slot = S->free_slots.back();
     // build meta, records (as masw_model_batch_create builds them), k and a
     // zero scan state in the packed upload buffer; the next tick sends it
-    double* reg = reinterpret_cast<double*>(S->h_upload + S->upload_used);
+    double* reg = reinterpret_cast<double*>(S->h_upload[S->up_cur] + S->upload_used);
     int32_t* meta = (int32_t*)reg;
     meta[0] = n_layers + 1;
     meta[1] = scan_limit_host(S->grid, beta[n_layers]);
@@ -678,7 +708,7 @@ int masw_server_poll(masw_server* S, int64_t request_id, double* ct, int32_t* ct
 int masw_server_get_stats(const masw_server* S, masw_server_stats* st) {
     if (!S || !st) return MASW_EINVAL;
     st->in_flight = (int32_t)(S->cfg.max_slots - (int32_t)S->free_slots.size());
-    st->active_items = S->n_active + (int32_t)S->pending.size();
+    st->active_items = S->n_active + S->pending_active + (int32_t)S->pending.size();
     st->bytes_in_flight = S->bytes_in_flight;
     st->ticks = S->ticks;
     st->completed = S->completed;
@@ -705,27 +735,43 @@ int masw_server_run_trace(masw_server* S, int32_t n_requests, const int32_t* n_l
     std::vector<int32_t> slot_q(S->cfg.max_slots, -1);
     int next = 0, done = 0;
     int64_t refused = 0, max_in_flight = 0;
+    bool blocked = false;  // the next arrival was refused: wait for a tick to free room
     const double t0 = now_s();
-    while (done < n_requests) {
+    // admit every request that has arrived, while slots and bytes allow
+    auto admit = [&]() -> int {
         double t = now_s() - t0;
-        if (t > timeout_s) return MASW_ETIMEOUT;
-        while (next < n_requests && arrival_s[next] <= t) {
+        while (next < n_requests && arrival_s[next] <= t && !blocked) {
             int64_t id;
             int rc = masw_server_submit(S, n_layers[next], h + hoff[next], alpha + loff[next],
                                         beta + loff[next], rho + loff[next], n_lambda[next],
                                         lambda + woff[next], &id);
-            if (rc == MASW_EADMIT) {  // wait for slots or bytes to free up
+            if (rc == MASW_EADMIT) {
                 ++refused;
+                blocked = true;
                 break;
             }
             if (rc) return rc;
             slot_q[S->id_slot[id]] = next;
             ++next;
         }
-        max_in_flight = std::max<int64_t>(max_in_flight, S->cfg.max_slots - (int64_t)S->free_slots.size());
-        if (S->n_active + (int)S->pending.size() > 0) {
-            int rc = run_tick(S);
-            if (rc) return rc;
+        max_in_flight =
+            std::max<int64_t>(max_in_flight, S->cfg.max_slots - (int64_t)S->free_slots.size());
+        return MASW_OK;
+    };
+    while (done < n_requests) {
+        if (now_s() - t0 > timeout_s) return MASW_ETIMEOUT;
+        int rc = admit();
+        if (rc) return rc;
+        bool launched = false;
+        if ((rc = tick_launch(S, &launched))) return rc;
+        if (launched) {
+            // the GPU runs the tick; keep admitting into the other upload half
+            while (cudaEventQuery(S->ev) == cudaErrorNotReady) {
+                if ((rc = admit())) return rc;
+                if (now_s() - t0 > timeout_s) return MASW_ETIMEOUT;
+            }
+            if ((rc = tick_finish(S))) return rc;
+            blocked = false;
             double tc = now_s() - t0;
             for (int slot : S->just_done) {
                 int q = slot_q[slot];
@@ -736,6 +782,7 @@ int masw_server_run_trace(masw_server* S, int32_t n_requests, const int32_t* n_l
                 ++done;
             }
         } else if (next < n_requests) {
+            blocked = false;
             double wait = arrival_s[next] - (now_s() - t0);
             if (wait > 0)
                 std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 1e-3)));
