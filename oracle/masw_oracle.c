@@ -14,6 +14,10 @@
  *   Section 2.1: K is the 2(N+1) x 2(N+1) global stiffness matrix of the
  *   stiffness matrix method (N finite layers over a half-space).
  *   Algorithm 2 (Section 2.1): misfit = (1/l) * sum |C_t - C_e| / C_e.
+ *   Higher modes (no paper counterpart): the same scan carried past its first
+ *   change, listing the first M sign changes in order (oracle_scan_changes);
+ *   the Python wrapper labels each with the change in K's negative-eigenvalue
+ *   count (numpy's symmetric eigensolver on the dense K).
  *
  * Deliberately plain: K is assembled as a DENSE matrix and its determinant is
  * taken by dense LU with partial pivoting (sign = parity of row swaps times
@@ -259,6 +263,38 @@ int oracle_scan(int N, const double* h, const double* alpha, const double* beta,
     }
     free(K);
     return status;
+}
+
+/* Algorithm 1 continued past its first change (higher modes): the first
+ * max_changes grid indices n >= 1, in increasing order, whose determinant
+ * sign differs from that of V[n-1], below the scan limit. idx[0..*n_found)
+ * receives them. Returns ORACLE_OK when max_changes were found, else
+ * ORACLE_NO_ROOT (fewer; *n_found may be 0). */
+int oracle_scan_changes(int N, const double* h, const double* alpha, const double* beta,
+                        const double* rho, double lambda, double c0, double dc, int n_c,
+                        int max_changes, int* idx, int* n_found) {
+    double k = 2.0 * M_PI / lambda;
+    *n_found = 0;
+    if (max_changes < 1) return ORACLE_EINVAL;
+    if (!in_domain(N, h, k)) return ORACLE_EINVAL;
+    int n_lim = oracle_scan_limit(beta[N], c0, dc, n_c);
+    int n = 2 * (N + 1);
+    double* K = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    if (!K) return ORACLE_ENOMEM;
+    if (n_lim >= 2) {
+        int s_old, s_new;
+        double la;
+        oracle_assemble(N, h, alpha, beta, rho, k, oracle_grid_velocity(c0, dc, 0), K);
+        oracle_lu_det(n, K, &s_old, &la);
+        for (int j = 1; j < n_lim && *n_found < max_changes; ++j) {
+            oracle_assemble(N, h, alpha, beta, rho, k, oracle_grid_velocity(c0, dc, j), K);
+            oracle_lu_det(n, K, &s_new, &la);
+            if (s_new != s_old) idx[(*n_found)++] = j;
+            s_old = s_new;
+        }
+    }
+    free(K);
+    return *n_found == max_changes ? ORACLE_OK : ORACLE_NO_ROOT;
 }
 
 /* Ragged batch: models are concatenated; model m has n_layers[m] finite

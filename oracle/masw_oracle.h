@@ -32,6 +32,9 @@ int oracle_scan_limit(double beta_hs, double c0, double dc, int n_c);
 int oracle_scan(int N, const double* h, const double* alpha, const double* beta,
                 const double* rho, double lambda, double c0, double dc, int n_c, double* ct,
                 int* idx);
+int oracle_scan_changes(int N, const double* h, const double* alpha, const double* beta,
+                        const double* rho, double lambda, double c0, double dc, int n_c,
+                        int max_changes, int* idx, int* n_found);
 int oracle_dispersion(int n_models, const int* n_layers, const double* h, const double* alpha,
                       const double* beta, const double* rho, const int* n_lambda,
                       const double* lambda, double c0, double dc, int n_c, double* ct,

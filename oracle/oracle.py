@@ -71,6 +71,8 @@ def _load():
     lib.oracle_scan_limit.argtypes = [d, d, d, i]
     lib.oracle_scan.restype = i
     lib.oracle_scan.argtypes = [i, p, p, p, p, d, d, d, i, p, p]
+    lib.oracle_scan_changes.restype = i
+    lib.oracle_scan_changes.argtypes = [i, p, p, p, p, d, d, d, i, i, p, p]
     lib.oracle_dispersion.restype = i
     lib.oracle_dispersion.argtypes = [i, p, p, p, p, p, p, p, d, d, i, p, p, p, i]
     lib.oracle_refine.restype = i
@@ -162,6 +164,35 @@ def scan(h, alpha, beta, rho, lam, c0, dc, n_c) -> tuple[int, float, int]:
     st = _load().oracle_scan(h.size, _ptr(h), _ptr(alpha), _ptr(beta), _ptr(rho), lam, c0,
                              dc, n_c, ctypes.byref(ct), ctypes.byref(idx))
     return st, ct.value, idx.value
+
+
+def negative_eigenvalues(h, alpha, beta, rho, k, c) -> int:
+    """Number of negative eigenvalues of the assembled K(k, c) (numpy's
+    symmetric eigensolver on the oracle's dense matrix)."""
+    return int((np.linalg.eigvalsh(assemble(h, alpha, beta, rho, k, c)) < 0.0).sum())
+
+
+def scan_changes(h, alpha, beta, rho, lam, c0, dc, n_c, max_changes):
+    """Algorithm 1 continued (higher modes): the first max_changes sign
+    changes of det K along the grid, each with the change in the number of
+    negative eigenvalues of K across it (Wittrick-Williams: +1 where a mode of
+    the layered structure is crossed, -1 at a pole, a mode of a clamped
+    layer). Returns (status, idx[max_changes], delta[max_changes]) with -1 /
+    0 padding; status OK when max_changes were found, else NO_ROOT."""
+    h, alpha, beta, rho = _f64(h), _f64(alpha), _f64(beta), _f64(rho)
+    idx = np.full(max_changes, -1, dtype=np.int32)
+    nf = ctypes.c_int()
+    st = _load().oracle_scan_changes(h.size, _ptr(h), _ptr(alpha), _ptr(beta), _ptr(rho), lam,
+                                     c0, dc, n_c, max_changes, _ptr(idx), ctypes.byref(nf))
+    if st not in (OK, NO_ROOT):
+        raise ValueError(f"oracle_scan_changes failed ({st})")
+    k = 2.0 * np.pi / lam
+    delta = np.zeros(max_changes, dtype=np.int32)
+    for m in range(nf.value):
+        n = int(idx[m])
+        delta[m] = (negative_eigenvalues(h, alpha, beta, rho, k, grid_velocity(c0, dc, n))
+                    - negative_eigenvalues(h, alpha, beta, rho, k, grid_velocity(c0, dc, n - 1)))
+    return st, idx, delta
 
 
 def dispersion(models, c0, dc, n_c, n_threads: int = 0):
