@@ -222,6 +222,34 @@ int masw_last_scan_screen(masw_batch* batch, int32_t* n32);
  * precision-0 plan). Synchronises the batch stream. */
 int masw_last_scan_unresolved(const masw_batch* batch, int32_t* n);
 
+/* ---------------------------------------------------------------------
+ * Higher modes. The paper keeps only the first sign change (Algorithm 1,
+ * Section 2.1) and names no higher modes; this carries the same scan past it.
+ * --------------------------------------------------------------------- */
+#define MASW_MAX_CHANGES 15
+
+/* The first max_changes (1..MASW_MAX_CHANGES) sign changes of det K(k, V[n])
+ * along the grid for every item: the n >= 1, in increasing order below the
+ * scan limit (V[n] < beta_halfspace), whose sign differs from V[n-1]'s
+ * (Algorithm 1 stops at the first). Each change carries delta_count, the
+ * change in the number of negative eigenvalues of K across it
+ * (Wittrick-Williams): +1 where a mode of the layered structure is crossed
+ * (a root of det K: the fundamental, then higher modes), -1 at a pole (a
+ * mode of one layer with both faces clamped, where det K changes sign
+ * through infinity), other values where both fall between two grid points.
+ * Outputs are [n_items][max_changes] in item order (host or device buffers
+ * per out_mem_space, any may be NULL): ct = V[n] (NaN when fewer changes),
+ * ct_idx = n (-1), status MASW_FOUND / MASW_NO_ROOT, delta_count (0). The
+ * first change is masw_dispersion's (the batch plan); from one point below it
+ * the scan runs in FP64 at every grid point (no FP32 screen: next to a pole an
+ * FP32 error can hide a root-pole pair inside one grid interval). It also
+ * leaves masw_dispersion's outputs of the batch updated. Runs on the batch
+ * stream; synchronises it for host outputs. Device buffers of n_items x
+ * max_changes are allocated on first use. MASW_EINVAL for max_changes out of
+ * range. */
+int masw_dispersion_changes(masw_batch* batch, int32_t max_changes, double* ct, int32_t* ct_idx,
+                            int32_t* status, int32_t* delta_count, int32_t out_mem_space);
+
 /* Items of the most recent counting-search scan (plan precision 2) that fell
  * back to the linear FP32 screen (change above the pole-free bound, at V[0],
  * or an even count jump); -1 for other plans. Synchronises the batch stream. */

@@ -74,6 +74,13 @@ struct masw_batch {
     int32_t* d_unres = nullptr;
     int32_t* d_fallback = nullptr;
     int32_t* d_counters = nullptr;  // SCAN_COUNTERS
+    // higher modes (allocated on first use, for chg_cap changes per item)
+    int chg_cap = 0;
+    double* d_chg_ct = nullptr;
+    int32_t* d_chg_idx = nullptr;
+    int32_t* d_chg_status = nullptr;
+    int32_t* d_chg_delta = nullptr;
+    int32_t* d_chg_counters = nullptr;
 
     masw_plan plan{};
     cudaGraphExec_t graph = nullptr;
@@ -275,7 +282,9 @@ static void free_batch(masw_batch* B) {
                     B->d_item_model, B->d_order_sorted, B->d_order_natural, B->d_grad_off,
                     B->d_counter, B->d_ct, B->d_idx, B->d_status, B->d_croot, B->d_rows, B->d_bs,
                     B->d_dphi, B->d_ce, B->d_misfit, B->d_gb, B->d_gh, B->d_layers32,
-                    B->d_n32, B->d_ref, B->d_unres, B->d_fallback, B->d_counters};
+                    B->d_n32, B->d_ref, B->d_unres, B->d_fallback, B->d_counters,
+                    B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta,
+                    B->d_chg_counters};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete B;
@@ -621,6 +630,42 @@ int masw_dispersion(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* status,
     int rc = run_scan(B);
     if (rc) return rc;
     return finish_outputs(B, ct, ct_idx, status);
+}
+
+int masw_dispersion_changes(masw_batch* B, int32_t max_changes, double* ct, int32_t* ct_idx,
+                            int32_t* status, int32_t* delta_count, int32_t out_mem_space) {
+    if (!B || max_changes < 1 || max_changes > MASW_MAX_CHANGES ||
+        (out_mem_space != MASW_HOST && out_mem_space != MASW_DEVICE))
+        return MASW_EINVAL;
+    const size_t nw = B->n_items, ne = nw * (size_t)max_changes;
+    if (max_changes > B->chg_cap) {
+        void* old[] = {B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta};
+        for (void* q : old)
+            if (q) cudaFree(q);
+        B->d_chg_ct = nullptr;
+        B->d_chg_idx = B->d_chg_status = B->d_chg_delta = nullptr;
+        B->chg_cap = 0;
+        if (dev_alloc(&B->d_chg_ct, ne) || dev_alloc(&B->d_chg_idx, ne) ||
+            dev_alloc(&B->d_chg_status, ne) || dev_alloc(&B->d_chg_delta, ne))
+            return MASW_ENOMEM;
+        B->chg_cap = max_changes;
+    }
+    if (!B->d_chg_counters && dev_alloc(&B->d_chg_counters, 1)) return MASW_ENOMEM;
+    // the first change: Algorithm 1 with the batch plan (an FP64 decision)
+    int rc0 = run_scan(B);
+    if (rc0) return rc0;
+    CK(launch_changes(B->dev(B->plan.ordered != 0), to_scan_plan(B, B->plan), max_changes,
+                      B->d_idx, B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta,
+                      B->d_chg_counters, B->stream));
+    bool sync = false;
+    int rc;
+    if ((rc = copy_out(ct, B->d_chg_ct, ne, B->stream, &sync)) ||
+        (rc = copy_out(ct_idx, B->d_chg_idx, ne, B->stream, &sync)) ||
+        (rc = copy_out(status, B->d_chg_status, ne, B->stream, &sync)) ||
+        (rc = copy_out(delta_count, B->d_chg_delta, ne, B->stream, &sync)))
+        return rc;
+    if (sync) CK(cudaStreamSynchronize(B->stream));
+    return MASW_OK;
 }
 
 int masw_dispersion_plain(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* status,

@@ -258,6 +258,38 @@ __device__ inline int det_inertia(const double* __restrict__ lay, int N, double 
     return cnt;
 }
 
+// Sign of det K (as det_sign: 0 for an exact zero or a failed rescaling) and
+// the number of its negative eigenvalues (as det_inertia: -1 for a failed
+// rescaling) in one pass. Requires c < beta_halfspace.
+__device__ inline int det_sign_count(const double* __restrict__ lay, int N, double k, double c,
+                                     int* count) {
+    double c2 = c * c;
+    HState st{0.0, 0.0, 0.0, 1.0};
+    int sg = 1, cnt = 0;
+    double sv[3];
+    for (int j = 0; j < N; ++j) {
+        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2);
+        double f = st.w * n.Dh;
+        bool ok;
+        double det = schur_layer(st, n, &ok, sv);
+        sg *= sgn(det);
+        cnt += det < 0.0 ? 1 : (det > 0.0 ? (((sv[0] < 0.0) != (f < 0.0)) ? 2 : 0) : 1);
+        if (!ok) {
+            *count = -1;
+            return 0;
+        }
+    }
+    HalfNum hn = halfspace_numerators(lay + N * LAYER_STRIDE, c2);
+    double f = st.w * hn.den;
+    double s00 = fma(hn.den, st.p00, st.w * hn.m00);
+    double s01 = fma(hn.den, st.p01, st.w * hn.m01);
+    double s11 = fma(hn.den, st.p11, st.w * hn.m11);
+    double det = fma(s00, s11, -s01 * s01);
+    cnt += det < 0.0 ? 1 : (det > 0.0 ? (((s00 < 0.0) != (f < 0.0)) ? 2 : 0) : 1);
+    *count = cnt;
+    return sg * sgn(det);
+}
+
 // Sign and ln|det K| including the dropped factor k^(2(N+1)) (parity checks).
 __device__ inline int det_sign_log(const double* __restrict__ lay, int N, double k, double c,
                                    double* log_abs) {

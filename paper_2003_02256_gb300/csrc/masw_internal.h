@@ -50,6 +50,14 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
                                int search, int item_begin, int item_end, cudaStream_t s,
                                cudaEvent_t* phase_ev);
 
+// Algorithm 1 continued: the first M sign changes per item with their
+// negative-eigenvalue count changes, scanned in FP64 from one point below the
+// first change `first` (the batch scan's index, -1: none); outputs
+// [n_items][M]; counter: 1 (masw_kernels.cu).
+cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const int32_t* first,
+                           double* ct, int32_t* idx, int32_t* status, int32_t* delta,
+                           int32_t* counter, cudaStream_t s);
+
 cudaError_t launch_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p, int32_t* counter,
                         int item_begin, int item_end, cudaStream_t s);
 cudaError_t launch_det_eval(const DevBatch& b, int n, const int32_t* item, const double* c,

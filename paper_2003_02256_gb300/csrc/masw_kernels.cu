@@ -716,6 +716,108 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ higher modes
+//
+// Algorithm 1 carried past its first change: the first M sign changes of
+// det K along the grid (V[0] upward, below the scan limit), each labelled with
+// the change in K's negative-eigenvalue count across it (Wittrick-Williams:
+// +1 where a mode of the layered structure is crossed, a root of det K; -1 at
+// a pole, a mode of a clamped layer). The first change is the batch scan's
+// result (an FP64 decision); from one point below it on, changes_scan64_kernel
+// scans in FP64 itself. An FP32 screen is not used past the first change:
+// next to a pole an FP32 rounding error can move the pole across a grid point,
+// and a root-pole pair inside one grid interval then vanishes from the FP32
+// signs without any sign or count change at the points around it.
+
+struct ChangesOut {
+    double* ct;      // [n_items][M]
+    int32_t* idx;
+    int32_t* status;
+    int32_t* delta;
+};
+
+__device__ __forceinline__ void write_change(const DevBatch& b, const ChangesOut& o, size_t e, int n,
+                                             int delta) {
+    if (n >= 0) {
+        o.ct[e] = grid_c(b.c0, b.dc, n);
+        o.idx[e] = n;
+        o.status[e] = 0;
+        o.delta[e] = delta;
+    } else {
+        o.ct[e] = __longlong_as_double(0x7ff8000000000000LL);
+        o.idx[e] = -1;
+        o.status[e] = 1;
+        o.delta[e] = 0;
+    }
+}
+
+// One warp per item (persistent, popping b.order): FP64 sign and count at
+// 32 consecutive points per chunk from first[item] - 1; a change at n needs
+// n > the start point. Items whose first change is -1 have none.
+__global__ void __launch_bounds__(256) changes_scan64_kernel(DevBatch b, ChangesOut o, int M,
+                                                             const int32_t* __restrict__ first,
+                                                             int32_t* counter) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= b.n_items) return;
+        const int item = b.order[t];
+        const size_t e0 = (size_t)item * M;
+        const int n1 = first[item];
+        int found = 0;
+        if (n1 >= 1) {
+            const int m = b.item_model[item];
+            const int lo = b.model_loff[m];
+            const int N = b.model_loff[m + 1] - lo - 1;
+            const double* lay = b.layers + (size_t)lo * LAYER_STRIDE;
+            const double k = b.k[item];
+            const int nlim = b.model_nlim[m];
+            const int start = n1 - 1;
+            int carry_s = 0, carry_c = 0;
+            for (int base = start; base < nlim && found < M; base += 32) {
+                const int n = base + lane;
+                int cnt = 0;
+                const int sg = n < nlim ? det_sign_count(lay, N, k, grid_c(b.c0, b.dc, n), &cnt) : 0;
+                int ps = __shfl_up_sync(FULL, sg, 1), pc = __shfl_up_sync(FULL, cnt, 1);
+                if (lane == 0) {
+                    ps = carry_s;
+                    pc = carry_c;
+                }
+                const int d = (cnt >= 0 && pc >= 0) ? cnt - pc : 0;
+                unsigned msk = __ballot_sync(FULL, n > start && n < nlim && sg != ps);
+                while (msk && found < M) {
+                    const int l = __ffs(msk) - 1;
+                    const int dl = __shfl_sync(FULL, d, l);
+                    if (lane == 0) write_change(b, o, e0 + found, base + l, dl);
+                    ++found;
+                    msk &= msk - 1;
+                }
+                carry_s = __shfl_sync(FULL, sg, 31);
+                carry_c = __shfl_sync(FULL, cnt, 31);
+            }
+        }
+        if (lane == 0)
+            for (int mi = found; mi < M; ++mi) write_change(b, o, e0 + mi, -1, 0);
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const int32_t* first,
+                           double* ct, int32_t* idx, int32_t* status, int32_t* delta,
+                           int32_t* counter, cudaStream_t s) {
+    if (b.n_items == 0) return cudaSuccess;
+    if (M < 1) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const int wpb = p.warps_per_block;
+    ChangesOut o{ct, idx, status, delta};
+    changes_scan64_kernel<<<std::max(1, std::min(p.blocks, (b.n_items + wpb - 1) / wpb)), 32 * wpb,
+                            0, s>>>(b, o, M, first, counter);
+    return cudaGetLastError();
+}
+
 // -------------------------------------------------------------- det eval
 
 __global__ void det_eval_kernel(DevBatch b, int n, const int32_t* __restrict__ item,

@@ -74,6 +74,7 @@ def load():
         "masw_batch_info": [p, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "masw_dispersion": [p, p, p, p, i32],
         "masw_dispersion_plain": [p, p, p, p, i32],
+        "masw_dispersion_changes": [p, i32, p, p, p, p, i32],
         "masw_misfit": [p, p, i32, d, p],
         "masw_misfit_grad": [p, p, i32, d, p, p, p],
         "masw_roots": [p, p],
@@ -192,6 +193,19 @@ def dispersion_plain(handle, ct, ct_idx, status):
     space = _space(next(x for x in (ct, ct_idx, status) if x is not None))
     _check(load().masw_dispersion_plain(ctypes.c_void_p(handle), _ptr(ct), _ptr(ct_idx),
                                         _ptr(status), space), "masw_dispersion_plain")
+
+
+MAX_CHANGES = 15
+
+
+def dispersion_changes(handle, max_changes, ct, ct_idx, status, delta_count):
+    """Algorithm 1 continued: the first max_changes sign changes per item
+    with the change in K's negative-eigenvalue count across each
+    (masw_dispersion_changes); outputs [n_items * max_changes]."""
+    space = _space(next(x for x in (ct, ct_idx, status, delta_count) if x is not None))
+    _check(load().masw_dispersion_changes(ctypes.c_void_p(handle), int(max_changes), _ptr(ct),
+                                          _ptr(ct_idx), _ptr(status), _ptr(delta_count), space),
+           "masw_dispersion_changes")
 
 
 def misfit(handle, ce, kind, sigma, out):
@@ -338,6 +352,16 @@ class Batch:
         st = np.empty(self.n_items, dtype=np.int32)
         (dispersion_plain if plain else dispersion)(self.handle, ct, idx, st)
         return ct, idx, st
+
+    def changes(self, max_changes: int):
+        """(ct, idx, status, delta_count), each of shape (n_items, max_changes)."""
+        shape = (self.n_items, int(max_changes))
+        ct = np.empty(shape)
+        idx = np.empty(shape, dtype=np.int32)
+        st = np.empty(shape, dtype=np.int32)
+        dl = np.empty(shape, dtype=np.int32)
+        dispersion_changes(self.handle, max_changes, ct, idx, st, dl)
+        return ct, idx, st, dl
 
     def roots(self):
         out = np.empty(self.n_items)
