@@ -345,6 +345,23 @@ def run_extras(args, masw, torch):
                                          "50..500 times (0.5 m or 2000 m on 2-layer models); "
                                          "c grid 50..1200 step 0.25", "targets_m_s": stress}
 
+    # higher modes: the first 3 sign changes per item (FP64 past the first)
+    hm, hg = W.uniform_batch()
+    with masw.Batch(hm, hg) as b:
+        _, hidx, hst, hdl = b.changes(3)
+        hms = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.changes(3)
+            hms.append(time.perf_counter() - t0)
+    out["higher_modes"] = {"workload": "uniform_batch (1024 models), first 3 sign changes per item, "
+                                       "host outputs", "curves_per_s": hm.n_models / min(hms),
+                           "ms": 1e3 * min(hms),
+                           "changes_found_fraction": float(np.mean(hst == 0)),
+                           "roots_fraction_of_found": float(np.mean(hdl[hst == 0] == 1)),
+                           "poles_fraction_of_found": float(np.mean(hdl[hst == 0] == -1))}
+
     # first use: batch creation (upload, records, graph capture) and the first
     # scan of a fresh batch vs the warm median (CUDA context and library
     # already loaded in this process)
