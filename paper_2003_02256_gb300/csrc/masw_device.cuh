@@ -61,6 +61,25 @@ __device__ __forceinline__ bool pow2_normaliser(double x, double* scale) {
     return true;
 }
 
+// v * 2^delta by adding delta to the exponent field, on the integer pipe
+// (an FP64 multiply, even predicated off, takes a slot of the FP64 pipe, the
+// scarce one). Exactly the product for a normal v and a normal result. Zero,
+// subnormals and inf/NaN are returned unchanged, a result below the normal
+// range flushes to a signed zero and one above it saturates to a signed
+// infinity; in the recurrence v / w stays within a few hundred binades of 1
+// (stiffness ratios), so neither end is reached for finite inputs.
+__device__ __forceinline__ double scale_pow2(double v, int delta) {
+    const long long bits = __double_as_longlong(v);
+    const int e = (int)((bits >> 52) & 0x7ff);
+    const int ne = e + delta;
+    const long long sign = bits & (long long)0x8000000000000000ULL;
+    long long out = bits + ((long long)delta << 52);
+    out = ne <= 0 ? sign : out;
+    out = ne >= 0x7ff ? (sign | 0x7ff0000000000000LL) : out;
+    out = (e == 0 || e == 0x7ff) ? bits : out;
+    return __longlong_as_double(out);
+}
+
 // ----------------------------------------------------------- plain doubles
 
 struct Wave { double E, C, Sd, Sm; };
@@ -179,12 +198,14 @@ __device__ __forceinline__ double schur_layer(HState& st, const LayerNum& n, boo
     double p01 = fma(-n.n01, det, -w * q01);
     double p11 = fma(n.n11, det, -w * q11);
     double wn = n.Dh * det;
-    double sc;
+    double sc = 1.0;
     *ok = pow2_normaliser(wn, &sc);
-    st.p00 = p00 * sc;
-    st.p01 = p01 * sc;
-    st.p11 = p11 * sc;
-    st.w = wn * sc;
+    // scale by the power of two sc = 2^delta on the integer pipe
+    const int delta = 1023 - (int)((__double_as_longlong(wn) >> 52) & 0x7ff);
+    st.p00 = scale_pow2(p00, delta);
+    st.p01 = scale_pow2(p01, delta);
+    st.p11 = scale_pow2(p11, delta);
+    st.w = scale_pow2(wn, delta);
     return det;
 }
 

@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
 // where the count jumps by an even number go to the fallback list, with the
 // grid index to scan from in n32; uncertified items go to the FP64 re-scan
 // with V[0]'s sign. Certified items keep SCREEN_COUNTED in n32.
-__global__ void __launch_bounds__(128) count_certify_kernel(DevBatch b, const float* __restrict__ layers32,
+__global__ void __launch_bounds__(128, 7) count_certify_kernel(DevBatch b, const float* __restrict__ layers32,
                                                             ScanOut o, int32_t* __restrict__ n32,
                                                             int32_t* ref_sign, int32_t* unresolved,
                                                             int32_t* n_unresolved, int32_t* fallback,
