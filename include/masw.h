@@ -255,6 +255,14 @@ int masw_dispersion_changes(masw_batch* batch, int32_t max_changes, double* ct, 
  * or an even count jump); -1 for other plans. Synchronises the batch stream. */
 int masw_last_scan_fallback(const masw_batch* batch, int32_t* n);
 
+/* The library's own FP64 exponential (e^x for x <= 0, a table-driven method;
+ * used for e^(-k h w) in the element stiffness) and CUDA's exp at the same n
+ * host points x (all <= 0, else MASW_EINVAL), into host arrays y_lib and
+ * y_cuda; a diagnostic for testing its error bound. No paper counterpart.
+ * Allocates and frees a device buffer of 3n doubles; synchronises
+ * cuda_stream. */
+int masw_exp_check(int32_t n, const double* x, double* y_lib, double* y_cuda, void* cuda_stream);
+
 /* FP64 fused multiply-add throughput of this GPU in flop/s (2 per DFMA),
  * measured by a dependent-chain microbenchmark on `cuda_stream`. */
 int masw_fp64_peak(void* cuda_stream, double* flops);

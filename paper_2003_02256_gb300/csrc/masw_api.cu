@@ -668,6 +668,26 @@ int masw_dispersion_changes(masw_batch* B, int32_t max_changes, double* ct, int3
     return MASW_OK;
 }
 
+int masw_exp_check(int32_t n, const double* x, double* y_lib, double* y_cuda, void* cuda_stream) {
+    if (n < 0 || (n > 0 && (!x || !y_lib || !y_cuda))) return MASW_EINVAL;
+    for (int32_t i = 0; i < n; ++i)
+        if (!(x[i] <= 0.0)) return MASW_EINVAL;
+    if (n == 0) return MASW_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    double* d = nullptr;
+    if (dev_alloc(&d, 3 * (size_t)n)) return MASW_ENOMEM;
+    cudaError_t e = cudaMemcpyAsync(d, x, n * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_exp_check(n, d, d + n, d + 2 * (size_t)n, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(y_lib, d + n, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(y_cuda, d + 2 * (size_t)n, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    CK(e);
+    return MASW_OK;
+}
+
 int masw_dispersion_plain(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* status,
                           int32_t out_mem_space) {
     if (!B || (out_mem_space != MASW_HOST && out_mem_space != MASW_DEVICE)) return MASW_EINVAL;

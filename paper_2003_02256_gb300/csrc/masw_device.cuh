@@ -80,6 +80,79 @@ __device__ __forceinline__ double scale_pow2(double v, int delta) {
     return __longlong_as_double(out);
 }
 
+// ------------------------------------------------- e^x for x <= 0 (FP64)
+//
+// Table-driven exponential after P. T. P. Tang, "Table-driven implementation
+// of the exponential function in IEEE floating-point arithmetic" (ACM TOMS
+// 15(2), 1989), restated for FMA hardware:
+//   x = (64 m + j) ln2/64 + r,  j = 0..63,  |r| <= ln2/128 (+ rounding),
+//   e^x = 2^m * 2^(j/64) * e^r.
+// n = 64 m + j is x * 64/ln2 rounded to nearest with the 1.5 * 2^52 shifter;
+// r = x - n ln2/64 in two FMAs with ln2/64 split into its nearest double and
+// the remainder; e^r - 1 by its Taylor polynomial of degree 6 (truncation
+// below |r|^7/7! < 1e-19); 2^(j/64) from a table of the nearest doubles
+// (computed with 60-digit arithmetic, checked by a CPU test); 2^m added to the
+// exponent field. 11 FP64 operations. The library's e^(-k h w) only needs
+// x <= 0; below -708 (under the smallest normal double) it returns 0.
+static __device__ const double EXP2_J64[64] = {
+    0x1.0000000000000p+0, 0x1.02c9a3e778061p+0,
+    0x1.059b0d3158574p+0, 0x1.0874518759bc8p+0,
+    0x1.0b5586cf9890fp+0, 0x1.0e3ec32d3d1a2p+0,
+    0x1.11301d0125b51p+0, 0x1.1429aaea92de0p+0,
+    0x1.172b83c7d517bp+0, 0x1.1a35beb6fcb75p+0,
+    0x1.1d4873168b9aap+0, 0x1.2063b88628cd6p+0,
+    0x1.2387a6e756238p+0, 0x1.26b4565e27cddp+0,
+    0x1.29e9df51fdee1p+0, 0x1.2d285a6e4030bp+0,
+    0x1.306fe0a31b715p+0, 0x1.33c08b26416ffp+0,
+    0x1.371a7373aa9cbp+0, 0x1.3a7db34e59ff7p+0,
+    0x1.3dea64c123422p+0, 0x1.4160a21f72e2ap+0,
+    0x1.44e086061892dp+0, 0x1.486a2b5c13cd0p+0,
+    0x1.4bfdad5362a27p+0, 0x1.4f9b2769d2ca7p+0,
+    0x1.5342b569d4f82p+0, 0x1.56f4736b527dap+0,
+    0x1.5ab07dd485429p+0, 0x1.5e76f15ad2148p+0,
+    0x1.6247eb03a5585p+0, 0x1.6623882552225p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.6dfb23c651a2fp+0,
+    0x1.71f75e8ec5f74p+0, 0x1.75feb564267c9p+0,
+    0x1.7a11473eb0187p+0, 0x1.7e2f336cf4e62p+0,
+    0x1.82589994cce13p+0, 0x1.868d99b4492edp+0,
+    0x1.8ace5422aa0dbp+0, 0x1.8f1ae99157736p+0,
+    0x1.93737b0cdc5e5p+0, 0x1.97d829fde4e50p+0,
+    0x1.9c49182a3f090p+0, 0x1.a0c667b5de565p+0,
+    0x1.a5503b23e255dp+0, 0x1.a9e6b5579fdbfp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b33a2b84f15fbp+0,
+    0x1.b7f76f2fb5e47p+0, 0x1.bcc1e904bc1d2p+0,
+    0x1.c199bdd85529cp+0, 0x1.c67f12e57d14bp+0,
+    0x1.cb720dcef9069p+0, 0x1.d072d4a07897cp+0,
+    0x1.d5818dcfba487p+0, 0x1.da9e603db3285p+0,
+    0x1.dfc97337b9b5fp+0, 0x1.e502ee78b3ff6p+0,
+    0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0,
+    0x1.f50765b6e4540p+0, 0x1.fa7c1819e90d8p+0,
+};
+constexpr double INV_LN2_64 = 0x1.71547652b82fep+6;   // 64 / ln 2
+constexpr double LN2_64_HI = 0x1.62e42fefa39efp-7;    // ln 2 / 64, nearest double
+constexpr double LN2_64_LO = 0x1.abc9e3b39803fp-62;   // ln 2 / 64 - LN2_64_HI
+
+__device__ __forceinline__ double exp_neg(double x) {
+    const double shifter = 6755399441055744.0;  // 1.5 * 2^52
+    const double d = fma(x, INV_LN2_64, shifter);
+    const double n = d - shifter;
+    const int ni = __double2loint(d);  // n as an integer (low word of d)
+    double r = fma(-n, LN2_64_HI, x);
+    r = fma(-n, LN2_64_LO, r);
+    double p = fma(r, inv_fact(6), inv_fact(5));
+    p = fma(p, r, inv_fact(4));
+    p = fma(p, r, inv_fact(3));
+    p = fma(p, r, inv_fact(2));
+    p = fma(p, r, 1.0);
+    const double em1 = p * r;  // e^r - 1
+    const int j = ni & 63;
+    const int m = (ni - j) / 64;
+    const double t = __ldg(&EXP2_J64[j]);
+    const double y = fma(t, em1, t);  // 2^(j/64) e^r, in [0.99, 2)
+    const double out = __longlong_as_double(__double_as_longlong(y) + ((long long)m << 52));
+    return x < -708.0 ? 0.0 : out;
+}
+
 // ----------------------------------------------------------- plain doubles
 
 struct Wave { double E, C, Sd, Sm; };
@@ -118,7 +191,7 @@ __device__ __forceinline__ Wave wave_fns(double kh, double w2) {
     } else if (w2 > 0.0) {
         double rw = rsqrt(w2);
         double w = w2 * rw;
-        double E = exp(-kh * w);
+        double E = exp_neg(-kh * w);
         double E2 = E * E;
         double t = fma(-0.5, E2, 0.5);
         o.E = E;

@@ -73,6 +73,8 @@ cudaError_t launch_grad_reduce(const DevBatch& b, const double* rows, const doub
 cudaError_t launch_update_beta_h(const DevBatch& b, const double* h, const double* beta,
                                  double* layers, float* layers32, int32_t* nlim, int32_t* err,
                                  cudaStream_t s);
+cudaError_t launch_exp_check(int n, const double* x, double* y_lib, double* y_cuda,
+                             cudaStream_t s);
 cudaError_t launch_fp64_peak(int blocks, int threads, int iters, double* sink, cudaStream_t s);
 
 }  // namespace masw

@@ -818,6 +818,24 @@ cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const in
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ math check
+
+// The library's e^x (exp_neg, x <= 0) beside CUDA's exp at the same points.
+__global__ void exp_check_kernel(int n, const double* __restrict__ x, double* y_lib,
+                                 double* y_cuda) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    y_lib[i] = exp_neg(x[i]);
+    y_cuda[i] = exp(x[i]);
+}
+
+cudaError_t launch_exp_check(int n, const double* x, double* y_lib, double* y_cuda,
+                             cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    exp_check_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, x, y_lib, y_cuda);
+    return cudaGetLastError();
+}
+
 // -------------------------------------------------------------- det eval
 
 __global__ void det_eval_kernel(DevBatch b, int n, const int32_t* __restrict__ item,

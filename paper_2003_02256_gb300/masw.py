@@ -291,6 +291,18 @@ def last_scan_fallback(handle) -> int:
     return n.value
 
 
+def exp_check(x, stream=None):
+    """(library e^x, CUDA exp(x)) at host points x <= 0 (masw_exp_check)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y_lib = np.empty_like(x)
+    y_cuda = np.empty_like(x)
+    f = load().masw_exp_check
+    f.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    _check(f(x.size, _ptr(x), _ptr(y_lib), _ptr(y_cuda), _stream_handle(stream)), "masw_exp_check")
+    return y_lib, y_cuda
+
+
 def fp64_peak(stream=None) -> float:
     f = ctypes.c_double()
     _check(load().masw_fp64_peak(_stream_handle(stream), ctypes.byref(f)), "masw_fp64_peak")
