@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libmasw.so")
 SOURCES = ["masw_kernels.cu", "masw_api.cu", "masw_noalloc.cu", "masw_serve.cu"]
-HEADERS = ["masw_device.cuh", "masw_adjoint.cuh", "masw_internal.h", "masw_screen.cuh"]
+HEADERS = ["masw_device.cuh", "masw_adjoint.cuh", "masw_internal.h", "masw_screen.cuh",
+           "masw_count.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include")]

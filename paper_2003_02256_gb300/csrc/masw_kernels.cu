@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "masw_adjoint.cuh"
+#include "masw_count.cuh"
 #include "masw_device.cuh"
 #include "masw_internal.h"
 #include "masw_screen.cuh"
@@ -465,32 +466,21 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
     }
 }
 
-// Counting search and its FP64 certificate (plan precision 2), fused, two
-// lanes per item (natural item order: a warp's 16 items share a model and
-// have adjacent wavelengths, so their branches agree). Fusing lets warps in
-// the FP32 search and warps in the FP64 certificate share an SM: the two use
-// different pipes.
-//  * Search. Inside the pole-free range [0, npf) of pole_free_points_f the
-//    FP32 negative-eigenvalue count (inertia_f) is a non-decreasing step
-//    function of the grid index, 0 at c = 0. The pair evaluates the top of
-//    the range and its midpoint, then splits the bracket in three per step
-//    (one point per lane): about log3(npf) steps instead of a linear walk.
-//    An odd count at the first nonzero point is Algorithm 1's first change.
-//  * Certificate. The FP64 count (det_inertia) is 0 at V[n-1] (so 0, and
-//    V[0]'s sign, at every point below) and odd at V[n] (the sign differs).
-//    When the FP32 count was off by one next to the change (count 0 at both
-//    points: the change is higher; nonzero at V[n-1]: lower), the pair takes
-//    one FP64 step of two points in that direction, inside the range.
-// Items whose change lies above the range (count 0 at its top), at V[0], or
-// where the count jumps by an even number go to the fallback list, with the
-// grid index to scan from in n32; uncertified items go to the FP64 re-scan
-// with V[0]'s sign. Certified items keep SCREEN_COUNTED in n32.
+// Counting search and its FP64 certificate (plan precision 2) fused in one
+// kernel, two lanes per item (count_certify_pair; natural item order: a
+// warp's 16 items share a model and have adjacent wavelengths, so their
+// branches agree). Fusing lets warps in the FP32 search and warps in the FP64
+// certificate share an SM: the two use different pipes. Items whose change
+// lies above the pole-free range, at V[0], or where the count jumps by an
+// even number go to the fallback list, with the grid index to scan from in
+// n32; uncertified items go to the FP64 re-scan with V[0]'s sign. Certified
+// items keep SCREEN_COUNTED in n32.
 __global__ void __launch_bounds__(128, 7) count_certify_kernel(DevBatch b, const float* __restrict__ layers32,
-                                                            ScanOut o, int32_t* __restrict__ n32,
-                                                            int32_t* ref_sign, int32_t* unresolved,
-                                                            int32_t* n_unresolved, int32_t* fallback,
-                                                            int32_t* n_fallback, int item_begin,
-                                                            int item_end) {
+                                                               ScanOut o, int32_t* __restrict__ n32,
+                                                               int32_t* ref_sign, int32_t* unresolved,
+                                                               int32_t* n_unresolved, int32_t* fallback,
+                                                               int32_t* n_fallback, int item_begin,
+                                                               int item_end) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int item = item_begin + (t >> 1);
     if (item >= item_end) return;  // both lanes of a pair leave together
@@ -507,98 +497,20 @@ __global__ void __launch_bounds__(128, 7) count_certify_kernel(DevBatch b, const
         }
         return;
     }
-    const float* lay32 = layers32 + (size_t)lo_rec * LAYER_STRIDE32;
-    const float kf = (float)b.k[item];
-    const float c0f = (float)b.c0, dcf = (float)b.dc;
-    const int npf = pole_free_points_f(lay32, N, kf, c0f, dcf, nlim);
-    int n = -1, start = 0;
-    if (npf >= 1) {
-        int lo = -1, hi = npf - 1;
-        const int mid = (hi - 1) >> 1;  // midpoint of (lo, hi); -1 when hi == 0
-        const int pt = half ? mid : hi;
-        const int cnt = pt >= 0 ? inertia_f(lay32, N, kf, fmaf((float)pt, dcf, c0f)) : 0;
-        const int oth = __shfl_xor_sync(pair, cnt, 1);
-        const int c_top = half ? oth : cnt, c_mid = half ? cnt : oth;
-        if (c_top == 0) {
-            start = npf;  // no mode below the bound: scan linearly above it
-        } else {
-            int chi = c_top;
-            if (mid >= 0) {
-                if (c_mid >= 1) {
-                    hi = mid;
-                    chi = c_mid;
-                } else {
-                    lo = mid;
-                }
-            }
-            while (hi - lo > 1) {
-                const int len = hi - lo;
-                const int a = lo + (len + 1) / 3, bq = lo + (2 * len + 1) / 3;  // lo < a <= bq < hi
-                const int q = half ? bq : a;
-                const int c = inertia_f(lay32, N, kf, fmaf((float)q, dcf, c0f));
-                const int co = __shfl_xor_sync(pair, c, 1);
-                const int ca = half ? co : c, cb = half ? c : co;
-                if (ca >= 1) {
-                    hi = a;
-                    chi = ca;
-                } else if (cb >= 1) {
-                    lo = a;
-                    hi = bq;
-                    chi = cb;
-                } else {
-                    lo = bq;
-                }
-            }
-            if (hi >= 1 && (chi & 1)) n = hi;
-        }
-    }
-    if (n < 1) {
-        if (!half) {
-            n32[item] = start;
-            fallback[atomicAdd(n_fallback, 1)] = item;
-        }
-        return;
-    }
     const double* lay = b.layers + (size_t)lo_rec * LAYER_STRIDE;
-    const double k = b.k[item];
-    const int v = det_inertia(lay, N, k, grid_c(b.c0, b.dc, n - 1 + half));
-    const int vo = __shfl_xor_sync(pair, v, 1);
-    const int va = half ? vo : v;  // V[n-1]
-    const int vb = half ? v : vo;  // V[n]
-    int cert = (va == 0 && vb > 0 && (vb & 1)) ? n : -1;
-    if (cert < 0 && va >= 0 && vb >= 0) {
-        const bool up = va == 0 && vb == 0;
-        const bool down = va > 0 && n >= 3;
-        if (up || down) {
-            const int p = (up ? n + 1 : n - 3) + half;
-            const int w = p < nlim ? det_inertia(lay, N, k, grid_c(b.c0, b.dc, p)) : -1;
-            const int wo = __shfl_xor_sync(pair, w, 1);
-            const int c_lo = half ? wo : w, c_hi = half ? w : wo;
-            if (up) {
-                // count 0 at n; first nonzero at n+1, or at n+2 with n+1 inside the range
-                if (c_lo > 0) {
-                    if (c_lo & 1) cert = n + 1;
-                } else if (c_lo == 0 && c_hi > 0 && (c_hi & 1) && n + 1 < npf) {
-                    cert = n + 2;
-                }
-            } else {
-                // count nonzero at n-1; first nonzero at n-1 or n-2
-                if (c_hi == 0) {
-                    if (va & 1) cert = n - 1;
-                } else if (c_hi > 0 && c_lo == 0 && (c_hi & 1)) {
-                    cert = n - 2;
-                }
-            }
-        }
-    }
+    const PairCount r = count_certify_pair(layers32 + (size_t)lo_rec * LAYER_STRIDE32, lay, N,
+                                           b.k[item], b.c0, b.dc, nlim, half, pair);
     if (half) return;
-    if (cert >= 1) {
-        n32[item] = cert | SCREEN_COUNTED;
-        write_result(b, o, item, cert);
-    } else {
-        n32[item] = n;
-        ref_sign[item] = det_sign(lay, N, k, grid_c(b.c0, b.dc, 0));
+    if (r.cert >= 1) {
+        n32[item] = r.cert | SCREEN_COUNTED;
+        write_result(b, o, item, r.cert);
+    } else if (r.n >= 1) {
+        n32[item] = r.n;
+        ref_sign[item] = det_sign(lay, N, b.k[item], grid_c(b.c0, b.dc, 0));
         unresolved[atomicAdd(n_unresolved, 1)] = item;
+    } else {
+        n32[item] = r.start;
+        fallback[atomicAdd(n_fallback, 1)] = item;
     }
 }
 

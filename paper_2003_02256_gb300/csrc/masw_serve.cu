@@ -25,12 +25,12 @@
 // a scatter kernel moves each block into its slot. Slot layout:
 //   [meta: 4 x i32 (nrec, nlim, n_lambda, 0)] [records: rmax x 8 f64]
 //   [FP32 records: rmax x 8 f32] [k: imax f64]
-//   [scan state: imax x (base, carry, phase, ref) i32]
+//   [scan state: imax x (base, carry, phase, located index) i32]
 // Each item runs the default scan of the batch path: in the tick after its
-// admission, a thread-per-item counting search (the FP32 negative-eigenvalue
-// count bisected below the pole-free bound) locates the first sign change,
-// and the tick's FP64 check (count 0 at V[n-1], odd at V[n]) decides it, so
-// most requests finish in one tick. Items whose change lies above the bound
+// admission, a lane pair runs the counting search (the FP32 negative-
+// eigenvalue count split below the pole-free bound) and its FP64 certificate
+// (count 0 at V[n-1], odd at V[n]; count_certify_pair), so most requests
+// finish in one tick. Items whose change lies above the bound
 // continue with paired FP32 chunks from the bound, up to `chunks_per_tick`
 // per tick, and get the FP64 sign check at V[0], V[n-1], V[n]; when a check
 // does not confirm, the item continues with FP64 chunks, one per tick, from a
@@ -45,6 +45,7 @@
 #include <vector>
 
 #include "../../include/masw.h"
+#include "masw_count.cuh"
 #include "masw_device.cuh"
 #include "masw_internal.h"
 #include "masw_screen.cuh"
@@ -86,6 +87,24 @@ __device__ __forceinline__ int32_t* slot_state(const SlotView& v, int s) {
 
 enum { PH_SCREEN = 0, PH_FP64 = 1, PH_FP64_WINDOW = 2 };
 
+// Write an item's result into the mapped host arrays (res < 0: no change
+// below the limit) and count it off its request; the request's slot joins
+// the done list with its last item.
+__device__ __forceinline__ void finish_item(const SlotView& v, int item, int slot, int res,
+                                            double c0, double dc) {
+    if (res >= 0) {
+        v.ct[item] = grid_c(c0, dc, res);
+        v.idx[item] = res;
+        v.status[item] = MASW_FOUND;
+    } else {
+        v.ct[item] = __longlong_as_double(0x7ff8000000000000LL);
+        v.idx[item] = -1;
+        v.status[item] = MASW_NO_ROOT;
+    }
+    __threadfence_system();
+    if (atomicSub(&v.remaining[slot], 1) == 1) v.done[atomicAdd(&v.counters[1], 1)] = slot;
+}
+
 // Upload descriptor of one admitted request inside the packed upload buffer.
 struct UploadDesc { int32_t slot, offset, bytes, n_lambda; };
 
@@ -102,17 +121,21 @@ __global__ void __launch_bounds__(256) serve_scatter_kernel(SlotView v, const un
     if (threadIdx.x == 0) v.remaining[d.slot] = d.n_lambda;
 }
 
-// Tick, part 0 (one thread per item admitted since the last tick): the
-// counting search of the batch path (search32_kernel). A located index goes
-// to the check list flagged SCREEN_COUNTED; otherwise the item enters the
-// linear FP32 screen at the next tick, from the end of the pole-free range
-// (carrying the positive sign of count 0) or from V[0].
-__global__ void __launch_bounds__(128) serve_search_kernel(SlotView v, const int32_t* __restrict__ items,
-                                                           int n_items, int32_t* active_out,
-                                                           int32_t* check_list, double c0, double dc) {
+// Tick, part 0 (two lanes per item admitted since the last tick): the
+// counting search and its FP64 certificate of the batch path
+// (count_certify_pair). A certified item is finished here. Otherwise the item
+// continues at the next tick: with the linear FP32 screen from the end of the
+// pole-free range (carrying the positive sign of count 0) or from V[0], or,
+// when the certificate failed, with the FP64 scan from a window 17 points
+// below the located index (its first point checked against V[0]'s sign).
+__global__ void __launch_bounds__(128, 7) serve_count_kernel(SlotView v, const int32_t* __restrict__ items,
+                                                             int n_items, int32_t* active_out,
+                                                             double c0, double dc) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_items) return;
-    const int item = items[t];
+    if ((t >> 1) >= n_items) return;  // both lanes of a pair leave together
+    const int half = t & 1;
+    const unsigned pair = 3u << ((threadIdx.x & 31) & 30);
+    const int item = items[t >> 1];
     const int slot = item / v.imax;
     const int j = item - slot * v.imax;
     const int32_t* meta = slot_meta(v, slot);
@@ -120,44 +143,29 @@ __global__ void __launch_bounds__(128) serve_search_kernel(SlotView v, const int
     const int nlim = meta[1];
     int32_t* stt = slot_state(v, slot) + 4 * j;
     if (nlim < 2) {
-        stt[3] = -2;
-        check_list[atomicAdd(&v.counters[2], 1)] = item;
+        if (!half) finish_item(v, item, slot, -1, c0, dc);
         return;
     }
-    const float* lay = slot_records32(v, slot);
-    const float k = (float)slot_k(v, slot)[j];
-    const float c0f = (float)c0, dcf = (float)dc;
-    const int npf = pole_free_points_f(lay, N, k, c0f, dcf, nlim);
-    int start = 0, res = -1;
-    if (npf >= 1) {
-        int hi = npf - 1;
-        int chi = inertia_f(lay, N, k, fmaf((float)hi, dcf, c0f));
-        if (chi == 0) {
-            start = npf;
-        } else {
-            int lo = -1;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                const int cm = inertia_f(lay, N, k, fmaf((float)mid, dcf, c0f));
-                if (cm >= 1) {
-                    hi = mid;
-                    chi = cm;
-                } else {
-                    lo = mid;
-                }
-            }
-            if (hi >= 1 && (chi & 1)) res = hi;
-        }
+    const double* lay = slot_records(v, slot);
+    const double k = slot_k(v, slot)[j];
+    const PairCount r =
+        count_certify_pair(slot_records32(v, slot), lay, N, k, c0, dc, nlim, half, pair);
+    if (half) return;
+    if (r.cert >= 1) {
+        finish_item(v, item, slot, r.cert, c0, dc);
+        return;
     }
-    if (res >= 1) {
-        stt[3] = res | SCREEN_COUNTED;
-        check_list[atomicAdd(&v.counters[2], 1)] = item;
+    if (r.n >= 1) {
+        const bool win = r.n >= 18;
+        stt[0] = win ? r.n - 17 : 0;
+        stt[1] = win ? det_sign(lay, N, k, grid_c(c0, dc, 0)) : 0;
+        stt[2] = win ? PH_FP64_WINDOW : PH_FP64;
     } else {
-        stt[0] = start;
-        stt[1] = start > 0 ? 1 : 0;
+        stt[0] = r.start;
+        stt[1] = r.start > 0 ? 1 : 0;
         stt[2] = PH_SCREEN;
-        active_out[atomicAdd(&v.counters[0], 1)] = item;
     }
+    active_out[atomicAdd(&v.counters[0], 1)] = item;
 }
 
 // Tick, part 1 (one warp per active item). PH_SCREEN: up to `chunks` paired
@@ -245,17 +253,7 @@ __global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
     }
     if (lane == 0) {
         if (finished) {
-            if (res >= 0) {
-                v.ct[item] = grid_c(c0, dc, res);
-                v.idx[item] = res;
-                v.status[item] = MASW_FOUND;
-            } else {
-                v.ct[item] = __longlong_as_double(0x7ff8000000000000LL);
-                v.idx[item] = -1;
-                v.status[item] = MASW_NO_ROOT;
-            }
-            __threadfence_system();
-            if (atomicSub(&v.remaining[slot], 1) == 1) v.done[atomicAdd(&v.counters[1], 1)] = slot;
+            finish_item(v, item, slot, res, c0, dc);
         } else {
             stt[0] = base;
             stt[1] = carry;
@@ -270,11 +268,10 @@ __global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
     }
 }
 
-// Tick, part 2 (one thread per item on the check list): an index of the
-// counting search is accepted when the FP64 count is 0 at V[n-1] and odd at
-// V[n]; a linear screen's index when the FP64 signs at V[0], V[n-1], V[n]
-// (or V[0] and the last scanned point) agree with it; otherwise the item
-// continues with the FP64 scan.
+// Tick, part 2 (one thread per item the linear screen located this tick):
+// the index is accepted when the FP64 signs at V[0], V[n-1], V[n] (or V[0]
+// and the last scanned point) agree with it; otherwise the item continues
+// with the FP64 scan.
 __global__ void serve_check_kernel(SlotView v, const int32_t* __restrict__ check_list,
                                    const int32_t* __restrict__ n_check, int32_t* active_out,
                                    double c0, double dc) {
@@ -289,20 +286,11 @@ __global__ void serve_check_kernel(SlotView v, const int32_t* __restrict__ check
     const double* lay = slot_records(v, slot);
     const double k = slot_k(v, slot)[j];
     int32_t* stt = slot_state(v, slot) + 4 * j;
-    int n = stt[3];
+    const int n = stt[3];
     int res = -1;
     bool ok;
     if (nlim < 2) {
         ok = true;
-    } else if (n >= 0 && (n & SCREEN_COUNTED)) {
-        n &= ~SCREEN_COUNTED;
-        const int ia = det_inertia(lay, N, k, grid_c(c0, dc, n - 1));
-        ok = ia == 0;
-        if (ok) {
-            const int ib = det_inertia(lay, N, k, grid_c(c0, dc, n));
-            ok = ib > 0 && (ib & 1);
-        }
-        res = n;
     } else {
         int s0 = det_sign(lay, N, k, grid_c(c0, dc, 0));
         if (n >= 1) {
@@ -315,17 +303,7 @@ __global__ void serve_check_kernel(SlotView v, const int32_t* __restrict__ check
         }
     }
     if (ok) {
-        if (res >= 0) {
-            v.ct[item] = grid_c(c0, dc, res);
-            v.idx[item] = res;
-            v.status[item] = MASW_FOUND;
-        } else {
-            v.ct[item] = __longlong_as_double(0x7ff8000000000000LL);
-            v.idx[item] = -1;
-            v.status[item] = MASW_NO_ROOT;
-        }
-        __threadfence_system();
-        if (atomicSub(&v.remaining[slot], 1) == 1) v.done[atomicAdd(&v.counters[1], 1)] = slot;
+        finish_item(v, item, slot, res, c0, dc);
     } else {
         // FP64 from 17 points below the screen's index (first point checked
         // against V[0]'s sign), or from V[0] when the index is that small
@@ -474,8 +452,8 @@ int tick_launch_impl(masw_server* S, bool* launched) {
     if (cudaMemsetAsync(S->v.counters, 0, 3 * sizeof(int32_t), S->stream) != cudaSuccess)
         return MASW_ECUDA;
     if (n_new) {
-        serve_search_kernel<<<(n_new + 127) / 128, 128, 0, S->stream>>>(
-            S->v, new_items, n_new, S->active[1 - S->cur], S->check, S->grid.c0, S->grid.dc);
+        serve_count_kernel<<<(2 * n_new + 127) / 128, 128, 0, S->stream>>>(
+            S->v, new_items, n_new, S->active[1 - S->cur], S->grid.c0, S->grid.dc);
         if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
     }
     if (S->n_active) {
@@ -488,8 +466,8 @@ int tick_launch_impl(masw_server* S, bool* launched) {
                                                                 S->grid.dc);
         if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
     }
-    // every item that entered the check list this tick (at most n_active + n_new)
-    serve_check_kernel<<<(S->n_active + n_new + 127) / 128, 128, 0, S->stream>>>(
+    // every item that entered the check list this tick (at most n_active)
+    serve_check_kernel<<<(S->n_active + 127) / 128 + 1, 128, 0, S->stream>>>(
         S->v, S->check, S->v.counters + 2, S->active[1 - S->cur], S->grid.c0, S->grid.dc);
     if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
     // counters and the done list (first counters[1] entries) come back together
