@@ -384,6 +384,54 @@ __device__ inline int det_sign_count(const double* __restrict__ lay, int N, doub
     return sg * sgn(det);
 }
 
+// x = m * 2^e with |m| in [1, 2) for a normal x (integer pipe); zero,
+// subnormals and inf/NaN are returned unchanged with e = 0.
+__device__ __forceinline__ double split_pow2(double x, int* e) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0 || ex == 0x7ff) {
+        *e = 0;
+        return x;
+    }
+    *e = ex - 1023;
+    return __longlong_as_double((b & (long long)0x800fffffffffffffULL) | (1023LL << 52));
+}
+
+// det K(k, c) up to the positive factor k^(2(N+1)) mu_ref-free scaling of
+// the elements, as f * 2^(*e2): det K = prod_j det Shat_j / (w_j Dh_j)^2, the
+// numerator and denominator products kept as (mantissa, exponent) pairs so
+// that nothing over- or underflows. f = 0 at an exact zero; NaN when the
+// rescaling failed. Requires c < beta_halfspace.
+__device__ inline double det_scaled(const double* __restrict__ lay, int N, double k, double c,
+                                    int* e2) {
+    double c2 = c * c;
+    HState st{0.0, 0.0, 0.0, 1.0};
+    double num = 1.0, den = 1.0;
+    int e = 0, ea, eb;
+    for (int j = 0; j < N; ++j) {
+        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2);
+        const double wD = st.w * n.Dh;
+        bool ok;
+        const double det = schur_layer(st, n, &ok);
+        num = split_pow2(num * det, &ea);
+        den = split_pow2(den * (wD * wD), &eb);
+        e += ea - eb;
+        if (!ok) {
+            *e2 = 0;
+            return __longlong_as_double(0x7ff8000000000000LL);
+        }
+    }
+    HalfNum hn = halfspace_numerators(lay + N * LAYER_STRIDE, c2);
+    const double wD = st.w * hn.den;
+    double s00 = fma(hn.den, st.p00, st.w * hn.m00);
+    double s01 = fma(hn.den, st.p01, st.w * hn.m01);
+    double s11 = fma(hn.den, st.p11, st.w * hn.m11);
+    num = split_pow2(num * fma(s00, s11, -s01 * s01), &ea);
+    den = split_pow2(den * (wD * wD), &eb);
+    *e2 = e + ea - eb;
+    return num / den;
+}
+
 // Sign and ln|det K| including the dropped factor k^(2(N+1)) (parity checks).
 __device__ inline int det_sign_log(const double* __restrict__ lay, int N, double k, double c,
                                    double* log_abs) {

@@ -776,6 +776,24 @@ cudaError_t launch_det_eval(const DevBatch& b, int n, const int32_t* item, const
 
 // ---------------------------------------------------------------- refine
 
+// det K relative to 2^e_ref (the scale of the bracket's ends).
+__device__ __forceinline__ double det_rel(const double* __restrict__ lay, int N, double k, double c,
+                                          int e_ref) {
+    int e;
+    const double f = det_scaled(lay, N, k, c, &e);
+    const int d = max(-1100, min(1100, e - e_ref));
+    return ldexp(f, d);
+}
+
+// Refined root inside [V[idx-1], V[idx]] (the change located by the scan) to
+// a bracket narrower than rel_tol * c: Illinois (modified regula falsi) on
+// det K, which has a simple zero there; the secant point of the bracket ends
+// replaces the end of its own sign, and when one end is kept twice in a row
+// its value is halved, so both ends converge (superlinearly, order ~1.44).
+// A secant point outside the bracket's interior is replaced by the midpoint,
+// and every 8th step is a bisection step, so the bracket also shrinks at
+// least as fast as in bisection. Returns the midpoint of the final bracket;
+// an exact zero returns its point.
 __global__ void refine_kernel(DevBatch b, const int32_t* __restrict__ idx, double rel_tol,
                               double* croot) {
     int it = blockIdx.x * blockDim.x + threadIdx.x;
@@ -789,15 +807,36 @@ __global__ void refine_kernel(DevBatch b, const int32_t* __restrict__ idx, doubl
     const double* lay = b.layers + (size_t)lo_rec * LAYER_STRIDE;
     double k = b.k[it];
     double lo = grid_c(b.c0, b.dc, id - 1), hi = grid_c(b.c0, b.dc, id);
-    int s_lo = det_sign(lay, N, k, lo);
-    int s_hi = det_sign(lay, N, k, hi);
-    if (s_lo == s_hi) { croot[it] = nan; return; }
-    if (s_lo == 0) { croot[it] = lo; return; }
+    int e_lo, e_hi;
+    double f_lo = det_scaled(lay, N, k, lo, &e_lo);
+    double f_hi = det_scaled(lay, N, k, hi, &e_hi);
+    if (!(f_lo == f_lo) || !(f_hi == f_hi) || (f_lo > 0.0) == (f_hi > 0.0) && f_lo != 0.0 &&
+                                                 f_hi != 0.0) {
+        croot[it] = nan;
+        return;
+    }
+    if (f_lo == 0.0) { croot[it] = lo; return; }
+    if (f_hi == 0.0) { croot[it] = hi; return; }
+    const int e_ref = max(e_lo, e_hi);
+    f_lo = ldexp(f_lo, e_lo - e_ref);
+    f_hi = ldexp(f_hi, e_hi - e_ref);
+    int side = 0;
     for (int i = 0; i < 200 && (hi - lo) > rel_tol * hi; ++i) {
-        double mid = 0.5 * (lo + hi);
-        int sm = det_sign(lay, N, k, mid);
-        if (sm == 0) { lo = hi = mid; break; }
-        if (sm == s_lo) lo = mid; else hi = mid;
+        double x = (i % 8 == 7) ? 0.5 * (lo + hi) : hi - f_hi * (hi - lo) / (f_hi - f_lo);
+        if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
+        const double fx = det_rel(lay, N, k, x, e_ref);
+        if (fx == 0.0 || !(fx == fx)) { lo = hi = x; break; }
+        if ((fx > 0.0) == (f_hi > 0.0)) {
+            hi = x;
+            f_hi = fx;
+            if (side == 1) f_lo *= 0.5;
+            side = 1;
+        } else {
+            lo = x;
+            f_lo = fx;
+            if (side == -1) f_hi *= 0.5;
+            side = -1;
+        }
     }
     croot[it] = 0.5 * (lo + hi);
 }
