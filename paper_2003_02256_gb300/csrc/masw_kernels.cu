@@ -786,65 +786,89 @@ __device__ __forceinline__ double det_rel(const double* __restrict__ lay, int N,
 }
 
 // Refined root inside [V[idx-1], V[idx]] (the change located by the scan) to
-// a bracket narrower than rel_tol * c: Illinois (modified regula falsi) on
-// det K, which has a simple zero there; the secant point of the bracket ends
-// replaces the end of its own sign, and when one end is kept twice in a row
-// its value is halved, so both ends converge (superlinearly, order ~1.44).
-// A secant point outside the bracket's interior is replaced by the midpoint,
-// and every 8th step is a bisection step, so the bracket also shrinks at
-// least as fast as in bisection. Returns the midpoint of the final bracket;
-// an exact zero returns its point.
-__global__ void refine_kernel(DevBatch b, const int32_t* __restrict__ idx, double rel_tol,
-                              double* croot) {
-    int it = blockIdx.x * blockDim.x + threadIdx.x;
-    if (it >= b.n_items) return;
-    int id = idx[it];
-    double nan = __longlong_as_double(0x7ff8000000000000LL);
-    if (id < 1) { croot[it] = nan; return; }
-    int m = b.item_model[it];
-    int lo_rec = b.model_loff[m];
-    int N = b.model_loff[m + 1] - lo_rec - 1;
-    const double* lay = b.layers + (size_t)lo_rec * LAYER_STRIDE;
-    double k = b.k[it];
-    double lo = grid_c(b.c0, b.dc, id - 1), hi = grid_c(b.c0, b.dc, id);
-    int e_lo, e_hi;
-    double f_lo = det_scaled(lay, N, k, lo, &e_lo);
-    double f_hi = det_scaled(lay, N, k, hi, &e_hi);
-    if (!(f_lo == f_lo) || !(f_hi == f_hi) || (f_lo > 0.0) == (f_hi > 0.0) && f_lo != 0.0 &&
-                                                 f_hi != 0.0) {
-        croot[it] = nan;
+// a bracket narrower than rel_tol * c, two lanes per item. Illinois (modified
+// regula falsi) on det K, which has a simple zero there: the secant point x of
+// the bracket ends is evaluated a quarter tolerance on either side (one point
+// per lane); when the two straddle the zero the bracket closes, otherwise the
+// nearer point replaces the end of its sign, and an end kept twice in a row
+// has its value halved, so both ends converge. Every 8th step uses the
+// midpoint, so the bracket also shrinks at least as fast as in bisection.
+// Returns the midpoint of the final bracket; an exact zero returns its point.
+__global__ void __launch_bounds__(128) refine_kernel(DevBatch b, const int32_t* __restrict__ idx,
+                                                     double rel_tol, double* croot) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int it = t >> 1;
+    if (it >= b.n_items) return;  // both lanes of a pair leave together
+    const int half = t & 1;
+    const unsigned pair = 3u << ((threadIdx.x & 31) & 30);
+    const int id = idx[it];
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    if (id < 1) {
+        if (!half) croot[it] = nan;
         return;
     }
-    if (f_lo == 0.0) { croot[it] = lo; return; }
-    if (f_hi == 0.0) { croot[it] = hi; return; }
-    const int e_ref = max(e_lo, e_hi);
-    f_lo = ldexp(f_lo, e_lo - e_ref);
-    f_hi = ldexp(f_hi, e_hi - e_ref);
-    int side = 0;
-    for (int i = 0; i < 200 && (hi - lo) > rel_tol * hi; ++i) {
-        double x = (i % 8 == 7) ? 0.5 * (lo + hi) : hi - f_hi * (hi - lo) / (f_hi - f_lo);
-        if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
-        const double fx = det_rel(lay, N, k, x, e_ref);
-        if (fx == 0.0 || !(fx == fx)) { lo = hi = x; break; }
-        if ((fx > 0.0) == (f_hi > 0.0)) {
-            hi = x;
-            f_hi = fx;
-            if (side == 1) f_lo *= 0.5;
-            side = 1;
-        } else {
-            lo = x;
-            f_lo = fx;
-            if (side == -1) f_hi *= 0.5;
-            side = -1;
+    const int m = b.item_model[it];
+    const int lo_rec = b.model_loff[m];
+    const int N = b.model_loff[m + 1] - lo_rec - 1;
+    const double* lay = b.layers + (size_t)lo_rec * LAYER_STRIDE;
+    const double k = b.k[it];
+    double lo = grid_c(b.c0, b.dc, id - 1), hi = grid_c(b.c0, b.dc, id);
+    int e_own;
+    const double f_own = det_scaled(lay, N, k, half ? hi : lo, &e_own);
+    const double f_oth = __shfl_xor_sync(pair, f_own, 1);
+    const int e_oth = __shfl_xor_sync(pair, e_own, 1);
+    double f_lo = half ? f_oth : f_own, f_hi = half ? f_own : f_oth;
+    const int e_lo = half ? e_oth : e_own, e_hi = half ? e_own : e_oth;
+    double result;
+    if (!(f_lo == f_lo) || !(f_hi == f_hi) ||
+        ((f_lo > 0.0) == (f_hi > 0.0) && f_lo != 0.0 && f_hi != 0.0)) {
+        result = nan;
+    } else if (f_lo == 0.0) {
+        result = lo;
+    } else if (f_hi == 0.0) {
+        result = hi;
+    } else {
+        const int e_ref = max(e_lo, e_hi);
+        f_lo = ldexp(f_lo, e_lo - e_ref);
+        f_hi = ldexp(f_hi, e_hi - e_ref);
+        int side = 0;
+        for (int i = 0; i < 200 && (hi - lo) > rel_tol * hi; ++i) {
+            double x = (i % 8 == 7) ? 0.5 * (lo + hi) : hi - f_hi * (hi - lo) / (f_hi - f_lo);
+            if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
+            const double eps = 0.25 * rel_tol * hi;
+            const double p0 = fmax(x - eps, lo + 0.25 * (x - lo));
+            const double p1 = fmin(x + eps, hi - 0.25 * (hi - x));
+            const double fp = det_rel(lay, N, k, half ? p1 : p0, e_ref);
+            const double fq = __shfl_xor_sync(pair, fp, 1);
+            const double f0 = half ? fq : fp, f1 = half ? fp : fq;
+            if (f0 == 0.0 || !(f0 == f0)) { lo = hi = p0; break; }
+            if (f1 == 0.0 || !(f1 == f1)) { lo = hi = p1; break; }
+            if ((f0 > 0.0) != (f1 > 0.0)) {  // the zero lies between the two points
+                lo = p0;
+                hi = p1;
+                f_lo = f0;
+                f_hi = f1;
+            } else if ((f0 > 0.0) == (f_hi > 0.0)) {  // both on the upper end's side
+                hi = p0;
+                f_hi = f0;
+                if (side == 1) f_lo *= 0.5;
+                side = 1;
+            } else {  // both on the lower end's side
+                lo = p1;
+                f_lo = f1;
+                if (side == -1) f_hi *= 0.5;
+                side = -1;
+            }
         }
+        result = 0.5 * (lo + hi);
     }
-    croot[it] = 0.5 * (lo + hi);
+    if (!half) croot[it] = result;
 }
 
 cudaError_t launch_refine(const DevBatch& b, const int32_t* idx, double rel_tol, double* croot,
                           cudaStream_t s) {
     if (b.n_items <= 0) return cudaSuccess;
-    refine_kernel<<<(b.n_items + 63) / 64, 64, 0, s>>>(b, idx, rel_tol, croot);
+    refine_kernel<<<(2 * b.n_items + 127) / 128, 128, 0, s>>>(b, idx, rel_tol, croot);
     return cudaGetLastError();
 }
 
