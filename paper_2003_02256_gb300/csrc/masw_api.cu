@@ -791,7 +791,7 @@ static int run_roots(masw_batch* B) {
 static int run_root_grad(masw_batch* B) {
     int rc;
     if ((rc = ensure(&B->d_rows, B->grad_len)) ||
-        (rc = ensure(&B->d_bs, 8 * (B->grad_len + B->n_items))))
+        (rc = ensure(&B->d_bs, 12 * (B->grad_len + B->n_items))))
         return rc;
     if ((rc = run_roots(B))) return rc;
     CK(launch_root_grad(B->dev(false), B->d_croot, B->d_rows, B->d_bs, B->stream));

@@ -911,6 +911,15 @@ __device__ __forceinline__ void elem_blocks(const double* L, double k, double c2
     *K21 = {E, -F, F, G};
 }
 
+// The blocks of elem_blocks from its six stored entries (A, B, Dd, E, F, G).
+__device__ __forceinline__ void stored_blocks(const double* E6, M2* K11, M2* K12, M2* K21, M2* K22) {
+    const double A = E6[0], B = E6[1], Dd = E6[2], E = E6[3], F = E6[4], G = E6[5];
+    *K11 = {A, B, B, Dd};
+    *K22 = {A, -B, -B, Dd};
+    *K12 = {E, F, -F, G};
+    *K21 = {E, -F, F, G};
+}
+
 // One thread per item. Row layout: dC/dbeta_0..beta_N, dC/dh_0..h_{N-1}.
 // The null vector u of K(C*) comes from a twisted block factorization: a
 // top-down Schur sweep (S_j = P_j + K11_j) and a bottom-up one (B_j, the
@@ -920,8 +929,10 @@ __device__ __forceinline__ void elem_blocks(const double* L, double k, double c2
 // amplitude. u starts there and is propagated upward with the top-down
 // factors and downward with the bottom-up ones, so it only ever decays and
 // neither a thick top layer (mode confined to the surface) nor a deep one
-// breaks it. `bs` holds 16 doubles per node of the item, starting at
-// 8 * grad_off[item] + 8 * item = 16 * (sum of (N+1) of earlier items).
+// breaks it. Each layer's element entries are evaluated once (first sweep)
+// and kept for the other three sweeps. `bs` holds 24 doubles per node of the
+// item, starting at 12 * grad_off[item] + 12 * item = 24 * (sum of (N+1) of
+// earlier items).
 __global__ void __launch_bounds__(64) root_grad_kernel(DevBatch b, const double* __restrict__ croot,
                                                        double* rows, double* bs) {
     int it = blockIdx.x * blockDim.x + threadIdx.x;
@@ -930,7 +941,7 @@ __global__ void __launch_bounds__(64) root_grad_kernel(DevBatch b, const double*
     int lo_rec = b.model_loff[m];
     int N = b.model_loff[m + 1] - lo_rec - 1;
     double* row = rows + b.grad_off[it];
-    double* ws = bs + 8 * b.grad_off[it] + 8 * (int64_t)it;
+    double* ws = bs + 12 * b.grad_off[it] + 12 * (int64_t)it;
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
     double c = croot[it];
     if (!(c == c)) {
@@ -941,36 +952,39 @@ __global__ void __launch_bounds__(64) root_grad_kernel(DevBatch b, const double*
     double k = b.k[it];
     double c2 = c * c;
     // node j slot: [0..3] S_j (top-down), [4..7] M_j = B_{j+1} + K22_j,
-    //              [8..11] B_j (bottom-up), [12..15] P_j
+    //              [8..11] B_j (bottom-up), [12..15] P_j,
+    //              [16..21] layer j's element entries (A, B, Dd, E, F, G)
     M2 P = {0.0, 0.0, 0.0, 0.0};
     for (int j = 0; j < N; ++j) {
         M2 K11, K12, K21, K22;
         elem_blocks(lay + j * LAYER_STRIDE, k, c2, &K11, &K12, &K21, &K22);
+        double* E6 = ws + 24 * j + 16;
+        E6[0] = K11.a; E6[1] = K11.b; E6[2] = K11.d; E6[3] = K12.a; E6[4] = K12.b; E6[5] = K12.d;
         M2 S = madd(P, K11);
-        st(ws + 16 * j, S);
-        st(ws + 16 * j + 12, P);
+        st(ws + 24 * j, S);
+        st(ws + 24 * j + 12, P);
         P = msub(K22, mmul(K21, msolve(S, K12)));
     }
-    st(ws + 16 * N + 12, P);
+    st(ws + 24 * N + 12, P);
     HalfNum hn = halfspace_numerators(lay + N * LAYER_STRIDE, c2);
     double iden = 1.0 / hn.den;
     M2 Bv = {hn.m00 * iden, hn.m01 * iden, hn.m01 * iden, hn.m11 * iden};
-    st(ws + 16 * N + 8, Bv);
+    st(ws + 24 * N + 8, Bv);
     for (int j = N - 1; j >= 0; --j) {
         M2 K11, K12, K21, K22;
-        elem_blocks(lay + j * LAYER_STRIDE, k, c2, &K11, &K12, &K21, &K22);
+        stored_blocks(ws + 24 * j + 16, &K11, &K12, &K21, &K22);
         M2 Mj = madd(Bv, K22);
-        st(ws + 16 * j + 4, Mj);
+        st(ws + 24 * j + 4, Mj);
         Bv = msub(K11, mmul(K12, msolve(Mj, K21)));
-        st(ws + 16 * j + 8, Bv);
+        st(ws + 24 * j + 8, Bv);
     }
     // twist node: most singular condensed block
     int js = N;
     double best = 1e300;
     for (int j = 0; j <= N; ++j) {
         M2 Pj, Bj;
-        ld(ws + 16 * j + 12, &Pj);
-        ld(ws + 16 * j + 8, &Bj);
+        ld(ws + 24 * j + 12, &Pj);
+        ld(ws + 24 * j + 8, &Bj);
         M2 G = madd(Pj, Bj);
         double nrm = G.a * G.a + G.b * G.b + G.c * G.c + G.d * G.d;
         double sng = fabs(mdet(G)) / nrm;
@@ -979,8 +993,8 @@ __global__ void __launch_bounds__(64) root_grad_kernel(DevBatch b, const double*
     M2 G;
     {
         M2 Pj, Bj;
-        ld(ws + 16 * js + 12, &Pj);
-        ld(ws + 16 * js + 8, &Bj);
+        ld(ws + 24 * js + 12, &Pj);
+        ld(ws + 24 * js + 8, &Bj);
         G = madd(Pj, Bj);
     }
     // null vector of the 2x2 G from its larger row
@@ -990,37 +1004,37 @@ __global__ void __launch_bounds__(64) root_grad_kernel(DevBatch b, const double*
     double nn = fmax(fabs(nx), fabs(nz));
     nx /= nn; nz /= nn;
     // store u_j in the P slot (no longer needed): [12], [13]
-    ws[16 * js + 12] = nx;
-    ws[16 * js + 13] = nz;
+    ws[24 * js + 12] = nx;
+    ws[24 * js + 13] = nz;
     for (int j = js - 1; j >= 0; --j) {  // upward: u_j = -S_j^-1 K12_j u_{j+1}
         M2 K11, K12, K21, K22, S;
-        elem_blocks(lay + j * LAYER_STRIDE, k, c2, &K11, &K12, &K21, &K22);
-        ld(ws + 16 * j, &S);
-        double x = ws[16 * (j + 1) + 12], z = ws[16 * (j + 1) + 13];
+        stored_blocks(ws + 24 * j + 16, &K11, &K12, &K21, &K22);
+        ld(ws + 24 * j, &S);
+        double x = ws[24 * (j + 1) + 12], z = ws[24 * (j + 1) + 13];
         double v0 = K12.a * x + K12.b * z, v1 = K12.c * x + K12.d * z, o0, o1;
         mvsolve(S, v0, v1, &o0, &o1);
-        ws[16 * j + 12] = -o0;
-        ws[16 * j + 13] = -o1;
+        ws[24 * j + 12] = -o0;
+        ws[24 * j + 13] = -o1;
     }
     for (int j = js + 1; j <= N; ++j) {  // downward: u_j = -M_{j-1}^-1 K21_{j-1} u_{j-1}
         M2 K11, K12, K21, K22, Mj;
-        elem_blocks(lay + (j - 1) * LAYER_STRIDE, k, c2, &K11, &K12, &K21, &K22);
-        ld(ws + 16 * (j - 1) + 4, &Mj);
-        double x = ws[16 * (j - 1) + 12], z = ws[16 * (j - 1) + 13];
+        stored_blocks(ws + 24 * (j - 1) + 16, &K11, &K12, &K21, &K22);
+        ld(ws + 24 * (j - 1) + 4, &Mj);
+        double x = ws[24 * (j - 1) + 12], z = ws[24 * (j - 1) + 13];
         double v0 = K21.a * x + K21.b * z, v1 = K21.c * x + K21.d * z, o0, o1;
         mvsolve(Mj, v0, v1, &o0, &o1);
-        ws[16 * j + 12] = -o0;
-        ws[16 * j + 13] = -o1;
+        ws[24 * j + 12] = -o0;
+        ws[24 * j + 13] = -o1;
     }
     // implicit-function rule with dual-number element derivatives
     HalfD H = halfspace_d(lay + N * LAYER_STRIDE, c);
-    D4 qh = half_quad(H, ws[16 * N + 12], ws[16 * N + 13]);
+    D4 qh = half_quad(H, ws[24 * N + 12], ws[24 * N + 13]);
     double den = qh.d0;
     row[N] = qh.d1;
     for (int j = 0; j < N; ++j) {
         ElemD K = layer_element_d(lay + j * LAYER_STRIDE, k, c);
-        D4 q = elem_quad(K, ws[16 * j + 12], ws[16 * j + 13], ws[16 * (j + 1) + 12],
-                         ws[16 * (j + 1) + 13]);
+        D4 q = elem_quad(K, ws[24 * j + 12], ws[24 * j + 13], ws[24 * (j + 1) + 12],
+                         ws[24 * (j + 1) + 13]);
         den += q.d0;
         row[j] = q.d1;
         row[N + 1 + j] = q.d2;
