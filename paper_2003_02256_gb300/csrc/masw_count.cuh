@@ -7,13 +7,16 @@
 //    function of the grid index, 0 at c = 0 (Wittrick-Williams below the
 //    lowest clamped-layer mode). The pair evaluates the top of the range and
 //    its midpoint, then splits the bracket in three per step (one point per
-//    lane): about log3(npf) steps instead of Algorithm 1's linear walk. An
-//    odd count at the first nonzero point is Algorithm 1's first change.
+//    lane): about log3(npf) steps instead of Algorithm 1's linear walk. The
+//    first nonzero point goes to the certificate whatever its FP32 parity.
 //  * Certificate (FP64). The count (det_inertia) is 0 at V[n-1] (so 0, and
 //    V[0]'s sign, at every point below) and odd at V[n] (the sign differs).
 //    When the FP32 count was off by one next to the change (count 0 at both
 //    points: the change is higher; nonzero at V[n-1]: lower), the pair takes
-//    one FP64 step of two points in that direction, inside the range.
+//    one FP64 step of two points in that direction, inside the range. An
+//    even FP64 count (two or more) after count 0 means no sign change there:
+//    a second search looks for the first odd count above it, certified the
+//    same way; failing that the linear scan takes over from that point.
 #pragma once
 
 #include "masw_device.cuh"
@@ -24,8 +27,47 @@ namespace masw {
 struct PairCount {
     int cert;   // certified first change (>= 1), or -1
     int n;      // the search's index when the certificate failed (>= 1), or -1
-    int start;  // n < 1: the linear scan's start (npf when the range holds no change, else 0)
+    int start;  // cert and n < 1: the linear scan's start (npf when the range holds no
+                // change, the located point after an even FP64 count, else 0)
 };
+
+// First grid index in (lo, top] whose FP32 negative-eigenvalue count is at
+// least `target`, the count being non-decreasing there and below `target` at
+// lo; -1 when the count at `top` is below `target`. The pair evaluates `top`
+// and the bracket's midpoint, then splits the bracket in three per step (one
+// point per lane). Both lanes return the same index.
+__device__ __forceinline__ int pair_search(const float* __restrict__ lay32, int N, float kf,
+                                           float c0f, float dcf, int lo, int top, int target,
+                                           int half, unsigned pair) {
+    int hi = top;
+    const int mid = lo + ((hi - lo) >> 1);
+    const int pt = half ? mid : hi;
+    const int cnt = pt > lo ? inertia_f(lay32, N, kf, fmaf((float)pt, dcf, c0f)) : 0;
+    const int oth = __shfl_xor_sync(pair, cnt, 1);
+    const int c_top = half ? oth : cnt, c_mid = half ? cnt : oth;
+    if (c_top < target) return -1;
+    if (mid > lo) {
+        if (c_mid >= target) hi = mid;
+        else lo = mid;
+    }
+    while (hi - lo > 1) {
+        const int len = hi - lo;
+        const int a = lo + (len + 1) / 3, bq = lo + (2 * len + 1) / 3;  // lo < a <= bq < hi
+        const int q = half ? bq : a;
+        const int c = inertia_f(lay32, N, kf, fmaf((float)q, dcf, c0f));
+        const int co = __shfl_xor_sync(pair, c, 1);
+        const int ca = half ? co : c, cb = half ? c : co;
+        if (ca >= target) {
+            hi = a;
+        } else if (cb >= target) {
+            lo = a;
+            hi = bq;
+        } else {
+            lo = bq;
+        }
+    }
+    return hi;
+}
 
 // Both lanes of the pair (lane bit 0 = half, `pair` = their shuffle mask)
 // call this with the same item and get the same result. Requires nlim >= 2.
@@ -37,48 +79,15 @@ __device__ __forceinline__ PairCount count_certify_pair(const float* __restrict_
     const float c0f = (float)c0, dcf = (float)dc;
     const int npf = pole_free_points_f(lay32, N, kf, c0f, dcf, nlim);
     PairCount out{-1, -1, 0};
-    int n = -1;
-    if (npf >= 1) {
-        int lo = -1, hi = npf - 1;
-        const int mid = (hi - 1) >> 1;  // midpoint of (lo, hi); -1 when hi == 0
-        const int pt = half ? mid : hi;
-        const int cnt = pt >= 0 ? inertia_f(lay32, N, kf, fmaf((float)pt, dcf, c0f)) : 0;
-        const int oth = __shfl_xor_sync(pair, cnt, 1);
-        const int c_top = half ? oth : cnt, c_mid = half ? cnt : oth;
-        if (c_top == 0) {
-            out.start = npf;  // no mode below the bound: scan linearly above it
-        } else {
-            int chi = c_top;
-            if (mid >= 0) {
-                if (c_mid >= 1) {
-                    hi = mid;
-                    chi = c_mid;
-                } else {
-                    lo = mid;
-                }
-            }
-            while (hi - lo > 1) {
-                const int len = hi - lo;
-                const int a = lo + (len + 1) / 3, bq = lo + (2 * len + 1) / 3;  // lo < a <= bq < hi
-                const int q = half ? bq : a;
-                const int c = inertia_f(lay32, N, kf, fmaf((float)q, dcf, c0f));
-                const int co = __shfl_xor_sync(pair, c, 1);
-                const int ca = half ? co : c, cb = half ? c : co;
-                if (ca >= 1) {
-                    hi = a;
-                    chi = ca;
-                } else if (cb >= 1) {
-                    lo = a;
-                    hi = bq;
-                    chi = cb;
-                } else {
-                    lo = bq;
-                }
-            }
-            if (hi >= 1 && (chi & 1)) n = hi;
-        }
+    if (npf < 1) return out;
+    // count 0 at c = 0 (static stiffness positive definite); the FP64
+    // certificate decides the parity at the first nonzero point
+    const int n = pair_search(lay32, N, kf, c0f, dcf, -1, npf - 1, 1, half, pair);
+    if (n < 0) {
+        out.start = npf;  // no mode below the bound: scan linearly above it
+        return out;
     }
-    if (n < 1) return out;
+    if (n < 1) return out;  // a mode below V[0]: Algorithm 1 from V[0]
     const int v = det_inertia(lay, N, k, grid_c(c0, dc, n - 1 + half));
     const int vo = __shfl_xor_sync(pair, v, 1);
     const int va = half ? vo : v;  // V[n-1]
@@ -107,6 +116,24 @@ __device__ __forceinline__ PairCount count_certify_pair(const float* __restrict_
                     cert = n - 2;
                 }
             }
+        }
+    }
+    if (cert < 0 && va == 0 && vb >= 2 && !(vb & 1)) {
+        // FP64: count 0 below n and even at n (two modes inside one interval,
+        // no sign change there). The first change is the first point above n
+        // whose count is odd: search for the first count above vb and certify
+        // count vb one point below it (so vb, an even count, all the way from
+        // n) and an odd count at it; otherwise the linear scan starts at n.
+        const int m = pair_search(lay32, N, kf, c0f, dcf, n, npf - 1, vb + 1, half, pair);
+        if (m > n) {
+            const int u = det_inertia(lay, N, k, grid_c(c0, dc, m - 1 + half));
+            const int uo = __shfl_xor_sync(pair, u, 1);
+            const int ua = half ? uo : u, ub = half ? u : uo;
+            if (ua == vb && ub > vb && (ub & 1)) cert = m;
+        }
+        if (cert < 0) {
+            out.start = n;
+            return out;
         }
     }
     out.cert = cert;

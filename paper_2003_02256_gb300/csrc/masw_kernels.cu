@@ -396,8 +396,8 @@ __global__ void __launch_bounds__(128) verify64_list_kernel(DevBatch b, ScanOut 
 // Linear paired FP32 scan of the fallback items of count_certify_kernel, one
 // block per listed item (few items, each a long walk: the block's warps take
 // consecutive 64-point sub-chunks, 64 x warps points per round), from the
-// start index in n32 (the points below it carry count 0, i.e. a positive
-// FP32 sign). The first change of a round is the smallest index any warp
+// start index in n32 (the points below it carry V[0]'s sign, the positive
+// sign of an even negative-eigenvalue count). The first change of a round is the smallest index any warp
 // found; warp w's first point compares with warp w-1's last.
 __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float* __restrict__ layers32,
                                                          int32_t* n32, const int32_t* __restrict__ fallback,
@@ -471,10 +471,10 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
 // warp's 16 items share a model and have adjacent wavelengths, so their
 // branches agree). Fusing lets warps in the FP32 search and warps in the FP64
 // certificate share an SM: the two use different pipes. Items whose change
-// lies above the pole-free range, at V[0], or where the count jumps by an
-// even number go to the fallback list, with the grid index to scan from in
-// n32; uncertified items go to the FP64 re-scan with V[0]'s sign. Certified
-// items keep SCREEN_COUNTED in n32.
+// lies above the pole-free range, at V[0], or behind an even FP64 count go to
+// the fallback list, with the grid index to scan from in n32; uncertified
+// items go to the FP64 re-scan with V[0]'s sign. Certified items keep
+// SCREEN_COUNTED in n32.
 __global__ void __launch_bounds__(128, 7) count_certify_kernel(DevBatch b, const float* __restrict__ layers32,
                                                                ScanOut o, int32_t* __restrict__ n32,
                                                                int32_t* ref_sign, int32_t* unresolved,
