@@ -123,8 +123,11 @@ int masw_model_batch_create(const masw_models_desc* models, const masw_grid* gri
 int masw_model_batch_destroy(masw_batch* batch);
 
 /* Replace the layer parameters of an existing batch (same n_layers and
- * n_lambda; wavelengths unchanged). Pointers live in mem_space. Used by
- * inversion loops and samplers; a captured scan graph stays valid. */
+ * n_lambda; wavelengths unchanged). Pointers live in mem_space. The checks
+ * of masw_model_batch_create, the layer records and the scan limits run on
+ * the GPU, queued after the work already on the batch stream; the call
+ * synchronises the stream once. MASW_EINVAL leaves the batch unchanged.
+ * Used by inversion loops and samplers; a captured scan graph stays valid. */
 int masw_model_batch_update(masw_batch* batch, const double* h, const double* alpha,
                             const double* beta, const double* rho, int32_t mem_space);
 

@@ -74,6 +74,9 @@ struct masw_batch {
     int32_t* d_unres = nullptr;
     int32_t* d_fallback = nullptr;
     int32_t* d_counters = nullptr;  // SCAN_COUNTERS
+    // model updates (allocated on first use): staged host arrays, error flag
+    double* d_upd = nullptr;
+    int32_t* d_upd_err = nullptr;
     // higher modes (allocated on first use, for chg_cap changes per item)
     int chg_cap = 0;
     double* d_chg_ct = nullptr;
@@ -282,7 +285,7 @@ static void free_batch(masw_batch* B) {
                     B->d_item_model, B->d_order_sorted, B->d_order_natural, B->d_grad_off,
                     B->d_counter, B->d_ct, B->d_idx, B->d_status, B->d_croot, B->d_rows, B->d_bs,
                     B->d_dphi, B->d_ce, B->d_misfit, B->d_gb, B->d_gh, B->d_layers32,
-                    B->d_n32, B->d_ref, B->d_unres, B->d_fallback, B->d_counters,
+                    B->d_n32, B->d_ref, B->d_unres, B->d_fallback, B->d_counters, B->d_upd, B->d_upd_err,
                     B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta,
                     B->d_chg_counters};
     for (void* p : ptrs)
@@ -558,27 +561,37 @@ int masw_model_batch_destroy(masw_batch* B) {
 int masw_model_batch_update(masw_batch* B, const double* h, const double* alpha, const double* beta,
                             const double* rho, int32_t mem_space) {
     if (!B || (mem_space != MASW_HOST && mem_space != MASW_DEVICE)) return MASW_EINVAL;
-    bool dev = mem_space == MASW_DEVICE;
-    int64_t nh = B->n_records - B->n_models;
-    std::vector<double> hv, a, b, r;
-    int rc;
-    if ((rc = fetch(hv, h, nh, dev)) || (rc = fetch(a, alpha, B->n_records, dev)) ||
-        (rc = fetch(b, beta, B->n_records, dev)) || (rc = fetch(r, rho, B->n_records, dev)))
-        return rc;
-    if ((rc = validate_layers(B->n_layers, hv, a, b, r))) return rc;
-    std::vector<int32_t> nlim(B->n_models);
-    for (int32_t m = 0; m < B->n_models; ++m) nlim[m] = scan_limit(B->grid, b[B->loff[m + 1] - 1]);
-    std::vector<double> rec;
-    build_records(B, hv, a, b, r, rec);
-    std::vector<float> rec32;
-    build_records32(B, rec, rec32);
-    // the upload is ordered after work already queued on the batch stream
+    const int64_t nh = B->n_records - B->n_models, nr = B->n_records;
+    if ((nh > 0 && !h) || (nr > 0 && (!alpha || !beta || !rho))) return MASW_EINVAL;
+    // staging for host arrays (h, alpha, beta, rho) and the validation flag
+    if (!B->d_upd && dev_alloc(&B->d_upd, (size_t)(nh + 3 * nr))) return MASW_ENOMEM;
+    if (!B->d_upd_err && dev_alloc(&B->d_upd_err, 1)) return MASW_ENOMEM;
+    const double *dh = h, *da = alpha, *db = beta, *dr = rho;
+    if (mem_space == MASW_HOST) {
+        double* st = B->d_upd;
+        dh = st;
+        da = st + nh;
+        db = st + nh + nr;
+        dr = st + nh + 2 * nr;
+        const double* src[4] = {h, alpha, beta, rho};
+        double* dst[4] = {st, st + nh, st + nh + nr, st + nh + 2 * nr};
+        const int64_t cnt[4] = {nh, nr, nr, nr};
+        for (int q = 0; q < 4; ++q)
+            if (cnt[q] > 0)
+                CK(cudaMemcpyAsync(dst[q], src[q], cnt[q] * sizeof(double), cudaMemcpyHostToDevice,
+                                   B->stream));
+    }
+    // queued after the work already on the batch stream: validation, then the
+    // records and scan limits (skipped on a validation error), then the flag
+    CK(cudaMemsetAsync(B->d_upd_err, 0, sizeof(int32_t), B->stream));
+    CK(launch_model_update(B->dev(false), dh, da, db, dr, B->d_layers, B->d_layers32, B->d_nlim,
+                           B->d_upd_err, B->stream));
+    int32_t err = 0;
+    CK(cudaMemcpyAsync(&err, B->d_upd_err, sizeof(int32_t), cudaMemcpyDeviceToHost, B->stream));
+    CK(cudaMemcpyAsync(B->nlim.data(), B->d_nlim, B->nlim.size() * sizeof(int32_t),
+                       cudaMemcpyDeviceToHost, B->stream));
     CK(cudaStreamSynchronize(B->stream));
-    CK(cudaMemcpy(B->d_layers, rec.data(), rec.size() * sizeof(double), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(B->d_layers32, rec32.data(), rec32.size() * sizeof(float), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(B->d_nlim, nlim.data(), nlim.size() * 4, cudaMemcpyHostToDevice));
-    B->nlim = nlim;
-    return MASW_OK;
+    return err ? MASW_EINVAL : MASW_OK;
 }
 
 int masw_model_batch_update_beta_h(masw_batch* B, const double* h, const double* beta) {

@@ -70,6 +70,11 @@ cudaError_t launch_misfit(const DevBatch& b, const double* ct, const double* ce,
                           double sigma, double* misfit, double* dphi_dc, cudaStream_t s);
 cudaError_t launch_grad_reduce(const DevBatch& b, const double* rows, const double* dphi_dc,
                                double* grad_beta, double* grad_h, cudaStream_t s);
+// Model update on the device: validation flag in err (which must start at 0),
+// then records and scan limits unless it was set (masw_kernels.cu).
+cudaError_t launch_model_update(const DevBatch& b, const double* h, const double* alpha,
+                                const double* beta, const double* rho, double* layers,
+                                float* layers32, int32_t* nlim, int32_t* err, cudaStream_t s);
 cudaError_t launch_update_beta_h(const DevBatch& b, const double* h, const double* beta,
                                  double* layers, float* layers32, int32_t* nlim, int32_t* err,
                                  cudaStream_t s);

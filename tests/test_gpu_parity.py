@@ -287,6 +287,43 @@ def test_graph_replay_after_update_gives_fresh_results(masw, oracle_lib):
     assert not np.array_equal(r1[1], r2[1])
 
 
+def test_update_validates_first_and_matches_a_fresh_batch(masw):
+    """masw_model_batch_update builds the records on the device: an invalid
+    update is refused and leaves the batch as it was; a valid one (host or
+    device pointers) gives determinants identical to a fresh batch's."""
+    import torch
+    m1, g = W.ragged_batch(n_models=12, seed=21)
+    m2, _ = W.ragged_batch(n_models=12, seed=21)
+    m2 = W.Models(m2.n_layers, m2.h * 1.1, m2.alpha * 0.97, m2.beta * 0.97, m2.rho, m2.n_lambda,
+                  m2.lam)
+    rng = np.random.default_rng(4)
+    items = rng.integers(0, m1.n_items, 64).astype(np.int32)
+    cs = rng.uniform(60.0, 300.0, 64)
+    with masw.Batch(m1, g) as b:
+        before = b.dispersion()
+        bad = [dict(h=-m1.h), dict(alpha=m1.beta * 1.1), dict(rho=np.where(np.arange(m1.rho.size) == 3,
+                                                                             np.nan, m1.rho))]
+        for kw in bad:
+            with pytest.raises(masw.MaswError) as ei:
+                b.update(kw.get("h", m1.h), kw.get("alpha", m1.alpha), m1.beta, kw.get("rho", m1.rho))
+            assert ei.value.code == masw.EINVAL
+            after = b.dispersion()
+            assert np.array_equal(after[1], before[1]) and np.array_equal(after[2], before[2])
+        b.update(m2.h, m2.alpha, m2.beta, m2.rho)
+        s_host, l_host = b.det_eval(items, cs)
+        r_host = b.dispersion()
+        dev = [torch.as_tensor(x, device="cuda") for x in (m2.h, m2.alpha, m2.beta, m2.rho)]
+        b.update(m1.h, m1.alpha, m1.beta, m1.rho)
+        b.update(*dev)
+        s_dev, l_dev = b.det_eval(items, cs)
+    with masw.Batch(m2, g) as fresh:
+        s_f, l_f = fresh.det_eval(items, cs)
+        r_f = fresh.dispersion()
+    assert np.array_equal(s_host, s_f) and np.array_equal(l_host, l_f)
+    assert np.array_equal(s_dev, s_f) and np.array_equal(l_dev, l_f)
+    assert np.array_equal(r_host[1], r_f[1]) and np.array_equal(r_host[2], r_f[2])
+
+
 def test_device_pointer_inputs_and_outputs(masw):
     import torch
     m, g = W.ragged_batch(n_models=10, seed=8)
