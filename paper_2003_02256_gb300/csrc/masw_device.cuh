@@ -225,12 +225,13 @@ __device__ __forceinline__ LayerNum layer_numerators(const double* __restrict__ 
     double s2 = 1.0 - q;
     Wave R = wave_fns(kh, r2);
     Wave S = wave_fns(kh, s2);
-    double ErEs = R.E * S.E;
-    double CrCs = R.C * S.C;
-    double Dh = fma(2.0, ErEs - CrCs, fma(R.Sd, S.Sd, R.Sm * S.Sm));
+    // E_r E_s - C_r C_s and Sd_r Sd_s are shared by D and b
+    double u = fma(R.E, S.E, -R.C * S.C);
+    double SdSd = R.Sd * S.Sd;
+    double Dh = fma(2.0, u, fma(R.Sm, S.Sm, SdSd));
     double A1 = fma(R.C, S.Sd, -S.C * R.Sm);
     double D1 = fma(S.C, R.Sd, -R.C * S.Sm);
-    double B1 = fma(s2 + 3.0, CrCs - ErEs, -fma(S.Sm, fma(2.0, R.Sm, R.Sd), R.Sd * S.Sd));
+    double B1 = fma(s2 + 3.0, -u, -fma(S.Sm, fma(2.0, R.Sm, R.Sd), SdSd));
     double E1 = fma(R.Sm, S.E, -R.E * S.Sd);
     double F1 = fma(R.E, S.C, -R.C * S.E);
     double G1 = fma(S.Sm, R.E, -S.E * R.Sd);
