@@ -1161,77 +1161,85 @@ __global__ void update_beta_h_kernel(DevBatch b, const double* __restrict__ h,
     nlim[m] = (int32_t)n;
 }
 
-// Model update from (h, alpha, beta, rho), concatenated as at creation.
-// Step 1, one thread per model: the creation checks (h finite and positive,
-// alpha, beta, rho finite and positive, 3 alpha^2 > 4 beta^2).
-__global__ void validate_models_kernel(DevBatch b, const double* __restrict__ h,
-                                       const double* __restrict__ alpha,
-                                       const double* __restrict__ beta,
-                                       const double* __restrict__ rho, int32_t* err) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+// Model update from (h, alpha, beta, rho), concatenated as at creation; one
+// warp per model, lanes over its layers (coalesced record stores).
+// Step 1: the creation checks (h finite and positive, alpha, beta, rho finite
+// and positive, 3 alpha^2 > 4 beta^2).
+__global__ void __launch_bounds__(128) validate_models_kernel(DevBatch b, const double* __restrict__ h,
+                                                              const double* __restrict__ alpha,
+                                                              const double* __restrict__ beta,
+                                                              const double* __restrict__ rho,
+                                                              int32_t* err) {
+    const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (m >= b.n_models) return;
     const int lo = b.model_loff[m];
     const int N = b.model_loff[m + 1] - lo - 1;
     const int h0 = lo - m;
     bool ok = true;
-    for (int i = 0; i < N; ++i) ok = ok && isfinite(h[h0 + i]) && h[h0 + i] > 0.0;
-    for (int i = 0; i <= N; ++i) {
+    for (int i = lane; i <= N; i += 32) {
         const double a = alpha[lo + i], be = beta[lo + i], r = rho[lo + i];
         ok = ok && isfinite(a) && a > 0.0 && isfinite(be) && be > 0.0 && isfinite(r) && r > 0.0 &&
              3.0 * a * a > 4.0 * be * be;
+        if (i < N) ok = ok && isfinite(h[h0 + i]) && h[h0 + i] > 0.0;
     }
-    if (!ok) atomicOr(err, 1);
+    if (__any_sync(0xffffffffu, !ok) && lane == 0) atomicOr(err, 1);
 }
 
-// Step 2, one thread per model, nothing written when step 1 flagged an
-// error: the FP64 and FP32 layer records and the scan limit, with the
-// arithmetic of the host build at creation (products and quotients only, so
-// no contraction changes a bit).
-__global__ void build_records_kernel(DevBatch b, const double* __restrict__ h,
-                                     const double* __restrict__ alpha,
-                                     const double* __restrict__ beta,
-                                     const double* __restrict__ rho, double* layers,
-                                     float* layers32, int32_t* nlim,
-                                     const int32_t* __restrict__ err) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+// Step 2, nothing written when step 1 flagged an error: the FP64 and FP32
+// layer records and the scan limit, with the arithmetic of the host build at
+// creation (products and quotients only, so no contraction changes a bit).
+__global__ void __launch_bounds__(128) build_records_kernel(DevBatch b, const double* __restrict__ h,
+                                                            const double* __restrict__ alpha,
+                                                            const double* __restrict__ beta,
+                                                            const double* __restrict__ rho,
+                                                            double* layers, float* layers32,
+                                                            int32_t* nlim,
+                                                            const int32_t* __restrict__ err) {
+    const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (m >= b.n_models || *err) return;
     const int lo = b.model_loff[m];
     const int N = b.model_loff[m + 1] - lo - 1;
     const int h0 = lo - m;
     const double mref = rho[lo + N] * beta[lo + N] * beta[lo + N];
-    for (int i = 0; i <= N; ++i) {
+    for (int i = lane; i <= N; i += 32) {
         const double a = alpha[lo + i], be = beta[lo + i], r = rho[lo + i];
         double* L = layers + (size_t)(lo + i) * LAYER_STRIDE;
-        L[L_H] = (i < N) ? h[h0 + i] : 0.0;
-        L[L_MU] = r * be * be;
+        const double lh = (i < N) ? h[h0 + i] : 0.0, lmu = r * be * be;
+        const double ia2 = 1.0 / (a * a), ib2 = 1.0 / (be * be);
+        L[L_H] = lh;
+        L[L_MU] = lmu;
         L[L_RHO] = r;
-        L[L_IA2] = 1.0 / (a * a);
-        L[L_IB2] = 1.0 / (be * be);
+        L[L_IA2] = ia2;
+        L[L_IB2] = ib2;
         L[L_BETA] = be;
         L[L_RATIO] = a / be;
         L[7] = 0.0;
         float* F = layers32 + (size_t)(lo + i) * LAYER_STRIDE32;
-        F[F_H] = (float)L[L_H];
-        F[F_MU] = (float)(L[L_MU] / mref);
-        F[F_RHO] = (float)(L[L_RHO] / mref);
-        F[F_IA2] = (float)L[L_IA2];
-        F[F_IB2] = (float)L[L_IB2];
-        F[F_DIB] = (float)(L[L_IB2] - L[L_IA2]);
+        F[F_H] = (float)lh;
+        F[F_MU] = (float)(lmu / mref);
+        F[F_RHO] = (float)(r / mref);
+        F[F_IA2] = (float)ia2;
+        F[F_IB2] = (float)ib2;
+        F[F_DIB] = (float)(ib2 - ia2);
         F[6] = F[7] = 0.0f;
     }
-    const double bhs = beta[lo + N];
-    const double est = floor((bhs - b.c0) / b.dc);
-    long long n = (long long)fmax(0.0, fmin(est, (double)b.n_c));
-    while (n > 0 && !(grid_c(b.c0, b.dc, (int)(n - 1)) < bhs)) --n;
-    while (n < b.n_c && grid_c(b.c0, b.dc, (int)n) < bhs) ++n;
-    nlim[m] = (int32_t)n;
+    if (lane == 0) {
+        const double bhs = beta[lo + N];
+        const double est = floor((bhs - b.c0) / b.dc);
+        long long n = (long long)fmax(0.0, fmin(est, (double)b.n_c));
+        while (n > 0 && !(grid_c(b.c0, b.dc, (int)(n - 1)) < bhs)) --n;
+        while (n < b.n_c && grid_c(b.c0, b.dc, (int)n) < bhs) ++n;
+        nlim[m] = (int32_t)n;
+    }
 }
 
 cudaError_t launch_model_update(const DevBatch& b, const double* h, const double* alpha,
                                 const double* beta, const double* rho, double* layers,
                                 float* layers32, int32_t* nlim, int32_t* err, cudaStream_t s) {
     if (b.n_models <= 0) return cudaSuccess;
-    const int blocks = (b.n_models + 127) / 128;
+    const int blocks = (b.n_models + 3) / 4;  // 4 warps (models) per block
     validate_models_kernel<<<blocks, 128, 0, s>>>(b, h, alpha, beta, rho, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
