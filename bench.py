@@ -296,6 +296,8 @@ def run_extras(args, masw, torch):
         _, _, hist = inversion.gradient_inversion(b, ce_true, iters=10)
         torch.cuda.synchronize()
         t_grad = time.perf_counter() - t0
+        inversion.metropolis(b, ce_true, steps=2, step_frac=0.01)  # warm-up (first torch RNG use)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, _, _, acc = inversion.metropolis(b, ce_true, steps=20, step_frac=0.01)
         torch.cuda.synchronize()
