@@ -215,16 +215,14 @@ __global__ void __launch_bounds__(256) screen32_kernel(DevBatch b, const float* 
     }
 }
 
-// Paired linear FP32 scan of one item by one warp from grid index `start`
-// (`carry`: the FP32 sign assumed at V[start - 1]; unused for start 0): lane
-// l evaluates the adjacent points base + 2l and base + 2l + 1 with packed
-// FP32x2 arithmetic (64 points per chunk); the first change is the first set
-// bit of the interleaved masks. Returns the index (warp-uniform) or -1.
+// Paired linear FP32 scan of one item by one warp from V[0]: lane l
+// evaluates the adjacent points base + 2l and base + 2l + 1 with packed FP32x2
+// arithmetic (64 points per chunk); the first change is the first set bit of
+// the interleaved masks. Returns the index (warp-uniform) or -1.
 __device__ __forceinline__ int screen_paired_item(const float* __restrict__ lay, int N, float k,
-                                                  float c0, float dc, int nlim, int start,
-                                                  int carry, int lane) {
-    int res = -1;
-    for (int base = start; base < nlim && res < 0; base += 64) {
+                                                  float c0, float dc, int nlim, int lane) {
+    int res = -1, carry = 0;
+    for (int base = 0; base < nlim && res < 0; base += 64) {
         const int n0 = base + 2 * lane, n1 = n0 + 1;
         int s0 = 0, s1 = 0;
         if (n1 < nlim) {
@@ -279,7 +277,7 @@ __global__ void __launch_bounds__(256) screen32p_kernel(DevBatch b, const float*
         }
         const float k = (float)b.k[item];
         const int nlim = b.model_nlim[m];
-        int res = nlim >= 2 ? screen_paired_item(lay, N, k, c0, dc, nlim, 0, 0, lane) : -1;
+        int res = nlim >= 2 ? screen_paired_item(lay, N, k, c0, dc, nlim, lane) : -1;
         if (lane == 0) n32out[item] = res;
         __syncwarp();
         if (persistent) {

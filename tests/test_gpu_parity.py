@@ -427,3 +427,30 @@ def test_misfit_gradient_matches_oracle_finite_differences(masw, oracle_lib):
         ref = np.r_[gb_ref, gh_ref]
         got = np.r_[gbeta[loff[k]:loff[k + 1]], gh[hoff[k]:hoff[k + 1]]]
         assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_grid_finer_than_fp32_resolution(masw, oracle_lib):
+    """Test velocities 1e-5 m/s apart near 188 m/s: FP32 cannot tell
+    neighbouring grid points apart (its spacing there is ~1.5e-5), so the
+    counting search only locates each change approximately; the FP64
+    certificate, its walk and the FP64 re-scan still return the FP64 scan's
+    index for every item, for both two-precision plans. 24 wavelengths of one
+    model put their roots inside the 0.4 m/s window."""
+    base, _ = W.uniform_batch(n_models=1, n_layers=4, n_lambda=2, lam_max=40.0, seed=31)
+    h, a, b, r, _ = base.model(0)
+    lam = np.linspace(10.0, 10.45, 24)
+    m = W.Models(np.array([4], np.int32), h, a, b, r, np.array([24], np.int32), lam)
+    g = W.Grid(188.40, 1e-5, 40000)
+    out = {}
+    for p in (0, 1, 2):
+        with masw.Batch(m, g) as bt:
+            bt.set_plan(precision=p)
+            out[p] = bt.dispersion()
+    for p in (1, 2):
+        assert np.array_equal(out[p][1], out[0][1]), p
+        assert np.array_equal(out[p][2], out[0][2]), p
+    assert (out[0][2] == 0).all()
+    # and the oracle agrees within the parity bar on a few of them
+    for j in (0, 11, 23):
+        st, _, idx = oracle_lib.scan(h, a, b, r, lam[j], g.c0, g.dc, g.n_c)
+        assert st == 0 and abs(idx - out[0][1][j]) <= 1
