@@ -27,6 +27,7 @@ _SO = os.path.join(_BUILD, "libmasw_oracle.so")
 OK = 0
 NO_ROOT = 1
 EINVAL = -1
+MAX_KH = 300.0  # domain of the plain hyperbolic functions: k h <= MAX_KH in every layer
 ENOMEM = -2
 MAX_LAYERS = 256
 

@@ -207,6 +207,27 @@ def uniform_stress(target: float, repeats: int, n_models: int = 256) -> tuple[Mo
     return m, Grid(50.0, 0.25, 4601)
 
 
+def extreme_batch(n_models: int = 256, n_lambda: int = 32, seed: int = SEED + 8
+                  ) -> tuple[Models, Grid]:
+    """Models outside the paper's ranges, for robustness tests: 1..30 layers
+    with log-uniform thicknesses 0.05..50 m, unsorted shear speeds 60..1500 m/s
+    (low-velocity layers, strong contrasts), Poisson ratios 0.1..0.45,
+    densities 1000..3000 kg/m^3, a half-space 1.0..1.5 times faster than the
+    fastest layer, and n_lambda log-spaced wavelengths 0.5..500 m per model;
+    c grid 50..2500 m/s step 0.5."""
+    rng = np.random.default_rng(seed)
+    profiles = []
+    for N in rng.integers(1, 31, n_models):
+        beta = rng.uniform(60.0, 1500.0, N + 1)
+        beta[N] = beta[:N].max() * rng.uniform(1.0, 1.5)
+        nu = rng.uniform(0.1, 0.45, N + 1)
+        h = np.exp(rng.uniform(np.log(0.05), np.log(50.0), N))
+        profiles.append((h, alpha_from_nu(beta, nu), beta, rng.uniform(1000.0, 3000.0, N + 1)))
+    lams = [np.geomspace(0.5, 500.0, n_lambda)] * n_models
+    m = _pack(profiles, lams, {"workload": f"extreme models x {n_models}, seed {seed}"})
+    return m, Grid(50.0, 0.5, 4901)
+
+
 def differentiation_batch(n_models: int = 512, n_layers: int = 12, n_lambda: int = 150,
                           grid: Grid | None = None, seed: int = SEED + 4,
                           spread: float = 0.05) -> tuple[Models, Grid, Models]:

@@ -56,16 +56,18 @@ def test_the_bound_is_nearly_tight(oracle_lib):
     assert max(np.abs(d[flips])) / (k * 1900.0 * beta ** 2) > 1e3
 
 
-@pytest.mark.parametrize("which", ["uniform", "ragged"])
+@pytest.mark.parametrize("which", ["uniform", "ragged", "extreme"])
 def test_negative_eigenvalue_count_is_monotone_and_marks_the_first_change(oracle_lib, which):
-    rng = np.random.default_rng(32 if which == "uniform" else 33)
+    rng = np.random.default_rng({"uniform": 32, "ragged": 33, "extreme": 34}[which])
     if which == "uniform":
         m, g = W.uniform_batch(n_models=16, n_lambda=10)
-    else:
+    elif which == "ragged":
         m, g = W.ragged_batch(n_models=24, lambdas=(8, 12))
+    else:
+        m, g = W.extreme_batch(n_models=40, n_lambda=12)
     item_model = np.repeat(np.arange(m.n_models), m.n_lambda)
     checked = 0
-    for it in rng.choice(m.n_items, 40, replace=False):
+    for it in rng.choice(m.n_items, 40 if which != "extreme" else 100, replace=False):
         h, a, b, r, _ = m.model(item_model[it])
         lam = m.lam[it]
         k = 2.0 * np.pi / lam

@@ -93,6 +93,25 @@ def test_full_size_first_change_and_sampled_oracle(masw, oracle_lib, which):
     assert_changes_parity(idx[items], st[items], dl[items], o_idx, o_dl)
 
 
+
+def test_extreme_models_changes(masw, oracle_lib):
+    """Models outside the paper's ranges (thin stiff layers, low-velocity
+    layers, up to 30 layers): the first change is the batch scan's index and a
+    sample of (item, change) entries matches the oracle's continued scan."""
+    m, g = W.extreme_batch(n_models=128, seed=W.SEED + 9)
+    M = 4
+    with masw.Batch(m, g) as b:
+        _, idx, st, dl = b.changes(M)
+        _, idx1, st1 = b.dispersion()
+    assert np.array_equal(idx[:, 0], np.where(st1 == 0, idx1, -1))
+    assert set(np.unique(dl)) <= {-1, 0, 1}
+    hmax = np.array([m.model(q)[0].max() for q in range(m.n_models)])
+    item_model = np.repeat(np.arange(m.n_models), m.n_lambda)
+    inside = np.nonzero(2 * np.pi / m.lam * hmax[item_model] <= oracle_lib.MAX_KH)[0]
+    items = np.random.default_rng(9).choice(inside, size=120, replace=False)
+    o_idx, o_dl = oracle_changes(oracle_lib, m, g, items, M)
+    assert_changes_parity(idx[items], st[items], dl[items], o_idx, o_dl)
+
 def test_edges_limits_and_device_outputs(masw, oracle_lib):
     torch = pytest.importorskip("torch")
     # grid above the fundamental root, a model with no scannable points, M = 1 and 15

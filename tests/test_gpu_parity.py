@@ -42,6 +42,14 @@ def oracle_items(oracle_lib, models, grid, items):
     return ct, idx, st
 
 
+def oracle_domain(oracle_lib, models):
+    """Items the oracle accepts: k h <= its MAX_KH in every layer (it uses the
+    plain, unscaled hyperbolic functions)."""
+    hmax = np.array([models.model(q)[0].max() for q in range(models.n_models)])
+    item_model = np.repeat(np.arange(models.n_models), models.n_lambda)
+    return np.nonzero(2 * np.pi / models.lam * hmax[item_model] <= oracle_lib.MAX_KH)[0]
+
+
 def assert_index_parity(g_idx, g_st, o_idx, o_st, frac=0.999):
     assert (g_st == o_st).all(), np.nonzero(g_st != o_st)
     ok = o_st == 0
@@ -454,3 +462,26 @@ def test_grid_finer_than_fp32_resolution(masw, oracle_lib):
     for j in (0, 11, 23):
         st, _, idx = oracle_lib.scan(h, a, b, r, lam[j], g.c0, g.dc, g.n_c)
         assert st == 0 and abs(idx - out[0][1][j]) <= 1
+
+
+@pytest.mark.parametrize("seed", [101, 102])
+def test_extreme_models_two_precision_equals_fp64_scan(masw, oracle_lib, seed):
+    """Both two-precision plans against the pure FP64 scan, item for item, on
+    models chosen to stress the counting search (tight pole-free bounds,
+    low-velocity layers, thin stiff layers, large k h); a sample against the
+    oracle at the parity bar."""
+    m, g = W.extreme_batch(seed=seed)
+    with masw.Batch(m, g) as bt:
+        bt.set_plan(precision=0)
+        ref = bt.dispersion()
+        for p in (1, 2):
+            bt.set_plan(precision=p)
+            got = bt.dispersion()
+            assert np.array_equal(got[1], ref[1]), (p, np.nonzero(got[1] != ref[1])[0][:10])
+            assert np.array_equal(got[2], ref[2]), p
+        fb = bt.last_scan_fallback()
+    assert (ref[2] == 0).mean() > 0.5 and fb >= 0
+    items = np.random.default_rng(seed).choice(oracle_domain(oracle_lib, m), size=48,
+                                               replace=False)
+    o_ct, o_idx, o_st = oracle_items(oracle_lib, m, g, items)
+    assert_index_parity(ref[1][items], ref[2][items], o_idx, o_st)
