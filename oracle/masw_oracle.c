@@ -18,6 +18,10 @@
  *   change, listing the first M sign changes in order (oracle_scan_changes);
  *   the Python wrapper labels each with the change in K's negative-eigenvalue
  *   count (numpy's symmetric eigensolver on the dense K).
+ *   Leaky continuation (Section 3.4: the paper's stiffness matrices are
+ *   complex): Algorithm 1 over the whole grid, test velocities at or above
+ *   the half-space shear speed included, with the sign of the real part of
+ *   the complex determinant (oracle_scan_leaky).
  *
  * Deliberately plain: K is assembled as a DENSE matrix and its determinant is
  * taken by dense LU with partial pivoting (sign = parity of row swaps times
@@ -61,7 +65,15 @@
  *   - C_t is the upper end V[n] of the first sign-changing pair.
  *   - Domain: k h <= ORACLE_MAX_KH for every layer (the unscaled cosh/sinh
  *     products would overflow beyond it); outside it calls return EINVAL.
+ *   - Leaky continuation: at c >= beta of the half-space its vertical
+ *     slownesses are imaginary; r and s are the principal complex square
+ *     roots of 1 - c^2/alpha^2 and 1 - c^2/beta^2 (the same closed form
+ *     continued), the finite layers stay real, and the sign of a complex
+ *     determinant is the sign of its real part. Taking the other root for
+ *     both r and s conjugates K and det K, so that sign is the same on
+ *     either branch.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -203,6 +215,100 @@ void oracle_lu_det(int n, double* A, int* sign, double* log_abs) {
     *log_abs = la;
 }
 
+/* ------------------------------------------------ leaky continuation */
+
+/* 2x2 half-space stiffness for any c > 0, complex: the closed form above with
+ * r = csqrt(1 - c^2/alpha^2) and s = csqrt(1 - c^2/beta^2) (principal roots;
+ * real below the wave speeds, +i * sqrt(.) above them). Row-major. */
+void oracle_halfspace_stiffness_complex(double k, double c, double alpha, double beta,
+                                        double rho, double complex* Kh) {
+    double mu = rho * beta * beta;
+    double q = (c * c) / (beta * beta);
+    double complex r = csqrt(1.0 - (c * c) / (alpha * alpha) + 0.0 * I);
+    double complex s = csqrt(1.0 - q + 0.0 * I);
+    double complex den = 1.0 - r * s;
+    double km = k * mu;
+    double complex off = (2.0 * r * s - 1.0 - s * s) / den;
+    Kh[0] = km * r * q / den;
+    Kh[1] = km * off;
+    Kh[2] = km * off;
+    Kh[3] = km * s * q / den;
+}
+
+/* Dense complex global stiffness, n = 2(N+1), row-major: the real layer
+ * blocks of oracle_assemble plus the complex half-space block. */
+void oracle_assemble_complex(int N, const double* h, const double* alpha,
+                             const double* beta, const double* rho, double k, double c,
+                             double complex* K) {
+    int n = 2 * (N + 1);
+    for (size_t i = 0; i < (size_t)n * (size_t)n; ++i) K[i] = 0.0;
+    double Ke[16];
+    for (int i = 0; i < N; ++i) {
+        oracle_layer_stiffness(k, c, h[i], alpha[i], beta[i], rho[i], Ke);
+        int base = 2 * i;
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b)
+                K[(size_t)(base + a) * n + (base + b)] += Ke[a * 4 + b];
+    }
+    double complex Kh[4];
+    oracle_halfspace_stiffness_complex(k, c, alpha[N], beta[N], rho[N], Kh);
+    int base = 2 * N;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            K[(size_t)(base + a) * n + (base + b)] += Kh[a * 2 + b];
+}
+
+/* Complex determinant by LU with partial pivoting (largest modulus). A is
+ * overwritten. The determinant is kept as phase * exp(log_abs) with |phase|
+ * = 1 (the product of the pivots' unit phases and the row-swap signs);
+ * phase = 0 and log_abs = -inf when singular. */
+void oracle_lu_det_complex(int n, double complex* A, double complex* phase, double* log_abs) {
+    double complex ph = 1.0;
+    double la = 0.0;
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        double best = cabs(A[(size_t)col * n + col]);
+        for (int row = col + 1; row < n; ++row) {
+            double v = cabs(A[(size_t)row * n + col]);
+            if (v > best) { best = v; piv = row; }
+        }
+        if (!(best > 0.0)) {
+            *phase = 0.0;
+            *log_abs = -INFINITY;
+            return;
+        }
+        if (piv != col) {
+            for (int j = 0; j < n; ++j) {
+                double complex t = A[(size_t)col * n + j];
+                A[(size_t)col * n + j] = A[(size_t)piv * n + j];
+                A[(size_t)piv * n + j] = t;
+            }
+            ph = -ph;
+        }
+        double complex p = A[(size_t)col * n + col];
+        ph *= p / cabs(p);
+        la += log(cabs(p));
+        for (int row = col + 1; row < n; ++row) {
+            double complex m = A[(size_t)row * n + col] / p;
+            if (m == 0.0) continue;
+            for (int j = col + 1; j < n; ++j)
+                A[(size_t)row * n + j] -= m * A[(size_t)col * n + j];
+        }
+    }
+    *phase = ph;
+    *log_abs = la;
+}
+
+/* Sign of Re det K(k, c) for any c > 0 and ln|det K|. */
+static int det_re_sign(int N, const double* h, const double* alpha, const double* beta,
+                       const double* rho, double k, double c, double complex* K,
+                       double* log_abs) {
+    oracle_assemble_complex(N, h, alpha, beta, rho, k, c, K);
+    double complex ph;
+    oracle_lu_det_complex(2 * (N + 1), K, &ph, log_abs);
+    return sgn(creal(ph));
+}
+
 /* Domain of the plain (unscaled) hyperbolic functions: products of two
  * cosh(k h x) stay finite while k h <= ORACLE_MAX_KH for every layer. */
 static int in_domain(int N, const double* h, double k) {
@@ -228,6 +334,51 @@ int oracle_scan_limit(double beta_hs, double c0, double dc, int n_c) {
     int n = 0;
     while (n < n_c && oracle_grid_velocity(c0, dc, n) < beta_hs) ++n;
     return n;
+}
+
+/* Sign of Re det K(k, c) (complex half-space block at c >= beta_hs) and
+ * ln|det K|, for any c > 0. */
+int oracle_det_leaky(int N, const double* h, const double* alpha, const double* beta,
+                     const double* rho, double k, double c, int* sign_re, double* log_abs) {
+    if (!in_domain(N, h, k) || !(c > 0.0)) return ORACLE_EINVAL;
+    int n = 2 * (N + 1);
+    double complex* K = (double complex*)malloc(sizeof(double complex) * (size_t)n * (size_t)n);
+    if (!K) return ORACLE_ENOMEM;
+    *sign_re = det_re_sign(N, h, alpha, beta, rho, k, c, K, log_abs);
+    free(K);
+    return ORACLE_OK;
+}
+
+/* Algorithm 1 over the whole grid V[0..n_c-1] with the sign of Re det K
+ * (leaky continuation). Returns ORACLE_OK or ORACLE_NO_ROOT. */
+int oracle_scan_leaky(int N, const double* h, const double* alpha, const double* beta,
+                      const double* rho, double lambda, double c0, double dc, int n_c,
+                      double* ct, int* idx) {
+    double k = 2.0 * M_PI / lambda;
+    *ct = NAN;
+    *idx = -1;
+    if (!in_domain(N, h, k) || !(c0 > 0.0)) return ORACLE_EINVAL;
+    int n = 2 * (N + 1);
+    double complex* K = (double complex*)malloc(sizeof(double complex) * (size_t)n * (size_t)n);
+    if (!K) return ORACLE_ENOMEM;
+    int status = ORACLE_NO_ROOT;
+    double la;
+    if (n_c >= 2) {
+        int s_old = det_re_sign(N, h, alpha, beta, rho, k, oracle_grid_velocity(c0, dc, 0), K, &la);
+        for (int j = 1; j < n_c; ++j) {
+            double c = oracle_grid_velocity(c0, dc, j);
+            int s_new = det_re_sign(N, h, alpha, beta, rho, k, c, K, &la);
+            if (s_new != s_old) {
+                *ct = c;
+                *idx = j;
+                status = ORACLE_OK;
+                break;
+            }
+            s_old = s_new;
+        }
+    }
+    free(K);
+    return status;
 }
 
 /* Algorithm 1 for one wavelength. Returns ORACLE_OK or ORACLE_NO_ROOT. */

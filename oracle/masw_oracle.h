@@ -49,6 +49,17 @@ int oracle_root_grad_fd(int N, const double* h, const double* alpha, const doubl
                         const double* rho, double lambda, double c0, double dc, int n_c,
                         int idx, double rel_step, double rel_tol, double* dC_dbeta,
                         double* dC_dh);
+int oracle_det_leaky(int N, const double* h, const double* alpha, const double* beta,
+                     const double* rho, double k, double c, int* sign_re, double* log_abs);
+int oracle_scan_leaky(int N, const double* h, const double* alpha, const double* beta,
+                      const double* rho, double lambda, double c0, double dc, int n_c,
+                      double* ct, int* idx);
+/* complex matrices as interleaved (re, im) doubles (C99 double complex) */
+void oracle_halfspace_stiffness_complex(double k, double c, double alpha, double beta,
+                                        double rho, double _Complex* Kh);
+void oracle_assemble_complex(int N, const double* h, const double* alpha, const double* beta,
+                             const double* rho, double k, double c, double _Complex* K);
+void oracle_lu_det_complex(int n, double _Complex* A, double _Complex* phase, double* log_abs);
 double oracle_misfit_paper(int L, const double* ct, const double* ce);
 double oracle_misfit_lsq(int L, const double* ct, const double* ce, double sigma);
 

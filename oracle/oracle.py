@@ -82,6 +82,16 @@ def _load():
     lib.oracle_root.argtypes = [i, p, p, p, p, d, d, d, i, i, d, p]
     lib.oracle_root_grad_fd.restype = i
     lib.oracle_root_grad_fd.argtypes = [i, p, p, p, p, d, d, d, i, i, d, d, p, p]
+    lib.oracle_det_leaky.restype = i
+    lib.oracle_det_leaky.argtypes = [i, p, p, p, p, d, d, p, p]
+    lib.oracle_scan_leaky.restype = i
+    lib.oracle_scan_leaky.argtypes = [i, p, p, p, p, d, d, d, i, p, p]
+    lib.oracle_halfspace_stiffness_complex.restype = None
+    lib.oracle_halfspace_stiffness_complex.argtypes = [d, d, d, d, d, p]
+    lib.oracle_assemble_complex.restype = None
+    lib.oracle_assemble_complex.argtypes = [i, p, p, p, p, d, d, p]
+    lib.oracle_lu_det_complex.restype = None
+    lib.oracle_lu_det_complex.argtypes = [i, p, p, p]
     lib.oracle_misfit_paper.restype = d
     lib.oracle_misfit_paper.argtypes = [i, p, p]
     lib.oracle_misfit_lsq.restype = d
@@ -214,6 +224,55 @@ def dispersion(models, c0, dc, n_c, n_threads: int = 0):
     if err != OK:
         raise MemoryError("oracle_dispersion")
     return ct, idx, st
+
+
+def halfspace_stiffness_complex(k, c, alpha, beta, rho) -> np.ndarray:
+    """2x2 complex half-space stiffness for any c > 0 (principal roots r, s)."""
+    out = np.empty(4, dtype=np.complex128)
+    _load().oracle_halfspace_stiffness_complex(k, c, alpha, beta, rho, _ptr(out))
+    return out.reshape(2, 2)
+
+
+def assemble_complex(h, alpha, beta, rho, k, c) -> np.ndarray:
+    """Dense complex global stiffness (real layers, complex half-space)."""
+    h, alpha, beta, rho = _f64(h), _f64(alpha), _f64(beta), _f64(rho)
+    n = 2 * (h.size + 1)
+    K = np.empty((n, n), dtype=np.complex128)
+    _load().oracle_assemble_complex(h.size, _ptr(h), _ptr(alpha), _ptr(beta), _ptr(rho), k, c,
+                                    _ptr(K))
+    return K
+
+
+def lu_det_complex(A) -> tuple[complex, float]:
+    """(phase, ln|det|) of a dense complex matrix, det = phase * exp(ln|det|)."""
+    A = np.array(A, dtype=np.complex128, copy=True, order="C")
+    ph = np.zeros(1, dtype=np.complex128)
+    la = ctypes.c_double()
+    _load().oracle_lu_det_complex(A.shape[0], _ptr(A), _ptr(ph), ctypes.byref(la))
+    return complex(ph[0]), la.value
+
+
+def det_leaky(h, alpha, beta, rho, k, c) -> tuple[int, float]:
+    """(sign of Re det K, ln|det K|) for any c > 0 (leaky continuation)."""
+    h, alpha, beta, rho = _f64(h), _f64(alpha), _f64(beta), _f64(rho)
+    sg = ctypes.c_int()
+    la = ctypes.c_double()
+    st = _load().oracle_det_leaky(h.size, _ptr(h), _ptr(alpha), _ptr(beta), _ptr(rho), k, c,
+                                  ctypes.byref(sg), ctypes.byref(la))
+    if st != OK:
+        raise ValueError(f"oracle_det_leaky failed ({st})")
+    return sg.value, la.value
+
+
+def scan_leaky(h, alpha, beta, rho, lam, c0, dc, n_c) -> tuple[int, float, int]:
+    """Algorithm 1 over the whole grid with the sign of Re det K:
+    (status, C_t, index)."""
+    h, alpha, beta, rho = _f64(h), _f64(alpha), _f64(beta), _f64(rho)
+    ct = ctypes.c_double()
+    idx = ctypes.c_int()
+    st = _load().oracle_scan_leaky(h.size, _ptr(h), _ptr(alpha), _ptr(beta), _ptr(rho), lam,
+                                   c0, dc, n_c, ctypes.byref(ct), ctypes.byref(idx))
+    return st, ct.value, idx.value
 
 
 def refine(h, alpha, beta, rho, lam, c_lo, c_hi, rel_tol=1e-13) -> float:
