@@ -364,6 +364,24 @@ def run_extras(args, masw, torch):
                            "roots_fraction_of_found": float(np.mean(hdl[hst == 0] == 1)),
                            "poles_fraction_of_found": float(np.mean(hdl[hst == 0] == -1))}
 
+    # leaky continuation: the whole grid with the sign of Re det K
+    lm, lg = W.leaky_batch()
+    with masw.Batch(lm, lg) as b:
+        _, lidx, lst = b.leaky()
+        _, _, lst1 = b.dispersion()
+        lms, lscan = [], []
+        for _ in range(5):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.leaky()
+            lms.append(time.perf_counter() - t0)
+            lscan.append(b.last_scan_ms())
+    out["leaky"] = {"workload": lm.meta["workload"] + ", host outputs",
+                    "curves_per_s": lm.n_models / min(lms), "ms": 1e3 * min(lms),
+                    "batch_scan_ms": float(np.median(lscan)),
+                    "found_fraction": float(np.mean(lst == 0)),
+                    "continued_fraction": float(np.mean((lst1 != 0) & (lst == 0)))}
+
     # first use: batch creation (upload, records, graph capture) and the first
     # scan of a fresh batch vs the warm median (CUDA context and library
     # already loaded in this process)

@@ -253,6 +253,31 @@ int masw_last_scan_unresolved(const masw_batch* batch, int32_t* n);
 int masw_dispersion_changes(masw_batch* batch, int32_t max_changes, double* ct, int32_t* ct_idx,
                             int32_t* status, int32_t* delta_count, int32_t out_mem_space);
 
+/* ---------------------------------------------------------------------
+ * Leaky continuation. The paper builds its stiffness matrices in complex
+ * arithmetic (Section 3.4) and takes the sign of their determinants
+ * (Algorithm 1); masw_dispersion scans only below the half-space shear speed,
+ * where K is real. This scans the whole grid.
+ * --------------------------------------------------------------------- */
+
+/* Algorithm 1 over every test velocity V[0..n_c-1] with the sign of Re det K:
+ * at c >= beta_halfspace the half-space block is complex, with
+ * s = i sqrt(c^2/beta^2 - 1) and r = sqrt(1 - c^2/alpha^2) or
+ * i sqrt(c^2/alpha^2 - 1) in the same closed form; the finite layers stay
+ * real. Taking the other root for both r and s conjugates det K, so the sign
+ * of its real part does not depend on the branch. For each item: ct = V[n]
+ * and ct_idx = n for the first n >= 1 whose sign differs from V[n-1]'s,
+ * status MASW_FOUND; MASW_NO_ROOT (NaN, -1) when there is none on the whole
+ * grid. Below beta_halfspace the sign is masw_dispersion's, so every item that
+ * masw_dispersion resolves keeps its result; the others are continued in FP64
+ * from the scan limit. Outputs per item in item order (host or device buffers
+ * per out_mem_space, any may be NULL). Also leaves masw_dispersion's outputs
+ * of the batch updated. Runs on the batch stream; synchronises it for host
+ * outputs. Device buffers of n_items entries are allocated on first use
+ * (MASW_ENOMEM when that fails). */
+int masw_dispersion_leaky(masw_batch* batch, double* ct, int32_t* ct_idx, int32_t* status,
+                          int32_t out_mem_space);
+
 /* Items of the most recent counting-search scan (plan precision 2) that fell
  * back to the linear FP32 screen (change above the pole-free bound, at V[0],
  * or an even count jump); -1 for other plans. Synchronises the batch stream. */

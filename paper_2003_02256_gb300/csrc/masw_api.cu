@@ -84,7 +84,9 @@ struct masw_batch {
     int32_t* d_chg_status = nullptr;
     int32_t* d_chg_delta = nullptr;
     int32_t* d_chg_counters = nullptr;
-
+    // leaky continuation (allocated on first use): per-item outputs, counter
+    double* d_lk_ct = nullptr;
+    int32_t* d_lk_idx = nullptr;  // [n_items] idx, then [n_items] status, then counter
     masw_plan plan{};
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -287,7 +289,7 @@ static void free_batch(masw_batch* B) {
                     B->d_dphi, B->d_ce, B->d_misfit, B->d_gb, B->d_gh, B->d_layers32,
                     B->d_n32, B->d_ref, B->d_unres, B->d_fallback, B->d_counters, B->d_upd, B->d_upd_err,
                     B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta,
-                    B->d_chg_counters};
+                    B->d_chg_counters, B->d_lk_ct, B->d_lk_idx};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete B;
@@ -676,6 +678,30 @@ int masw_dispersion_changes(masw_batch* B, int32_t max_changes, double* ct, int3
         (rc = copy_out(ct_idx, B->d_chg_idx, ne, B->stream, &sync)) ||
         (rc = copy_out(status, B->d_chg_status, ne, B->stream, &sync)) ||
         (rc = copy_out(delta_count, B->d_chg_delta, ne, B->stream, &sync)))
+        return rc;
+    if (sync) CK(cudaStreamSynchronize(B->stream));
+    return MASW_OK;
+}
+
+int masw_dispersion_leaky(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* status,
+                          int32_t out_mem_space) {
+    if (!B || (out_mem_space != MASW_HOST && out_mem_space != MASW_DEVICE)) return MASW_EINVAL;
+    const size_t nw = B->n_items;
+    if ((!B->d_lk_ct && dev_alloc(&B->d_lk_ct, std::max<size_t>(nw, 1))) ||
+        (!B->d_lk_idx && dev_alloc(&B->d_lk_idx, 2 * nw + 1)))
+        return MASW_ENOMEM;
+    // below the half-space shear speed: Algorithm 1 with the batch plan
+    int rc0 = run_scan(B);
+    if (rc0) return rc0;
+    int32_t* lk_status = B->d_lk_idx + nw;
+    ScanOut o{B->d_lk_ct, B->d_lk_idx, lk_status};
+    CK(launch_leaky(B->dev(B->plan.ordered != 0), to_scan_plan(B, B->plan), B->d_idx,
+                    B->d_status, o, B->d_lk_idx + 2 * nw, B->stream));
+    bool sync = false;
+    int rc;
+    if ((rc = copy_out(ct, B->d_lk_ct, nw, B->stream, &sync)) ||
+        (rc = copy_out(ct_idx, B->d_lk_idx, nw, B->stream, &sync)) ||
+        (rc = copy_out(status, lk_status, nw, B->stream, &sync)))
         return rc;
     if (sync) CK(cudaStreamSynchronize(B->stream));
     return MASW_OK;

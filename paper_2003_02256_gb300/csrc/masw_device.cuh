@@ -325,6 +325,65 @@ __device__ __forceinline__ int det_sign(const double* __restrict__ lay, int N, d
     return sg * sgn(fma(s00, s11, -s01 * s01));
 }
 
+// Sign of Re det K(k, c) for any c > 0: Algorithm 1's sign continued to test
+// velocities at or above the half-space shear speed, where the paper's
+// complex stiffness matrices (Section 3.4) have a complex half-space block.
+// The finite layers stay real (even functions), so only the last 2x2 pivot is
+// complex. There s = i sqrt(q - 1) and r = sqrt(1 - p) or i sqrt(p - 1)
+// (the same closed form continued; the other root for both conjugates det K
+// and leaves the sign of its real part unchanged). With u = 1 - r s (never 0
+// there) and K_hs = k M / u, M = [[rho c^2 r, mu (q - 2u)], [.., rho c^2 s]],
+// the pivot is S = Phat / w + M / u = Shat / (u w) with Shat = u Phat + w M, so
+// det S = det Shat / (u w)^2 and sign Re det S = sign Re(det Shat conj(u)^2):
+// no division. Below the shear speed this is det_sign's arithmetic exactly.
+__device__ inline int det_sign_leaky(const double* __restrict__ lay, int N, double k, double c) {
+    double c2 = c * c;
+    HState st{0.0, 0.0, 0.0, 1.0};
+    int sg = 1;
+    for (int j = 0; j < N; ++j) {
+        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2);
+        bool ok;
+        double det = schur_layer(st, n, &ok);
+        sg *= sgn(det);
+        if (!ok) return 0;
+    }
+    const double* __restrict__ H = lay + N * LAYER_STRIDE;
+    const double q = c2 * H[L_IB2];
+    if (q < 1.0) {
+        HalfNum hn = halfspace_numerators(H, c2);
+        double s00 = fma(hn.den, st.p00, st.w * hn.m00);
+        double s01 = fma(hn.den, st.p01, st.w * hn.m01);
+        double s11 = fma(hn.den, st.p11, st.w * hn.m11);
+        return sg * sgn(fma(s00, s11, -s01 * s01));
+    }
+    const double p = c2 * H[L_IA2];
+    const double sig = sqrt(q - 1.0);  // s = i sig
+    double r_re, r_im, u_re, u_im;
+    if (p < 1.0) {  // r real: r s = i r sig
+        r_re = sqrt(1.0 - p);
+        r_im = 0.0;
+        u_re = 1.0;
+        u_im = -r_re * sig;
+    } else {        // r = i r_im: r s = -r_im sig
+        r_re = 0.0;
+        r_im = sqrt(p - 1.0);
+        u_re = fma(r_im, sig, 1.0);
+        u_im = 0.0;
+    }
+    const double rc2 = H[L_RHO] * c2, mu = H[L_MU], w = st.w;
+    // Shat = u Phat + w M (Phat real)
+    const double a_re = fma(u_re, st.p00, w * rc2 * r_re), a_im = fma(u_im, st.p00, w * rc2 * r_im);
+    const double b_re = fma(u_re, st.p01, w * mu * fma(-2.0, u_re, q));
+    const double b_im = fma(u_im, st.p01, w * mu * (-2.0 * u_im));
+    const double d_re = u_re * st.p11, d_im = fma(u_im, st.p11, w * rc2 * sig);
+    // det Shat = a d - b^2
+    const double t_re = fma(a_re, d_re, -a_im * d_im) - fma(b_re, b_re, -b_im * b_im);
+    const double t_im = fma(a_re, d_im, a_im * d_re) - 2.0 * b_re * b_im;
+    // conj(u)^2 = (u_re^2 - u_im^2, -2 u_re u_im)
+    const double v_re = fma(u_re, u_re, -u_im * u_im), v_im = -2.0 * u_re * u_im;
+    return sg * sgn(fma(t_re, v_re, -t_im * v_im));
+}
+
 // Number of negative eigenvalues of K(k, c) (Sylvester's law of inertia over
 // the 2x2 Schur pivots S_j = Shat_j / (w Dh)): a pivot with det < 0 has one,
 // one with det > 0 has two when its diagonal is negative. A zero determinant

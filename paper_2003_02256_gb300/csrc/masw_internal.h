@@ -58,6 +58,13 @@ cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const in
                            double* ct, int32_t* idx, int32_t* status, int32_t* delta,
                            int32_t* counter, cudaStream_t s);
 
+// Leaky continuation: Algorithm 1 over the whole grid with the sign of Re det K
+// (complex half-space block at c >= beta_hs); items the batch scan resolved
+// (status_in 0) keep idx_in; outputs o; counter: 1 (masw_kernels.cu).
+cudaError_t launch_leaky(const DevBatch& b, const ScanPlan& p, const int32_t* idx_in,
+                         const int32_t* status_in, const ScanOut& o, int32_t* counter,
+                         cudaStream_t s);
+
 cudaError_t launch_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p, int32_t* counter,
                         int item_begin, int item_end, cudaStream_t s);
 cudaError_t launch_det_eval(const DevBatch& b, int n, const int32_t* item, const double* c,

@@ -728,6 +728,77 @@ cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const in
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------ leaky continuation
+//
+// Algorithm 1 over the whole grid with the sign of Re det K (det_sign_leaky):
+// test velocities at or above the half-space shear speed included. Below it
+// K is real and this is Algorithm 1 itself, so an item whose batch scan found
+// a change keeps it; the others have the same sign at V[0..nlim-1] and are
+// continued here in FP64 from V[max(nlim, 1) - 1]. One warp per item
+// (persistent, popping b.order), 32 consecutive points per chunk.
+
+__global__ void __launch_bounds__(256) leaky_scan64_kernel(DevBatch b, ScanOut o,
+                                                           const int32_t* __restrict__ idx_in,
+                                                           const int32_t* __restrict__ status_in,
+                                                           int32_t* counter) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= b.n_items) return;
+        const int item = b.order[t];
+        int found = -1;
+        if (status_in[item] == 0) {
+            found = idx_in[item];
+        } else {
+            const int m = b.item_model[item];
+            const int lo = b.model_loff[m];
+            const int N = b.model_loff[m + 1] - lo - 1;
+            const double* lay = b.layers + (size_t)lo * LAYER_STRIDE;
+            const double k = b.k[item];
+            const int start = max(b.model_nlim[m], 1);
+            int carry = 0;
+            for (int base = start - 1; base < b.n_c; base += 32) {
+                const int n = base + lane;
+                const int sg = n < b.n_c ? det_sign_leaky(lay, N, k, grid_c(b.c0, b.dc, n)) : 0;
+                int ps = __shfl_up_sync(FULL, sg, 1);
+                if (lane == 0) ps = carry;
+                const unsigned msk = __ballot_sync(FULL, n >= start && n < b.n_c && sg != ps);
+                if (msk) {
+                    found = base + __ffs(msk) - 1;
+                    break;
+                }
+                carry = __shfl_sync(FULL, sg, 31);
+            }
+        }
+        if (lane == 0) {
+            if (found >= 0) {
+                o.ct[item] = grid_c(b.c0, b.dc, found);
+                o.idx[item] = found;
+                o.status[item] = 0;
+            } else {
+                o.ct[item] = __longlong_as_double(0x7ff8000000000000LL);
+                o.idx[item] = -1;
+                o.status[item] = 1;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_leaky(const DevBatch& b, const ScanPlan& p, const int32_t* idx_in,
+                         const int32_t* status_in, const ScanOut& o, int32_t* counter,
+                         cudaStream_t s) {
+    if (b.n_items == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const int wpb = p.warps_per_block;
+    leaky_scan64_kernel<<<std::max(1, std::min(p.blocks, (b.n_items + wpb - 1) / wpb)), 32 * wpb,
+                          0, s>>>(b, o, idx_in, status_in, counter);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ math check
 
 // The library's e^x (exp_neg, x <= 0) beside CUDA's exp at the same points.

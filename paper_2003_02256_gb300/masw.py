@@ -75,6 +75,7 @@ def load():
         "masw_dispersion": [p, p, p, p, i32],
         "masw_dispersion_plain": [p, p, p, p, i32],
         "masw_dispersion_changes": [p, i32, p, p, p, p, i32],
+        "masw_dispersion_leaky": [p, p, p, p, i32],
         "masw_misfit": [p, p, i32, d, p],
         "masw_misfit_grad": [p, p, i32, d, p, p, p],
         "masw_roots": [p, p],
@@ -206,6 +207,14 @@ def dispersion_changes(handle, max_changes, ct, ct_idx, status, delta_count):
     _check(load().masw_dispersion_changes(ctypes.c_void_p(handle), int(max_changes), _ptr(ct),
                                           _ptr(ct_idx), _ptr(status), _ptr(delta_count), space),
            "masw_dispersion_changes")
+
+
+def dispersion_leaky(handle, ct, ct_idx, status):
+    """Algorithm 1 over the whole grid with the sign of Re det K (complex
+    half-space block at and above its shear speed; masw_dispersion_leaky)."""
+    space = _space(next(x for x in (ct, ct_idx, status) if x is not None))
+    _check(load().masw_dispersion_leaky(ctypes.c_void_p(handle), _ptr(ct), _ptr(ct_idx),
+                                        _ptr(status), space), "masw_dispersion_leaky")
 
 
 def misfit(handle, ce, kind, sigma, out):
@@ -374,6 +383,14 @@ class Batch:
         dl = np.empty(shape, dtype=np.int32)
         dispersion_changes(self.handle, max_changes, ct, idx, st, dl)
         return ct, idx, st, dl
+
+    def leaky(self):
+        """(ct, idx, status) of the whole-grid scan with the sign of Re det K."""
+        ct = np.empty(self.n_items)
+        idx = np.empty(self.n_items, dtype=np.int32)
+        st = np.empty(self.n_items, dtype=np.int32)
+        dispersion_leaky(self.handle, ct, idx, st)
+        return ct, idx, st
 
     def roots(self):
         out = np.empty(self.n_items)

@@ -228,6 +228,18 @@ def extreme_batch(n_models: int = 256, n_lambda: int = 32, seed: int = SEED + 8
     return m, Grid(50.0, 0.5, 4901)
 
 
+def leaky_batch(n_models: int = 1024, n_lambda: int = 200) -> tuple[Models, Grid]:
+    """The uniform batch's models on a c grid 700..1700 m/s step 0.25, which
+    starts above most of their fundamental modes and above about half of
+    their half-space shear speeds (5 / 50 / 95 % at 526 / 691 / 855 m/s for
+    the full batch), so most first sign changes lie where the half-space
+    block is complex."""
+    m, _ = uniform_batch(n_models=n_models, n_lambda=n_lambda)
+    m.meta = dict(m.meta, workload=f"uniform_batch models x {n_models}, {n_lambda} lambda; "
+                                   "c grid 700..1700 step 0.25 (leaky continuation)")
+    return m, Grid(700.0, 0.25, 4001)
+
+
 def differentiation_batch(n_models: int = 512, n_layers: int = 12, n_lambda: int = 150,
                           grid: Grid | None = None, seed: int = SEED + 4,
                           spread: float = 0.05) -> tuple[Models, Grid, Models]:
