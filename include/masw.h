@@ -207,8 +207,10 @@ int masw_last_scan_ms(const masw_batch* batch, float* ms);
  * scan launched without a graph (plan use_graph 0), from CUDA events between
  * the launches on the batch stream. Plan precision 1: ms[0] FP32 screen,
  * ms[1] FP64 check, ms[2] FP64 re-scan. Plan precision 2: ms[0] counting
- * search with its FP64 certificate (one fused kernel), ms[1] linear scan and
- * FP64 check of the fallback items, ms[2] FP64 re-scan. MASW_EINVAL when that
+ * search with its FP64 certificate (one fused kernel), ms[1] linear FP32 scan
+ * and FP64 check of the fallback items and the FP64 mode-count search of the
+ * items that failed a check, ms[2] FP64 re-scan (items whose FP64 counts
+ * failed). Plan precision 1: ms[1] also includes that search. MASW_EINVAL when that
  * scan was graph-replayed. */
 int masw_last_scan_phases(const masw_batch* batch, float* ms);
 
@@ -221,8 +223,10 @@ int masw_last_scan_phases(const masw_batch* batch, float* ms);
 int masw_last_scan_screen(masw_batch* batch, int32_t* n32);
 
 /* Items of the most recent two-precision scan (plan precision 1 or 2) whose FP32
- * screen disagreed with the FP64 check and were re-scanned in FP64 (-1 for a
- * precision-0 plan). Synchronises the batch stream. */
+ * result failed its FP64 check (the counting certificate, or the three-point
+ * check on the Wittrick-Williams mode count) and whose first change was then
+ * searched on the FP64 mode count from V[0] (-1 for a precision-0 plan).
+ * Synchronises the batch stream. */
 int masw_last_scan_unresolved(const masw_batch* batch, int32_t* n);
 
 /* ---------------------------------------------------------------------
@@ -243,15 +247,29 @@ int masw_last_scan_unresolved(const masw_batch* batch, int32_t* n);
  * Outputs are [n_items][max_changes] in item order (host or device buffers
  * per out_mem_space, any may be NULL): ct = V[n] (NaN when fewer changes),
  * ct_idx = n (-1), status MASW_FOUND / MASW_NO_ROOT, delta_count (0). The
- * first change is masw_dispersion's (the batch plan); from one point below it
- * the scan runs in FP64 at every grid point (no FP32 screen: next to a pole an
- * FP32 error can hide a root-pole pair inside one grid interval). It also
+ * first change is masw_dispersion's (the batch plan). Past it, with plan
+ * precision 1 or 2, the changes are found by FP64 search on the
+ * Wittrick-Williams count T = s + 2 J0 (s: negative eigenvalues of K; J0:
+ * modes of the finite layers with both faces clamped, counted by halving each
+ * layer's thickness), which never decreases along the grid and jumps by an odd
+ * amount exactly where det K changes sign: about 2 log3(n_lim) evaluations per
+ * event. Items whose FP64 counts fail (see masw_last_changes_linear) and plan
+ * precision 0 use the FP64 scan at every grid point from one point below the
+ * first change. No FP32 screen is used past the first change: next to a pole
+ * an FP32 error can hide a root-pole pair inside one grid interval. It also
  * leaves masw_dispersion's outputs of the batch updated. Runs on the batch
  * stream; synchronises it for host outputs. Device buffers of n_items x
  * max_changes are allocated on first use. MASW_EINVAL for max_changes out of
  * range. */
 int masw_dispersion_changes(masw_batch* batch, int32_t max_changes, double* ct, int32_t* ct_idx,
                             int32_t* status, int32_t* delta_count, int32_t out_mem_space);
+
+/* Items of the most recent masw_dispersion_changes call whose FP64 mode counts
+ * failed (a rescaling failure, or the count not monotone at the evaluated
+ * points) and that were scanned at every grid point instead; -1 when that
+ * call used the plain FP64 scan (plan precision 0) or none was made.
+ * Synchronises the batch stream. */
+int masw_last_changes_linear(const masw_batch* batch, int32_t* n);
 
 /* ---------------------------------------------------------------------
  * Leaky continuation. The paper builds its stiffness matrices in complex
@@ -279,8 +297,10 @@ int masw_dispersion_leaky(masw_batch* batch, double* ct, int32_t* ct_idx, int32_
                           int32_t out_mem_space);
 
 /* Items of the most recent counting-search scan (plan precision 2) that fell
- * back to the linear FP32 screen (change above the pole-free bound, at V[0],
- * or an even count jump); -1 for other plans. Synchronises the batch stream. */
+ * back from the FP32 search (change above the pole-free bound, a mode below
+ * V[0], or an even count jump) to the linear FP32 scan, checked like plan
+ * precision 1 on the FP64 mode count; -1 for other plans. Synchronises the
+ * batch stream. */
 int masw_last_scan_fallback(const masw_batch* batch, int32_t* n);
 
 /* The library's own FP64 exponential (e^x for x <= 0, a table-driven method;

@@ -70,7 +70,7 @@ struct masw_batch {
     // two-precision scan
     float* d_layers32 = nullptr;
     int32_t* d_n32 = nullptr;
-    int32_t* d_ref = nullptr;
+    int32_t* d_search = nullptr;
     int32_t* d_unres = nullptr;
     int32_t* d_fallback = nullptr;
     int32_t* d_counters = nullptr;  // SCAN_COUNTERS
@@ -83,7 +83,8 @@ struct masw_batch {
     int32_t* d_chg_idx = nullptr;
     int32_t* d_chg_status = nullptr;
     int32_t* d_chg_delta = nullptr;
-    int32_t* d_chg_counters = nullptr;
+    int32_t* d_chg_counters = nullptr;  // CHANGES_COUNTERS, then an n_items list
+    bool changes_counted = false;
     // leaky continuation (allocated on first use): per-item outputs, counter
     double* d_lk_ct = nullptr;
     int32_t* d_lk_idx = nullptr;  // [n_items] idx, then [n_items] status, then counter
@@ -287,7 +288,7 @@ static void free_batch(masw_batch* B) {
                     B->d_item_model, B->d_order_sorted, B->d_order_natural, B->d_grad_off,
                     B->d_counter, B->d_ct, B->d_idx, B->d_status, B->d_croot, B->d_rows, B->d_bs,
                     B->d_dphi, B->d_ce, B->d_misfit, B->d_gb, B->d_gh, B->d_layers32,
-                    B->d_n32, B->d_ref, B->d_unres, B->d_fallback, B->d_counters, B->d_upd, B->d_upd_err,
+                    B->d_n32, B->d_search, B->d_unres, B->d_fallback, B->d_counters, B->d_upd, B->d_upd_err,
                     B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta,
                     B->d_chg_counters, B->d_lk_ct, B->d_lk_idx};
     for (void* p : ptrs)
@@ -336,7 +337,7 @@ static cudaError_t enqueue_scan(masw_batch* B, const masw_plan& p, cudaStream_t 
     if (p.precision >= 1) {
         ScanOut o{B->d_ct, B->d_idx, B->d_status};
         return launch_screen_scan(B->dev(p.ordered != 0), o, to_scan_plan(B, p), B->d_layers32,
-                                  B->d_n32, B->d_ref, B->d_unres, B->d_fallback, B->d_counters,
+                                  B->d_n32, B->d_search, B->d_unres, B->d_fallback, B->d_counters,
                                   p.precision == 2, 0, (int)B->n_items, s,
                                   phase_events ? B->phase_ev : nullptr);
     }
@@ -516,7 +517,7 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
         dev_alloc(&B->d_grad_off, nw + 1) || dev_alloc(&B->d_counter, 1) ||
         dev_alloc(&B->d_ct, nw) || dev_alloc(&B->d_idx, nw) || dev_alloc(&B->d_status, nw) ||
         dev_alloc(&B->d_layers32, rec32.size()) || dev_alloc(&B->d_n32, nw) ||
-        dev_alloc(&B->d_ref, nw) || dev_alloc(&B->d_unres, nw) || dev_alloc(&B->d_fallback, nw) ||
+        dev_alloc(&B->d_search, nw) || dev_alloc(&B->d_unres, nw) || dev_alloc(&B->d_fallback, nw) ||
         dev_alloc(&B->d_counters, SCAN_COUNTERS)) {
         free_batch(B);
         return MASW_ENOMEM;
@@ -665,13 +666,16 @@ int masw_dispersion_changes(masw_batch* B, int32_t max_changes, double* ct, int3
             return MASW_ENOMEM;
         B->chg_cap = max_changes;
     }
-    if (!B->d_chg_counters && dev_alloc(&B->d_chg_counters, 1)) return MASW_ENOMEM;
+    if (!B->d_chg_counters && dev_alloc(&B->d_chg_counters, CHANGES_COUNTERS + nw))
+        return MASW_ENOMEM;
     // the first change: Algorithm 1 with the batch plan (an FP64 decision)
     int rc0 = run_scan(B);
     if (rc0) return rc0;
     CK(launch_changes(B->dev(B->plan.ordered != 0), to_scan_plan(B, B->plan), max_changes,
                       B->d_idx, B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta,
-                      B->d_chg_counters, B->stream));
+                      B->d_chg_counters, B->d_chg_counters + CHANGES_COUNTERS,
+                      B->plan.precision >= 1, B->stream));
+    B->changes_counted = B->plan.precision >= 1;
     bool sync = false;
     int rc;
     if ((rc = copy_out(ct, B->d_chg_ct, ne, B->stream, &sync)) ||
@@ -739,7 +743,7 @@ int masw_dispersion_plain(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* s
     CK(cudaEventRecord(B->ev0, B->stream));
     for (int32_t m = 0; m < B->n_models; ++m) {
         if (p.precision >= 1)
-            CK(launch_screen_scan(d, o, sp, B->d_layers32, B->d_n32, B->d_ref, B->d_unres,
+            CK(launch_screen_scan(d, o, sp, B->d_layers32, B->d_n32, B->d_search, B->d_unres,
                                   B->d_fallback, B->d_counters, p.precision == 2, B->woff[m],
                                   B->woff[m + 1], B->stream, nullptr));
         else
@@ -777,7 +781,7 @@ int masw_last_scan_unresolved(const masw_batch* B, int32_t* n) {
     }
     int32_t v = 0;
     CK(cudaStreamSynchronize(B->stream));
-    CK(cudaMemcpy(&v, B->d_counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&v, B->d_counters + 5, sizeof(int32_t), cudaMemcpyDeviceToHost));
     *n = v;
     return MASW_OK;
 }
@@ -791,6 +795,19 @@ int masw_last_scan_fallback(const masw_batch* B, int32_t* n) {
     int32_t v = 0;
     CK(cudaStreamSynchronize(B->stream));
     CK(cudaMemcpy(&v, B->d_counters + 3, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    *n = v;
+    return MASW_OK;
+}
+
+int masw_last_changes_linear(const masw_batch* B, int32_t* n) {
+    if (!B || !n) return MASW_EINVAL;
+    if (!B->changes_counted || !B->d_chg_counters) {
+        *n = -1;
+        return MASW_OK;
+    }
+    int32_t v = 0;
+    CK(cudaStreamSynchronize(B->stream));
+    CK(cudaMemcpy(&v, B->d_chg_counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
     *n = v;
     return MASW_OK;
 }

@@ -16,7 +16,9 @@
 //    one FP64 step of two points in that direction, inside the range. An
 //    even FP64 count (two or more) after count 0 means no sign change there:
 //    a second search looks for the first odd count above it, certified the
-//    same way; failing that the linear scan takes over from that point.
+//    same way. Items left without a certificate fall back: the batch path
+//    searches the FP64 mode count s + 2 J0 from V[0] (masw_modes.cuh), the
+//    serving tick scans linearly from `start`.
 #pragma once
 
 #include "masw_device.cuh"
@@ -27,7 +29,7 @@ namespace masw {
 struct PairCount {
     int cert;   // certified first change (>= 1), or -1
     int n;      // the search's index when the certificate failed (>= 1), or -1
-    int start;  // cert and n < 1: the linear scan's start (npf when the range holds no
+    int start;  // cert and n < 1: a linear scan's start (npf when the range holds no
                 // change, the located point after an even FP64 count, else 0)
 };
 
@@ -123,7 +125,7 @@ __device__ __forceinline__ PairCount count_certify_pair(const float* __restrict_
         // no sign change there). The first change is the first point above n
         // whose count is odd: search for the first count above vb and certify
         // count vb one point below it (so vb, an even count, all the way from
-        // n) and an odd count at it; otherwise the linear scan starts at n.
+        // n) and an odd count at it; otherwise the item falls back with start n.
         const int m = pair_search(lay32, N, kf, c0f, dcf, n, npf - 1, vb + 1, half, pair);
         if (m > n) {
             const int u = det_inertia(lay, N, k, grid_c(c0, dc, m - 1 + half));

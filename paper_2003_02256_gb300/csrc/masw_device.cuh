@@ -444,6 +444,59 @@ __device__ inline int det_sign_count(const double* __restrict__ lay, int N, doub
     return sg * sgn(det);
 }
 
+// Number of modes of one layer with both faces clamped below c (J0 of
+// Wittrick-Williams for that element). A clamped layer of thickness h is two
+// clamped halves joined at a free middle node, whose stiffness is
+// K22(h/2) + K11(h/2) = diag(2a, 2d) (the half layer's diagonal entries), so
+// J0(h) = 2 J0(h/2) + [a(h/2) < 0] + [d(h/2) < 0]; the recursion ends at the
+// thickness h/2^L under whose pole-free bound beta sqrt(1 + (pi/(k h))^2) c
+// lies (J0 = 0 there): 2^L > k h sqrt(c^2/beta^2 - 1) / pi. The even functions
+// at h/2^L come from wave_fns and are doubled level by level,
+// E(2x) = E^2, C(2x) = 2C^2 - E^2, Sd(2x) = 2 Sd C, Sm(2x) = 2 Sm C (the
+// e^-x scaling of real w carried along); the signs of a and d are those of
+// their numerators times that of D, all scaled by the same positive factor.
+// Zero below the layer's shear speed.
+__device__ inline int clamped_modes(const double* __restrict__ L, double k, double c2) {
+    const double q = c2 * L[L_IB2];
+    if (!(q > 1.0)) return 0;
+    const double x = k * L[L_H] * sqrt(q - 1.0) * 0.31830988618379067;  // 1/pi
+    if (!(x >= 1.0)) return 0;
+    // levels: 2^lv > x >= 2^(lv-1)
+    const int lv = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1022;
+    const double khf = scale_pow2(k * L[L_H], -lv);
+    Wave R = wave_fns(khf, 1.0 - c2 * L[L_IA2]);
+    Wave S = wave_fns(khf, 1.0 - q);
+    int J = 0;
+    for (int j = lv; j >= 1; --j) {
+        if (j < lv) {
+            R = Wave{R.E * R.E, fma(2.0 * R.C, R.C, -R.E * R.E), 2.0 * R.Sd * R.C, 2.0 * R.Sm * R.C};
+            S = Wave{S.E * S.E, fma(2.0 * S.C, S.C, -S.E * S.E), 2.0 * S.Sd * S.C, 2.0 * S.Sm * S.C};
+        }
+        const double D = fma(2.0, fma(R.E, S.E, -R.C * S.C), fma(R.Sd, S.Sd, R.Sm * S.Sm));
+        const double an = fma(R.C, S.Sd, -S.C * R.Sm);
+        const double dn = fma(S.C, R.Sd, -R.C * S.Sm);
+        J = 2 * J + (int)((an < 0.0) != (D < 0.0)) + (int)((dn < 0.0) != (D < 0.0));
+    }
+    return J;
+}
+
+// Wittrick-Williams mode count of the layered structure below c, split as
+// (s, J0): s = negative eigenvalues of K (det_inertia; -1 when the rescaling
+// failed), J0 = clamped modes of all finite layers (the half-space has none
+// below its shear speed). J = J0 + s, the number of modes below c, never
+// decreases with c, and neither does T = J + J0 = s + 2 J0, whose parity is
+// that of s: det K changes sign between two test velocities exactly when T
+// jumps by an odd amount between them. Requires c < beta_halfspace.
+__device__ inline int mode_count_T(const double* __restrict__ lay, int N, double k, double c,
+                                   int* s_out) {
+    const int s = det_inertia(lay, N, k, c);
+    const double c2 = c * c;
+    int j0 = 0;
+    for (int j = 0; j < N; ++j) j0 += clamped_modes(lay + j * LAYER_STRIDE, k, c2);
+    *s_out = s;
+    return s < 0 ? -1 : s + 2 * j0;
+}
+
 // x = m * 2^e with |m| in [1, 2) for a normal x (integer pipe); zero,
 // subnormals and inf/NaN are returned unchanged with e = 0.
 __device__ __forceinline__ double split_pow2(double x, int* e) {

@@ -38,25 +38,31 @@ struct ScanPlan {
     int stage_layers;     // layer records staged in shared memory per warp (0 = read global)
 };
 
-// FP32 screen + FP64 decision (masw_screen.cuh, masw_kernels.cu). search 0:
-// linear FP32 screen; 1: counting search with the linear screen as fallback.
-// n32, ref_sign, unresolved, fallback: n_items each; counters: SCAN_COUNTERS.
-constexpr int SCAN_COUNTERS = 5;
+// FP32 screen + FP64 decision (masw_screen.cuh, masw_kernels.cu). counting
+// 0: linear FP32 screen; 1: counting search with the linear screen as
+// fallback. Both check on the FP64 mode count and search it for the items
+// that fail. n32, search, unresolved, fallback: n_items each; counters:
+// SCAN_COUNTERS ([5]: items that failed their FP64 check).
+constexpr int SCAN_COUNTERS = 7;
 // n32 flag of an index located by the counting search (MASW_SCREEN_COUNTED)
 constexpr int32_t SCREEN_COUNTED = 1 << 30;
 cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p,
-                               const float* layers32, int32_t* n32, int32_t* ref_sign,
+                               const float* layers32, int32_t* n32, int32_t* search,
                                int32_t* unresolved, int32_t* fallback, int32_t* counters,
-                               int search, int item_begin, int item_end, cudaStream_t s,
+                               int counting, int item_begin, int item_end, cudaStream_t s,
                                cudaEvent_t* phase_ev);
 
 // Algorithm 1 continued: the first M sign changes per item with their
-// negative-eigenvalue count changes, scanned in FP64 from one point below the
-// first change `first` (the batch scan's index, -1: none); outputs
-// [n_items][M]; counter: 1 (masw_kernels.cu).
+// negative-eigenvalue count changes, from the first change `first` (the batch
+// scan's index, -1: none); outputs [n_items][M]. counting 0: FP64 linear scan
+// from one point below it; 1: FP64 search on the monotone mode count
+// s + 2 J0, items whose counts fail going to the linear scan (linear:
+// n_items entries). counters: CHANGES_COUNTERS, [1] = linear-scan items
+// (masw_kernels.cu).
+constexpr int CHANGES_COUNTERS = 2;
 cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const int32_t* first,
                            double* ct, int32_t* idx, int32_t* status, int32_t* delta,
-                           int32_t* counter, cudaStream_t s);
+                           int32_t* counters, int32_t* linear, int counting, cudaStream_t s);
 
 // Leaky continuation: Algorithm 1 over the whole grid with the sign of Re det K
 // (complex half-space block at c >= beta_hs); items the batch scan resolved

@@ -22,6 +22,7 @@
 #include "masw_count.cuh"
 #include "masw_device.cuh"
 #include "masw_internal.h"
+#include "masw_modes.cuh"
 #include "masw_screen.cuh"
 
 namespace masw {
@@ -135,17 +136,25 @@ cudaError_t launch_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p, 
 
 // ------------------------------------------------- two-precision scan
 //
+// Plan precision 1 (linear):
 // 1. screen32_kernel: the scan of scan_kernel in FP32 (det_sign_f), giving
 //    the FP32 first sign change n32 per item (-1 if none below the limit).
-// 2. verify64_kernel: one thread per item, FP64 signs (det_sign) at V[0],
-//    V[n32-1], V[n32]; the item is resolved to n32 when V[0] and V[n32-1]
-//    agree and V[n32] differs (or, for n32 = -1, to "no root" when V[0] and
-//    the last scanned point agree); otherwise it goes to the unresolved list.
-// 3. resolve64_kernel: one warp per unresolved item, FP64 chunked scan
-//    starting 16 points below n32 (its first point must carry V[0]'s sign,
-//    else from V[0]), continuing until the first FP64 change.
-// Every reported index is a sign change of the FP64 recurrence whose lower
-// point carries the FP64 sign of V[0].
+// 2. verify64_kernel: one thread per item, the FP64 mode count T = s + 2 J0
+//    (mode_count_T; never decreasing, odd jumps exactly at the sign changes)
+//    at V[0], V[n32-1], V[n32]: the item is resolved to n32 when T(V[0]) =
+//    T(V[n32-1]) and T jumps by an odd amount at n32 (for n32 = -1, to "no
+//    root" when T(V[0]) equals T at the last point); otherwise it goes to
+//    the search list.
+// Plan precision 2 (counting): count_certify_kernel (FP32 search on the
+// negative-eigenvalue count below the pole-free bound, FP64 certificate);
+// its fallback items take fallback32_kernel (linear FP32 scan) and
+// verify64_list_kernel (the check of 2. over the list); uncertified and
+// unverified items go to the search list.
+// Both: first_count64_kernel searches the listed items' first change on the
+// FP64 mode count from V[0]; items whose FP64 counts fail take
+// resolve64_kernel, the FP64 scan from V[0].
+// Every reported index is where the FP64 mode count first jumps by an odd
+// amount (the FP64 sign first changes) or, for the last few, the FP64 scan's.
 
 template <int CPL>
 __global__ void __launch_bounds__(256) screen32_kernel(DevBatch b, const float* __restrict__ layers32,
@@ -302,11 +311,16 @@ __device__ __forceinline__ void write_result(const DevBatch& b, const ScanOut& o
     }
 }
 
-// Three-point FP64 check of a linear screen's index n (-1: no change seen):
-// FP64 signs at V[0], V[n-1], V[n] (or V[0] and the last scanned point).
+// Three-point FP64 check of a linear screen's index n (-1: no change seen)
+// on the mode count T = s + 2 J0 (mode_count_T), which never decreases along
+// the grid and jumps by an odd amount exactly at the sign changes: T(V[n-1])
+// = T(V[0]) leaves no change (no event at all) below n, an odd T(V[n]) -
+// T(V[n-1]) makes n a change; with no change seen, T(V[nlim-1]) = T(V[0]).
+// Signs alone would pass two changes that an FP32 screen missed together (a
+// root and a pole inside one grid interval). Anything else goes to the FP64
+// mode-count search from V[0] (first_count64_kernel).
 __device__ __forceinline__ void verify_item(const DevBatch& b, const ScanOut& o, int item, int n,
-                                            int32_t* ref_sign, int32_t* unresolved,
-                                            int32_t* n_unresolved) {
+                                            int32_t* search, int32_t* n_search) {
     const int m = b.item_model[item];
     const int lo = b.model_loff[m];
     const int N = b.model_loff[m + 1] - lo - 1;
@@ -317,32 +331,21 @@ __device__ __forceinline__ void verify_item(const DevBatch& b, const ScanOut& o,
         write_result(b, o, item, -1);
         return;
     }
-    int s0 = det_sign(lay, N, k, grid_c(b.c0, b.dc, 0));
-    bool ok;
-    if (n >= 1) {
-        int sa = (n == 1) ? s0 : det_sign(lay, N, k, grid_c(b.c0, b.dc, n - 1));
-        int sb = det_sign(lay, N, k, grid_c(b.c0, b.dc, n));
-        ok = (sa == s0) && (sb != sa);
-    } else {
-        int sz = det_sign(lay, N, k, grid_c(b.c0, b.dc, nlim - 1));
-        ok = (sz == s0);
-    }
-    if (ok) {
-        write_result(b, o, item, n >= 1 ? n : -1);
-    } else {
-        ref_sign[item] = s0;
-        unresolved[atomicAdd(n_unresolved, 1)] = item;
-    }
+    int sv;
+    const int T0 = mode_count_T(lay, N, k, grid_c(b.c0, b.dc, 0), &sv);
+    const int Ta = (n == 1) ? T0 : mode_count_T(lay, N, k, grid_c(b.c0, b.dc, n >= 1 ? n - 1 : nlim - 1), &sv);
+    const int Tb = n >= 1 ? mode_count_T(lay, N, k, grid_c(b.c0, b.dc, n), &sv) : -1;
+    if (mode_count_verified(n, T0, Ta, Tb)) write_result(b, o, item, n >= 1 ? n : -1);
+    else search[atomicAdd(n_search, 1)] = item;
 }
 
 __global__ void verify64_kernel(DevBatch b, ScanOut o, const int32_t* __restrict__ n32,
-                                int32_t* ref_sign, int32_t* unresolved, int32_t* n_unresolved,
-                                int item_begin, int item_end) {
+                                int32_t* search, int32_t* n_search, int item_begin, int item_end) {
     // natural item order: a warp's threads share a model and have adjacent
     // wavelengths, so their FP64 branches (series / exp / sincos) agree
     const int item = item_begin + blockIdx.x * blockDim.x + threadIdx.x;
     if (item >= item_end) return;
-    verify_item(b, o, item, n32[item], ref_sign, unresolved, n_unresolved);
+    verify_item(b, o, item, n32[item], search, n_search);
 }
 
 // The same check over a device-counted list (the fallback items of the
@@ -353,8 +356,7 @@ __global__ void __launch_bounds__(128) verify64_list_kernel(DevBatch b, ScanOut 
                                                             const int32_t* __restrict__ n32,
                                                             const int32_t* __restrict__ list,
                                                             const int32_t* __restrict__ n_list,
-                                                            int32_t* ref_sign, int32_t* unresolved,
-                                                            int32_t* n_unresolved) {
+                                                            int32_t* search, int32_t* n_search) {
     const int total = *n_list;
     const int lane = threadIdx.x & 31;
     const int sub = lane & 3;
@@ -376,18 +378,14 @@ __global__ void __launch_bounds__(128) verify64_list_kernel(DevBatch b, ScanOut 
         const int n = n32[item];
         // lane 0: V[0]; lane 1: V[n-1] (no change seen: the last point); lane 2: V[n]
         const int pt = sub == 0 ? 0 : sub == 1 ? (n >= 1 ? n - 1 : nlim - 1) : sub == 2 ? (n >= 1 ? n : -1) : -1;
-        const int sg = pt >= 0 ? det_sign(lay, N, k, grid_c(b.c0, b.dc, pt)) : 0;
-        const int s0 = __shfl_sync(quad, sg, q0);
-        const int sa = __shfl_sync(quad, sg, q0 + 1);
-        const int sb = __shfl_sync(quad, sg, q0 + 2);
+        int sv;
+        const int T = pt >= 0 ? mode_count_T(lay, N, k, grid_c(b.c0, b.dc, pt), &sv) : -1;
+        const int T0 = __shfl_sync(quad, T, q0);
+        const int Ta = __shfl_sync(quad, T, q0 + 1);
+        const int Tb = __shfl_sync(quad, T, q0 + 2);
         if (sub != 0) continue;
-        const bool ok = n >= 1 ? (sa == s0 && sb != sa) : (sa == s0);
-        if (ok) {
-            write_result(b, o, item, n >= 1 ? n : -1);
-        } else {
-            ref_sign[item] = s0;
-            unresolved[atomicAdd(n_unresolved, 1)] = item;
-        }
+        if (mode_count_verified(n, T0, Ta, Tb)) write_result(b, o, item, n >= 1 ? n : -1);
+        else search[atomicAdd(n_search, 1)] = item;
     }
 }
 
@@ -464,21 +462,21 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
     }
 }
 
+
 // Counting search and its FP64 certificate (plan precision 2) fused in one
 // kernel, two lanes per item (count_certify_pair; natural item order: a
 // warp's 16 items share a model and have adjacent wavelengths, so their
 // branches agree). Fusing lets warps in the FP32 search and warps in the FP64
 // certificate share an SM: the two use different pipes. Items whose change
 // lies above the pole-free range, at V[0], or behind an even FP64 count go to
-// the fallback list, with the grid index to scan from in n32; uncertified
-// items go to the FP64 re-scan with V[0]'s sign. Certified items keep
-// SCREEN_COUNTED in n32.
+// the fallback list (linear FP32 scan and mode-count check); uncertified items
+// go to the FP64 mode-count search. Certified items keep SCREEN_COUNTED in
+// n32.
 __global__ void __launch_bounds__(128, 7) count_certify_kernel(DevBatch b, const float* __restrict__ layers32,
                                                                ScanOut o, int32_t* __restrict__ n32,
-                                                               int32_t* ref_sign, int32_t* unresolved,
-                                                               int32_t* n_unresolved, int32_t* fallback,
-                                                               int32_t* n_fallback, int item_begin,
-                                                               int item_end) {
+                                                               int32_t* search, int32_t* n_search,
+                                                               int32_t* fallback, int32_t* n_fallback,
+                                                               int item_begin, int item_end) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int item = item_begin + (t >> 1);
     if (item >= item_end) return;  // both lanes of a pair leave together
@@ -504,17 +502,123 @@ __global__ void __launch_bounds__(128, 7) count_certify_kernel(DevBatch b, const
         write_result(b, o, item, r.cert);
     } else if (r.n >= 1) {
         n32[item] = r.n;
-        ref_sign[item] = det_sign(lay, N, b.k[item], grid_c(b.c0, b.dc, 0));
-        unresolved[atomicAdd(n_unresolved, 1)] = item;
+        search[atomicAdd(n_search, 1)] = item;
     } else {
         n32[item] = r.start;
         fallback[atomicAdd(n_fallback, 1)] = item;
     }
 }
 
+// Items that failed their FP64 check (the counting search's certificate or
+// the three-point mode-count check of a linear FP32 scan; mostly items with
+// an even jump of the mode count below their first change, a mode trapped in
+// a low-velocity layer next to a pole of that layer): Algorithm 1's first
+// change as the first odd jump of the FP64 mode count T = s + 2 J0 above V[0].
+// A group of G lanes per item (groups pop the list): lane l of the group
+// holds T at V[x_l], x_l = l top / (G - 1) (x_0 = 0, x_{G-1} = top), for the
+// whole item; an event's bracket between two of those points is narrowed with
+// G - 1 interior points per round until it is one grid step wide; an odd jump
+// ends the search, an even one moves on to the next event. n32 gets the index
+// found (-1: none). Items whose FP64 counts fail (rescaling, or T not
+// monotone at the evaluated points) go to the FP64 re-scan from V[0].
+template <int G>
+__global__ void __launch_bounds__(256) first_count64_kernel(DevBatch b, ScanOut o, int32_t* n32,
+                                                            const int32_t* __restrict__ list,
+                                                            const int32_t* __restrict__ n_list,
+                                                            int32_t* counter, int32_t* unresolved,
+                                                            int32_t* n_unresolved) {
+    static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "lanes per item: a power of two");
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int gbase = lane - gl;
+    const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << gbase);
+    const int total = *n_list;
+    for (;;) {
+        int t = 0;
+        if (gl == 0) t = atomicAdd(counter, 1);
+        t = __shfl_sync(gmask, t, 0, G);
+        if (t >= total) return;  // the whole group leaves together
+        const int item = list[t];
+        const int m = b.item_model[item];
+        const int l0 = b.model_loff[m];
+        const int N = b.model_loff[m + 1] - l0 - 1;
+        const double* lay = b.layers + (size_t)l0 * LAYER_STRIDE;
+        const double k = b.k[item];
+        const int top = b.model_nlim[m] - 1;  // >= 1 for listed items
+        const int xl = (int)(((long long)gl * top) / (G - 1));
+        int sl;
+        const int Tl = mode_count_T(lay, N, k, grid_c(b.c0, b.dc, xl), &sl);
+        const int Tprev = __shfl_up_sync(gmask, Tl, 1, G);
+        bool bad = (__ballot_sync(gmask, Tl < 0 || (gl > 0 && Tl < Tprev)) & gmask) != 0;
+        int Pn = 0, PT = __shfl_sync(gmask, Tl, 0, G), res = -1;
+        while (!bad) {
+            // coarse bracket: first sample above P with a larger T
+            const unsigned msk = (__ballot_sync(gmask, xl > Pn && Tl > PT) & gmask) >> gbase;
+            if (!msk) break;  // no event up to V[top]
+            const int f = __ffs(msk) - 1;
+            int hn = __shfl_sync(gmask, xl, f, G), hT = __shfl_sync(gmask, Tl, f, G);
+            const int xb = __shfl_sync(gmask, xl, f > 0 ? f - 1 : 0, G);
+            if (xb > Pn && __shfl_sync(gmask, Tl, f > 0 ? f - 1 : 0, G) != PT) {
+                bad = true;  // T not monotone between P and that sample
+                break;
+            }
+            int lo = max(Pn, xb);
+            while (hn - lo > 1) {
+                const int len = hn - lo;
+                const int y = lo + (int)(((long long)(gl + 1) * len) / G);
+                const bool in = gl < G - 1 && y > lo && y < hn;
+                int sy = 0, Ty = -1;
+                if (in) Ty = mode_count_T(lay, N, k, grid_c(b.c0, b.dc, y), &sy);
+                const int Typ = __shfl_up_sync(gmask, Ty, 1, G);
+                const bool inp = __shfl_up_sync(gmask, (int)in, 1, G) != 0;
+                if ((__ballot_sync(gmask, in && (Ty < PT || Ty > hT || (gl > 0 && inp && Ty < Typ))) &
+                     gmask) != 0) {
+                    bad = true;
+                    break;
+                }
+                const unsigned up = (__ballot_sync(gmask, in && Ty > PT) & gmask) >> gbase;
+                const unsigned lw = (__ballot_sync(gmask, in && Ty == PT) & gmask) >> gbase;
+                if (up) {
+                    const int g = __ffs(up) - 1;
+                    hn = __shfl_sync(gmask, y, g, G);
+                    hT = __shfl_sync(gmask, Ty, g, G);
+                    const unsigned below = lw & ((1u << g) - 1u);
+                    if (below) lo = __shfl_sync(gmask, y, 31 - __clz(below), G);
+                } else {
+                    lo = __shfl_sync(gmask, y, 31 - __clz(lw), G);  // lw != 0: len >= 2
+                }
+            }
+            if (bad) break;
+            if ((hT - PT) & 1) {
+                res = hn;
+                break;
+            }
+            Pn = hn;  // an even jump: no sign change here
+            PT = hT;
+        }
+        if (gl == 0) {
+            if (bad) {
+                n32[item] = 0;
+                unresolved[atomicAdd(n_unresolved, 1)] = item;
+            } else {
+                n32[item] = res;
+                write_result(b, o, item, res);
+            }
+        }
+        __syncwarp(gmask);
+    }
+}
+
+// Lanes per item of first_count64_kernel. Evaluations per event fall with G
+// and rounds per event rise; the kernel ends with its slowest items (many even
+// events), so both count. On the 8192-model ragged batch (1773 listed items)
+// the kernel took 3.05 / 1.86 / 2.33 ms for G = 8 / 16 / 32.
+constexpr int SEARCH_LANES = 16;
+
+// Items whose FP64 mode counts failed (a rescaling failure, or the count not
+// monotone at the evaluated points): Algorithm 1 in FP64 from V[0], one warp
+// per item, 32 points per chunk.
 __global__ void __launch_bounds__(256) resolve64_kernel(DevBatch b, ScanOut o,
-                                                        const int32_t* __restrict__ n32,
-                                                        const int32_t* __restrict__ ref_sign,
                                                         const int32_t* __restrict__ unresolved,
                                                         const int32_t* __restrict__ n_unresolved,
                                                         int32_t* counter) {
@@ -532,26 +636,8 @@ __global__ void __launch_bounds__(256) resolve64_kernel(DevBatch b, ScanOut o,
         const double* lay = b.layers + (size_t)lo * LAYER_STRIDE;
         const double k = b.k[item];
         const int nlim = b.model_nlim[m];
-        const int ref = ref_sign[item];
-        const int n = n32[item];
-        int base = 0, carry = 0, res = -1;
-        if (n >= 18) {
-            // window from n - 17: its first point must carry V[0]'s sign
-            base = n - 17;
-            int nn = base + lane;
-            int sg = (nn < nlim) ? det_sign(lay, N, k, grid_c(b.c0, b.dc, nn)) : 0;
-            int first = __shfl_sync(FULL, sg, 0);
-            if (first != ref) {
-                base = 0;  // an FP64 change below the window: scan from V[0]
-            } else {
-                int prev = __shfl_up_sync(FULL, sg, 1);
-                unsigned msk = __ballot_sync(FULL, lane >= 1 && nn < nlim && sg != prev);
-                if (msk) res = base + __ffs(msk) - 1;
-                carry = __shfl_sync(FULL, sg, 31);
-                base += 32;
-            }
-        }
-        for (; base < nlim && res < 0; base += 32) {
+        int carry = 0, res = -1;
+        for (int base = 0; base < nlim && res < 0; base += 32) {
             int nn = base + lane;
             int sg = (nn < nlim) ? det_sign(lay, N, k, grid_c(b.c0, b.dc, nn)) : 0;
             int prev = __shfl_up_sync(FULL, sg, 1);
@@ -566,22 +652,22 @@ __global__ void __launch_bounds__(256) resolve64_kernel(DevBatch b, ScanOut o,
 }
 
 cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p,
-                               const float* layers32, int32_t* n32, int32_t* ref_sign,
+                               const float* layers32, int32_t* n32, int32_t* search,
                                int32_t* unresolved, int32_t* fallback, int32_t* counters,
-                               int search, int item_begin, int item_end, cudaStream_t s,
+                               int counting, int item_begin, int item_end, cudaStream_t s,
                                cudaEvent_t* phase_ev) {
     if (item_end <= item_begin) return cudaSuccess;
     // counters: [0] screen queue, [1] unresolved count, [2] resolve queue,
-    // [3] fallback count, [4] fallback queue
+    // [3] fallback count, [4] fallback queue, [5] search count, [6] search queue
     cudaError_t e = cudaMemsetAsync(counters, 0, SCAN_COUNTERS * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     int wpb = p.warps_per_block;
     int blocks = p.persistent ? p.blocks : (item_end - item_begin + wpb - 1) / wpb;
     size_t shm = (size_t)wpb * p.stage_layers * LAYER_STRIDE32 * sizeof(float);
     int n = item_end - item_begin;
-    if (search) {
-        count_certify_kernel<<<(2 * n + 127) / 128, 128, 0, s>>>(b, layers32, o, n32, ref_sign,
-                                                                 unresolved, counters + 1, fallback,
+    if (counting) {
+        count_certify_kernel<<<(2 * n + 127) / 128, 128, 0, s>>>(b, layers32, o, n32, search,
+                                                                 counters + 5, fallback,
                                                                  counters + 3, item_begin, item_end);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (phase_ev && (e = cudaEventRecord(phase_ev[0], s)) != cudaSuccess) return e;
@@ -590,9 +676,8 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
             b, layers32, n32, fallback, counters + 3, counters + 4, p.stage_layers);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         verify64_list_kernel<<<std::max(1, std::min(p.blocks, (4 * n + 127) / 128)), 128, 0, s>>>(
-            b, o, n32, fallback, counters + 3, ref_sign, unresolved, counters + 1);
+            b, o, n32, fallback, counters + 3, search, counters + 5);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (phase_ev && (e = cudaEventRecord(phase_ev[1], s)) != cudaSuccess) return e;
     } else {
         switch (p.cpl) {
             case 1:
@@ -615,14 +700,17 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (phase_ev && (e = cudaEventRecord(phase_ev[0], s)) != cudaSuccess) return e;
-        verify64_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, o, n32, ref_sign, unresolved,
-                                                        counters + 1, item_begin, item_end);
+        verify64_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, o, n32, search, counters + 5, item_begin,
+                                                        item_end);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (phase_ev && (e = cudaEventRecord(phase_ev[1], s)) != cudaSuccess) return e;
     }
+    first_count64_kernel<SEARCH_LANES><<<std::max(1, std::min(p.blocks, (n + wpb - 1) / wpb)),
+                                         32 * wpb, 0, s>>>(b, o, n32, search, counters + 5,
+                                                           counters + 6, unresolved, counters + 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (phase_ev && (e = cudaEventRecord(phase_ev[1], s)) != cudaSuccess) return e;
     int rblocks = std::max(1, std::min(p.blocks, (n + wpb - 1) / wpb));
-    resolve64_kernel<<<rblocks, 32 * wpb, 0, s>>>(b, o, n32, ref_sign, unresolved, counters + 1,
-                                                  counters + 2);
+    resolve64_kernel<<<rblocks, 32 * wpb, 0, s>>>(b, o, unresolved, counters + 1, counters + 2);
     return cudaGetLastError();
 }
 
@@ -633,11 +721,13 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
 // the change in K's negative-eigenvalue count across it (Wittrick-Williams:
 // +1 where a mode of the layered structure is crossed, a root of det K; -1 at
 // a pole, a mode of a clamped layer). The first change is the batch scan's
-// result (an FP64 decision); from one point below it on, changes_scan64_kernel
-// scans in FP64 itself. An FP32 screen is not used past the first change:
-// next to a pole an FP32 rounding error can move the pole across a grid point,
-// and a root-pole pair inside one grid interval then vanishes from the FP32
-// signs without any sign or count change at the points around it.
+// result (an FP64 decision). Past it, changes_count64_kernel searches the
+// FP64 mode count (plan precision >= 1) and changes_scan64_kernel scans in
+// FP64 at every grid point (plan precision 0, and the items whose counts
+// fail). An FP32 screen is not used past the first change: next to a pole an
+// FP32 rounding error can move the pole across a grid point, and a root-pole
+// pair inside one grid interval then vanishes from the FP32 signs without any
+// sign or count change at the points around it.
 
 struct ChangesOut {
     double* ct;      // [n_items][M]
@@ -661,19 +751,23 @@ __device__ __forceinline__ void write_change(const DevBatch& b, const ChangesOut
     }
 }
 
-// One warp per item (persistent, popping b.order): FP64 sign and count at
-// 32 consecutive points per chunk from first[item] - 1; a change at n needs
-// n > the start point. Items whose first change is -1 have none.
+// One warp per item (persistent, popping b.order, or the list of *n_list
+// items when list is given): FP64 sign and count at 32 consecutive points per
+// chunk from first[item] - 1; a change at n needs n > the start point. Items
+// whose first change is -1 have none.
 __global__ void __launch_bounds__(256) changes_scan64_kernel(DevBatch b, ChangesOut o, int M,
                                                              const int32_t* __restrict__ first,
-                                                             int32_t* counter) {
+                                                             int32_t* counter,
+                                                             const int32_t* __restrict__ list,
+                                                             const int32_t* __restrict__ n_list) {
     const int lane = threadIdx.x & 31;
+    const int n_work = list ? *n_list : b.n_items;
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(counter, 1);
         t = __shfl_sync(FULL, t, 0);
-        if (t >= b.n_items) return;
-        const int item = b.order[t];
+        if (t >= n_work) return;
+        const int item = list ? list[t] : b.order[t];
         const size_t e0 = (size_t)item * M;
         const int n1 = first[item];
         int found = 0;
@@ -714,17 +808,72 @@ __global__ void __launch_bounds__(256) changes_scan64_kernel(DevBatch b, Changes
     }
 }
 
+// Counting form (plan precision >= 1): a pair of lanes per item checks the
+// first change n1 on the mode count (T and s in FP64 at V[n1-1] and V[n1]:
+// T must jump by an odd amount) and then takes the next M - 1 changes from
+// next_change (masw_modes.cuh). An item whose FP64 counts fail is listed for
+// the linear scan.
+__global__ void __launch_bounds__(128) changes_count64_kernel(DevBatch b, ChangesOut o, int M,
+                                                              const int32_t* __restrict__ first,
+                                                              int32_t* linear, int32_t* n_linear) {
+    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 1);
+    const int half = threadIdx.x & 1;
+    const unsigned pair = 3u << (threadIdx.x & 30);
+    if (t >= b.n_items) return;  // both lanes of a pair leave together
+    const int item = b.order[t];
+    const size_t e0 = (size_t)item * M;
+    const int n1 = first[item];
+    int found = 0;
+    bool bad = false;
+    if (n1 >= 1) {
+        const int m = b.item_model[item];
+        const int l0 = b.model_loff[m];
+        const int N = b.model_loff[m + 1] - l0 - 1;
+        const double* lay = b.layers + (size_t)l0 * LAYER_STRIDE;
+        const double k = b.k[item];
+        TPoint below, P;
+        eval_pair(lay, N, k, b.c0, b.dc, n1 - 1, n1, half, pair, &below, &P);
+        ModeSearch st = mode_search_init(lay, N, k, b.c0, b.dc, b.model_nlim[m] - 1, half, pair,
+                                         P, TPoint{-1, -1, 0});
+        st.bad = st.bad || below.T < 0 || P.T <= below.T || !((P.T - below.T) & 1);
+        if (half == 0) write_change(b, o, e0, n1, P.s - below.s);
+        found = 1;
+        while (found < M) {
+            int d = 0;
+            const int n = next_change(st, &d);
+            if (n < 0) break;
+            if (half == 0) write_change(b, o, e0 + found, n, d);
+            ++found;
+        }
+        bad = st.bad;
+        if (bad && half == 0) linear[atomicAdd(n_linear, 1)] = item;
+    }
+    if (half == 0 && !bad)
+        for (int mi = found; mi < M; ++mi) write_change(b, o, e0 + mi, -1, 0);
+}
+
 cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const int32_t* first,
                            double* ct, int32_t* idx, int32_t* status, int32_t* delta,
-                           int32_t* counter, cudaStream_t s) {
+                           int32_t* counters, int32_t* linear, int counting, cudaStream_t s) {
     if (b.n_items == 0) return cudaSuccess;
     if (M < 1) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+    cudaError_t e = cudaMemsetAsync(counters, 0, CHANGES_COUNTERS * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     const int wpb = p.warps_per_block;
+    const int lblocks = std::max(1, std::min(p.blocks, (b.n_items + wpb - 1) / wpb));
     ChangesOut o{ct, idx, status, delta};
-    changes_scan64_kernel<<<std::max(1, std::min(p.blocks, (b.n_items + wpb - 1) / wpb)), 32 * wpb,
-                            0, s>>>(b, o, M, first, counter);
+    if (!counting) {
+        changes_scan64_kernel<<<lblocks, 32 * wpb, 0, s>>>(b, o, M, first, counters, nullptr,
+                                                          nullptr);
+        return cudaGetLastError();
+    }
+    const long long threads = 2LL * b.n_items;
+    changes_count64_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(b, o, M, first, linear,
+                                                                           counters + 1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    changes_scan64_kernel<<<lblocks, 32 * wpb, 0, s>>>(b, o, M, first, counters, linear,
+                                                      counters + 1);
     return cudaGetLastError();
 }
 

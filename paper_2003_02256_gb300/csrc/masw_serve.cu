@@ -48,6 +48,7 @@
 #include "masw_count.cuh"
 #include "masw_device.cuh"
 #include "masw_internal.h"
+#include "masw_modes.cuh"
 #include "masw_screen.cuh"
 
 using namespace masw;
@@ -85,7 +86,7 @@ __device__ __forceinline__ int32_t* slot_state(const SlotView& v, int s) {
                       v.imax);
 }
 
-enum { PH_SCREEN = 0, PH_FP64 = 1, PH_FP64_WINDOW = 2 };
+enum { PH_SCREEN = 0, PH_FP64 = 1 };
 
 // Write an item's result into the mapped host arrays (res < 0: no change
 // below the limit) and count it off its request; the request's slot joins
@@ -121,13 +122,44 @@ __global__ void __launch_bounds__(256) serve_scatter_kernel(SlotView v, const un
     if (threadIdx.x == 0) v.remaining[d.slot] = d.n_lambda;
 }
 
+// The first change of one item from the FP64 mode-count search from V[0]
+// (both lanes of its pair; `topp` is V[nlim-1] when already evaluated, else
+// T = -1). Finishes the item and returns true; when the counts fail, queues
+// the FP64 scan from V[0] for the next ticks and returns false.
+__device__ bool search_or_rescan(SlotView v, int item, int slot, const double* lay, int N,
+                                 double k, double c0, double dc, int nlim, TPoint topp, int half,
+                                 unsigned pair, int32_t* active_out, const TPoint* p0 = nullptr) {
+    TPoint P, dummy;
+    if (p0) {
+        P = *p0;
+    } else {
+        eval_pair(lay, N, k, c0, dc, 0, topp.T < 0 ? nlim - 1 : -1, half, pair, &P, &dummy);
+        if (topp.T < 0) topp = dummy;
+    }
+    ModeSearch st = mode_search_init(lay, N, k, c0, dc, nlim - 1, half, pair, P, topp);
+    int d = 0;
+    const int n = next_change(st, &d);
+    if (half) return !st.bad;
+    if (!st.bad) {
+        finish_item(v, item, slot, n, c0, dc);
+        return true;
+    }
+    int32_t* stt = slot_state(v, slot) + 4 * (item - slot * v.imax);
+    stt[0] = 0;
+    stt[1] = 0;
+    stt[2] = PH_FP64;
+    active_out[atomicAdd(&v.counters[0], 1)] = item;
+    return false;
+}
+
 // Tick, part 0 (two lanes per item admitted since the last tick): the
 // counting search and its FP64 certificate of the batch path
-// (count_certify_pair). A certified item is finished here. Otherwise the item
-// continues at the next tick: with the linear FP32 screen from the end of the
-// pole-free range (carrying the positive sign of count 0) or from V[0], or,
-// when the certificate failed, with the FP64 scan from a window 17 points
-// below the located index (its first point checked against V[0]'s sign).
+// (count_certify_pair). A certified item is finished here. When the
+// certificate failed, the pair searches the first change on the FP64 mode
+// count from V[0] (next_change) and finishes the item too (if those counts
+// fail, the FP64 scan from V[0] follows at the next ticks). The fallback
+// items continue at the next tick with the linear FP32 screen from the end of
+// the pole-free range (carrying the positive sign of count 0) or from V[0].
 __global__ void __launch_bounds__(128, 7) serve_count_kernel(SlotView v, const int32_t* __restrict__ items,
                                                              int n_items, int32_t* active_out,
                                                              double c0, double dc) {
@@ -150,22 +182,20 @@ __global__ void __launch_bounds__(128, 7) serve_count_kernel(SlotView v, const i
     const double k = slot_k(v, slot)[j];
     const PairCount r =
         count_certify_pair(slot_records32(v, slot), lay, N, k, c0, dc, nlim, half, pair);
-    if (half) return;
     if (r.cert >= 1) {
-        finish_item(v, item, slot, r.cert, c0, dc);
+        if (!half) finish_item(v, item, slot, r.cert, c0, dc);
         return;
     }
     if (r.n >= 1) {
-        const bool win = r.n >= 18;
-        stt[0] = win ? r.n - 17 : 0;
-        stt[1] = win ? det_sign(lay, N, k, grid_c(c0, dc, 0)) : 0;
-        stt[2] = win ? PH_FP64_WINDOW : PH_FP64;
-    } else {
+        if (search_or_rescan(v, item, slot, lay, N, k, c0, dc, nlim,
+                             TPoint{nlim - 1, -1, 0}, half, pair, active_out))
+            return;
+    } else if (!half) {
         stt[0] = r.start;
         stt[1] = r.start > 0 ? 1 : 0;
         stt[2] = PH_SCREEN;
+        active_out[atomicAdd(&v.counters[0], 1)] = item;
     }
-    active_out[atomicAdd(&v.counters[0], 1)] = item;
 }
 
 // Tick, part 1 (one warp per active item). PH_SCREEN: up to `chunks` paired
@@ -224,29 +254,20 @@ __global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
             }
         }
     } else if (base < nlim) {
-        // one FP64 chunk per tick; a PH_FP64_WINDOW chunk starts below the
-        // screen's index and its first point must carry V[0]'s sign (carry)
+        // one FP64 chunk per tick
         const double* lay = slot_records(v, slot);
         int n = base + lane;
         int sg = (n < nlim) ? det_sign(lay, N, k, grid_c(c0, dc, n)) : 0;
         int prev = __shfl_up_sync(FULL, sg, 1);
-        bool window = phase == PH_FP64_WINDOW;
         if (lane == 0) prev = carry;
-        if (window && __shfl_sync(FULL, sg, 0) != carry) {
-            base = 0;  // an FP64 change below the window: scan from V[0]
-            carry = 0;
-            phase = PH_FP64;
+        unsigned msk = __ballot_sync(FULL, n >= 1 && n < nlim && sg != prev);
+        if (msk) {
+            res = base + __ffs(msk) - 1;
+            finished = true;
         } else {
-            unsigned msk = __ballot_sync(FULL, n >= 1 && n < nlim && sg != prev);
-            if (msk) {
-                res = base + __ffs(msk) - 1;
-                finished = true;
-            } else {
-                carry = __shfl_sync(FULL, sg, 31);
-                base += 32;
-                phase = PH_FP64;
-                finished = base >= nlim;
-            }
+            carry = __shfl_sync(FULL, sg, 31);
+            base += 32;
+            finished = base >= nlim;
         }
     } else {
         finished = true;
@@ -268,51 +289,41 @@ __global__ void __launch_bounds__(256) serve_tick_kernel(SlotView v,
     }
 }
 
-// Tick, part 2 (one thread per item the linear screen located this tick):
-// the index is accepted when the FP64 signs at V[0], V[n-1], V[n] (or V[0]
-// and the last scanned point) agree with it; otherwise the item continues
-// with the FP64 scan.
-__global__ void serve_check_kernel(SlotView v, const int32_t* __restrict__ check_list,
-                                   const int32_t* __restrict__ n_check, int32_t* active_out,
-                                   double c0, double dc) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= *n_check) return;
+// Tick, part 2 (two lanes per item the linear screen located this tick):
+// the three-point check of the batch path on the FP64 mode count
+// (mode_count_verified at V[0], V[n-1], V[n], or V[0] and the last point
+// when the screen saw no change). An item that fails it takes the FP64
+// mode-count search from V[0] in this kernel (search_or_rescan).
+__global__ void __launch_bounds__(128) serve_check_kernel(SlotView v,
+                                                          const int32_t* __restrict__ check_list,
+                                                          const int32_t* __restrict__ n_check,
+                                                          int32_t* active_out, double c0, double dc) {
+    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 1);
+    const int half = threadIdx.x & 1;
+    const unsigned pair = 3u << (threadIdx.x & 30);
+    if (t >= *n_check) return;  // both lanes of a pair leave together
     const int item = check_list[t];
     const int slot = item / v.imax;
     const int j = item - slot * v.imax;
     const int32_t* meta = slot_meta(v, slot);
     const int N = meta[0] - 1;
     const int nlim = meta[1];
+    if (nlim < 2) {
+        if (!half) finish_item(v, item, slot, -1, c0, dc);
+        return;
+    }
     const double* lay = slot_records(v, slot);
     const double k = slot_k(v, slot)[j];
-    int32_t* stt = slot_state(v, slot) + 4 * j;
-    const int n = stt[3];
-    int res = -1;
-    bool ok;
-    if (nlim < 2) {
-        ok = true;
-    } else {
-        int s0 = det_sign(lay, N, k, grid_c(c0, dc, 0));
-        if (n >= 1) {
-            int sa = (n == 1) ? s0 : det_sign(lay, N, k, grid_c(c0, dc, n - 1));
-            int sb = det_sign(lay, N, k, grid_c(c0, dc, n));
-            ok = (sa == s0) && (sb != sa);
-            res = n;
-        } else {
-            ok = det_sign(lay, N, k, grid_c(c0, dc, nlim - 1)) == s0;
-        }
+    const int n = slot_state(v, slot)[4 * j + 3];  // screen index (-2: none below the limit)
+    TPoint p0, pa, pb{-1, -1, 0}, unused;
+    eval_pair(lay, N, k, c0, dc, 0, n >= 1 ? n - 1 : nlim - 1, half, pair, &p0, &pa);
+    if (n >= 1) eval_pair(lay, N, k, c0, dc, n, -1, half, pair, &pb, &unused);
+    if (mode_count_verified(n, p0.T, pa.T, pb.T)) {
+        if (!half) finish_item(v, item, slot, n >= 1 ? n : -1, c0, dc);
+        return;
     }
-    if (ok) {
-        finish_item(v, item, slot, res, c0, dc);
-    } else {
-        // FP64 from 17 points below the screen's index (first point checked
-        // against V[0]'s sign), or from V[0] when the index is that small
-        bool win = n >= 18;
-        stt[0] = win ? n - 17 : 0;
-        stt[1] = win ? det_sign(lay, N, k, grid_c(c0, dc, 0)) : 0;
-        stt[2] = win ? PH_FP64_WINDOW : PH_FP64;
-        active_out[atomicAdd(&v.counters[0], 1)] = item;
-    }
+    const TPoint topp = n >= 1 ? TPoint{nlim - 1, -1, 0} : pa;
+    search_or_rescan(v, item, slot, lay, N, k, c0, dc, nlim, topp, half, pair, active_out, &p0);
 }
 
 double now_s() {
@@ -467,7 +478,7 @@ int tick_launch_impl(masw_server* S, bool* launched) {
         if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
     }
     // every item that entered the check list this tick (at most n_active)
-    serve_check_kernel<<<(S->n_active + 127) / 128 + 1, 128, 0, S->stream>>>(
+    serve_check_kernel<<<(2 * S->n_active + 127) / 128 + 1, 128, 0, S->stream>>>(
         S->v, S->check, S->v.counters + 2, S->active[1 - S->cur], S->grid.c0, S->grid.dc);
     if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
     // counters and the done list (first counters[1] entries) come back together

@@ -291,6 +291,15 @@ def last_scan_unresolved(handle) -> int:
     return n.value
 
 
+def last_changes_linear(handle) -> int:
+    f = load().masw_last_changes_linear
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
+    f.restype = ctypes.c_int
+    n = ctypes.c_int32()
+    _check(f(ctypes.c_void_p(handle), ctypes.byref(n)), "masw_last_changes_linear")
+    return n.value
+
+
 def last_scan_fallback(handle) -> int:
     f = load().masw_last_scan_fallback
     f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
@@ -448,6 +457,9 @@ class Batch:
 
     def last_scan_fallback(self) -> int:
         return last_scan_fallback(self.handle)
+
+    def last_changes_linear(self) -> int:
+        return last_changes_linear(self.handle)
 
 
 # ------------------------------------------------------------ no allocation

@@ -145,3 +145,28 @@ def test_edges_limits_and_device_outputs(masw, oracle_lib):
         _, idx, st, dl = b.changes(M)
         assert np.array_equal(d_idx.cpu().numpy().reshape(-1, M), idx)
         assert np.array_equal(d_dl.cpu().numpy().reshape(-1, M), dl)
+
+
+@pytest.mark.parametrize("which", ["uniform", "ragged", "extreme"])
+def test_counting_search_equals_the_linear_fp64_scan(masw, which):
+    """Plan precision 2 (search on the monotone mode count s + 2 J0) against
+    precision 0 (FP64 sign and count at every grid point) item for item, all
+    M entries and labels, at full size."""
+    if which == "uniform":
+        m, g = W.uniform_batch()
+    elif which == "ragged":
+        m, g = W.ragged_batch(n_models=2048)
+    else:
+        m, g = W.extreme_batch(seed=W.SEED + 11)
+    M = 4
+    with masw.Batch(m, g) as b:
+        b.set_plan(precision=0)
+        ref = b.changes(M)
+        assert b.last_changes_linear() == -1
+        b.set_plan(precision=2)
+        got = b.changes(M)
+        n_lin = b.last_changes_linear()
+    for x, y in zip(got[1:], ref[1:]):
+        bad = np.nonzero((x != y).any(axis=1))[0]
+        assert bad.size == 0, (which, bad[:10], x[bad[:3]], y[bad[:3]])
+    assert 0 <= n_lin <= max(2, m.n_items // 1000), n_lin

@@ -464,7 +464,7 @@ def test_grid_finer_than_fp32_resolution(masw, oracle_lib):
         assert st == 0 and abs(idx - out[0][1][j]) <= 1
 
 
-@pytest.mark.parametrize("seed", [101, 102])
+@pytest.mark.parametrize("seed", [101, 102, W.SEED + 11])
 def test_extreme_models_two_precision_equals_fp64_scan(masw, oracle_lib, seed):
     """Both two-precision plans against the pure FP64 scan, item for item, on
     models chosen to stress the counting search (tight pole-free bounds,
