@@ -273,7 +273,7 @@ int masw_last_changes_linear(const masw_batch* batch, int32_t* n);
 
 /* ---------------------------------------------------------------------
  * Leaky continuation. The paper builds its stiffness matrices in complex
- * arithmetic (Section 3.4) and takes the sign of their determinants
+ * arithmetic (Section 3.3) and takes the sign of their determinants
  * (Algorithm 1); masw_dispersion scans only below the half-space shear speed,
  * where K is real. This scans the whole grid.
  * --------------------------------------------------------------------- */

@@ -18,7 +18,7 @@
  *   change, listing the first M sign changes in order (oracle_scan_changes);
  *   the Python wrapper labels each with the change in K's negative-eigenvalue
  *   count (numpy's symmetric eigensolver on the dense K).
- *   Leaky continuation (Section 3.4: the paper's stiffness matrices are
+ *   Leaky continuation (Section 3.3: the paper's stiffness matrices are
  *   complex): Algorithm 1 over the whole grid, test velocities at or above
  *   the half-space shear speed included, with the sign of the real part of
  *   the complex determinant (oracle_scan_leaky).

@@ -327,7 +327,7 @@ __device__ __forceinline__ int det_sign(const double* __restrict__ lay, int N, d
 
 // Sign of Re det K(k, c) for any c > 0: Algorithm 1's sign continued to test
 // velocities at or above the half-space shear speed, where the paper's
-// complex stiffness matrices (Section 3.4) have a complex half-space block.
+// complex stiffness matrices (Section 3.3) have a complex half-space block.
 // The finite layers stay real (even functions), so only the last 2x2 pivot is
 // complex. There s = i sqrt(q - 1) and r = sqrt(1 - p) or i sqrt(p - 1)
 // (the same closed form continued; the other root for both conjugates det K

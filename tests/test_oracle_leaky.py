@@ -1,7 +1,7 @@
 """Pins of the oracle's leaky continuation: Algorithm 1 over the whole grid,
 test velocities at or above the half-space shear speed included, where the
 half-space block is complex (the paper builds its stiffness matrices in
-complex arithmetic, Section 3.4) and the sign is that of Re det K.
+complex arithmetic, Section 3.3) and the sign is that of Re det K.
 
 Independent routes:
 - the complex half-space block against the eigenvectors of the P-SV
