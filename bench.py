@@ -58,7 +58,7 @@ FP64_DFMA_PER_CLK_SM = 2.0
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one count_certify launch per model (ncu,
 # 128-model case: 504.8 KB read, 0 written), scaled by the models of a launch.
-CERTIFY_DRAM_BYTES_PER_MODEL = 504.832e3 / 128
+CERTIFY_DRAM_BYTES_PER_MODEL = 505.088e3 / 128
 # DRAM bytes (read + write) of one scan launch per model, from the ncu capture
 # of the 64-model case (281.6 KB read, 0 written), scaled by the models of a
 # launch; traffic grows with the number of items.

@@ -405,6 +405,7 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
     const int w = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const int total = *n_fallback;
+    if (total == 0) return;  // uniform across the block: no barrier is skipped by part of it
     const float c0 = (float)b.c0, dc = (float)b.dc;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -533,6 +534,7 @@ __global__ void __launch_bounds__(256) first_count64_kernel(DevBatch b, ScanOut 
     const int gbase = lane - gl;
     const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << gbase);
     const int total = *n_list;
+    if (total == 0) return;  // the usual case: no atomics on the queue
     for (;;) {
         int t = 0;
         if (gl == 0) t = atomicAdd(counter, 1);
@@ -624,6 +626,7 @@ __global__ void __launch_bounds__(256) resolve64_kernel(DevBatch b, ScanOut o,
                                                         int32_t* counter) {
     const int lane = threadIdx.x & 31;
     const int total = *n_unresolved;
+    if (total == 0) return;  // the usual case: no atomics on the queue
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(counter, 1);
