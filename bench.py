@@ -254,7 +254,33 @@ def run_extras(args, masw, torch):
     one-request-at-a-time path, per arrival rate)."""
     from paper_2003_02256_gb300 import serving
     out = {}
+    only = set(args.extras.split(",")) if args.extras else None
+
+    def want(name):
+        return only is None or name in only
+
     # ragged batch
+    if want("ragged_batch"):
+        out.update(extra_ragged(args, masw))
+    if want("differentiation") or want("inversion"):
+        out.update(extra_differentiation_inversion(masw, torch))
+    if want("partition_study"):
+        out.update(extra_partition_study(masw))
+    if want("uniform_stress"):
+        out.update(extra_uniform_stress(masw))
+    if want("higher_modes"):
+        out.update(extra_higher_modes(masw, torch))
+    if want("leaky"):
+        out.update(extra_leaky(masw, torch))
+    if want("first_call"):
+        out.update(extra_first_call(masw))
+    if want("serving"):
+        out.update(extra_serving(args, serving))
+    return out
+
+
+def extra_ragged(args, masw):
+    out = {}
     m3, g3 = W.ragged_batch(n_models=args.ragged_models)
     with masw.Batch(m3, g3) as b:
         plan = b.autotune(reps=1)
@@ -271,6 +297,11 @@ def run_extras(args, masw, torch):
                     "2x total depth, 10% low-velocity layer; c grid 50..1200 step 0.25",
         "items": m3.n_items, "batched_curves_per_s": m3.n_models / (min(times) * 1e-3),
         "plain_curves_per_s": m3.n_models / plain_s, "plan": plan.as_dict()}
+    return out
+
+
+def extra_differentiation_inversion(masw, torch):
+    out = {}
     # differentiation batch
     m4, g4, true = W.differentiation_batch()
     gold = np.loadtxt(os.path.join(ROOT, "tests", "golden", "differentiation_true_roots.txt"))
@@ -309,6 +340,11 @@ def run_extras(args, masw, torch):
                         "metropolis_chain_steps_per_s": m4.n_models * 20 / t_mc,
                         "metropolis_acceptance": float(np.mean(acc))}
 
+    return out
+
+
+def extra_partition_study(masw):
+    out = {}
     # partition study (Section 3.2): per-wavelength work of Algorithm 1 on a
     # 40-wavelength decreasing curve, split over P ranks contiguously or modularly
     m1, g1 = W.single_curve()
@@ -327,6 +363,11 @@ def run_extras(args, masw, torch):
         "paper_section_3_2": {"3": {"modular": 2.8, "contiguous": 1.9},
                               "8": {"modular": 7.0, "contiguous": 4.2}}}
 
+    return out
+
+
+def extra_uniform_stress(masw):
+    out = {}
     # uniform-work stress curves: one wavelength repeated per curve, roots
     # near 72 / 238 / 256 m/s
     stress = {}
@@ -347,6 +388,11 @@ def run_extras(args, masw, torch):
                                          "50..500 times (0.5 m or 2000 m on 2-layer models); "
                                          "c grid 50..1200 step 0.25", "targets_m_s": stress}
 
+    return out
+
+
+def extra_higher_modes(masw, torch):
+    out = {}
     # higher modes: the first 3 sign changes per item (FP64 past the first)
     hm, hg = W.uniform_batch()
     with masw.Batch(hm, hg) as b:
@@ -364,24 +410,68 @@ def run_extras(args, masw, torch):
                            "roots_fraction_of_found": float(np.mean(hdl[hst == 0] == 1)),
                            "poles_fraction_of_found": float(np.mean(hdl[hst == 0] == -1))}
 
-    # leaky continuation: the whole grid with the sign of Re det K
+    return out
+
+
+def extra_leaky(masw, torch):
+    """Leaky continuation: the whole grid with the sign of Re det K. Besides
+    the host-output rate, an FP64 roofline of the continuation kernel: the
+    layer-evaluations the linear scan needs for the items the batch scan
+    leaves without a change (from one point below the scan limit to the
+    change, or to the end of the grid) x F_LAYER_FLOPS, over the kernel's
+    device time (CUDA events around the device-output call on the batch
+    stream, less the batch scan's own event time)."""
+    out = {}
     lm, lg = W.leaky_batch()
+    n_rec = lm.n_layers.astype(np.int64) + 1
+    beta_hs = np.array([lm.model(q)[2][-1] for q in range(lm.n_models)])
+    grid = lg.c0 + lg.dc * np.arange(lg.n_c)
+    nlim = np.searchsorted(grid, beta_hs, side="left")
+    item_model = np.repeat(np.arange(lm.n_models), lm.n_lambda)
     with masw.Batch(lm, lg) as b:
         _, lidx, lst = b.leaky()
         _, _, lst1 = b.dispersion()
-        lms, lscan = [], []
+        lms, lscan, kms = [], [], []
         for _ in range(5):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             b.leaky()
             lms.append(time.perf_counter() - t0)
             lscan.append(b.last_scan_ms())
+        d_ct = torch.empty(lm.n_items, dtype=torch.float64, device="cuda")
+        d_idx = torch.empty(lm.n_items, dtype=torch.int32, device="cuda")
+        d_st = torch.empty(lm.n_items, dtype=torch.int32, device="cuda")
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            masw.dispersion_leaky(b.handle, d_ct, d_idx, d_st)
+            e1.record()
+            torch.cuda.synchronize()
+            kms.append(e0.elapsed_time(e1) - b.last_scan_ms())
+    cont = lst1 != 0
+    start = np.maximum(nlim[item_model], 1)
+    last = np.where(lst == 0, lidx, lg.n_c - 1)
+    evals = float(np.sum(((last - start + 2) * n_rec[item_model])[cont]))
+    k_ms = float(np.median(kms))
+    achieved = evals * F_LAYER_FLOPS / (k_ms * 1e-3) / 1e12
+    peak = FP64_DFMA_PER_CLK_SM * 2.0 * masw.sm_count() * SM_MAX_MHZ * 1e6 / 1e12
     out["leaky"] = {"workload": lm.meta["workload"] + ", host outputs",
                     "curves_per_s": lm.n_models / min(lms), "ms": 1e3 * min(lms),
                     "batch_scan_ms": float(np.median(lscan)),
+                    "continuation_kernel_ms": k_ms,
                     "found_fraction": float(np.mean(lst == 0)),
-                    "continued_fraction": float(np.mean((lst1 != 0) & (lst == 0)))}
+                    "continued_fraction": float(np.mean(cont)),
+                    "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved,
+                                 "peak": peak, "frac": achieved / peak,
+                                 "kernel": "leaky_scan64_kernel (FP64 pipe)",
+                                 "layer_evals": evals, "flops_per_layer_eval": F_LAYER_FLOPS}}
+    return out
 
+
+def extra_first_call(masw):
+    out = {}
     # first use: batch creation (upload, records, graph capture) and the first
     # scan of a fresh batch vs the warm median (CUDA context and library
     # already loaded in this process)
@@ -401,6 +491,11 @@ def run_extras(args, masw, torch):
                          "create_ms": 1e3 * (t1 - t0), "first_dispersion_ms": 1e3 * (t2 - t1),
                          "warm_median_ms": 1e3 * float(np.median(warm))}
 
+    return out
+
+
+def extra_serving(args, serving):
+    out = {}
     # serving
     sampler = W.RandomWalkSampler()
     reqs = W.concat([sampler.next() for _ in range(args.serving_requests)])
@@ -432,6 +527,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--extras", default=None,
+                    help="comma-separated subset of the extras (ragged_batch, differentiation, "
+                         "inversion, partition_study, uniform_stress, higher_modes, leaky, "
+                         "first_call, serving); default all")
     ap.add_argument("--ragged-models", type=int, default=8192)
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--precision", type=int, default=None, choices=[0, 1, 2],

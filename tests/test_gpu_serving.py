@@ -150,3 +150,22 @@ def test_fallback_items_match_the_batch_path(env):
     for q in range(m.n_models):
         sl = slice(woff[q], woff[q + 1])
         assert np.array_equal(outs[q][1], ref[1][sl]) and np.array_equal(outs[q][2], ref[2][sl])
+
+
+@pytest.mark.parametrize("chunks", [1, 8])
+def test_extreme_models_served_equal_the_fp64_scan(env, chunks):
+    """The extreme-model batch whose fallback items include roots and poles one
+    grid step apart (an FP32 screen loses such pairs): every served item
+    equals the batch path's plain FP64 scan (trace replay, all requests at
+    once, so every tick mixes counted, fallback and searched items)."""
+    masw, serving = env
+    m, g = W.extreme_batch(seed=W.SEED + 11)
+    with masw.Batch(m, g) as b:
+        b.set_plan(precision=0)
+        _, ref_idx, ref_st = b.dispersion()
+    with serving.Server(g, max_slots=m.n_models, max_lambda=int(m.n_lambda.max()),
+                        chunks_per_tick=chunks) as srv:
+        lat, ct, idx, st, stats = srv.run_trace(m, np.zeros(m.n_models), timeout_s=120.0)
+    bad = np.nonzero((idx != ref_idx) | (st != ref_st))[0]
+    assert bad.size == 0, (bad[:10], idx[bad[:5]], ref_idx[bad[:5]])
+    assert stats["refused"] == 0 and np.isfinite(lat).all()
