@@ -173,6 +173,17 @@ int masw_misfit(masw_batch* batch, const double* ce, int32_t kind, double sigma,
 int masw_misfit_grad(masw_batch* batch, const double* ce, int32_t kind, double sigma,
                      double* misfit, double* grad_beta, double* grad_h);
 
+/* Wittrick-Williams counts of K(k_item, c) at n arbitrary points, by the
+ * arithmetic of the mode-count search: s = the number of negative eigenvalues
+ * of K (Sylvester's inertia of the 2x2 Schur pivots), j0 = the number of
+ * modes below c of the finite layers with both faces clamped (each layer's
+ * thickness halved until c lies under the pole-free bound). s + j0 is the
+ * number of modes of the layered structure below c. item, c, s, j0: host or
+ * device, length n. Points with c outside (0, beta_halfspace), or whose
+ * rescaling failed, get -1 in both. */
+int masw_mode_count(masw_batch* batch, int32_t n, const int32_t* item, const double* c,
+                    int32_t* s, int32_t* j0);
+
 /* Refined roots C* per item (host or device, length n_items; NaN where
  * Algorithm 1 found none). */
 int masw_roots(masw_batch* batch, double* croot);

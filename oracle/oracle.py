@@ -183,6 +183,31 @@ def negative_eigenvalues(h, alpha, beta, rho, k, c) -> int:
     return int((np.linalg.eigvalsh(assemble(h, alpha, beta, rho, k, c)) < 0.0).sum())
 
 
+def clamped_modes(k, c, h, alpha, beta, rho, max_sublayers=400) -> int:
+    """Number of modes below c of one layer with both faces clamped (the J0
+    of Wittrick-Williams for that element), by brute force: the layer cut
+    into m equal sublayers, each under its pole-free bound beta sqrt(1 +
+    (pi / (k h/m))^2) (so none of them has a clamped mode below c), assembled
+    over the m - 1 interior nodes; by Wittrick-Williams the count is the
+    number of negative eigenvalues of that dense matrix (numpy's symmetric
+    eigensolver). -1 when more than max_sublayers would be needed."""
+    m = 2
+    while beta * np.sqrt(1.0 + (np.pi * m / (k * h)) ** 2) <= c:
+        m += 1
+        if m > max_sublayers:
+            return -1
+    Ke = layer_stiffness(k, c, h / m, alpha, beta, rho)
+    n = 2 * (m - 1)
+    K = np.zeros((n, n))
+    for i in range(m):
+        for p in range(4):
+            for q in range(4):
+                a, b = i + p // 2, i + q // 2
+                if 1 <= a <= m - 1 and 1 <= b <= m - 1:
+                    K[2 * (a - 1) + p % 2, 2 * (b - 1) + q % 2] += Ke[p, q]
+    return int((np.linalg.eigvalsh(K) < 0.0).sum())
+
+
 def scan_changes(h, alpha, beta, rho, lam, c0, dc, n_c, max_changes):
     """Algorithm 1 continued (higher modes): the first max_changes sign
     changes of det K along the grid, each with the change in the number of

@@ -933,6 +933,39 @@ int masw_det_eval(masw_batch* B, int32_t n, const int32_t* item, const double* c
     return rc;
 }
 
+int masw_mode_count(masw_batch* B, int32_t n, const int32_t* item, const double* c, int32_t* s,
+                    int32_t* j0) {
+    if (!B || n < 0 || (n > 0 && (!item || !c || !s || !j0))) return MASW_EINVAL;
+    if (n == 0) return MASW_OK;
+    int32_t *d_item = nullptr, *d_s = nullptr, *d_j0 = nullptr;
+    double* d_c = nullptr;
+    int rc = MASW_OK;
+    if (dev_alloc(&d_item, n) || dev_alloc(&d_s, n) || dev_alloc(&d_j0, n) || dev_alloc(&d_c, n))
+        rc = MASW_ENOMEM;
+    bool sync = false;
+    if (!rc) rc = copy_in(d_item, item, n, B->stream);
+    if (!rc) rc = copy_in(d_c, c, n, B->stream);
+    if (!rc) {
+        cudaError_t e = launch_mode_count(B->dev(false), n, d_item, d_c, d_s, d_j0, B->stream);
+        if (e != cudaSuccess) {
+            record_cuda_error(e, "mode_count", __LINE__);
+            rc = MASW_ECUDA;
+        }
+    }
+    if (!rc) rc = copy_out(s, d_s, n, B->stream, &sync);
+    if (!rc) rc = copy_out(j0, d_j0, n, B->stream, &sync);
+    cudaError_t e = cudaStreamSynchronize(B->stream);
+    if (!rc && e != cudaSuccess) {
+        record_cuda_error(e, "mode_count sync", __LINE__);
+        rc = MASW_ECUDA;
+    }
+    cudaFree(d_item);
+    cudaFree(d_s);
+    cudaFree(d_j0);
+    cudaFree(d_c);
+    return rc;
+}
+
 int masw_get_plan(const masw_batch* B, masw_plan* plan) {
     if (!B || !plan) return MASW_EINVAL;
     *plan = B->plan;

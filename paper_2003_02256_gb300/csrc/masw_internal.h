@@ -75,6 +75,8 @@ cudaError_t launch_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p, 
                         int item_begin, int item_end, cudaStream_t s);
 cudaError_t launch_det_eval(const DevBatch& b, int n, const int32_t* item, const double* c,
                             int32_t* sign, double* log_abs, cudaStream_t s);
+cudaError_t launch_mode_count(const DevBatch& b, int n, const int32_t* item, const double* c,
+                              int32_t* s, int32_t* j0, cudaStream_t st);
 cudaError_t launch_refine(const DevBatch& b, const int32_t* idx, double rel_tol, double* croot,
                           cudaStream_t s);
 cudaError_t launch_root_grad(const DevBatch& b, const double* croot, double* rows, double* bs,

@@ -988,6 +988,37 @@ __global__ void det_eval_kernel(DevBatch b, int n, const int32_t* __restrict__ i
     log_abs[t] = la;
 }
 
+// Wittrick-Williams counts at arbitrary points: s (negative eigenvalues of K)
+// and J0 (clamped-layer modes below c) by the arithmetic of the mode-count
+// search (mode_count_T). -1 for c outside (0, beta_halfspace) or a failed
+// rescaling.
+__global__ void mode_count_kernel(DevBatch b, int n, const int32_t* __restrict__ item,
+                                  const double* __restrict__ c, int32_t* s_out, int32_t* j0_out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int it = item[t];
+    s_out[t] = -1;
+    j0_out[t] = -1;
+    if (it < 0 || it >= b.n_items) return;
+    const int m = b.item_model[it];
+    const int lo = b.model_loff[m];
+    const int N = b.model_loff[m + 1] - lo - 1;
+    const double* lay = b.layers + (size_t)lo * LAYER_STRIDE;
+    if (!(c[t] > 0.0 && c[t] < lay[N * LAYER_STRIDE + L_BETA])) return;
+    int sv;
+    const int T = mode_count_T(lay, N, b.k[it], c[t], &sv);
+    if (T < 0) return;
+    s_out[t] = sv;
+    j0_out[t] = (T - sv) / 2;
+}
+
+cudaError_t launch_mode_count(const DevBatch& b, int n, const int32_t* item, const double* c,
+                              int32_t* s, int32_t* j0, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    mode_count_kernel<<<(n + 127) / 128, 128, 0, st>>>(b, n, item, c, s, j0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_det_eval(const DevBatch& b, int n, const int32_t* item, const double* c,
                             int32_t* sign, double* log_abs, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;

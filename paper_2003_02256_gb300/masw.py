@@ -76,6 +76,7 @@ def load():
         "masw_dispersion_plain": [p, p, p, p, i32],
         "masw_dispersion_changes": [p, i32, p, p, p, p, i32],
         "masw_dispersion_leaky": [p, p, p, p, i32],
+        "masw_mode_count": [p, i32, p, p, p, p],
         "masw_misfit": [p, p, i32, d, p],
         "masw_misfit_grad": [p, p, i32, d, p, p, p],
         "masw_roots": [p, p],
@@ -241,6 +242,12 @@ def root_grad(handle, rows=None) -> int:
 def det_eval(handle, item, c, sign, log_abs):
     _check(load().masw_det_eval(ctypes.c_void_p(handle), int(len(item)), _ptr(item), _ptr(c),
                                 _ptr(sign), _ptr(log_abs)), "masw_det_eval")
+
+
+def mode_count(handle, item, c, s, j0):
+    """Wittrick-Williams counts (s, J0) at arbitrary points (masw_mode_count)."""
+    _check(load().masw_mode_count(ctypes.c_void_p(handle), int(len(item)), _ptr(item), _ptr(c),
+                                  _ptr(s), _ptr(j0)), "masw_mode_count")
 
 
 def get_plan(handle) -> Plan:
@@ -432,6 +439,15 @@ class Batch:
         la = np.empty(item.size)
         det_eval(self.handle, item, c, sign, la)
         return sign, la
+
+    def mode_count(self, item, c):
+        """(s, J0) at the points: negative eigenvalues of K and clamped-layer modes."""
+        item = np.ascontiguousarray(item, dtype=np.int32)
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        s = np.empty(item.size, dtype=np.int32)
+        j0 = np.empty(item.size, dtype=np.int32)
+        mode_count(self.handle, item, c, s, j0)
+        return s, j0
 
     def update(self, h, alpha, beta, rho):
         model_batch_update(self.handle, *(np.ascontiguousarray(x, dtype=np.float64)

@@ -140,6 +140,7 @@ def test_clamped_layer_mode_count_by_halving_matches_dense_subdivision(oracle_li
         J = clamped_modes_halving(oracle_lib, k, c, h, alpha, beta, 1900.0)
         assert J == clamped_modes_dense(oracle_lib, k, c, h, alpha, beta, 1900.0, m)
         assert J == clamped_modes_dense(oracle_lib, k, c, h, alpha, beta, 1900.0, m + 7)
+        assert J == oracle_lib.clamped_modes(k, c, h, alpha, beta, 1900.0)
         nonzero += J > 0
     assert nonzero >= 60
 
