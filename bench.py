@@ -56,9 +56,11 @@ FP32_FFMA_PER_CLK_SM = 128.0
 # the maximum SM clock.
 FP64_DFMA_PER_CLK_SM = 2.0
 SM_MAX_MHZ = 2070.0
-# DRAM bytes (read + write) of one count_certify launch per model (ncu,
-# 128-model case: 504.8 KB read, 0 written), scaled by the models of a launch.
-CERTIFY_DRAM_BYTES_PER_MODEL = 505.088e3 / 128
+# DRAM bytes (read + write) of one count_certify launch (ncu, 128-model case:
+# 521.2 KB read, 0 written): the exponential's 16 KB table once per launch,
+# the rest (records and item tables) scaled by the models of a launch.
+CERTIFY_DRAM_BYTES_FIXED = 2048 * 8
+CERTIFY_DRAM_BYTES_PER_MODEL = (521.216e3 - CERTIFY_DRAM_BYTES_FIXED) / 128
 # DRAM bytes (read + write) of one scan launch per model, from the ncu capture
 # of the 64-model case (281.6 KB read, 0 written), scaled by the models of a
 # launch; traffic grows with the number of items.
@@ -233,7 +235,7 @@ def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, s
     achieved = e64 * F_LAYER_FLOPS / t0
     return {"bound": "alu", "unit": "TFLOP/s",
             "achieved": achieved / 1e12, "peak": peak64 / 1e12, "frac": achieved / peak64,
-            "traffic": CERTIFY_DRAM_BYTES_PER_MODEL * models.n_models,
+            "traffic": CERTIFY_DRAM_BYTES_FIXED + CERTIFY_DRAM_BYTES_PER_MODEL * models.n_models,
             "kernel": "count_certify_kernel (FP64 pipe; FP32 search alongside)",
             "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
             "layer_evals_per_launch": e64, "flops_per_layer_eval": F_LAYER_FLOPS,

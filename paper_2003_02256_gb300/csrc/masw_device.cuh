@@ -84,86 +84,535 @@ __device__ __forceinline__ double scale_pow2(double v, int delta) {
 //
 // Table-driven exponential after P. T. P. Tang, "Table-driven implementation
 // of the exponential function in IEEE floating-point arithmetic" (ACM TOMS
-// 15(2), 1989), restated for FMA hardware with a 256-entry table:
-//   x = (256 m + j) ln2/256 + r,  j = 0..255,  |r| <= ln2/512 (+ rounding),
-//   e^x = 2^m * 2^(j/256) * e^r.
-// n = 256 m + j is x * 256/ln2 rounded to nearest with the 1.5 * 2^52
-// shifter; r = x - n ln2/256 in two FMAs with ln2/256 split into its nearest
-// double and the remainder; e^r - 1 by its Taylor polynomial of degree 4
-// (truncation below |r|^5/5! < 4e-17); 2^(j/256) from a table of the nearest
-// doubles (computed with 60-digit arithmetic, checked by a CPU test); 2^m
-// added to the exponent field. 9 FP64 operations (a 64-entry table needs a
-// degree-6 polynomial: 11). The library's e^(-k h w) only needs x <= 0;
-// below -708 (under the smallest normal double) it returns 0.
-static __device__ const double EXP2_TABLE[256] = {
-    0x1.0000000000000p+0, 0x1.00b1afa5abcbfp+0, 0x1.0163da9fb3335p+0, 0x1.02168143b0281p+0,
-    0x1.02c9a3e778061p+0, 0x1.037d42e11bbccp+0, 0x1.04315e86e7f85p+0, 0x1.04e5f72f654b1p+0,
-    0x1.059b0d3158574p+0, 0x1.0650a0e3c1f89p+0, 0x1.0706b29ddf6dep+0, 0x1.07bd42b72a836p+0,
-    0x1.0874518759bc8p+0, 0x1.092bdf66607e0p+0, 0x1.09e3ecac6f383p+0, 0x1.0a9c79b1f3919p+0,
-    0x1.0b5586cf9890fp+0, 0x1.0c0f145e46c85p+0, 0x1.0cc922b7247f7p+0, 0x1.0d83b23395decp+0,
-    0x1.0e3ec32d3d1a2p+0, 0x1.0efa55fdfa9c5p+0, 0x1.0fb66affed31bp+0, 0x1.1073028d7233ep+0,
-    0x1.11301d0125b51p+0, 0x1.11edbab5e2ab6p+0, 0x1.12abdc06c31ccp+0, 0x1.136a814f204abp+0,
-    0x1.1429aaea92de0p+0, 0x1.14e95934f312ep+0, 0x1.15a98c8a58e51p+0, 0x1.166a45471c3c2p+0,
-    0x1.172b83c7d517bp+0, 0x1.17ed48695bbc0p+0, 0x1.18af9388c8deap+0, 0x1.1972658375d2fp+0,
-    0x1.1a35beb6fcb75p+0, 0x1.1af99f8138a1cp+0, 0x1.1bbe084045cd4p+0, 0x1.1c82f95281c6bp+0,
-    0x1.1d4873168b9aap+0, 0x1.1e0e75eb44027p+0, 0x1.1ed5022fcd91dp+0, 0x1.1f9c18438ce4dp+0,
-    0x1.2063b88628cd6p+0, 0x1.212be3578a819p+0, 0x1.21f49917ddc96p+0, 0x1.22bdda27912d1p+0,
-    0x1.2387a6e756238p+0, 0x1.2451ffb82140ap+0, 0x1.251ce4fb2a63fp+0, 0x1.25e85711ece75p+0,
-    0x1.26b4565e27cddp+0, 0x1.2780e341ddf29p+0, 0x1.284dfe1f56381p+0, 0x1.291ba7591bb70p+0,
-    0x1.29e9df51fdee1p+0, 0x1.2ab8a66d10f13p+0, 0x1.2b87fd0dad990p+0, 0x1.2c57e39771b2fp+0,
-    0x1.2d285a6e4030bp+0, 0x1.2df961f641589p+0, 0x1.2ecafa93e2f56p+0, 0x1.2f9d24abd886bp+0,
-    0x1.306fe0a31b715p+0, 0x1.31432edeeb2fdp+0, 0x1.32170fc4cd831p+0, 0x1.32eb83ba8ea32p+0,
-    0x1.33c08b26416ffp+0, 0x1.3496266e3fa2dp+0, 0x1.356c55f929ff1p+0, 0x1.36431a2de883bp+0,
-    0x1.371a7373aa9cbp+0, 0x1.37f26231e754ap+0, 0x1.38cae6d05d866p+0, 0x1.39a401b7140efp+0,
-    0x1.3a7db34e59ff7p+0, 0x1.3b57fbfec6cf4p+0, 0x1.3c32dc313a8e5p+0, 0x1.3d0e544ede173p+0,
-    0x1.3dea64c123422p+0, 0x1.3ec70df1c5175p+0, 0x1.3fa4504ac801cp+0, 0x1.40822c367a024p+0,
-    0x1.4160a21f72e2ap+0, 0x1.423fb2709468ap+0, 0x1.431f5d950a897p+0, 0x1.43ffa3f84b9d4p+0,
-    0x1.44e086061892dp+0, 0x1.45c2042a7d232p+0, 0x1.46a41ed1d0057p+0, 0x1.4786d668b3237p+0,
-    0x1.486a2b5c13cd0p+0, 0x1.494e1e192aed2p+0, 0x1.4a32af0d7d3dep+0, 0x1.4b17dea6db7d7p+0,
-    0x1.4bfdad5362a27p+0, 0x1.4ce41b817c114p+0, 0x1.4dcb299fddd0dp+0, 0x1.4eb2d81d8abffp+0,
-    0x1.4f9b2769d2ca7p+0, 0x1.508417f4531eep+0, 0x1.516daa2cf6642p+0, 0x1.5257de83f4eefp+0,
-    0x1.5342b569d4f82p+0, 0x1.542e2f4f6ad27p+0, 0x1.551a4ca5d920fp+0, 0x1.56070dde910d2p+0,
-    0x1.56f4736b527dap+0, 0x1.57e27dbe2c4cfp+0, 0x1.58d12d497c7fdp+0, 0x1.59c0827ff07ccp+0,
-    0x1.5ab07dd485429p+0, 0x1.5ba11fba87a03p+0, 0x1.5c9268a5946b7p+0, 0x1.5d84590998b93p+0,
-    0x1.5e76f15ad2148p+0, 0x1.5f6a320dceb71p+0, 0x1.605e1b976dc09p+0, 0x1.6152ae6cdf6f4p+0,
-    0x1.6247eb03a5585p+0, 0x1.633dd1d1929fdp+0, 0x1.6434634ccc320p+0, 0x1.652b9febc8fb7p+0,
-    0x1.6623882552225p+0, 0x1.671c1c70833f6p+0, 0x1.68155d44ca973p+0, 0x1.690f4b19e9538p+0,
-    0x1.6a09e667f3bcdp+0, 0x1.6b052fa75173ep+0, 0x1.6c012750bdabfp+0, 0x1.6cfdcddd47645p+0,
-    0x1.6dfb23c651a2fp+0, 0x1.6ef9298593ae5p+0, 0x1.6ff7df9519484p+0, 0x1.70f7466f42e87p+0,
-    0x1.71f75e8ec5f74p+0, 0x1.72f8286ead08ap+0, 0x1.73f9a48a58174p+0, 0x1.74fbd35d7cbfdp+0,
-    0x1.75feb564267c9p+0, 0x1.77024b1ab6e09p+0, 0x1.780694fde5d3fp+0, 0x1.790b938ac1cf6p+0,
-    0x1.7a11473eb0187p+0, 0x1.7b17b0976cfdbp+0, 0x1.7c1ed0130c132p+0, 0x1.7d26a62ff86f0p+0,
-    0x1.7e2f336cf4e62p+0, 0x1.7f3878491c491p+0, 0x1.80427543e1a12p+0, 0x1.814d2add106d9p+0,
-    0x1.82589994cce13p+0, 0x1.8364c1eb941f7p+0, 0x1.8471a4623c7adp+0, 0x1.857f4179f5b21p+0,
-    0x1.868d99b4492edp+0, 0x1.879cad931a436p+0, 0x1.88ac7d98a6699p+0, 0x1.89bd0a478580fp+0,
-    0x1.8ace5422aa0dbp+0, 0x1.8be05bad61778p+0, 0x1.8cf3216b5448cp+0, 0x1.8e06a5e0866d9p+0,
-    0x1.8f1ae99157736p+0, 0x1.902fed0282c8ap+0, 0x1.9145b0b91ffc6p+0, 0x1.925c353aa2fe2p+0,
-    0x1.93737b0cdc5e5p+0, 0x1.948b82b5f98e5p+0, 0x1.95a44cbc8520fp+0, 0x1.96bdd9a7670b3p+0,
-    0x1.97d829fde4e50p+0, 0x1.98f33e47a22a2p+0, 0x1.9a0f170ca07bap+0, 0x1.9b2bb4d53fe0dp+0,
-    0x1.9c49182a3f090p+0, 0x1.9d674194bb8d5p+0, 0x1.9e86319e32323p+0, 0x1.9fa5e8d07f29ep+0,
-    0x1.a0c667b5de565p+0, 0x1.a1e7aed8eb8bbp+0, 0x1.a309bec4a2d33p+0, 0x1.a42c980460ad8p+0,
-    0x1.a5503b23e255dp+0, 0x1.a674a8af46052p+0, 0x1.a799e1330b358p+0, 0x1.a8bfe53c12e59p+0,
-    0x1.a9e6b5579fdbfp+0, 0x1.ab0e521356ebap+0, 0x1.ac36bbfd3f37ap+0, 0x1.ad5ff3a3c2774p+0,
-    0x1.ae89f995ad3adp+0, 0x1.afb4ce622f2ffp+0, 0x1.b0e07298db666p+0, 0x1.b20ce6c9a8952p+0,
-    0x1.b33a2b84f15fbp+0, 0x1.b468415b749b1p+0, 0x1.b59728de5593ap+0, 0x1.b6c6e29f1c52ap+0,
-    0x1.b7f76f2fb5e47p+0, 0x1.b928cf22749e4p+0, 0x1.ba5b030a1064ap+0, 0x1.bb8e0b79a6f1fp+0,
-    0x1.bcc1e904bc1d2p+0, 0x1.bdf69c3f3a207p+0, 0x1.bf2c25bd71e09p+0, 0x1.c06286141b33dp+0,
-    0x1.c199bdd85529cp+0, 0x1.c2d1cd9fa652cp+0, 0x1.c40ab5fffd07ap+0, 0x1.c544778fafb22p+0,
-    0x1.c67f12e57d14bp+0, 0x1.c7ba88988c933p+0, 0x1.c8f6d9406e7b5p+0, 0x1.ca3405751c4dbp+0,
-    0x1.cb720dcef9069p+0, 0x1.ccb0f2e6d1675p+0, 0x1.cdf0b555dc3fap+0, 0x1.cf3155b5bab74p+0,
-    0x1.d072d4a07897cp+0, 0x1.d1b532b08c968p+0, 0x1.d2f87080d89f2p+0, 0x1.d43c8eacaa1d6p+0,
-    0x1.d5818dcfba487p+0, 0x1.d6c76e862e6d3p+0, 0x1.d80e316c98398p+0, 0x1.d955d71ff6075p+0,
-    0x1.da9e603db3285p+0, 0x1.dbe7cd63a8315p+0, 0x1.dd321f301b460p+0, 0x1.de7d5641c0658p+0,
-    0x1.dfc97337b9b5fp+0, 0x1.e11676b197d17p+0, 0x1.e264614f5a129p+0, 0x1.e3b333b16ee12p+0,
-    0x1.e502ee78b3ff6p+0, 0x1.e653924676d76p+0, 0x1.e7a51fbc74c83p+0, 0x1.e8f7977cdb740p+0,
-    0x1.ea4afa2a490dap+0, 0x1.eb9f4867cca6ep+0, 0x1.ecf482d8e67f1p+0, 0x1.ee4aaa2188510p+0,
-    0x1.efa1bee615a27p+0, 0x1.f0f9c1cb6412ap+0, 0x1.f252b376bba97p+0, 0x1.f3ac948dd7274p+0,
-    0x1.f50765b6e4540p+0, 0x1.f6632798844f8p+0, 0x1.f7bfdad9cbe14p+0, 0x1.f91d802243c89p+0,
-    0x1.fa7c1819e90d8p+0, 0x1.fbdba3692d514p+0, 0x1.fd3c22b8f71f1p+0, 0x1.fe9d96b2a23d9p+0,
+// 15(2), 1989), restated for FMA hardware with a 2048-entry table:
+//   x = (2048 m + j) ln2/2048 + r,  j = 0..2047,  |r| <= ln2/4096 (+ rounding),
+//   e^x = 2^m * 2^(j/2048) * e^r.
+// n = 2048 m + j is x * 2048/ln2 rounded to nearest with the 1.5 * 2^52
+// shifter; r = x - n ln2/2048 in two FMAs with ln2/2048 split into its nearest
+// double and the remainder; e^r - 1 by its Taylor polynomial of degree 3
+// (truncation below |r|^4/4! < 4e-17); 2^(j/2048) from a table of the nearest
+// doubles (computed with 60-digit arithmetic, checked by a CPU test; 16 KB,
+// read through the L1 cache); 2^m added to the exponent field. 8 FP64
+// operations (64 entries need a degree-6 polynomial: 11; 256 entries degree
+// 4: 9). The library's e^(-k h w) only needs x <= 0; below -708 (under the
+// smallest normal double) it returns 0.
+static __device__ const double EXP2_TABLE[2048] = {
+    0x1.0000000000000p+0, 0x1.00162f3904052p+0, 0x1.002c605e2e8cfp+0, 0x1.0042936faa3d8p+0,
+    0x1.0058c86da1c0ap+0, 0x1.006eff583fc3dp+0, 0x1.0085382faef83p+0, 0x1.009b72f41a12bp+0,
+    0x1.00b1afa5abcbfp+0, 0x1.00c7ee448ee02p+0, 0x1.00de2ed0ee0f5p+0, 0x1.00f4714af41d3p+0,
+    0x1.010ab5b2cbd11p+0, 0x1.0120fc089ff63p+0, 0x1.0137444c9b5b5p+0, 0x1.014d8e7ee8d2fp+0,
+    0x1.0163da9fb3335p+0, 0x1.017a28af25567p+0, 0x1.019078ad6a19fp+0, 0x1.01a6ca9aac5f3p+0,
+    0x1.01bd1e77170b4p+0, 0x1.01d37442d5070p+0, 0x1.01e9cbfe113efp+0, 0x1.020025a8f6a35p+0,
+    0x1.02168143b0281p+0, 0x1.022cdece68c4fp+0, 0x1.02433e494b755p+0, 0x1.02599fb483385p+0,
+    0x1.027003103b10ep+0, 0x1.0286685c9e059p+0, 0x1.029ccf99d720ap+0, 0x1.02b338c811703p+0,
+    0x1.02c9a3e778061p+0, 0x1.02e010f835f7bp+0, 0x1.02f67ffa765e6p+0, 0x1.030cf0ee64571p+0,
+    0x1.032363d42b027p+0, 0x1.0339d8abf5851p+0, 0x1.03504f75ef071p+0, 0x1.0366c83242b47p+0,
+    0x1.037d42e11bbccp+0, 0x1.0393bf82a5538p+0, 0x1.03aa3e170aafep+0, 0x1.03c0be9e770cbp+0,
+    0x1.03d7411915a8ap+0, 0x1.03edc58711c63p+0, 0x1.04044be896ab6p+0, 0x1.041ad43dcfa24p+0,
+    0x1.04315e86e7f85p+0, 0x1.0447eac40aff0p+0, 0x1.045e78f5640b9p+0, 0x1.0475091b1e76dp+0,
+    0x1.048b9b35659d8p+0, 0x1.04a22f4464e00p+0, 0x1.04b8c54847a28p+0, 0x1.04cf5d41394cfp+0,
+    0x1.04e5f72f654b1p+0, 0x1.04fc9312f70c5p+0, 0x1.051330ec1a03fp+0, 0x1.0529d0baf9a8fp+0,
+    0x1.0540727fc1762p+0, 0x1.0557163a9ce9fp+0, 0x1.056dbbebb786bp+0, 0x1.058463933cd29p+0,
+    0x1.059b0d3158574p+0, 0x1.05b1b8c635a28p+0, 0x1.05c866520045bp+0, 0x1.05df15d4e3d5ep+0,
+    0x1.05f5c74f0bec2p+0, 0x1.060c7ac0a4252p+0, 0x1.06233029d8216p+0, 0x1.0639e78ad3853p+0,
+    0x1.0650a0e3c1f89p+0, 0x1.06675c34cf276p+0, 0x1.067e197e26c14p+0, 0x1.0694d8bff479ap+0,
+    0x1.06ab99fa6407cp+0, 0x1.06c25d2da1268p+0, 0x1.06d92259d794dp+0, 0x1.06efe97f33152p+0,
+    0x1.0706b29ddf6dep+0, 0x1.071d7db608693p+0, 0x1.07344ac7d9d51p+0, 0x1.074b19d37f833p+0,
+    0x1.0761ead925493p+0, 0x1.0778bdd8f7005p+0, 0x1.078f92d32085dp+0, 0x1.07a669c7cdba9p+0,
+    0x1.07bd42b72a836p+0, 0x1.07d41da162c8cp+0, 0x1.07eafa86a2771p+0, 0x1.0801d967157e8p+0,
+    0x1.0818ba42e7d30p+0, 0x1.082f9d1a456c5p+0, 0x1.084681ed5a462p+0, 0x1.085d68bc525fcp+0,
+    0x1.0874518759bc8p+0, 0x1.088b3c4e9c635p+0, 0x1.08a22912465f2p+0, 0x1.08b917d283be8p+0,
+    0x1.08d0088f8093fp+0, 0x1.08e6fb4968f5dp+0, 0x1.08fdf00068fe2p+0, 0x1.0914e6b4accafp+0,
+    0x1.092bdf66607e0p+0, 0x1.0942da15b03cdp+0, 0x1.0959d6c2c830dp+0, 0x1.0970d56dd4875p+0,
+    0x1.0987d61701716p+0, 0x1.099ed8be7b23dp+0, 0x1.09b5dd646dd77p+0, 0x1.09cce40905c8cp+0,
+    0x1.09e3ecac6f383p+0, 0x1.09faf74ed66a0p+0, 0x1.0a1203f067a63p+0, 0x1.0a2912914f38cp+0,
+    0x1.0a402331b9715p+0, 0x1.0a5735d1d2a39p+0, 0x1.0a6e4a71c726ep+0, 0x1.0a856111c3568p+0,
+    0x1.0a9c79b1f3919p+0, 0x1.0ab39452843b1p+0, 0x1.0acab0f3a1b9cp+0, 0x1.0ae1cf9578784p+0,
+    0x1.0af8f03834e52p+0, 0x1.0b1012dc0372cp+0, 0x1.0b27378110974p+0, 0x1.0b3e5e2788ccbp+0,
+    0x1.0b5586cf9890fp+0, 0x1.0b6cb1796c65ep+0, 0x1.0b83de2530d11p+0, 0x1.0b9b0cd3125bfp+0,
+    0x1.0bb23d833d93fp+0, 0x1.0bc97035df0a2p+0, 0x1.0be0a4eb2353bp+0, 0x1.0bf7dba337098p+0,
+    0x1.0c0f145e46c85p+0, 0x1.0c264f1c7f30ep+0, 0x1.0c3d8bde0ce7ap+0, 0x1.0c54caa31c94fp+0,
+    0x1.0c6c0b6bdae53p+0, 0x1.0c834e3874886p+0, 0x1.0c9a93091632ap+0, 0x1.0cb1d9ddec9bbp+0,
+    0x1.0cc922b7247f7p+0, 0x1.0ce06d94ea9d7p+0, 0x1.0cf7ba776bb94p+0, 0x1.0d0f095ed49a3p+0,
+    0x1.0d265a4b520bap+0, 0x1.0d3dad3d10dc9p+0, 0x1.0d5502343de02p+0, 0x1.0d6c593105ed4p+0,
+    0x1.0d83b23395decp+0, 0x1.0d9b0d3c1a933p+0, 0x1.0db26a4ac0ed5p+0, 0x1.0dc9c95fb5d37p+0,
+    0x1.0de12a7b26300p+0, 0x1.0df88d9d3ef15p+0, 0x1.0e0ff2c62d096p+0, 0x1.0e2759f61d6e6p+0,
+    0x1.0e3ec32d3d1a2p+0, 0x1.0e562e6bb90a8p+0, 0x1.0e6d9bb1be415p+0, 0x1.0e850aff79c41p+0,
+    0x1.0e9c7c55189c6p+0, 0x1.0eb3efb2c7d7bp+0, 0x1.0ecb6518b4874p+0, 0x1.0ee2dc870bc07p+0,
+    0x1.0efa55fdfa9c5p+0, 0x1.0f11d17dae37fp+0, 0x1.0f294f0653b45p+0, 0x1.0f40ce9818366p+0,
+    0x1.0f58503328e6dp+0, 0x1.0f6fd3d7b2f26p+0, 0x1.0f875985e389bp+0, 0x1.0f9ee13de7e15p+0,
+    0x1.0fb66affed31bp+0, 0x1.0fcdf6cc20b73p+0, 0x1.0fe584a2afb21p+0, 0x1.0ffd1483c7669p+0,
+    0x1.1014a66f951cep+0, 0x1.102c3a6646210p+0, 0x1.1043d06807c2fp+0, 0x1.105b68750756ap+0,
+    0x1.1073028d7233ep+0, 0x1.108a9eb175b68p+0, 0x1.10a23ce13f3e2p+0, 0x1.10b9dd1cfc2e8p+0,
+    0x1.10d17f64d9ef1p+0, 0x1.10e923b905eb7p+0, 0x1.1100ca19ad92fp+0, 0x1.11187286fe591p+0,
+    0x1.11301d0125b51p+0, 0x1.1147c98851223p+0, 0x1.115f781cae1fap+0, 0x1.117728be6a309p+0,
+    0x1.118edb6db2dc1p+0, 0x1.11a6902ab5ad2p+0, 0x1.11be46f5a032cp+0, 0x1.11d5ffce9fffep+0,
+    0x1.11edbab5e2ab6p+0, 0x1.120577ab95d00p+0, 0x1.121d36afe70c9p+0, 0x1.1234f7c30403ep+0,
+    0x1.124cbae51a5c8p+0, 0x1.1264801657c12p+0, 0x1.127c4756e9e05p+0, 0x1.129410a6fe6cbp+0,
+    0x1.12abdc06c31ccp+0, 0x1.12c3a97665aafp+0, 0x1.12db78f613d5bp+0, 0x1.12f34a85fb5f7p+0,
+    0x1.130b1e264a0e9p+0, 0x1.1322f3d72dad5p+0, 0x1.133acb98d40a2p+0, 0x1.1352a56b6af72p+0,
+    0x1.136a814f204abp+0, 0x1.13825f4421defp+0, 0x1.139a3f4a9d922p+0, 0x1.13b22162c1466p+0,
+    0x1.13ca058cbae1ep+0, 0x1.13e1ebc8b84ebp+0, 0x1.13f9d416e77afp+0, 0x1.1411be777658bp+0,
+    0x1.1429aaea92de0p+0, 0x1.144199706b04ep+0, 0x1.14598a092ccb7p+0, 0x1.14717cb50633ap+0,
+    0x1.1489717425438p+0, 0x1.14a16846b804fp+0, 0x1.14b9612cec861p+0, 0x1.14d15c26f0d8bp+0,
+    0x1.14e95934f312ep+0, 0x1.15015857214e8p+0, 0x1.1519598da9a9ap+0, 0x1.15315cd8ba461p+0,
+    0x1.154962388149ep+0, 0x1.156169ad2cdefp+0, 0x1.15797336eb333p+0, 0x1.15917ed5ea789p+0,
+    0x1.15a98c8a58e51p+0, 0x1.15c19c5464b2ap+0, 0x1.15d9ae343c1f2p+0, 0x1.15f1c22a0d6cap+0,
+    0x1.1609d83606e12p+0, 0x1.1621f05856c68p+0, 0x1.163a0a912b6acp+0, 0x1.165226e0b3200p+0,
+    0x1.166a45471c3c2p+0, 0x1.168265c495194p+0, 0x1.169a88594c157p+0, 0x1.16b2ad056f92cp+0,
+    0x1.16cad3c92df73p+0, 0x1.16e2fca4b5ad0p+0, 0x1.16fb279835224p+0, 0x1.171354a3dac91p+0,
+    0x1.172b83c7d517bp+0, 0x1.1743b50452885p+0, 0x1.175be85981992p+0, 0x1.17741dc790cc7p+0,
+    0x1.178c554eaea89p+0, 0x1.17a48eef09b7dp+0, 0x1.17bccaa8d0888p+0, 0x1.17d5087c31ad2p+0,
+    0x1.17ed48695bbc0p+0, 0x1.18058a707d4fbp+0, 0x1.181dce91c506ap+0, 0x1.183614cd61836p+0,
+    0x1.184e5d23816c9p+0, 0x1.1866a794536ccp+0, 0x1.187ef4200632bp+0, 0x1.189742c6c8711p+0,
+    0x1.18af9388c8deap+0, 0x1.18c7e66636363p+0, 0x1.18e03b5f3f36bp+0, 0x1.18f8927412a2fp+0,
+    0x1.1910eba4df41fp+0, 0x1.192946f1d3decp+0, 0x1.1941a45b1f487p+0, 0x1.195a03e0f0522p+0,
+    0x1.1972658375d2fp+0, 0x1.198ac942dea64p+0, 0x1.19a32f1f59ab4p+0, 0x1.19bb971915c57p+0,
+    0x1.19d4013041dc2p+0, 0x1.19ec6d650cdadp+0, 0x1.1a04dbb7a5b13p+0, 0x1.1a1d4c283b52dp+0,
+    0x1.1a35beb6fcb75p+0, 0x1.1a4e336418da9p+0, 0x1.1a66aa2fbebc7p+0, 0x1.1a7f231a1d60cp+0,
+    0x1.1a979e2363cf8p+0, 0x1.1ab01b4bc114dp+0, 0x1.1ac89a936440dp+0, 0x1.1ae11bfa7c67bp+0,
+    0x1.1af99f8138a1cp+0, 0x1.1b122527c80b7p+0, 0x1.1b2aacee59c53p+0, 0x1.1b4336d51cf38p+0,
+    0x1.1b5bc2dc40bf0p+0, 0x1.1b745103f4548p+0, 0x1.1b8ce14c66e4cp+0, 0x1.1ba573b5c7a4bp+0,
+    0x1.1bbe084045cd4p+0, 0x1.1bd69eec109b8p+0, 0x1.1bef37b95750bp+0, 0x1.1c07d2a849321p+0,
+    0x1.1c206fb91588fp+0, 0x1.1c390eebeba2ep+0, 0x1.1c51b040fad15p+0, 0x1.1c6a53b8726a0p+0,
+    0x1.1c82f95281c6bp+0, 0x1.1c9ba10f58454p+0, 0x1.1cb44aef2547ap+0, 0x1.1cccf6f21833fp+0,
+    0x1.1ce5a51860746p+0, 0x1.1cfe55622d773p+0, 0x1.1d1707cfaeaedp+0, 0x1.1d2fbc611391cp+0,
+    0x1.1d4873168b9aap+0, 0x1.1d612bf046484p+0, 0x1.1d79e6ee731d7p+0, 0x1.1d92a41141a12p+0,
+    0x1.1dab6358e15e8p+0, 0x1.1dc424c581e4bp+0, 0x1.1ddce85752c71p+0, 0x1.1df5ae0e839d2p+0,
+    0x1.1e0e75eb44027p+0, 0x1.1e273fedc396bp+0, 0x1.1e400c1631fdbp+0, 0x1.1e58da64bedf8p+0,
+    0x1.1e71aad999e82p+0, 0x1.1e8a7d74f2c7ep+0, 0x1.1ea35236f9330p+0, 0x1.1ebc291fdce22p+0,
+    0x1.1ed5022fcd91dp+0, 0x1.1eeddd66fb02dp+0, 0x1.1f06bac594fa0p+0, 0x1.1f1f9a4bcb409p+0,
+    0x1.1f387bf9cda38p+0, 0x1.1f515fcfcbf45p+0, 0x1.1f6a45cdf6085p+0, 0x1.1f832df47bb94p+0,
+    0x1.1f9c18438ce4dp+0, 0x1.1fb504bb596cep+0, 0x1.1fcdf35c1137ap+0, 0x1.1fe6e425e42f3p+0,
+    0x1.1fffd7190241ep+0, 0x1.2018cc359b625p+0, 0x1.2031c37bdf872p+0, 0x1.204abcebfeab3p+0,
+    0x1.2063b88628cd6p+0, 0x1.207cb64a8df0fp+0, 0x1.2095b6395e1d2p+0, 0x1.20aeb852c95d7p+0,
+    0x1.20c7bc96ffc18p+0, 0x1.20e0c306315d1p+0, 0x1.20f9cba08e483p+0, 0x1.2112d666469efp+0,
+    0x1.212be3578a819p+0, 0x1.2144f2748a14ap+0, 0x1.215e03bd7580cp+0, 0x1.217717327cf2cp+0,
+    0x1.21902cd3d09b9p+0, 0x1.21a944a1a0b07p+0, 0x1.21c25e9c1d6aap+0, 0x1.21db7ac37707bp+0,
+    0x1.21f49917ddc96p+0, 0x1.220db99981f59p+0, 0x1.2226dc4893d64p+0, 0x1.2240012543b9cp+0,
+    0x1.2259282fc1f27p+0, 0x1.227251683ed71p+0, 0x1.228b7cceeac25p+0, 0x1.22a4aa63f6134p+0,
+    0x1.22bdda27912d1p+0, 0x1.22d70c19ec773p+0, 0x1.22f0403b385d2p+0, 0x1.2309768ba54ecp+0,
+    0x1.2322af0b63bffp+0, 0x1.233be9baa428fp+0, 0x1.2355269997062p+0, 0x1.236e65a86cd81p+0,
+    0x1.2387a6e756238p+0, 0x1.23a0ea5683718p+0, 0x1.23ba2ff6254f4p+0, 0x1.23d377c66c4e1p+0,
+    0x1.23ecc1c78903ap+0, 0x1.24060df9ac09bp+0, 0x1.241f5c5d05fe6p+0, 0x1.2438acf1c783ep+0,
+    0x1.2451ffb82140ap+0, 0x1.246b54b043df6p+0, 0x1.2484abda600efp+0, 0x1.249e0536a6828p+0,
+    0x1.24b760c547f15p+0, 0x1.24d0be8675170p+0, 0x1.24ea1e7a5eb35p+0, 0x1.250380a1358a3p+0,
+    0x1.251ce4fb2a63fp+0, 0x1.25364b886e0d0p+0, 0x1.254fb44931561p+0, 0x1.25691f3da5140p+0,
+    0x1.25828c65fa1ffp+0, 0x1.259bfbc261576p+0, 0x1.25b56d530b9bcp+0, 0x1.25cee11829d31p+0,
+    0x1.25e85711ece75p+0, 0x1.2601cf4085c6ep+0, 0x1.261b49a425645p+0, 0x1.2634c63cfcb65p+0,
+    0x1.264e450b3cb82p+0, 0x1.2667c60f1668ep+0, 0x1.26814948bacc3p+0, 0x1.269aceb85ae9dp+0,
+    0x1.26b4565e27cddp+0, 0x1.26cde03a52888p+0, 0x1.26e76c4d0c2e5p+0, 0x1.2700fa9685d82p+0,
+    0x1.271a8b16f0a30p+0, 0x1.27341dce7db03p+0, 0x1.274db2bd5e254p+0, 0x1.276749e3c32c0p+0,
+    0x1.2780e341ddf29p+0, 0x1.279a7ed7dfab5p+0, 0x1.27b41ca5f98cbp+0, 0x1.27cdbcac5cd1cp+0,
+    0x1.27e75eeb3ab98p+0, 0x1.28010362c4877p+0, 0x1.281aaa132b832p+0, 0x1.283452fca0f8ap+0,
+    0x1.284dfe1f56381p+0, 0x1.2867ab7b7c95fp+0, 0x1.28815b11456b1p+0, 0x1.289b0ce0e2147p+0,
+    0x1.28b4c0ea83f36p+0, 0x1.28ce772e5c6d7p+0, 0x1.28e82fac9cecap+0, 0x1.2901ea6576df0p+0,
+    0x1.291ba7591bb70p+0, 0x1.29356687bceb6p+0, 0x1.294f27f18bf72p+0, 0x1.2968eb96ba59ap+0,
+    0x1.2982b17779965p+0, 0x1.299c7993fb354p+0, 0x1.29b643ec70c27p+0, 0x1.29d010810bce8p+0,
+    0x1.29e9df51fdee1p+0, 0x1.2a03b05f78ba5p+0, 0x1.2a1d83a9add08p+0, 0x1.2a375930ced25p+0,
+    0x1.2a5130f50d65cp+0, 0x1.2a6b0af69b350p+0, 0x1.2a84e735a9eecp+0, 0x1.2a9ec5b26b45bp+0,
+    0x1.2ab8a66d10f13p+0, 0x1.2ad28965ccac9p+0, 0x1.2aec6e9cd037bp+0, 0x1.2b0656124d56bp+0,
+    0x1.2b203fc675d1fp+0, 0x1.2b3a2bb97b763p+0, 0x1.2b5419eb90148p+0, 0x1.2b6e0a5ce5823p+0,
+    0x1.2b87fd0dad990p+0, 0x1.2ba1f1fe1a36ep+0, 0x1.2bbbe92e5d3e3p+0, 0x1.2bd5e29ea8959p+0,
+    0x1.2befde4f2e280p+0, 0x1.2c09dc401fe4cp+0, 0x1.2c23dc71afbf7p+0, 0x1.2c3ddee40fb02p+0,
+    0x1.2c57e39771b2fp+0, 0x1.2c71ea8c07c89p+0, 0x1.2c8bf3c203f5fp+0, 0x1.2ca5ff3998446p+0,
+    0x1.2cc00cf2f6c18p+0, 0x1.2cda1cee517f3p+0, 0x1.2cf42f2bda93dp+0, 0x1.2d0e43abc41a0p+0,
+    0x1.2d285a6e4030bp+0, 0x1.2d42737380fb4p+0, 0x1.2d5c8ebbb8a15p+0, 0x1.2d76ac47194efp+0,
+    0x1.2d90cc15d5346p+0, 0x1.2daaee281e867p+0, 0x1.2dc5127e277e3p+0, 0x1.2ddf39182258fp+0,
+    0x1.2df961f641589p+0, 0x1.2e138d18b6c33p+0, 0x1.2e2dba7fb4e33p+0, 0x1.2e47ea2b6e077p+0,
+    0x1.2e621c1c14833p+0, 0x1.2e7c5051daadfp+0, 0x1.2e9686ccf2e3bp+0, 0x1.2eb0bf8d8f849p+0,
+    0x1.2ecafa93e2f56p+0, 0x1.2ee537e01f9f1p+0, 0x1.2eff777277ef0p+0, 0x1.2f19b94b1e570p+0,
+    0x1.2f33fd6a454d2p+0, 0x1.2f4e43d01f4bep+0, 0x1.2f688c7cded23p+0, 0x1.2f82d770b6634p+0,
+    0x1.2f9d24abd886bp+0, 0x1.2fb7742e77c89p+0, 0x1.2fd1c5f8c6b93p+0, 0x1.2fec1a0af7ed6p+0,
+    0x1.300670653dfe4p+0, 0x1.3020c907cb896p+0, 0x1.303b23f2d330bp+0, 0x1.30558126879a7p+0,
+    0x1.306fe0a31b715p+0, 0x1.308a4268c1648p+0, 0x1.30a4a677ac276p+0, 0x1.30bf0cd00e71ep+0,
+    0x1.30d975721b004p+0, 0x1.30f3e05e04933p+0, 0x1.310e4d93fdefbp+0, 0x1.3128bd1439df5p+0,
+    0x1.31432edeeb2fdp+0, 0x1.315da2f444b39p+0, 0x1.3178195479413p+0, 0x1.319291ffbbb3cp+0,
+    0x1.31ad0cf63eeacp+0, 0x1.31c78a3835ca1p+0, 0x1.31e209c5d33a0p+0, 0x1.31fc8b9f4a275p+0,
+    0x1.32170fc4cd831p+0, 0x1.323196369042ep+0, 0x1.324c1ef4c560ap+0, 0x1.3266a9ff9fdacp+0,
+    0x1.3281375752b40p+0, 0x1.329bc6fc10f3ap+0, 0x1.32b658ee0da54p+0, 0x1.32d0ed2d7bd8ep+0,
+    0x1.32eb83ba8ea32p+0, 0x1.33061c95791ccp+0, 0x1.3320b7be6e633p+0, 0x1.333b5535a1984p+0,
+    0x1.3355f4fb45e20p+0, 0x1.3370970f8e6b3p+0, 0x1.338b3b72ae62dp+0, 0x1.33a5e224d8fc7p+0,
+    0x1.33c08b26416ffp+0, 0x1.33db36771af9cp+0, 0x1.33f5e41798daap+0, 0x1.34109407ee57fp+0,
+    0x1.342b46484ebb4p+0, 0x1.3445fad8ed52cp+0, 0x1.3460b1b9fd712p+0, 0x1.347b6aebb26d5p+0,
+    0x1.3496266e3fa2dp+0, 0x1.34b0e441d8719p+0, 0x1.34cba466b03e1p+0, 0x1.34e666dcfa710p+0,
+    0x1.35012ba4ea77dp+0, 0x1.351bf2beb3c42p+0, 0x1.3536bc2a89cc4p+0, 0x1.355187e8a00aep+0,
+    0x1.356c55f929ff1p+0, 0x1.3587265c5b2c7p+0, 0x1.35a1f912671b1p+0, 0x1.35bcce1b81578p+0,
+    0x1.35d7a577dd72bp+0, 0x1.35f27f27af022p+0, 0x1.360d5b2b299fcp+0, 0x1.3628398280ea0p+0,
+    0x1.36431a2de883bp+0, 0x1.365dfd2d94143p+0, 0x1.3678e281b7475p+0, 0x1.3693ca2a85cd7p+0,
+    0x1.36aeb428335b4p+0, 0x1.36c9a07af3aa2p+0, 0x1.36e48f22fa77cp+0, 0x1.36ff80207b865p+0,
+    0x1.371a7373aa9cbp+0, 0x1.3735691cbb85fp+0, 0x1.3750611be211cp+0, 0x1.376b5b7152147p+0,
+    0x1.3786581d3f669p+0, 0x1.37a1571fdde55p+0, 0x1.37bc587961726p+0, 0x1.37d75c29fdf3fp+0,
+    0x1.37f26231e754ap+0, 0x1.380d6a9151839p+0, 0x1.3828754870746p+0, 0x1.38438257781f6p+0,
+    0x1.385e91be9c811p+0, 0x1.3879a37e119abp+0, 0x1.3894b7960b71fp+0, 0x1.38afce06be10ep+0,
+    0x1.38cae6d05d866p+0, 0x1.38e601f31de57p+0, 0x1.39011f6f3345fp+0, 0x1.391c3f44d1c41p+0,
+    0x1.393761742d808p+0, 0x1.395285fd7aa09p+0, 0x1.396dace0ed4e1p+0, 0x1.3988d61eb9b74p+0,
+    0x1.39a401b7140efp+0, 0x1.39bf2faa308c8p+0, 0x1.39da5ff8436bcp+0, 0x1.39f592a180ed3p+0,
+    0x1.3a10c7a61d55bp+0, 0x1.3a2bff064ceecp+0, 0x1.3a4738c244064p+0, 0x1.3a6274da36eedp+0,
+    0x1.3a7db34e59ff7p+0, 0x1.3a98f41ee193cp+0, 0x1.3ab4374c020bdp+0, 0x1.3acf7cd5efcc6p+0,
+    0x1.3aeac4bcdf3eap+0, 0x1.3b060f0104d04p+0, 0x1.3b215ba294f39p+0, 0x1.3b3caaa1c41f7p+0,
+    0x1.3b57fbfec6cf4p+0, 0x1.3b734fb9d182fp+0, 0x1.3b8ea5d318befp+0, 0x1.3ba9fe4ad10c4p+0,
+    0x1.3bc559212ef89p+0, 0x1.3be0b6566715fp+0, 0x1.3bfc15eaadfb1p+0, 0x1.3c1777de38434p+0,
+    0x1.3c32dc313a8e5p+0, 0x1.3c4e42e3e9808p+0, 0x1.3c69abf679c2ep+0, 0x1.3c8517692002ep+0,
+    0x1.3ca0853c10f28p+0, 0x1.3cbbf56f81488p+0, 0x1.3cd76803a5c00p+0, 0x1.3cf2dcf8b318dp+0,
+    0x1.3d0e544ede173p+0, 0x1.3d29ce065b842p+0, 0x1.3d454a1f602d0p+0, 0x1.3d60c89a20e40p+0,
+    0x1.3d7c4976d27fap+0, 0x1.3d97ccb5a9db3p+0, 0x1.3db35256dbd67p+0, 0x1.3dceda5a9d55cp+0,
+    0x1.3dea64c123422p+0, 0x1.3e05f18aa2891p+0, 0x1.3e2180b7501ccp+0, 0x1.3e3d124760f3dp+0,
+    0x1.3e58a63b0a09bp+0, 0x1.3e743c92805e2p+0, 0x1.3e8fd54df8f5cp+0, 0x1.3eab706da8d99p+0,
+    0x1.3ec70df1c5175p+0, 0x1.3ee2adda82c14p+0, 0x1.3efe502816ee3p+0, 0x1.3f19f4dab6b9cp+0,
+    0x1.3f359bf29743fp+0, 0x1.3f51456fedb16p+0, 0x1.3f6cf152ef2b8p+0, 0x1.3f889f9bd0e02p+0,
+    0x1.3fa4504ac801cp+0, 0x1.3fc0036009c78p+0, 0x1.3fdbb8dbcb6d2p+0, 0x1.3ff770be4232fp+0,
+    0x1.40132b07a35dfp+0, 0x1.402ee7b82437bp+0, 0x1.404aa6cffa0e5p+0, 0x1.4066684f5a34bp+0,
+    0x1.40822c367a024p+0, 0x1.409df2858ed31p+0, 0x1.40b9bb3cce07cp+0, 0x1.40d5865c6d05ap+0,
+    0x1.40f153e4a136ap+0, 0x1.410d23d5a0095p+0, 0x1.4128f62f9ef0ep+0, 0x1.4144caf2d3653p+0,
+    0x1.4160a21f72e2ap+0, 0x1.417c7bb5b2ea5p+0, 0x1.419857b5c901fp+0, 0x1.41b4361feab3fp+0,
+    0x1.41d016f44d8f5p+0, 0x1.41ebfa332727ap+0, 0x1.4207dfdcad153p+0, 0x1.4223c7f114f50p+0,
+    0x1.423fb2709468ap+0, 0x1.425b9f5b61163p+0, 0x1.42778eb1b0a8bp+0, 0x1.42938073b8cf9p+0,
+    0x1.42af74a1af3f1p+0, 0x1.42cb6b3bc9b00p+0, 0x1.42e764423ddfdp+0, 0x1.43035fb54190bp+0,
+    0x1.431f5d950a897p+0, 0x1.433b5de1ce958p+0, 0x1.4357609bc3850p+0, 0x1.437365c31f2ccp+0,
+    0x1.438f6d5817663p+0, 0x1.43ab775ae20f7p+0, 0x1.43c783cbb50b4p+0, 0x1.43e392aac6413p+0,
+    0x1.43ffa3f84b9d4p+0, 0x1.441bb7b47b105p+0, 0x1.4437cddf8a8fep+0, 0x1.4453e679b0160p+0,
+    0x1.4470018321a1ap+0, 0x1.448c1efc15362p+0, 0x1.44a83ee4c0dbdp+0, 0x1.44c4613d5a9f9p+0,
+    0x1.44e086061892dp+0, 0x1.44fcad3f30cbep+0, 0x1.4518d6e8d965bp+0, 0x1.45350303487fep+0,
+    0x1.4551318eb43ecp+0, 0x1.456d628b52cb4p+0, 0x1.458995f95a532p+0, 0x1.45a5cbd90108bp+0,
+    0x1.45c2042a7d232p+0, 0x1.45de3eee04de2p+0, 0x1.45fa7c23ce7a4p+0, 0x1.4616bbcc103cbp+0,
+    0x1.4632fde7006f4p+0, 0x1.464f4274d5609p+0, 0x1.466b8975c563ep+0, 0x1.4687d2ea06d15p+0,
+    0x1.46a41ed1d0057p+0, 0x1.46c06d2d5761dp+0, 0x1.46dcbdfcd34c8p+0, 0x1.46f911407a306p+0,
+    0x1.471566f8827d0p+0, 0x1.4731bf2522a6ap+0, 0x1.474e19c691265p+0, 0x1.476a76dd0479cp+0,
+    0x1.4786d668b3237p+0, 0x1.47a33869d3aa7p+0, 0x1.47bf9ce09c9abp+0, 0x1.47dc03cd4484ep+0,
+    0x1.47f86d3001fe5p+0, 0x1.4814d9090ba11p+0, 0x1.48314758980bfp+0, 0x1.484db81edde28p+0,
+    0x1.486a2b5c13cd0p+0, 0x1.4886a11070788p+0, 0x1.48a3193c2a96cp+0, 0x1.48bf93df78de3p+0,
+    0x1.48dc10fa920a1p+0, 0x1.48f8908dacda7p+0, 0x1.491512990013fp+0, 0x1.4931971cc2802p+0,
+    0x1.494e1e192aed2p+0, 0x1.496aa78e702dfp+0, 0x1.4987337cc91a5p+0, 0x1.49a3c1e46c8ebp+0,
+    0x1.49c052c5916c4p+0, 0x1.49dce6206e991p+0, 0x1.49f97bf53affdp+0, 0x1.4a1614442d900p+0,
+    0x1.4a32af0d7d3dep+0, 0x1.4a4f4c5161028p+0, 0x1.4a6bec100fdbap+0, 0x1.4a888e49c0cbdp+0,
+    0x1.4aa532feaada6p+0, 0x1.4ac1da2f05135p+0, 0x1.4ade83db0687ap+0, 0x1.4afb3002e64cep+0,
+    0x1.4b17dea6db7d7p+0, 0x1.4b348fc71d388p+0, 0x1.4b514363e2a20p+0, 0x1.4b6df97d62e2cp+0,
+    0x1.4b8ab213d5283p+0, 0x1.4ba76d2770a49p+0, 0x1.4bc42ab86c8f1p+0, 0x1.4be0eac700237p+0,
+    0x1.4bfdad5362a27p+0, 0x1.4c1a725dcb517p+0, 0x1.4c3739e6717aap+0, 0x1.4c5403ed8c6d2p+0,
+    0x1.4c70d073537cap+0, 0x1.4c8d9f77fe01dp+0, 0x1.4caa70fbc35a1p+0, 0x1.4cc744fedae78p+0,
+    0x1.4ce41b817c114p+0, 0x1.4d00f483de431p+0, 0x1.4d1dd00638ed8p+0, 0x1.4d3aae08c3860p+0,
+    0x1.4d578e8bb586bp+0, 0x1.4d74718f466ecp+0, 0x1.4d915713adc1ep+0, 0x1.4dae3f192308cp+0,
+    0x1.4dcb299fddd0dp+0, 0x1.4de816a815ac6p+0, 0x1.4e05063202327p+0, 0x1.4e21f83ddafefp+0,
+    0x1.4e3eeccbd7b2ap+0, 0x1.4e5be3dc2ff30p+0, 0x1.4e78dd6f1b6a6p+0, 0x1.4e95d984d1c81p+0,
+    0x1.4eb2d81d8abffp+0, 0x1.4ecfd9397e0aep+0, 0x1.4eecdcd8e3669p+0, 0x1.4f09e2fbf2958p+0,
+    0x1.4f26eba2e35f0p+0, 0x1.4f43f6cded8f4p+0, 0x1.4f61047d48f73p+0, 0x1.4f7e14b12d6cbp+0,
+    0x1.4f9b2769d2ca7p+0, 0x1.4fb83ca770efep+0, 0x1.4fd5546a3fc17p+0, 0x1.4ff26eb277284p+0,
+    0x1.500f8b804f127p+0, 0x1.502caad3ff72dp+0, 0x1.5049ccadc0412p+0, 0x1.5066f10dc97a0p+0,
+    0x1.508417f4531eep+0, 0x1.50a1416195360p+0, 0x1.50be6d55c7ca9p+0, 0x1.50db9bd122ec9p+0,
+    0x1.50f8ccd3deb0dp+0, 0x1.5116005e33311p+0, 0x1.51333670588bfp+0, 0x1.51506f0a86e4ep+0,
+    0x1.516daa2cf6642p+0, 0x1.518ae7d7df36ep+0, 0x1.51a8280b798f4p+0, 0x1.51c56ac7fda42p+0,
+    0x1.51e2b00da3b14p+0, 0x1.51fff7dca3f75p+0, 0x1.521d423536bbep+0, 0x1.523a8f1794495p+0,
+    0x1.5257de83f4eefp+0, 0x1.5275307a9100ep+0, 0x1.529284fba0d84p+0, 0x1.52afdc075cd2fp+0,
+    0x1.52cd359dfd53dp+0, 0x1.52ea91bfbac28p+0, 0x1.5307f06ccd8bap+0, 0x1.532551a56e20cp+0,
+    0x1.5342b569d4f82p+0, 0x1.53601bba3a8d1p+0, 0x1.537d8496d75fcp+0, 0x1.539aefffe3f54p+0,
+    0x1.53b85df598d78p+0, 0x1.53d5ce782e955p+0, 0x1.53f34187ddc28p+0, 0x1.5410b724def7bp+0,
+    0x1.542e2f4f6ad27p+0, 0x1.544baa07b9f54p+0, 0x1.5469274e05078p+0, 0x1.5486a72284b58p+0,
+    0x1.54a4298571b06p+0, 0x1.54c1ae7704ae4p+0, 0x1.54df35f7766a3p+0, 0x1.54fcc006ffa42p+0,
+    0x1.551a4ca5d920fp+0, 0x1.5537dbd43baa5p+0, 0x1.55556d92600f1p+0, 0x1.557301e07f22cp+0,
+    0x1.559098bed1bdfp+0, 0x1.55ae322d90be2p+0, 0x1.55cbce2cf505bp+0, 0x1.55e96cbd377bep+0,
+    0x1.56070dde910d2p+0, 0x1.5624b1913aaa8p+0, 0x1.564257d56d4a2p+0, 0x1.566000ab61e73p+0,
+    0x1.567dac1351819p+0, 0x1.569b5a0d751e4p+0, 0x1.56b90a9a05c72p+0, 0x1.56d6bdb93c8b0p+0,
+    0x1.56f4736b527dap+0, 0x1.57122bb080b7dp+0, 0x1.572fe68900573p+0, 0x1.574da3f50a7e5p+0,
+    0x1.576b63f4d854cp+0, 0x1.57892688a3072p+0, 0x1.57a6ebb0a3c6dp+0, 0x1.57c4b36d13ca5p+0,
+    0x1.57e27dbe2c4cfp+0, 0x1.58004aa4268f1p+0, 0x1.581e1a1f3bd60p+0, 0x1.583bec2fa56c1p+0,
+    0x1.5859c0d59ca07p+0, 0x1.587798115ac76p+0, 0x1.589571e31939fp+0, 0x1.58b34e4b11567p+0,
+    0x1.58d12d497c7fdp+0, 0x1.58ef0ede941e4p+0, 0x1.590cf30a919edp+0, 0x1.592ad9cdae738p+0,
+    0x1.5948c32824135p+0, 0x1.5966af1a2bfa5p+0, 0x1.59849da3ffa96p+0, 0x1.59a28ec5d8a69p+0,
+    0x1.59c0827ff07ccp+0, 0x1.59de78d280bbep+0, 0x1.59fc71bdc2f8ep+0, 0x1.5a1a6d41f0cdbp+0,
+    0x1.5a386b5f43d92p+0, 0x1.5a566c15f5bf3p+0, 0x1.5a746f664028bp+0, 0x1.5a9275505cc38p+0,
+    0x1.5ab07dd485429p+0, 0x1.5ace88f2f35dcp+0, 0x1.5aec96abe0d1fp+0, 0x1.5b0aa6ff87610p+0,
+    0x1.5b28b9ee20d1ep+0, 0x1.5b46cf77e6f06p+0, 0x1.5b64e79d138d8p+0, 0x1.5b83025de07f2p+0,
+    0x1.5ba11fba87a03p+0, 0x1.5bbf3fb342d0ap+0, 0x1.5bdd62484bf56p+0, 0x1.5bfb8779dcf88p+0,
+    0x1.5c19af482fc8fp+0, 0x1.5c37d9b37e5abp+0, 0x1.5c5606bc02a6dp+0, 0x1.5c743661f6ab6p+0,
+    0x1.5c9268a5946b7p+0, 0x1.5cb09d8715ef3p+0, 0x1.5cced506b543ap+0, 0x1.5ced0f24ac7b2p+0,
+    0x1.5d0b4be135accp+0, 0x1.5d298b3c8af4cp+0, 0x1.5d47cd36e6747p+0, 0x1.5d6611d082522p+0,
+    0x1.5d84590998b93p+0, 0x1.5da2a2e263d9fp+0, 0x1.5dc0ef5b1de9ep+0, 0x1.5ddf3e7401238p+0,
+    0x1.5dfd902d47c65p+0, 0x1.5e1be4872c16dp+0, 0x1.5e3a3b81e85ecp+0, 0x1.5e58951db6eccp+0,
+    0x1.5e76f15ad2148p+0, 0x1.5e955039742eep+0, 0x1.5eb3b1b9d799ap+0, 0x1.5ed215dc36b7bp+0,
+    0x1.5ef07ca0cbf0fp+0, 0x1.5f0ee607d1b29p+0, 0x1.5f2d5211826e8p+0, 0x1.5f4bc0be189bep+0,
+    0x1.5f6a320dceb71p+0, 0x1.5f88a600df413p+0, 0x1.5fa71c9784c0bp+0, 0x1.5fc595d1f9c0fp+0,
+    0x1.5fe411b078d26p+0, 0x1.600290333c8acp+0, 0x1.6021115a7f849p+0, 0x1.603f95267c5f9p+0,
+    0x1.605e1b976dc09p+0, 0x1.607ca4ad8e517p+0, 0x1.609b306918c13p+0, 0x1.60b9beca47c3ep+0,
+    0x1.60d84fd15612ap+0, 0x1.60f6e37e7e6bbp+0, 0x1.611579d1fb925p+0, 0x1.613412cc084f1p+0,
+    0x1.6152ae6cdf6f4p+0, 0x1.61714cb4bbc5bp+0, 0x1.618feda3d829fp+0, 0x1.61ae913a6f78dp+0,
+    0x1.61cd3778bc944p+0, 0x1.61ebe05efa634p+0, 0x1.620a8bed63d1fp+0, 0x1.62293a2433d18p+0,
+    0x1.6247eb03a5585p+0, 0x1.62669e8bf361bp+0, 0x1.628554bd58ee5p+0, 0x1.62a40d981103cp+0,
+    0x1.62c2c91c56acdp+0, 0x1.62e1874a64f97p+0, 0x1.6300482276fe8p+0, 0x1.631f0ba4c7d64p+0,
+    0x1.633dd1d1929fdp+0, 0x1.635c9aa9127fbp+0, 0x1.637b662b829f5p+0, 0x1.639a34591e2d5p+0,
+    0x1.63b90532205d8p+0, 0x1.63d7d8b6c468ap+0, 0x1.63f6aee7458cdp+0, 0x1.641587c3df0d3p+0,
+    0x1.6434634ccc320p+0, 0x1.645341824848bp+0, 0x1.647222648ea3dp+0, 0x1.649105f3da9b2p+0,
+    0x1.64afec30678b7p+0, 0x1.64ced51a70d6bp+0, 0x1.64edc0b231e41p+0, 0x1.650caef7e61fdp+0,
+    0x1.652b9febc8fb7p+0, 0x1.654a938e15ed7p+0, 0x1.656989df08719p+0, 0x1.658882dedc08cp+0,
+    0x1.65a77e8dcc390p+0, 0x1.65c67cec148d8p+0, 0x1.65e57df9f096bp+0, 0x1.660481b79bea1p+0,
+    0x1.6623882552225p+0, 0x1.664291434edf4p+0, 0x1.66619d11cdc5fp+0, 0x1.6680ab910a809p+0,
+    0x1.669fbcc140be7p+0, 0x1.66bed0a2ac343p+0, 0x1.66dde735889b8p+0, 0x1.66fd007a11b33p+0,
+    0x1.671c1c70833f6p+0, 0x1.673b3b1919094p+0, 0x1.675a5c740edf5p+0, 0x1.67798081a0951p+0,
+    0x1.6798a7420a036p+0, 0x1.67b7d0b587083p+0, 0x1.67d6fcdc5386ap+0, 0x1.67f62bb6ab672p+0,
+    0x1.68155d44ca973p+0, 0x1.68349186ed099p+0, 0x1.6853c87d4eb62p+0, 0x1.687302282b9a1p+0,
+    0x1.68923e87bfb7ap+0, 0x1.68b17d9c47168p+0, 0x1.68d0bf65fdc34p+0, 0x1.68f003e51fcfep+0,
+    0x1.690f4b19e9538p+0, 0x1.692e9504966a8p+0, 0x1.694de1a563367p+0, 0x1.696d30fc8bde0p+0,
+    0x1.698c830a4c8d4p+0, 0x1.69abd7cee1755p+0, 0x1.69cb2f4a86ccap+0, 0x1.69ea897d78ceep+0,
+    0x1.6a09e667f3bcdp+0, 0x1.6a29460a33dc8p+0, 0x1.6a48a86475795p+0, 0x1.6a680d76f4e3cp+0,
+    0x1.6a877541ee718p+0, 0x1.6aa6dfc59e7d9p+0, 0x1.6ac64d0241683p+0, 0x1.6ae5bcf81396cp+0,
+    0x1.6b052fa75173ep+0, 0x1.6b24a510376f9p+0, 0x1.6b441d3301feep+0, 0x1.6b63980fed9c4p+0,
+    0x1.6b8315a736c75p+0, 0x1.6ba295f91a04ep+0, 0x1.6bc21905d3df0p+0, 0x1.6be19ecda0e53p+0,
+    0x1.6c012750bdabfp+0, 0x1.6c20b28f66cd2p+0, 0x1.6c404089d8e7dp+0, 0x1.6c5fd14050a07p+0,
+    0x1.6c7f64b30aa09p+0, 0x1.6c9efae243971p+0, 0x1.6cbe93ce38381p+0, 0x1.6cde2f77253cfp+0,
+    0x1.6cfdcddd47645p+0, 0x1.6d1d6f00db723p+0, 0x1.6d3d12e21e2fbp+0, 0x1.6d5cb9814c6b5p+0,
+    0x1.6d7c62dea2f8ap+0, 0x1.6d9c0efa5eb0dp+0, 0x1.6dbbbdd4bc720p+0, 0x1.6ddb6f6df91fcp+0,
+    0x1.6dfb23c651a2fp+0, 0x1.6e1adade02e99p+0, 0x1.6e3a94b549e71p+0, 0x1.6e5a514c63941p+0,
+    0x1.6e7a10a38cee8p+0, 0x1.6e99d2bb02f99p+0, 0x1.6eb9979302bddp+0, 0x1.6ed95f2bc9490p+0,
+    0x1.6ef9298593ae5p+0, 0x1.6f18f6a09f060p+0, 0x1.6f38c67d286ddp+0, 0x1.6f58991b6d08bp+0,
+    0x1.6f786e7ba9fefp+0, 0x1.6f98469e1c7e1p+0, 0x1.6fb8218301b90p+0, 0x1.6fd7ff2a96e7ep+0,
+    0x1.6ff7df9519484p+0, 0x1.7017c2c2c61cdp+0, 0x1.7037a8b3daadbp+0, 0x1.7057916894485p+0,
+    0x1.70777ce1303f6p+0, 0x1.70976b1debeaep+0, 0x1.70b75c1f04a84p+0, 0x1.70d74fe4b7da2p+0,
+    0x1.70f7466f42e87p+0, 0x1.71173fbee3409p+0, 0x1.71373bd3d6551p+0, 0x1.71573aae599dfp+0,
+    0x1.71773c4eaa988p+0, 0x1.719740b506c74p+0, 0x1.71b747e1abb24p+0, 0x1.71d751d4d6e6bp+0,
+    0x1.71f75e8ec5f74p+0, 0x1.72176e0fb67bdp+0, 0x1.72378057e611ap+0, 0x1.72579567925b6p+0,
+    0x1.7277ad3ef9011p+0, 0x1.7297c7de57afep+0, 0x1.72b7e545ec1a8p+0, 0x1.72d80575f3f90p+0,
+    0x1.72f8286ead08ap+0, 0x1.73184e30550c2p+0, 0x1.733876bb29cb8p+0, 0x1.7358a20f69143p+0,
+    0x1.7378d02d50b8fp+0, 0x1.739901151e91ep+0, 0x1.73b934c7107c7p+0, 0x1.73d96b43645b8p+0,
+    0x1.73f9a48a58174p+0, 0x1.7419e09c299d3p+0, 0x1.743a1f7916e05p+0, 0x1.745a61215dd8ep+0,
+    0x1.747aa5953c849p+0, 0x1.749aecd4f0e66p+0, 0x1.74bb36e0b906dp+0, 0x1.74db83b8d2f39p+0,
+    0x1.74fbd35d7cbfdp+0, 0x1.751c25cef4843p+0, 0x1.753c7b0d785e8p+0, 0x1.755cd31946722p+0,
+    0x1.757d2df29ce7cp+0, 0x1.759d8b99b9ed7p+0, 0x1.75bdec0edbb6bp+0, 0x1.75de4f52407c5p+0,
+    0x1.75feb564267c9p+0, 0x1.761f1e44cbfb2p+0, 0x1.763f89f46f40fp+0, 0x1.765ff8734e9cap+0,
+    0x1.768069c1a861dp+0, 0x1.76a0dddfbae9fp+0, 0x1.76c154cdc4937p+0, 0x1.76e1ce8c03c29p+0,
+    0x1.77024b1ab6e09p+0, 0x1.7722ca7a1c5c8p+0, 0x1.77434caa72aa7p+0, 0x1.7763d1abf8444p+0,
+    0x1.7784597eeba8fp+0, 0x1.77a4e4238b5d0p+0, 0x1.77c5719a15ea6p+0, 0x1.77e601e2c9e07p+0,
+    0x1.780694fde5d3fp+0, 0x1.78272aeba85f2p+0, 0x1.7847c3ac50219p+0, 0x1.78685f401bc05p+0,
+    0x1.7888fda749e5dp+0, 0x1.78a99ee219421p+0, 0x1.78ca42f0c88a5p+0, 0x1.78eae9d396795p+0,
+    0x1.790b938ac1cf6p+0, 0x1.792c401689522p+0, 0x1.794cef772bcc9p+0, 0x1.796da1ace80f4p+0,
+    0x1.798e56b7fcf03p+0, 0x1.79af0e98a94adp+0, 0x1.79cfc94f2bfffp+0, 0x1.79f086dbc3f5ep+0,
+    0x1.7a11473eb0187p+0, 0x1.7a320a782f58cp+0, 0x1.7a52d08880ad9p+0, 0x1.7a73996fe3130p+0,
+    0x1.7a94652e958aap+0, 0x1.7ab533c4d71b7p+0, 0x1.7ad60532e6d20p+0, 0x1.7af6d97903c04p+0,
+    0x1.7b17b0976cfdbp+0, 0x1.7b388a8e61a72p+0, 0x1.7b59675e20defp+0, 0x1.7b7a4706e9cd1p+0,
+    0x1.7b9b2988fb9ecp+0, 0x1.7bbc0ee49586dp+0, 0x1.7bdcf719f6bd7p+0, 0x1.7bfde2295e808p+0,
+    0x1.7c1ed0130c132p+0, 0x1.7c3fc0d73ebe2p+0, 0x1.7c60b47635cf9p+0, 0x1.7c81aaf0309b3p+0,
+    0x1.7ca2a4456e7a3p+0, 0x1.7cc3a0762ecb2p+0, 0x1.7ce49f82b0f24p+0, 0x1.7d05a16b34593p+0,
+    0x1.7d26a62ff86f0p+0, 0x1.7d47add13ca87p+0, 0x1.7d68b84f407f8p+0, 0x1.7d89c5aa4373ep+0,
+    0x1.7daad5e2850acp+0, 0x1.7dcbe8f844cebp+0, 0x1.7decfeebc24fep+0, 0x1.7e0e17bd3d240p+0,
+    0x1.7e2f336cf4e62p+0, 0x1.7e5051fb29370p+0, 0x1.7e71736819bcdp+0, 0x1.7e9297b406234p+0,
+    0x1.7eb3bedf2e1b9p+0, 0x1.7ed4e8e9d15c8p+0, 0x1.7ef615d42fa24p+0, 0x1.7f17459e88aebp+0,
+    0x1.7f3878491c491p+0, 0x1.7f59add42a3e4p+0, 0x1.7f7ae63ff260ap+0, 0x1.7f9c218cb4881p+0,
+    0x1.7fbd5fbab091fp+0, 0x1.7fdea0ca26616p+0, 0x1.7fffe4bb55decp+0, 0x1.80212b8e7ef82p+0,
+    0x1.80427543e1a12p+0, 0x1.8063c1dbbdd2dp+0, 0x1.80851156538bep+0, 0x1.80a663b3e2d09p+0,
+    0x1.80c7b8f4abaa9p+0, 0x1.80e91118ee294p+0, 0x1.810a6c20ea617p+0, 0x1.812bca0ce06d9p+0,
+    0x1.814d2add106d9p+0, 0x1.816e8e91ba871p+0, 0x1.818ff52b1ee50p+0, 0x1.81b15ea97db82p+0,
+    0x1.81d2cb0d1736ap+0, 0x1.81f43a562b9c4p+0, 0x1.8215ac84fb2a6p+0, 0x1.82372199c627dp+0,
+    0x1.82589994cce13p+0, 0x1.827a14764fa86p+0, 0x1.829b923e8ed53p+0, 0x1.82bd12edcac4ap+0,
+    0x1.82de968443d9ap+0, 0x1.83001d023a7c8p+0, 0x1.8321a667ef1b2p+0, 0x1.834332b5a2291p+0,
+    0x1.8364c1eb941f7p+0, 0x1.8386540a057cfp+0, 0x1.83a7e91136c5dp+0, 0x1.83c9810168840p+0,
+    0x1.83eb1bdadb46dp+0, 0x1.840cb99dcfa38p+0, 0x1.842e5a4a8634ap+0, 0x1.844ffde13f9a7p+0,
+    0x1.8471a4623c7adp+0, 0x1.84934dcdbd813p+0, 0x1.84b4fa24035eap+0, 0x1.84d6a9654ec9ep+0,
+    0x1.84f85b91e07f1p+0, 0x1.851a10a9f9403p+0, 0x1.853bc8add9d4cp+0, 0x1.855d839dc309cp+0,
+    0x1.857f4179f5b21p+0, 0x1.85a10242b2a5fp+0, 0x1.85c2c5f83ac35p+0, 0x1.85e48c9aceedep+0,
+    0x1.8606562ab00ecp+0, 0x1.862822a81f14dp+0, 0x1.8649f2135cf48p+0, 0x1.866bc46caaa7fp+0,
+    0x1.868d99b4492edp+0, 0x1.86af71ea798e7p+0, 0x1.86d14d0f7cd1dp+0, 0x1.86f32b239409bp+0,
+    0x1.87150c27004c2p+0, 0x1.8736f01a02b53p+0, 0x1.8758d6fcdc666p+0, 0x1.877ac0cfce86dp+0,
+    0x1.879cad931a436p+0, 0x1.87be9d4700ce9p+0, 0x1.87e08febc3608p+0, 0x1.88028581a3370p+0,
+    0x1.88247e08e1957p+0, 0x1.88467981bfc4fp+0, 0x1.886877ec7f144p+0, 0x1.888a794960d7cp+0,
+    0x1.88ac7d98a6699p+0, 0x1.88ce84da91297p+0, 0x1.88f08f0f627cbp+0, 0x1.89129c375bce8p+0,
+    0x1.8934ac52be8f7p+0, 0x1.8956bf61cc361p+0, 0x1.8978d564c63e7p+0, 0x1.899aee5bee2a4p+0,
+    0x1.89bd0a478580fp+0, 0x1.89df2927cdcfbp+0, 0x1.8a014afd08a94p+0, 0x1.8a236fc777a60p+0,
+    0x1.8a4597875c644p+0, 0x1.8a67c23cf887cp+0, 0x1.8a89efe88dba1p+0, 0x1.8aac208a5daa7p+0,
+    0x1.8ace5422aa0dbp+0, 0x1.8af08ab1b49e9p+0, 0x1.8b12c437bf1d4p+0, 0x1.8b3500b50b4fdp+0,
+    0x1.8b574029db01ep+0, 0x1.8b7982967004fp+0, 0x1.8b9bc7fb0c302p+0, 0x1.8bbe1057f1602p+0,
+    0x1.8be05bad61778p+0, 0x1.8c02a9fb9e5e9p+0, 0x1.8c24fb42ea033p+0, 0x1.8c474f8386591p+0,
+    0x1.8c69a6bdb5598p+0, 0x1.8c8c00f1b903ap+0, 0x1.8cae5e1fd35c4p+0, 0x1.8cd0be48466dep+0,
+    0x1.8cf3216b5448cp+0, 0x1.8d1587893f02ep+0, 0x1.8d37f0a248b7fp+0, 0x1.8d5a5cb6b3896p+0,
+    0x1.8d7ccbc6c19e6p+0, 0x1.8d9f3dd2b523dp+0, 0x1.8dc1b2dad04c4p+0, 0x1.8de42adf55502p+0,
+    0x1.8e06a5e0866d9p+0, 0x1.8e2923dea5e85p+0, 0x1.8e4ba4d9f60a1p+0, 0x1.8e6e28d2b9221p+0,
+    0x1.8e90afc931857p+0, 0x1.8eb339bda18f0p+0, 0x1.8ed5c6b04b9f6p+0, 0x1.8ef856a1721cdp+0,
+    0x1.8f1ae99157736p+0, 0x1.8f3d7f803e150p+0, 0x1.8f60186e68793p+0, 0x1.8f82b45c191d6p+0,
+    0x1.8fa553499284bp+0, 0x1.8fc7f5371737ep+0, 0x1.8fea9a24e9c5cp+0, 0x1.900d42134cc29p+0,
+    0x1.902fed0282c8ap+0, 0x1.90529af2ce77ep+0, 0x1.90754be472760p+0, 0x1.9097ffd7b16e8p+0,
+    0x1.90bab6ccce12cp+0, 0x1.90dd70c40b19bp+0, 0x1.91002dbdab403p+0, 0x1.9122edb9f148fp+0,
+    0x1.9145b0b91ffc6p+0, 0x1.916876bb7a289p+0, 0x1.918b3fc142a19p+0, 0x1.91ae0bcabc413p+0,
+    0x1.91d0dad829e70p+0, 0x1.91f3ace9ce785p+0, 0x1.921681ffece05p+0, 0x1.92395a1ac8100p+0,
+    0x1.925c353aa2fe2p+0, 0x1.927f135fc0a74p+0, 0x1.92a1f48a640dcp+0, 0x1.92c4d8bad039cp+0,
+    0x1.92e7bff148396p+0, 0x1.930aaa2e0f204p+0, 0x1.932d977168083p+0, 0x1.935087bb96107p+0,
+    0x1.93737b0cdc5e5p+0, 0x1.939671657e1cep+0, 0x1.93b96ac5be7d1p+0, 0x1.93dc672de0b57p+0,
+    0x1.93ff669e2802bp+0, 0x1.94226916d7a71p+0, 0x1.94456e9832eadp+0, 0x1.946877227d1bfp+0,
+    0x1.948b82b5f98e5p+0, 0x1.94ae9152eb9b9p+0, 0x1.94d1a2f996a33p+0, 0x1.94f4b7aa3e0aap+0,
+    0x1.9517cf65253d1p+0, 0x1.953aea2a8fab7p+0, 0x1.955e07fac0ccdp+0, 0x1.958128d5fc1dcp+0,
+    0x1.95a44cbc8520fp+0, 0x1.95c773ae9f5ecp+0, 0x1.95ea9dac8e658p+0, 0x1.960dcab695c95p+0,
+    0x1.9630faccf9243p+0, 0x1.96542deffc160p+0, 0x1.9677641fe2446p+0, 0x1.969a9d5cef5afp+0,
+    0x1.96bdd9a7670b3p+0, 0x1.96e118ff8d0c6p+0, 0x1.97045b65a51bap+0, 0x1.9727a0d9f2fc0p+0,
+    0x1.974ae95cba768p+0, 0x1.976e34ee3f59dp+0, 0x1.9791838ec57abp+0, 0x1.97b4d53e90b39p+0,
+    0x1.97d829fde4e50p+0, 0x1.97fb81cd05f52p+0, 0x1.981edcac37d05p+0, 0x1.98423a9bbe688p+0,
+    0x1.98659b9bddb5bp+0, 0x1.9888ffacd9b5dp+0, 0x1.98ac66cef66c8p+0, 0x1.98cfd10277e37p+0,
+    0x1.98f33e47a22a2p+0, 0x1.9916ae9eb9561p+0, 0x1.993a220801829p+0, 0x1.995d9883bed0dp+0,
+    0x1.9981121235681p+0, 0x1.99a48eb3a9753p+0, 0x1.99c80e685f2b5p+0, 0x1.99eb91309ac33p+0,
+    0x1.9a0f170ca07bap+0, 0x1.9a329ffcb4995p+0, 0x1.9a562c011b66dp+0, 0x1.9a79bb1a1934cp+0,
+    0x1.9a9d4d47f2598p+0, 0x1.9ac0e28aeb316p+0, 0x1.9ae47ae3481edp+0, 0x1.9b0816514d89ep+0,
+    0x1.9b2bb4d53fe0dp+0, 0x1.9b4f566f6397ap+0, 0x1.9b72fb1ffd285p+0, 0x1.9b96a2e75112ep+0,
+    0x1.9bba4dc5a3dd3p+0, 0x1.9bddfbbb3a131p+0, 0x1.9c01acc858463p+0, 0x1.9c2560ed430e4p+0,
+    0x1.9c49182a3f090p+0, 0x1.9c6cd27f90d9fp+0, 0x1.9c908fed7d2aap+0, 0x1.9cb4507448aa9p+0,
+    0x1.9cd81414380f2p+0, 0x1.9cfbdacd9013dp+0, 0x1.9d1fa4a09579dp+0, 0x1.9d43718d8d089p+0,
+    0x1.9d674194bb8d5p+0, 0x1.9d8b14b665db3p+0, 0x1.9daeeaf2d0cb8p+0, 0x1.9dd2c44a413d6p+0,
+    0x1.9df6a0bcfc15ep+0, 0x1.9e1a804b46403p+0, 0x1.9e3e62f564ad5p+0, 0x1.9e6248bb9c545p+0,
+    0x1.9e86319e32323p+0, 0x1.9eaa1d9d6b4a0p+0, 0x1.9ece0cb98ca4bp+0, 0x1.9ef1fef2db513p+0,
+    0x1.9f15f4499c647p+0, 0x1.9f39ecbe14f97p+0, 0x1.9f5de8508a311p+0, 0x1.9f81e70141324p+0,
+    0x1.9fa5e8d07f29ep+0, 0x1.9fc9edbe894adp+0, 0x1.9fedf5cba4ce0p+0, 0x1.a01200f816f25p+0,
+    0x1.a0360f4424fcbp+0, 0x1.a05a20b01437fp+0, 0x1.a07e353c29f50p+0, 0x1.a0a24ce8ab8adp+0,
+    0x1.a0c667b5de565p+0, 0x1.a0ea85a407ba5p+0, 0x1.a10ea6b36d1fep+0, 0x1.a132cae453f5ep+0,
+    0x1.a156f23701b15p+0, 0x1.a17b1cabbbcd4p+0, 0x1.a19f4a42c7ca9p+0, 0x1.a1c37afc6b306p+0,
+    0x1.a1e7aed8eb8bbp+0, 0x1.a20be5d88e6fbp+0, 0x1.a2301ffb99757p+0, 0x1.a2545d42523c1p+0,
+    0x1.a2789dacfe68cp+0, 0x1.a29ce13be3a6cp+0, 0x1.a2c127ef47a74p+0, 0x1.a2e571c77021ap+0,
+    0x1.a309bec4a2d33p+0, 0x1.a32e0ee7257f5p+0, 0x1.a352622f3def6p+0, 0x1.a376b89d31f2fp+0,
+    0x1.a39b1231475f7p+0, 0x1.a3bf6eebc4108p+0, 0x1.a3e3ceccede7cp+0, 0x1.a40831d50accdp+0,
+    0x1.a42c980460ad8p+0, 0x1.a451015b357d9p+0, 0x1.a4756dd9cf36ep+0, 0x1.a499dd8073d96p+0,
+    0x1.a4be504f696b1p+0, 0x1.a4e2c646f5f7fp+0, 0x1.a5073f675f924p+0, 0x1.a52bbbb0ec521p+0,
+    0x1.a5503b23e255dp+0, 0x1.a574bdc087c1bp+0, 0x1.a599438722c03p+0, 0x1.a5bdcc77f981ep+0,
+    0x1.a5e25893523d4p+0, 0x1.a606e7d9732f1p+0, 0x1.a62b7a4aa29a1p+0, 0x1.a6500fe726c72p+0,
+    0x1.a674a8af46052p+0, 0x1.a69944a346a93p+0, 0x1.a6bde3c36f0e6p+0, 0x1.a6e286100595fp+0,
+    0x1.a7072b8950a73p+0, 0x1.a72bd42f96afap+0, 0x1.a75080031e22bp+0, 0x1.a7752f042d7a1p+0,
+    0x1.a799e1330b358p+0, 0x1.a7be968ffddaep+0, 0x1.a7e34f1b4bf62p+0, 0x1.a8080ad53c195p+0,
+    0x1.a82cc9be14dcap+0, 0x1.a8518bd61cde7p+0, 0x1.a876511d9ac32p+0, 0x1.a89b1994d5354p+0,
+    0x1.a8bfe53c12e59p+0, 0x1.a8e4b4139a8acp+0, 0x1.a909861bb2e1dp+0, 0x1.a92e5b54a2adcp+0,
+    0x1.a95333beb0b7ep+0, 0x1.a9780f5a23cf6p+0, 0x1.a99cee2742c9dp+0, 0x1.a9c1d0265482cp+0,
+    0x1.a9e6b5579fdbfp+0, 0x1.aa0b9dbb6bbd5p+0, 0x1.aa308951ff14dp+0, 0x1.aa55781ba0d6ap+0,
+    0x1.aa7a6a1897fd2p+0, 0x1.aa9f5f492b88cp+0, 0x1.aac457ada2803p+0, 0x1.aae9534643f03p+0,
+    0x1.ab0e521356ebap+0, 0x1.ab335415228bbp+0, 0x1.ab58594bedefap+0, 0x1.ab7d61b8003cdp+0,
+    0x1.aba26d59a09eep+0, 0x1.abc77c311647ap+0, 0x1.abec8e3ea86eep+0, 0x1.ac11a3829e52cp+0,
+    0x1.ac36bbfd3f37ap+0, 0x1.ac5bd7aed267dp+0, 0x1.ac80f6979f340p+0, 0x1.aca618b7ecf31p+0,
+    0x1.accb3e100301ep+0, 0x1.acf066a028c3ap+0, 0x1.ad159268a5a1cp+0, 0x1.ad3ac169c10bbp+0,
+    0x1.ad5ff3a3c2774p+0, 0x1.ad852916f1606p+0, 0x1.adaa61c395493p+0, 0x1.adcf9da9f5b9fp+0,
+    0x1.adf4dcca5a413p+0, 0x1.ae1a1f250a73bp+0, 0x1.ae3f64ba4dec6p+0, 0x1.ae64ad8a6c4c5p+0,
+    0x1.ae89f995ad3adp+0, 0x1.aeaf48dc58659p+0, 0x1.aed49b5eb5803p+0, 0x1.aef9f11d0c44bp+0,
+    0x1.af1f4a17a4735p+0, 0x1.af44a64ec5d26p+0, 0x1.af6a05c2b82e9p+0, 0x1.af8f6873c35acp+0,
+    0x1.afb4ce622f2ffp+0, 0x1.afda378e438d7p+0, 0x1.afffa3f84858cp+0, 0x1.b02513a0857dbp+0,
+    0x1.b04a868742ee4p+0, 0x1.b06ffcacc8a2ap+0, 0x1.b09576115e994p+0, 0x1.b0baf2b54cd6dp+0,
+    0x1.b0e07298db666p+0, 0x1.b105f5bc5258fp+0, 0x1.b12b7c1ff9c61p+0, 0x1.b15105c419cb6p+0,
+    0x1.b17692a8fa8cdp+0, 0x1.b19c22cee4349p+0, 0x1.b1c1b6361ef31p+0, 0x1.b1e74cdef2fefp+0,
+    0x1.b20ce6c9a8952p+0, 0x1.b23283f687f8fp+0, 0x1.b2582465d973cp+0, 0x1.b27dc817e5555p+0,
+    0x1.b2a36f0cf3f3ap+0, 0x1.b2c919454daafp+0, 0x1.b2eec6c13adddp+0, 0x1.b314778103f50p+0,
+    0x1.b33a2b84f15fbp+0, 0x1.b35fe2cd4b932p+0, 0x1.b3859d5a5b0b1p+0, 0x1.b3ab5b2c68495p+0,
+    0x1.b3d11c43bbd62p+0, 0x1.b3f6e0a09e3ffp+0, 0x1.b41ca843581bap+0, 0x1.b442732c32044p+0,
+    0x1.b468415b749b1p+0, 0x1.b48e12d16887dp+0, 0x1.b4b3e78e56786p+0, 0x1.b4d9bf9287210p+0,
+    0x1.b4ff9ade433c6p+0, 0x1.b5257971d38b2p+0, 0x1.b54b5b4d80d4ap+0, 0x1.b571407193e63p+0,
+    0x1.b59728de5593ap+0, 0x1.b5bd14940eb70p+0, 0x1.b5e303930830cp+0, 0x1.b608f5db8ae79p+0,
+    0x1.b62eeb6ddfc87p+0, 0x1.b654e44a4fc6cp+0, 0x1.b67ae07123dc3p+0, 0x1.b6a0dfe2a508bp+0,
+    0x1.b6c6e29f1c52ap+0, 0x1.b6ece8a6d2c6ap+0, 0x1.b712f1fa1177bp+0, 0x1.b738fe99217f1p+0,
+    0x1.b75f0e844bfc6p+0, 0x1.b78521bbda15cp+0, 0x1.b7ab384014f76p+0, 0x1.b7d1521145d3fp+0,
+    0x1.b7f76f2fb5e47p+0, 0x1.b81d8f9bae684p+0, 0x1.b843b35578a51p+0, 0x1.b869da5d5de6fp+0,
+    0x1.b89004b3a7804p+0, 0x1.b8b632589ec9bp+0, 0x1.b8dc634c8d228p+0, 0x1.b902978fbbf01p+0,
+    0x1.b928cf22749e4p+0, 0x1.b94f0a05009f3p+0, 0x1.b9754837a96b7p+0, 0x1.b99b89bab881fp+0,
+    0x1.b9c1ce8e77680p+0, 0x1.b9e816b32fa95p+0, 0x1.ba0e62292ad7dp+0, 0x1.ba34b0f0b28c0p+0,
+    0x1.ba5b030a1064ap+0, 0x1.ba8158758e06dp+0, 0x1.baa7b133751e3p+0, 0x1.bace0d440f5cap+0,
+    0x1.baf46ca7a67a7p+0, 0x1.bb1acf5e84367p+0, 0x1.bb413568f255ap+0, 0x1.bb679ec73aa38p+0,
+    0x1.bb8e0b79a6f1fp+0, 0x1.bbb47b8081194p+0, 0x1.bbdaeedc12f82p+0, 0x1.bc01658ca673bp+0,
+    0x1.bc27df9285775p+0, 0x1.bc4e5cedf9f50p+0, 0x1.bc74dd9f4de4fp+0, 0x1.bc9b61a6cb460p+0,
+    0x1.bcc1e904bc1d2p+0, 0x1.bce873b96a760p+0, 0x1.bd0f01c520628p+0, 0x1.bd35932827fb0p+0,
+    0x1.bd5c27e2cb5e5p+0, 0x1.bd82bff554b1bp+0, 0x1.bda95b600e20bp+0, 0x1.bdcffa2341dd7p+0,
+    0x1.bdf69c3f3a207p+0, 0x1.be1d41b44128ap+0, 0x1.be43ea82a13b5p+0, 0x1.be6a96aaa4a46p+0,
+    0x1.be91462c95b60p+0, 0x1.beb7f908bec8ep+0, 0x1.bedeaf3f6a3c2p+0, 0x1.bf0568d0e2756p+0,
+    0x1.bf2c25bd71e09p+0, 0x1.bf52e60562f02p+0, 0x1.bf79a9a9001d2p+0, 0x1.bfa070a893e6cp+0,
+    0x1.bfc73b0468d30p+0, 0x1.bfee08bcc96e0p+0, 0x1.c014d9d2004aap+0, 0x1.c03bae4458020p+0,
+    0x1.c06286141b33dp+0, 0x1.c089614194863p+0, 0x1.c0b03fcd0ea5cp+0, 0x1.c0d721b6d445ap+0,
+    0x1.c0fe06ff301f4p+0, 0x1.c124efa66cf2cp+0, 0x1.c14bdbacd586ap+0, 0x1.c172cb12b4a7dp+0,
+    0x1.c199bdd85529cp+0, 0x1.c1c0b3fe01e67p+0, 0x1.c1e7ad8405be6p+0, 0x1.c20eaa6aab985p+0,
+    0x1.c235aab23e61ep+0, 0x1.c25cae5b090edp+0, 0x1.c283b56556999p+0, 0x1.c2aabfd172031p+0,
+    0x1.c2d1cd9fa652cp+0, 0x1.c2f8ded03e967p+0, 0x1.c31ff36385e29p+0, 0x1.c3470b59c7521p+0,
+    0x1.c36e26b34e065p+0, 0x1.c395457065275p+0, 0x1.c3bc679157e38p+0, 0x1.c3e38d16716fcp+0,
+    0x1.c40ab5fffd07ap+0, 0x1.c431e24e45ed2p+0, 0x1.c45912019768cp+0, 0x1.c480451a3cc98p+0,
+    0x1.c4a77b9881650p+0, 0x1.c4ceb57cb0975p+0, 0x1.c4f5f2c715c31p+0, 0x1.c51d3377fc517p+0,
+    0x1.c544778fafb22p+0, 0x1.c56bbf0e7b5b6p+0, 0x1.c59309f4aac9fp+0, 0x1.c5ba584289812p+0,
+    0x1.c5e1a9f8630adp+0, 0x1.c608ff1682f76p+0, 0x1.c630579d34dddp+0, 0x1.c657b38cc45b9p+0,
+    0x1.c67f12e57d14bp+0, 0x1.c6a675a7aab3ep+0, 0x1.c6cddbd398ea4p+0, 0x1.c6f54569936f8p+0,
+    0x1.c71cb269e601fp+0, 0x1.c74422d4dc667p+0, 0x1.c76b96aac2686p+0, 0x1.c7930debe3d9cp+0,
+    0x1.c7ba88988c933p+0, 0x1.c7e206b10873bp+0, 0x1.c8098835a3611p+0, 0x1.c8310d26a9479p+0,
+    0x1.c8589584661a1p+0, 0x1.c880214f25d1fp+0, 0x1.c8a7b087346f4p+0, 0x1.c8cf432cddf8bp+0,
+    0x1.c8f6d9406e7b5p+0, 0x1.c91e72c2320b0p+0, 0x1.c9460fb274c22p+0, 0x1.c96db01182c1bp+0,
+    0x1.c99553dfa8313p+0, 0x1.c9bcfb1d313eep+0, 0x1.c9e4a5ca6a1f8p+0, 0x1.ca0c53e79f0e7p+0,
+    0x1.ca3405751c4dbp+0, 0x1.ca5bba732e25dp+0, 0x1.ca8372e220e61p+0, 0x1.caab2ec240e43p+0,
+    0x1.cad2ee13da7cbp+0, 0x1.cafab0d73a12ap+0, 0x1.cb22770cac0f9p+0, 0x1.cb4a40b47ce3fp+0,
+    0x1.cb720dcef9069p+0, 0x1.cb99de5c6cf50p+0, 0x1.cbc1b25d25337p+0, 0x1.cbe989d16e4cbp+0,
+    0x1.cc1164b994d23p+0, 0x1.cc394315e55bfp+0, 0x1.cc6124e6ac88bp+0, 0x1.cc890a2c36fddp+0,
+    0x1.ccb0f2e6d1675p+0, 0x1.ccd8df16c877cp+0, 0x1.cd00cebc68e87p+0, 0x1.cd28c1d7ff795p+0,
+    0x1.cd50b869d8f0fp+0, 0x1.cd78b272421c9p+0, 0x1.cda0aff187d02p+0, 0x1.cdc8b0e7f6e61p+0,
+    0x1.cdf0b555dc3fap+0, 0x1.ce18bd3b84c4bp+0, 0x1.ce40c8993d63dp+0, 0x1.ce68d76f53122p+0,
+    0x1.ce90e9be12cb9p+0, 0x1.ceb8ff85c992ap+0, 0x1.cee118c6c4709p+0, 0x1.cf09358150754p+0,
+    0x1.cf3155b5bab74p+0, 0x1.cf5979645053cp+0, 0x1.cf81a08d5e6ecp+0, 0x1.cfa9cb313232ep+0,
+    0x1.cfd1f95018d17p+0, 0x1.cffa2aea5f825p+0, 0x1.d022600053845p+0, 0x1.d04a9892421ccp+0,
+    0x1.d072d4a07897cp+0, 0x1.d09b142b44480p+0, 0x1.d0c35732f2870p+0, 0x1.d0eb9db7d0b4fp+0,
+    0x1.d113e7ba2c38cp+0, 0x1.d13c353a527ffp+0, 0x1.d164863890feep+0, 0x1.d18cdab535307p+0,
+    0x1.d1b532b08c968p+0, 0x1.d1dd8e2ae4b97p+0, 0x1.d205ed248b287p+0, 0x1.d22e4f9dcd795p+0,
+    0x1.d256b596f948cp+0, 0x1.d27f1f105c3a0p+0, 0x1.d2a78c0a43f72p+0, 0x1.d2cffc84fe310p+0,
+    0x1.d2f87080d89f2p+0, 0x1.d320e7fe20ffap+0, 0x1.d34962fd2517ap+0, 0x1.d371e17e32b2ep+0,
+    0x1.d39a638197a3cp+0, 0x1.d3c2e907a1c38p+0, 0x1.d3eb72109ef21p+0, 0x1.d413fe9cdd164p+0,
+    0x1.d43c8eacaa1d6p+0, 0x1.d465224053fbdp+0, 0x1.d48db95828ac7p+0, 0x1.d4b653f47630fp+0,
+    0x1.d4def2158a91fp+0, 0x1.d50793bbb3de9p+0, 0x1.d53038e7402cep+0, 0x1.d558e1987d99ap+0,
+    0x1.d5818dcfba487p+0, 0x1.d5aa3d8d44639p+0, 0x1.d5d2f0d16a1c3p+0, 0x1.d5fba79c79aa1p+0,
+    0x1.d62461eec14bep+0, 0x1.d64d1fc88f472p+0, 0x1.d675e12a31e7fp+0, 0x1.d69ea613f7816p+0,
+    0x1.d6c76e862e6d3p+0, 0x1.d6f03a81250bfp+0, 0x1.d7190a0529c51p+0, 0x1.d741dd128b06ap+0,
+    0x1.d76ab3a99745bp+0, 0x1.d7938dca9cfdfp+0, 0x1.d7bc6b75eab1fp+0, 0x1.d7e54cabceeb1p+0,
+    0x1.d80e316c98398p+0, 0x1.d83719b895343p+0, 0x1.d86005901478fp+0, 0x1.d888f4f364ac5p+0,
+    0x1.d8b1e7e2d479dp+0, 0x1.d8dade5eb2939p+0, 0x1.d903d8674db2bp+0, 0x1.d92cd5fcf4971p+0,
+    0x1.d955d71ff6075p+0, 0x1.d97edbd0a0d11p+0, 0x1.d9a7e40f43c89p+0, 0x1.d9d0efdc2dc92p+0,
+    0x1.d9f9ff37adb4ap+0, 0x1.da23122212740p+0, 0x1.da4c289baaf6ep+0, 0x1.da7542a4c633ep+0,
+    0x1.da9e603db3285p+0, 0x1.dac78166c0d87p+0, 0x1.daf0a6203e4f5p+0, 0x1.db19ce6a7a9eep+0,
+    0x1.db42fa45c4dfdp+0, 0x1.db6c29b26c31dp+0, 0x1.db955cb0bfbb6p+0, 0x1.dbbe93410ea9dp+0,
+    0x1.dbe7cd63a8315p+0, 0x1.dc110b18db8cfp+0, 0x1.dc3a4c60f7feap+0, 0x1.dc63913c4ccf3p+0,
+    0x1.dc8cd9ab294e4p+0, 0x1.dcb625addcd27p+0, 0x1.dcdf7544b6b92p+0, 0x1.dd08c87006669p+0,
+    0x1.dd321f301b460p+0, 0x1.dd5b798544c98p+0, 0x1.dd84d76fd269ep+0, 0x1.ddae38f013a72p+0,
+    0x1.ddd79e065807dp+0, 0x1.de0106b2ef19bp+0, 0x1.de2a72f628712p+0, 0x1.de53e2d053a9ap+0,
+    0x1.de7d5641c0658p+0, 0x1.dea6cd4abe4ddp+0, 0x1.ded047eb9d12dp+0, 0x1.def9c624ac6b6p+0,
+    0x1.df2347f63c159p+0, 0x1.df4ccd609bd61p+0, 0x1.df7656641b78cp+0, 0x1.df9fe3010ad03p+0,
+    0x1.dfc97337b9b5fp+0, 0x1.dff30708780a8p+0, 0x1.e01c9e7395b56p+0, 0x1.e046397962a4cp+0,
+    0x1.e06fd81a2ece1p+0, 0x1.e0997a564a2d6p+0, 0x1.e0c3202e04c5dp+0, 0x1.e0ecc9a1aea18p+0,
+    0x1.e11676b197d17p+0, 0x1.e140275e106d8p+0, 0x1.e169dba768949p+0, 0x1.e193938df06c8p+0,
+    0x1.e1bd4f11f8220p+0, 0x1.e1e70e33cfe8dp+0, 0x1.e210d0f3c7fbap+0, 0x1.e23a9752309c0p+0,
+    0x1.e264614f5a129p+0, 0x1.e28e2eeb94aecp+0, 0x1.e2b8002730c71p+0, 0x1.e2e1d5027eb91p+0,
+    0x1.e30bad7dcee90p+0, 0x1.e335899971c26p+0, 0x1.e35f6955b7b78p+0, 0x1.e3894cb2f141ap+0,
+    0x1.e3b333b16ee12p+0, 0x1.e3dd1e51811d3p+0, 0x1.e4070c9378842p+0, 0x1.e430fe77a5ab3p+0,
+    0x1.e45af3fe592e8p+0, 0x1.e484ed27e3b15p+0, 0x1.e4aee9f495ddcp+0, 0x1.e4d8ea64c0651p+0,
+    0x1.e502ee78b3ff6p+0, 0x1.e52cf630c16bep+0, 0x1.e557018d3970bp+0, 0x1.e581108e6cdafp+0,
+    0x1.e5ab2334ac7eep+0, 0x1.e5d539804937ap+0, 0x1.e5ff537193e75p+0, 0x1.e6297108dd773p+0,
+    0x1.e653924676d76p+0, 0x1.e67db72ab0ff2p+0, 0x1.e6a7dfb5dcecap+0, 0x1.e6d20be84ba53p+0,
+    0x1.e6fc3bc24e350p+0, 0x1.e7266f4435af7p+0, 0x1.e750a66e532ebp+0, 0x1.e77ae140f7d42p+0,
+    0x1.e7a51fbc74c83p+0, 0x1.e7cf61e11b3a4p+0, 0x1.e7f9a7af3c60bp+0, 0x1.e823f12729791p+0,
+    0x1.e84e3e4933c7ep+0, 0x1.e8788f15ac98ap+0, 0x1.e8a2e38ce53dfp+0, 0x1.e8cd3baf2f118p+0,
+    0x1.e8f7977cdb740p+0, 0x1.e921f6f63bcd2p+0, 0x1.e94c5a1ba18bdp+0, 0x1.e976c0ed5e25dp+0,
+    0x1.e9a12b6bc3181p+0, 0x1.e9cb999721e6ap+0, 0x1.e9f60b6fcc1c7p+0, 0x1.ea2080f6134bcp+0,
+    0x1.ea4afa2a490dap+0, 0x1.ea75770cbf025p+0, 0x1.ea9ff79dc6d14p+0, 0x1.eaca7bddb228cp+0,
+    0x1.eaf503ccd2be5p+0, 0x1.eb1f8f6b7a4e9p+0, 0x1.eb4a1eb9fa9d1p+0, 0x1.eb74b1b8a5749p+0,
+    0x1.eb9f4867cca6ep+0, 0x1.ebc9e2c7c20d0p+0, 0x1.ebf480d8d786dp+0, 0x1.ec1f229b5efb8p+0,
+    0x1.ec49c80faa594p+0, 0x1.ec7471360b955p+0, 0x1.ec9f1e0ed4ac2p+0, 0x1.ecc9ce9a57a12p+0,
+    0x1.ecf482d8e67f1p+0, 0x1.ed1f3acad3578p+0, 0x1.ed49f67070435p+0, 0x1.ed74b5ca0f628p+0,
+    0x1.ed9f78d802dc2p+0, 0x1.edca3f9a9cde5p+0, 0x1.edf50a122f9e6p+0, 0x1.ee1fd83f0d58cp+0,
+    0x1.ee4aaa2188510p+0, 0x1.ee757fb9f2d1dp+0, 0x1.eea059089f2d0p+0, 0x1.eecb360ddfbb8p+0,
+    0x1.eef616ca06dd6p+0, 0x1.ef20fb3d66f9ep+0, 0x1.ef4be368527f6p+0, 0x1.ef76cf4b1be36p+0,
+    0x1.efa1bee615a27p+0, 0x1.efccb23992408p+0, 0x1.eff7a945e4487p+0, 0x1.f022a40b5e4c6p+0,
+    0x1.f04da28a52e59p+0, 0x1.f078a4c314b47p+0, 0x1.f0a3aab5f6609p+0, 0x1.f0ceb4634a98ap+0,
+    0x1.f0f9c1cb6412ap+0, 0x1.f124d2ee958b9p+0, 0x1.f14fe7cd31c7bp+0, 0x1.f17b00678b927p+0,
+    0x1.f1a61cbdf5be7p+0, 0x1.f1d13cd0c3256p+0, 0x1.f1fc60a046a84p+0, 0x1.f227882cd32f3p+0,
+    0x1.f252b376bba97p+0, 0x1.f27de27e530dap+0, 0x1.f2a91543ec595p+0, 0x1.f2d44bc7da917p+0,
+    0x1.f2ff860a70c22p+0, 0x1.f32ac40c01fe8p+0, 0x1.f35605cce1613p+0, 0x1.f3814b4d620bdp+0,
+    0x1.f3ac948dd7274p+0, 0x1.f3d7e18e93e39p+0, 0x1.f403324feb781p+0, 0x1.f42e86d231233p+0,
+    0x1.f459df15b82acp+0, 0x1.f4853b1ad3dbbp+0, 0x1.f4b09ae1d78a1p+0, 0x1.f4dbfe6b16915p+0,
+    0x1.f50765b6e4540p+0, 0x1.f532d0c5943c0p+0, 0x1.f55e3f9779ba5p+0, 0x1.f589b22ce8474p+0,
+    0x1.f5b5288633625p+0, 0x1.f5e0a2a3ae925p+0, 0x1.f60c2085ad652p+0, 0x1.f637a22c83701p+0,
+    0x1.f6632798844f8p+0, 0x1.f68eb0ca03a75p+0, 0x1.f6ba3dc155226p+0, 0x1.f6e5ce7ecc72fp+0,
+    0x1.f7116302bd526p+0, 0x1.f73cfb4d7b819p+0, 0x1.f768975f5ac86p+0, 0x1.f7943738aef61p+0,
+    0x1.f7bfdad9cbe14p+0, 0x1.f7eb824305679p+0, 0x1.f8172d74af6e1p+0, 0x1.f842dc6f1de12p+0,
+    0x1.f86e8f32a4b45p+0, 0x1.f89a45bf97e28p+0, 0x1.f8c600164b6dcp+0, 0x1.f8f1be37135f9p+0,
+    0x1.f91d802243c89p+0, 0x1.f94945d830c0cp+0, 0x1.f9750f592e677p+0, 0x1.f9a0dca590e33p+0,
+    0x1.f9ccadbdac61dp+0, 0x1.f9f882a1d5187p+0, 0x1.fa245b525f439p+0, 0x1.fa5037cf9f26ep+0,
+    0x1.fa7c1819e90d8p+0, 0x1.faa7fc319149cp+0, 0x1.fad3e416ec354p+0, 0x1.faffcfca4e310p+0,
+    0x1.fb2bbf4c0ba54p+0, 0x1.fb57b29c7901ap+0, 0x1.fb83a9bbeabd1p+0, 0x1.fbafa4aab555cp+0,
+    0x1.fbdba3692d514p+0, 0x1.fc07a5f7a73c7p+0, 0x1.fc33ac5677ab8p+0, 0x1.fc5fb685f33a0p+0,
+    0x1.fc8bc4866e8adp+0, 0x1.fcb7d6583e482p+0, 0x1.fce3ebfbb7237p+0, 0x1.fd1005712dd5bp+0,
+    0x1.fd3c22b8f71f1p+0, 0x1.fd6843d367c72p+0, 0x1.fd9468c0d49ccp+0, 0x1.fdc0918192765p+0,
+    0x1.fdecbe15f6314p+0, 0x1.fe18ee7e54b2bp+0, 0x1.fe4522bb02e6ep+0, 0x1.fe715acc55c18p+0,
+    0x1.fe9d96b2a23d9p+0, 0x1.fec9d66e3d5d9p+0, 0x1.fef619ff7c2b3p+0, 0x1.ff226166b3b7ap+0,
+    0x1.ff4eaca4391b6p+0, 0x1.ff7afbb861765p+0, 0x1.ffa74ea381efcp+0, 0x1.ffd3a565efb65p+0,
 };
-constexpr double INV_LN2_N = 0x1.71547652b82fep+8;   // 256 / ln 2
-constexpr double LN2_N_HI = 0x1.62e42fefa39efp-9;    // ln 2 / 256, nearest double
-constexpr double LN2_N_LO = 0x1.abc9e3b39803fp-64;   // ln 2 / 256 - LN2_N_HI
+constexpr double INV_LN2_N = 0x1.71547652b82fep+11;   // 2048 / ln 2
+constexpr double LN2_N_HI = 0x1.62e42fefa39efp-12;    // ln 2 / 2048, nearest double
+constexpr double LN2_N_LO = 0x1.abc9e3b39803fp-67;   // ln 2 / 2048 - LN2_N_HI
 
 __device__ __forceinline__ double exp_neg(double x) {
     const double shifter = 6755399441055744.0;  // 1.5 * 2^52
@@ -172,14 +621,13 @@ __device__ __forceinline__ double exp_neg(double x) {
     const int ni = __double2loint(d);  // n as an integer (low word of d)
     double r = fma(-n, LN2_N_HI, x);
     r = fma(-n, LN2_N_LO, r);
-    double p = fma(r, inv_fact(4), inv_fact(3));
-    p = fma(p, r, inv_fact(2));
+    double p = fma(r, inv_fact(3), inv_fact(2));
     p = fma(p, r, 1.0);
     const double em1 = p * r;  // e^r - 1
-    const int j = ni & 255;
-    const int m = (ni - j) / 256;
+    const int j = ni & 2047;
+    const int m = (ni - j) / 2048;
     const double t = __ldg(&EXP2_TABLE[j]);
-    const double y = fma(t, em1, t);  // 2^(j/256) e^r, in [0.99, 2)
+    const double y = fma(t, em1, t);  // 2^(j/2048) e^r, in [0.99, 2)
     const double out = __longlong_as_double(__double_as_longlong(y) + ((long long)m << 52));
     return x < -708.0 ? 0.0 : out;
 }
