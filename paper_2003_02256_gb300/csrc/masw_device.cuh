@@ -49,7 +49,29 @@ constexpr double SERIES_U = 1.0;
 
 __host__ __device__ constexpr double inv_fact(int n) { return n <= 1 ? 1.0 : inv_fact(n - 1) / (double)n; }
 
-__device__ __forceinline__ int sgn(double x) { return (x > 0.0) - (x < 0.0); }
+// Sign tests and magnitude comparisons of doubles on the integer pipe: an
+// FP64 compare takes a slot of the FP64 pipe, the scarce one, while the bit
+// patterns of non-NaN doubles order like their magnitudes (sign bit apart).
+// Each helper gives the FP64 comparison's result for every input, NaN
+// included (a comparison with NaN is false).
+constexpr long long MAG_MASK = 0x7fffffffffffffffLL;
+constexpr long long INF_BITS = 0x7ff0000000000000LL;
+// x < 0 (false for -0.0 and NaN)
+__device__ __forceinline__ bool lt0(double x) {
+    const long long b = __double_as_longlong(x);
+    const long long m = b & MAG_MASK;
+    return b < 0 && m != 0 && m <= INF_BITS;
+}
+// x > 0 (false for +0.0 and NaN)
+__device__ __forceinline__ bool gt0(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= INF_BITS;
+}
+// |x| < |y| for a finite y (false when x is NaN)
+__device__ __forceinline__ bool abs_lt(double x, double y) {
+    return (__double_as_longlong(x) & MAG_MASK) < (__double_as_longlong(y) & MAG_MASK);
+}
+__device__ __forceinline__ int sgn(double x) { return (int)gt0(x) - (int)lt0(x); }
 
 // 2^-(exponent of x) for a normal x; returns false for 0, subnormal, inf, NaN
 // or a value so large that the scale would be subnormal.
@@ -629,7 +651,7 @@ __device__ __forceinline__ double exp_neg(double x) {
     const double t = __ldg(&EXP2_TABLE[j]);
     const double y = fma(t, em1, t);  // 2^(j/2048) e^r, in [0.99, 2)
     const double out = __longlong_as_double(__double_as_longlong(y) + ((long long)m << 52));
-    return x < -708.0 ? 0.0 : out;
+    return (lt0(x) && abs_lt(-708.0, x)) ? 0.0 : out;  // x < -708
 }
 
 // ----------------------------------------------------------- plain doubles
@@ -642,7 +664,7 @@ struct Wave { double E, C, Sd, Sm; };
 __device__ __forceinline__ Wave wave_fns(double kh, double w2) {
     double u = kh * kh * w2;
     Wave o;
-    if (fabs(u) < SERIES_U) {
+    if (abs_lt(u, SERIES_U)) {
         double pc = inv_fact(18);
         pc = fma(pc, u, inv_fact(16));
         pc = fma(pc, u, inv_fact(14));
@@ -667,7 +689,7 @@ __device__ __forceinline__ Wave wave_fns(double kh, double w2) {
         o.C = pc;
         o.Sd = khps;
         o.Sm = w2 * khps;
-    } else if (w2 > 0.0) {
+    } else if (gt0(w2)) {
         double rw = rsqrt(w2);
         double w = w2 * rw;
         double E = exp_neg(-kh * w);
@@ -878,7 +900,7 @@ __device__ inline int det_inertia(const double* __restrict__ lay, int N, double 
         double f = st.w * n.Dh;
         bool ok;
         double det = schur_layer(st, n, &ok, sv);
-        cnt += det < 0.0 ? 1 : (det > 0.0 ? (((sv[0] < 0.0) != (f < 0.0)) ? 2 : 0) : 1);
+        cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(sv[0]) != lt0(f)) ? 2 : 0) : 1);
         if (!ok) return -1;
     }
     HalfNum hn = halfspace_numerators(lay + N * LAYER_STRIDE, c2);
@@ -887,7 +909,7 @@ __device__ inline int det_inertia(const double* __restrict__ lay, int N, double 
     double s01 = fma(hn.den, st.p01, st.w * hn.m01);
     double s11 = fma(hn.den, st.p11, st.w * hn.m11);
     double det = fma(s00, s11, -s01 * s01);
-    cnt += det < 0.0 ? 1 : (det > 0.0 ? (((s00 < 0.0) != (f < 0.0)) ? 2 : 0) : 1);
+    cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(s00) != lt0(f)) ? 2 : 0) : 1);
     return cnt;
 }
 
@@ -906,7 +928,7 @@ __device__ inline int det_sign_count(const double* __restrict__ lay, int N, doub
         bool ok;
         double det = schur_layer(st, n, &ok, sv);
         sg *= sgn(det);
-        cnt += det < 0.0 ? 1 : (det > 0.0 ? (((sv[0] < 0.0) != (f < 0.0)) ? 2 : 0) : 1);
+        cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(sv[0]) != lt0(f)) ? 2 : 0) : 1);
         if (!ok) {
             *count = -1;
             return 0;
@@ -918,7 +940,7 @@ __device__ inline int det_sign_count(const double* __restrict__ lay, int N, doub
     double s01 = fma(hn.den, st.p01, st.w * hn.m01);
     double s11 = fma(hn.den, st.p11, st.w * hn.m11);
     double det = fma(s00, s11, -s01 * s01);
-    cnt += det < 0.0 ? 1 : (det > 0.0 ? (((s00 < 0.0) != (f < 0.0)) ? 2 : 0) : 1);
+    cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(s00) != lt0(f)) ? 2 : 0) : 1);
     *count = cnt;
     return sg * sgn(det);
 }
@@ -954,7 +976,7 @@ __device__ inline int clamped_modes(const double* __restrict__ L, double k, doub
         const double D = fma(2.0, fma(R.E, S.E, -R.C * S.C), fma(R.Sd, S.Sd, R.Sm * S.Sm));
         const double an = fma(R.C, S.Sd, -S.C * R.Sm);
         const double dn = fma(S.C, R.Sd, -R.C * S.Sm);
-        J = 2 * J + (int)((an < 0.0) != (D < 0.0)) + (int)((dn < 0.0) != (D < 0.0));
+        J = 2 * J + (int)(lt0(an) != lt0(D)) + (int)(lt0(dn) != lt0(D));
     }
     return J;
 }
