@@ -661,8 +661,9 @@ struct Wave { double E, C, Sd, Sm; };
 // Scaled even functions of w = sqrt(w2) at kh: (E, C, Sd, Sm) equal
 // e^-x * (1, cosh x, sinh(x)/w, w sinh x) with x = kh w for real w and large
 // x, and (1, cosh, sinh/w, w sinh) otherwise (imaginary w gives cos/sin).
-__device__ __forceinline__ Wave wave_fns(double kh, double w2) {
-    double u = kh * kh * w2;
+// kh2 = kh * kh, formed once for the element's two waves.
+__device__ __forceinline__ Wave wave_fns(double kh, double kh2, double w2) {
+    double u = kh2 * w2;
     Wave o;
     if (abs_lt(u, SERIES_U)) {
         double pc = inv_fact(18);
@@ -724,8 +725,9 @@ __device__ __forceinline__ LayerNum layer_numerators(const double* __restrict__ 
     double q = c2 * ib2;
     double r2 = fma(-c2, ia2, 1.0);
     double s2 = 1.0 - q;
-    Wave R = wave_fns(kh, r2);
-    Wave S = wave_fns(kh, s2);
+    const double kh2 = kh * kh;
+    Wave R = wave_fns(kh, kh2, r2);
+    Wave S = wave_fns(kh, kh2, s2);
     // E_r E_s - C_r C_s and Sd_r Sd_s are shared by D and b
     double u = fma(R.E, S.E, -R.C * S.C);
     double SdSd = R.Sd * S.Sd;
@@ -965,8 +967,9 @@ __device__ inline int clamped_modes(const double* __restrict__ L, double k, doub
     // levels: 2^lv > x >= 2^(lv-1)
     const int lv = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1022;
     const double khf = scale_pow2(k * L[L_H], -lv);
-    Wave R = wave_fns(khf, 1.0 - c2 * L[L_IA2]);
-    Wave S = wave_fns(khf, 1.0 - q);
+    const double khf2 = khf * khf;
+    Wave R = wave_fns(khf, khf2, 1.0 - c2 * L[L_IA2]);
+    Wave S = wave_fns(khf, khf2, 1.0 - q);
     int J = 0;
     for (int j = lv; j >= 1; --j) {
         if (j < lv) {
