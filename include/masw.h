@@ -123,10 +123,16 @@ int masw_model_batch_create(const masw_models_desc* models, const masw_grid* gri
 int masw_model_batch_destroy(masw_batch* batch);
 
 /* Replace the layer parameters of an existing batch (same n_layers and
- * n_lambda; wavelengths unchanged). Pointers live in mem_space. The checks
- * of masw_model_batch_create, the layer records and the scan limits run on
- * the GPU, queued after the work already on the batch stream; the call
- * synchronises the stream once. MASW_EINVAL leaves the batch unchanged.
+ * n_lambda; wavelengths unchanged). Pointers live in mem_space. The layer
+ * records and the scan limits are rebuilt on the GPU, queued after the work
+ * already on the batch stream. MASW_HOST: the arrays are checked on the host
+ * with the rules of masw_model_batch_create (MASW_EINVAL before anything is
+ * queued) and the call returns without synchronising; the copies read the
+ * arrays when the stream reaches them, so pinned (page-locked) arrays must
+ * stay unchanged until the batch stream next synchronises (any call with host
+ * outputs does), while pageable ones are staged before the call returns.
+ * MASW_DEVICE: the checks run on the GPU and the call synchronises the stream
+ * once to return their result. MASW_EINVAL leaves the batch unchanged.
  * Used by inversion loops and samplers; a captured scan graph stays valid. */
 int masw_model_batch_update(masw_batch* batch, const double* h, const double* alpha,
                             const double* beta, const double* rho, int32_t mem_space);

@@ -204,11 +204,10 @@ static int32_t scan_limit(const masw_grid& g, double beta_hs) {
 
 static bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
-static int validate_layers(const std::vector<int32_t>& nl, const std::vector<double>& h,
-                           const std::vector<double>& a, const std::vector<double>& b,
-                           const std::vector<double>& r) {
+static int validate_layers(const int32_t* nl, size_t n_models, const double* h, const double* a,
+                           const double* b, const double* r) {
     size_t ih = 0, il = 0;
-    for (size_t m = 0; m < nl.size(); ++m) {
+    for (size_t m = 0; m < n_models; ++m) {
         for (int i = 0; i < nl[m]; ++i)
             if (!finite_pos(h[ih++])) return MASW_EINVAL;
         for (int i = 0; i <= nl[m]; ++i, ++il) {
@@ -218,6 +217,12 @@ static int validate_layers(const std::vector<int32_t>& nl, const std::vector<dou
         }
     }
     return MASW_OK;
+}
+
+static int validate_layers(const std::vector<int32_t>& nl, const std::vector<double>& h,
+                           const std::vector<double>& a, const std::vector<double>& b,
+                           const std::vector<double>& r) {
+    return validate_layers(nl.data(), nl.size(), h.data(), a.data(), b.data(), r.data());
 }
 
 static void build_records(masw_batch* B, const std::vector<double>& h, const std::vector<double>& a,
@@ -571,6 +576,11 @@ int masw_model_batch_update(masw_batch* B, const double* h, const double* alpha,
     if (!B->d_upd_err && dev_alloc(&B->d_upd_err, 1)) return MASW_ENOMEM;
     const double *dh = h, *da = alpha, *db = beta, *dr = rho;
     if (mem_space == MASW_HOST) {
+        // host arrays: checked here with the creation rules, so the update is
+        // queued without a round trip (the device check below then finds
+        // nothing); the copies read the arrays when the stream reaches them
+        if (validate_layers(B->n_layers.data(), B->n_layers.size(), h, alpha, beta, rho))
+            return MASW_EINVAL;
         double* st = B->d_upd;
         dh = st;
         da = st + nh;
@@ -589,6 +599,8 @@ int masw_model_batch_update(masw_batch* B, const double* h, const double* alpha,
     CK(cudaMemsetAsync(B->d_upd_err, 0, sizeof(int32_t), B->stream));
     CK(launch_model_update(B->dev(false), dh, da, db, dr, B->d_layers, B->d_layers32, B->d_nlim,
                            B->d_upd_err, B->stream));
+    if (mem_space == MASW_HOST) return MASW_OK;
+    // device arrays: one synchronisation returns the device check's flag
     int32_t err = 0;
     CK(cudaMemcpyAsync(&err, B->d_upd_err, sizeof(int32_t), cudaMemcpyDeviceToHost, B->stream));
     CK(cudaMemcpyAsync(B->nlim.data(), B->d_nlim, B->nlim.size() * sizeof(int32_t),

@@ -317,6 +317,15 @@ def test_update_validates_first_and_matches_a_fresh_batch(masw):
             assert ei.value.code == masw.EINVAL
             after = b.dispersion()
             assert np.array_equal(after[1], before[1]) and np.array_equal(after[2], before[2])
+        for kw in bad:  # the same with device pointers (checked on the device)
+            dbad = [torch.as_tensor(np.ascontiguousarray(x), device="cuda")
+                    for x in (kw.get("h", m1.h), kw.get("alpha", m1.alpha), m1.beta,
+                              kw.get("rho", m1.rho))]
+            with pytest.raises(masw.MaswError) as ei:
+                b.update(*dbad)
+            assert ei.value.code == masw.EINVAL
+            after = b.dispersion()
+            assert np.array_equal(after[1], before[1]) and np.array_equal(after[2], before[2])
         b.update(m2.h, m2.alpha, m2.beta, m2.rho)
         s_host, l_host = b.det_eval(items, cs)
         r_host = b.dispersion()
