@@ -5,9 +5,10 @@
 // FP64 recurrence of masw_device.cuh costs ~64x the same arithmetic in FP32.
 // The screen evaluates the same element stiffness and the same homogeneous
 // Schur recurrence in FP32 to LOCATE the first sign change n32; the result
-// reported by the library is always decided by the FP64 recurrence
-// (masw_device.cuh::det_sign) at V[0], V[n32-1] and V[n32], with an FP64
-// window re-scan and finally a full FP64 scan whenever they disagree.
+// reported by the library is always decided in FP64: the Wittrick-Williams
+// mode count of the FP64 recurrence (masw_device.cuh::mode_count_T) at V[0],
+// V[n32-1] and V[n32], and when it does not confirm, the FP64 search on that
+// count (masw_modes.cuh) or finally the FP64 scan.
 //
 // FP32-specific care: stiffnesses are divided by the half-space shear
 // modulus (a positive common factor, so no sign changes) to keep the

@@ -30,11 +30,13 @@
 // admission, a lane pair runs the counting search (the FP32 negative-
 // eigenvalue count split below the pole-free bound) and its FP64 certificate
 // (count 0 at V[n-1], odd at V[n]; count_certify_pair), so most requests
-// finish in one tick. Items whose change lies above the bound
-// continue with paired FP32 chunks from the bound, up to `chunks_per_tick`
-// per tick, and get the FP64 sign check at V[0], V[n-1], V[n]; when a check
-// does not confirm, the item continues with FP64 chunks, one per tick, from a
-// window below the located index (or from V[0]).
+// finish in one tick; an uncertified item takes the FP64 search on the
+// Wittrick-Williams mode count from V[0] in the same kernel (masw_modes.cuh).
+// Items whose change lies above the bound continue with paired FP32 chunks
+// from the bound, up to `chunks_per_tick` per tick, and get the batch path's
+// three-point FP64 check on the mode count at V[0], V[n-1], V[n]; when it does
+// not confirm, the same mode-count search. Items whose FP64 counts fail
+// continue with FP64 chunks, one per tick, from V[0].
 // Results are written by the kernel into mapped pinned host memory, so
 // retiring a request is a host memcpy.
 #include <algorithm>
