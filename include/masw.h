@@ -239,6 +239,16 @@ int masw_last_scan_phases(const masw_batch* batch, float* ms);
 #define MASW_SCREEN_COUNTED (1 << 30)
 int masw_last_scan_screen(masw_batch* batch, int32_t* n32);
 
+/* Test routing of the two-precision and counting plans, so that tests can
+ * run every item through the paths that ordinary inputs rarely reach; the
+ * results must not change. 0: normal. 1: the counting search's items all go to
+ * the linear FP32 scan from V[0] (plan precision 2). 2: also, every item fails
+ * its three-point FP64 check and takes the FP64 mode-count search. 3: also,
+ * every searched item takes the FP64 scan from V[0], and every higher-mode
+ * item the FP64 scan at every grid point. Synchronises the batch stream and
+ * rebuilds the scan graph. MASW_EINVAL outside 0..3. */
+int masw_set_route(masw_batch* batch, int32_t route);
+
 /* Items of the most recent two-precision scan (plan precision 1 or 2) whose FP32
  * result failed its FP64 check (the counting certificate, or the three-point
  * check on the Wittrick-Williams mode count) and whose first change was then

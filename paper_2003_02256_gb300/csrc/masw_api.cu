@@ -89,6 +89,7 @@ struct masw_batch {
     double* d_lk_ct = nullptr;
     int32_t* d_lk_idx = nullptr;  // [n_items] idx, then [n_items] status, then counter
     masw_plan plan{};
+    int32_t route = 0;  // masw_set_route
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t phase_ev[2] = {nullptr, nullptr};
@@ -110,6 +111,7 @@ struct masw_batch {
         b.c0 = grid.c0;
         b.dc = grid.dc;
         b.n_c = grid.n_c;
+        b.route = route;
         return b;
     }
 };
@@ -988,6 +990,13 @@ int masw_set_plan(masw_batch* B, const masw_plan* plan) {
     if (!B || !plan || !plan_ok(*plan)) return MASW_EINVAL;
     CK(cudaStreamSynchronize(B->stream));
     B->plan = *plan;
+    return rebuild_graph(B);
+}
+
+int masw_set_route(masw_batch* B, int32_t route) {
+    if (!B || route < 0 || route > 3) return MASW_EINVAL;
+    CK(cudaStreamSynchronize(B->stream));
+    B->route = route;
     return rebuild_graph(B);
 }
 

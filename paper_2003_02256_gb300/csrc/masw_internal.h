@@ -21,6 +21,7 @@ struct DevBatch {
     int32_t n_items;
     double c0, dc;
     int32_t n_c;
+    int32_t route;  // test routing (masw_set_route): 0 normal, 1..3 force the slower paths
 };
 
 struct ScanOut {

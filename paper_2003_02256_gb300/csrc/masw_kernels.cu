@@ -335,8 +335,8 @@ __device__ __forceinline__ void verify_item(const DevBatch& b, const ScanOut& o,
     const int T0 = mode_count_T(lay, N, k, grid_c(b.c0, b.dc, 0), &sv);
     const int Ta = (n == 1) ? T0 : mode_count_T(lay, N, k, grid_c(b.c0, b.dc, n >= 1 ? n - 1 : nlim - 1), &sv);
     const int Tb = n >= 1 ? mode_count_T(lay, N, k, grid_c(b.c0, b.dc, n), &sv) : -1;
-    if (mode_count_verified(n, T0, Ta, Tb)) write_result(b, o, item, n >= 1 ? n : -1);
-    else search[atomicAdd(n_search, 1)] = item;
+    if (b.route < 2 && mode_count_verified(n, T0, Ta, Tb)) write_result(b, o, item, n >= 1 ? n : -1);
+    else search[atomicAdd(n_search, 1)] = item;  // (test routing 2, 3: every item)
 }
 
 __global__ void verify64_kernel(DevBatch b, ScanOut o, const int32_t* __restrict__ n32,
@@ -384,8 +384,10 @@ __global__ void __launch_bounds__(128) verify64_list_kernel(DevBatch b, ScanOut 
         const int Ta = __shfl_sync(quad, T, q0 + 1);
         const int Tb = __shfl_sync(quad, T, q0 + 2);
         if (sub != 0) continue;
-        if (mode_count_verified(n, T0, Ta, Tb)) write_result(b, o, item, n >= 1 ? n : -1);
-        else search[atomicAdd(n_search, 1)] = item;
+        if (b.route < 2 && mode_count_verified(n, T0, Ta, Tb))
+            write_result(b, o, item, n >= 1 ? n : -1);
+        else
+            search[atomicAdd(n_search, 1)] = item;  // (test routing 2, 3: every item)
     }
 }
 
@@ -498,7 +500,10 @@ __global__ void __launch_bounds__(128, 7) count_certify_kernel(DevBatch b, const
     const PairCount r = count_certify_pair(layers32 + (size_t)lo_rec * LAYER_STRIDE32, lay, N,
                                            b.k[item], b.c0, b.dc, nlim, half, pair);
     if (half) return;
-    if (r.cert >= 1) {
+    if (b.route >= 1) {  // test routing: every item through the linear FP32 scan from V[0]
+        n32[item] = 0;
+        fallback[atomicAdd(n_fallback, 1)] = item;
+    } else if (r.cert >= 1) {
         n32[item] = r.cert | SCREEN_COUNTED;
         write_result(b, o, item, r.cert);
     } else if (r.n >= 1) {
@@ -599,7 +604,7 @@ __global__ void __launch_bounds__(256) first_count64_kernel(DevBatch b, ScanOut 
             PT = hT;
         }
         if (gl == 0) {
-            if (bad) {
+            if (bad || b.route >= 3) {  // (test routing 3: every item to the FP64 scan)
                 n32[item] = 0;
                 unresolved[atomicAdd(n_unresolved, 1)] = item;
             } else {
@@ -848,7 +853,7 @@ __global__ void __launch_bounds__(128) changes_count64_kernel(DevBatch b, Change
             if (half == 0) write_change(b, o, e0 + found, n, d);
             ++found;
         }
-        bad = st.bad;
+        bad = st.bad || b.route >= 3;  // (test routing 3: every item to the linear scan)
         if (bad && half == 0) linear[atomicAdd(n_linear, 1)] = item;
     }
     if (half == 0 && !bad)

@@ -270,6 +270,7 @@ extern "C" int masw_dispersion_noalloc(const masw_models_desc* md, const masw_gr
     d.c0 = grid->c0;
     d.dc = grid->dc;
     d.n_c = grid->n_c;
+    d.route = 0;
     ScanPlan p;
     p.warps_per_block = 8;
     p.cpl = 1;

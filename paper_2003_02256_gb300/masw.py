@@ -77,6 +77,7 @@ def load():
         "masw_dispersion_changes": [p, i32, p, p, p, p, i32],
         "masw_dispersion_leaky": [p, p, p, p, i32],
         "masw_mode_count": [p, i32, p, p, p, p],
+        "masw_set_route": [p, i32],
         "masw_misfit": [p, p, i32, d, p],
         "masw_misfit_grad": [p, p, i32, d, p, p, p],
         "masw_roots": [p, p],
@@ -248,6 +249,11 @@ def mode_count(handle, item, c, s, j0):
     """Wittrick-Williams counts (s, J0) at arbitrary points (masw_mode_count)."""
     _check(load().masw_mode_count(ctypes.c_void_p(handle), int(len(item)), _ptr(item), _ptr(c),
                                   _ptr(s), _ptr(j0)), "masw_mode_count")
+
+
+def set_route(handle, route: int):
+    """Test routing through the slower paths (masw_set_route)."""
+    _check(load().masw_set_route(ctypes.c_void_p(handle), int(route)), "masw_set_route")
 
 
 def get_plan(handle) -> Plan:
@@ -439,6 +445,9 @@ class Batch:
         la = np.empty(item.size)
         det_eval(self.handle, item, c, sign, la)
         return sign, la
+
+    def set_route(self, route: int):
+        set_route(self.handle, route)
 
     def mode_count(self, item, c):
         """(s, J0) at the points: negative eigenvalues of K and clamped-layer modes."""

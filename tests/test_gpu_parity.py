@@ -494,3 +494,33 @@ def test_extreme_models_two_precision_equals_fp64_scan(masw, oracle_lib, seed):
                                                replace=False)
     o_ct, o_idx, o_st = oracle_items(oracle_lib, m, g, items)
     assert_index_parity(ref[1][items], ref[2][items], o_idx, o_st)
+
+
+@pytest.mark.parametrize("route", [1, 2, 3])
+def test_forced_routes_give_the_fp64_scan(masw, route):
+    """masw_set_route sends every item through the paths ordinary inputs
+    rarely reach: the linear FP32 scan from V[0] (1), the FP64 mode-count
+    search after a failed check (2), the FP64 scan from V[0] (3). Every plan
+    still reports the pure FP64 scan's indices, on uniform, ragged and
+    extreme models, and the higher modes match too."""
+    cases = [W.uniform_batch(n_models=32, n_lambda=40), W.ragged_batch(n_models=48),
+             W.extreme_batch(n_models=64, seed=W.SEED + 11)]
+    for m, g in cases:
+        with masw.Batch(m, g) as b:
+            b.set_plan(precision=0)
+            ref = b.dispersion()
+            ref_ch = b.changes(3)
+            b.set_route(route)
+            for p in (1, 2):
+                b.set_plan(precision=p)
+                got = b.dispersion()
+                assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2]), (route, p)
+            ch = b.changes(3)
+            assert all(np.array_equal(x, y) for x, y in zip(ch[1:], ref_ch[1:])), route
+            if route == 3:
+                assert b.last_changes_linear() == m.n_items - int(np.sum(ref[2] != 0))
+            b.set_route(0)
+    with masw.Batch(*W.uniform_batch(n_models=2, n_lambda=2)) as b:
+        for bad in (-1, 4):
+            with pytest.raises(masw.MaswError):
+                b.set_route(bad)
