@@ -407,6 +407,13 @@ int masw_server_poll(masw_server* server, int64_t request_id, double* ct, int32_
 
 int masw_server_get_stats(const masw_server* server, masw_server_stats* stats);
 
+/* Test routing of the server's scan, as masw_set_route: 1 every new item
+ * takes the linear FP32 screen from V[0]; 2 also fails every three-point FP64
+ * check (mode-count search); 3 also sends every searched item to the FP64
+ * scan from V[0], one chunk per tick. Applies from the next tick; results must
+ * not change. MASW_EINVAL outside 0..3. */
+int masw_server_set_route(masw_server* server, int32_t route);
+
 /* Replay a request trace natively: request i (concatenated host arrays as in
  * masw_models_desc) arrives arrival_s[i] seconds (non-decreasing) after the
  * call starts; the loop admits arrived requests while slots and bytes allow,

@@ -69,6 +69,7 @@ struct SlotView {
     int32_t* remaining;  // [slots] items still running
     int32_t* done;       // [slots] slots finished during the tick
     int32_t* counters;   // [0] survivors, [1] done count, [2] check-list count
+    int32_t route;       // test routing (masw_server_set_route), 0 normal
 };
 
 __device__ __forceinline__ const int32_t* slot_meta(const SlotView& v, int s) {
@@ -141,8 +142,9 @@ __device__ bool search_or_rescan(SlotView v, int item, int slot, const double* l
     ModeSearch st = mode_search_init(lay, N, k, c0, dc, nlim - 1, half, pair, P, topp);
     int d = 0;
     const int n = next_change(st, &d);
-    if (half) return !st.bad;
-    if (!st.bad) {
+    const bool bad = st.bad || v.route >= 3;  // (test routing 3: the FP64 scan for every item)
+    if (half) return !bad;
+    if (!bad) {
         finish_item(v, item, slot, n, c0, dc);
         return true;
     }
@@ -182,8 +184,9 @@ __global__ void __launch_bounds__(128, 7) serve_count_kernel(SlotView v, const i
     }
     const double* lay = slot_records(v, slot);
     const double k = slot_k(v, slot)[j];
-    const PairCount r =
+    PairCount r =
         count_certify_pair(slot_records32(v, slot), lay, N, k, c0, dc, nlim, half, pair);
+    if (v.route >= 1) r = PairCount{-1, -1, 0};  // test routing: the linear screen from V[0]
     if (r.cert >= 1) {
         if (!half) finish_item(v, item, slot, r.cert, c0, dc);
         return;
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(128) serve_check_kernel(SlotView v,
     TPoint p0, pa, pb{-1, -1, 0}, unused;
     eval_pair(lay, N, k, c0, dc, 0, n >= 1 ? n - 1 : nlim - 1, half, pair, &p0, &pa);
     if (n >= 1) eval_pair(lay, N, k, c0, dc, n, -1, half, pair, &pb, &unused);
-    if (mode_count_verified(n, p0.T, pa.T, pb.T)) {
+    if (v.route < 2 && mode_count_verified(n, p0.T, pa.T, pb.T)) {
         if (!half) finish_item(v, item, slot, n >= 1 ? n : -1, c0, dc);
         return;
     }
@@ -693,6 +696,12 @@ int masw_server_poll(masw_server* S, int64_t request_id, double* ct, int32_t* ct
     if (slot < 0) return MASW_EINVAL;
     if (!S->slot_done[slot]) return MASW_EAGAIN;
     retire_slot(S, slot, ct, ct_idx, status);
+    return MASW_OK;
+}
+
+int masw_server_set_route(masw_server* S, int32_t route) {
+    if (!S || route < 0 || route > 3) return MASW_EINVAL;
+    S->v.route = route;
     return MASW_OK;
 }
 

@@ -116,6 +116,13 @@ class Server:
         masw._check(rc, "masw_server_poll")
         return ct, idx, st
 
+    def set_route(self, route: int):
+        """Test routing through the slower paths (masw_server_set_route)."""
+        f = _lib().masw_server_set_route
+        f.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+        f.restype = ctypes.c_int
+        masw._check(f(ctypes.c_void_p(self.handle), int(route)), "masw_server_set_route")
+
     def stats(self) -> dict:
         s = ServerStats()
         masw._check(_lib().masw_server_get_stats(ctypes.c_void_p(self.handle), ctypes.byref(s)),

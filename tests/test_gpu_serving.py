@@ -169,3 +169,25 @@ def test_extreme_models_served_equal_the_fp64_scan(env, chunks):
     bad = np.nonzero((idx != ref_idx) | (st != ref_st))[0]
     assert bad.size == 0, (bad[:10], idx[bad[:5]], ref_idx[bad[:5]])
     assert stats["refused"] == 0 and np.isfinite(lat).all()
+
+
+@pytest.mark.parametrize("route", [1, 2, 3])
+def test_forced_routes_served_equal_the_fp64_scan(env, route):
+    """masw_server_set_route sends every served item through the linear FP32
+    screen from V[0] (1), then the failed check and the mode-count search
+    (2), then the FP64 scan at one chunk per tick (3); the results stay the
+    pure FP64 scan's."""
+    masw, serving = env
+    m, g = W.extreme_batch(n_models=48, seed=W.SEED + 11)
+    with masw.Batch(m, g) as b:
+        b.set_plan(precision=0)
+        _, ref_idx, ref_st = b.dispersion()
+    with serving.Server(g, max_slots=m.n_models, max_lambda=int(m.n_lambda.max()),
+                        chunks_per_tick=4) as srv:
+        srv.set_route(route)
+        lat, ct, idx, st, stats = srv.run_trace(m, np.zeros(m.n_models), timeout_s=300.0)
+    assert np.array_equal(idx, ref_idx) and np.array_equal(st, ref_st), route
+    with serving.Server(g, max_slots=2) as srv:
+        for bad in (-1, 4):
+            with pytest.raises(masw.MaswError):
+                srv.set_route(bad)
