@@ -57,10 +57,10 @@ FP32_FFMA_PER_CLK_SM = 128.0
 FP64_DFMA_PER_CLK_SM = 2.0
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one count_certify launch (ncu, 128-model case:
-# 521.2 KB read, 0 written): the exponential's 16 KB table once per launch,
+# 527.1 KB read, 0 written): the exponential's 16 KB table once per launch,
 # the rest (records and item tables) scaled by the models of a launch.
 CERTIFY_DRAM_BYTES_FIXED = 2048 * 8
-CERTIFY_DRAM_BYTES_PER_MODEL = (521.216e3 - CERTIFY_DRAM_BYTES_FIXED) / 128
+CERTIFY_DRAM_BYTES_PER_MODEL = (527.104e3 - CERTIFY_DRAM_BYTES_FIXED) / 128
 # DRAM bytes (read + write) of one scan launch per model, from the ncu capture
 # of the 64-model case (281.6 KB read, 0 written), scaled by the models of a
 # launch; traffic grows with the number of items.
