@@ -40,6 +40,8 @@ struct masw_batch {
     cudaStream_t stream = nullptr;
     int sm_count = 0;
 
+    // nlim: scan limits at creation, for the processing order only (updates
+    // rebuild the device copy, d_nlim)
     std::vector<int32_t> n_layers, n_lambda, loff, woff, nlim, item_model;
     std::vector<double> lambda, kvec;
     std::vector<int32_t> order_sorted, order_natural;
@@ -605,8 +607,6 @@ int masw_model_batch_update(masw_batch* B, const double* h, const double* alpha,
     // device arrays: one synchronisation returns the device check's flag
     int32_t err = 0;
     CK(cudaMemcpyAsync(&err, B->d_upd_err, sizeof(int32_t), cudaMemcpyDeviceToHost, B->stream));
-    CK(cudaMemcpyAsync(B->nlim.data(), B->d_nlim, B->nlim.size() * sizeof(int32_t),
-                       cudaMemcpyDeviceToHost, B->stream));
     CK(cudaStreamSynchronize(B->stream));
     return err ? MASW_EINVAL : MASW_OK;
 }
