@@ -891,19 +891,28 @@ cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const in
 // test velocities at or above the half-space shear speed included. Below it
 // K is real and this is Algorithm 1 itself, so an item whose batch scan found
 // a change keeps it; the others have the same sign at V[0..nlim-1] and are
-// continued here in FP64 from V[max(nlim, 1) - 1]. One warp per item
-// (persistent, popping b.order), 32 consecutive points per chunk.
-
+// continued here in FP64 from V[max(nlim, 1) - 1]. A group of G lanes per
+// item (groups pop b.order), G consecutive points per chunk. Smaller groups
+// evaluate fewer points past an item's change, but the lanes of a warp then
+// hold different items at different velocities and their branches (series,
+// exponential, sine and cosine per layer) diverge: on the leaky workload
+// (1024 uniform-batch models, c 700..1700 m/s) G = 8 took 62.5 ms against
+// 43.7 ms for a warp per item.
+template <int G>
 __global__ void __launch_bounds__(256) leaky_scan64_kernel(DevBatch b, ScanOut o,
                                                            const int32_t* __restrict__ idx_in,
                                                            const int32_t* __restrict__ status_in,
                                                            int32_t* counter) {
+    static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "lanes per item: a power of two");
     const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int gbase = lane - gl;
+    const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << gbase);
     for (;;) {
         int t = 0;
-        if (lane == 0) t = atomicAdd(counter, 1);
-        t = __shfl_sync(FULL, t, 0);
-        if (t >= b.n_items) return;
+        if (gl == 0) t = atomicAdd(counter, 1);
+        t = __shfl_sync(gmask, t, 0, G);
+        if (t >= b.n_items) return;  // the whole group leaves together
         const int item = b.order[t];
         int found = -1;
         if (status_in[item] == 0) {
@@ -916,20 +925,21 @@ __global__ void __launch_bounds__(256) leaky_scan64_kernel(DevBatch b, ScanOut o
             const double k = b.k[item];
             const int start = max(b.model_nlim[m], 1);
             int carry = 0;
-            for (int base = start - 1; base < b.n_c; base += 32) {
-                const int n = base + lane;
+            for (int base = start - 1; base < b.n_c; base += G) {
+                const int n = base + gl;
                 const int sg = n < b.n_c ? det_sign_leaky(lay, N, k, grid_c(b.c0, b.dc, n)) : 0;
-                int ps = __shfl_up_sync(FULL, sg, 1);
-                if (lane == 0) ps = carry;
-                const unsigned msk = __ballot_sync(FULL, n >= start && n < b.n_c && sg != ps);
+                int ps = __shfl_up_sync(gmask, sg, 1, G);
+                if (gl == 0) ps = carry;
+                const unsigned msk =
+                    (__ballot_sync(gmask, n >= start && n < b.n_c && sg != ps) & gmask) >> gbase;
                 if (msk) {
                     found = base + __ffs(msk) - 1;
                     break;
                 }
-                carry = __shfl_sync(FULL, sg, 31);
+                carry = __shfl_sync(gmask, sg, G - 1, G);
             }
         }
-        if (lane == 0) {
+        if (gl == 0) {
             if (found >= 0) {
                 o.ct[item] = grid_c(b.c0, b.dc, found);
                 o.idx[item] = found;
@@ -940,9 +950,13 @@ __global__ void __launch_bounds__(256) leaky_scan64_kernel(DevBatch b, ScanOut o
                 o.status[item] = 1;
             }
         }
-        __syncwarp();
+        __syncwarp(gmask);
     }
 }
+
+// lanes per item of leaky_scan64_kernel (a warp: consecutive points of one
+// item take the same branches)
+constexpr int LEAKY_LANES = 32;
 
 cudaError_t launch_leaky(const DevBatch& b, const ScanPlan& p, const int32_t* idx_in,
                          const int32_t* status_in, const ScanOut& o, int32_t* counter,
@@ -951,8 +965,8 @@ cudaError_t launch_leaky(const DevBatch& b, const ScanPlan& p, const int32_t* id
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     const int wpb = p.warps_per_block;
-    leaky_scan64_kernel<<<std::max(1, std::min(p.blocks, (b.n_items + wpb - 1) / wpb)), 32 * wpb,
-                          0, s>>>(b, o, idx_in, status_in, counter);
+    leaky_scan64_kernel<LEAKY_LANES><<<std::max(1, std::min(p.blocks, (b.n_items + wpb - 1) / wpb)),
+                                       32 * wpb, 0, s>>>(b, o, idx_in, status_in, counter);
     return cudaGetLastError();
 }
 

@@ -121,3 +121,22 @@ def test_edges_and_device_outputs(masw, oracle_lib):
     with masw.Batch(m.subset([0]), g) as b:
         _, idx, st = b.leaky()
     assert (st == 1).all()
+
+
+def test_invalid_arguments_of_the_new_entry_points(masw):
+    """Argument errors come back as MASW_EINVAL without touching the batch."""
+    import ctypes
+    m, g = W.uniform_batch(n_models=2, n_lambda=3)
+    lib = masw.load()
+    with masw.Batch(m, g) as b:
+        h = ctypes.c_void_p(b.handle)
+        assert lib.masw_dispersion_leaky(h, None, None, None, 7) == masw.EINVAL
+        assert lib.masw_dispersion_leaky(None, None, None, None, 0) == masw.EINVAL
+        assert lib.masw_mode_count(h, -1, None, None, None, None) == masw.EINVAL
+        assert lib.masw_mode_count(h, 2, None, None, None, None) == masw.EINVAL
+        assert lib.masw_mode_count(h, 0, None, None, None, None) == 0
+        assert lib.masw_last_changes_linear(h, None) == masw.EINVAL
+        n = ctypes.c_int32(99)
+        assert lib.masw_last_changes_linear(h, ctypes.byref(n)) == 0 and n.value == -1
+        ct, idx, st = b.leaky()  # still usable
+        assert (st == 0).all()
