@@ -828,7 +828,9 @@ __global__ void __launch_bounds__(128) changes_count64_kernel(DevBatch b, Change
     const int half = threadIdx.x & 1;
     const unsigned pair = 3u << (threadIdx.x & 30);
     if (t >= b.n_items) return;  // both lanes of a pair leave together
-    const int item = b.order[t];
+    // natural item order: a warp's 16 items share a model and have adjacent
+    // wavelengths, so their evaluations take the same branches
+    const int item = t;
     const size_t e0 = (size_t)item * M;
     const int n1 = first[item];
     int found = 0;
