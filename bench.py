@@ -40,10 +40,14 @@ UNIT = "curves/s"
 WORKLOAD = ("uniform_batch: 1024 models x (8 layers + half-space), h~U[1,8] m, beta_1~U[100,250] "
             "+U[10,120] per layer, nu~U[0.25,0.4], rho~U[1700,2100]; 200 log-spaced lambda "
             "1..150 m; c grid 50..1200 m/s step 0.25 (4601 points); FP64")
-# FP64 flops per layer-evaluation of the scan kernel (element assembly + one
-# Schur step): 2*DFMA + DADD + DMUL executed per evaluated (layer, c) pair,
-# from ncu instruction counters on this workload (profiles/).
-F_LAYER_FLOPS = 162.3
+# FP64 flops per layer-evaluation (element assembly + one Schur step):
+# 2*DFMA + DMUL + DADD executed per evaluated (layer, c) pair, from ncu
+# instruction counters of the fused counting kernel's FP64 certificate on the
+# 128-model case of this workload (23.07 M DFMA, 19.57 M DMUL, 3.70 M DADD over
+# 460,800 layer-evaluations; profiles/). Every FP64 kernel runs the same
+# element and Schur arithmetic. (The plain FP64 scan measured 162.3 before the
+# exponential, rescaling and comparison changes.)
+F_LAYER_FLOPS = 150.6
 # FP32 flops per layer-evaluation of the screen kernel (2*FFMA + FMUL + FADD
 # per executed (layer, c) pair: 29.6 FFMA, 54.2 FMUL, 16.4 FADD; ncu
 # instruction counters of the 64-model case, profiles/).
