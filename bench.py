@@ -183,16 +183,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, every 200 ms"}
 
 
-def cpu_oracle_rate(models, grid, n_models: int, threads: int = 0):
-    """Time the CPU oracle on the first n_models models of the workload, on
-    `threads` host threads (0: all cores). Returns (curves/s, threads,
-    sample description)."""
+def cpu_oracle_rate(models, grid, n_models: int, threads: int = 0, banded: bool = False):
+    """Time the CPU oracle (dense LU), or with banded=True the CPU banded
+    baseline (the paper's serial banded elimination restated), on the first
+    n_models models of the workload, on `threads` host threads (0: all
+    cores). Returns (curves/s, threads, sample description)."""
     import oracle
     oracle.build()
     cores = threads or os.cpu_count() or 1
     sub = models.subset(range(n_models))
+    run = oracle.dispersion_banded if banded else oracle.dispersion
     t0 = time.perf_counter()
-    oracle.dispersion(sub.as_dict(), grid.c0, grid.dc, grid.n_c, n_threads=cores)
+    run(sub.as_dict(), grid.c0, grid.dc, grid.n_c, n_threads=cores)
     dt = time.perf_counter() - t0
     return n_models / dt, cores, f"first {n_models} of the 1024 models, all 200 wavelengths, " \
                                  f"{dt:.1f} s on {cores} threads"
@@ -766,8 +768,16 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_oracle_rate(models, grid, min(256, models.n_models))
         v1, _, sample1 = cpu_oracle_rate(models, grid, min(8, models.n_models), threads=1)
+        vb, _, sample_b = cpu_oracle_rate(models, grid, min(512, models.n_models), banded=True)
+        vb1, _, sample_b1 = cpu_oracle_rate(models, grid, min(16, models.n_models), threads=1,
+                                            banded=True)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-               "single_thread": {"value": v1, "unit": UNIT, "sample": sample1}}
+               "single_thread": {"value": v1, "unit": UNIT, "sample": sample1},
+               "banded": {"value": vb, "unit": UNIT, "cores": cores,
+                          "kind": "CPU banded elimination (the paper's serial C, sparse variant, "
+                                  "restated; pinned to the oracle)",
+                          "sample": sample_b,
+                          "single_thread": {"value": vb1, "unit": UNIT, "sample": sample_b1}}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -491,6 +491,116 @@ int oracle_dispersion(int n_models, const int* n_layers, const double* h,
     return err;
 }
 
+/* ------------------------------------- CPU banded baseline (timed only)
+ *
+ * The paper's serial C with banded elimination (Section 2.1; Section 3.1, the
+ * "sparse" variant) restated for the benchmark's second CPU line; the oracle
+ * itself stays the dense LU above, and the tests pin this to it. K is block
+ * tridiagonal in 2x2 interface blocks, so det K = prod_j det S_j with
+ *   S_0 = K11^(1),  S_j = K22^(j) + K11^(j+1) - K21^(j) S_{j-1}^-1 K12^(j),
+ * and S_N takes the half-space block: O(N) work per test velocity, the same
+ * element and half-space stiffness as the oracle. No pivoting (K is positive
+ * definite below the first root); a singular pivot block gives sign 0. */
+static int det_sign_banded(int N, const double* h, const double* alpha, const double* beta,
+                           const double* rho, double k, double c) {
+    double S[4] = {0.0, 0.0, 0.0, 0.0};
+    double Ke[16];
+    int sg = 1;
+    for (int i = 0; i < N; ++i) {
+        oracle_layer_stiffness(k, c, h[i], alpha[i], beta[i], rho[i], Ke);
+        S[0] += Ke[0];
+        S[1] += Ke[1];
+        S[2] += Ke[4];
+        S[3] += Ke[5];
+        double d = S[0] * S[3] - S[1] * S[2];
+        if (d == 0.0 || d != d) return 0;
+        sg *= sgn(d);
+        /* next S = K22 - K21 S^-1 K12, S^-1 = adj(S) / d */
+        double i00 = S[3] / d, i01 = -S[1] / d, i10 = -S[2] / d, i11 = S[0] / d;
+        double t00 = i00 * Ke[2] + i01 * Ke[6], t01 = i00 * Ke[3] + i01 * Ke[7];
+        double t10 = i10 * Ke[2] + i11 * Ke[6], t11 = i10 * Ke[3] + i11 * Ke[7];
+        S[0] = Ke[10] - (Ke[8] * t00 + Ke[9] * t10);
+        S[1] = Ke[11] - (Ke[8] * t01 + Ke[9] * t11);
+        S[2] = Ke[14] - (Ke[12] * t00 + Ke[13] * t10);
+        S[3] = Ke[15] - (Ke[12] * t01 + Ke[13] * t11);
+    }
+    double Kh[4];
+    oracle_halfspace_stiffness(k, c, alpha[N], beta[N], rho[N], Kh);
+    for (int q = 0; q < 4; ++q) S[q] += Kh[q];
+    return sg * sgn(S[0] * S[3] - S[1] * S[2]);
+}
+
+int oracle_det_sign_banded(int N, const double* h, const double* alpha, const double* beta,
+                           const double* rho, double k, double c, int* sign) {
+    if (!in_domain(N, h, k)) return ORACLE_EINVAL;
+    *sign = det_sign_banded(N, h, alpha, beta, rho, k, c);
+    return ORACLE_OK;
+}
+
+/* Algorithm 1 for one wavelength with the banded determinant sign. */
+int oracle_scan_banded(int N, const double* h, const double* alpha, const double* beta,
+                       const double* rho, double lambda, double c0, double dc, int n_c,
+                       double* ct, int* idx) {
+    double k = 2.0 * M_PI / lambda;
+    *ct = NAN;
+    *idx = -1;
+    if (!in_domain(N, h, k)) return ORACLE_EINVAL;
+    int n_lim = oracle_scan_limit(beta[N], c0, dc, n_c);
+    if (n_lim < 2) return ORACLE_NO_ROOT;
+    int s_old = det_sign_banded(N, h, alpha, beta, rho, k, oracle_grid_velocity(c0, dc, 0));
+    for (int j = 1; j < n_lim; ++j) {
+        double c = oracle_grid_velocity(c0, dc, j);
+        int s_new = det_sign_banded(N, h, alpha, beta, rho, k, c);
+        if (s_new != s_old) {
+            *ct = c;
+            *idx = j;
+            return ORACLE_OK;
+        }
+        s_old = s_new;
+    }
+    return ORACLE_NO_ROOT;
+}
+
+/* The banded scan over a ragged batch (layout of oracle_dispersion),
+ * OpenMP over items. */
+int oracle_dispersion_banded(int n_models, const int* n_layers, const double* h,
+                             const double* alpha, const double* beta, const double* rho,
+                             const int* n_lambda, const double* lambda, double c0, double dc,
+                             int n_c, double* ct, int* idx, int* status, int n_threads) {
+    int64_t* hoff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_models + 1));
+    int64_t* loff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_models + 1));
+    int64_t* woff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_models + 1));
+    if (!hoff || !loff || !woff) { free(hoff); free(loff); free(woff); return ORACLE_ENOMEM; }
+    hoff[0] = loff[0] = woff[0] = 0;
+    for (int m = 0; m < n_models; ++m) {
+        hoff[m + 1] = hoff[m] + n_layers[m];
+        loff[m + 1] = loff[m] + n_layers[m] + 1;
+        woff[m + 1] = woff[m] + n_lambda[m];
+    }
+    int64_t n_items = woff[n_models];
+    int* item_model = (int*)malloc(sizeof(int) * (size_t)(n_items > 0 ? n_items : 1));
+    if (!item_model) { free(hoff); free(loff); free(woff); return ORACLE_ENOMEM; }
+    for (int m = 0; m < n_models; ++m)
+        for (int64_t j = woff[m]; j < woff[m + 1]; ++j) item_model[j] = m;
+    int err = ORACLE_OK;
+#ifdef _OPENMP
+    int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+    for (int64_t it = 0; it < n_items; ++it) {
+        int m = item_model[it];
+        int st = oracle_scan_banded(n_layers[m], h + hoff[m], alpha + loff[m], beta + loff[m],
+                                    rho + loff[m], lambda[it], c0, dc, n_c, &ct[it], &idx[it]);
+        if (st < 0) err = st;
+        status[it] = st;
+    }
+    free(item_model);
+    free(hoff);
+    free(loff);
+    free(woff);
+    return err;
+}
+
 /* Continuous root inside [c_lo, c_hi] by bisection on sgn det K, until the
  * bracket is narrower than rel_tol * c_hi. Requires a sign change at the
  * ends; returns ORACLE_NO_ROOT otherwise. The root is the bracket midpoint. */

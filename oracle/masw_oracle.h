@@ -60,6 +60,16 @@ void oracle_halfspace_stiffness_complex(double k, double c, double alpha, double
 void oracle_assemble_complex(int N, const double* h, const double* alpha, const double* beta,
                              const double* rho, double k, double c, double _Complex* K);
 void oracle_lu_det_complex(int n, double _Complex* A, double _Complex* phase, double* log_abs);
+/* CPU banded baseline (the benchmark's second CPU line; pinned to the dense LU) */
+int oracle_det_sign_banded(int N, const double* h, const double* alpha, const double* beta,
+                           const double* rho, double k, double c, int* sign);
+int oracle_scan_banded(int N, const double* h, const double* alpha, const double* beta,
+                       const double* rho, double lambda, double c0, double dc, int n_c,
+                       double* ct, int* idx);
+int oracle_dispersion_banded(int n_models, const int* n_layers, const double* h,
+                             const double* alpha, const double* beta, const double* rho,
+                             const int* n_lambda, const double* lambda, double c0, double dc,
+                             int n_c, double* ct, int* idx, int* status, int n_threads);
 double oracle_misfit_paper(int L, const double* ct, const double* ce);
 double oracle_misfit_lsq(int L, const double* ct, const double* ce, double sigma);
 

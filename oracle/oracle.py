@@ -92,6 +92,12 @@ def _load():
     lib.oracle_assemble_complex.argtypes = [i, p, p, p, p, d, d, p]
     lib.oracle_lu_det_complex.restype = None
     lib.oracle_lu_det_complex.argtypes = [i, p, p, p]
+    lib.oracle_det_sign_banded.restype = i
+    lib.oracle_det_sign_banded.argtypes = [i, p, p, p, p, d, d, p]
+    lib.oracle_scan_banded.restype = i
+    lib.oracle_scan_banded.argtypes = [i, p, p, p, p, d, d, d, i, p, p]
+    lib.oracle_dispersion_banded.restype = i
+    lib.oracle_dispersion_banded.argtypes = [i, p, p, p, p, p, p, p, d, d, i, p, p, p, i]
     lib.oracle_misfit_paper.restype = d
     lib.oracle_misfit_paper.argtypes = [i, p, p]
     lib.oracle_misfit_lsq.restype = d
@@ -298,6 +304,46 @@ def scan_leaky(h, alpha, beta, rho, lam, c0, dc, n_c) -> tuple[int, float, int]:
     st = _load().oracle_scan_leaky(h.size, _ptr(h), _ptr(alpha), _ptr(beta), _ptr(rho), lam,
                                    c0, dc, n_c, ctypes.byref(ct), ctypes.byref(idx))
     return st, ct.value, idx.value
+
+
+def det_sign_banded(h, alpha, beta, rho, k, c) -> int:
+    """Sign of det K by the banded (2x2 block) elimination of the CPU
+    baseline."""
+    h, alpha, beta, rho = _f64(h), _f64(alpha), _f64(beta), _f64(rho)
+    sg = ctypes.c_int()
+    st = _load().oracle_det_sign_banded(h.size, _ptr(h), _ptr(alpha), _ptr(beta), _ptr(rho), k,
+                                        c, ctypes.byref(sg))
+    if st != OK:
+        raise ValueError(f"oracle_det_sign_banded failed ({st})")
+    return sg.value
+
+
+def scan_banded(h, alpha, beta, rho, lam, c0, dc, n_c) -> tuple[int, float, int]:
+    """Algorithm 1 with the banded determinant sign: (status, C_t, index)."""
+    h, alpha, beta, rho = _f64(h), _f64(alpha), _f64(beta), _f64(rho)
+    ct = ctypes.c_double()
+    idx = ctypes.c_int()
+    st = _load().oracle_scan_banded(h.size, _ptr(h), _ptr(alpha), _ptr(beta), _ptr(rho), lam,
+                                    c0, dc, n_c, ctypes.byref(ct), ctypes.byref(idx))
+    return st, ct.value, idx.value
+
+
+def dispersion_banded(models, c0, dc, n_c, n_threads: int = 0):
+    """The CPU banded baseline over a ragged batch (layout of dispersion)."""
+    nl = _i32(models["n_layers"])
+    nw = _i32(models["n_lambda"])
+    h, a, b, r = (_f64(models[k]) for k in ("h", "alpha", "beta", "rho"))
+    lam = _f64(models["lambda"])
+    L = lam.size
+    ct = np.empty(L)
+    idx = np.empty(L, dtype=np.int32)
+    st = np.empty(L, dtype=np.int32)
+    err = _load().oracle_dispersion_banded(nl.size, _ptr(nl), _ptr(h), _ptr(a), _ptr(b), _ptr(r),
+                                           _ptr(nw), _ptr(lam), c0, dc, n_c, _ptr(ct), _ptr(idx),
+                                           _ptr(st), n_threads)
+    if err != OK:
+        raise MemoryError("oracle_dispersion_banded")
+    return ct, idx, st
 
 
 def refine(h, alpha, beta, rho, lam, c_lo, c_hi, rel_tol=1e-13) -> float:
