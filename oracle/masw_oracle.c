@@ -26,7 +26,9 @@
  * Deliberately plain: K is assembled as a DENSE matrix and its determinant is
  * taken by dense LU with partial pivoting (sign = parity of row swaps times
  * the signs of U's diagonal, magnitude kept as sum of log|u_ii|). No banded
- * structure, no recurrence, no reuse between test velocities.
+ * structure, no recurrence, no reuse between test velocities. (One section
+ * near the end is not part of the oracle: the benchmark's CPU banded baseline,
+ * the paper's serial banded elimination restated and pinned to the dense LU.)
  *
  * Stiffness entries. The paper only names the stiffness matrix method; the
  * entries below are derived from textbook P-SV elastodynamics. With fields
