@@ -792,7 +792,10 @@ def main():
                 "clocks": clk.summary(),
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": {0: 2, 1: 4, 2: 5}[plan.precision] * args.steps,
+                # per step: the scan's kernels (precision 0: scan; 1: screen, check,
+                # mode-count search, re-scan; 2: counting search + certificate,
+                # fallback scan, check, mode-count search, re-scan) and the misfit
+                "gpu_launches": {0: 2, 1: 5, 2: 6}[plan.precision] * args.steps,
                 "roofline": roofline,
                 "cpu_baseline": cpu,
                 "plain_gpu": None if plain_value is None else {
