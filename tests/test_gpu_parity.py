@@ -50,13 +50,31 @@ def oracle_domain(oracle_lib, models):
     return np.nonzero(2 * np.pi / models.lam * hmax[item_model] <= oracle_lib.MAX_KH)[0]
 
 
-def assert_index_parity(g_idx, g_st, o_idx, o_st, frac=0.999):
+def assert_index_parity(g_idx, g_st, o_idx, o_st, frac=0.999, explain=None):
+    """The parity bar; with explain = (oracle_lib, models, grid, items) every
+    index that differs is checked to lie where det K is within rounding of
+    zero: at the grid point whose sign the two sides disagree on (the lower
+    of the two indices), the oracle's ln|det K| is below both neighbours' by
+    more than ln(1e6), i.e. the root is closer to that point than 1e-6 of a
+    grid step."""
     assert (g_st == o_st).all(), np.nonzero(g_st != o_st)
     ok = o_st == 0
     d = np.abs(g_idx[ok].astype(np.int64) - o_idx[ok])
     assert d.max(initial=0) <= 1, d.max()
     assert (d == 0).mean() >= frac if d.size else True
     assert (g_idx[~ok] == -1).all()
+    if explain is not None:
+        oracle_lib, models, grid, items = explain
+        item_model = np.repeat(np.arange(models.n_models), models.n_lambda)
+        items = np.arange(g_idx.size) if items is None else np.asarray(items)
+        for j in np.nonzero(ok & (g_idx != o_idx))[0]:
+            it = int(items[j])
+            h, a, b, r, _ = models.model(item_model[it])
+            k = 2.0 * math.pi / models.lam[it]
+            p = int(min(g_idx[j], o_idx[j]))
+            la = [oracle_lib.det(h, a, b, r, k, oracle_lib.grid_velocity(grid.c0, grid.dc, n))[1]
+                  for n in (p - 1, p, p + 1)]
+            assert la[1] < min(la[0], la[2]) - math.log(1e6), (it, p, la)
 
 
 # ------------------------------------------------------------- full parity
@@ -75,7 +93,7 @@ def test_uniform_batch_small_matches_oracle(masw, oracle_lib):
     o_ct, o_idx, o_st = oracle_lib.dispersion(m.as_dict(), g.c0, g.dc, g.n_c)
     with masw.Batch(m, g) as b:
         ct, idx, st = b.dispersion()
-    assert_index_parity(idx, st, o_idx, o_st)
+    assert_index_parity(idx, st, o_idx, o_st, explain=(oracle_lib, m, g, None))
     same = idx == o_idx
     assert np.array_equal(ct[same & (st == 0)], o_ct[same & (st == 0)])
 
@@ -85,7 +103,7 @@ def test_ragged_batch_small_matches_oracle(masw, oracle_lib):
     o_ct, o_idx, o_st = oracle_lib.dispersion(m.as_dict(), g.c0, g.dc, g.n_c)
     with masw.Batch(m, g) as b:
         ct, idx, st = b.dispersion()
-    assert_index_parity(idx, st, o_idx, o_st)
+    assert_index_parity(idx, st, o_idx, o_st, explain=(oracle_lib, m, g, None))
 
 
 def test_coarse_grid_with_ragged_tail(masw, oracle_lib):
@@ -98,7 +116,7 @@ def test_coarse_grid_with_ragged_tail(masw, oracle_lib):
             for cpl in (1, 2, 4):
                 b.set_plan(cpl=cpl, precision=precision)
                 ct, idx, st = b.dispersion()
-                assert_index_parity(idx, st, o_idx, o_st)
+                assert_index_parity(idx, st, o_idx, o_st, explain=(oracle_lib, m, g, None))
 
 
 # ---------------------------------------------------- full-size, sampled
@@ -114,7 +132,7 @@ def test_full_size_sampled_against_oracle(masw, oracle_lib, which):
     rng = np.random.default_rng(11)
     items = rng.choice(m.n_items, size=400, replace=False)
     o_ct, o_idx, o_st = oracle_items(oracle_lib, m, g, items)
-    assert_index_parity(idx[items], st[items], o_idx, o_st)
+    assert_index_parity(idx[items], st[items], o_idx, o_st, explain=(oracle_lib, m, g, items))
     # properties that hold at any size: C_t on the grid, below beta_hs
     found = st == 0
     assert found.mean() > 0.99
@@ -212,7 +230,7 @@ def test_max_layers_model(masw, oracle_lib):
     o_ct, o_idx, o_st = oracle_lib.dispersion(m.as_dict(), g.c0, g.dc, g.n_c)
     with masw.Batch(m, g) as b:
         ct, idx, st = b.dispersion()
-    assert_index_parity(idx, st, o_idx, o_st, frac=0.66)
+    assert_index_parity(idx, st, o_idx, o_st, frac=0.66, explain=(oracle_lib, m, g, None))
 
 
 def test_invalid_inputs_are_rejected(masw):
@@ -493,7 +511,8 @@ def test_extreme_models_two_precision_equals_fp64_scan(masw, oracle_lib, seed):
     items = np.random.default_rng(seed).choice(oracle_domain(oracle_lib, m), size=48,
                                                replace=False)
     o_ct, o_idx, o_st = oracle_items(oracle_lib, m, g, items)
-    assert_index_parity(ref[1][items], ref[2][items], o_idx, o_st)
+    assert_index_parity(ref[1][items], ref[2][items], o_idx, o_st,
+                        explain=(oracle_lib, m, g, items))
 
 
 @pytest.mark.parametrize("route", [1, 2, 3])
