@@ -1,9 +1,13 @@
 """The multi-rank path on CPU: world_size-2 gloo groups split the items of a
 ragged batch (modular and contiguous partitions), each rank runs the CPU
 oracle on its shard, results gather on rank 0 and equal a one-process run;
-the timing reduction takes the max over ranks."""
+the timing reduction takes the max over ranks; a rank that fails before the
+gather surfaces on the other rank as an error of that collective, within the
+process group's timeout, instead of a hang."""
+import datetime
 import os
 import socket
+import time
 
 import numpy as np
 import pytest
@@ -85,3 +89,33 @@ def test_modular_partition_balances_a_variable_curve_better(oracle_lib):
         assert mod > con
         assert mod <= P + 1e-12 and con <= P + 1e-12
     assert sharding.partition_speedup(work, 1) == 1.0
+
+
+def _failing_worker(rank, world, port, out_path):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        raise RuntimeError("rank 1 fails before its shard is gathered")
+    t0 = time.time()
+    try:
+        sharding.gather(np.zeros(3), np.arange(3), 6)
+        status = "no-error"
+    except Exception as e:  # the peer's failure reaches this rank through the collective
+        status = "error:" + type(e).__name__
+    with open(out_path, "w") as f:
+        f.write(f"{status} {time.time() - t0:.2f}")
+
+
+def test_a_failed_rank_surfaces_as_an_error_on_the_others(tmp_path):
+    out = str(tmp_path / "status.txt")
+    ctx = mp.start_processes(_failing_worker, args=(2, _port(), out), nprocs=2, join=False,
+                             start_method="spawn")
+    for proc in ctx.processes:
+        proc.join(120)
+    codes = [proc.exitcode for proc in ctx.processes]
+    assert codes[1] not in (0, None), codes  # the failing rank
+    status, elapsed = open(out).read().split()
+    assert status.startswith("error:"), status
+    assert float(elapsed) < 60.0
