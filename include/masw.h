@@ -239,6 +239,13 @@ int masw_last_scan_phases(const masw_batch* batch, float* ms);
 #define MASW_SCREEN_COUNTED (1 << 30)
 int masw_last_scan_screen(masw_batch* batch, int32_t* n32);
 
+/* Test hook: the k-th next device allocation made by the library's batch
+ * entry points fails with MASW_ENOMEM (k = 0: the next one; once), so that
+ * tests can check that every partial failure is reported and cleaned up;
+ * k < 0 disables it. Process-wide and not synchronised with other threads:
+ * for tests only. */
+int masw_test_fail_alloc(int32_t k);
+
 /* Test routing of the two-precision and counting plans, so that tests can
  * run every item through the paths that ordinary inputs rarely reach; the
  * results must not change. 0: normal. 1: the counting search's items all go to

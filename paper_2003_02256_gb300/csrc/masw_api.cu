@@ -12,6 +12,7 @@
 //   ct, idx, status [items] results of the last scan
 // plus lazily allocated buffers for roots, gradient rows and misfits.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -147,8 +148,20 @@ static bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// masw_test_fail_alloc: ordinal of the next device allocation to fail (-1: none)
+static std::atomic<int> g_alloc_fail_at{-1};
+
 template <typename T>
 static int dev_alloc(T** p, size_t n) {
+    // test hook (masw_test_fail_alloc): the allocation with this ordinal fails
+    const int at = g_alloc_fail_at.load();
+    if (at >= 0) {
+        g_alloc_fail_at.store(at - 1);
+        if (at == 0) {
+            *p = nullptr;
+            return MASW_ENOMEM;
+        }
+    }
     if (n == 0) n = 1;
     cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
     if (e != cudaSuccess) {
@@ -991,6 +1004,11 @@ int masw_set_plan(masw_batch* B, const masw_plan* plan) {
     CK(cudaStreamSynchronize(B->stream));
     B->plan = *plan;
     return rebuild_graph(B);
+}
+
+int masw_test_fail_alloc(int32_t k) {
+    g_alloc_fail_at.store(k < 0 ? -1 : (int)k);
+    return MASW_OK;
 }
 
 int masw_set_route(masw_batch* B, int32_t route) {

@@ -78,6 +78,7 @@ def load():
         "masw_dispersion_leaky": [p, p, p, p, i32],
         "masw_mode_count": [p, i32, p, p, p, p],
         "masw_set_route": [p, i32],
+        "masw_test_fail_alloc": [i32],
         "masw_misfit": [p, p, i32, d, p],
         "masw_misfit_grad": [p, p, i32, d, p, p, p],
         "masw_roots": [p, p],
@@ -249,6 +250,11 @@ def mode_count(handle, item, c, s, j0):
     """Wittrick-Williams counts (s, J0) at arbitrary points (masw_mode_count)."""
     _check(load().masw_mode_count(ctypes.c_void_p(handle), int(len(item)), _ptr(item), _ptr(c),
                                   _ptr(s), _ptr(j0)), "masw_mode_count")
+
+
+def test_fail_alloc(k: int):
+    """Test hook: the k-th next device allocation fails (masw_test_fail_alloc)."""
+    _check(load().masw_test_fail_alloc(int(k)), "masw_test_fail_alloc")
 
 
 def set_route(handle, route: int):
