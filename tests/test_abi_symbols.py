@@ -48,3 +48,16 @@ def test_null_arguments_are_rejected_without_touching_the_gpu(lib):
     assert f(None, None, None, None) == 1
     assert lib.masw_dispersion(None, None, None, None, 0) == 1
     assert lib.masw_misfit(None, None, 0, ctypes.c_double(1.0), None) == 1
+
+
+def test_new_entry_points_reject_bad_arguments_without_the_gpu(lib):
+    """Argument checks come before any CUDA call, so they answer on a machine
+    without a GPU too."""
+    p, i32 = ctypes.c_void_p, ctypes.c_int32
+    assert lib.masw_dispersion_leaky(None, None, None, None, i32(0)) == 1
+    assert lib.masw_dispersion_changes(None, i32(3), None, None, None, None, i32(0)) == 1
+    assert lib.masw_mode_count(None, i32(1), None, None, None, None) == 1
+    assert lib.masw_set_route(None, i32(0)) == 1
+    assert lib.masw_server_set_route(None, i32(0)) == 1
+    assert lib.masw_last_changes_linear(None, None) == 1
+    assert lib.masw_test_fail_alloc(i32(-1)) == 0
