@@ -1,21 +1,44 @@
 // masw_kernels.cu -- CUDA kernels of the dispersion-curve engine (sm_103a).
 //
-//  scan_kernel      Algorithm 1 (Section 2.1): one warp per (model, wavelength)
-//                   item, lanes stride the test-velocity grid 32*CPL points at
-//                   a time, first sign change by __ballot_sync/__ffs, early
-//                   exit. Replaces the paper's GPU steps 2-4 (form matrices,
-//                   banded elimination, block sign search + combine; Section
-//                   2.3): nothing is materialised, so there is no memory wall.
-//                   Persistent mode: warps pop items from a queue ordered by
-//                   predicted scan length (the GPU form of the modular
-//                   wavelength partition of Section 2.2).
-//  det_eval_kernel  sign and ln|det K| at arbitrary (item, c) points (parity).
-//  refine_kernel    bisection on sgn det K inside [V[idx-1], V[idx]].
-//  root_grad_kernel null-vector adjoint dC*/dtheta at the refined root.
-//  misfit_kernel    Algorithm 2 (and the least-squares form) per model, plus
-//                   dPhi/dC per item; deterministic warp reductions.
-//  grad_reduce      dPhi/dtheta = sum_j dPhi/dC_j dC_j/dtheta per model.
-//  fp64_peak_kernel DFMA throughput microbenchmark (roofline denominator).
+// Algorithm 1 (Section 2.1), three plans:
+//  scan_kernel            precision 0: one warp per (model, wavelength) item,
+//                         lanes stride the test-velocity grid 32*CPL points at
+//                         a time in FP64, first sign change by __ballot_sync /
+//                         __ffs, early exit. Replaces the paper's GPU steps 2-4
+//                         (form matrices, banded elimination, block sign search
+//                         + combine; Section 2.3): nothing is materialised, so
+//                         there is no memory wall. Persistent mode: warps pop
+//                         items from a queue ordered by predicted scan length
+//                         (the GPU form of the modular partition, Section 2.2).
+//  screen32_kernel,       precision 1: the same scan in FP32 (packed FP32x2 for
+//  screen32p_kernel       the paired form), then verify64_kernel: a three-point
+//                         FP64 check on the Wittrick-Williams mode count.
+//  count_certify_kernel   precision 2 (default): FP32 search on the
+//                         negative-eigenvalue count below the pole-free bound
+//                         and its FP64 certificate, a lane pair per item; the
+//                         fallback items take fallback32_kernel (linear FP32
+//                         scan) and verify64_list_kernel (the check).
+//  first_count64_kernel   both two-precision plans: items that failed a check,
+//                         FP64 search on the mode count from V[0].
+//  resolve64_kernel       items whose FP64 counts failed: FP64 scan from V[0].
+// Beyond the first change:
+//  changes_count64_kernel higher modes, FP64 search on the mode count;
+//  changes_scan64_kernel  higher modes, FP64 scan at every grid point.
+//  leaky_scan64_kernel    the whole grid with the sign of Re det K (complex
+//                         half-space block above its shear speed).
+// Around the scan:
+//  det_eval_kernel        sign and ln|det K| at arbitrary (item, c) points.
+//  mode_count_kernel      (s, J0) at arbitrary points.
+//  refine_kernel          the root inside [V[idx-1], V[idx]] by the Illinois
+//                         method (modified regula falsi) on det K.
+//  root_grad_kernel       null-vector adjoint dC*/dtheta at the refined root.
+//  misfit_kernel          Algorithm 2 (and the least-squares form) per model,
+//                         plus dPhi/dC per item; deterministic warp reductions.
+//  grad_reduce_kernel     dPhi/dtheta = sum_j dPhi/dC_j dC_j/dtheta per model.
+//  validate_models_kernel, build_records_kernel, update_beta_h_kernel
+//                         model updates on the device.
+//  exp_check_kernel       the library's exponential beside CUDA's (tests).
+//  fp64_peak_kernel       DFMA throughput microbenchmark (roofline denominator).
 #include <algorithm>
 
 #include "masw_adjoint.cuh"
