@@ -10,7 +10,10 @@
 //   k           [items] f64 2 pi / lambda;  item_model [items] i32
 //   order       [items] i32 processing order (longest predicted scan first)
 //   ct, idx, status [items] results of the last scan
-// plus lazily allocated buffers for roots, gradient rows and misfits.
+//   FP32 records, screen indices, the search / re-scan / fallback lists and
+//   their counters (two-precision plans)
+// plus lazily allocated buffers for roots, gradient rows and misfits, model
+// updates, the higher modes and the leaky continuation.
 #include <algorithm>
 #include <atomic>
 #include <cmath>

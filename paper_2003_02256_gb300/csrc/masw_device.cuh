@@ -32,7 +32,12 @@
 //    signs of w^2, so c near alpha_i or beta_i (w -> 0) has no 0/0;
 //  * the Schur recurrence is homogeneous: P = Phat / w with a scalar weight,
 //    det S_j has the sign of det Shat_j, and (Phat, w) are rescaled by a
-//    power of two every step -- no division at all on the scan path.
+//    power of two every step -- no division at all on the scan path;
+//  * e^x from a 2048-entry table (8 FP64 operations), and sign tests and
+//    magnitude comparisons of doubles on the integer pipe (bit patterns).
+// Also here: the Wittrick-Williams mode count (the pivots' inertia plus the
+// clamped-layer modes, counted by halving each layer's thickness) and the
+// complex last pivot of the leaky continuation.
 #pragma once
 
 #include <cuda_runtime.h>
