@@ -59,3 +59,21 @@ def test_client_results_equal_the_python_binding(tmp_path):
     assert [int(r[2]) for r in rec["leaky"]] == st_l.tolist()
     assert np.allclose([float(r[1]) for r in rec["misfit"]], phi, rtol=1e-12)
     assert (st == 0).all()
+
+
+def test_header_compiles_as_cpp_with_c_linkage(tmp_path):
+    """include/masw.h also serves C++ callers: its extern "C" block keeps the
+    symbols unmangled, so a C++ translation unit links against libmasw."""
+    from paper_2003_02256_gb300 import build
+    so = build.build()
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no g++")
+    src = tmp_path / "client.cpp"
+    src.write_text('#include "masw.h"\nint main() { return masw_strerror(0) ? 0 : 1; }\n')
+    out = str(tmp_path / "client_cpp")
+    libdir = os.path.dirname(so)
+    subprocess.run([gxx, "-std=c++17", "-Wall", "-Wextra", "-Werror", "-I",
+                    os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lmasw",
+                    "-Wl,-rpath," + libdir, "-o", out], check=True)
+    assert subprocess.run([out]).returncode == 0
