@@ -81,6 +81,6 @@ def test_gradient_steps_reduce_the_misfit(env, oracle_lib):
             opt.step()
             with torch.no_grad():
                 h.clamp_(min=0.3)
-            first = float(phi) if first is None else first
+            first = float(phi.detach()) if first is None else first
         last = float(autograd.misfit(beta.detach(), h.detach(), b, ce).sum())
     assert last < 0.5 * first
