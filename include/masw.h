@@ -169,6 +169,18 @@ int masw_dispersion_plain(masw_batch* batch, double* ct, int32_t* ct_idx, int32_
  * (sigma > 0 used by LSQ only). A model with an item without root gets NaN. */
 int masw_misfit(masw_batch* batch, const double* ce, int32_t kind, double sigma, double* misfit);
 
+/* One whole evaluation with every result returned: Algorithm 1 for every item
+ * and Algorithm 2 per model, then C_t and the misfit copied out together, as
+ * the paper's GPU procedure copies both back to the host at its end (Section
+ * 2.3). ce and misfit as masw_misfit; ct, ct_idx, status as masw_dispersion
+ * (any may be NULL). Each pointer may be host or device memory on its own.
+ * Host buffers are read and written by asynchronous copies on the batch
+ * stream, and the call synchronises that stream once, at its end, when any
+ * of them is host memory (pinned host memory makes the copies fastest);
+ * with device pointers only it returns without waiting. */
+int masw_misfit_curves(masw_batch* batch, const double* ce, int32_t kind, double sigma,
+                       double* misfit, double* ct, int32_t* ct_idx, int32_t* status);
+
 /* Misfit evaluated on the refined continuous roots C* (bisection inside the
  * first sign-changing bracket to a relative width of 1e-13) and its exact
  * gradient by the implicit-function rule d(C*)/d(theta) = -(u^T dK/dtheta u) /
@@ -444,17 +456,24 @@ int masw_server_run_trace(masw_server* server, int32_t n_requests, const int32_t
  * work-queue counter) goes to one fixed array of MASW_NOALLOC_SCRATCH_BYTES
  * in device memory that every GPU loading the library holds until exit.
  *  - models: like masw_model_batch_create (host or device arrays, mem_space);
- *    grid as there. ct, ct_idx, status: DEVICE buffers of sum(n_lambda)
- *    entries, same meaning as masw_dispersion; results equal its results.
+ *    grid as there. Every input array must lie in the space mem_space
+ *    declares (device or managed memory for MASW_DEVICE, host memory for
+ *    MASW_HOST); a mixed call returns MASW_EINVAL before any copy or launch.
+ *    ct, ct_idx, status: DEVICE buffers of sum(n_lambda) entries, same
+ *    meaning as masw_dispersion; results equal its results.
+ *  - It runs the plain FP64 scan (one warp per item, 32 test velocities per
+ *    chunk, items in their natural order), not masw_dispersion's default
+ *    counting plan: the same indices, at the FP64 scan's lower throughput.
  *  - Limits: n_models <= MASW_NOALLOC_MAX_MODELS, sum(N_m + 1) <=
  *    MASW_NOALLOC_MAX_RECORDS, sum(n_lambda) <= MASW_NOALLOC_MAX_ITEMS;
  *    beyond them the call returns MASW_ETOOBIG and touches nothing.
  *  - The first call on a device looks up the array's device address (once,
- *    with that device current); make that first call before any stream
- *    capture on that device.
- *  - It validates on the GPU and waits for that check (it synchronises
- *    cuda_stream once before launching the scan), then enqueues the scan and
- *    returns; the outputs are complete when cuda_stream reaches that point.
+ *    with that device current).
+ *  - Every call validates on the GPU and waits for that check: it copies an
+ *    error word to the host and synchronises cuda_stream before it launches
+ *    the scan, then enqueues the scan and returns; the outputs are complete
+ *    when cuda_stream reaches that point. Because of that synchronisation no
+ *    call may be made while a stream capture is under way.
  *  - All calls share the one array and every call overwrites it: calls that
  *    may run at the same time on the GPU (other streams, other threads) race
  *    and give wrong results. Calls on one stream are ordered and safe. */

@@ -866,6 +866,30 @@ int masw_misfit(masw_batch* B, const double* ce, int32_t kind, double sigma, dou
     return MASW_OK;
 }
 
+int masw_misfit_curves(masw_batch* B, const double* ce, int32_t kind, double sigma,
+                       double* misfit, double* ct, int32_t* ct_idx, int32_t* status) {
+    if (!B || !ce || !misfit || (kind != MASW_MISFIT_PAPER && kind != MASW_MISFIT_LSQ))
+        return MASW_EINVAL;
+    if (kind == MASW_MISFIT_LSQ && !(sigma > 0.0 && std::isfinite(sigma))) return MASW_EINVAL;
+    int rc;
+    if ((rc = ensure(&B->d_ce, B->n_items)) || (rc = ensure(&B->d_misfit, B->n_models))) return rc;
+    // the observed curve goes in without a wait: the one synchronisation at
+    // the end covers the caller's host buffer as well
+    bool sync = !is_device_ptr(ce);
+    if (B->n_items > 0)
+        CK(cudaMemcpyAsync(B->d_ce, ce, B->n_items * sizeof(double),
+                           sync ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, B->stream));
+    if ((rc = run_scan(B))) return rc;
+    CK(launch_misfit(B->dev(false), B->d_ct, B->d_ce, kind, sigma, B->d_misfit, nullptr, B->stream));
+    if ((rc = copy_out(misfit, B->d_misfit, B->n_models, B->stream, &sync)) ||
+        (rc = copy_out(ct, B->d_ct, B->n_items, B->stream, &sync)) ||
+        (rc = copy_out(ct_idx, B->d_idx, B->n_items, B->stream, &sync)) ||
+        (rc = copy_out(status, B->d_status, B->n_items, B->stream, &sync)))
+        return rc;
+    if (sync) CK(cudaStreamSynchronize(B->stream));
+    return MASW_OK;
+}
+
 static int run_roots(masw_batch* B) {
     int rc;
     if ((rc = ensure(&B->d_croot, B->n_items))) return rc;

@@ -81,13 +81,28 @@ int scratch_address(unsigned char** out) {
     return MASW_OK;
 }
 
-bool is_device(const void* p) {
+// Memory type of a pointer as the CUDA runtime sees it; pageable host memory
+// the runtime has never seen reads as cudaMemoryTypeUnregistered.
+cudaMemoryType memory_type(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return cudaMemoryTypeUnregistered;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return a.type;
+}
+
+bool is_device(const void* p) {
+    const cudaMemoryType t = memory_type(p);
+    return t == cudaMemoryTypeDevice || t == cudaMemoryTypeManaged;
+}
+
+// An input array the declared space can read: device (or managed) memory for
+// MASW_DEVICE, anything but plain device memory for MASW_HOST. A host array
+// passed as MASW_DEVICE would reach the prep kernel as an illegal address,
+// and a device array passed as MASW_HOST would be read on the host.
+bool in_space(const void* p, bool dev_in) {
+    return dev_in ? is_device(p) : memory_type(p) != cudaMemoryTypeDevice;
 }
 
 __device__ __forceinline__ bool fpos(double x) { return isfinite(x) && x > 0.0; }
@@ -165,6 +180,11 @@ extern "C" int masw_dispersion_noalloc(const masw_models_desc* md, const masw_gr
     if (!is_device(ct) || !is_device(ct_idx) || !is_device(status)) return MASW_EINVAL;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const bool dev_in = md->mem_space == MASW_DEVICE;
+    // every input array in the declared space, before any copy or launch
+    const void* inputs[] = {md->n_layers, md->n_lambda, md->h, md->alpha, md->beta, md->rho,
+                            md->lambda};
+    for (const void* in : inputs)
+        if (in && !in_space(in, dev_in)) return MASW_EINVAL;
     const int M = md->n_models;
 
     unsigned char* base = nullptr;

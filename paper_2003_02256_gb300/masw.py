@@ -225,6 +225,17 @@ def misfit(handle, ce, kind, sigma, out):
                               _ptr(out)), "masw_misfit")
 
 
+def misfit_curves(handle, ce, kind, sigma, out, ct, ct_idx, status):
+    """masw_misfit_curves: Algorithm 1 + Algorithm 2 with the curves and the
+    misfit returned together (each buffer host or device)."""
+    f = load().masw_misfit_curves
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    _check(f(ctypes.c_void_p(handle), _ptr(ce), int(kind), float(sigma), _ptr(out), _ptr(ct),
+             _ptr(ct_idx), _ptr(status)), "masw_misfit_curves")
+
+
 def misfit_grad(handle, ce, kind, sigma, out, grad_beta, grad_h):
     _check(load().masw_misfit_grad(ctypes.c_void_p(handle), _ptr(ce), int(kind), float(sigma),
                                    _ptr(out), _ptr(grad_beta), _ptr(grad_h)), "masw_misfit_grad")
@@ -436,6 +447,16 @@ class Batch:
         misfit(self.handle, np.ascontiguousarray(ce, dtype=np.float64), kind, sigma, out)
         return out
 
+    def misfit_curves(self, ce, kind=MISFIT_LSQ, sigma=2.0):
+        """(misfit, ct, idx, status) from one evaluation."""
+        out = np.empty(self.n_models)
+        ct = np.empty(self.n_items)
+        idx = np.empty(self.n_items, dtype=np.int32)
+        st = np.empty(self.n_items, dtype=np.int32)
+        misfit_curves(self.handle, np.ascontiguousarray(ce, dtype=np.float64), kind, sigma, out,
+                      ct, idx, st)
+        return out, ct, idx, st
+
     def misfit_grad(self, ce, kind=MISFIT_LSQ, sigma=2.0):
         n_rec = int(np.sum(self.models.n_layers) + self.n_models)
         out = np.empty(self.n_models)
@@ -510,7 +531,10 @@ def dispersion_noalloc(n_layers, h, alpha, beta, rho, n_lambda, lam, grid, ct, c
     f.argtypes = [ctypes.POINTER(ModelsDesc), ctypes.POINTER(GridDesc), ctypes.c_void_p,
                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     f.restype = ctypes.c_int
-    space = _space(beta)
+    spaces = {_space(x) for x in (n_layers, h, alpha, beta, rho, n_lambda, lam) if x is not None}
+    if len(spaces) != 1:
+        raise ValueError("dispersion_noalloc: model arrays must all be host or all be device")
+    space = spaces.pop()
     desc = ModelsDesc(int(len(n_layers)), _ptr(n_layers), _ptr(h), _ptr(alpha), _ptr(beta),
                       _ptr(rho), _ptr(n_lambda), _ptr(lam), space)
     g = GridDesc(float(grid[0]), float(grid[1]), int(grid[2]))

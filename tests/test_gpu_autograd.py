@@ -1,12 +1,17 @@
 """torch.autograd over the adjoint misfit gradient (differentiation workload).
 
-Checks the backward pass against central finite differences of the forward
-pass (relative step 1e-4, the bar 1e-5 of the gradient norm) and that a few
-gradient steps lower the misfit of a perturbed model toward the true one.
+Checks the backward pass per component (1e-5 relative, tests/gradcheck.py)
+against the oracle's gradient of the same weighted misfit, and against
+central finite differences of the forward pass itself (relative step 1e-4).
+The forward's roots are refined to a relative bracket of 1e-13, which puts
+up to ~1e-5 relative noise on single difference quotients, so that second
+check is held to 1e-5 of the largest component. Also: a few gradient steps
+lower the misfit of a perturbed model toward the true one.
 """
 import numpy as np
 import pytest
 
+from gradcheck import assert_grad_close, root_grad_reference
 from paper_2003_02256_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -60,9 +65,29 @@ def test_backward_matches_finite_differences_of_forward(env, oracle_lib):
             hp[i] += d
             hm[i] -= d
             fd_h[i] = (f(m.beta, hp) - f(m.beta, hm)) / (2 * d)
-    ref = np.r_[fd_b, fd_h]
+        f(m.beta, m.h)  # the batch back on the unperturbed model
+        _, idx, st = b.dispersion()
+    fd = np.r_[fd_b, fd_h]
     got = np.r_[gb, gh]
-    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+    assert np.abs(got - fd).max() <= 1e-5 * np.abs(fd).max()
+    # per component against the oracle's gradient of the same weighted misfit
+    assert (st == 0).all()
+    hoff, loff, woff = m.layer_offsets()
+    ref_b = np.zeros_like(gb)
+    ref_h = np.zeros_like(gh)
+    for k in range(m.n_models):
+        hk, ak, bk, rk, lam = m.model(k)
+        N = hk.size
+        for j in range(lam.size):
+            it = woff[k] + j
+            c = oracle_lib.root(hk, ak, bk, rk, lam[j], g.c0, g.dc, g.n_c, int(idx[it]))
+            dc = root_grad_reference(oracle_lib, hk, ak, bk, rk, lam[j], g, idx[it])
+            wgt = float(w[k]) * (c - ce[it]) / 4.0  # LSQ misfit, sigma = 2
+            ref_b[loff[k]:loff[k + 1]] += wgt * dc[:N + 1]
+            ref_h[hoff[k]:hoff[k + 1]] += wgt * dc[N + 1:]
+    for k in range(m.n_models):
+        assert_grad_close(np.r_[gb[loff[k]:loff[k + 1]], gh[hoff[k]:hoff[k + 1]]],
+                          np.r_[ref_b[loff[k]:loff[k + 1]], ref_h[hoff[k]:hoff[k + 1]]], where=k)
 
 
 def test_gradient_steps_reduce_the_misfit(env, oracle_lib):
