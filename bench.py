@@ -1,20 +1,33 @@
 """Benchmark: dispersion curves per second on GB300.
 
-A step is one MASW evaluation of a whole batch -- Algorithm 1 (theoretical
-dispersion curve of every (model, wavelength) item) followed by Algorithm 2
-(misfit per model) -- on the uniform workload: 1024 models of 8 layers over a
-half-space, 200 log-spaced wavelengths 1..150 m, test velocities 50..1200 m/s
-step 0.25 (4601 points), FP64. Inputs are resident in device memory when the
-timed region starts; L2 is flushed (256 MB write) between timed steps.
+A step is one MASW evaluation of a whole batch -- Algorithm 1 (the
+theoretical dispersion curve of every (model, wavelength) item) followed by
+Algorithm 2 (least-squares misfit per model). The default workload is the
+ragged batch: 8192 models of 3..30 layers over a half-space, 30..400
+log-spaced wavelengths from 1 m to twice the model's total thickness
+(1,740,640 items), 10 % of the models with a low-velocity layer, test
+velocities 50..1200 m/s in steps of 0.25 (4601 points), FP64 decisions.
+Inputs are resident in device memory when the timed region starts; L2 is
+flushed (256 MB write) between timed steps.
 
-Also reported on the same line: the plain one-curve-per-launch GPU path,
-the end-to-end figure through the C ABI with host buffers, the roofline of
-the scan kernel against the measured FP64 peak, and the CPU oracle on a
-bounded sample (``cpu_baseline``). ``--impl reference`` times the CPU oracle
-alone (the reference arm).
+The same line carries:
+- the plain one-curve-per-launch GPU path;
+- the end-to-end figure through the C ABI with host buffers: the models and
+  the observed curve uploaded, the curves and the misfit read back, every
+  step;
+- the roofline of the dominant kernel, with clocks sampled during the timed
+  steps;
+- the CPU oracle on a bounded sample (cpu_baseline), with the CPU-rank
+  partition study of Section 3.2.
+
+Extras: the uniform batch measured the same way, the autotuner's plan
+against the default, differentiation, inversion, uniform stress, higher
+modes, the leaky continuation, the first call, the allocation-free entry
+point and serving. ``--impl reference`` times the CPU oracle alone (the
+reference arm).
 
 Multi-GPU: one process per GPU (torchrun); each rank evaluates its own
-1024-model batch (weak scaling, no data-path collective).
+seeded batch (weak scaling, no data-path collective).
 """
 from __future__ import annotations
 
@@ -37,9 +50,27 @@ from paper_2003_02256_gb300 import workloads as W  # noqa: E402
 
 METRIC = "dispersion curves/sec (model x all lambda) and p50/p99 latency vs plain GPU"
 UNIT = "curves/s"
-WORKLOAD = ("uniform_batch: 1024 models x (8 layers + half-space), h~U[1,8] m, beta_1~U[100,250] "
-            "+U[10,120] per layer, nu~U[0.25,0.4], rho~U[1700,2100]; 200 log-spaced lambda "
-            "1..150 m; c grid 50..1200 m/s step 0.25 (4601 points); FP64")
+WORKLOADS = {
+    "ragged": ("ragged_batch: 8192 models, N~U{3..30} layers + half-space, n_lambda~U{30..400} "
+               "log-spaced from 1 m to 2x the model's total thickness (1,740,640 items), 10% of "
+               "the models with a low-velocity layer; h~U[1,8] m, beta_1~U[100,250] +U[10,120] "
+               "per layer, nu~U[0.25,0.4], rho~U[1700,2100]; c grid 50..1200 m/s step 0.25 "
+               "(4601 points); FP64 decisions"),
+    "uniform": ("uniform_batch: 1024 models x (8 layers + half-space), h~U[1,8] m, "
+                "beta_1~U[100,250] +U[10,120] per layer, nu~U[0.25,0.4], rho~U[1700,2100]; 200 "
+                "log-spaced lambda 1..150 m; c grid 50..1200 m/s step 0.25 (4601 points); FP64 "
+                "decisions"),
+}
+DEFAULT_MODELS = {"ragged": 8192, "uniform": 1024}
+
+
+def make_workload(name: str, n_models: int, rank: int = 0):
+    """The seeded batch of one rank (weak scaling: rank r draws its own shard)."""
+    if name == "uniform":
+        return W.uniform_batch(n_models=n_models, seed=W.SEED + 1000 * rank)
+    return W.ragged_batch(n_models=n_models, seed=W.SEED + 3 + 1000 * rank)
+
+
 # FP64 flops per layer-evaluation (element assembly + one Schur step):
 # 2*DFMA + DMUL + DADD executed per evaluated (layer, c) pair, from ncu
 # instruction counters of the fused counting kernel's FP64 certificate on the
@@ -61,11 +92,12 @@ FP32_FFMA_PER_CLK_SM = 128.0
 # the maximum SM clock.
 FP64_DFMA_PER_CLK_SM = 2.0
 SM_MAX_MHZ = 2070.0
-# DRAM bytes (read + write) of one count_certify launch (ncu, 128-model case:
-# 527.1 KB read, 0 written): the exponential's 16 KB table once per launch,
-# the rest (records and item tables) scaled by the models of a launch.
-CERTIFY_DRAM_BYTES_FIXED = 2048 * 8
-CERTIFY_DRAM_BYTES_PER_MODEL = (527.104e3 - CERTIFY_DRAM_BYTES_FIXED) / 128
+# DRAM bytes (read + write) of one count_certify launch, from ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the full workload, as
+# (bytes, models of that launch); the records, wavenumbers and item tables are
+# read once, the outputs stay in L2. Scaled by the models of a launch; None
+# where no capture of the current kernel exists.
+CERTIFY_DRAM_BYTES = {"uniform": (3.492096e6, 1024), "ragged": None}
 # DRAM bytes (read + write) of one scan launch per model, from the ncu capture
 # of the 64-model case (281.6 KB read, 0 written), scaled by the models of a
 # launch; traffic grows with the number of items.
@@ -183,36 +215,121 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, every 200 ms"}
 
 
-def cpu_oracle_rate(models, grid, n_models: int, threads: int = 0, banded: bool = False):
+def cpu_oracle_rate(models, grid, sample, threads: int = 0, banded: bool = False):
     """Time the CPU oracle (dense LU), or with banded=True the CPU banded
-    baseline (the paper's serial banded elimination restated), on the first
-    n_models models of the workload, on `threads` host threads (0: all
+    baseline (the paper's serial banded elimination restated), on the models
+    with indices ``sample`` of the workload, on `threads` host threads (0: all
     cores). Returns (curves/s, threads, sample description)."""
     import oracle
     oracle.build()
     cores = threads or os.cpu_count() or 1
-    sub = models.subset(range(n_models))
+    sample = np.asarray(sample)
+    sub = models.subset(sample)
     run = oracle.dispersion_banded if banded else oracle.dispersion
     t0 = time.perf_counter()
     run(sub.as_dict(), grid.c0, grid.dc, grid.n_c, n_threads=cores)
     dt = time.perf_counter() - t0
-    return n_models / dt, cores, f"first {n_models} of the 1024 models, all 200 wavelengths, " \
-                                 f"{dt:.1f} s on {cores} threads"
+    step = int(sample[1] - sample[0]) if sample.size > 1 else 1
+    return sample.size / dt, cores, (f"{sample.size} of the {models.n_models} models (every "
+                                     f"{step}th from {int(sample[0])}), all their wavelengths "
+                                     f"({sub.n_items} items), {dt:.1f} s on {cores} threads")
+
+
+def _partition_rank(rank, world, reps, barrier, queue):
+    """One CPU rank of the partition study: Algorithm 1 with the oracle on its
+    share of the 40 wavelengths of the variable curve, for each partition,
+    timed between two barriers (the same start for every rank)."""
+    import oracle
+    m, g = W.single_curve()
+    h, a, b, r, _ = m.model(0)
+    lam = sharding.variable_curve_wavelengths(40)
+    out = {}
+    for mode in ("contiguous", "modular"):
+        mine = sharding.shard(lam.size, rank, world, mode)
+        times = []
+        for _ in range(3):
+            barrier.wait()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                idx = [oracle.scan(h, a, b, r, lam[i], g.c0, g.dc, g.n_c)[2] for i in mine]
+            times.append(time.perf_counter() - t0)
+        out[mode] = (times, mine.tolist(), idx)
+    queue.put((rank, out))
+
+
+def cpu_partition_study(ranks=(1, 2, 3, 4, 8, 16), reps: int = 20):
+    """Section 3.2 on CPU ranks: the 40-wavelength decreasing curve split over
+    P spawned processes (contiguous blocks or the paper's modular partition),
+    each running the oracle's Algorithm 1 on its share ``reps`` times; the
+    wall time of a run is that of the slowest rank (median of 3 runs), and
+    the speedup is the one-rank time over it. Beside it, the cost model
+    (total work over the busiest rank's, work = determinants evaluated)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    cores = os.cpu_count() or 1
+    m, g = W.single_curve()
+    h, a, b, r, _ = m.model(0)
+    lam = sharding.variable_curve_wavelengths(40)
+    serial_idx = [oracle.scan(h, a, b, r, l, g.c0, g.dc, g.n_c)[2] for l in lam]
+    work = np.asarray(serial_idx, dtype=np.float64) + 1.0
+    res = {}
+    for P in ranks:
+        if P > cores:
+            continue
+        barrier, queue = ctx.Barrier(P), ctx.Queue()
+        procs = [ctx.Process(target=_partition_rank, args=(q, P, reps, barrier, queue))
+                 for q in range(P)]
+        for p in procs:
+            p.start()
+        got = [queue.get(timeout=600) for _ in range(P)]
+        for p in procs:
+            p.join(timeout=60)
+        row = {}
+        for mode in ("contiguous", "modular"):
+            idx = np.full(lam.size, -1)
+            for _, out in got:
+                idx[out[mode][1]] = out[mode][2]
+            assert np.array_equal(idx, serial_idx), "gathered indices differ from one rank's"
+            wall = [max(out[mode][0][k] for _, out in got) for k in range(3)]
+            row[mode] = {"wall_s": float(np.median(wall)),
+                         "cost_model_speedup": sharding.partition_speedup(work, P, mode)}
+        res[P] = row
+    t1 = np.median([res[1][mode]["wall_s"] for mode in ("contiguous", "modular")])
+    for P, row in res.items():
+        for mode in row:
+            row[mode]["speedup"] = float(t1 / row[mode]["wall_s"])
+    return {"workload": "single-curve model (4 layers + half-space, c grid 50..500 step 0.5), "
+                        f"40 log-spaced decreasing wavelengths 60..1 m, Algorithm 1 x {reps} per "
+                        "run on each rank's share; ranks = spawned processes, one per core",
+            "cores": cores,
+            "ranks": {str(P): row for P, row in res.items()},
+            "paper_section_3_2": {"3": {"modular": 2.8, "contiguous": 1.9},
+                                  "8": {"modular": 7.0, "contiguous": 4.2}}}
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle (Algorithm 1 by dense LU, all host
+    cores) on the same workload, metric and unit; each step a bounded sample
+    of the workload's models (strided through the batch)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    models, grid = W.uniform_batch()
+    n_models = args.models or DEFAULT_MODELS[args.workload]
+    models, grid = make_workload(args.workload, n_models, 0)
     per_step = 16
-    for _ in range(args.warmup):
-        cpu_oracle_rate(models, grid, 4)
-    times = []
-    cores = os.cpu_count() or 1
+    stride = max(1, n_models // (per_step * max(1, args.steps)))
     import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    for w in range(args.warmup):
+        sub = models.subset(range(w, min(n_models, w + 4)))
+        oracle.dispersion(sub.as_dict(), grid.c0, grid.dc, grid.n_c, n_threads=cores)
+    times = []
     for s in range(args.steps):
-        sub = models.subset(range((s * per_step) % 1024, (s * per_step) % 1024 + per_step))
+        ms = [(s * per_step + q) * stride % n_models for q in range(per_step)]
+        sub = models.subset(ms)
         t0 = time.perf_counter()
         oracle.dispersion(sub.as_dict(), grid.c0, grid.dc, grid.n_c, n_threads=cores)
         times.append(time.perf_counter() - t0)
@@ -221,9 +338,10 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_models_per_step": per_step},
+            "config": {"workload": WORKLOADS[args.workload], "sample_models_per_step": per_step},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{per_step} models x 200 wavelengths per step"},
+                             "sample": f"{per_step} models per step (every {stride}th model), "
+                                       "all their wavelengths"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -280,37 +398,250 @@ def counting_evals(models, grid, idx, st, nlim, n32):
     return e32, e64_counted, e64_fallback, float(np.mean(counted))
 
 
-def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, sms):
+def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, sms, workload):
     """Roofline of the dominant kernel of a counting-search scan, the fused
     search + FP64 certificate: its FP64 work (2 layer-evaluation chains per
     counted item) against the FP64 pipe, from algorithmic layer evaluations /
     device time. Its FP32 search work runs on the FP32 pipe beside it and is
-    reported separately."""
+    reported separately. Also the linear scan's count (Algorithm 1's
+    (idx + 1)(N + 1) layer-evaluations per item) and how much of it the
+    counting search leaves out."""
     e32, e64, e64_fb, frac_counted = counting_evals(models, grid, idx, st, nlim, n32)
+    linear = algorithmic_layer_evals(models, idx, st, nlim)
     peak32 = FP32_FFMA_PER_CLK_SM * 2.0 * sms * SM_MAX_MHZ * 1e6
     t0 = phases[0] * 1e-3
     achieved = e64 * F_LAYER_FLOPS / t0
+    cap = CERTIFY_DRAM_BYTES.get(workload)
     return {"bound": "alu", "unit": "TFLOP/s",
             "achieved": achieved / 1e12, "peak": peak64 / 1e12, "frac": achieved / peak64,
-            "traffic": CERTIFY_DRAM_BYTES_FIXED + CERTIFY_DRAM_BYTES_PER_MODEL * models.n_models,
+            "traffic": None if cap is None else cap[0] * models.n_models / cap[1],
             "kernel": "count_certify_kernel (FP64 pipe; FP32 search alongside)",
             "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
+            "frac_of_fp64_microbenchmark": achieved / micro,
             "layer_evals_per_launch": e64, "flops_per_layer_eval": F_LAYER_FLOPS,
+            "kernel_ms": phases[0],
             "search_layer_evals_fp32": e32,
             "search_fp32_frac_of_fp32_peak": e32 * F_LAYER_FLOPS_FP32 / t0 / peak32,
             "fallback_check_layer_evals_fp64": e64_fb,
-            "phases_ms": {"count_certify": phases[0], "fallback": phases[1],
-                          "resolve64": phases[2]},
+            "linear_scan_layer_evals": linear,
+            "linear_scan_over_counting_evals": linear / max(1, e32 + e64 + e64_fb),
+            "phases_ms": {"count_certify": phases[0],
+                          "fallback_check_search": phases[1], "resolve64": phases[2]},
             "counted_fraction": frac_counted,
             "fp64_peak_microbenchmark": micro / 1e12}
 
 
+def device_steps(torch, step, steps, flush, stream, after=None):
+    """CUDA-event times (ms) of ``steps`` calls of ``step`` on ``stream``, L2
+    flushed before each; ``after`` is called after each step has finished."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        if after:
+            after()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def kernel_phases(torch, masw, batch, step, steps, flush, stream):
+    """Per-kernel device times of the scan (ms, mean over ``steps`` timed
+    steps): the same kernels launched without the graph, so that CUDA events
+    on the batch stream sit between them (masw_last_scan_phases)."""
+    plan = batch.plan()
+    batch.set_plan(use_graph=0)
+    ph = []
+    device_steps(torch, step, steps, flush, stream,
+                 after=lambda: ph.append(masw.last_scan_phases(batch.handle)))
+    batch.set_plan(use_graph=plan.use_graph)
+    return [float(np.mean([p[i] for p in ph])) for i in range(3)]
+
+
+def e2e_rate(torch, masw, models, grid, ce_host, plan, steps, warmup, n_pipe):
+    """End to end through the C ABI with host buffers, every step: the models
+    (h, alpha, beta, rho) and the observed curve C_e uploaded from pinned host
+    memory (masw_model_batch_update, masw_misfit_curves), Algorithms 1 and 2,
+    and the curves (C_t, index, status) and the misfit read back into pinned
+    host memory. With n_pipe > 1 the steps alternate between n_pipe batches,
+    each on its own stream and host thread, so one step's copies overlap
+    another's kernels. Returns (curves/s, H2D bytes, D2H bytes per step)."""
+    import threading
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hh, ha, hb, hr, hce = (pin(x) for x in (models.h, models.alpha, models.beta, models.rho,
+                                            ce_host))
+    streams = [torch.cuda.Stream() for _ in range(n_pipe)]
+    batches = [masw.Batch(models, grid, stream=st.cuda_stream) for st in streams]
+    outs = []
+    for b in batches:
+        masw.set_plan(b.handle, plan)
+        outs.append((torch.empty(models.n_models, dtype=torch.float64).pin_memory(),
+                     torch.empty(models.n_items, dtype=torch.float64).pin_memory(),
+                     torch.empty(models.n_items, dtype=torch.int32).pin_memory(),
+                     torch.empty(models.n_items, dtype=torch.int32).pin_memory()))
+
+    def one(q):
+        masw.model_batch_update(batches[q].handle, hh, ha, hb, hr)
+        masw.misfit_curves(batches[q].handle, hce, masw.MISFIT_LSQ, 2.0, *outs[q])
+
+    for _ in range(warmup):
+        for q in range(n_pipe):
+            one(q)
+    torch.cuda.synchronize()
+    go = threading.Barrier(n_pipe + 1)
+    errors = []
+
+    def worker(q):
+        go.wait()
+        try:
+            for _ in range(q, steps, n_pipe):
+                one(q)
+        except Exception as e:  # surfaced after the join
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(q,)) for q in range(n_pipe)]
+    for t in threads:
+        t.start()
+    go.wait()
+    t0 = time.perf_counter()
+    for t in threads:
+        t.join()
+    elapsed = time.perf_counter() - t0
+    if errors:
+        raise errors[0]
+    for b in batches:
+        b.close()
+    elapsed = sharding.max_over_ranks(elapsed, device="cuda")
+    h2d = sum(x.numel() * x.element_size() for x in (hh, ha, hb, hr, hce))
+    d2h = sum(x.numel() * x.element_size() for x in outs[0])
+    return models.n_models * steps / elapsed, h2d, d2h
+
+
+def measure(args, torch, masw, workload, n_models, rank, world, with_plain=True):
+    """The whole measurement of one workload: device-timed steps (value),
+    clocks, per-kernel times and the roofline of the dominant kernel, the
+    plain one-curve-per-launch path and the end-to-end figures."""
+    stream = torch.cuda.current_stream()
+    models, grid = make_workload(workload, n_models, rank)
+    ce_host = W.noisy_observation(np.full(models.n_items, 250.0), sigma=30.0, seed=rank)
+    batch = masw.Batch(models, grid)
+    if args.precision is not None:
+        batch.set_plan(precision=args.precision)
+    if args.cpl is not None:
+        batch.set_plan(cpl=args.cpl)
+    plan = batch.autotune(reps=3) if args.autotune else batch.plan()
+
+    # results of one pass (parity-checked in tests; used for the algorithmic count)
+    ct, idx, st = batch.dispersion()
+    bhs = np.array([models.model(q)[2][-1] for q in range(models.n_models)])
+    nlim = np.searchsorted(grid.c0 + grid.dc * np.arange(grid.n_c), bhs, side="left")
+    n32 = None
+    if plan.precision >= 1:
+        n32 = np.empty(models.n_items, dtype=np.int32)
+        masw.last_scan_screen(batch.handle, n32)
+    unresolved = batch.last_scan_unresolved()
+    fallback = batch.last_scan_fallback()
+
+    ce = torch.from_numpy(ce_host).cuda()
+    phi = torch.empty(models.n_models, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        masw.misfit(batch.handle, ce, masw.MISFIT_LSQ, 2.0, phi)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    scan_ms = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        step_ms = device_steps(torch, step, args.steps, flush, stream,
+                               after=lambda: scan_ms.append(batch.last_scan_ms()))
+    total_ms = sharding.max_over_ranks(float(np.sum(step_ms)), device="cuda")
+    value = world * models.n_models * args.steps / (total_ms * 1e-3)
+
+    # per-kernel times over the same number of timed steps, graph-free
+    phases = kernel_phases(torch, masw, batch, step, args.steps, flush, stream) \
+        if plan.precision >= 1 else None
+
+    micro = masw.fp64_peak()
+    sms = masw.sm_count()
+    peak = FP64_DFMA_PER_CLK_SM * 2.0 * sms * SM_MAX_MHZ * 1e6
+    units = algorithmic_layer_evals(models, idx, st, nlim)
+    if plan.precision == 2:
+        roofline = counting_roofline(models, grid, idx, st, nlim, n32, phases, peak, micro, sms,
+                                     workload)
+        roofline.update({"scan_ms": float(np.mean(scan_ms)), "unresolved_items": unresolved,
+                         "fallback_items": fallback})
+    elif plan.precision == 0:
+        scan_avg = float(np.mean(scan_ms)) * 1e-3
+        achieved = units * F_LAYER_FLOPS / scan_avg
+        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": SCAN_DRAM_BYTES_PER_MODEL * models.n_models,
+                    "kernel": "scan_kernel (FP64 pipe)",
+                    "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
+                    "peak_microbenchmark": micro / 1e12,
+                    "layer_evals_per_launch": units, "flops_per_layer_eval": F_LAYER_FLOPS,
+                    "executed_layer_evals_per_launch":
+                        executed_layer_evals(models, idx, st, nlim, plan.cpl),
+                    "scan_ms": scan_avg * 1e3}
+    else:
+        peak32 = FP32_FFMA_PER_CLK_SM * 2.0 * sms * SM_MAX_MHZ * 1e6
+        t_screen = phases[0] * 1e-3
+        achieved = units * F_LAYER_FLOPS_FP32 / t_screen
+        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak32 / 1e12,
+                    "unit": "TFLOP/s", "frac": achieved / peak32,
+                    "traffic": SCREEN_DRAM_BYTES_PER_MODEL * models.n_models,
+                    "kernel": "screen32_kernel (FP32 pipe)",
+                    "peak_source": "derived: 128 FFMA/clk/SM x 2 flop x SMs x 2070 MHz",
+                    "layer_evals_per_launch": units,
+                    "flops_per_layer_eval": F_LAYER_FLOPS_FP32,
+                    "scan_ms": float(np.mean(scan_ms)),
+                    "phases_ms": {"screen32": phases[0], "check_search": phases[1],
+                                  "resolve64": phases[2]},
+                    "fp64_peak_derived": peak / 1e12, "fp64_peak_microbenchmark": micro / 1e12,
+                    "unresolved_items": unresolved}
+
+    # plain one-curve-per-launch path (one launch + sync per model)
+    plain = None
+    if with_plain and not args.no_plain:
+        plain_ms = []
+        for _ in range(2):
+            t0 = time.perf_counter()
+            batch.dispersion(plain=True)
+            plain_ms.append(1e3 * (time.perf_counter() - t0))
+        pv = models.n_models / (min(plain_ms) * 1e-3)
+        plain = {"value": pv, "unit": UNIT, "ms_per_step": min(plain_ms),
+                 "speedup_of_batched": value / world / pv}
+
+    # end to end through the C ABI with host buffers: pipelined (the line's
+    # figure) and one batch on one thread (for the gap)
+    e2e_steps = max(args.steps, 2)
+    ev_p, h2d, d2h = e2e_rate(torch, masw, models, grid, ce_host, plan, e2e_steps, args.warmup, 2)
+    ev_1, _, _ = e2e_rate(torch, masw, models, grid, ce_host, plan, e2e_steps, args.warmup, 1)
+    e2e = {"value": world * ev_p, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h,
+           "how": "every step: models + C_e uploaded from pinned host memory, Algorithms 1+2, "
+                  "curves (C_t, index, status) + misfit read back to pinned host memory "
+                  "(masw_model_batch_update + masw_misfit_curves); steps alternate between 2 "
+                  "batches on 2 streams driven by 2 host threads",
+           "one_batch_one_thread": world * ev_1,
+           "frac_of_device_value": ev_p * world / value}
+    batch.close()
+    return {"models": models, "grid": grid, "value": value, "total_ms": total_ms,
+            "step_ms_median": float(np.median(step_ms)), "clocks": clk.summary(),
+            "roofline": roofline, "plan": plan.as_dict(), "plain": plain, "e2e": e2e,
+            "found_fraction": float(np.mean(st == 0)),
+            "launches_per_step": {0: 2, 1: 5, 2: 6}[plan.precision]}
+
+
 def run_extras(args, masw, torch):
-    """Secondary workloads on the same line: the ragged batch (autotuned
-    persistent graph vs one launch per model), the differentiation batch
-    (misfit + adjoint gradient per second) and the serving trace (p50/p99
-    latency and curves/s of the continuous-batching server vs the plain
-    one-request-at-a-time path, per arrival rate)."""
+    """Secondary workloads on the same line."""
     from paper_2003_02256_gb300 import serving
     out = {}
     only = set(args.extras.split(",")) if args.extras else None
@@ -318,13 +649,18 @@ def run_extras(args, masw, torch):
     def want(name):
         return only is None or name in only
 
-    # ragged batch
-    if want("ragged_batch"):
-        out.update(extra_ragged(args, masw))
+    other = "uniform" if args.workload == "ragged" else "ragged"
+    if want(other + "_batch"):
+        r = measure(args, torch, masw, other, DEFAULT_MODELS[other], 0, 1)
+        out[other + "_batch"] = {
+            "workload": WORKLOADS[other], "value": r["value"], "unit": UNIT,
+            "ms_per_step": r["total_ms"] / args.steps, "clocks": r["clocks"],
+            "roofline": r["roofline"], "plain_gpu": r["plain"], "e2e": r["e2e"],
+            "plan": r["plan"]}
+    if want("autotune"):
+        out.update(extra_autotune(args, masw, torch))
     if want("differentiation") or want("inversion"):
         out.update(extra_differentiation_inversion(masw, torch))
-    if want("partition_study"):
-        out.update(extra_partition_study(masw))
     if want("uniform_stress"):
         out.update(extra_uniform_stress(masw))
     if want("higher_modes"):
@@ -333,30 +669,37 @@ def run_extras(args, masw, torch):
         out.update(extra_leaky(masw, torch))
     if want("first_call"):
         out.update(extra_first_call(masw))
+    if want("noalloc"):
+        out.update(extra_noalloc(masw, torch))
     if want("serving"):
-        out.update(extra_serving(args, serving))
+        out.update(extra_serving(args, serving, masw))
     return out
 
 
-def extra_ragged(args, masw):
-    out = {}
-    m3, g3 = W.ragged_batch(n_models=args.ragged_models)
+def extra_autotune(args, masw, torch):
+    """The autotuner's plan against the default plan on the ragged batch:
+    median of 10 scans each (CUDA events on the batch stream)."""
+    m3, g3 = W.ragged_batch()
     with masw.Batch(m3, g3) as b:
-        plan = b.autotune(reps=1)
-        b.dispersion()
-        times = []
-        for _ in range(2):
+        default = b.plan()
+
+        def med():
             b.dispersion()
-            times.append(b.last_scan_ms())
+            t = []
+            for _ in range(10):
+                b.dispersion()
+                t.append(b.last_scan_ms())
+            return float(np.median(t))
+
+        t_default = med()
         t0 = time.perf_counter()
-        b.dispersion(plain=True)
-        plain_s = time.perf_counter() - t0
-    out["ragged_batch"] = {
-        "workload": f"{m3.n_models} models, N~U{{3..30}}, n_lambda~U{{30..400}} log-spaced to "
-                    "2x total depth, 10% low-velocity layer; c grid 50..1200 step 0.25",
-        "items": m3.n_items, "batched_curves_per_s": m3.n_models / (min(times) * 1e-3),
-        "plain_curves_per_s": m3.n_models / plain_s, "plan": plan.as_dict()}
-    return out
+        tuned = b.autotune(reps=3)
+        t_tune = time.perf_counter() - t0
+        t_tuned = med()
+    return {"autotune": {"workload": "ragged_batch (8192 models), scan only, host outputs",
+                         "default_plan": default.as_dict(), "default_scan_ms": t_default,
+                         "tuned_plan": tuned.as_dict(), "tuned_scan_ms": t_tuned,
+                         "tuning_s": t_tune}}
 
 
 def extra_differentiation_inversion(masw, torch):
@@ -368,13 +711,14 @@ def extra_differentiation_inversion(masw, torch):
     with masw.Batch(m4, g4) as b:
         b.misfit_grad(ce)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        reps = 2
-        for _ in range(reps):
+        ts = []
+        for _ in range(10):
+            t0 = time.perf_counter()
             b.misfit_grad(ce)
-        dt = (time.perf_counter() - t0) / reps
+            ts.append(time.perf_counter() - t0)
+        dt = float(np.median(ts))
     out["differentiation"] = {"workload": "512 models x 12 layers, 150 wavelengths, LSQ misfit "
-                                          "+ adjoint gradient (beta, h)",
+                                          "+ adjoint gradient (beta, h), host outputs",
                               "gradients_per_s": m4.n_models / dt, "ms_per_batch": 1e3 * dt}
     # inversion loops (one inversion per model of the differentiation batch)
     from paper_2003_02256_gb300 import inversion
@@ -398,30 +742,6 @@ def extra_differentiation_inversion(masw, torch):
                         "misfit_ratio_after_10_steps": float(np.median(hist[-1] / hist[0])),
                         "metropolis_chain_steps_per_s": m4.n_models * 20 / t_mc,
                         "metropolis_acceptance": float(np.mean(acc))}
-
-    return out
-
-
-def extra_partition_study(masw):
-    out = {}
-    # partition study (Section 3.2): per-wavelength work of Algorithm 1 on a
-    # 40-wavelength decreasing curve, split over P ranks contiguously or modularly
-    m1, g1 = W.single_curve()
-    lam = sharding.variable_curve_wavelengths(40)
-    var = W.Models(m1.n_layers, m1.h, m1.alpha, m1.beta, m1.rho,
-                   np.array([lam.size], np.int32), lam)
-    with masw.Batch(var, g1) as b:
-        _, vidx, vst = b.dispersion()
-    work = vidx.astype(np.float64) + 1.0
-    out["partition_study"] = {
-        "workload": "single-curve model, 40 log-spaced decreasing wavelengths 60..1 m, "
-                    "work = determinants evaluated by Algorithm 1 (idx + 1)",
-        "speedup": {str(P): {"modular": sharding.partition_speedup(work, P, "modular"),
-                             "contiguous": sharding.partition_speedup(work, P, "contiguous")}
-                    for P in (1, 2, 3, 4, 8, 16, 20, 24)},
-        "paper_section_3_2": {"3": {"modular": 2.8, "contiguous": 1.9},
-                              "8": {"modular": 7.0, "contiguous": 4.2}}}
-
     return out
 
 
@@ -553,54 +873,149 @@ def extra_first_call(masw):
     return out
 
 
-def extra_serving(args, serving):
+def extra_noalloc(masw, torch):
+    """The allocation-free entry point (plain FP64 scan, items in natural
+    order) against masw_dispersion (default plan, graph-replayed) on the
+    largest uniform batch it accepts: 320 models x 200 wavelengths (64,000
+    items), device inputs and outputs; median of 5 calls each, CUDA events on
+    the current stream."""
+    m, g = W.uniform_batch(n_models=320)
+    stream = torch.cuda.current_stream()
+    arrs = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
+            (m.n_layers.astype(np.int32), m.h, m.alpha, m.beta, m.rho,
+             m.n_lambda.astype(np.int32), m.lam)]
+    out = [torch.empty(m.n_items, dtype=t, device="cuda")
+           for t in (torch.float64, torch.int32, torch.int32)]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    t_na = timed(lambda: masw.dispersion_noalloc(*arrs, (g.c0, g.dc, g.n_c), *out))
+    idx_na = out[1].cpu().numpy()
+    with masw.Batch(m, g) as b:
+        t_b = timed(lambda: masw.dispersion(b.handle, *out))
+        same = bool(np.array_equal(out[1].cpu().numpy(), idx_na))
+    return {"noalloc": {"workload": "uniform_batch, 320 models x 200 wavelengths (64,000 items), "
+                                    "device inputs and outputs",
+                        "noalloc_ms": t_na, "noalloc_curves_per_s": m.n_models / (t_na * 1e-3),
+                        "dispersion_ms": t_b, "dispersion_curves_per_s": m.n_models / (t_b * 1e-3),
+                        "identical_indices": same,
+                        "noalloc_plan": "plain FP64 scan, one warp per item, natural order"}}
+
+
+def plain_per_request(masw, reqs, arrival_s, grid, limit_s=10.0):
+    """The plain per-request path: each request, when it arrives (or when the
+    previous one has finished), gets its own batch (masw_model_batch_create),
+    one masw_dispersion_plain call (one launch per curve, synchronised) and
+    masw_model_batch_destroy. Returns per-request latencies (s); requests not
+    started within ``limit_s`` are left out (the count is returned)."""
+    hoff, loff, woff = reqs.layer_offsets()
+    lat = []
+    t0 = time.perf_counter()
+    for i in range(reqs.n_models):
+        now = time.perf_counter() - t0
+        if now > limit_s:
+            break
+        if arrival_s[i] > now:
+            time.sleep(arrival_s[i] - now)
+        one = reqs.subset([i])
+        with masw.Batch(one, grid) as b:
+            b.dispersion(plain=True)
+        lat.append(time.perf_counter() - t0 - arrival_s[i])
+    return np.asarray(lat), len(lat)
+
+
+def extra_serving(args, serving, masw):
+    """Serving: a seeded random-walk trace (one model per request, 3..30
+    layers, 30..400 wavelengths), Poisson arrivals. The full trace
+    (``--serving-requests``, 200k by default) is replayed at 1e4 and 1e5 per
+    second; the other rates replay a bounded prefix. Beside the continuous-
+    batching server: the same trace through a one-slot server (one request at
+    a time, on the device path of the server) and through the plain
+    per-request path (batch create + masw_dispersion_plain + destroy), both on
+    a prefix; and the admission cap binding (a 64 MB cap on the 1e5/s trace)."""
     out = {}
-    # serving
     sampler = W.RandomWalkSampler()
-    reqs = W.concat([sampler.next() for _ in range(args.serving_requests)])
+    t0 = time.perf_counter()
+    n_full = args.serving_requests
+    reqs_full = W.concat([sampler.next() for _ in range(n_full)])
+    gen_s = time.perf_counter() - t0
     grid = W.Grid(50.0, 0.25, 4601)
+    n_prefix = min(2000, n_full)
+    prefix = reqs_full.subset(range(n_prefix))
     rates = {}
     for rate in (1e3, 3e3, 1e4, 3e4, 1e5, 1e6):
+        full = rate in (1e4, 1e5)
+        reqs = reqs_full if full else prefix
         arr = W.poisson_arrivals(reqs.n_models, rate=rate)
         with serving.Server(grid, max_slots=2048, chunks_per_tick=8,
                             mem_cap_bytes=16 << 30) as srv:
             lat, _, _, _, st = srv.run_trace(reqs, arr)
-        with serving.Server(grid, max_slots=1, chunks_per_tick=1 << 20) as plain:
-            lat_p, _, _, _, _ = plain.run_trace(reqs, arr)
-        rates[f"{rate:g}"] = {"served": serving.latency_summary(lat, arr, reqs.n_models),
-                              "plain": serving.latency_summary(lat_p, arr, reqs.n_models),
-                              "ticks": st["ticks"], "max_in_flight": st["max_in_flight"]}
-    out["serving"] = {"workload": f"{reqs.n_models} random-walk model evaluations per rate "
-                                  "(layers 3..30, wavelengths 30..400), Poisson arrivals, "
-                                  "16 GB admission cap", "rates_per_s": rates}
+        row = {"requests": reqs.n_models, "served": serving.latency_summary(lat, arr, reqs.n_models),
+               "ticks": st["ticks"], "refused": st["refused"], "max_in_flight": st["max_in_flight"]}
+        arr_p = W.poisson_arrivals(n_prefix, rate=rate)
+        with serving.Server(grid, max_slots=1, chunks_per_tick=1 << 20) as one_slot:
+            lat_1, _, _, _, _ = one_slot.run_trace(prefix, arr_p)
+        row["one_slot_server"] = dict(serving.latency_summary(lat_1, arr_p, n_prefix),
+                                      requests=n_prefix)
+        lat_p, done = plain_per_request(masw, prefix, arr_p, grid)
+        row["plain_per_request"] = dict(serving.latency_summary(lat_p, arr_p[:done], done),
+                                        requests=done)
+        rates[f"{rate:g}"] = row
+    # admission by memory: the 1e5/s trace under a 64 MB cap
+    cap = 64 << 20
+    arr = W.poisson_arrivals(reqs_full.n_models, rate=1e5)
+    with serving.Server(grid, max_slots=2048, chunks_per_tick=8, mem_cap_bytes=cap) as srv:
+        lat, _, _, _, st = srv.run_trace(reqs_full, arr)
+    capped = {"mem_cap_bytes": cap, "rate_per_s": 1e5, "requests": reqs_full.n_models,
+              "served": serving.latency_summary(lat, arr, reqs_full.n_models),
+              "ticks": st["ticks"], "refused": st["refused"], "max_in_flight": st["max_in_flight"]}
+    out["serving"] = {"workload": f"random-walk model evaluations (layers 3..30, wavelengths "
+                                  f"30..400), Poisson arrivals, 16 GB admission cap; "
+                                  f"{n_full} requests at 1e4 and 1e5 per s, the first "
+                                  f"{n_prefix} at the other rates and on the plain arms "
+                                  "(one-slot server; per-request batch + masw_dispersion_plain)",
+                      "trace_generation_s": gen_s, "rates_per_s": rates,
+                      "admission_cap_binding": capped}
     return out
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="ragged", choices=["ragged", "uniform"],
+                    help="main workload (the line's config)")
+    ap.add_argument("--models", type=int, default=None,
+                    help="models per GPU (default: the workload's own; smaller only for "
+                         "profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="autotune the plan before timing (default: the library's plan)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--extras", default=None,
-                    help="comma-separated subset of the extras (ragged_batch, differentiation, "
-                         "inversion, partition_study, uniform_stress, higher_modes, leaky, "
-                         "first_call, serving); default all")
-    ap.add_argument("--ragged-models", type=int, default=8192)
-    ap.add_argument("--serving-requests", type=int, default=2000)
+                    help="comma-separated subset of the extras (uniform_batch or ragged_batch, "
+                         "autotune, differentiation, inversion, uniform_stress, higher_modes, "
+                         "leaky, first_call, noalloc, serving); default all")
+    ap.add_argument("--serving-requests", type=int, default=200000)
     ap.add_argument("--precision", type=int, default=None, choices=[0, 1, 2],
                     help="scan plan: 0 FP64 scan, 1 FP32 screen + FP64 decision, 2 counting "
                          "search + FP64 certificate (default: library)")
     ap.add_argument("--cpl", type=int, default=None, choices=[1, 2, 4],
                     help="scan plan test velocities per lane (2: paired FP32x2 screen)")
-    ap.add_argument("--workload", default="uniform", choices=["uniform", "ragged"],
-                    help="main workload (ragged only for profiling the ragged batch)")
-    ap.add_argument("--models", type=int, default=1024,
-                    help="models per GPU (smaller only for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -614,151 +1029,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    stream = torch.cuda.current_stream()
 
-    # weak scaling: the job's models are world x args.models seeded models; rank r
-    # evaluates its contiguous shard (seeded per shard), no data-path collective
-    if args.workload == "uniform":
-        models, grid = W.uniform_batch(n_models=args.models, seed=W.SEED + 1000 * rank)
-    else:
-        models, grid = W.ragged_batch(n_models=args.models, seed=W.SEED + 3 + 1000 * rank)
-    ce_host = W.noisy_observation(np.full(models.n_items, 250.0), sigma=30.0, seed=rank)
-    batch = masw.Batch(models, grid)
-    if args.precision is not None:
-        batch.set_plan(precision=args.precision)
-    if args.cpl is not None:
-        batch.set_plan(cpl=args.cpl)
-    if not args.no_autotune:
-        plan = batch.autotune(reps=1)
-    else:
-        plan = batch.plan()
-
-    # results of one pass (parity-checked in tests; used for the algorithmic count)
-    ct, idx, st = batch.dispersion()
-    nlim = np.array([int(np.sum(grid.c0 + np.arange(grid.n_c) * grid.dc < models.model(m)[2][-1]))
-                     for m in range(models.n_models)])
-    units = algorithmic_layer_evals(models, idx, st, nlim)
-    executed = executed_layer_evals(models, idx, st, nlim, plan.cpl)
-
-    ce = torch.from_numpy(ce_host).cuda()
-    phi = torch.empty(models.n_models, dtype=torch.float64, device="cuda")
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    def step():
-        masw.misfit(batch.handle, ce, masw.MISFIT_LSQ, 2.0, phi)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    scan_ms = []
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-            torch.cuda.synchronize()
-            scan_ms.append(batch.last_scan_ms())
-        torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(np.sum(step_ms))
-    total_ms = sharding.max_over_ranks(total_ms, device="cuda")
-    value = world * models.n_models * args.steps / (total_ms * 1e-3)
-
-    # plain one-curve-per-launch path (same kernel body, one launch + sync per model)
-    plain_ms = []
-    for _ in range(0 if args.no_plain else 2):
-        t0 = time.perf_counter()
-        batch.dispersion(plain=True)
-        plain_ms.append(1e3 * (time.perf_counter() - t0))
-    plain_value = models.n_models / (min(plain_ms) * 1e-3) if plain_ms else None
-
-    # end to end through the C ABI with host buffers: upload of the step's
-    # model parameters and C_e from pinned memory, misfit read back to host
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-    hh, ha, hb, hr, hce = (pin(x) for x in (models.h, models.alpha, models.beta, models.rho, ce_host))
-    hphi = torch.empty(models.n_models, dtype=torch.float64).pin_memory()
-    e2e_ms = []
-    for k in range(args.warmup + args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        masw.model_batch_update(batch.handle, hh, ha, hb, hr)
-        masw.misfit(batch.handle, hce, masw.MISFIT_LSQ, 2.0, hphi)
-        torch.cuda.synchronize()
-        if k >= args.warmup:
-            e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_total = float(np.sum(e2e_ms))
-    e2e_total = sharding.max_over_ranks(e2e_total, device="cuda")
-    e2e_value = world * models.n_models * args.steps / (e2e_total * 1e-3)
-    h2d = sum(x.numel() * 8 for x in (hh, ha, hb, hr, hce))
-    d2h = hphi.numel() * 8
-
-    # per-kernel device times of the two-precision scan (same kernels, launched
-    # without the graph so events can sit between them)
-    phases = None
-    unresolved = None
-    fallback = None
-    n32 = None
-    if plan.precision >= 1:
-        batch.set_plan(use_graph=0)
-        ph = []
-        for _ in range(3):
-            flush.zero_()
-            batch.dispersion()
-            ph.append(masw.last_scan_phases(batch.handle))
-        unresolved = batch.last_scan_unresolved()
-        fallback = batch.last_scan_fallback()
-        n32 = np.empty(models.n_items, dtype=np.int32)
-        masw.last_scan_screen(batch.handle, n32)
-        batch.set_plan(use_graph=plan.use_graph)
-        phases = [float(np.mean([p[i] for p in ph])) for i in range(3)]
-
-    # roofline of the scan kernel: algorithmic FP64 flops / device time, against
-    # the FP64 peak derived from unit counts and the maximum SM clock
-    # (2 DFMA per clock per SM x 2 flops x SMs x 2070 MHz); the live DFMA
-    # microbenchmark is reported beside it
-    micro = masw.fp64_peak()
-    peak = FP64_DFMA_PER_CLK_SM * 2.0 * masw.sm_count() * SM_MAX_MHZ * 1e6
-    scan_avg = float(np.mean(scan_ms)) * 1e-3
-    if phases is None:
-        achieved = units * F_LAYER_FLOPS / scan_avg
-        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                    "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": SCAN_DRAM_BYTES_PER_MODEL * models.n_models,
-                    "kernel": "scan_kernel (FP64 pipe)",
-                    "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
-                    "peak_microbenchmark": micro / 1e12,
-                    "layer_evals_per_launch": units, "flops_per_layer_eval": F_LAYER_FLOPS,
-                    "executed_layer_evals_per_launch": executed,
-                    "scan_ms": scan_avg * 1e3}
-    elif plan.precision == 2:
-        roofline = counting_roofline(models, grid, idx, st, nlim, n32, phases, peak, micro,
-                                     masw.sm_count())
-        roofline.update({"scan_ms": scan_avg * 1e3, "unresolved_items": unresolved,
-                         "fallback_items": fallback})
-    else:
-        peak32 = FP32_FFMA_PER_CLK_SM * 2.0 * masw.sm_count() * SM_MAX_MHZ * 1e6
-        t_screen = phases[0] * 1e-3
-        achieved = units * F_LAYER_FLOPS_FP32 / t_screen
-        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak32 / 1e12,
-                    "unit": "TFLOP/s", "frac": achieved / peak32,
-                    "traffic": SCREEN_DRAM_BYTES_PER_MODEL * models.n_models,
-                    "kernel": "screen32_kernel (FP32 pipe)",
-                    "peak_source": "derived: 128 FFMA/clk/SM x 2 flop x SMs x 2070 MHz",
-                    "layer_evals_per_launch": units,
-                    "flops_per_layer_eval": F_LAYER_FLOPS_FP32,
-                    "executed_layer_evals_per_launch": executed,
-                    "scan_ms": scan_avg * 1e3,
-                    "phases_ms": {"screen32": phases[0], "verify64": phases[1],
-                                  "resolve64": phases[2]},
-                    "fp64_peak_derived": peak / 1e12, "fp64_peak_microbenchmark": micro / 1e12,
-                    "unresolved_items": unresolved}
+    n_models = args.models or DEFAULT_MODELS[args.workload]
+    r = measure(args, torch, masw, args.workload, n_models, rank, world)
+    models, grid = r["models"], r["grid"]
 
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
@@ -766,45 +1040,45 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample = cpu_oracle_rate(models, grid, min(256, models.n_models))
-        v1, _, sample1 = cpu_oracle_rate(models, grid, min(8, models.n_models), threads=1)
-        vb, _, sample_b = cpu_oracle_rate(models, grid, min(512, models.n_models), banded=True)
-        vb1, _, sample_b1 = cpu_oracle_rate(models, grid, min(16, models.n_models), threads=1,
-                                            banded=True)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-               "single_thread": {"value": v1, "unit": UNIT, "sample": sample1},
+        stride = max(1, models.n_models // 256)
+        sample = np.arange(0, models.n_models, stride)[:256]
+        v, cores, desc = cpu_oracle_rate(models, grid, sample)
+        v1, _, desc1 = cpu_oracle_rate(models, grid, sample[:8], threads=1)
+        vb, _, desc_b = cpu_oracle_rate(models, grid, sample, banded=True)
+        vb1, _, desc_b1 = cpu_oracle_rate(models, grid, sample[:8], threads=1, banded=True)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "single_thread": {"value": v1, "unit": UNIT, "sample": desc1},
                "banded": {"value": vb, "unit": UNIT, "cores": cores,
                           "kind": "CPU banded elimination (the paper's serial C, sparse variant, "
                                   "restated; pinned to the oracle)",
-                          "sample": sample_b,
-                          "single_thread": {"value": vb1, "unit": UNIT, "sample": sample_b1}}}
+                          "sample": desc_b,
+                          "single_thread": {"value": vb1, "unit": UNIT, "sample": desc_b1}},
+               "partition_study": cpu_partition_study()}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "models_per_gpu": models.n_models,
-                           "items_per_gpu": models.n_items, "seed": W.SEED,
+                "config": {"workload": WORKLOADS[args.workload],
+                           "models_per_gpu": models.n_models, "items_per_gpu": models.n_items,
+                           "seed": int(models.meta.get("seed", W.SEED)),
                            "l2": "flushed between timed steps (256 MB write)",
                            "step": "Algorithm 1 scan of every item + Algorithm 2 misfit",
-                           "plan": plan.as_dict(), "parallelism": f"replicas x{world}"},
-                "clocks": clk.summary(),
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h},
+                           "step_ms_median": r["step_ms_median"],
+                           "plan": r["plan"], "parallelism": f"replicas x{world}"},
+                "clocks": r["clocks"],
+                "e2e": r["e2e"],
                 # per step: the scan's kernels (precision 0: scan; 1: screen, check,
                 # mode-count search, re-scan; 2: counting search + certificate,
                 # fallback scan, check, mode-count search, re-scan) and the misfit
-                "gpu_launches": {0: 2, 1: 5, 2: 6}[plan.precision] * args.steps,
-                "roofline": roofline,
+                "gpu_launches": r["launches_per_step"] * args.steps,
+                "roofline": r["roofline"],
                 "cpu_baseline": cpu,
-                "plain_gpu": None if plain_value is None else {
-                    "value": plain_value, "unit": UNIT, "ms_per_step": min(plain_ms),
-                    "speedup_of_batched": value / world / plain_value},
-                "found_fraction": float(np.mean(st == 0)),
+                "plain_gpu": r["plain"],
+                "found_fraction": r["found_fraction"],
                 "extras": extras}
         print(json.dumps(line), flush=True)
-    batch.close()
     if dist:
         dist.destroy_process_group()
 

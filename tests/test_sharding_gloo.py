@@ -119,3 +119,18 @@ def test_a_failed_rank_surfaces_as_an_error_on_the_others(tmp_path):
     status, elapsed = open(out).read().split()
     assert status.startswith("error:"), status
     assert float(elapsed) < 60.0
+
+
+def test_timed_partition_study_on_cpu_ranks():
+    """The timed CPU-rank study of Section 3.2 (spawned processes running the
+    oracle on their shares) gathers exactly the one-rank indices for both
+    partitions and reports a wall time and a speedup per rank count."""
+    import bench
+    out = bench.cpu_partition_study(ranks=(1, 2, 3), reps=2)
+    assert set(out["ranks"]) == {"1", "2", "3"}
+    for P, row in out["ranks"].items():
+        for mode in ("contiguous", "modular"):
+            assert row[mode]["wall_s"] > 0 and row[mode]["speedup"] > 0
+            assert row[mode]["cost_model_speedup"] >= 1.0
+    assert out["ranks"]["3"]["modular"]["cost_model_speedup"] > \
+        out["ranks"]["3"]["contiguous"]["cost_model_speedup"]
