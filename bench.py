@@ -97,7 +97,10 @@ SM_MAX_MHZ = 2070.0
 # (bytes, models of that launch); the records, wavenumbers and item tables are
 # read once, the outputs stay in L2. Scaled by the models of a launch; None
 # where no capture of the current kernel exists.
-CERTIFY_DRAM_BYTES = {"uniform": (3.492096e6, 1024), "ragged": None}
+# uniform: 3.49 MB for the 1024-model launch; ragged: 8.73 MB for the launch
+# over the first 2048 models (429,978 items), scaled by the algorithmic bytes
+# (records, wavenumbers, item tables: x 4.024) to the 8192-model launch.
+CERTIFY_DRAM_BYTES = {"uniform": (3.492864e6, 1024), "ragged": (35.152e6, 8192)}
 # DRAM bytes (read + write) of one scan launch per model, from the ncu capture
 # of the 64-model case (281.6 KB read, 0 written), scaled by the models of a
 # launch; traffic grows with the number of items.
@@ -568,7 +571,8 @@ def measure(args, torch, masw, workload, n_models, rank, world, with_plain=True)
     phases = kernel_phases(torch, masw, batch, step, args.steps, flush, stream) \
         if plan.precision >= 1 else None
 
-    micro = masw.fp64_peak()
+    with ClockSampler(torch.cuda.current_device()) as clk_micro:
+        micro = float(np.median([masw.fp64_peak() for _ in range(3)]))
     sms = masw.sm_count()
     peak = FP64_DFMA_PER_CLK_SM * 2.0 * sms * SM_MAX_MHZ * 1e6
     units = algorithmic_layer_evals(models, idx, st, nlim)
@@ -576,7 +580,8 @@ def measure(args, torch, masw, workload, n_models, rank, world, with_plain=True)
         roofline = counting_roofline(models, grid, idx, st, nlim, n32, phases, peak, micro, sms,
                                      workload)
         roofline.update({"scan_ms": float(np.mean(scan_ms)), "unresolved_items": unresolved,
-                         "fallback_items": fallback})
+                         "fallback_items": fallback,
+                         "fp64_peak_microbenchmark_clocks": clk_micro.summary()})
     elif plan.precision == 0:
         scan_avg = float(np.mean(scan_ms)) * 1e-3
         achieved = units * F_LAYER_FLOPS / scan_avg
@@ -972,21 +977,40 @@ def extra_serving(args, serving, masw):
         row["plain_per_request"] = dict(serving.latency_summary(lat_p, arr_p[:done], done),
                                         requests=done)
         rates[f"{rate:g}"] = row
-    # admission by memory: the 1e5/s trace under a 64 MB cap
-    cap = 64 << 20
+    # admission by memory: the 1e5/s trace under a 1 MB cap (the trace holds
+    # up to ~1000 requests of a few KB each in flight, far below 16 GB)
+    cap = 1 << 20
     arr = W.poisson_arrivals(reqs_full.n_models, rate=1e5)
     with serving.Server(grid, max_slots=2048, chunks_per_tick=8, mem_cap_bytes=cap) as srv:
         lat, _, _, _, st = srv.run_trace(reqs_full, arr)
     capped = {"mem_cap_bytes": cap, "rate_per_s": 1e5, "requests": reqs_full.n_models,
               "served": serving.latency_summary(lat, arr, reqs_full.n_models),
               "ticks": st["ticks"], "refused": st["refused"], "max_in_flight": st["max_in_flight"]}
+    # where a tick's time goes: the profiled server on the 1e5/s trace and at
+    # 1e6/s (the served ceiling), per-tick means of the device parts (CUDA
+    # events between them) and of the host's launch, finish and admission
+    ticks_prof = {}
+    for rate, reqs in ((1e5, reqs_full), (1e6, prefix)):
+        arr = W.poisson_arrivals(reqs.n_models, rate=rate)
+        with serving.Server(grid, max_slots=2048, chunks_per_tick=8,
+                            mem_cap_bytes=16 << 30) as srv:
+            srv.profile(True)
+            t0 = time.perf_counter()
+            lat, _, _, _, st = srv.run_trace(reqs, arr)
+            wall = time.perf_counter() - t0
+            prof = srv.profile(False)
+        n = max(prof["ticks"], 1.0)
+        ticks_prof[f"{rate:g}"] = dict(
+            {k: v / n for k, v in prof.items() if k != "ticks"}, ticks=prof["ticks"],
+            requests=reqs.n_models, wall_ms_per_tick=1e3 * wall / n,
+            served=serving.latency_summary(lat, arr, reqs.n_models))
     out["serving"] = {"workload": f"random-walk model evaluations (layers 3..30, wavelengths "
                                   f"30..400), Poisson arrivals, 16 GB admission cap; "
                                   f"{n_full} requests at 1e4 and 1e5 per s, the first "
                                   f"{n_prefix} at the other rates and on the plain arms "
                                   "(one-slot server; per-request batch + masw_dispersion_plain)",
                       "trace_generation_s": gen_s, "rates_per_s": rates,
-                      "admission_cap_binding": capped}
+                      "admission_cap_binding": capped, "tick_profile_ms_per_tick": ticks_prof}
     return out
 
 

@@ -109,6 +109,9 @@ typedef struct {
                                 the pole-free bound min_i beta_i sqrt(1 + (pi/(k h_i))^2)),
                                 certified in FP64 by count 0 at V[n-1] and odd at V[n]; items
                                 outside the bound take the linear screen of 1. Default: 2 */
+    int32_t count_block;     /* precision 2: threads per block of the counting kernel, 64, 128
+                                (default) or 256 (two lanes per item, items of a block
+                                consecutive; launch bounds of 14, 7 or 3 resident blocks) */
 } masw_plan;
 
 /* Copy and validate a model batch into batch-owned device memory and bind it
@@ -221,9 +224,12 @@ int masw_det_eval(masw_batch* batch, int32_t n, const int32_t* item, const doubl
 int masw_get_plan(const masw_batch* batch, masw_plan* plan);
 int masw_set_plan(masw_batch* batch, const masw_plan* plan);
 
-/* Time candidate plans on this batch (reps timed scans each, CUDA events on
- * the batch stream), keep the fastest, return it in *best (may be NULL).
- * Results never depend on the plan. Winners are cached per (max layers,
+/* Time candidate plans on this batch (median of reps timed scans each,
+ * CUDA events on the batch stream), keep the fastest, return it in *best
+ * (may be NULL). The search is staged: the counting kernel's block size
+ * (precision 2), then warps_per_block x blocks_per_sm, then cpl x ordered,
+ * each stage keeping the best of the previous ones, and last the flat
+ * (non-persistent) launch. Results never depend on the plan. Winners are cached per (max layers,
  * n_c, item-count bucket) in-process and, when the environment variable
  * MASW_PLAN_CACHE names a file, across processes. */
 int masw_autotune(masw_batch* batch, int32_t reps, masw_plan* best);
@@ -432,6 +438,20 @@ int masw_server_get_stats(const masw_server* server, masw_server_stats* stats);
  * scan from V[0], one chunk per tick. Applies from the next tick; results must
  * not change. MASW_EINVAL outside 0..3. */
 int masw_server_set_route(masw_server* server, int32_t route);
+
+/* Opt-in profile of the server's ticks, for measurement: enable = 1 starts
+ * it (zeroing the totals; it waits for the server's stream once), 0 stops
+ * it; out (may be NULL) receives MASW_SERVER_PROFILE_VALUES totals:
+ *   [0] ticks profiled;
+ *   device milliseconds (CUDA events between the parts of each tick):
+ *   [1] upload and scatter of the newly admitted requests, [2] count kernel
+ *   (counting search + certificate of the new items), [3] tick kernel (linear
+ *   FP32 chunks), [4] check kernel, [5] read-back of counters and done list;
+ *   host milliseconds: [6] launching ticks (staging included), [7] finishing
+ *   ticks (the wait for the tick's event included), [8] admitting requests
+ *   (masw_server_submit). While on, every tick records six more events. */
+#define MASW_SERVER_PROFILE_VALUES 9
+int masw_server_profile(masw_server* server, int32_t enable, double* out);
 
 /* Replay a request trace natively: request i (concatenated host arrays as in
  * masw_models_desc) arrives arrival_s[i] seconds (non-decreasing) after the

@@ -333,6 +333,7 @@ static masw_plan default_plan(const masw_batch* B) {
     p.stage_layers = std::min(B->max_layers + 1, 32);
     p.use_graph = 1;
     p.precision = 2;
+    p.count_block = 128;
     return p;
 }
 
@@ -340,7 +341,8 @@ static bool plan_ok(const masw_plan& p) {
     bool wpb = p.warps_per_block == 1 || p.warps_per_block == 2 || p.warps_per_block == 4 ||
                p.warps_per_block == 8;
     bool cpl = p.cpl == 1 || p.cpl == 2 || p.cpl == 4;
-    return wpb && cpl && p.precision >= 0 && p.precision <= 2 && p.blocks_per_sm >= 1 &&
+    bool cb = p.count_block == 64 || p.count_block == 128 || p.count_block == 256;
+    return wpb && cpl && cb && p.precision >= 0 && p.precision <= 2 && p.blocks_per_sm >= 1 &&
            p.blocks_per_sm <= 32 && p.stage_layers >= 0 &&
            p.stage_layers <= MASW_MAX_LAYERS + 1 &&
            (size_t)p.warps_per_block * p.stage_layers * LAYER_STRIDE * sizeof(double) <= 48 * 1024;
@@ -353,6 +355,7 @@ static ScanPlan to_scan_plan(const masw_batch* B, const masw_plan& p) {
     s.blocks = p.blocks_per_sm * B->sm_count;
     s.persistent = p.persistent;
     s.stage_layers = p.stage_layers;
+    s.count_block = p.count_block;
     return s;
 }
 
@@ -1067,9 +1070,9 @@ void load_cache_file() {
     if (!f) return;
     int a, b, c;
     masw_plan p;
-    while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d", &a, &b, &c, &p.warps_per_block, &p.cpl,
-                  &p.blocks_per_sm, &p.persistent, &p.ordered, &p.stage_layers, &p.use_graph,
-                  &p.precision) == 11)
+    while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d", &a, &b, &c, &p.warps_per_block,
+                  &p.cpl, &p.blocks_per_sm, &p.persistent, &p.ordered, &p.stage_layers,
+                  &p.use_graph, &p.precision, &p.count_block) == 12)
         if (plan_ok(p)) g_cache[{a, b, c}] = p;
     fclose(f);
 }
@@ -1081,9 +1084,10 @@ void save_cache_file() {
     if (!f) return;
     for (auto& kv : g_cache) {
         const masw_plan& p = kv.second;
-        fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first),
+        fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first),
                 std::get<1>(kv.first), std::get<2>(kv.first), p.warps_per_block, p.cpl,
-                p.blocks_per_sm, p.persistent, p.ordered, p.stage_layers, p.use_graph, p.precision);
+                p.blocks_per_sm, p.persistent, p.ordered, p.stage_layers, p.use_graph, p.precision,
+                p.count_block);
     }
     fclose(f);
 }
@@ -1103,35 +1107,78 @@ int masw_autotune(masw_batch* B, int32_t reps, masw_plan* best) {
             return MASW_OK;
         }
     }
-    std::vector<masw_plan> cands;
-    int stage = std::min(B->max_layers + 1, 32);
-    for (int wpb : {2, 4, 8})
-        for (int cpl : {1, 2})
-            for (int bps : {2, 4, 8, 16}) {
-                masw_plan p{wpb, cpl, bps, 1, 1, stage, 1, B->plan.precision};
-                if (plan_ok(p)) cands.push_back(p);
-            }
-    masw_plan flat{8, 1, 1, 0, 1, stage, 1, B->plan.precision};
-    if (plan_ok(flat)) cands.push_back(flat);
-    float best_ms = 1e30f;
-    masw_plan bestp = B->plan;
-    for (const masw_plan& p : cands) {
+    // median of reps timed scans (one warm-up scan first) of a candidate
+    auto time_plan = [&](const masw_plan& p, float* ms_out) -> int {
         int rc = masw_set_plan(B, &p);
         if (rc) return rc;
         if ((rc = run_scan(B))) return rc;  // warm-up
-        float tot = 0.f;
+        std::vector<float> t;
         for (int r = 0; r < reps; ++r) {
             if ((rc = run_scan(B))) return rc;
             float ms;
             if ((rc = masw_last_scan_ms(B, &ms))) return rc;
-            tot += ms;
+            t.push_back(ms);
         }
-        if (tot / reps < best_ms) {
-            best_ms = tot / reps;
+        std::sort(t.begin(), t.end());
+        *ms_out = t[t.size() / 2];
+        return MASW_OK;
+    };
+    masw_plan bestp = B->plan;
+    bestp.persistent = 1;
+    bestp.use_graph = 1;
+    bestp.stage_layers = std::min(B->max_layers + 1, 32);
+    float best_ms = 1e30f;
+    auto consider = [&](const masw_plan& p) -> int {
+        if (!plan_ok(p)) return MASW_OK;
+        float ms = 0.f;
+        int rc = time_plan(p, &ms);
+        if (rc) return rc;
+        if (ms < best_ms) {
+            best_ms = ms;
             bestp = p;
         }
+        return MASW_OK;
+    };
+    int rc = consider(bestp);
+    // stage 1: the counting kernel's block size (its launch bounds follow)
+    if (!rc && bestp.precision == 2) {
+        const masw_plan base = bestp;
+        for (int cb : {64, 128, 256}) {
+            masw_plan p = base;
+            p.count_block = cb;
+            if ((rc = consider(p))) break;
+        }
     }
-    int rc = masw_set_plan(B, &bestp);
+    // stage 2: warps per block x persistent blocks per SM of the other kernels
+    if (!rc) {
+        const masw_plan base = bestp;
+        for (int wpb : {1, 2, 4, 8})
+            for (int bps : {1, 2, 4, 8, 16}) {
+                masw_plan p = base;
+                p.warps_per_block = wpb;
+                p.blocks_per_sm = bps;
+                if ((rc = consider(p))) break;
+            }
+    }
+    // stage 3: test velocities per lane x queue order
+    if (!rc) {
+        const masw_plan base = bestp;
+        for (int cpl : {1, 2, 4})
+            for (int ord : {0, 1}) {
+                masw_plan p = base;
+                p.cpl = cpl;
+                p.ordered = ord;
+                if ((rc = consider(p))) break;
+            }
+    }
+    // last: one item per warp, no queue
+    if (!rc) {
+        masw_plan p = bestp;
+        p.persistent = 0;
+        rc = consider(p);
+    }
+    if (rc) return rc;
+    rc = masw_set_plan(B, &bestp);
     if (rc) return rc;
     {
         std::lock_guard<std::mutex> lk(g_cache_mu);

@@ -77,6 +77,13 @@ __device__ __forceinline__ bool abs_lt(double x, double y) {
     return (__double_as_longlong(x) & MAG_MASK) < (__double_as_longlong(y) & MAG_MASK);
 }
 __device__ __forceinline__ int sgn(double x) { return (int)gt0(x) - (int)lt0(x); }
+// w * x < 0 for the FP64 product, for a weight w with |w| in [1, 2) (the
+// recurrence's normalised weight): the product is negative exactly when w
+// and x are nonzero non-NaN numbers of opposite sign (with |w| >= 1 it never
+// underflows to zero). Integer pipe only.
+__device__ __forceinline__ bool wprod_lt0(double w, double x) {
+    return (lt0(w) && gt0(x)) || (gt0(w) && lt0(x));
+}
 
 // 2^-(exponent of x) for a normal x; returns false for 0, subnormal, inf, NaN
 // or a value so large that the scale would be subnormal.
@@ -904,19 +911,19 @@ __device__ inline int det_inertia(const double* __restrict__ lay, int N, double 
     double sv[3];
     for (int j = 0; j < N; ++j) {
         LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2);
-        double f = st.w * n.Dh;
+        const bool f_neg = wprod_lt0(st.w, n.Dh);  // sign of w Dh, the pivot's scale
         bool ok;
         double det = schur_layer(st, n, &ok, sv);
-        cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(sv[0]) != lt0(f)) ? 2 : 0) : 1);
+        cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(sv[0]) != f_neg) ? 2 : 0) : 1);
         if (!ok) return -1;
     }
     HalfNum hn = halfspace_numerators(lay + N * LAYER_STRIDE, c2);
-    double f = st.w * hn.den;
+    const bool f_neg = wprod_lt0(st.w, hn.den);
     double s00 = fma(hn.den, st.p00, st.w * hn.m00);
     double s01 = fma(hn.den, st.p01, st.w * hn.m01);
     double s11 = fma(hn.den, st.p11, st.w * hn.m11);
     double det = fma(s00, s11, -s01 * s01);
-    cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(s00) != lt0(f)) ? 2 : 0) : 1);
+    cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(s00) != f_neg) ? 2 : 0) : 1);
     return cnt;
 }
 
@@ -931,23 +938,23 @@ __device__ inline int det_sign_count(const double* __restrict__ lay, int N, doub
     double sv[3];
     for (int j = 0; j < N; ++j) {
         LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2);
-        double f = st.w * n.Dh;
+        const bool f_neg = wprod_lt0(st.w, n.Dh);
         bool ok;
         double det = schur_layer(st, n, &ok, sv);
         sg *= sgn(det);
-        cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(sv[0]) != lt0(f)) ? 2 : 0) : 1);
+        cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(sv[0]) != f_neg) ? 2 : 0) : 1);
         if (!ok) {
             *count = -1;
             return 0;
         }
     }
     HalfNum hn = halfspace_numerators(lay + N * LAYER_STRIDE, c2);
-    double f = st.w * hn.den;
+    const bool f_neg = wprod_lt0(st.w, hn.den);
     double s00 = fma(hn.den, st.p00, st.w * hn.m00);
     double s01 = fma(hn.den, st.p01, st.w * hn.m01);
     double s11 = fma(hn.den, st.p11, st.w * hn.m11);
     double det = fma(s00, s11, -s01 * s01);
-    cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(s00) != lt0(f)) ? 2 : 0) : 1);
+    cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(s00) != f_neg) ? 2 : 0) : 1);
     *count = cnt;
     return sg * sgn(det);
 }

@@ -497,8 +497,12 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
 // lies above the pole-free range, at V[0], or behind an even FP64 count go to
 // the fallback list (linear FP32 scan and mode-count check); uncertified items
 // go to the FP64 mode-count search. Certified items keep SCREEN_COUNTED in
-// n32.
-__global__ void __launch_bounds__(128, 7) count_certify_kernel(DevBatch b, const float* __restrict__ layers32,
+// n32. B threads per block (plan count_block: 64, 128 or 256), each block's
+// B/2 items consecutive, so its warps share the records of one or two models
+// in L1; the launch bounds ask for 896 resident threads per SM (at most 73
+// registers a thread) for B = 64 and 128, and 768 for 256.
+template <int B>
+__global__ void __launch_bounds__(B, (B == 256 ? 3 : 896 / B)) count_certify_kernel(DevBatch b, const float* __restrict__ layers32,
                                                                ScanOut o, int32_t* __restrict__ n32,
                                                                int32_t* search, int32_t* n_search,
                                                                int32_t* fallback, int32_t* n_fallback,
@@ -697,9 +701,27 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
     size_t shm = (size_t)wpb * p.stage_layers * LAYER_STRIDE32 * sizeof(float);
     int n = item_end - item_begin;
     if (counting) {
-        count_certify_kernel<<<(2 * n + 127) / 128, 128, 0, s>>>(b, layers32, o, n32, search,
-                                                                 counters + 5, fallback,
-                                                                 counters + 3, item_begin, item_end);
+        const int cb = p.count_block;
+        const int grid = (2 * n + cb - 1) / cb;
+        switch (cb) {
+            case 64:
+                count_certify_kernel<64><<<grid, 64, 0, s>>>(b, layers32, o, n32, search,
+                                                             counters + 5, fallback, counters + 3,
+                                                             item_begin, item_end);
+                break;
+            case 128:
+                count_certify_kernel<128><<<grid, 128, 0, s>>>(b, layers32, o, n32, search,
+                                                               counters + 5, fallback, counters + 3,
+                                                               item_begin, item_end);
+                break;
+            case 256:
+                count_certify_kernel<256><<<grid, 256, 0, s>>>(b, layers32, o, n32, search,
+                                                               counters + 5, fallback, counters + 3,
+                                                               item_begin, item_end);
+                break;
+            default:
+                return cudaErrorInvalidValue;
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (phase_ev && (e = cudaEventRecord(phase_ev[0], s)) != cudaSuccess) return e;
         fallback32_kernel<<<std::max(1, std::min(p.blocks, n)), 256,

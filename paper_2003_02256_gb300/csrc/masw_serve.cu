@@ -387,6 +387,12 @@ struct masw_server {
     int32_t pending_active = 0;  // new items of a launched, unfinished tick
     int64_t ticks = 0;
     int64_t completed = 0;
+    // opt-in tick profile (masw_server_profile): events between the parts of
+    // a tick, accumulated when the tick finishes
+    bool prof = false;
+    bool prof_pending = false;          // the launched tick recorded its events
+    cudaEvent_t pev[6] = {};            // start, scatter, count, tick, check, read-back done
+    double prof_acc[MASW_SERVER_PROFILE_VALUES] = {};
 };
 
 namespace {
@@ -402,6 +408,8 @@ void server_free(masw_server* S) {
     for (void* p : host)
         if (p) cudaFreeHost(p);
     if (S->ev) cudaEventDestroy(S->ev);
+    for (cudaEvent_t e : S->pev)
+        if (e) cudaEventDestroy(e);
     delete S;
 }
 
@@ -438,11 +446,17 @@ int run_tick(masw_server* S) {
     if (rc == MASW_OK && launched) rc = tick_finish(S);
     return rc;
 }
+// Profile event k of the tick being launched (no-op unless profiling).
+bool prof_mark(masw_server* S, int k) {
+    return !S->prof || cudaEventRecord(S->pev[k], S->stream) == cudaSuccess;
+}
 int tick_launch_impl(masw_server* S, bool* launched) {
     *launched = false;
     S->just_done.clear();
     int n_new = (int)S->pending.size();
     if (S->n_active + n_new == 0) return MASW_OK;
+    const double t_host = S->prof ? now_s() : 0.0;
+    if (!prof_mark(S, 0)) return MASW_ECUDA;
     const int32_t* new_items = nullptr;
     if (n_new) {
         // one transfer: staged blocks, then descriptors, then the new item ids
@@ -465,6 +479,7 @@ int tick_launch_impl(masw_server* S, bool* launched) {
         S->upload_used = 0;
         S->up_cur = 1 - S->up_cur;  // later submits stage into the other half
     }
+    if (!prof_mark(S, 1)) return MASW_ECUDA;
     if (cudaMemsetAsync(S->v.counters, 0, 3 * sizeof(int32_t), S->stream) != cudaSuccess)
         return MASW_ECUDA;
     if (n_new) {
@@ -472,6 +487,7 @@ int tick_launch_impl(masw_server* S, bool* launched) {
             S->v, new_items, n_new, S->active[1 - S->cur], S->grid.c0, S->grid.dc);
         if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
     }
+    if (!prof_mark(S, 2)) return MASW_ECUDA;
     if (S->n_active) {
         int wpb = S->cfg.warps_per_block;
         int blocks = (S->n_active + wpb - 1) / wpb;
@@ -482,21 +498,41 @@ int tick_launch_impl(masw_server* S, bool* launched) {
                                                                 S->grid.dc);
         if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
     }
+    if (!prof_mark(S, 3)) return MASW_ECUDA;
     // every item that entered the check list this tick (at most n_active)
     serve_check_kernel<<<(2 * S->n_active + 127) / 128 + 1, 128, 0, S->stream>>>(
         S->v, S->check, S->v.counters + 2, S->active[1 - S->cur], S->grid.c0, S->grid.dc);
     if (cudaGetLastError() != cudaSuccess) return MASW_ECUDA;
+    if (!prof_mark(S, 4)) return MASW_ECUDA;
     // counters and the done list (first counters[1] entries) come back together
     if (cudaMemcpyAsync(S->h_counters, S->v.counters, (4 + S->cfg.max_slots) * sizeof(int32_t),
                         cudaMemcpyDeviceToHost, S->stream) != cudaSuccess ||
-        cudaEventRecord(S->ev, S->stream) != cudaSuccess)
+        !prof_mark(S, 5) || cudaEventRecord(S->ev, S->stream) != cudaSuccess)
         return MASW_ECUDA;
     S->pending_active = n_new;  // items of this tick (for the stats until it finishes)
     *launched = true;
+    if (S->prof) {
+        S->prof_pending = true;
+        S->prof_acc[6] += 1e3 * (now_s() - t_host);
+    }
     return MASW_OK;
 }
 int tick_finish_impl(masw_server* S) {
+    const double t_host = S->prof ? now_s() : 0.0;
     if (cudaEventSynchronize(S->ev) != cudaSuccess) return MASW_ECUDA;
+    if (S->prof_pending) {
+        // device time of each part of the tick; the event after the read-back
+        // has completed, so every earlier one has too
+        for (int k = 0; k < 5; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, S->pev[k], S->pev[k + 1]) != cudaSuccess)
+                return MASW_ECUDA;
+            S->prof_acc[1 + k] += ms;
+        }
+        S->prof_acc[0] += 1.0;
+        S->prof_acc[7] += 1e3 * (now_s() - t_host);
+        S->prof_pending = false;
+    }
     int survivors = S->h_counters[0], n_done = S->h_counters[1];
     for (int i = 0; i < n_done; ++i) {
         S->slot_done[S->h_done[i]] = 1;
@@ -605,9 +641,39 @@ int masw_server_destroy(masw_server* S) {
     return MASW_OK;
 }
 
+static int server_submit(masw_server* S, int32_t n_layers, const double* h, const double* alpha,
+                         const double* beta, const double* rho, int32_t n_lambda,
+                         const double* lambda, int64_t* request_id);
+
 int masw_server_submit(masw_server* S, int32_t n_layers, const double* h, const double* alpha,
                        const double* beta, const double* rho, int32_t n_lambda,
                        const double* lambda, int64_t* request_id) {
+    if (!S || !S->prof) return server_submit(S, n_layers, h, alpha, beta, rho, n_lambda, lambda,
+                                             request_id);
+    const double t = now_s();
+    const int rc = server_submit(S, n_layers, h, alpha, beta, rho, n_lambda, lambda, request_id);
+    S->prof_acc[8] += 1e3 * (now_s() - t);
+    return rc;
+}
+
+int masw_server_profile(masw_server* S, int32_t enable, double* out) {
+    if (!S || (enable != 0 && enable != 1)) return MASW_EINVAL;
+    if (enable && !S->prof) {
+        if (cudaStreamSynchronize(S->stream) != cudaSuccess) return MASW_ECUDA;
+        for (cudaEvent_t& e : S->pev)
+            if (!e && cudaEventCreate(&e) != cudaSuccess) return MASW_ECUDA;
+        for (double& v : S->prof_acc) v = 0.0;
+        S->prof_pending = false;
+    }
+    S->prof = enable == 1;
+    if (out)
+        for (int k = 0; k < MASW_SERVER_PROFILE_VALUES; ++k) out[k] = S->prof_acc[k];
+    return MASW_OK;
+}
+
+static int server_submit(masw_server* S, int32_t n_layers, const double* h, const double* alpha,
+                         const double* beta, const double* rho, int32_t n_lambda,
+                         const double* lambda, int64_t* request_id) {
     if (!S || !alpha || !beta || !rho || !lambda || !request_id || (n_layers > 0 && !h))
         return MASW_EINVAL;
     if (n_layers < 0 || n_layers > S->cfg.max_layers || n_lambda < 1 || n_lambda > S->v.imax)

@@ -46,7 +46,8 @@ class Plan(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_int32), ("cpl", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("ordered", ctypes.c_int32), ("stage_layers", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("count_block", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -123,6 +123,21 @@ class Server:
         f.restype = ctypes.c_int
         masw._check(f(ctypes.c_void_p(self.handle), int(route)), "masw_server_set_route")
 
+    PROFILE_KEYS = ("ticks", "upload_scatter_ms", "count_kernel_ms", "tick_kernel_ms",
+                    "check_kernel_ms", "readback_ms", "host_launch_ms", "host_finish_ms",
+                    "host_admit_ms")
+
+    def profile(self, enable: bool) -> dict:
+        """masw_server_profile: start (and zero) or stop the per-tick profile;
+        returns the totals so far (device and host milliseconds)."""
+        f = _lib().masw_server_profile
+        f.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+        f.restype = ctypes.c_int
+        out = np.zeros(len(self.PROFILE_KEYS))
+        masw._check(f(ctypes.c_void_p(self.handle), int(bool(enable)), _p(out)),
+                    "masw_server_profile")
+        return dict(zip(self.PROFILE_KEYS, out.tolist()))
+
     def stats(self) -> dict:
         s = ServerStats()
         masw._check(_lib().masw_server_get_stats(ctypes.c_void_p(self.handle), ctypes.byref(s)),

@@ -63,3 +63,4 @@ def test_new_entry_points_reject_bad_arguments_without_the_gpu(lib):
     assert lib.masw_test_fail_alloc(i32(-1)) == 0
     d = ctypes.c_double
     assert lib.masw_misfit_curves(None, None, i32(1), d(2.0), None, None, None, None) == 1
+    assert lib.masw_server_profile(None, i32(1), None) == 1

@@ -117,6 +117,29 @@ def test_plain_per_request_mode_matches(env):
     assert s["p99_ms"] >= s["p50_ms"] > 0
 
 
+def test_tick_profile_changes_nothing_and_accounts_for_every_tick(env):
+    """masw_server_profile: with the profile on, results are those of the
+    batch entry point, every tick is profiled, every part's time is finite
+    and non-negative, and turning it off freezes the totals."""
+    masw, serving = env
+    reqs = requests(40, seed=11)
+    grid = W.Grid(50.0, 0.25, 4601)
+    with masw.Batch(reqs, grid) as b:
+        _, ref_idx, ref_st = b.dispersion()
+    arr = W.poisson_arrivals(reqs.n_models, rate=5e4, seed=4)
+    with serving.Server(grid, max_slots=16, chunks_per_tick=2) as srv:
+        zero = srv.profile(True)
+        assert all(v == 0.0 for v in zero.values())
+        _, _, idx, st, stats = srv.run_trace(reqs, arr)
+        prof = srv.profile(False)
+        assert srv.profile(False) == prof
+    assert np.array_equal(idx, ref_idx) and np.array_equal(st, ref_st)
+    assert prof["ticks"] == stats["ticks"]
+    vals = np.array(list(prof.values()))
+    assert np.isfinite(vals).all() and (vals >= 0).all()
+    assert prof["count_kernel_ms"] > 0 and prof["host_admit_ms"] > 0
+
+
 def test_fallback_items_match_the_batch_path(env):
     """Items whose change lies above the pole-free bound or below V[0] leave
     the counting search for the linear screen; served results still equal
