@@ -74,11 +74,10 @@ def make_workload(name: str, n_models: int, rank: int = 0):
 # FP64 flops per layer-evaluation (element assembly + one Schur step):
 # 2*DFMA + DMUL + DADD executed per evaluated (layer, c) pair, from ncu
 # instruction counters of the fused counting kernel's FP64 certificate on the
-# 128-model case of this workload (23.07 M DFMA, 19.57 M DMUL, 3.70 M DADD over
-# 460,800 layer-evaluations; profiles/). Every FP64 kernel runs the same
-# element and Schur arithmetic. (The plain FP64 scan measured 162.3 before the
-# exponential, rescaling and comparison changes.)
-F_LAYER_FLOPS = 150.6
+# full 1024-model uniform launch (186.6 M DFMA, 143.0 M DMUL, 33.3 M DADD over
+# 3,686,400 layer-evaluations; profiles/). Every FP64 kernel runs the same
+# element and Schur arithmetic.
+F_LAYER_FLOPS = 149.1
 # FP32 flops per layer-evaluation of the screen kernel (2*FFMA + FMUL + FADD
 # per executed (layer, c) pair: 29.6 FFMA, 54.2 FMUL, 16.4 FADD; ncu
 # instruction counters of the 64-model case, profiles/).

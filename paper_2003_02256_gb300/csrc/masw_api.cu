@@ -261,6 +261,7 @@ static void build_records(masw_batch* B, const std::vector<double>& h, const std
             L[L_IB2] = 1.0 / (b[il] * b[il]);
             L[L_BETA] = b[il];
             L[L_RATIO] = a[il] / b[il];
+            L[L_IRHO] = 1.0 / r[il];
         }
     }
 }
@@ -356,6 +357,7 @@ static ScanPlan to_scan_plan(const masw_batch* B, const masw_plan& p) {
     s.persistent = p.persistent;
     s.stage_layers = p.stage_layers;
     s.count_block = p.count_block;
+    s.sms = B->sm_count;
     return s;
 }
 

@@ -46,7 +46,8 @@
 namespace masw {
 
 // Per-layer record in device memory (one 64-byte line per layer).
-enum LayerField { L_H = 0, L_MU = 1, L_RHO = 2, L_IA2 = 3, L_IB2 = 4, L_BETA = 5, L_RATIO = 6 };
+enum LayerField { L_H = 0, L_MU = 1, L_RHO = 2, L_IA2 = 3, L_IB2 = 4, L_BETA = 5, L_RATIO = 6,
+                  L_IRHO = 7 };
 constexpr int LAYER_STRIDE = 8;
 
 // |(k h w)^2| below this threshold uses the Taylor series of cosh and sinh.
@@ -725,14 +726,18 @@ __device__ __forceinline__ Wave wave_fns(double kh, double kh2, double w2) {
     return o;
 }
 
-// Numerators of one layer's element stiffness over the common denominator Dh
+// Numerators of one layer's element stiffness over a common denominator Dh
 // (k dropped): K11 = [[n00, n01], [n01, n11]] / Dh, K22 = same with -n01,
-// K12 = [[ce, cf], [-cf, cg]] / Dh.
+// K12 = [[ce, cf], [-cf, cg]] / Dh. In the closed form every numerator but b's
+// carries the factor rho c^2, and b's carries mu = rho c^2 / q; here rho c^2
+// goes into the denominator (Dh = D / (rho c^2)) and b's numerator takes
+// mu / (rho c^2) = beta^2 / c^2, so one reciprocal of c^2 per evaluation (ic2)
+// replaces six of the seven scaling products per layer.
 struct LayerNum { double Dh, n00, n01, n11, ce, cf, cg; };
 
 __device__ __forceinline__ LayerNum layer_numerators(const double* __restrict__ L, double k,
-                                                     double c2) {
-    double h = L[L_H], mu = L[L_MU], rho = L[L_RHO], ia2 = L[L_IA2], ib2 = L[L_IB2];
+                                                     double c2, double ic2) {
+    double h = L[L_H], mu = L[L_MU], ia2 = L[L_IA2], ib2 = L[L_IB2];
     double kh = k * h;
     double q = c2 * ib2;
     double r2 = fma(-c2, ia2, 1.0);
@@ -750,17 +755,20 @@ __device__ __forceinline__ LayerNum layer_numerators(const double* __restrict__ 
     double E1 = fma(R.Sm, S.E, -R.E * S.Sd);
     double F1 = fma(R.E, S.C, -R.C * S.E);
     double G1 = fma(S.Sm, R.E, -S.E * R.Sd);
-    double rc2 = rho * c2;
+    const double irc2 = L[L_IRHO] * ic2;  // 1 / (rho c^2)
     LayerNum o;
-    o.Dh = Dh;
-    o.n00 = rc2 * A1;
-    o.n01 = mu * B1;
-    o.n11 = rc2 * D1;
-    o.ce = rc2 * E1;
-    o.cf = rc2 * F1;
-    o.cg = rc2 * G1;
+    o.Dh = Dh * irc2;
+    o.n00 = A1;
+    o.n01 = (mu * irc2) * B1;
+    o.n11 = D1;
+    o.ce = E1;
+    o.cf = F1;
+    o.cg = G1;
     return o;
 }
+
+// 1 / c^2 for layer_numerators, once per evaluation (correctly rounded).
+__device__ __forceinline__ double inv_c2(double c2) { return __drcp_rn(c2); }
 
 // Homogeneous Schur state: P = (p00, p01; p01, p11) / w.
 struct HState { double p00, p01, p11, w; };
@@ -824,10 +832,11 @@ __device__ __forceinline__ HalfNum halfspace_numerators(const double* __restrict
 // (N finite layers, then the half-space). Requires c < beta_halfspace.
 __device__ __forceinline__ int det_sign(const double* __restrict__ lay, int N, double k, double c) {
     double c2 = c * c;
+    const double ic2 = inv_c2(c2);
     HState st{0.0, 0.0, 0.0, 1.0};
     int sg = 1;
     for (int j = 0; j < N; ++j) {
-        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2);
+        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2, ic2);
         bool ok;
         double det = schur_layer(st, n, &ok);
         sg *= sgn(det);
@@ -853,10 +862,11 @@ __device__ __forceinline__ int det_sign(const double* __restrict__ lay, int N, d
 // no division. Below the shear speed this is det_sign's arithmetic exactly.
 __device__ inline int det_sign_leaky(const double* __restrict__ lay, int N, double k, double c) {
     double c2 = c * c;
+    const double ic2 = inv_c2(c2);
     HState st{0.0, 0.0, 0.0, 1.0};
     int sg = 1;
     for (int j = 0; j < N; ++j) {
-        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2);
+        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2, ic2);
         bool ok;
         double det = schur_layer(st, n, &ok);
         sg *= sgn(det);
@@ -906,11 +916,12 @@ __device__ inline int det_sign_leaky(const double* __restrict__ lay, int N, doub
 // det_sign reports (same arithmetic). Requires c < beta_halfspace.
 __device__ inline int det_inertia(const double* __restrict__ lay, int N, double k, double c) {
     double c2 = c * c;
+    const double ic2 = inv_c2(c2);
     HState st{0.0, 0.0, 0.0, 1.0};
     int cnt = 0;
     double sv[3];
     for (int j = 0; j < N; ++j) {
-        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2);
+        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2, ic2);
         const bool f_neg = wprod_lt0(st.w, n.Dh);  // sign of w Dh, the pivot's scale
         bool ok;
         double det = schur_layer(st, n, &ok, sv);
@@ -933,11 +944,12 @@ __device__ inline int det_inertia(const double* __restrict__ lay, int N, double 
 __device__ inline int det_sign_count(const double* __restrict__ lay, int N, double k, double c,
                                      int* count) {
     double c2 = c * c;
+    const double ic2 = inv_c2(c2);
     HState st{0.0, 0.0, 0.0, 1.0};
     int sg = 1, cnt = 0;
     double sv[3];
     for (int j = 0; j < N; ++j) {
-        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2);
+        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2, ic2);
         const bool f_neg = wprod_lt0(st.w, n.Dh);
         bool ok;
         double det = schur_layer(st, n, &ok, sv);
@@ -1034,11 +1046,12 @@ __device__ __forceinline__ double split_pow2(double x, int* e) {
 __device__ inline double det_scaled(const double* __restrict__ lay, int N, double k, double c,
                                     int* e2) {
     double c2 = c * c;
+    const double ic2 = inv_c2(c2);
     HState st{0.0, 0.0, 0.0, 1.0};
     double num = 1.0, den = 1.0;
     int e = 0, ea, eb;
     for (int j = 0; j < N; ++j) {
-        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2);
+        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2, ic2);
         const double wD = st.w * n.Dh;
         bool ok;
         const double det = schur_layer(st, n, &ok);
@@ -1065,11 +1078,12 @@ __device__ inline double det_scaled(const double* __restrict__ lay, int N, doubl
 __device__ inline int det_sign_log(const double* __restrict__ lay, int N, double k, double c,
                                    double* log_abs) {
     double c2 = c * c;
+    const double ic2 = inv_c2(c2);
     HState st{0.0, 0.0, 0.0, 1.0};
     int sg = 1;
     double la = 0.0;  // sum of ln|det S_j|, det S_j = det Shat / (w Dh)^2
     for (int j = 0; j < N; ++j) {
-        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2);
+        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2, ic2);
         double wD = st.w * n.Dh;
         bool ok;
         double det = schur_layer(st, n, &ok);

@@ -757,13 +757,17 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
                                                         item_end);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    first_count64_kernel<SEARCH_LANES><<<std::max(1, std::min(p.blocks, (n + wpb - 1) / wpb)),
-                                         32 * wpb, 0, s>>>(b, o, n32, search, counters + 5,
-                                                           counters + 6, unresolved, counters + 1);
+    // The mode-count search and the FP64 re-scan work through short lists
+    // (0.1 % and none of the ragged batch's items): one warp per block and up
+    // to 8 blocks per SM spread the list over every SM, where blocks of
+    // several warps would stack a list of a thousand items on a few SMs.
+    const int lblocks = std::max(1, std::min(8 * (p.sms > 0 ? p.sms : 152), n));
+    first_count64_kernel<SEARCH_LANES><<<lblocks, 32, 0, s>>>(b, o, n32, search, counters + 5,
+                                                             counters + 6, unresolved,
+                                                             counters + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (phase_ev && (e = cudaEventRecord(phase_ev[1], s)) != cudaSuccess) return e;
-    int rblocks = std::max(1, std::min(p.blocks, (n + wpb - 1) / wpb));
-    resolve64_kernel<<<rblocks, 32 * wpb, 0, s>>>(b, o, unresolved, counters + 1, counters + 2);
+    resolve64_kernel<<<lblocks, 32, 0, s>>>(b, o, unresolved, counters + 1, counters + 2);
     return cudaGetLastError();
 }
 
@@ -1219,7 +1223,7 @@ __device__ __forceinline__ void st(double* p, M2 m) { p[0] = m.a; p[1] = m.b; p[
 // from the layer's symmetry: K22 = [[A, -B], [-B, Dd]], K21 = K12^T).
 __device__ __forceinline__ void elem_blocks(const double* L, double k, double c2, M2* K11, M2* K12,
                                             M2* K21, M2* K22) {
-    LayerNum n = layer_numerators(L, k, c2);
+    LayerNum n = layer_numerators(L, k, c2, inv_c2(c2));
     double id = 1.0 / n.Dh;
     double A = n.n00 * id, B = n.n01 * id, Dd = n.n11 * id;
     double E = n.ce * id, F = n.cf * id, G = n.cg * id;
@@ -1533,7 +1537,7 @@ __global__ void __launch_bounds__(128) build_records_kernel(DevBatch b, const do
         L[L_IB2] = ib2;
         L[L_BETA] = be;
         L[L_RATIO] = a / be;
-        L[7] = 0.0;
+        L[L_IRHO] = 1.0 / r;
         float* F = layers32 + (size_t)(lo + i) * LAYER_STRIDE32;
         F[F_H] = (float)lh;
         F[F_MU] = (float)(lmu / mref);

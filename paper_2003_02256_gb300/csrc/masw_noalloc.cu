@@ -142,7 +142,7 @@ __global__ void noalloc_prep_kernel(int n_models, const int32_t* __restrict__ lo
             L[L_IB2] = 1.0 / (b * b);
             L[L_BETA] = b;
             L[L_RATIO] = a / b;
-            L[7] = 0.0;
+            L[L_IRHO] = 1.0 / r;
         }
         // grid points with V[n] < beta of the half-space
         double bhs = beta[rec0 + N];

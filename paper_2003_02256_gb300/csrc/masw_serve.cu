@@ -710,7 +710,7 @@ static int server_submit(masw_server* S, int32_t n_layers, const double* h, cons
         L[L_IB2] = 1.0 / (b * b);
         L[L_BETA] = b;
         L[L_RATIO] = a / b;
-        L[7] = 0.0;
+        L[L_IRHO] = 1.0 / r;
     }
     // FP32 records of the screen (stiffnesses over the half-space shear modulus)
     float* rec32 = (float*)(rec + (size_t)S->v.rmax * LAYER_STRIDE);
