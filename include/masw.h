@@ -363,6 +363,19 @@ int masw_last_scan_fallback(const masw_batch* batch, int32_t* n);
  * cuda_stream. */
 int masw_exp_check(int32_t n, const double* x, double* y_lib, double* y_cuda, void* cuda_stream);
 
+/* The element stiffness of finite layer layer[t] (0-based) of item item[t]'s
+ * model at test velocity c[t] > 0, from the FP64 element and from the
+ * double-float element of the counting certificate; a diagnostic for testing
+ * the latter's accuracy. No paper counterpart. Outputs (host arrays, 7
+ * doubles per point): the common denominator and the numerators
+ * (D, K11 00, K11 01, K11 11, K12 00, K12 01, K12 11) with K = numerator / D
+ * in units of k (the two may scale D and the numerators by different
+ * positive factors; the ratios are the element's entries). MASW_EINVAL for an
+ * item or layer out of range or a non-positive c. Allocates and frees a
+ * device buffer of 16 n doubles; synchronises the batch stream. */
+int masw_element_check(masw_batch* batch, int32_t n, const int32_t* item, const int32_t* layer,
+                       const double* c, double* fp64, double* df);
+
 /* FP64 fused multiply-add throughput of this GPU in flop/s (2 per DFMA),
  * measured by a dependent-chain microbenchmark on `cuda_stream`. */
 int masw_fp64_peak(void* cuda_stream, double* flops);

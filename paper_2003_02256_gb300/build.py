@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libmasw.so")
 SOURCES = ["masw_kernels.cu", "masw_api.cu", "masw_noalloc.cu", "masw_serve.cu"]
 HEADERS = ["masw_device.cuh", "masw_adjoint.cuh", "masw_internal.h", "masw_screen.cuh",
-           "masw_count.cuh", "masw_modes.cuh"]
+           "masw_count.cuh", "masw_modes.cuh", "masw_df.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include")]

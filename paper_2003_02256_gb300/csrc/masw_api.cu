@@ -29,6 +29,7 @@
 
 #include "../../include/masw.h"
 #include "masw_device.cuh"
+#include "masw_df.cuh"
 #include "masw_internal.h"
 #include "masw_screen.cuh"
 
@@ -75,6 +76,7 @@ struct masw_batch {
     double* d_gh = nullptr;
     // two-precision scan
     float* d_layers32 = nullptr;
+    float* d_layers_df = nullptr;  // double-float records of the counting certificate
     int32_t* d_n32 = nullptr;
     int32_t* d_search = nullptr;
     int32_t* d_unres = nullptr;
@@ -105,6 +107,7 @@ struct masw_batch {
     DevBatch dev(bool ordered) const {
         DevBatch b;
         b.layers = d_layers;
+        b.layers_df = d_layers_df;
         b.model_loff = d_loff;
         b.model_nlim = d_nlim;
         b.model_woff = d_woff;
@@ -313,7 +316,7 @@ static void free_batch(masw_batch* B) {
     void* ptrs[] = {B->d_layers, B->d_loff,  B->d_woff,  B->d_nlim,   B->d_k,
                     B->d_item_model, B->d_order_sorted, B->d_order_natural, B->d_grad_off,
                     B->d_counter, B->d_ct, B->d_idx, B->d_status, B->d_croot, B->d_rows, B->d_bs,
-                    B->d_dphi, B->d_ce, B->d_misfit, B->d_gb, B->d_gh, B->d_layers32,
+                    B->d_dphi, B->d_ce, B->d_misfit, B->d_gb, B->d_gh, B->d_layers32, B->d_layers_df,
                     B->d_n32, B->d_search, B->d_unres, B->d_fallback, B->d_counters, B->d_upd, B->d_upd_err,
                     B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta,
                     B->d_chg_counters, B->d_lk_ct, B->d_lk_idx};
@@ -535,6 +538,9 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
     build_records(B, h, a, b, r, rec);
     std::vector<float> rec32;
     build_records32(B, rec, rec32);
+    std::vector<float> recdf((size_t)B->n_records * LAYER_STRIDE_DF);
+    for (int64_t i = 0; i < B->n_records; ++i)
+        df_record(&rec[(size_t)i * LAYER_STRIDE], &recdf[(size_t)i * LAYER_STRIDE_DF]);
 
     if ((rc = masw_sm_count(&B->sm_count))) {
         free_batch(B);
@@ -546,7 +552,8 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
         dev_alloc(&B->d_order_sorted, nw) || dev_alloc(&B->d_order_natural, nw) ||
         dev_alloc(&B->d_grad_off, nw + 1) || dev_alloc(&B->d_counter, 1) ||
         dev_alloc(&B->d_ct, nw) || dev_alloc(&B->d_idx, nw) || dev_alloc(&B->d_status, nw) ||
-        dev_alloc(&B->d_layers32, rec32.size()) || dev_alloc(&B->d_n32, nw) ||
+        dev_alloc(&B->d_layers32, rec32.size()) || dev_alloc(&B->d_layers_df, recdf.size()) ||
+        dev_alloc(&B->d_n32, nw) ||
         dev_alloc(&B->d_search, nw) || dev_alloc(&B->d_unres, nw) || dev_alloc(&B->d_fallback, nw) ||
         dev_alloc(&B->d_counters, SCAN_COUNTERS)) {
         free_batch(B);
@@ -558,6 +565,7 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = up(B->d_layers, rec.data(), rec.size() * sizeof(double));
     if (e == cudaSuccess) e = up(B->d_layers32, rec32.data(), rec32.size() * sizeof(float));
+    if (e == cudaSuccess) e = up(B->d_layers_df, recdf.data(), recdf.size() * sizeof(float));
     if (e == cudaSuccess) e = up(B->d_loff, B->loff.data(), B->loff.size() * 4);
     if (e == cudaSuccess) e = up(B->d_woff, B->woff.data(), B->woff.size() * 4);
     if (e == cudaSuccess) e = up(B->d_nlim, B->nlim.data(), B->nlim.size() * 4);
@@ -622,7 +630,8 @@ int masw_model_batch_update(masw_batch* B, const double* h, const double* alpha,
     // queued after the work already on the batch stream: validation, then the
     // records and scan limits (skipped on a validation error), then the flag
     CK(cudaMemsetAsync(B->d_upd_err, 0, sizeof(int32_t), B->stream));
-    CK(launch_model_update(B->dev(false), dh, da, db, dr, B->d_layers, B->d_layers32, B->d_nlim,
+    CK(launch_model_update(B->dev(false), dh, da, db, dr, B->d_layers, B->d_layers32,
+                           B->d_layers_df, B->d_nlim,
                            B->d_upd_err, B->stream));
     if (mem_space == MASW_HOST) return MASW_OK;
     // device arrays: one synchronisation returns the device check's flag
@@ -649,7 +658,8 @@ int masw_model_batch_update_beta_h(masw_batch* B, const double* h, const double*
     if (hdev) dh = const_cast<double*>(h);
     int32_t herr = 0;
     CK(cudaMemsetAsync(B->d_counter, 0, sizeof(int32_t), B->stream));
-    CK(launch_update_beta_h(B->dev(false), dh, db, B->d_layers, B->d_layers32, B->d_nlim,
+    CK(launch_update_beta_h(B->dev(false), dh, db, B->d_layers, B->d_layers32, B->d_layers_df,
+                            B->d_nlim,
                             B->d_counter, B->stream));
     CK(cudaMemcpyAsync(&herr, B->d_counter, sizeof(int32_t), cudaMemcpyDeviceToHost, B->stream));
     CK(cudaStreamSynchronize(B->stream));
@@ -743,6 +753,39 @@ int masw_dispersion_leaky(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* s
         (rc = copy_out(status, lk_status, nw, B->stream, &sync)))
         return rc;
     if (sync) CK(cudaStreamSynchronize(B->stream));
+    return MASW_OK;
+}
+
+int masw_element_check(masw_batch* B, int32_t n, const int32_t* item, const int32_t* layer,
+                       const double* c, double* fp64, double* df) {
+    if (!B || n < 0 || (n > 0 && (!item || !layer || !c || !fp64 || !df))) return MASW_EINVAL;
+    for (int32_t t = 0; t < n; ++t) {
+        if (item[t] < 0 || item[t] >= B->n_items) return MASW_EINVAL;
+        const int32_t m = B->item_model[item[t]];
+        if (layer[t] < 0 || layer[t] >= B->n_layers[m] || !(std::isfinite(c[t]) && c[t] > 0.0))
+            return MASW_EINVAL;
+    }
+    if (n == 0) return MASW_OK;
+    // one buffer: item, layer (int32 each), c, then the two outputs (7 doubles per point)
+    double* d = nullptr;
+    if (dev_alloc(&d, (size_t)n * 16)) return MASW_ENOMEM;
+    int32_t* d_item = reinterpret_cast<int32_t*>(d);
+    int32_t* d_layer = d_item + n;
+    double* d_c = d + n;
+    double* d_fp = d_c + n;
+    double* d_df = d_fp + 7 * (size_t)n;
+    cudaStream_t s = B->stream;
+    cudaError_t e = cudaMemcpyAsync(d_item, item, n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_layer, layer, n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_c, c, n * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_element_check(B->dev(false), n, d_item, d_layer, d_c, d_fp, d_df, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(fp64, d_fp, 7 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(df, d_df, 7 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    CK(e);
     return MASW_OK;
 }
 

@@ -9,7 +9,8 @@
 //    its midpoint, then splits the bracket in three per step (one point per
 //    lane): about log3(npf) steps instead of Algorithm 1's linear walk. The
 //    first nonzero point goes to the certificate whatever its FP32 parity.
-//  * Certificate (FP64). The count (det_inertia) is 0 at V[n-1] (so 0, and
+//  * Certificate (FP64 recurrence over double-float elements,
+//    det_inertia_df in masw_df.cuh). The count is 0 at V[n-1] (so 0, and
 //    V[0]'s sign, at every point below) and odd at V[n] (the sign differs).
 //    When the FP32 count was off by one next to the change (count 0 at both
 //    points: the change is higher; nonzero at V[n-1]: lower), the pair takes
@@ -22,6 +23,7 @@
 #pragma once
 
 #include "masw_device.cuh"
+#include "masw_df.cuh"
 #include "masw_screen.cuh"
 
 namespace masw {
@@ -74,6 +76,7 @@ __device__ __forceinline__ int pair_search(const float* __restrict__ lay32, int 
 // Both lanes of the pair (lane bit 0 = half, `pair` = their shuffle mask)
 // call this with the same item and get the same result. Requires nlim >= 2.
 __device__ __forceinline__ PairCount count_certify_pair(const float* __restrict__ lay32,
+                                                        const float* __restrict__ laydf,
                                                         const double* __restrict__ lay, int N,
                                                         double k, double c0, double dc, int nlim,
                                                         int half, unsigned pair) {
@@ -90,7 +93,7 @@ __device__ __forceinline__ PairCount count_certify_pair(const float* __restrict_
         return out;
     }
     if (n < 1) return out;  // a mode below V[0]: Algorithm 1 from V[0]
-    const int v = det_inertia(lay, N, k, grid_c(c0, dc, n - 1 + half));
+    const int v = det_inertia_df(laydf, lay, N, k, grid_c(c0, dc, n - 1 + half));
     const int vo = __shfl_xor_sync(pair, v, 1);
     const int va = half ? vo : v;  // V[n-1]
     const int vb = half ? v : vo;  // V[n]
@@ -100,7 +103,7 @@ __device__ __forceinline__ PairCount count_certify_pair(const float* __restrict_
         const bool down = va > 0 && n >= 3;
         if (up || down) {
             const int p = (up ? n + 1 : n - 3) + half;
-            const int w = p < nlim ? det_inertia(lay, N, k, grid_c(c0, dc, p)) : -1;
+            const int w = p < nlim ? det_inertia_df(laydf, lay, N, k, grid_c(c0, dc, p)) : -1;
             const int wo = __shfl_xor_sync(pair, w, 1);
             const int c_lo = half ? wo : w, c_hi = half ? w : wo;
             if (up) {
@@ -128,7 +131,7 @@ __device__ __forceinline__ PairCount count_certify_pair(const float* __restrict_
         // n) and an odd count at it; otherwise the item falls back with start n.
         const int m = pair_search(lay32, N, kf, c0f, dcf, n, npf - 1, vb + 1, half, pair);
         if (m > n) {
-            const int u = det_inertia(lay, N, k, grid_c(c0, dc, m - 1 + half));
+            const int u = det_inertia_df(laydf, lay, N, k, grid_c(c0, dc, m - 1 + half));
             const int uo = __shfl_xor_sync(pair, u, 1);
             const int ua = half ? uo : u, ub = half ? u : uo;
             if (ua == vb && ub > vb && (ub & 1)) cert = m;

@@ -10,6 +10,8 @@ namespace masw {
 // Device view of a ragged model batch.
 struct DevBatch {
     const double* layers;      // [n_records][LAYER_STRIDE] records, per model N finite + 1 half-space
+    const float* layers_df;    // [n_records][LAYER_STRIDE_DF] double-float records of the same
+                               // layers (counting certificate), or nullptr: split on the fly
     const int32_t* model_loff; // [n_models + 1] record offsets
     const int32_t* model_nlim; // [n_models] number of grid points below beta_halfspace
     const int32_t* model_woff; // [n_models + 1] item offsets (items of model m are contiguous)
@@ -92,10 +94,13 @@ cudaError_t launch_grad_reduce(const DevBatch& b, const double* rows, const doub
 // then records and scan limits unless it was set (masw_kernels.cu).
 cudaError_t launch_model_update(const DevBatch& b, const double* h, const double* alpha,
                                 const double* beta, const double* rho, double* layers,
-                                float* layers32, int32_t* nlim, int32_t* err, cudaStream_t s);
+                                float* layers32, float* layers_df, int32_t* nlim, int32_t* err,
+                                cudaStream_t s);
 cudaError_t launch_update_beta_h(const DevBatch& b, const double* h, const double* beta,
-                                 double* layers, float* layers32, int32_t* nlim, int32_t* err,
-                                 cudaStream_t s);
+                                 double* layers, float* layers32, float* layers_df, int32_t* nlim,
+                                 int32_t* err, cudaStream_t s);
+cudaError_t launch_element_check(const DevBatch& b, int n, const int32_t* item, const int32_t* layer,
+                                 const double* c, double* fp64, double* df, cudaStream_t s);
 cudaError_t launch_exp_check(int n, const double* x, double* y_lib, double* y_cuda,
                              cudaStream_t s);
 cudaError_t launch_fp64_peak(int blocks, int threads, int iters, double* sink, cudaStream_t s);

@@ -44,6 +44,7 @@
 #include "masw_adjoint.cuh"
 #include "masw_count.cuh"
 #include "masw_device.cuh"
+#include "masw_df.cuh"
 #include "masw_internal.h"
 #include "masw_modes.cuh"
 #include "masw_screen.cuh"
@@ -524,7 +525,8 @@ __global__ void __launch_bounds__(B, (B == 256 ? 3 : 896 / B)) count_certify_ker
         return;
     }
     const double* lay = b.layers + (size_t)lo_rec * LAYER_STRIDE;
-    const PairCount r = count_certify_pair(layers32 + (size_t)lo_rec * LAYER_STRIDE32, lay, N,
+    const float* laydf = b.layers_df ? b.layers_df + (size_t)lo_rec * LAYER_STRIDE_DF : nullptr;
+    const PairCount r = count_certify_pair(layers32 + (size_t)lo_rec * LAYER_STRIDE32, laydf, lay, N,
                                            b.k[item], b.c0, b.dc, nlim, half, pair);
     if (half) return;
     if (b.route >= 1) {  // test routing: every item through the linear FP32 scan from V[0]
@@ -1024,6 +1026,37 @@ cudaError_t launch_leaky(const DevBatch& b, const ScanPlan& p, const int32_t* id
 // ------------------------------------------------------------ math check
 
 // The library's e^x (exp_neg, x <= 0) beside CUDA's exp at the same points.
+// The element's seven values (LayerNum: Dh, n00, n01, n11, ce, cf, cg) of
+// layer `layer` of item `item` at c, from the FP64 element (fp64, 7 per
+// point) and the double-float one (df) (tests).
+__global__ void element_check_kernel(DevBatch b, int n, const int32_t* __restrict__ item,
+                                     const int32_t* __restrict__ layer,
+                                     const double* __restrict__ c, double* fp64, double* df) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int it = item[t];
+    const int m = b.item_model[it];
+    const int rec = b.model_loff[m] + layer[t];
+    const double cc = c[t], c2 = cc * cc, k = b.k[it];
+    const LayerNum a = layer_numerators(b.layers + (size_t)rec * LAYER_STRIDE, k, c2, inv_c2(c2));
+    const DF cd = from_double(cc), c2d = dmul(cd, cd);
+    const LayerNum d = layer_numerators_df(b.layers_df + (size_t)rec * LAYER_STRIDE_DF,
+                                           from_double(k), c2d, drcp(c2d));
+    const double va[7] = {a.Dh, a.n00, a.n01, a.n11, a.ce, a.cf, a.cg};
+    const double vd[7] = {d.Dh, d.n00, d.n01, d.n11, d.ce, d.cf, d.cg};
+    for (int q = 0; q < 7; ++q) {
+        fp64[7 * (size_t)t + q] = va[q];
+        df[7 * (size_t)t + q] = vd[q];
+    }
+}
+
+cudaError_t launch_element_check(const DevBatch& b, int n, const int32_t* item, const int32_t* layer,
+                                 const double* c, double* fp64, double* df, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    element_check_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, n, item, layer, c, fp64, df);
+    return cudaGetLastError();
+}
+
 __global__ void exp_check_kernel(int n, const double* __restrict__ x, double* y_lib,
                                  double* y_cuda) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1446,7 +1479,8 @@ cudaError_t launch_grad_reduce(const DevBatch& b, const double* rows, const doub
 // limit; any invalid value sets *err (records are then unspecified).
 __global__ void update_beta_h_kernel(DevBatch b, const double* __restrict__ h,
                                      const double* __restrict__ beta, double* layers,
-                                     float* layers32, int32_t* nlim, int32_t* err) {
+                                     float* layers32, float* layers_df, int32_t* nlim,
+                                     int32_t* err) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= b.n_models) return;
     int lo = b.model_loff[m];
@@ -1474,6 +1508,7 @@ __global__ void update_beta_h_kernel(DevBatch b, const double* __restrict__ h,
             F[F_IB2] = (float)L[L_IB2];
             F[F_DIB] = (float)(L[L_IB2] - L[L_IA2]);
         }
+        if (layers_df) df_record(L, layers_df + (size_t)(lo + i) * LAYER_STRIDE_DF);
     }
     double bhs = beta[lo + N];
     double est = floor((bhs - b.c0) / b.dc);
@@ -1516,7 +1551,7 @@ __global__ void __launch_bounds__(128) build_records_kernel(DevBatch b, const do
                                                             const double* __restrict__ beta,
                                                             const double* __restrict__ rho,
                                                             double* layers, float* layers32,
-                                                            int32_t* nlim,
+                                                            float* layers_df, int32_t* nlim,
                                                             const int32_t* __restrict__ err) {
     const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -1546,6 +1581,7 @@ __global__ void __launch_bounds__(128) build_records_kernel(DevBatch b, const do
         F[F_IB2] = (float)ib2;
         F[F_DIB] = (float)(ib2 - ia2);
         F[6] = F[7] = 0.0f;
+        if (layers_df) df_record(L, layers_df + (size_t)(lo + i) * LAYER_STRIDE_DF);
     }
     if (lane == 0) {
         const double bhs = beta[lo + N];
@@ -1559,22 +1595,24 @@ __global__ void __launch_bounds__(128) build_records_kernel(DevBatch b, const do
 
 cudaError_t launch_model_update(const DevBatch& b, const double* h, const double* alpha,
                                 const double* beta, const double* rho, double* layers,
-                                float* layers32, int32_t* nlim, int32_t* err, cudaStream_t s) {
+                                float* layers32, float* layers_df, int32_t* nlim, int32_t* err,
+                                cudaStream_t s) {
     if (b.n_models <= 0) return cudaSuccess;
     const int blocks = (b.n_models + 3) / 4;  // 4 warps (models) per block
     validate_models_kernel<<<blocks, 128, 0, s>>>(b, h, alpha, beta, rho, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    build_records_kernel<<<blocks, 128, 0, s>>>(b, h, alpha, beta, rho, layers, layers32, nlim, err);
+    build_records_kernel<<<blocks, 128, 0, s>>>(b, h, alpha, beta, rho, layers, layers32, layers_df,
+                                                nlim, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update_beta_h(const DevBatch& b, const double* h, const double* beta,
-                                 double* layers, float* layers32, int32_t* nlim, int32_t* err,
-                                 cudaStream_t s) {
+                                 double* layers, float* layers32, float* layers_df, int32_t* nlim,
+                                 int32_t* err, cudaStream_t s) {
     if (b.n_models <= 0) return cudaSuccess;
     update_beta_h_kernel<<<(b.n_models + 127) / 128, 128, 0, s>>>(b, h, beta, layers, layers32,
-                                                                  nlim, err);
+                                                                  layers_df, nlim, err);
     return cudaGetLastError();
 }
 

@@ -278,6 +278,7 @@ extern "C" int masw_dispersion_noalloc(const masw_models_desc* md, const masw_gr
     }
     DevBatch d;
     d.layers = records;
+    d.layers_df = nullptr;
     d.model_loff = d_loff;
     d.model_nlim = d_nlim;
     d.model_woff = d_woff;

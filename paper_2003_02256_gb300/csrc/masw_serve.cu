@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(128, 7) serve_count_kernel(SlotView v, const i
     const double* lay = slot_records(v, slot);
     const double k = slot_k(v, slot)[j];
     PairCount r =
-        count_certify_pair(slot_records32(v, slot), lay, N, k, c0, dc, nlim, half, pair);
+        count_certify_pair(slot_records32(v, slot), nullptr, lay, N, k, c0, dc, nlim, half, pair);
     if (v.route >= 1) r = PairCount{-1, -1, 0};  // test routing: the linear screen from V[0]
     if (r.cert >= 1) {
         if (!half) finish_item(v, item, slot, r.cert, c0, dc);

@@ -352,6 +352,22 @@ def exp_check(x, stream=None):
     return y_lib, y_cuda
 
 
+def element_check(handle, item, layer, c):
+    """(fp64, df): the element's denominator and six numerators (7 per point)
+    from the FP64 element and the double-float one (masw_element_check)."""
+    item = np.ascontiguousarray(item, dtype=np.int32)
+    layer = np.ascontiguousarray(layer, dtype=np.int32)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    fp = np.empty((item.size, 7))
+    df = np.empty((item.size, 7))
+    f = load().masw_element_check
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 5
+    f.restype = ctypes.c_int
+    _check(f(ctypes.c_void_p(handle), item.size, _ptr(item), _ptr(layer), _ptr(c), _ptr(fp),
+             _ptr(df)), "masw_element_check")
+    return fp, df
+
+
 def fp64_peak(stream=None) -> float:
     f = ctypes.c_double()
     _check(load().masw_fp64_peak(_stream_handle(stream), ctypes.byref(f)), "masw_fp64_peak")
