@@ -71,13 +71,19 @@ def make_workload(name: str, n_models: int, rank: int = 0):
     return W.ragged_batch(n_models=n_models, seed=W.SEED + 3 + 1000 * rank)
 
 
-# FP64 flops per layer-evaluation (element assembly + one Schur step):
-# 2*DFMA + DMUL + DADD executed per evaluated (layer, c) pair, from ncu
-# instruction counters of the fused counting kernel's FP64 certificate on the
-# full 1024-model uniform launch (186.6 M DFMA, 143.0 M DMUL, 33.3 M DADD over
-# 3,686,400 layer-evaluations; profiles/). Every FP64 kernel runs the same
-# element and Schur arithmetic.
+# Algorithmic FP64 work of one layer-evaluation (element assembly + one
+# Schur step) in flops, 2*DFMA + DMUL + DADD: measured by ncu instruction
+# counters on the FP64 element (the counting kernel's certificate before its
+# element moved to double-float: 186.6 M DFMA, 143.0 M DMUL, 33.3 M DADD over
+# 3,686,400 layer-evaluations of the full 1024-model uniform launch; profiles/).
+# Every FP64 kernel runs this arithmetic; it is the per-unit figure of the
+# rooflines below.
 F_LAYER_FLOPS = 149.1
+# FP64 flops the counting kernel executes per layer-evaluation now that the
+# element runs in double-float on the FP32 pipe and only the Schur step (and
+# the exact conversions) on the FP64 pipe: 55.6 M DFMA, 57.6 M DMUL, 39.9 M
+# DADD over the same 3,686,400 layer-evaluations (ncu; profiles/).
+F_LAYER_FLOPS_EXECUTED64 = 56.6
 # FP32 flops per layer-evaluation of the screen kernel (2*FFMA + FMUL + FADD
 # per executed (layer, c) pair: 29.6 FFMA, 54.2 FMUL, 16.4 FADD; ncu
 # instruction counters of the 64-model case, profiles/).
@@ -96,10 +102,9 @@ SM_MAX_MHZ = 2070.0
 # (bytes, models of that launch); the records, wavenumbers and item tables are
 # read once, the outputs stay in L2. Scaled by the models of a launch; None
 # where no capture of the current kernel exists.
-# uniform: 3.49 MB for the 1024-model launch; ragged: 8.73 MB for the launch
-# over the first 2048 models (429,978 items), scaled by the algorithmic bytes
-# (records, wavenumbers, item tables: x 4.024) to the 8192-model launch.
-CERTIFY_DRAM_BYTES = {"uniform": (3.492864e6, 1024), "ragged": (35.152e6, 8192)}
+# uniform: 3.57 MB for the 1024-model launch (double-float records included);
+# ragged: none yet for the current kernel.
+CERTIFY_DRAM_BYTES = {"uniform": (3.569152e6, 1024), "ragged": None}
 # DRAM bytes (read + write) of one scan launch per model, from the ncu capture
 # of the 64-model case (281.6 KB read, 0 written), scaled by the models of a
 # launch; traffic grows with the number of items.
@@ -417,10 +422,16 @@ def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, s
     return {"bound": "alu", "unit": "TFLOP/s",
             "achieved": achieved / 1e12, "peak": peak64 / 1e12, "frac": achieved / peak64,
             "traffic": None if cap is None else cap[0] * models.n_models / cap[1],
-            "kernel": "count_certify_kernel (FP64 pipe; FP32 search alongside)",
+            "kernel": "count_certify_kernel (FP64 certificate: double-float element on the FP32 "
+                      "pipe, Schur step on the FP64 pipe; FP32 search alongside)",
+            "work": "the certificate's layer-evaluations x the FP64 element + Schur step's "
+                    "149.1 flops each",
             "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
             "frac_of_fp64_microbenchmark": achieved / micro,
             "layer_evals_per_launch": e64, "flops_per_layer_eval": F_LAYER_FLOPS,
+            "layer_evals_per_s": e64 / t0,
+            "fp64_flops_executed_per_layer_eval": F_LAYER_FLOPS_EXECUTED64,
+            "fp64_pipe_frac_executed": e64 * F_LAYER_FLOPS_EXECUTED64 / t0 / peak64,
             "kernel_ms": phases[0],
             "search_layer_evals_fp32": e32,
             "search_fp32_frac_of_fp32_peak": e32 * F_LAYER_FLOPS_FP32 / t0 / peak32,
