@@ -40,7 +40,7 @@ struct PairCount {
 // lo; -1 when the count at `top` is below `target`. The pair evaluates `top`
 // and the bracket's midpoint, then splits the bracket in three per step (one
 // point per lane). Both lanes return the same index.
-__device__ __forceinline__ int pair_search(const float* __restrict__ lay32, int N, float kf,
+static __device__ __noinline__ int pair_search(const float* __restrict__ lay32, int N, float kf,
                                            float c0f, float dcf, int lo, int top, int target,
                                            int half, unsigned pair) {
     int hi = top;

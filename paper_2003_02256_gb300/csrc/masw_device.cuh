@@ -909,38 +909,12 @@ __device__ inline int det_sign_leaky(const double* __restrict__ lay, int N, doub
     return sg * sgn(fma(t_re, v_re, -t_im * v_im));
 }
 
-// Number of negative eigenvalues of K(k, c) (Sylvester's law of inertia over
-// the 2x2 Schur pivots S_j = Shat_j / (w Dh)): a pivot with det < 0 has one,
-// one with det > 0 has two when its diagonal is negative. A zero determinant
-// counts as one; -1 when the rescaling failed. The parity equals the sign
-// det_sign reports (same arithmetic). Requires c < beta_halfspace.
-__device__ inline int det_inertia(const double* __restrict__ lay, int N, double k, double c) {
-    double c2 = c * c;
-    const double ic2 = inv_c2(c2);
-    HState st{0.0, 0.0, 0.0, 1.0};
-    int cnt = 0;
-    double sv[3];
-    for (int j = 0; j < N; ++j) {
-        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2, ic2);
-        const bool f_neg = wprod_lt0(st.w, n.Dh);  // sign of w Dh, the pivot's scale
-        bool ok;
-        double det = schur_layer(st, n, &ok, sv);
-        cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(sv[0]) != f_neg) ? 2 : 0) : 1);
-        if (!ok) return -1;
-    }
-    HalfNum hn = halfspace_numerators(lay + N * LAYER_STRIDE, c2);
-    const bool f_neg = wprod_lt0(st.w, hn.den);
-    double s00 = fma(hn.den, st.p00, st.w * hn.m00);
-    double s01 = fma(hn.den, st.p01, st.w * hn.m01);
-    double s11 = fma(hn.den, st.p11, st.w * hn.m11);
-    double det = fma(s00, s11, -s01 * s01);
-    cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(s00) != f_neg) ? 2 : 0) : 1);
-    return cnt;
-}
-
 // Sign of det K (as det_sign: 0 for an exact zero or a failed rescaling) and
-// the number of its negative eigenvalues (as det_inertia: -1 for a failed
-// rescaling) in one pass. Requires c < beta_halfspace.
+// the number of its negative eigenvalues in one pass (Sylvester's law of
+// inertia over the 2x2 Schur pivots S_j = Shat_j / (w Dh): a pivot with
+// det < 0 has one, one with det > 0 has two when its diagonal is negative, a
+// zero determinant counts as one; -1 for a failed rescaling). Requires
+// c < beta_halfspace.
 __device__ inline int det_sign_count(const double* __restrict__ lay, int N, double k, double c,
                                      int* count) {
     double c2 = c * c;
@@ -1006,23 +980,6 @@ __device__ inline int clamped_modes(const double* __restrict__ L, double k, doub
         J = 2 * J + (int)(lt0(an) != lt0(D)) + (int)(lt0(dn) != lt0(D));
     }
     return J;
-}
-
-// Wittrick-Williams mode count of the layered structure below c, split as
-// (s, J0): s = negative eigenvalues of K (det_inertia; -1 when the rescaling
-// failed), J0 = clamped modes of all finite layers (the half-space has none
-// below its shear speed). J = J0 + s, the number of modes below c, never
-// decreases with c, and neither does T = J + J0 = s + 2 J0, whose parity is
-// that of s: det K changes sign between two test velocities exactly when T
-// jumps by an odd amount between them. Requires c < beta_halfspace.
-__device__ inline int mode_count_T(const double* __restrict__ lay, int N, double k, double c,
-                                   int* s_out) {
-    const int s = det_inertia(lay, N, k, c);
-    const double c2 = c * c;
-    int j0 = 0;
-    for (int j = 0; j < N; ++j) j0 += clamped_modes(lay + j * LAYER_STRIDE, k, c2);
-    *s_out = s;
-    return s < 0 ? -1 : s + 2 * j0;
 }
 
 // x = m * 2^e with |m| in [1, 2) for a normal x (integer pipe); zero,

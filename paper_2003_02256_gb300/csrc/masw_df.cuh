@@ -454,8 +454,9 @@ __device__ __forceinline__ DF dexp_neg(DF x) {
     return dscale(v, __int_as_float((m + 127) << 23));
 }
 
-// e^y - 1 for y <= 0.
-__device__ __forceinline__ DF dexpm1_neg(DF y) {
+// e^y - 1 for y <= 0. Kept out of line (called three times per element):
+// the element's code must stay within the instruction cache.
+static __device__ __noinline__ DF dexpm1_neg(DF y) {
     if (y.hi > -0.35f) {
         const float nf = rintf(__fmul_rn(y.hi, DF_INV_LN2_256));  // -130 <= n <= 0
         const int i = -(int)nf;
@@ -506,8 +507,9 @@ __device__ __forceinline__ void dseries(DF u, DF* chm1, DF* sh) {
 // U1 = C - 1 (cosh - 1 unscaled) in the series branch, where E = 1.
 struct WaveDF { DF E, C, Sd, Sm, U1; bool series; };
 
-// The scaled even functions of masw_device.cuh::wave_fns in double-float.
-__device__ __forceinline__ WaveDF wave_df(DF kh, DF kh2, DF w2) {
+// The scaled even functions of masw_device.cuh::wave_fns in double-float
+// (out of line: called twice per element).
+static __device__ __noinline__ WaveDF wave_df(DF kh, DF kh2, DF w2) {
     const DF u = dmul(kh2, w2);
     WaveDF o;
     o.series = fabsf(u.hi) < (float)SERIES_U;
@@ -636,13 +638,18 @@ __device__ __forceinline__ LayerNum layer_numerators_df(const float* __restrict_
     return o;
 }
 
-// det_inertia (masw_device.cuh) with the finite layers' elements in
-// double-float: the count of negative eigenvalues of K(k, c) from the FP64
-// recurrence. laydf: the N finite layers' double-float records, or nullptr
-// to split the FP64 records on the fly (the same values). Requires
-// c < beta_halfspace.
-__device__ inline int det_inertia_df(const float* __restrict__ laydf,
-                                     const double* __restrict__ lay, int N, double k, double c) {
+// Number of negative eigenvalues of K(k, c) from the FP64 recurrence over the
+// finite layers' elements in double-float (Sylvester's law of inertia over the
+// 2x2 Schur pivots S_j = Shat_j / (w Dh): a pivot with det < 0 has one, one
+// with det > 0 has two when its diagonal is negative; a zero determinant
+// counts as one; -1 when the rescaling failed). Its parity is the sign of
+// det K. laydf: the N finite layers' double-float records, or nullptr to split
+// the FP64 records on the fly (the same values). Requires c < beta_halfspace.
+// Out of line: the counting certificate calls it from three places, and one
+// copy of the element keeps the kernel within the instruction cache.
+static __device__ __noinline__ int det_inertia_df(const float* __restrict__ laydf,
+                                           const double* __restrict__ lay, int N, double k,
+                                           double c) {
     const double c2 = c * c;
     const DF kd = from_double(k), cd = from_double(c);
     const DF c2d = dmul(cd, cd);
@@ -669,6 +676,25 @@ __device__ inline int det_inertia_df(const float* __restrict__ laydf,
     double det = fma(s00, s11, -s01 * s01);
     cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(s00) != f_neg) ? 2 : 0) : 1);
     return cnt;
+}
+
+// Wittrick-Williams mode count of the layered structure below c, split as
+// (s, J0): s = negative eigenvalues of K (det_inertia_df; -1 when the
+// rescaling failed), J0 = clamped modes of all finite layers (clamped_modes,
+// from the FP64 records; the half-space has none below its shear speed).
+// J = J0 + s, the number of modes below c, never decreases with c, and
+// neither does T = J + J0 = s + 2 J0, whose parity is that of s: det K changes
+// sign between two test velocities exactly when T jumps by an odd amount
+// between them. laydf as for det_inertia_df. Requires c < beta_halfspace.
+__device__ inline int mode_count_T_df(const float* __restrict__ laydf,
+                                      const double* __restrict__ lay, int N, double k, double c,
+                                      int* s_out) {
+    const int s = det_inertia_df(laydf, lay, N, k, c);
+    const double c2 = c * c;
+    int j0 = 0;
+    for (int j = 0; j < N; ++j) j0 += clamped_modes(lay + j * LAYER_STRIDE, k, c2);
+    *s_out = s;
+    return s < 0 ? -1 : s + 2 * j0;
 }
 
 }  // namespace masw

@@ -38,6 +38,10 @@
 //  validate_models_kernel, build_records_kernel, update_beta_h_kernel
 //                         model updates on the device.
 //  exp_check_kernel       the library's exponential beside CUDA's (tests).
+// "FP64 count" below: the Wittrick-Williams count of the FP64 Schur
+// recurrence over element stiffnesses in double-float (det_inertia_df,
+// mode_count_T_df in masw_df.cuh); the FP64 scans (scan_kernel,
+// resolve64_kernel, changes_scan64_kernel) take the plain FP64 element.
 //  fp64_peak_kernel       DFMA throughput microbenchmark (roofline denominator).
 #include <algorithm>
 
@@ -164,7 +168,7 @@ cudaError_t launch_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p, 
 // 1. screen32_kernel: the scan of scan_kernel in FP32 (det_sign_f), giving
 //    the FP32 first sign change n32 per item (-1 if none below the limit).
 // 2. verify64_kernel: one thread per item, the FP64 mode count T = s + 2 J0
-//    (mode_count_T; never decreasing, odd jumps exactly at the sign changes)
+//    (mode_count_T_df; never decreasing, odd jumps exactly at the sign changes)
 //    at V[0], V[n32-1], V[n32]: the item is resolved to n32 when T(V[0]) =
 //    T(V[n32-1]) and T jumps by an odd amount at n32 (for n32 = -1, to "no
 //    root" when T(V[0]) equals T at the last point); otherwise it goes to
@@ -323,6 +327,12 @@ __global__ void __launch_bounds__(256) screen32p_kernel(DevBatch b, const float*
     }
 }
 
+// The double-float records of the model whose records start at lo (nullptr
+// when the batch has none: split on the fly).
+__device__ __forceinline__ const float* records_df(const DevBatch& b, int lo) {
+    return b.layers_df ? b.layers_df + (size_t)lo * LAYER_STRIDE_DF : nullptr;
+}
+
 __device__ __forceinline__ void write_result(const DevBatch& b, const ScanOut& o, int item, int res) {
     if (res >= 0) {
         o.ct[item] = grid_c(b.c0, b.dc, res);
@@ -336,7 +346,7 @@ __device__ __forceinline__ void write_result(const DevBatch& b, const ScanOut& o
 }
 
 // Three-point FP64 check of a linear screen's index n (-1: no change seen)
-// on the mode count T = s + 2 J0 (mode_count_T), which never decreases along
+// on the mode count T = s + 2 J0 (mode_count_T_df), which never decreases along
 // the grid and jumps by an odd amount exactly at the sign changes: T(V[n-1])
 // = T(V[0]) leaves no change (no event at all) below n, an odd T(V[n]) -
 // T(V[n-1]) makes n a change; with no change seen, T(V[nlim-1]) = T(V[0]).
@@ -355,10 +365,13 @@ __device__ __forceinline__ void verify_item(const DevBatch& b, const ScanOut& o,
         write_result(b, o, item, -1);
         return;
     }
+    const float* laydf = records_df(b, lo);
     int sv;
-    const int T0 = mode_count_T(lay, N, k, grid_c(b.c0, b.dc, 0), &sv);
-    const int Ta = (n == 1) ? T0 : mode_count_T(lay, N, k, grid_c(b.c0, b.dc, n >= 1 ? n - 1 : nlim - 1), &sv);
-    const int Tb = n >= 1 ? mode_count_T(lay, N, k, grid_c(b.c0, b.dc, n), &sv) : -1;
+    const int T0 = mode_count_T_df(laydf, lay, N, k, grid_c(b.c0, b.dc, 0), &sv);
+    const int Ta = (n == 1) ? T0
+                            : mode_count_T_df(laydf, lay, N, k,
+                                              grid_c(b.c0, b.dc, n >= 1 ? n - 1 : nlim - 1), &sv);
+    const int Tb = n >= 1 ? mode_count_T_df(laydf, lay, N, k, grid_c(b.c0, b.dc, n), &sv) : -1;
     if (b.route < 2 && mode_count_verified(n, T0, Ta, Tb)) write_result(b, o, item, n >= 1 ? n : -1);
     else search[atomicAdd(n_search, 1)] = item;  // (test routing 2, 3: every item)
 }
@@ -403,7 +416,9 @@ __global__ void __launch_bounds__(128) verify64_list_kernel(DevBatch b, ScanOut 
         // lane 0: V[0]; lane 1: V[n-1] (no change seen: the last point); lane 2: V[n]
         const int pt = sub == 0 ? 0 : sub == 1 ? (n >= 1 ? n - 1 : nlim - 1) : sub == 2 ? (n >= 1 ? n : -1) : -1;
         int sv;
-        const int T = pt >= 0 ? mode_count_T(lay, N, k, grid_c(b.c0, b.dc, pt), &sv) : -1;
+        const int T = pt >= 0 ? mode_count_T_df(records_df(b, lo), lay, N, k,
+                                                grid_c(b.c0, b.dc, pt), &sv)
+                              : -1;
         const int T0 = __shfl_sync(quad, T, q0);
         const int Ta = __shfl_sync(quad, T, q0 + 1);
         const int Tb = __shfl_sync(quad, T, q0 + 2);
@@ -583,7 +598,8 @@ __global__ void __launch_bounds__(256) first_count64_kernel(DevBatch b, ScanOut 
         const int top = b.model_nlim[m] - 1;  // >= 1 for listed items
         const int xl = (int)(((long long)gl * top) / (G - 1));
         int sl;
-        const int Tl = mode_count_T(lay, N, k, grid_c(b.c0, b.dc, xl), &sl);
+        const float* laydf = records_df(b, l0);
+        const int Tl = mode_count_T_df(laydf, lay, N, k, grid_c(b.c0, b.dc, xl), &sl);
         const int Tprev = __shfl_up_sync(gmask, Tl, 1, G);
         bool bad = (__ballot_sync(gmask, Tl < 0 || (gl > 0 && Tl < Tprev)) & gmask) != 0;
         int Pn = 0, PT = __shfl_sync(gmask, Tl, 0, G), res = -1;
@@ -604,7 +620,7 @@ __global__ void __launch_bounds__(256) first_count64_kernel(DevBatch b, ScanOut 
                 const int y = lo + (int)(((long long)(gl + 1) * len) / G);
                 const bool in = gl < G - 1 && y > lo && y < hn;
                 int sy = 0, Ty = -1;
-                if (in) Ty = mode_count_T(lay, N, k, grid_c(b.c0, b.dc, y), &sy);
+                if (in) Ty = mode_count_T_df(laydf, lay, N, k, grid_c(b.c0, b.dc, y), &sy);
                 const int Typ = __shfl_up_sync(gmask, Ty, 1, G);
                 const bool inp = __shfl_up_sync(gmask, (int)in, 1, G) != 0;
                 if ((__ballot_sync(gmask, in && (Ty < PT || Ty > hT || (gl > 0 && inp && Ty < Typ))) &
@@ -893,8 +909,10 @@ __global__ void __launch_bounds__(128) changes_count64_kernel(DevBatch b, Change
         const double* lay = b.layers + (size_t)l0 * LAYER_STRIDE;
         const double k = b.k[item];
         TPoint below, P;
-        eval_pair(lay, N, k, b.c0, b.dc, n1 - 1, n1, half, pair, &below, &P);
-        ModeSearch st = mode_search_init(lay, N, k, b.c0, b.dc, b.model_nlim[m] - 1, half, pair,
+        const float* laydf = records_df(b, l0);
+        eval_pair(laydf, lay, N, k, b.c0, b.dc, n1 - 1, n1, half, pair, &below, &P);
+        ModeSearch st = mode_search_init(laydf, lay, N, k, b.c0, b.dc,
+                                         b.model_nlim[m] - 1, half, pair,
                                          P, TPoint{-1, -1, 0});
         st.bad = st.bad || below.T < 0 || P.T <= below.T || !((P.T - below.T) & 1);
         if (half == 0) write_change(b, o, e0, n1, P.s - below.s);
@@ -1093,7 +1111,7 @@ __global__ void det_eval_kernel(DevBatch b, int n, const int32_t* __restrict__ i
 
 // Wittrick-Williams counts at arbitrary points: s (negative eigenvalues of K)
 // and J0 (clamped-layer modes below c) by the arithmetic of the mode-count
-// search (mode_count_T). -1 for c outside (0, beta_halfspace) or a failed
+// search (mode_count_T_df). -1 for c outside (0, beta_halfspace) or a failed
 // rescaling.
 __global__ void mode_count_kernel(DevBatch b, int n, const int32_t* __restrict__ item,
                                   const double* __restrict__ c, int32_t* s_out, int32_t* j0_out) {
@@ -1109,7 +1127,7 @@ __global__ void mode_count_kernel(DevBatch b, int n, const int32_t* __restrict__
     const double* lay = b.layers + (size_t)lo * LAYER_STRIDE;
     if (!(c[t] > 0.0 && c[t] < lay[N * LAYER_STRIDE + L_BETA])) return;
     int sv;
-    const int T = mode_count_T(lay, N, b.k[it], c[t], &sv);
+    const int T = mode_count_T_df(records_df(b, lo), lay, N, b.k[it], c[t], &sv);
     if (T < 0) return;
     s_out[t] = sv;
     j0_out[t] = (T - sv) / 2;

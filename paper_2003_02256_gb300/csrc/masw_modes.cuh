@@ -1,7 +1,8 @@
-// masw_modes.cuh -- FP64 search for sign changes of det K on the
-// Wittrick-Williams mode count, run by a pair of adjacent lanes.
+// masw_modes.cuh -- search for sign changes of det K on the Wittrick-Williams
+// mode count (FP64 recurrence over double-float elements: mode_count_T_df),
+// run by a pair of adjacent lanes.
 //
-// T = s + 2 J0 (mode_count_T: s negative eigenvalues of K, J0 clamped-layer
+// T = s + 2 J0 (mode_count_T_df: s negative eigenvalues of K, J0 clamped-layer
 // modes) never decreases along the grid below the scan limit and jumps by an
 // odd amount exactly where det K changes sign, by Delta s there (the change
 // in the negative-eigenvalue count: +1 at a root, -1 at a pole). From a point
@@ -22,6 +23,7 @@
 #pragma once
 
 #include "masw_device.cuh"
+#include "masw_df.cuh"
 
 namespace masw {
 
@@ -31,12 +33,13 @@ struct TPoint {
 
 // Both lanes evaluate one point each (n0 on half 0, n1 on half 1; a negative
 // index evaluates nothing and gives T = -1) and both get both results.
-__device__ __forceinline__ void eval_pair(const double* __restrict__ lay, int N, double k,
+__device__ __forceinline__ void eval_pair(const float* __restrict__ laydf,
+                                          const double* __restrict__ lay, int N, double k,
                                           double c0, double dc, int n0, int n1, int half,
                                           unsigned pair, TPoint* a, TPoint* b) {
     const int n = half ? n1 : n0;
     int sv = 0, T = -1;
-    if (n >= 0) T = mode_count_T(lay, N, k, grid_c(c0, dc, n), &sv);
+    if (n >= 0) T = mode_count_T_df(laydf, lay, N, k, grid_c(c0, dc, n), &sv);
     const int so = __shfl_xor_sync(pair, sv, 1), To = __shfl_xor_sync(pair, T, 1);
     *a = half ? TPoint{n0, To, so} : TPoint{n0, T, sv};
     *b = half ? TPoint{n1, T, sv} : TPoint{n1, To, so};
@@ -54,6 +57,7 @@ __device__ __forceinline__ bool mode_count_verified(int n, int T0, int Ta, int T
 }
 
 struct ModeSearch {
+    const float* laydf;  // double-float records (nullptr: split on the fly)
     const double* lay;
     int N;
     double k, c0, dc;
@@ -66,10 +70,12 @@ struct ModeSearch {
     bool bad;     // the FP64 counts failed (rescaling, or T not monotone)
 };
 
-__device__ __forceinline__ ModeSearch mode_search_init(const double* lay, int N, double k,
-                                                       double c0, double dc, int top, int half,
-                                                       unsigned pair, TPoint P, TPoint topp) {
+__device__ __forceinline__ ModeSearch mode_search_init(const float* laydf, const double* lay,
+                                                       int N, double k, double c0, double dc,
+                                                       int top, int half, unsigned pair, TPoint P,
+                                                       TPoint topp) {
     ModeSearch st;
+    st.laydf = laydf;
     st.lay = lay;
     st.N = N;
     st.k = k;
@@ -105,7 +111,7 @@ __device__ inline int next_change(ModeSearch& st, int* delta) {
         } else {
             const int mid = lo + ((st.top - lo) >> 1);
             TPoint mp;
-            eval_pair(st.lay, st.N, st.k, st.c0, st.dc, st.top, mid > lo ? mid : -1, st.half,
+            eval_pair(st.laydf, st.lay, st.N, st.k, st.c0, st.dc, st.top, mid > lo ? mid : -1, st.half,
                       st.pair, &st.topp, &mp);
             if (st.topp.T < st.P.T || (mp.n >= 0 && (mp.T < st.P.T || mp.T > st.topp.T))) {
                 st.bad = true;
@@ -127,7 +133,7 @@ __device__ inline int next_change(ModeSearch& st, int* delta) {
             const int len = hi.n - lo;
             const int a = lo + (len + 1) / 3, bq = lo + (2 * len + 1) / 3;  // lo < a <= bq < hi
             TPoint pa, pb;
-            eval_pair(st.lay, st.N, st.k, st.c0, st.dc, a, bq, st.half, st.pair, &pa, &pb);
+            eval_pair(st.laydf, st.lay, st.N, st.k, st.c0, st.dc, a, bq, st.half, st.pair, &pa, &pb);
             if (pa.T < st.P.T || pb.T < pa.T || pb.T > hi.T) {
                 st.bad = true;
                 return -1;

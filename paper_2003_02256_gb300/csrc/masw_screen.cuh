@@ -6,7 +6,8 @@
 // The screen evaluates the same element stiffness and the same homogeneous
 // Schur recurrence in FP32 to LOCATE the first sign change n32; the result
 // reported by the library is always decided in FP64: the Wittrick-Williams
-// mode count of the FP64 recurrence (masw_device.cuh::mode_count_T) at V[0],
+// mode count of the FP64 recurrence over double-float elements
+// (masw_df.cuh::mode_count_T_df) at V[0],
 // V[n32-1] and V[n32], and when it does not confirm, the FP64 search on that
 // count (masw_modes.cuh) or finally the FP64 scan.
 //

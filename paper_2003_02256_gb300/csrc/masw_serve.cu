@@ -136,10 +136,10 @@ __device__ bool search_or_rescan(SlotView v, int item, int slot, const double* l
     if (p0) {
         P = *p0;
     } else {
-        eval_pair(lay, N, k, c0, dc, 0, topp.T < 0 ? nlim - 1 : -1, half, pair, &P, &dummy);
+        eval_pair(nullptr, lay, N, k, c0, dc, 0, topp.T < 0 ? nlim - 1 : -1, half, pair, &P, &dummy);
         if (topp.T < 0) topp = dummy;
     }
-    ModeSearch st = mode_search_init(lay, N, k, c0, dc, nlim - 1, half, pair, P, topp);
+    ModeSearch st = mode_search_init(nullptr, lay, N, k, c0, dc, nlim - 1, half, pair, P, topp);
     int d = 0;
     const int n = next_change(st, &d);
     const bool bad = st.bad || v.route >= 3;  // (test routing 3: the FP64 scan for every item)
@@ -321,8 +321,8 @@ __global__ void __launch_bounds__(128) serve_check_kernel(SlotView v,
     const double k = slot_k(v, slot)[j];
     const int n = slot_state(v, slot)[4 * j + 3];  // screen index (-2: none below the limit)
     TPoint p0, pa, pb{-1, -1, 0}, unused;
-    eval_pair(lay, N, k, c0, dc, 0, n >= 1 ? n - 1 : nlim - 1, half, pair, &p0, &pa);
-    if (n >= 1) eval_pair(lay, N, k, c0, dc, n, -1, half, pair, &pb, &unused);
+    eval_pair(nullptr, lay, N, k, c0, dc, 0, n >= 1 ? n - 1 : nlim - 1, half, pair, &p0, &pa);
+    if (n >= 1) eval_pair(nullptr, lay, N, k, c0, dc, n, -1, half, pair, &pb, &unused);
     if (v.route < 2 && mode_count_verified(n, p0.T, pa.T, pb.T)) {
         if (!half) finish_item(v, item, slot, n >= 1 ? n : -1, c0, dc);
         return;
