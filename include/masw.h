@@ -270,8 +270,11 @@ int masw_test_fail_alloc(int32_t k);
  * the linear FP32 scan from V[0] (plan precision 2). 2: also, every item fails
  * its three-point FP64 check and takes the FP64 mode-count search. 3: also,
  * every searched item takes the FP64 scan from V[0], and every higher-mode
- * item the FP64 scan at every grid point. Synchronises the batch stream and
- * rebuilds the scan graph. MASW_EINVAL outside 0..3. */
+ * item the FP64 scan at every grid point. 4 (no other routing): each
+ * higher-mode event that the FP32 search locates is displaced by 0, -1, +1,
+ * +3 or -7 grid points (by item index mod 5) before its FP64 certificate, so
+ * that the search's recovery steps run. Synchronises the batch stream and
+ * rebuilds the scan graph. MASW_EINVAL outside 0..4. */
 int masw_set_route(masw_batch* batch, int32_t route);
 
 /* Items of the most recent two-precision scan (plan precision 1 or 2) whose FP32
@@ -300,15 +303,18 @@ int masw_last_scan_unresolved(const masw_batch* batch, int32_t* n);
  * per out_mem_space, any may be NULL): ct = V[n] (NaN when fewer changes),
  * ct_idx = n (-1), status MASW_FOUND / MASW_NO_ROOT, delta_count (0). The
  * first change is masw_dispersion's (the batch plan). Past it, with plan
- * precision 1 or 2, the changes are found by FP64 search on the
- * Wittrick-Williams count T = s + 2 J0 (s: negative eigenvalues of K; J0:
- * modes of the finite layers with both faces clamped, counted by halving each
- * layer's thickness), which never decreases along the grid and jumps by an odd
- * amount exactly where det K changes sign: about 2 log3(n_lim) evaluations per
- * event. Items whose FP64 counts fail (see masw_last_changes_linear) and plan
+ * precision 1 or 2, the changes are found on the Wittrick-Williams count
+ * T = s + 2 J0 (s: negative eigenvalues of K; J0: modes of the finite layers
+ * with both faces clamped, counted by halving each layer's thickness), which
+ * never decreases along the grid and jumps by an odd amount exactly where
+ * det K changes sign: an FP32 search on T locates each rise (about log3(n_lim)
+ * FP32 evaluations) and the FP64 count at V[n-1] and V[n] certifies it; where
+ * the FP32 location is off, FP64 steps and the FP64 search on T take over.
+ * Items whose FP64 counts fail (see masw_last_changes_linear) and plan
  * precision 0 use the FP64 scan at every grid point from one point below the
- * first change. No FP32 screen is used past the first change: next to a pole
- * an FP32 error can hide a root-pole pair inside one grid interval. It also
+ * first change. No FP32 sign screen is used past the first change (next to a
+ * pole an FP32 error can hide a root-pole pair inside one grid interval): every
+ * gap between events is certified on the FP64 count. It also
  * leaves masw_dispersion's outputs of the batch updated. Runs on the batch
  * stream; synchronises it for host outputs. Device buffers of n_items x
  * max_changes are allocated on first use. MASW_EINVAL for max_changes out of

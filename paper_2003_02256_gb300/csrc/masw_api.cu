@@ -717,7 +717,7 @@ int masw_dispersion_changes(masw_batch* B, int32_t max_changes, double* ct, int3
     int rc0 = run_scan(B);
     if (rc0) return rc0;
     CK(launch_changes(B->dev(B->plan.ordered != 0), to_scan_plan(B, B->plan), max_changes,
-                      B->d_idx, B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta,
+                      B->d_idx, B->d_layers32, B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta,
                       B->d_chg_counters, B->d_chg_counters + CHANGES_COUNTERS,
                       B->plan.precision >= 1, B->stream));
     B->changes_counted = B->plan.precision >= 1;
@@ -1087,7 +1087,7 @@ int masw_test_fail_alloc(int32_t k) {
 }
 
 int masw_set_route(masw_batch* B, int32_t route) {
-    if (!B || route < 0 || route > 3) return MASW_EINVAL;
+    if (!B || route < 0 || route > 4) return MASW_EINVAL;
     CK(cudaStreamSynchronize(B->stream));
     B->route = route;
     return rebuild_graph(B);

@@ -23,8 +23,21 @@ struct DevBatch {
     int32_t n_items;
     double c0, dc;
     int32_t n_c;
-    int32_t route;  // test routing (masw_set_route): 0 normal, 1..3 force the slower paths
+    int32_t route;  // test routing (masw_set_route): 0 normal, 1..3 force the slower paths,
+                    // 4 displaces the FP32-located higher-mode events
 };
+
+// The cumulative level 0..3 of a test routing value (route 4 has none).
+__host__ __device__ inline int route_level(int route) { return route <= 3 ? route : 0; }
+
+// Test routing 4: grid points by which the higher-mode search displaces an
+// item's FP32-located events before their FP64 certificate (by item % 5), so
+// that every recovery branch runs.
+__host__ __device__ inline int route_displacement(int route, int item) {
+    if (route != 4) return 0;
+    const int d[5] = {0, -1, 1, 3, -7};
+    return d[item % 5];
+}
 
 struct ScanOut {
     double* ct;
@@ -66,8 +79,9 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
 // (masw_kernels.cu).
 constexpr int CHANGES_COUNTERS = 2;
 cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const int32_t* first,
-                           double* ct, int32_t* idx, int32_t* status, int32_t* delta,
-                           int32_t* counters, int32_t* linear, int counting, cudaStream_t s);
+                           const float* layers32, double* ct, int32_t* idx, int32_t* status,
+                           int32_t* delta, int32_t* counters, int32_t* linear, int counting,
+                           cudaStream_t s);
 
 // Leaky continuation: Algorithm 1 over the whole grid with the sign of Re det K
 // (complex half-space block at c >= beta_hs); items the batch scan resolved

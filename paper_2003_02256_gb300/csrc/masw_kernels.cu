@@ -22,7 +22,8 @@
 //                         FP64 search on the mode count from V[0].
 //  resolve64_kernel       items whose FP64 counts failed: FP64 scan from V[0].
 // Beyond the first change:
-//  changes_count64_kernel higher modes, FP64 search on the mode count;
+//  changes_count64_kernel higher modes, FP32 search on the mode count, each
+//                         event certified on the FP64 count;
 //  changes_scan64_kernel  higher modes, FP64 scan at every grid point.
 //  leaky_scan64_kernel    the whole grid with the sign of Re det K (complex
 //                         half-space block above its shear speed).
@@ -372,7 +373,7 @@ __device__ __forceinline__ void verify_item(const DevBatch& b, const ScanOut& o,
                             : mode_count_T_df(laydf, lay, N, k,
                                               grid_c(b.c0, b.dc, n >= 1 ? n - 1 : nlim - 1), &sv);
     const int Tb = n >= 1 ? mode_count_T_df(laydf, lay, N, k, grid_c(b.c0, b.dc, n), &sv) : -1;
-    if (b.route < 2 && mode_count_verified(n, T0, Ta, Tb)) write_result(b, o, item, n >= 1 ? n : -1);
+    if (route_level(b.route) < 2 && mode_count_verified(n, T0, Ta, Tb)) write_result(b, o, item, n >= 1 ? n : -1);
     else search[atomicAdd(n_search, 1)] = item;  // (test routing 2, 3: every item)
 }
 
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(128) verify64_list_kernel(DevBatch b, ScanOut 
         const int Ta = __shfl_sync(quad, T, q0 + 1);
         const int Tb = __shfl_sync(quad, T, q0 + 2);
         if (sub != 0) continue;
-        if (b.route < 2 && mode_count_verified(n, T0, Ta, Tb))
+        if (route_level(b.route) < 2 && mode_count_verified(n, T0, Ta, Tb))
             write_result(b, o, item, n >= 1 ? n : -1);
         else
             search[atomicAdd(n_search, 1)] = item;  // (test routing 2, 3: every item)
@@ -544,7 +545,7 @@ __global__ void __launch_bounds__(B, (B == 256 ? 3 : 896 / B)) count_certify_ker
     const PairCount r = count_certify_pair(layers32 + (size_t)lo_rec * LAYER_STRIDE32, laydf, lay, N,
                                            b.k[item], b.c0, b.dc, nlim, half, pair);
     if (half) return;
-    if (b.route >= 1) {  // test routing: every item through the linear FP32 scan from V[0]
+    if (route_level(b.route) >= 1) {  // test routing: every item through the linear FP32 scan from V[0]
         n32[item] = 0;
         fallback[atomicAdd(n_fallback, 1)] = item;
     } else if (r.cert >= 1) {
@@ -649,7 +650,7 @@ __global__ void __launch_bounds__(256) first_count64_kernel(DevBatch b, ScanOut 
             PT = hT;
         }
         if (gl == 0) {
-            if (bad || b.route >= 3) {  // (test routing 3: every item to the FP64 scan)
+            if (bad || route_level(b.route) >= 3) {  // (test routing 3: every item to the FP64 scan)
                 n32[item] = 0;
                 unresolved[atomicAdd(n_unresolved, 1)] = item;
             } else {
@@ -796,13 +797,16 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
 // the change in K's negative-eigenvalue count across it (Wittrick-Williams:
 // +1 where a mode of the layered structure is crossed, a root of det K; -1 at
 // a pole, a mode of a clamped layer). The first change is the batch scan's
-// result (an FP64 decision). Past it, changes_count64_kernel searches the
-// FP64 mode count (plan precision >= 1) and changes_scan64_kernel scans in
+// result (an FP64 decision). Past it, changes_count64_kernel locates each
+// rise of the mode count on its FP32 value and certifies it on the FP64 count
+// (next_change_f32; plan precision >= 1), and changes_scan64_kernel scans in
 // FP64 at every grid point (plan precision 0, and the items whose counts
-// fail). An FP32 screen is not used past the first change: next to a pole an
-// FP32 rounding error can move the pole across a grid point, and a root-pole
-// pair inside one grid interval then vanishes from the FP32 signs without any
-// sign or count change at the points around it.
+// fail). An FP32 sign screen is not used past the first change: next to a pole
+// an FP32 rounding error can move the pole across a grid point, and a
+// root-pole pair inside one grid interval then vanishes from the FP32 signs
+// without any sign or count change at the points around it. The FP32 count
+// only locates: the FP64 count at V[n-1] equal to the last event's certifies
+// that no event lies between.
 
 struct ChangesOut {
     double* ct;      // [n_items][M]
@@ -886,10 +890,11 @@ __global__ void __launch_bounds__(256) changes_scan64_kernel(DevBatch b, Changes
 // Counting form (plan precision >= 1): a pair of lanes per item checks the
 // first change n1 on the mode count (T and s in FP64 at V[n1-1] and V[n1]:
 // T must jump by an odd amount) and then takes the next M - 1 changes from
-// next_change (masw_modes.cuh). An item whose FP64 counts fail is listed for
-// the linear scan.
+// next_change_f32 (masw_modes.cuh; layers32: the FP32 records). An item whose
+// FP64 counts fail is listed for the linear scan.
 __global__ void __launch_bounds__(128) changes_count64_kernel(DevBatch b, ChangesOut o, int M,
                                                               const int32_t* __restrict__ first,
+                                                              const float* __restrict__ layers32,
                                                               int32_t* linear, int32_t* n_linear) {
     const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 1);
     const int half = threadIdx.x & 1;
@@ -917,14 +922,16 @@ __global__ void __launch_bounds__(128) changes_count64_kernel(DevBatch b, Change
         st.bad = st.bad || below.T < 0 || P.T <= below.T || !((P.T - below.T) & 1);
         if (half == 0) write_change(b, o, e0, n1, P.s - below.s);
         found = 1;
+        const float* lay32 = layers32 + (size_t)l0 * LAYER_STRIDE32;
+        st.displace = route_displacement(b.route, item);
         while (found < M) {
             int d = 0;
-            const int n = next_change(st, &d);
+            const int n = next_change_f32(st, lay32, &d);
             if (n < 0) break;
             if (half == 0) write_change(b, o, e0 + found, n, d);
             ++found;
         }
-        bad = st.bad || b.route >= 3;  // (test routing 3: every item to the linear scan)
+        bad = st.bad || route_level(b.route) >= 3;  // (test routing 3: every item to the linear scan)
         if (bad && half == 0) linear[atomicAdd(n_linear, 1)] = item;
     }
     if (half == 0 && !bad)
@@ -932,8 +939,9 @@ __global__ void __launch_bounds__(128) changes_count64_kernel(DevBatch b, Change
 }
 
 cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const int32_t* first,
-                           double* ct, int32_t* idx, int32_t* status, int32_t* delta,
-                           int32_t* counters, int32_t* linear, int counting, cudaStream_t s) {
+                           const float* layers32, double* ct, int32_t* idx, int32_t* status,
+                           int32_t* delta, int32_t* counters, int32_t* linear, int counting,
+                           cudaStream_t s) {
     if (b.n_items == 0) return cudaSuccess;
     if (M < 1) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(counters, 0, CHANGES_COUNTERS * sizeof(int32_t), s);
@@ -947,8 +955,8 @@ cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const in
         return cudaGetLastError();
     }
     const long long threads = 2LL * b.n_items;
-    changes_count64_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(b, o, M, first, linear,
-                                                                           counters + 1);
+    changes_count64_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
+        b, o, M, first, layers32, linear, counters + 1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     changes_scan64_kernel<<<lblocks, 32 * wpb, 0, s>>>(b, o, M, first, counters, linear,

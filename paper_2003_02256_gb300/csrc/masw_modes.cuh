@@ -15,15 +15,17 @@
 // evaluated point above the last event, and start from it when its T equals
 // the event's. About 2 log3(n_lim) FP64 evaluations per event.
 //
-// Used for the higher modes (Algorithm 1 carried past its first change) and,
-// from V[0], for the first change of the counting search's fallback items
-// (change above the pole-free range, a mode below V[0], double crossings),
-// which an FP32 linear screen could miss when a root and a pole share a grid
-// interval.
+// next_change runs from V[0] for the first change of the counting search's
+// fallback items (change above the pole-free range, a mode below V[0], double
+// crossings), which an FP32 linear screen could miss when a root and a pole
+// share a grid interval. The higher modes (Algorithm 1 carried past its first
+// change) take next_change_f32, which locates each rise on the FP32 count and
+// certifies it on the FP64 count, with next_change as its fallback.
 #pragma once
 
 #include "masw_device.cuh"
 #include "masw_df.cuh"
+#include "masw_screen.cuh"
 
 namespace masw {
 
@@ -68,6 +70,7 @@ struct ModeSearch {
     TPoint topp;  // V[top], T = -1 until evaluated
     TPoint cand;  // smallest evaluated point above P, n = -1: none
     bool bad;     // the FP64 counts failed (rescaling, or T not monotone)
+    int displace; // test routing: added to each FP32-located event (0 normally)
 };
 
 __device__ __forceinline__ ModeSearch mode_search_init(const float* laydf, const double* lay,
@@ -88,7 +91,36 @@ __device__ __forceinline__ ModeSearch mode_search_init(const float* laydf, const
     st.topp = topp;
     st.cand = TPoint{-1, 0, 0};
     st.bad = P.T < 0 || (topp.T >= 0 && topp.T < P.T);
+    st.displace = 0;
     return st;
+}
+
+// The first point of (lo, hi.n] with T > P.T, given T(lo) = P.T and
+// hi.T > P.T: the bracket split in three per step, one point per lane. Sets
+// st.cand to the smallest evaluated point above the result, st.bad when the
+// counts are not monotone.
+__device__ inline TPoint first_rise(ModeSearch& st, int lo, TPoint hi) {
+    while (hi.n - lo > 1) {
+        const int len = hi.n - lo;
+        const int a = lo + (len + 1) / 3, bq = lo + (2 * len + 1) / 3;  // lo < a <= bq < hi
+        TPoint pa, pb;
+        eval_pair(st.laydf, st.lay, st.N, st.k, st.c0, st.dc, a, bq, st.half, st.pair, &pa, &pb);
+        if (pa.T < st.P.T || pb.T < pa.T || pb.T > hi.T) {
+            st.bad = true;
+            return hi;
+        }
+        if (pa.T > st.P.T) {
+            st.cand = bq > a ? pb : hi;
+            hi = pa;
+        } else if (pb.T > st.P.T) {
+            st.cand = hi;
+            lo = a;
+            hi = pb;
+        } else {
+            lo = bq;
+        }
+    }
+    return hi;
 }
 
 // The next sign change above st.P: its grid index with *delta = Delta s, or -1
@@ -128,30 +160,130 @@ __device__ inline int next_change(ModeSearch& st, int* delta) {
                 }
             }
         }
-        // first point of (lo, hi] with T > P.T (T(lo) = P.T, T(hi) > P.T)
-        while (hi.n - lo > 1) {
-            const int len = hi.n - lo;
-            const int a = lo + (len + 1) / 3, bq = lo + (2 * len + 1) / 3;  // lo < a <= bq < hi
-            TPoint pa, pb;
-            eval_pair(st.laydf, st.lay, st.N, st.k, st.c0, st.dc, a, bq, st.half, st.pair, &pa, &pb);
-            if (pa.T < st.P.T || pb.T < pa.T || pb.T > hi.T) {
+        hi = first_rise(st, lo, hi);
+        if (st.bad) return -1;
+        const bool odd = (hi.T - st.P.T) & 1;
+        const int ds = hi.s - st.P.s;
+        st.P = hi;
+        if (odd) {
+            *delta = ds;
+            return hi.n;
+        }
+    }
+    return -1;
+}
+
+// ------------------------------------------------ FP32-located events
+//
+// The same events located on the FP32 count mode_count_T_f and certified on
+// the FP64 count: from the last event P (FP64 T and s), the pair searches
+// (lo, top] for the first point n whose FP32 count exceeds T(P), splitting the
+// bracket in three per step, then evaluates the FP64 count at V[n-1] and V[n]
+// (one point per lane). T(V[n-1]) = T(P) and T(V[n]) > T(P) place the first
+// rise of T above P at n, an event when the jump is odd; otherwise the FP32
+// count was off next to the rise. Located one point high or low, the pair
+// takes one FP64 step of two points down or up; further off, the FP64 search
+// (first_rise, next_change) takes over from the certified bracket. Per event
+// about log3(n_lim) FP32 steps and one FP64 step, against 2 log3(n_lim) FP64
+// evaluations per lane for next_change.
+
+// First index in (lo, top) whose FP32 count is at least target, else top.
+static __device__ __noinline__ int pair_search_T32(const float* __restrict__ lay32, int N,
+                                                   float kf, float c0f, float dcf, int lo, int top,
+                                                   int target, int half, unsigned pair) {
+    int hi = top;
+    while (hi - lo > 1) {
+        const int len = hi - lo;
+        const int a = lo + (len + 1) / 3, bq = lo + (2 * len + 1) / 3;  // lo < a <= bq < hi
+        const int q = half ? bq : a;
+        const int c = mode_count_T_f(lay32, N, kf, fmaf((float)q, dcf, c0f));
+        const int co = __shfl_xor_sync(pair, c, 1);
+        const int ca = half ? co : c, cb = half ? c : co;
+        if (ca >= target) {
+            hi = a;
+        } else if (cb >= target) {
+            lo = a;
+            hi = bq;
+        } else {
+            lo = bq;
+        }
+    }
+    return hi;
+}
+
+// next_change with events located on the FP32 count (lay32: the model's FP32
+// records). Same contract: both lanes call it and get the same result.
+__device__ inline int next_change_f32(ModeSearch& st, const float* __restrict__ lay32,
+                                      int* delta) {
+    const float kf = (float)st.k, c0f = (float)st.c0, dcf = (float)st.dc;
+    int lo = st.P.n;  // T(V[lo]) = T(P)
+    st.cand = TPoint{-1, 0, 0};
+    while (!st.bad && lo < st.top) {
+        if (st.topp.T >= 0 && st.topp.T == st.P.T) return -1;  // no event below the limit
+        int n = pair_search_T32(lay32, st.N, kf, c0f, dcf, lo, st.top, st.P.T + 1, st.half,
+                                st.pair);
+        if (st.displace) n = min(max(n + st.displace, lo + 1), st.top);
+        TPoint a, b;
+        eval_pair(st.laydf, st.lay, st.N, st.k, st.c0, st.dc, n - 1 > lo ? n - 1 : -1, n,
+                  st.half, st.pair, &a, &b);
+        if (n - 1 <= lo) a = TPoint{lo, st.P.T, st.P.s};
+        if (n == st.top) st.topp = b;
+        if (a.T < st.P.T || b.T < a.T || (st.topp.T >= 0 && b.T > st.topp.T)) {
+            st.bad = true;
+            return -1;
+        }
+        TPoint hi;
+        if (a.T == st.P.T && b.T > st.P.T) {
+            hi = b;  // certified: the first rise is at n
+        } else if (b.T == st.P.T) {
+            // no rise up to n: one step of two points up
+            if (n >= st.top) return -1;
+            TPoint u, v;
+            const int n2 = n + 2 <= st.top ? n + 2 : -1;
+            eval_pair(st.laydf, st.lay, st.N, st.k, st.c0, st.dc, n + 1, n2, st.half, st.pair,
+                      &u, &v);
+            if (u.n == st.top) st.topp = u;
+            if (v.n == st.top) st.topp = v;
+            if (u.T < st.P.T || (v.n >= 0 && v.T < u.T)) {
                 st.bad = true;
                 return -1;
             }
-            if (pa.T > st.P.T) {
-                st.cand = bq > a ? pb : hi;
-                hi = pa;
-            } else if (pb.T > st.P.T) {
-                st.cand = hi;
-                lo = a;
-                hi = pb;
+            if (u.T > st.P.T) {
+                hi = u;
+            } else if (v.n >= 0 && v.T > st.P.T) {
+                hi = v;
             } else {
-                lo = bq;
+                lo = v.n >= 0 ? v.n : n + 1;  // FP32 off: FP64 search from the certified point
+                st.cand = TPoint{lo, st.P.T, st.P.s};
+                return next_change(st, delta);
+            }
+        } else {
+            // a.T > P.T: the first rise is at or below n - 1; one step down
+            TPoint u, v;
+            const int n3 = n - 3 > lo ? n - 3 : -1, n2 = n - 2 > lo ? n - 2 : -1;
+            eval_pair(st.laydf, st.lay, st.N, st.k, st.c0, st.dc, n3, n2, st.half, st.pair, &u,
+                      &v);
+            if (n3 < 0) u = TPoint{lo, st.P.T, st.P.s};
+            if (n2 < 0) v = u;
+            if (u.T < st.P.T || v.T < u.T || v.T > a.T) {
+                st.bad = true;
+                return -1;
+            }
+            if (v.T == st.P.T) {
+                hi = a;  // rise at n - 1
+            } else if (u.T == st.P.T) {
+                hi = v;  // rise at n - 2
+            } else {
+                st.cand = TPoint{-1, 0, 0};
+                hi = first_rise(st, lo, u);  // further below: FP64 search in (lo, n - 3]
+                if (st.bad) return -1;
+                st.cand = TPoint{-1, 0, 0};
             }
         }
         const bool odd = (hi.T - st.P.T) & 1;
         const int ds = hi.s - st.P.s;
         st.P = hi;
+        lo = hi.n;
         if (odd) {
             *delta = ds;
             return hi.n;

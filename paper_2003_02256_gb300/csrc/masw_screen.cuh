@@ -222,6 +222,52 @@ __device__ __forceinline__ int inertia_f(const float* __restrict__ lay, int N, f
     return det_core_f<1>(lay, N, k, c);
 }
 
+// J0 of one layer (modes with both faces clamped below c) in FP32 from the
+// FP32 record: the thickness-halving count of clamped_modes (masw_device.cuh)
+// with wave_fns_f at the finest level, h / 2^lv with 2^lv > x =
+// k h sqrt(c^2/beta^2 - 1) / pi >= 2^(lv-1), and the doubling
+// E(2x) = E^2, C(2x) = 2C^2 - E^2, Sd(2x) = 2 Sd C, Sm(2x) = 2 Sm C up to h.
+// For locating events only: every located event is certified on the FP64
+// count.
+__device__ __forceinline__ int clamped_modes_f(const float* __restrict__ L, float k, float c2) {
+    const float q = c2 * L[F_IB2];
+    if (!(q > 1.0f)) return 0;
+    const float kh = k * L[F_H];
+    const float x = kh * sqrtf(q - 1.0f) * 0.318309886f;  // 1/pi
+    if (!(x >= 1.0f && x < 1.0e30f)) return 0;
+    const int lv = ((__float_as_int(x) >> 23) & 0xff) - 126;  // 2^lv > x >= 2^(lv-1)
+    const float khf = kh * __int_as_float((127 - lv) << 23);  // kh 2^-lv, exact
+    WaveF R = wave_fns_f(khf, fmaf(-c2, L[F_IA2], 1.0f));
+    WaveF S = wave_fns_f(khf, 1.0f - q);
+    int J = 0;
+    for (int j = lv; j >= 1; --j) {
+        if (j < lv) {
+            R = WaveF{R.E * R.E, fmaf(2.0f * R.C, R.C, -R.E * R.E), 2.0f * R.Sd * R.C,
+                      2.0f * R.Sm * R.C};
+            S = WaveF{S.E * S.E, fmaf(2.0f * S.C, S.C, -S.E * S.E), 2.0f * S.Sd * S.C,
+                      2.0f * S.Sm * S.C};
+        }
+        const float D = fmaf(2.0f, fmaf(R.E, S.E, -R.C * S.C), fmaf(R.Sd, S.Sd, R.Sm * S.Sm));
+        const float an = fmaf(R.C, S.Sd, -S.C * R.Sm);
+        const float dn = fmaf(S.C, R.Sd, -R.C * S.Sm);
+        J = 2 * J + (int)((an < 0.0f) != (D < 0.0f)) + (int)((dn < 0.0f) != (D < 0.0f));
+    }
+    return J;
+}
+
+// The Wittrick-Williams mode count T = s + 2 J0 in FP32 (inertia_f and
+// clamped_modes_f): exact T never decreases along the grid and jumps by an odd
+// amount where det K changes sign; the FP32 value may be off next to an event.
+// Requires c < beta_halfspace.
+__device__ __forceinline__ int mode_count_T_f(const float* __restrict__ lay, int N, float k,
+                                              float c) {
+    const int s = inertia_f(lay, N, k, c);
+    const float c2 = c * c;
+    int j0 = 0;
+    for (int j = 0; j < N; ++j) j0 += clamped_modes_f(lay + j * LAYER_STRIDE32, k, c2);
+    return s + 2 * j0;
+}
+
 }  // namespace masw
 
 // ---------------------------------------------------------------------

@@ -582,12 +582,13 @@ def test_extreme_models_two_precision_equals_fp64_scan(masw, oracle_lib, seed):
                         explain=(oracle_lib, m, g, items))
 
 
-@pytest.mark.parametrize("route", [1, 2, 3])
+@pytest.mark.parametrize("route", [1, 2, 3, 4])
 def test_forced_routes_give_the_fp64_scan(masw, route):
     """masw_set_route sends every item through the paths ordinary inputs
     rarely reach: the linear FP32 scan from V[0] (1), the FP64 mode-count
-    search after a failed check (2), the FP64 scan from V[0] (3). Every plan
-    still reports the pure FP64 scan's indices, on uniform, ragged and
+    search after a failed check (2), the FP64 scan from V[0] (3), higher-mode
+    events located off by -7..+3 points before their certificate (4). Every
+    plan still reports the pure FP64 scan's indices, on uniform, ragged and
     extreme models, and the higher modes match too."""
     cases = [W.uniform_batch(n_models=32, n_lambda=40), W.ragged_batch(n_models=48),
              W.extreme_batch(n_models=64, seed=W.SEED + 11)]
@@ -605,8 +606,10 @@ def test_forced_routes_give_the_fp64_scan(masw, route):
             assert all(np.array_equal(x, y) for x, y in zip(ch[1:], ref_ch[1:])), route
             if route == 3:
                 assert b.last_changes_linear() == m.n_items - int(np.sum(ref[2] != 0))
+            if route == 4:  # recovered by the FP64 steps and search, not the linear scan
+                assert b.last_changes_linear() <= max(2, m.n_items // 1000)
             b.set_route(0)
     with masw.Batch(*W.uniform_batch(n_models=2, n_lambda=2)) as b:
-        for bad in (-1, 4):
+        for bad in (-1, 5):
             with pytest.raises(masw.MaswError):
                 b.set_route(bad)
