@@ -369,6 +369,16 @@ int masw_last_scan_fallback(const masw_batch* batch, int32_t* n);
  * cuda_stream. */
 int masw_exp_check(int32_t n, const double* x, double* y_lib, double* y_cuda, void* cuda_stream);
 
+/* The library's own FP64 sine and cosine for 0 <= x < 5 pi / 4 (Cody-Waite
+ * reduction by a multiple of pi/2 and Taylor series; used by the
+ * clamped-layer mode count, whose arguments stay below pi) and CUDA's sincos
+ * at the same n host points x (each in [0, 1.25 * 3.141592653589793], else
+ * MASW_EINVAL), into host arrays s_lib, c_lib, s_cuda, c_cuda; a diagnostic
+ * for testing its error. No paper counterpart. Allocates and frees a device
+ * buffer of 5n doubles; synchronises cuda_stream. */
+int masw_sincos_check(int32_t n, const double* x, double* s_lib, double* c_lib, double* s_cuda,
+                      double* c_cuda, void* cuda_stream);
+
 /* The element stiffness of finite layer layer[t] (0-based) of item item[t]'s
  * model at test velocity c[t] > 0, from the FP64 element and from the
  * double-float element of the counting certificate; a diagnostic for testing

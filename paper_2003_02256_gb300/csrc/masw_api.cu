@@ -78,6 +78,7 @@ struct masw_batch {
     float* d_layers32 = nullptr;
     float* d_layers_df = nullptr;  // double-float records of the counting certificate
     int32_t* d_n32 = nullptr;
+    int32_t* d_cert = nullptr;  // per item: the counting certificate's FP64 counts (ScanOut)
     int32_t* d_search = nullptr;
     int32_t* d_unres = nullptr;
     int32_t* d_fallback = nullptr;
@@ -317,7 +318,8 @@ static void free_batch(masw_batch* B) {
                     B->d_item_model, B->d_order_sorted, B->d_order_natural, B->d_grad_off,
                     B->d_counter, B->d_ct, B->d_idx, B->d_status, B->d_croot, B->d_rows, B->d_bs,
                     B->d_dphi, B->d_ce, B->d_misfit, B->d_gb, B->d_gh, B->d_layers32, B->d_layers_df,
-                    B->d_n32, B->d_search, B->d_unres, B->d_fallback, B->d_counters, B->d_upd, B->d_upd_err,
+                    B->d_n32, B->d_cert, B->d_search, B->d_unres, B->d_fallback, B->d_counters,
+                    B->d_upd, B->d_upd_err,
                     B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta,
                     B->d_chg_counters, B->d_lk_ct, B->d_lk_idx};
     for (void* p : ptrs)
@@ -368,7 +370,7 @@ static ScanPlan to_scan_plan(const masw_batch* B, const masw_plan& p) {
 static cudaError_t enqueue_scan(masw_batch* B, const masw_plan& p, cudaStream_t s,
                                 bool phase_events = false) {
     if (p.precision >= 1) {
-        ScanOut o{B->d_ct, B->d_idx, B->d_status};
+        ScanOut o{B->d_ct, B->d_idx, B->d_status, B->d_cert};
         return launch_screen_scan(B->dev(p.ordered != 0), o, to_scan_plan(B, p), B->d_layers32,
                                   B->d_n32, B->d_search, B->d_unres, B->d_fallback, B->d_counters,
                                   p.precision == 2, 0, (int)B->n_items, s,
@@ -553,7 +555,7 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
         dev_alloc(&B->d_grad_off, nw + 1) || dev_alloc(&B->d_counter, 1) ||
         dev_alloc(&B->d_ct, nw) || dev_alloc(&B->d_idx, nw) || dev_alloc(&B->d_status, nw) ||
         dev_alloc(&B->d_layers32, rec32.size()) || dev_alloc(&B->d_layers_df, recdf.size()) ||
-        dev_alloc(&B->d_n32, nw) ||
+        dev_alloc(&B->d_n32, nw) || dev_alloc(&B->d_cert, nw) ||
         dev_alloc(&B->d_search, nw) || dev_alloc(&B->d_unres, nw) || dev_alloc(&B->d_fallback, nw) ||
         dev_alloc(&B->d_counters, SCAN_COUNTERS)) {
         free_batch(B);
@@ -717,7 +719,8 @@ int masw_dispersion_changes(masw_batch* B, int32_t max_changes, double* ct, int3
     int rc0 = run_scan(B);
     if (rc0) return rc0;
     CK(launch_changes(B->dev(B->plan.ordered != 0), to_scan_plan(B, B->plan), max_changes,
-                      B->d_idx, B->d_layers32, B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta,
+                      B->d_idx, B->plan.precision == 2 ? B->d_cert : nullptr, B->d_layers32,
+                      B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta,
                       B->d_chg_counters, B->d_chg_counters + CHANGES_COUNTERS,
                       B->plan.precision >= 1, B->stream));
     B->changes_counted = B->plan.precision >= 1;
@@ -789,6 +792,28 @@ int masw_element_check(masw_batch* B, int32_t n, const int32_t* item, const int3
     return MASW_OK;
 }
 
+int masw_sincos_check(int32_t n, const double* x, double* s_lib, double* c_lib, double* s_cuda,
+                      double* c_cuda, void* cuda_stream) {
+    if (n < 0 || (n > 0 && (!x || !s_lib || !c_lib || !s_cuda || !c_cuda))) return MASW_EINVAL;
+    for (int32_t i = 0; i < n; ++i)
+        if (!(x[i] >= 0.0 && x[i] <= 1.25 * 3.141592653589793)) return MASW_EINVAL;
+    if (n == 0) return MASW_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    double* d = nullptr;
+    if (dev_alloc(&d, 5 * (size_t)n)) return MASW_ENOMEM;
+    const size_t nn = (size_t)n;
+    cudaError_t e = cudaMemcpyAsync(d, x, nn * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_sincos_check(n, d, d + nn, d + 2 * nn, d + 3 * nn, d + 4 * nn, s);
+    double* outs[4] = {s_lib, c_lib, s_cuda, c_cuda};
+    for (int q = 0; q < 4 && e == cudaSuccess; ++q)
+        e = cudaMemcpyAsync(outs[q], d + (q + 1) * nn, nn * sizeof(double), cudaMemcpyDeviceToHost,
+                            s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    CK(e);
+    return MASW_OK;
+}
+
 int masw_exp_check(int32_t n, const double* x, double* y_lib, double* y_cuda, void* cuda_stream) {
     if (n < 0 || (n > 0 && (!x || !y_lib || !y_cuda))) return MASW_EINVAL;
     for (int32_t i = 0; i < n; ++i)
@@ -815,7 +840,7 @@ int masw_dispersion_plain(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* s
     masw_plan p = B->plan;
     p.persistent = 0;
     p.ordered = 0;
-    ScanOut o{B->d_ct, B->d_idx, B->d_status};
+    ScanOut o{B->d_ct, B->d_idx, B->d_status, B->d_cert};
     DevBatch d = B->dev(false);
     ScanPlan sp = to_scan_plan(B, p);
     CK(cudaEventRecord(B->ev0, B->stream));

@@ -33,7 +33,13 @@ struct PairCount {
     int n;      // the search's index when the certificate failed (>= 1), or -1
     int start;  // cert and n < 1: a linear scan's start (npf when the range holds no
                 // change, the located point after an even FP64 count, else 0)
+    int counts; // cert inside the pole-free range: the certificate's FP64 counts,
+                // s(V[cert]) << 16 | s(V[cert-1]) (there J0 = 0, so T = s); else -1
 };
+
+__device__ __forceinline__ int pack_counts(int s_lo, int s_hi) {
+    return (s_lo >= 0 && s_hi >= s_lo && s_hi < 32768) ? (s_hi << 16) | s_lo : -1;
+}
 
 // First grid index in (lo, top] whose FP32 negative-eigenvalue count is at
 // least `target`, the count being non-decreasing there and below `target` at
@@ -83,7 +89,7 @@ __device__ __forceinline__ PairCount count_certify_pair(const float* __restrict_
     const float kf = (float)k;
     const float c0f = (float)c0, dcf = (float)dc;
     const int npf = pole_free_points_f(lay32, N, kf, c0f, dcf, nlim);
-    PairCount out{-1, -1, 0};
+    PairCount out{-1, -1, 0, -1};
     if (npf < 1) return out;
     // count 0 at c = 0 (static stiffness positive definite); the FP64
     // certificate decides the parity at the first nonzero point
@@ -98,6 +104,7 @@ __device__ __forceinline__ PairCount count_certify_pair(const float* __restrict_
     const int va = half ? vo : v;  // V[n-1]
     const int vb = half ? v : vo;  // V[n]
     int cert = (va == 0 && vb > 0 && (vb & 1)) ? n : -1;
+    int s_lo = va, s_hi = vb;  // the FP64 counts at cert - 1 and cert
     if (cert < 0 && va >= 0 && vb >= 0) {
         const bool up = va == 0 && vb == 0;
         const bool down = va > 0 && n >= 3;
@@ -109,16 +116,28 @@ __device__ __forceinline__ PairCount count_certify_pair(const float* __restrict_
             if (up) {
                 // count 0 at n; first nonzero at n+1, or at n+2 with n+1 inside the range
                 if (c_lo > 0) {
-                    if (c_lo & 1) cert = n + 1;
+                    if (c_lo & 1) {
+                        cert = n + 1;
+                        s_lo = vb;
+                        s_hi = c_lo;
+                    }
                 } else if (c_lo == 0 && c_hi > 0 && (c_hi & 1) && n + 1 < npf) {
                     cert = n + 2;
+                    s_lo = c_lo;
+                    s_hi = c_hi;
                 }
             } else {
                 // count nonzero at n-1; first nonzero at n-1 or n-2
                 if (c_hi == 0) {
-                    if (va & 1) cert = n - 1;
+                    if (va & 1) {
+                        cert = n - 1;
+                        s_lo = c_hi;
+                        s_hi = va;
+                    }
                 } else if (c_hi > 0 && c_lo == 0 && (c_hi & 1)) {
                     cert = n - 2;
+                    s_lo = c_lo;
+                    s_hi = c_hi;
                 }
             }
         }
@@ -134,7 +153,11 @@ __device__ __forceinline__ PairCount count_certify_pair(const float* __restrict_
             const int u = det_inertia_df(laydf, lay, N, k, grid_c(c0, dc, m - 1 + half));
             const int uo = __shfl_xor_sync(pair, u, 1);
             const int ua = half ? uo : u, ub = half ? u : uo;
-            if (ua == vb && ub > vb && (ub & 1)) cert = m;
+            if (ua == vb && ub > vb && (ub & 1)) {
+                cert = m;
+                s_lo = ua;
+                s_hi = ub;
+            }
         }
         if (cert < 0) {
             out.start = n;
@@ -143,6 +166,7 @@ __device__ __forceinline__ PairCount count_certify_pair(const float* __restrict_
     }
     out.cert = cert;
     out.n = cert >= 1 ? -1 : n;
+    if (cert >= 1 && cert < npf) out.counts = pack_counts(s_lo, s_hi);
     return out;
 }
 

@@ -671,10 +671,48 @@ __device__ __forceinline__ double exp_neg(double x) {
 
 struct Wave { double E, C, Sd, Sm; };
 
+// sin x and cos x for 0 <= x < 5 pi / 4 (the clamped-layer count's finest
+// level keeps its arguments below pi). Cody-Waite reduction by the nearest
+// multiple j of pi/2 (j <= 2), with pi/2 split into the double P1 nearest it
+// and the remainder P2: x - j P1 is exact (Sterbenz), and the dropped third
+// part of pi/2 (below 1e-32) leaves r within an ulp. Taylor series in
+// r in [-pi/4, pi/4]: sin through r^17 (remainder below r^19/19! < 1e-19),
+// cos through r^16 (below r^18/18! < 3e-18), Horner in r^2.
+__device__ __forceinline__ void sincos_small(double x, double* sn, double* cs) {
+    const double P1 = 1.5707963267948966;     // pi/2 rounded to double
+    const double P2 = 6.123233995736766e-17;  // pi/2 - P1
+    const double j = rint(x * 0.6366197723675814);  // x * 2/pi
+    const double r = fma(-j, P2, fma(-j, P1, x));
+    const double z = r * r;
+    double ps = -inv_fact(17);
+    ps = fma(ps, z, inv_fact(15));
+    ps = fma(ps, z, -inv_fact(13));
+    ps = fma(ps, z, inv_fact(11));
+    ps = fma(ps, z, -inv_fact(9));
+    ps = fma(ps, z, inv_fact(7));
+    ps = fma(ps, z, -inv_fact(5));
+    ps = fma(ps, z, inv_fact(3));
+    const double sr = fma(-r * z, ps, r);
+    double pc = inv_fact(16);
+    pc = fma(pc, z, -inv_fact(14));
+    pc = fma(pc, z, inv_fact(12));
+    pc = fma(pc, z, -inv_fact(10));
+    pc = fma(pc, z, inv_fact(8));
+    pc = fma(pc, z, -inv_fact(6));
+    pc = fma(pc, z, inv_fact(4));
+    pc = fma(pc, z, -inv_fact(2));
+    const double cr = fma(pc, z, 1.0);
+    const int q = (int)j;
+    *sn = q == 0 ? sr : (q == 1 ? cr : -sr);
+    *cs = q == 0 ? cr : (q == 1 ? -sr : -cr);
+}
+
 // Scaled even functions of w = sqrt(w2) at kh: (E, C, Sd, Sm) equal
 // e^-x * (1, cosh x, sinh(x)/w, w sinh x) with x = kh w for real w and large
 // x, and (1, cosh, sinh/w, w sinh) otherwise (imaginary w gives cos/sin).
-// kh2 = kh * kh, formed once for the element's two waves.
+// kh2 = kh * kh, formed once for the element's two waves. SMALL: kh |w| is
+// below 5 pi / 4 for imaginary w (sincos_small).
+template <bool SMALL = false>
 __device__ __forceinline__ Wave wave_fns(double kh, double kh2, double w2) {
     double u = kh2 * w2;
     Wave o;
@@ -717,7 +755,10 @@ __device__ __forceinline__ Wave wave_fns(double kh, double kh2, double w2) {
         double rw = rsqrt(-w2);
         double w = -w2 * rw;
         double sn, cs;
-        sincos(kh * w, &sn, &cs);
+        if (SMALL)
+            sincos_small(kh * w, &sn, &cs);
+        else
+            sincos(kh * w, &sn, &cs);
         o.E = 1.0;
         o.C = cs;
         o.Sd = sn * rw;
@@ -966,8 +1007,9 @@ __device__ inline int clamped_modes(const double* __restrict__ L, double k, doub
     const int lv = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1022;
     const double khf = scale_pow2(k * L[L_H], -lv);
     const double khf2 = khf * khf;
-    Wave R = wave_fns(khf, khf2, 1.0 - c2 * L[L_IA2]);
-    Wave S = wave_fns(khf, khf2, 1.0 - q);
+    // kh w < pi at this level for both waves (c^2/alpha^2 - 1 < q - 1)
+    Wave R = wave_fns<true>(khf, khf2, 1.0 - c2 * L[L_IA2]);
+    Wave S = wave_fns<true>(khf, khf2, 1.0 - q);
     int J = 0;
     for (int j = lv; j >= 1; --j) {
         if (j < lv) {

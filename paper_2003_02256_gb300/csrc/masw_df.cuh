@@ -686,7 +686,8 @@ static __device__ __noinline__ int det_inertia_df(const float* __restrict__ layd
 // neither does T = J + J0 = s + 2 J0, whose parity is that of s: det K changes
 // sign between two test velocities exactly when T jumps by an odd amount
 // between them. laydf as for det_inertia_df. Requires c < beta_halfspace.
-__device__ inline int mode_count_T_df(const float* __restrict__ laydf,
+// Out of line: the mode-count searches call it from several places.
+static __device__ __noinline__ int mode_count_T_df(const float* __restrict__ laydf,
                                       const double* __restrict__ lay, int N, double k, double c,
                                       int* s_out) {
     const int s = det_inertia_df(laydf, lay, N, k, c);

@@ -43,6 +43,10 @@ struct ScanOut {
     double* ct;
     int32_t* idx;
     int32_t* status;
+    // counting kernel (or nullptr): per item PairCount::counts, the FP64
+    // counts of the certificate, -1 when the item was not certified in the
+    // pole-free range
+    int32_t* cert_counts = nullptr;
 };
 
 // Launch configuration of the scan (the batch plan).
@@ -79,7 +83,7 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
 // (masw_kernels.cu).
 constexpr int CHANGES_COUNTERS = 2;
 cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const int32_t* first,
-                           const float* layers32, double* ct, int32_t* idx, int32_t* status,
+                           const int32_t* cert_counts, const float* layers32, double* ct, int32_t* idx, int32_t* status,
                            int32_t* delta, int32_t* counters, int32_t* linear, int counting,
                            cudaStream_t s);
 
@@ -117,6 +121,8 @@ cudaError_t launch_element_check(const DevBatch& b, int n, const int32_t* item, 
                                  const double* c, double* fp64, double* df, cudaStream_t s);
 cudaError_t launch_exp_check(int n, const double* x, double* y_lib, double* y_cuda,
                              cudaStream_t s);
+cudaError_t launch_sincos_check(int n, const double* x, double* s_lib, double* c_lib,
+                                double* s_cuda, double* c_cuda, cudaStream_t s);
 cudaError_t launch_fp64_peak(int blocks, int threads, int iters, double* sink, cudaStream_t s);
 
 }  // namespace masw

@@ -19,7 +19,8 @@
 //                         fallback items take fallback32_kernel (linear FP32
 //                         scan) and verify64_list_kernel (the check).
 //  first_count64_kernel   both two-precision plans: items that failed a check,
-//                         FP64 search on the mode count from V[0].
+//                         search on the mode count from V[0] (FP32-located,
+//                         FP64-certified rises).
 //  resolve64_kernel       items whose FP64 counts failed: FP64 scan from V[0].
 // Beyond the first change:
 //  changes_count64_kernel higher modes, FP32 search on the mode count, each
@@ -38,7 +39,8 @@
 //  grad_reduce_kernel     dPhi/dtheta = sum_j dPhi/dC_j dC_j/dtheta per model.
 //  validate_models_kernel, build_records_kernel, update_beta_h_kernel
 //                         model updates on the device.
-//  exp_check_kernel       the library's exponential beside CUDA's (tests).
+//  exp_check_kernel,      the library's exponential, sine and cosine beside
+//  sincos_check_kernel    CUDA's (tests).
 // "FP64 count" below: the Wittrick-Williams count of the FP64 Schur
 // recurrence over element stiffnesses in double-float (det_inertia_df,
 // mode_count_T_df in masw_df.cuh); the FP64 scans (scan_kernel,
@@ -180,7 +182,8 @@ cudaError_t launch_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p, 
 // verify64_list_kernel (the check of 2. over the list); uncertified and
 // unverified items go to the search list.
 // Both: first_count64_kernel searches the listed items' first change on the
-// FP64 mode count from V[0]; items whose FP64 counts fail take
+// mode count from V[0] (each rise located on the FP32 count, certified on the
+// FP64 count); items whose FP64 counts fail take
 // resolve64_kernel, the FP64 scan from V[0].
 // Every reported index is where the FP64 mode count first jumps by an odd
 // amount (the FP64 sign first changes) or, for the last few, the FP64 scan's.
@@ -352,7 +355,7 @@ __device__ __forceinline__ void write_result(const DevBatch& b, const ScanOut& o
 // = T(V[0]) leaves no change (no event at all) below n, an odd T(V[n]) -
 // T(V[n-1]) makes n a change; with no change seen, T(V[nlim-1]) = T(V[0]).
 // Signs alone would pass two changes that an FP32 screen missed together (a
-// root and a pole inside one grid interval). Anything else goes to the FP64
+// root and a pole inside one grid interval). Anything else goes to the
 // mode-count search from V[0] (first_count64_kernel).
 __device__ __forceinline__ void verify_item(const DevBatch& b, const ScanOut& o, int item, int n,
                                             int32_t* search, int32_t* n_search) {
@@ -537,6 +540,7 @@ __global__ void __launch_bounds__(B, (B == 256 ? 3 : 896 / B)) count_certify_ker
         if (!half) {
             n32[item] = -1;
             write_result(b, o, item, -1);
+            if (o.cert_counts) o.cert_counts[item] = -1;
         }
         return;
     }
@@ -545,6 +549,7 @@ __global__ void __launch_bounds__(B, (B == 256 ? 3 : 896 / B)) count_certify_ker
     const PairCount r = count_certify_pair(layers32 + (size_t)lo_rec * LAYER_STRIDE32, laydf, lay, N,
                                            b.k[item], b.c0, b.dc, nlim, half, pair);
     if (half) return;
+    if (o.cert_counts) o.cert_counts[item] = route_level(b.route) >= 1 ? -1 : r.counts;
     if (route_level(b.route) >= 1) {  // test routing: every item through the linear FP32 scan from V[0]
         n32[item] = 0;
         fallback[atomicAdd(n_fallback, 1)] = item;
@@ -565,92 +570,44 @@ __global__ void __launch_bounds__(B, (B == 256 ? 3 : 896 / B)) count_certify_ker
 // an even jump of the mode count below their first change, a mode trapped in
 // a low-velocity layer next to a pole of that layer): Algorithm 1's first
 // change as the first odd jump of the FP64 mode count T = s + 2 J0 above V[0].
-// A group of G lanes per item (groups pop the list): lane l of the group
-// holds T at V[x_l], x_l = l top / (G - 1) (x_0 = 0, x_{G-1} = top), for the
-// whole item; an event's bracket between two of those points is narrowed with
-// G - 1 interior points per round until it is one grid step wide; an odd jump
-// ends the search, an even one moves on to the next event. n32 gets the index
-// found (-1: none). Items whose FP64 counts fail (rescaling, or T not
-// monotone at the evaluated points) go to the FP64 re-scan from V[0].
-template <int G>
-__global__ void __launch_bounds__(256) first_count64_kernel(DevBatch b, ScanOut o, int32_t* n32,
-                                                            const int32_t* __restrict__ list,
-                                                            const int32_t* __restrict__ n_list,
-                                                            int32_t* counter, int32_t* unresolved,
-                                                            int32_t* n_unresolved) {
-    static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "lanes per item: a power of two");
-    const int lane = threadIdx.x & 31;
-    const int gl = lane & (G - 1);
-    const int gbase = lane - gl;
-    const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << gbase);
+// A pair of lanes per item (pairs pop the list): the FP64 counts at V[0] and
+// V[top], then next_change_f32 (masw_modes.cuh), which locates each rise of T
+// on its FP32 value and certifies it on the FP64 count, an odd jump ending
+// the search and an even one moving on. n32 gets the index found (-1: none).
+// Items whose FP64 counts fail (rescaling, or T not monotone at the evaluated
+// points) go to the FP64 re-scan from V[0]. On the 8192-model ragged batch
+// (1773 listed items) this took 1.2 ms as a 16-lane multisection on the FP64
+// count alone.
+__global__ void __launch_bounds__(32) first_count64_kernel(DevBatch b, ScanOut o, int32_t* n32,
+                                                           const float* __restrict__ layers32,
+                                                           const int32_t* __restrict__ list,
+                                                           const int32_t* __restrict__ n_list,
+                                                           int32_t* counter, int32_t* unresolved,
+                                                           int32_t* n_unresolved) {
+    const int half = threadIdx.x & 1;
+    const unsigned pair = 3u << (threadIdx.x & 30);
     const int total = *n_list;
     if (total == 0) return;  // the usual case: no atomics on the queue
     for (;;) {
         int t = 0;
-        if (gl == 0) t = atomicAdd(counter, 1);
-        t = __shfl_sync(gmask, t, 0, G);
-        if (t >= total) return;  // the whole group leaves together
+        if (!half) t = atomicAdd(counter, 1);
+        t = __shfl_xor_sync(pair, t, 1) + t;  // one lane holds 0
+        if (t >= total) return;  // both lanes of the pair leave together
         const int item = list[t];
         const int m = b.item_model[item];
         const int l0 = b.model_loff[m];
         const int N = b.model_loff[m + 1] - l0 - 1;
         const double* lay = b.layers + (size_t)l0 * LAYER_STRIDE;
+        const float* laydf = records_df(b, l0);
         const double k = b.k[item];
         const int top = b.model_nlim[m] - 1;  // >= 1 for listed items
-        const int xl = (int)(((long long)gl * top) / (G - 1));
-        int sl;
-        const float* laydf = records_df(b, l0);
-        const int Tl = mode_count_T_df(laydf, lay, N, k, grid_c(b.c0, b.dc, xl), &sl);
-        const int Tprev = __shfl_up_sync(gmask, Tl, 1, G);
-        bool bad = (__ballot_sync(gmask, Tl < 0 || (gl > 0 && Tl < Tprev)) & gmask) != 0;
-        int Pn = 0, PT = __shfl_sync(gmask, Tl, 0, G), res = -1;
-        while (!bad) {
-            // coarse bracket: first sample above P with a larger T
-            const unsigned msk = (__ballot_sync(gmask, xl > Pn && Tl > PT) & gmask) >> gbase;
-            if (!msk) break;  // no event up to V[top]
-            const int f = __ffs(msk) - 1;
-            int hn = __shfl_sync(gmask, xl, f, G), hT = __shfl_sync(gmask, Tl, f, G);
-            const int xb = __shfl_sync(gmask, xl, f > 0 ? f - 1 : 0, G);
-            if (xb > Pn && __shfl_sync(gmask, Tl, f > 0 ? f - 1 : 0, G) != PT) {
-                bad = true;  // T not monotone between P and that sample
-                break;
-            }
-            int lo = max(Pn, xb);
-            while (hn - lo > 1) {
-                const int len = hn - lo;
-                const int y = lo + (int)(((long long)(gl + 1) * len) / G);
-                const bool in = gl < G - 1 && y > lo && y < hn;
-                int sy = 0, Ty = -1;
-                if (in) Ty = mode_count_T_df(laydf, lay, N, k, grid_c(b.c0, b.dc, y), &sy);
-                const int Typ = __shfl_up_sync(gmask, Ty, 1, G);
-                const bool inp = __shfl_up_sync(gmask, (int)in, 1, G) != 0;
-                if ((__ballot_sync(gmask, in && (Ty < PT || Ty > hT || (gl > 0 && inp && Ty < Typ))) &
-                     gmask) != 0) {
-                    bad = true;
-                    break;
-                }
-                const unsigned up = (__ballot_sync(gmask, in && Ty > PT) & gmask) >> gbase;
-                const unsigned lw = (__ballot_sync(gmask, in && Ty == PT) & gmask) >> gbase;
-                if (up) {
-                    const int g = __ffs(up) - 1;
-                    hn = __shfl_sync(gmask, y, g, G);
-                    hT = __shfl_sync(gmask, Ty, g, G);
-                    const unsigned below = lw & ((1u << g) - 1u);
-                    if (below) lo = __shfl_sync(gmask, y, 31 - __clz(below), G);
-                } else {
-                    lo = __shfl_sync(gmask, y, 31 - __clz(lw), G);  // lw != 0: len >= 2
-                }
-            }
-            if (bad) break;
-            if ((hT - PT) & 1) {
-                res = hn;
-                break;
-            }
-            Pn = hn;  // an even jump: no sign change here
-            PT = hT;
-        }
-        if (gl == 0) {
-            if (bad || route_level(b.route) >= 3) {  // (test routing 3: every item to the FP64 scan)
+        TPoint p0, ptop;
+        eval_pair(laydf, lay, N, k, b.c0, b.dc, 0, top, half, pair, &p0, &ptop);
+        ModeSearch st = mode_search_init(laydf, lay, N, k, b.c0, b.dc, top, half, pair, p0, ptop);
+        int d = 0;
+        const int res = next_change_f32(st, layers32 + (size_t)l0 * LAYER_STRIDE32, &d);
+        if (!half) {
+            if (st.bad || route_level(b.route) >= 3) {  // (test routing 3: every item to the FP64 scan)
                 n32[item] = 0;
                 unresolved[atomicAdd(n_unresolved, 1)] = item;
             } else {
@@ -658,15 +615,8 @@ __global__ void __launch_bounds__(256) first_count64_kernel(DevBatch b, ScanOut 
                 write_result(b, o, item, res);
             }
         }
-        __syncwarp(gmask);
     }
 }
-
-// Lanes per item of first_count64_kernel. Evaluations per event fall with G
-// and rounds per event rise; the kernel ends with its slowest items (many even
-// events), so both count. On the 8192-model ragged batch (1773 listed items)
-// the kernel took 3.05 / 1.86 / 2.33 ms for G = 8 / 16 / 32.
-constexpr int SEARCH_LANES = 16;
 
 // Items whose FP64 mode counts failed (a rescaling failure, or the count not
 // monotone at the evaluated points): Algorithm 1 in FP64 from V[0], one warp
@@ -781,9 +731,8 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
     // to 8 blocks per SM spread the list over every SM, where blocks of
     // several warps would stack a list of a thousand items on a few SMs.
     const int lblocks = std::max(1, std::min(8 * (p.sms > 0 ? p.sms : 152), n));
-    first_count64_kernel<SEARCH_LANES><<<lblocks, 32, 0, s>>>(b, o, n32, search, counters + 5,
-                                                             counters + 6, unresolved,
-                                                             counters + 1);
+    first_count64_kernel<<<lblocks, 32, 0, s>>>(b, o, n32, layers32, search, counters + 5,
+                                                counters + 6, unresolved, counters + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (phase_ev && (e = cudaEventRecord(phase_ev[1], s)) != cudaSuccess) return e;
     resolve64_kernel<<<lblocks, 32, 0, s>>>(b, o, unresolved, counters + 1, counters + 2);
@@ -889,11 +838,14 @@ __global__ void __launch_bounds__(256) changes_scan64_kernel(DevBatch b, Changes
 
 // Counting form (plan precision >= 1): a pair of lanes per item checks the
 // first change n1 on the mode count (T and s in FP64 at V[n1-1] and V[n1]:
-// T must jump by an odd amount) and then takes the next M - 1 changes from
+// T must jump by an odd amount; for items the counting kernel certified inside
+// the pole-free range, cert_counts holds both) and then takes the next M - 1
+// changes from
 // next_change_f32 (masw_modes.cuh; layers32: the FP32 records). An item whose
 // FP64 counts fail is listed for the linear scan.
 __global__ void __launch_bounds__(128) changes_count64_kernel(DevBatch b, ChangesOut o, int M,
                                                               const int32_t* __restrict__ first,
+                                                              const int32_t* __restrict__ cert_counts,
                                                               const float* __restrict__ layers32,
                                                               int32_t* linear, int32_t* n_linear) {
     const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 1);
@@ -915,7 +867,13 @@ __global__ void __launch_bounds__(128) changes_count64_kernel(DevBatch b, Change
         const double k = b.k[item];
         TPoint below, P;
         const float* laydf = records_df(b, l0);
-        eval_pair(laydf, lay, N, k, b.c0, b.dc, n1 - 1, n1, half, pair, &below, &P);
+        const int cc = cert_counts ? cert_counts[item] : -1;
+        if (cc >= 0) {  // the certificate's FP64 counts (J0 = 0 there)
+            below = TPoint{n1 - 1, cc & 0xffff, cc & 0xffff};
+            P = TPoint{n1, cc >> 16, cc >> 16};
+        } else {
+            eval_pair(laydf, lay, N, k, b.c0, b.dc, n1 - 1, n1, half, pair, &below, &P);
+        }
         ModeSearch st = mode_search_init(laydf, lay, N, k, b.c0, b.dc,
                                          b.model_nlim[m] - 1, half, pair,
                                          P, TPoint{-1, -1, 0});
@@ -939,7 +897,7 @@ __global__ void __launch_bounds__(128) changes_count64_kernel(DevBatch b, Change
 }
 
 cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const int32_t* first,
-                           const float* layers32, double* ct, int32_t* idx, int32_t* status,
+                           const int32_t* cert_counts, const float* layers32, double* ct, int32_t* idx, int32_t* status,
                            int32_t* delta, int32_t* counters, int32_t* linear, int counting,
                            cudaStream_t s) {
     if (b.n_items == 0) return cudaSuccess;
@@ -956,7 +914,7 @@ cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const in
     }
     const long long threads = 2LL * b.n_items;
     changes_count64_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(
-        b, o, M, first, layers32, linear, counters + 1);
+        b, o, M, first, cert_counts, layers32, linear, counters + 1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     changes_scan64_kernel<<<lblocks, 32 * wpb, 0, s>>>(b, o, M, first, counters, linear,
@@ -1095,6 +1053,21 @@ cudaError_t launch_exp_check(int n, const double* x, double* y_lib, double* y_cu
                              cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     exp_check_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, x, y_lib, y_cuda);
+    return cudaGetLastError();
+}
+
+__global__ void sincos_check_kernel(int n, const double* __restrict__ x, double* s_lib,
+                                    double* c_lib, double* s_cuda, double* c_cuda) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    sincos_small(x[i], s_lib + i, c_lib + i);
+    sincos(x[i], s_cuda + i, c_cuda + i);
+}
+
+cudaError_t launch_sincos_check(int n, const double* x, double* s_lib, double* c_lib,
+                                double* s_cuda, double* c_cuda, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    sincos_check_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, x, s_lib, c_lib, s_cuda, c_cuda);
     return cudaGetLastError();
 }
 

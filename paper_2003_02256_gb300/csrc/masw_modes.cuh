@@ -95,6 +95,37 @@ __device__ __forceinline__ ModeSearch mode_search_init(const float* laydf, const
     return st;
 }
 
+// J0 at c (clamped-layer modes of the N finite layers) with the layers split
+// between the pair's lanes; both lanes get the sum.
+static __device__ __noinline__ int j0_pair(const double* __restrict__ lay, int N, double k,
+                                           double c, int half, unsigned pair) {
+    const double c2 = c * c;
+    int j0 = 0;
+    for (int j = half; j < N; j += 2) j0 += clamped_modes(lay + j * LAYER_STRIDE, k, c2);
+    return j0 + __shfl_xor_sync(pair, j0, 1);
+}
+
+// eval_pair for two points above the last event, st.P.n < na < nb (na < 0:
+// not evaluated, T = -1): s at each point on its own lane (det_inertia_df),
+// J0 at V[nb] over both lanes (j0_pair). J0 never decreases along the grid,
+// so J0 at V[na] equals J0 at P when J0 at V[nb] does; only otherwise is it
+// counted, again over both lanes.
+__device__ __forceinline__ void eval_pair_above(const ModeSearch& st, int na, int nb, TPoint* a,
+                                                TPoint* b) {
+    const int n = st.half ? nb : na;
+    const int sv = n >= 0 ? det_inertia_df(st.laydf, st.lay, st.N, st.k, grid_c(st.c0, st.dc, n))
+                          : 0;
+    const int so = __shfl_xor_sync(st.pair, sv, 1);
+    const int sa = st.half ? so : sv, sb = st.half ? sv : so;
+    const int jp = (st.P.T - st.P.s) >> 1;
+    const int jb = j0_pair(st.lay, st.N, st.k, grid_c(st.c0, st.dc, nb), st.half, st.pair);
+    int ja = jp;
+    if (na >= 0 && jb != jp)
+        ja = j0_pair(st.lay, st.N, st.k, grid_c(st.c0, st.dc, na), st.half, st.pair);
+    *a = TPoint{na, (na < 0 || sa < 0) ? -1 : sa + 2 * ja, sa};
+    *b = TPoint{nb, sb < 0 ? -1 : sb + 2 * jb, sb};
+}
+
 // The first point of (lo, hi.n] with T > P.T, given T(lo) = P.T and
 // hi.T > P.T: the bracket split in three per step, one point per lane. Sets
 // st.cand to the smallest evaluated point above the result, st.bad when the
@@ -104,7 +135,12 @@ __device__ inline TPoint first_rise(ModeSearch& st, int lo, TPoint hi) {
         const int len = hi.n - lo;
         const int a = lo + (len + 1) / 3, bq = lo + (2 * len + 1) / 3;  // lo < a <= bq < hi
         TPoint pa, pb;
-        eval_pair(st.laydf, st.lay, st.N, st.k, st.c0, st.dc, a, bq, st.half, st.pair, &pa, &pb);
+        if (bq > a) {
+            eval_pair_above(st, a, bq, &pa, &pb);
+        } else {
+            eval_pair_above(st, -1, a, &pa, &pb);
+            pa = pb;
+        }
         if (pa.T < st.P.T || pb.T < pa.T || pb.T > hi.T) {
             st.bad = true;
             return hi;
@@ -143,8 +179,7 @@ __device__ inline int next_change(ModeSearch& st, int* delta) {
         } else {
             const int mid = lo + ((st.top - lo) >> 1);
             TPoint mp;
-            eval_pair(st.laydf, st.lay, st.N, st.k, st.c0, st.dc, st.top, mid > lo ? mid : -1, st.half,
-                      st.pair, &st.topp, &mp);
+            eval_pair_above(st, mid > lo ? mid : -1, st.top, &mp, &st.topp);
             if (st.topp.T < st.P.T || (mp.n >= 0 && (mp.T < st.P.T || mp.T > st.topp.T))) {
                 st.bad = true;
                 return -1;
@@ -224,8 +259,7 @@ __device__ inline int next_change_f32(ModeSearch& st, const float* __restrict__ 
                                 st.pair);
         if (st.displace) n = min(max(n + st.displace, lo + 1), st.top);
         TPoint a, b;
-        eval_pair(st.laydf, st.lay, st.N, st.k, st.c0, st.dc, n - 1 > lo ? n - 1 : -1, n,
-                  st.half, st.pair, &a, &b);
+        eval_pair_above(st, n - 1 > lo ? n - 1 : -1, n, &a, &b);
         if (n - 1 <= lo) a = TPoint{lo, st.P.T, st.P.s};
         if (n == st.top) st.topp = b;
         if (a.T < st.P.T || b.T < a.T || (st.topp.T >= 0 && b.T > st.topp.T)) {
@@ -239,9 +273,12 @@ __device__ inline int next_change_f32(ModeSearch& st, const float* __restrict__ 
             // no rise up to n: one step of two points up
             if (n >= st.top) return -1;
             TPoint u, v;
-            const int n2 = n + 2 <= st.top ? n + 2 : -1;
-            eval_pair(st.laydf, st.lay, st.N, st.k, st.c0, st.dc, n + 1, n2, st.half, st.pair,
-                      &u, &v);
+            if (n + 2 <= st.top) {
+                eval_pair_above(st, n + 1, n + 2, &u, &v);
+            } else {
+                eval_pair_above(st, -1, n + 1, &v, &u);
+                v = TPoint{-1, -1, 0};
+            }
             if (u.n == st.top) st.topp = u;
             if (v.n == st.top) st.topp = v;
             if (u.T < st.P.T || (v.n >= 0 && v.T < u.T)) {
@@ -261,8 +298,7 @@ __device__ inline int next_change_f32(ModeSearch& st, const float* __restrict__ 
             // a.T > P.T: the first rise is at or below n - 1; one step down
             TPoint u, v;
             const int n3 = n - 3 > lo ? n - 3 : -1, n2 = n - 2 > lo ? n - 2 : -1;
-            eval_pair(st.laydf, st.lay, st.N, st.k, st.c0, st.dc, n3, n2, st.half, st.pair, &u,
-                      &v);
+            if (n2 >= 0) eval_pair_above(st, n3, n2, &u, &v);
             if (n3 < 0) u = TPoint{lo, st.P.T, st.P.s};
             if (n2 < 0) v = u;
             if (u.T < st.P.T || v.T < u.T || v.T > a.T) {

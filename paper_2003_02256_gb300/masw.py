@@ -352,6 +352,19 @@ def exp_check(x, stream=None):
     return y_lib, y_cuda
 
 
+def sincos_check(x, stream=None):
+    """(library sin, cos, CUDA sin, cos) at host points 0 <= x <= 5 pi / 4
+    (masw_sincos_check)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    outs = [np.empty_like(x) for _ in range(4)]
+    f = load().masw_sincos_check
+    f.argtypes = [ctypes.c_int32] + [ctypes.c_void_p] * 6
+    f.restype = ctypes.c_int
+    _check(f(x.size, _ptr(x), *[_ptr(o) for o in outs], _stream_handle(stream)),
+           "masw_sincos_check")
+    return tuple(outs)
+
+
 def element_check(handle, item, layer, c):
     """(fp64, df): the element's denominator and six numerators (7 per point)
     from the FP64 element and the double-float one (masw_element_check)."""

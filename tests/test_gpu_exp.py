@@ -1,7 +1,9 @@
 """The library's FP64 exponential (e^x, x <= 0) against exact values and
 against CUDA's exp: within 1 ulp of the exact value on a sample checked with
 60-digit mpmath, and within 2 ulp of CUDA's exp on a dense sweep of
-[-708, 0]; 0 below -708."""
+[-708, 0]; 0 below -708. Its sine and cosine on [0, 5 pi / 4] (the
+clamped-layer count's range) the same way: within 2 ulp of the exact values,
+within 3 ulp of CUDA's sincos."""
 import math
 
 import mpmath as mp
@@ -46,3 +48,30 @@ def test_exp_within_one_ulp_of_exact(masw):
     with mp.workdps(40):
         exact = np.array([float(mp.exp(mp.mpf(float(v)))) for v in x])
     assert ulp_distance(y, exact).max() <= 1
+
+
+def test_sincos_within_two_ulp_of_exact(masw):
+    rng = np.random.default_rng(7)
+    hi = 5.0 * math.pi / 4.0
+    x = np.concatenate([rng.uniform(0.0, hi, 1500), rng.uniform(0.0, 1e-3, 200),
+                        math.pi / 2 + rng.uniform(-1e-6, 1e-6, 100),
+                        math.pi + rng.uniform(-1e-6, 0.0, 100),
+                        [0.0, 1e-300, math.pi / 4, math.pi / 2, 3 * math.pi / 4, math.pi,
+                         np.nextafter(math.pi, 0.0)]])
+    s, c, _, _ = masw.sincos_check(x)
+    with mp.workdps(40):
+        es = np.array([float(mp.sin(mp.mpf(float(v)))) for v in x])
+        ec = np.array([float(mp.cos(mp.mpf(float(v)))) for v in x])
+    ds, dc = ulp_distance(s, es), ulp_distance(c, ec)
+    assert ds.max() <= 2, (ds.max(), x[np.argmax(ds)])
+    assert dc.max() <= 2, (dc.max(), x[np.argmax(dc)])
+    z = np.nonzero(x == 0.0)[0]
+    assert (s[z] == 0.0).all() and (c[z] == 1.0).all()
+
+
+def test_sincos_against_cuda_on_a_dense_sweep(masw):
+    x = np.linspace(0.0, 5.0 * math.pi / 4.0, 400001)
+    s, c, sc, cc = masw.sincos_check(x)
+    ds, dc = ulp_distance(s, sc), ulp_distance(c, cc)
+    assert ds.max() <= 3, (ds.max(), x[np.argmax(ds)])
+    assert dc.max() <= 3, (dc.max(), x[np.argmax(dc)])
