@@ -112,6 +112,10 @@ typedef struct {
     int32_t count_block;     /* precision 2: threads per block of the counting kernel, 64, 128
                                 (default) or 256 (two lanes per item, items of a block
                                 consecutive; launch bounds of 14, 7 or 3 resident blocks) */
+    int32_t count_split;     /* precision 2: 1 (default) the FP32 search in a kernel of its own
+                                before the certificate's, 0 both in one kernel (same
+                                results); with 1, count_block 64 gives the certificate
+                                kernel 640 resident threads (96 registers) */
 } masw_plan;
 
 /* Copy and validate a model batch into batch-owned device memory and bind it
@@ -226,8 +230,8 @@ int masw_set_plan(masw_batch* batch, const masw_plan* plan);
 
 /* Time candidate plans on this batch (median of reps timed scans each,
  * CUDA events on the batch stream), keep the fastest, return it in *best
- * (may be NULL). The search is staged: the counting kernel's block size
- * (precision 2), then warps_per_block x blocks_per_sm, then cpl x ordered,
+ * (may be NULL). The search is staged: the counting kernel's block size and
+ * count_split (precision 2), then warps_per_block x blocks_per_sm, then cpl x ordered,
  * each stage keeping the best of the previous ones, and last the flat
  * (non-persistent) launch. Results never depend on the plan. Winners are cached per (max layers,
  * n_c, item-count bucket) in-process and, when the environment variable

@@ -340,6 +340,7 @@ static masw_plan default_plan(const masw_batch* B) {
     p.use_graph = 1;
     p.precision = 2;
     p.count_block = 128;
+    p.count_split = 1;
     return p;
 }
 
@@ -348,7 +349,8 @@ static bool plan_ok(const masw_plan& p) {
                p.warps_per_block == 8;
     bool cpl = p.cpl == 1 || p.cpl == 2 || p.cpl == 4;
     bool cb = p.count_block == 64 || p.count_block == 128 || p.count_block == 256;
-    return wpb && cpl && cb && p.precision >= 0 && p.precision <= 2 && p.blocks_per_sm >= 1 &&
+    bool cs = p.count_split == 0 || p.count_split == 1;
+    return wpb && cpl && cb && cs && p.precision >= 0 && p.precision <= 2 && p.blocks_per_sm >= 1 &&
            p.blocks_per_sm <= 32 && p.stage_layers >= 0 &&
            p.stage_layers <= MASW_MAX_LAYERS + 1 &&
            (size_t)p.warps_per_block * p.stage_layers * LAYER_STRIDE * sizeof(double) <= 48 * 1024;
@@ -362,6 +364,7 @@ static ScanPlan to_scan_plan(const masw_batch* B, const masw_plan& p) {
     s.persistent = p.persistent;
     s.stage_layers = p.stage_layers;
     s.count_block = p.count_block;
+    s.count_split = p.count_split;
     s.sms = B->sm_count;
     return s;
 }
@@ -1140,9 +1143,9 @@ void load_cache_file() {
     if (!f) return;
     int a, b, c;
     masw_plan p;
-    while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d", &a, &b, &c, &p.warps_per_block,
+    while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d", &a, &b, &c, &p.warps_per_block,
                   &p.cpl, &p.blocks_per_sm, &p.persistent, &p.ordered, &p.stage_layers,
-                  &p.use_graph, &p.precision, &p.count_block) == 12)
+                  &p.use_graph, &p.precision, &p.count_block, &p.count_split) == 13)
         if (plan_ok(p)) g_cache[{a, b, c}] = p;
     fclose(f);
 }
@@ -1154,10 +1157,10 @@ void save_cache_file() {
     if (!f) return;
     for (auto& kv : g_cache) {
         const masw_plan& p = kv.second;
-        fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first),
+        fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first),
                 std::get<1>(kv.first), std::get<2>(kv.first), p.warps_per_block, p.cpl,
                 p.blocks_per_sm, p.persistent, p.ordered, p.stage_layers, p.use_graph, p.precision,
-                p.count_block);
+                p.count_block, p.count_split);
     }
     fclose(f);
 }
@@ -1210,13 +1213,18 @@ int masw_autotune(masw_batch* B, int32_t reps, masw_plan* best) {
         return MASW_OK;
     };
     int rc = consider(bestp);
-    // stage 1: the counting kernel's block size (its launch bounds follow)
+    // stage 1: the counting kernel's block size (its launch bounds follow),
+    // with the search in the same kernel or in one of its own
     if (!rc && bestp.precision == 2) {
         const masw_plan base = bestp;
-        for (int cb : {64, 128, 256}) {
-            masw_plan p = base;
-            p.count_block = cb;
-            if ((rc = consider(p))) break;
+        for (int split : {0, 1}) {
+            for (int cb : {64, 128, 256}) {
+                masw_plan p = base;
+                p.count_block = cb;
+                p.count_split = split;
+                if ((rc = consider(p))) break;
+            }
+            if (rc) break;
         }
     }
     // stage 2: warps per block x persistent blocks per SM of the other kernels

@@ -79,21 +79,30 @@ static __device__ __noinline__ int pair_search(const float* __restrict__ lay32, 
     return hi;
 }
 
-// Both lanes of the pair (lane bit 0 = half, `pair` = their shuffle mask)
-// call this with the same item and get the same result. Requires nlim >= 2.
-__device__ __forceinline__ PairCount count_certify_pair(const float* __restrict__ lay32,
-                                                        const float* __restrict__ laydf,
-                                                        const double* __restrict__ lay, int N,
-                                                        double k, double c0, double dc, int nlim,
-                                                        int half, unsigned pair) {
+// The search stage: the first grid point in [0, npf) with a nonzero FP32
+// count (count 0 at c = 0: static stiffness positive definite), -1 when
+// there is none or npf < 1. Both lanes get the same index.
+__device__ __forceinline__ int count_search_pair(const float* __restrict__ lay32, int N, double k,
+                                                 double c0, double dc, int npf, int half,
+                                                 unsigned pair) {
+    if (npf < 1) return -1;
+    return pair_search(lay32, N, (float)k, (float)c0, (float)dc, -1, npf - 1, 1, half, pair);
+}
+
+// The certificate stage for the search's index n (count_search_pair) in the
+// pole-free range [0, npf). Both lanes of the pair (lane bit 0 = half, `pair`
+// = their shuffle mask) call it with the same item and get the same result.
+// Requires nlim >= 2.
+__device__ __forceinline__ PairCount certify_pair(const float* __restrict__ lay32,
+                                                  const float* __restrict__ laydf,
+                                                  const double* __restrict__ lay, int N, double k,
+                                                  double c0, double dc, int nlim, int npf, int n,
+                                                  int half, unsigned pair) {
     const float kf = (float)k;
     const float c0f = (float)c0, dcf = (float)dc;
-    const int npf = pole_free_points_f(lay32, N, kf, c0f, dcf, nlim);
     PairCount out{-1, -1, 0, -1};
     if (npf < 1) return out;
-    // count 0 at c = 0 (static stiffness positive definite); the FP64
-    // certificate decides the parity at the first nonzero point
-    const int n = pair_search(lay32, N, kf, c0f, dcf, -1, npf - 1, 1, half, pair);
+    // the FP64 certificate decides the parity at the first nonzero point
     if (n < 0) {
         out.start = npf;  // no mode below the bound: scan linearly above it
         return out;
@@ -168,6 +177,18 @@ __device__ __forceinline__ PairCount count_certify_pair(const float* __restrict_
     out.n = cert >= 1 ? -1 : n;
     if (cert >= 1 && cert < npf) out.counts = pack_counts(s_lo, s_hi);
     return out;
+}
+
+// Search and certificate in one call (count_search_pair, certify_pair).
+// Requires nlim >= 2.
+__device__ __forceinline__ PairCount count_certify_pair(const float* __restrict__ lay32,
+                                                        const float* __restrict__ laydf,
+                                                        const double* __restrict__ lay, int N,
+                                                        double k, double c0, double dc, int nlim,
+                                                        int half, unsigned pair) {
+    const int npf = pole_free_points_f(lay32, N, (float)k, (float)c0, (float)dc, nlim);
+    const int n = count_search_pair(lay32, N, k, c0, dc, npf, half, pair);
+    return certify_pair(lay32, laydf, lay, N, k, c0, dc, nlim, npf, n, half, pair);
 }
 
 }  // namespace masw

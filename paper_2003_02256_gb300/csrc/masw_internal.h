@@ -57,6 +57,7 @@ struct ScanPlan {
     int persistent;       // 1: warps pop items from a queue; 0: one item per warp
     int stage_layers;     // layer records staged in shared memory per warp (0 = read global)
     int count_block = 128;  // threads per block of the counting kernel: 64, 128 or 256
+    int count_split = 0;    // 1: the counting search in a kernel of its own
     int sms = 0;            // SM count (0: unknown)
 };
 

@@ -13,11 +13,13 @@
 //  screen32_kernel,       precision 1: the same scan in FP32 (packed FP32x2 for
 //  screen32p_kernel       the paired form), then verify64_kernel: a three-point
 //                         FP64 check on the Wittrick-Williams mode count.
-//  count_certify_kernel   precision 2 (default): FP32 search on the
-//                         negative-eigenvalue count below the pole-free bound
-//                         and its FP64 certificate, a lane pair per item; the
-//                         fallback items take fallback32_kernel (linear FP32
-//                         scan) and verify64_list_kernel (the check).
+//  count_search_kernel,   precision 2 (default): FP32 search on the
+//  count_certify_kernel   negative-eigenvalue count below the pole-free bound
+//                         and its FP64 certificate, a lane pair per item (two
+//                         kernels by default, plan count_split; one fused
+//                         kernel otherwise); the fallback items take
+//                         fallback32_kernel (linear FP32 scan) and
+//                         verify64_list_kernel (the check).
 //  first_count64_kernel   both two-precision plans: items that failed a check,
 //                         search on the mode count from V[0] (FP32-located,
 //                         FP64-certified rises).
@@ -520,9 +522,37 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
 // n32. B threads per block (plan count_block: 64, 128 or 256), each block's
 // B/2 items consecutive, so its warps share the records of one or two models
 // in L1; the launch bounds ask for 896 resident threads per SM (at most 73
-// registers a thread) for B = 64 and 128, and 768 for 256.
+// registers a thread) for B = 64 and 128, and 768 for 256; with SPLIT (plan
+// count_split: the search ran before in count_search_kernel, its index in
+// n32), 640 for B = 64 (96 registers, fewer spills), so that the block size
+// also picks among three register budgets.
+// Search stage alone (count_search_pair): the index goes to n32[item], for
+// count_certify_kernel<B, true>.
 template <int B>
-__global__ void __launch_bounds__(B, (B == 256 ? 3 : 896 / B)) count_certify_kernel(DevBatch b, const float* __restrict__ layers32,
+__global__ void __launch_bounds__(B) count_search_kernel(DevBatch b,
+                                                         const float* __restrict__ layers32,
+                                                         int32_t* __restrict__ n32, int item_begin,
+                                                         int item_end) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int item = item_begin + (t >> 1);
+    if (item >= item_end) return;  // both lanes of a pair leave together
+    const int half = t & 1;
+    const unsigned pair = 3u << ((threadIdx.x & 31) & 30);
+    const int m = b.item_model[item];
+    const int lo_rec = b.model_loff[m];
+    const int N = b.model_loff[m + 1] - lo_rec - 1;
+    const int nlim = b.model_nlim[m];
+    if (nlim < 2) return;
+    const float* lay32 = layers32 + (size_t)lo_rec * LAYER_STRIDE32;
+    const double k = b.k[item];
+    const int npf = pole_free_points_f(lay32, N, (float)k, (float)b.c0, (float)b.dc, nlim);
+    const int n = count_search_pair(lay32, N, k, b.c0, b.dc, npf, half, pair);
+    if (!half) n32[item] = n;
+}
+
+template <int B, bool SPLIT>
+__global__ void __launch_bounds__(B, (B == 256 ? 3 : (B == 64 && SPLIT ? 10 : 896 / B)))
+    count_certify_kernel(DevBatch b, const float* __restrict__ layers32,
                                                                ScanOut o, int32_t* __restrict__ n32,
                                                                int32_t* search, int32_t* n_search,
                                                                int32_t* fallback, int32_t* n_fallback,
@@ -546,8 +576,15 @@ __global__ void __launch_bounds__(B, (B == 256 ? 3 : 896 / B)) count_certify_ker
     }
     const double* lay = b.layers + (size_t)lo_rec * LAYER_STRIDE;
     const float* laydf = b.layers_df ? b.layers_df + (size_t)lo_rec * LAYER_STRIDE_DF : nullptr;
-    const PairCount r = count_certify_pair(layers32 + (size_t)lo_rec * LAYER_STRIDE32, laydf, lay, N,
-                                           b.k[item], b.c0, b.dc, nlim, half, pair);
+    const float* lay32 = layers32 + (size_t)lo_rec * LAYER_STRIDE32;
+    const double k = b.k[item];
+    PairCount r;
+    if (SPLIT) {
+        const int npf = pole_free_points_f(lay32, N, (float)k, (float)b.c0, (float)b.dc, nlim);
+        r = certify_pair(lay32, laydf, lay, N, k, b.c0, b.dc, nlim, npf, n32[item], half, pair);
+    } else {
+        r = count_certify_pair(lay32, laydf, lay, N, k, b.c0, b.dc, nlim, half, pair);
+    }
     if (half) return;
     if (o.cert_counts) o.cert_counts[item] = route_level(b.route) >= 1 ? -1 : r.counts;
     if (route_level(b.route) >= 1) {  // test routing: every item through the linear FP32 scan from V[0]
@@ -672,25 +709,25 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
     if (counting) {
         const int cb = p.count_block;
         const int grid = (2 * n + cb - 1) / cb;
-        switch (cb) {
-            case 64:
-                count_certify_kernel<64><<<grid, 64, 0, s>>>(b, layers32, o, n32, search,
-                                                             counters + 5, fallback, counters + 3,
-                                                             item_begin, item_end);
-                break;
-            case 128:
-                count_certify_kernel<128><<<grid, 128, 0, s>>>(b, layers32, o, n32, search,
-                                                               counters + 5, fallback, counters + 3,
-                                                               item_begin, item_end);
-                break;
-            case 256:
-                count_certify_kernel<256><<<grid, 256, 0, s>>>(b, layers32, o, n32, search,
-                                                               counters + 5, fallback, counters + 3,
-                                                               item_begin, item_end);
-                break;
+        if (p.count_split) {
+            count_search_kernel<128><<<(2 * n + 127) / 128, 128, 0, s>>>(b, layers32, n32,
+                                                                         item_begin, item_end);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+#define MASW_COUNT_LAUNCH(BS, SPL)                                                             \
+    count_certify_kernel<BS, SPL><<<grid, BS, 0, s>>>(b, layers32, o, n32, search, counters + 5, \
+                                                      fallback, counters + 3, item_begin, item_end)
+        switch (cb * 2 + (p.count_split ? 1 : 0)) {
+            case 128: MASW_COUNT_LAUNCH(64, false); break;
+            case 129: MASW_COUNT_LAUNCH(64, true); break;
+            case 256: MASW_COUNT_LAUNCH(128, false); break;
+            case 257: MASW_COUNT_LAUNCH(128, true); break;
+            case 512: MASW_COUNT_LAUNCH(256, false); break;
+            case 513: MASW_COUNT_LAUNCH(256, true); break;
             default:
                 return cudaErrorInvalidValue;
         }
+#undef MASW_COUNT_LAUNCH
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (phase_ev && (e = cudaEventRecord(phase_ev[0], s)) != cudaSuccess) return e;
         fallback32_kernel<<<std::max(1, std::min(p.blocks, n)), 256,

@@ -47,7 +47,7 @@ class Plan(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("ordered", ctypes.c_int32), ("stage_layers", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("count_block", ctypes.c_int32)]
+                ("count_block", ctypes.c_int32), ("count_split", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

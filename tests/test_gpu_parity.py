@@ -322,7 +322,10 @@ def test_every_plan_and_the_plain_path_give_identical_indices(masw):
                      dict(cpl=2), dict(cpl=4), dict(precision=0), dict(precision=0, cpl=2),
                      dict(precision=1, persistent=0), dict(precision=2),
                      dict(precision=2, use_graph=0), dict(precision=2, stage_layers=0),
-                     dict(precision=2, warps_per_block=1, blocks_per_sm=1)):
+                     dict(precision=2, count_split=1), dict(count_split=1, use_graph=1),
+                     dict(count_split=1, count_block=64), dict(count_split=1, count_block=256),
+                     dict(precision=2, warps_per_block=1, blocks_per_sm=1, count_split=0,
+                          count_block=128)):
             b.set_plan(**plan)
             got = b.dispersion()
             assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2]), plan
