@@ -102,10 +102,9 @@ SM_MAX_MHZ = 2070.0
 # (bytes, models of that launch); the records, wavenumbers and item tables are
 # read once, the outputs stay in L2. Scaled by the models of a launch; None
 # where no capture of the current kernel exists.
-# uniform: 3.57 MB for the 1024-model launch; ragged: 8.49 MB for the launch
-# over the first 2048 models (429,978 items), scaled by the algorithmic bytes
-# (records, wavenumbers, item tables: x 4.024) to the 8192-model launch.
-CERTIFY_DRAM_BYTES = {"uniform": (3.569152e6, 1024), "ragged": (34.157e6, 8192)}
+# No capture of the current certificate kernel (count_certify_kernel<128,
+# true>, the search's index read from n32) yet.
+CERTIFY_DRAM_BYTES = {}
 # DRAM bytes (read + write) of one scan launch per model, from the ncu capture
 # of the 64-model case (281.6 KB read, 0 written), scaled by the models of a
 # launch; traffic grows with the number of items.
@@ -407,24 +406,31 @@ def counting_evals(models, grid, idx, st, nlim, n32):
 
 
 def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, sms, workload):
-    """Roofline of the dominant kernel of a counting-search scan, the fused
-    search + FP64 certificate: its FP64 work (2 layer-evaluation chains per
-    counted item) against the FP64 pipe, from algorithmic layer evaluations /
-    device time. Its FP32 search work runs on the FP32 pipe beside it and is
-    reported separately. Also the linear scan's count (Algorithm 1's
-    (idx + 1)(N + 1) layer-evaluations per item) and how much of it the
+    """Roofline of the dominant kernel of a counting-search scan, the FP64
+    certificate (count_certify_kernel; with the fused plan, the search runs
+    inside it): its FP64 work (2 layer-evaluation chains per counted item)
+    against the FP64 pipe, from algorithmic layer evaluations / device time.
+    The FP32 search's work is reported against the FP32 pipe, over its own
+    kernel's time when it has one. Also the linear scan's count (Algorithm
+    1's (idx + 1)(N + 1) layer-evaluations per item) and how much of it the
     counting search leaves out."""
     e32, e64, e64_fb, frac_counted = counting_evals(models, grid, idx, st, nlim, n32)
     linear = algorithmic_layer_evals(models, idx, st, nlim)
     peak32 = FP32_FFMA_PER_CLK_SM * 2.0 * sms * SM_MAX_MHZ * 1e6
-    t0 = phases[0] * 1e-3
+    split = phases[3] is not None
+    t0 = (phases[4] if split else phases[0]) * 1e-3
+    t32 = (phases[3] if split else phases[0]) * 1e-3
     achieved = e64 * F_LAYER_FLOPS / t0
     cap = CERTIFY_DRAM_BYTES.get(workload)
+    kernel = ("count_certify_kernel (FP64 certificate: double-float element on the FP32 pipe, "
+              "Schur step on the FP64 pipe; the FP32 search in count_search_kernel before it)"
+              if split else
+              "count_certify_kernel (FP64 certificate: double-float element on the FP32 pipe, "
+              "Schur step on the FP64 pipe; FP32 search alongside)")
     return {"bound": "alu", "unit": "TFLOP/s",
             "achieved": achieved / 1e12, "peak": peak64 / 1e12, "frac": achieved / peak64,
             "traffic": None if cap is None else cap[0] * models.n_models / cap[1],
-            "kernel": "count_certify_kernel (FP64 certificate: double-float element on the FP32 "
-                      "pipe, Schur step on the FP64 pipe; FP32 search alongside)",
+            "kernel": kernel,
             "work": "the certificate's layer-evaluations x the FP64 element + Schur step's "
                     "149.1 flops each",
             "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
@@ -433,13 +439,14 @@ def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, s
             "layer_evals_per_s": e64 / t0,
             "fp64_flops_executed_per_layer_eval": F_LAYER_FLOPS_EXECUTED64,
             "fp64_pipe_frac_executed": e64 * F_LAYER_FLOPS_EXECUTED64 / t0 / peak64,
-            "kernel_ms": phases[0],
+            "kernel_ms": t0 * 1e3,
             "search_layer_evals_fp32": e32,
-            "search_fp32_frac_of_fp32_peak": e32 * F_LAYER_FLOPS_FP32 / t0 / peak32,
+            "search_fp32_frac_of_fp32_peak": e32 * F_LAYER_FLOPS_FP32 / t32 / peak32,
             "fallback_check_layer_evals_fp64": e64_fb,
             "linear_scan_layer_evals": linear,
             "linear_scan_over_counting_evals": linear / max(1, e32 + e64 + e64_fb),
-            "phases_ms": {"count_certify": phases[0],
+            "phases_ms": {"count_search_and_certify": phases[0],
+                          "count_search": phases[3], "count_certify": phases[4],
                           "fallback_check_search": phases[1], "resolve64": phases[2]},
             "counted_fraction": frac_counted,
             "fp64_peak_microbenchmark": micro / 1e12}
@@ -464,14 +471,19 @@ def device_steps(torch, step, steps, flush, stream, after=None):
 def kernel_phases(torch, masw, batch, step, steps, flush, stream):
     """Per-kernel device times of the scan (ms, mean over ``steps`` timed
     steps): the same kernels launched without the graph, so that CUDA events
-    on the batch stream sit between them (masw_last_scan_phases)."""
+    on the batch stream sit between them (masw_last_scan_phases, and
+    masw_last_count_phases for the split counting kernels). Returns the three
+    scan phases, then the search and certificate kernels (None when fused)."""
     plan = batch.plan()
     batch.set_plan(use_graph=0)
+    split = plan.precision == 2 and plan.count_split == 1
     ph = []
     device_steps(torch, step, steps, flush, stream,
-                 after=lambda: ph.append(masw.last_scan_phases(batch.handle)))
+                 after=lambda: ph.append(masw.last_scan_phases(batch.handle) +
+                                         (masw.last_count_phases(batch.handle) if split
+                                          else [None, None])))
     batch.set_plan(use_graph=plan.use_graph)
-    return [float(np.mean([p[i] for p in ph])) for i in range(3)]
+    return [None if ph[0][i] is None else float(np.mean([p[i] for p in ph])) for i in range(5)]
 
 
 def e2e_rate(torch, masw, models, grid, ce_host, plan, steps, warmup, n_pipe):
@@ -653,7 +665,7 @@ def measure(args, torch, masw, workload, n_models, rank, world, with_plain=True)
             "step_ms_median": float(np.median(step_ms)), "clocks": clk.summary(),
             "roofline": roofline, "plan": plan.as_dict(), "plain": plain, "e2e": e2e,
             "found_fraction": float(np.mean(st == 0)),
-            "launches_per_step": {0: 2, 1: 5, 2: 6}[plan.precision]}
+            "launches_per_step": {0: 2, 1: 5, 2: 6 + plan.count_split}[plan.precision]}
 
 
 def run_extras(args, masw, torch):

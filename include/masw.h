@@ -246,12 +246,18 @@ int masw_last_scan_ms(const masw_batch* batch, float* ms);
  * scan launched without a graph (plan use_graph 0), from CUDA events between
  * the launches on the batch stream. Plan precision 1: ms[0] FP32 screen,
  * ms[1] FP64 check, ms[2] FP64 re-scan. Plan precision 2: ms[0] counting
- * search with its FP64 certificate (one fused kernel), ms[1] linear FP32 scan
+ * search with its FP64 certificate (see masw_last_count_phases), ms[1] linear FP32 scan
  * and FP64 check of the fallback items and the FP64 mode-count search of the
  * items that failed a check, ms[2] FP64 re-scan (items whose FP64 counts
  * failed). Plan precision 1: ms[1] also includes that search. MASW_EINVAL when that
  * scan was graph-replayed. */
 int masw_last_scan_phases(const masw_batch* batch, float* ms);
+
+/* The two parts of ms[0] of masw_last_scan_phases for a plan with precision
+ * 2 and count_split 1: ms[0] the FP32 counting search (count_search_kernel),
+ * ms[1] its FP64 certificate (count_certify_kernel). MASW_EINVAL for other
+ * plans and for a graph-replayed or per-model (masw_dispersion_plain) scan. */
+int masw_last_count_phases(const masw_batch* batch, float* ms);
 
 /* The FP32 screen's first-change index per item (item order, -1 when the
  * screen saw none) from the most recent two-precision scan, host or device

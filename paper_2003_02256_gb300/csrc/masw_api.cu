@@ -101,8 +101,9 @@ struct masw_batch {
     int32_t route = 0;  // masw_set_route
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    cudaEvent_t phase_ev[2] = {nullptr, nullptr};
+    cudaEvent_t phase_ev[3] = {nullptr, nullptr, nullptr};  // after: counting, search, (split) FP32 search
     bool phases_valid = false;
+    bool count_phases_valid = false;  // phase_ev[2] recorded (split counting kernels)
     float last_ms = 0.f;
 
     DevBatch dev(bool ordered) const {
@@ -418,10 +419,12 @@ static int run_scan(masw_batch* B) {
     if (B->plan.use_graph && B->graph) {
         CK(cudaGraphLaunch(B->graph, B->stream));
         B->phases_valid = false;
+        B->count_phases_valid = false;
     } else {
         bool ph = B->plan.precision >= 1;
         CK(enqueue_scan(B, B->plan, B->stream, ph));
         B->phases_valid = ph;
+        B->count_phases_valid = ph && B->plan.precision == 2 && B->plan.count_split == 1;
     }
     CK(cudaEventRecord(B->ev1, B->stream));
     return MASW_OK;
@@ -583,6 +586,7 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
     if (e == cudaSuccess) e = cudaEventCreate(&B->ev1);
     if (e == cudaSuccess) e = cudaEventCreate(&B->phase_ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&B->phase_ev[1]);
+    if (e == cudaSuccess) e = cudaEventCreate(&B->phase_ev[2]);
     if (e != cudaSuccess) {
         record_cuda_error(e, "batch upload", __LINE__);
         free_batch(B);
@@ -846,6 +850,8 @@ int masw_dispersion_plain(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* s
     ScanOut o{B->d_ct, B->d_idx, B->d_status, B->d_cert};
     DevBatch d = B->dev(false);
     ScanPlan sp = to_scan_plan(B, p);
+    B->phases_valid = false;  // the per-model launches record no phase events
+    B->count_phases_valid = false;
     CK(cudaEventRecord(B->ev0, B->stream));
     for (int32_t m = 0; m < B->n_models; ++m) {
         if (p.precision >= 1)
@@ -867,6 +873,15 @@ int masw_last_scan_phases(const masw_batch* B, float* ms) {
     CK(cudaEventElapsedTime(&ms[0], B->ev0, B->phase_ev[0]));
     CK(cudaEventElapsedTime(&ms[1], B->phase_ev[0], B->phase_ev[1]));
     CK(cudaEventElapsedTime(&ms[2], B->phase_ev[1], B->ev1));
+    return MASW_OK;
+}
+
+int masw_last_count_phases(const masw_batch* B, float* ms) {
+    if (!B || !ms) return MASW_EINVAL;
+    if (!B->count_phases_valid) return MASW_EINVAL;
+    CK(cudaEventSynchronize(B->ev1));
+    CK(cudaEventElapsedTime(&ms[0], B->ev0, B->phase_ev[2]));
+    CK(cudaEventElapsedTime(&ms[1], B->phase_ev[2], B->phase_ev[0]));
     return MASW_OK;
 }
 

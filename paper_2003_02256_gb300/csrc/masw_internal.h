@@ -73,7 +73,7 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
                                const float* layers32, int32_t* n32, int32_t* search,
                                int32_t* unresolved, int32_t* fallback, int32_t* counters,
                                int counting, int item_begin, int item_end, cudaStream_t s,
-                               cudaEvent_t* phase_ev);
+                               cudaEvent_t* phase_ev);  // phase_ev: nullptr or 3 events
 
 // Algorithm 1 continued: the first M sign changes per item with their
 // negative-eigenvalue count changes, from the first change `first` (the batch

@@ -713,6 +713,7 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
             count_search_kernel<128><<<(2 * n + 127) / 128, 128, 0, s>>>(b, layers32, n32,
                                                                          item_begin, item_end);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (phase_ev && (e = cudaEventRecord(phase_ev[2], s)) != cudaSuccess) return e;
         }
 #define MASW_COUNT_LAUNCH(BS, SPL)                                                             \
     count_certify_kernel<BS, SPL><<<grid, BS, 0, s>>>(b, layers32, o, n32, search, counters + 5, \

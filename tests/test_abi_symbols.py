@@ -64,6 +64,7 @@ def test_new_entry_points_reject_bad_arguments_without_the_gpu(lib):
     d = ctypes.c_double
     assert lib.masw_misfit_curves(None, None, i32(1), d(2.0), None, None, None, None) == 1
     assert lib.masw_server_profile(None, i32(1), None) == 1
+    assert lib.masw_last_count_phases(None, None) == 1
     x = (d * 2)(1.0, 4.0)  # 4.0 is above 5 pi / 4
     out = [(d * 2)() for _ in range(4)]
     assert lib.masw_sincos_check(i32(2), x, *out, None) == 1

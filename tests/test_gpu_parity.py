@@ -335,6 +335,28 @@ def test_every_plan_and_the_plain_path_give_identical_indices(masw):
         assert np.array_equal(got[1], ref[1])
 
 
+def test_scan_phase_timers(masw):
+    """masw_last_scan_phases and masw_last_count_phases: the split counting
+    plan times its search and certificate kernels separately, inside the
+    first phase; fused, graph-replayed and per-model scans refuse."""
+    m, g = W.uniform_batch(n_models=64, n_lambda=50)
+    with masw.Batch(m, g) as b:
+        b.set_plan(precision=2, count_split=1, use_graph=0)
+        b.dispersion()
+        ph = masw.last_scan_phases(b.handle)
+        cp = masw.last_count_phases(b.handle)
+        assert min(ph) >= 0.0 and min(cp) > 0.0
+        assert cp[0] + cp[1] <= ph[0] * 1.001 + 1e-3
+        for plan, plain in ((dict(count_split=0), False), (dict(count_split=1, use_graph=1), False),
+                            (dict(count_split=1, use_graph=0), True)):
+            b.set_plan(**plan)
+            b.dispersion(plain=plain)
+            with pytest.raises(masw.MaswError):
+                masw.last_count_phases(b.handle)
+        with pytest.raises(masw.MaswError):
+            masw.last_scan_phases(b.handle)
+
+
 def test_graph_replay_after_update_gives_fresh_results(masw, oracle_lib):
     m1, g = W.uniform_batch(n_models=8, n_layers=6, n_lambda=20)
     m2, _ = W.uniform_batch(n_models=8, n_layers=6, n_lambda=20, seed=5)
