@@ -9,8 +9,10 @@
 //    its midpoint, then splits the bracket in three per step (one point per
 //    lane): about log3(npf) steps instead of Algorithm 1's linear walk. The
 //    first nonzero point goes to the certificate whatever its FP32 parity.
-//  * Certificate (FP64 recurrence over double-float elements,
-//    det_inertia_df in masw_df.cuh). The count is 0 at V[n-1] (so 0, and
+//  * Certificate (recurrence over double-float elements, det_inertia_dd in
+//    masw_df.cuh: the Schur step in double-float too, the half-space's in
+//    FP64; points above the pole-free range take det_inertia_df, the FP64
+//    step). The count is 0 at V[n-1] (so 0, and
 //    V[0]'s sign, at every point below) and odd at V[n] (the sign differs).
 //    When the FP32 count was off by one next to the change (count 0 at both
 //    points: the change is higher; nonzero at V[n-1]: lower), the pair takes
@@ -108,7 +110,7 @@ __device__ __forceinline__ PairCount certify_pair(const float* __restrict__ lay3
         return out;
     }
     if (n < 1) return out;  // a mode below V[0]: Algorithm 1 from V[0]
-    const int v = det_inertia_df(laydf, lay, N, k, grid_c(c0, dc, n - 1 + half));
+    const int v = det_inertia_dd(laydf, lay, N, k, grid_c(c0, dc, n - 1 + half));
     const int vo = __shfl_xor_sync(pair, v, 1);
     const int va = half ? vo : v;  // V[n-1]
     const int vb = half ? v : vo;  // V[n]
@@ -119,7 +121,10 @@ __device__ __forceinline__ PairCount certify_pair(const float* __restrict__ lay3
         const bool down = va > 0 && n >= 3;
         if (up || down) {
             const int p = (up ? n + 1 : n - 3) + half;
-            const int w = p < nlim ? det_inertia_df(laydf, lay, N, k, grid_c(c0, dc, p)) : -1;
+            // inside the pole-free range the Schur step in double-float, above it in FP64
+            const int w = p >= nlim ? -1
+                          : p < npf ? det_inertia_dd(laydf, lay, N, k, grid_c(c0, dc, p))
+                                    : det_inertia_df(laydf, lay, N, k, grid_c(c0, dc, p));
             const int wo = __shfl_xor_sync(pair, w, 1);
             const int c_lo = half ? wo : w, c_hi = half ? w : wo;
             if (up) {
@@ -159,7 +164,7 @@ __device__ __forceinline__ PairCount certify_pair(const float* __restrict__ lay3
         // n) and an odd count at it; otherwise the item falls back with start n.
         const int m = pair_search(lay32, N, kf, c0f, dcf, n, npf - 1, vb + 1, half, pair);
         if (m > n) {
-            const int u = det_inertia_df(laydf, lay, N, k, grid_c(c0, dc, m - 1 + half));
+            const int u = det_inertia_dd(laydf, lay, N, k, grid_c(c0, dc, m - 1 + half));
             const int uo = __shfl_xor_sync(pair, u, 1);
             const int ua = half ? uo : u, ub = half ? u : uo;
             if (ua == vb && ub > vb && (ub & 1)) {

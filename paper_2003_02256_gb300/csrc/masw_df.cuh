@@ -555,11 +555,15 @@ __host__ __device__ __forceinline__ void df_record(const double* L, float* out) 
     for (int i = 0; i < 6; ++i) split_double(v[i], out + 2 * i, out + 2 * i + 1);
 }
 
-// layer_numerators (masw_device.cuh) in double-float: the same LayerNum, in
-// doubles, for schur_layer. R = the record (12 floats); k, c^2 and 1/c^2 as
-// double-floats.
-__device__ __forceinline__ LayerNum layer_numerators_df(const float* __restrict__ R, DF k, DF c2,
-                                                        DF ic2) {
+// The element's denominator and six numerators as double-floats (the
+// values of LayerNum).
+struct LayerNumDD { DF Dh, n00, n01, n11, ce, cf, cg; };
+
+// layer_numerators (masw_device.cuh) in double-float: the same quantities as
+// LayerNum, kept as double-floats. R = the record (12 floats); k, c^2 and
+// 1/c^2 as double-floats.
+__device__ __forceinline__ LayerNumDD layer_numerators_dd(const float* __restrict__ R, DF k, DF c2,
+                                                          DF ic2) {
     const float4 A = *reinterpret_cast<const float4*>(R);
     const float4 B = *reinterpret_cast<const float4*>(R + 4);
     const float4 Cc = *reinterpret_cast<const float4*>(R + 8);
@@ -627,15 +631,80 @@ __device__ __forceinline__ LayerNum layer_numerators_df(const float* __restrict_
         G1 = dsub(dmul(Sw.Sm, Rw.E), dmul(Sw.E, Rw.Sd));
     }
     const DF irc2 = dmul(irho, ic2);  // 1 / (rho c^2)
-    LayerNum o;
-    o.Dh = to_double(dmul(Dh, irc2));
-    o.n00 = to_double(A1);
-    o.n01 = to_double(dmul(dmul(b2, ic2), B1));
-    o.n11 = to_double(D1);
-    o.ce = to_double(E1);
-    o.cf = to_double(F1);
-    o.cg = to_double(G1);
-    return o;
+    return LayerNumDD{dmul(Dh, irc2), A1, dmul(dmul(b2, ic2), B1), D1, E1, F1, G1};
+}
+
+// layer_numerators_dd rounded to doubles (the element check compares them
+// with the FP64 element).
+__device__ __forceinline__ LayerNum layer_numerators_df(const float* __restrict__ R, DF k, DF c2,
+                                                        DF ic2) {
+    const LayerNumDD d = layer_numerators_dd(R, k, c2, ic2);
+    return LayerNum{to_double(d.Dh), to_double(d.n00), to_double(d.n01), to_double(d.n11),
+                    to_double(d.ce), to_double(d.cf), to_double(d.cg)};
+}
+
+// ------------------------------------------------ Schur step in double-float
+//
+// GB300 issues 2 FP64 operations per clock per SM against 128 FP32 ones.
+// With the element on the FP32 pipe the FP64 Schur step (29 FP64 operations a
+// layer, plus the 7 conversions of the element's values) set the pace of the
+// certificate, so the step runs in double-float too: the homogeneous
+// division-free recurrence of schur_layer, each FP64 product a dmul and each
+// FP64 fused multiply-add a dfma, the state renormalised by a power of two per
+// layer (exponent on the integer pipe). Relative rounding of about 2^-47 per
+// operation, against the element's own error of about 1e-13 relative.
+
+// a * b + c for any signs (cancellation included): the product's rounding
+// error and cross terms are carried into the low word, the sum goes through
+// two error-free sums. Error about 2^-47 (|a b| + |c|).
+__device__ __forceinline__ DF dfma(DF a, DF b, DF c) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const DF s = two_sum(p, c.hi);
+    return two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+}
+
+struct HStateDD { DF p00, p01, p11, w; };
+
+// exponent field of a float (0: zero or subnormal, 255: inf or NaN)
+__device__ __forceinline__ int fexp(float x) { return (__float_as_int(x) >> 23) & 0xff; }
+
+// schur_layer (masw_device.cuh) in double-float: eliminates one layer's top
+// node, returns det(Shat) and its first diagonal entry in *s00o. *ok is false
+// when the new scale w is zero, subnormal, non-finite or outside
+// [2^-125, 2^127), or a new state entry is not finite.
+__device__ __forceinline__ DF schur_layer_dd(HStateDD& st, const LayerNumDD& n, bool* ok,
+                                             DF* s00o) {
+    const DF w = st.w;
+    const DF s00 = dfma(n.Dh, st.p00, dmul(w, n.n00));
+    const DF s01 = dfma(n.Dh, st.p01, dmul(w, n.n01));
+    const DF s11 = dfma(n.Dh, st.p11, dmul(w, n.n11));
+    const DF det = dfma(s00, s11, dneg(dmul(s01, s01)));
+    // T = adj(Shat) * [[ce, cf], [-cf, cg]];  Q = [[ce, -cf], [cf, cg]] * T
+    const DF t00 = dfma(s11, n.ce, dmul(s01, n.cf));
+    const DF t01 = dfma(s11, n.cf, dneg(dmul(s01, n.cg)));
+    const DF t10 = dneg(dfma(s01, n.ce, dmul(s00, n.cf)));
+    const DF t11 = dfma(s00, n.cg, dneg(dmul(s01, n.cf)));
+    const DF q00 = dfma(n.ce, t00, dneg(dmul(n.cf, t10)));
+    const DF q01 = dfma(n.ce, t01, dneg(dmul(n.cf, t11)));
+    const DF q11 = dfma(n.cf, t01, dmul(n.cg, t11));
+    const DF p00 = dfma(n.n00, det, dneg(dmul(w, q00)));
+    const DF p01 = dfma(dneg(n.n01), det, dneg(dmul(w, q01)));
+    const DF p11 = dfma(n.n11, det, dneg(dmul(w, q11)));
+    const DF wn = dmul(n.Dh, det);
+    // scale by 2^(127 - e), e = the exponent field of wn: w to [1, 2)
+    const int ew = fexp(wn.hi);
+    const float sc = __int_as_float((254 - min(max(ew, 2), 253)) << 23);
+    st.p00 = dscale(p00, sc);
+    st.p01 = dscale(p01, sc);
+    st.p11 = dscale(p11, sc);
+    st.w = dscale(wn, sc);
+    *ok = ew >= 2 && ew <= 253 && fexp(st.p00.hi) != 255 && fexp(st.p01.hi) != 255 &&
+          fexp(st.p11.hi) != 255;
+    *s00o = s00;
+    return det;
 }
 
 // Number of negative eigenvalues of K(k, c) from the FP64 recurrence over the
@@ -643,31 +712,48 @@ __device__ __forceinline__ LayerNum layer_numerators_df(const float* __restrict_
 // 2x2 Schur pivots S_j = Shat_j / (w Dh): a pivot with det < 0 has one, one
 // with det > 0 has two when its diagonal is negative; a zero determinant
 // counts as one; -1 when the rescaling failed). Its parity is the sign of
-// det K. laydf: the N finite layers' double-float records, or nullptr to split
-// the FP64 records on the fly (the same values). Requires c < beta_halfspace.
-// Out of line: the counting certificate calls it from three places, and one
-// copy of the element keeps the kernel within the instruction cache.
-static __device__ __noinline__ int det_inertia_df(const float* __restrict__ laydf,
-                                           const double* __restrict__ lay, int N, double k,
-                                           double c) {
+// det K. DD: the Schur step in double-float too (schur_layer_dd), for points
+// inside the pole-free range only: no element is near a pole there, while
+// above it the recurrence's cancellation next to the poles magnifies the
+// step's rounding (with it the higher-mode search missed 3 of 1.7 M events
+// that the FP64 scan finds); otherwise the FP64 step (schur_layer). laydf:
+// the N finite layers' double-float records, or nullptr to split the FP64
+// records on the fly (the same values). Requires c < beta_halfspace.
+template <bool DD>
+__device__ __forceinline__ int det_inertia_t(const float* __restrict__ laydf,
+                                             const double* __restrict__ lay, int N, double k,
+                                             double c) {
     const double c2 = c * c;
     const DF kd = from_double(k), cd = from_double(c);
     const DF c2d = dmul(cd, cd);
     const DF ic2d = drcp(c2d);
+    HStateDD sd{dfc(0.0f), dfc(0.0f), dfc(0.0f), dfc(1.0f)};
     HState st{0.0, 0.0, 0.0, 1.0};
     int cnt = 0;
-    double sv[3];
     for (int j = 0; j < N; ++j) {
         float rec[LAYER_STRIDE_DF];
         const float* R = laydf ? laydf + j * LAYER_STRIDE_DF : rec;
         if (!laydf) df_record(lay + j * LAYER_STRIDE, rec);
-        LayerNum n = layer_numerators_df(R, kd, c2d, ic2d);
-        const bool f_neg = wprod_lt0(st.w, n.Dh);
+        const LayerNumDD nd = layer_numerators_dd(R, kd, c2d, ic2d);
         bool ok;
-        double det = schur_layer(st, n, &ok, sv);
-        cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(sv[0]) != f_neg) ? 2 : 0) : 1);
+        if (DD) {
+            const bool f_neg = (sd.w.hi < 0.0f) != (nd.Dh.hi < 0.0f);  // sign of w Dh
+            DF s00;
+            const DF det = schur_layer_dd(sd, nd, &ok, &s00);
+            cnt += det.hi < 0.0f ? 1
+                                 : (det.hi > 0.0f ? (((s00.hi < 0.0f) != f_neg) ? 2 : 0) : 1);
+        } else {
+            const LayerNum n{to_double(nd.Dh), to_double(nd.n00), to_double(nd.n01),
+                             to_double(nd.n11), to_double(nd.ce), to_double(nd.cf),
+                             to_double(nd.cg)};
+            const bool f_neg = wprod_lt0(st.w, n.Dh);
+            double sv[3];
+            const double det = schur_layer(st, n, &ok, sv);
+            cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(sv[0]) != f_neg) ? 2 : 0) : 1);
+        }
         if (!ok) return -1;
     }
+    if (DD) st = HState{to_double(sd.p00), to_double(sd.p01), to_double(sd.p11), to_double(sd.w)};
     HalfNum hn = halfspace_numerators(lay + N * LAYER_STRIDE, c2);
     const bool f_neg = wprod_lt0(st.w, hn.den);
     double s00 = fma(hn.den, st.p00, st.w * hn.m00);
@@ -676,6 +762,19 @@ static __device__ __noinline__ int det_inertia_df(const float* __restrict__ layd
     double det = fma(s00, s11, -s01 * s01);
     cnt += lt0(det) ? 1 : (gt0(det) ? ((lt0(s00) != f_neg) ? 2 : 0) : 1);
     return cnt;
+}
+
+// Out of line: each is called from several places, and one copy of the
+// element keeps a kernel within the instruction cache.
+static __device__ __noinline__ int det_inertia_df(const float* __restrict__ laydf,
+                                                  const double* __restrict__ lay, int N, double k,
+                                                  double c) {
+    return det_inertia_t<false>(laydf, lay, N, k, c);
+}
+static __device__ __noinline__ int det_inertia_dd(const float* __restrict__ laydf,
+                                                  const double* __restrict__ lay, int N, double k,
+                                                  double c) {
+    return det_inertia_t<true>(laydf, lay, N, k, c);
 }
 
 // Wittrick-Williams mode count of the layered structure below c, split as
