@@ -102,9 +102,20 @@ SM_MAX_MHZ = 2070.0
 # (bytes, models of that launch); the records, wavenumbers and item tables are
 # read once, the outputs stay in L2. Scaled by the models of a launch; None
 # where no capture of the current kernel exists.
-# No capture of the current certificate kernel (count_certify_kernel<128,
-# true>, the search's index read from n32) yet.
-CERTIFY_DRAM_BYTES = {}
+# uniform: 4.37 MB for the 1024-model launch of count_certify_kernel<128,
+# true>; ragged: 10.45 MB for the launch over the first 2048 models (429,978
+# items), scaled by the algorithmic bytes (records, wavenumbers, item tables,
+# the search's indices: x 4.024) to the 8192-model launch.
+CERTIFY_DRAM_BYTES = {"uniform": (4.365568e6, 1024), "ragged": (42.054e6, 8192)}
+# Warp instructions a kernel issues per layer-evaluation (ncu
+# smsp__inst_executed.sum of one launch / its layer-evaluations counted as in
+# counting_evals), by workload (ragged: the 2048-model launch): the
+# certificate kernel per certificate layer-evaluation, the search kernel per
+# FP32 one. A kernel's ceiling is the SM's issue rate, ISSUE_PER_CLK_SM warp
+# instructions per clock, over this count.
+CERTIFY_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 50.62, "ragged": 53.26}
+SEARCH_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 4.85, "ragged": 5.08}
+ISSUE_PER_CLK_SM = 4
 # DRAM bytes (read + write) of one scan launch per model, from the ncu capture
 # of the 64-model case (281.6 KB read, 0 written), scaled by the models of a
 # launch; traffic grows with the number of items.
@@ -422,18 +433,29 @@ def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, s
     t32 = (phases[3] if split else phases[0]) * 1e-3
     achieved = e64 * F_LAYER_FLOPS / t0
     cap = CERTIFY_DRAM_BYTES.get(workload)
+    wi = CERTIFY_WARP_INSTR_PER_LAYER_EVAL.get(workload) if split else None
+    # the roof: the FP64 pipe for the plain FP64 element and step, the SM's
+    # instruction issue for the double-float form (its instruction mix
+    # measured by ncu); both in the algorithmic flops of a layer-evaluation
+    peak_issue = (ISSUE_PER_CLK_SM * sms * SM_MAX_MHZ * 1e6 / wi * F_LAYER_FLOPS) if wi else None
+    roof = peak_issue if peak_issue else peak64
     kernel = ("count_certify_kernel (FP64 certificate: double-float element on the FP32 pipe, "
               "Schur step on the FP64 pipe; the FP32 search in count_search_kernel before it)"
               if split else
               "count_certify_kernel (FP64 certificate: double-float element on the FP32 pipe, "
               "Schur step on the FP64 pipe; FP32 search alongside)")
     return {"bound": "alu", "unit": "TFLOP/s",
-            "achieved": achieved / 1e12, "peak": peak64 / 1e12, "frac": achieved / peak64,
+            "achieved": achieved / 1e12, "peak": roof / 1e12, "frac": achieved / roof,
             "traffic": None if cap is None else cap[0] * models.n_models / cap[1],
             "kernel": kernel,
             "work": "the certificate's layer-evaluations x the FP64 element + Schur step's "
                     "149.1 flops each",
-            "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz",
+            "peak_source": ("derived: 4 warp instructions issued/clk/SM x SMs x 2070 MHz / "
+                            f"{wi} warp instructions per layer-evaluation (ncu) x 149.1 flops"
+                            if peak_issue else
+                            "derived: 2 DFMA/clk/SM x 2 flop x SMs x 2070 MHz"),
+            "warp_instructions_per_layer_eval": wi,
+            "fp64_peak": peak64 / 1e12, "frac_of_fp64_peak": achieved / peak64,
             "frac_of_fp64_microbenchmark": achieved / micro,
             "layer_evals_per_launch": e64, "flops_per_layer_eval": F_LAYER_FLOPS,
             "layer_evals_per_s": e64 / t0,
@@ -442,6 +464,10 @@ def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, s
             "kernel_ms": t0 * 1e3,
             "search_layer_evals_fp32": e32,
             "search_fp32_frac_of_fp32_peak": e32 * F_LAYER_FLOPS_FP32 / t32 / peak32,
+            "search_frac_of_issue_ceiling": (
+                e32 / t32 / (ISSUE_PER_CLK_SM * sms * SM_MAX_MHZ * 1e6 /
+                             SEARCH_WARP_INSTR_PER_LAYER_EVAL[workload])
+                if split and workload in SEARCH_WARP_INSTR_PER_LAYER_EVAL else None),
             "fallback_check_layer_evals_fp64": e64_fb,
             "linear_scan_layer_evals": linear,
             "linear_scan_over_counting_evals": linear / max(1, e32 + e64 + e64_fb),

@@ -655,15 +655,19 @@ __device__ __forceinline__ LayerNum layer_numerators_df(const float* __restrict_
 // operation, against the element's own error of about 1e-13 relative.
 
 // a * b + c for any signs (cancellation included): the product's rounding
-// error and cross terms are carried into the low word, the sum goes through
-// two error-free sums. Error about 2^-47 (|a b| + |c|).
+// error and cross terms are carried into the low word, the leading words are
+// summed error-free (two_sum). Error about 2^-47 (|a b| + |c|). The last
+// renormalisation is a fast_two_sum: where the leading sum cancelled so far
+// that the low word t exceeds it, that step's error stays below 2^-23 |t|,
+// about 2^-46 (|a b| + |c|), the order of the bound, and the leading word
+// keeps the sign of the rounded sum.
 __device__ __forceinline__ DF dfma(DF a, DF b, DF c) {
     const float p = __fmul_rn(a.hi, b.hi);
     float e = __fmaf_rn(a.hi, b.hi, -p);
     e = __fmaf_rn(a.hi, b.lo, e);
     e = __fmaf_rn(a.lo, b.hi, e);
     const DF s = two_sum(p, c.hi);
-    return two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
 }
 
 struct HStateDD { DF p00, p01, p11, w; };
