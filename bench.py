@@ -473,7 +473,8 @@ def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, s
             "linear_scan_over_counting_evals": linear / max(1, e32 + e64 + e64_fb),
             "phases_ms": {"count_search_and_certify": phases[0],
                           "count_search": phases[3], "count_certify": phases[4],
-                          "fallback_check_search": phases[1], "resolve64": phases[2]},
+                          "fallback_check_search": phases[1], "resolve64": phases[2],
+                          "fallback_chain_beside_certificate": phases[5]},
             "counted_fraction": frac_counted,
             "fp64_peak_microbenchmark": micro / 1e12}
 
@@ -499,17 +500,19 @@ def kernel_phases(torch, masw, batch, step, steps, flush, stream):
     steps): the same kernels launched without the graph, so that CUDA events
     on the batch stream sit between them (masw_last_scan_phases, and
     masw_last_count_phases for the split counting kernels). Returns the three
-    scan phases, then the search and certificate kernels (None when fused)."""
+    scan phases, then the search and certificate kernels and the fallback
+    chain on the second stream (None when fused; 0 without the second
+    stream)."""
     plan = batch.plan()
     batch.set_plan(use_graph=0)
-    split = plan.precision == 2 and plan.count_split == 1
+    split = plan.precision == 2 and plan.count_split >= 1
     ph = []
     device_steps(torch, step, steps, flush, stream,
                  after=lambda: ph.append(masw.last_scan_phases(batch.handle) +
                                          (masw.last_count_phases(batch.handle) if split
-                                          else [None, None])))
+                                          else [None, None, None])))
     batch.set_plan(use_graph=plan.use_graph)
-    return [None if ph[0][i] is None else float(np.mean([p[i] for p in ph])) for i in range(5)]
+    return [None if ph[0][i] is None else float(np.mean([p[i] for p in ph])) for i in range(6)]
 
 
 def e2e_rate(torch, masw, models, grid, ce_host, plan, steps, warmup, n_pipe):
@@ -691,7 +694,8 @@ def measure(args, torch, masw, workload, n_models, rank, world, with_plain=True)
             "step_ms_median": float(np.median(step_ms)), "clocks": clk.summary(),
             "roofline": roofline, "plan": plan.as_dict(), "plain": plain, "e2e": e2e,
             "found_fraction": float(np.mean(st == 0)),
-            "launches_per_step": {0: 2, 1: 5, 2: 6 + plan.count_split}[plan.precision]}
+            "launches_per_step": {0: 2, 1: 5,
+                                  2: (6, 7, 11)[plan.count_split]}[plan.precision]}
 
 
 def run_extras(args, masw, torch):

@@ -112,10 +112,15 @@ typedef struct {
     int32_t count_block;     /* precision 2: threads per block of the counting kernel, 64, 128
                                 (default) or 256 (two lanes per item, items of a block
                                 consecutive; launch bounds of 14, 7 or 3 resident blocks) */
-    int32_t count_split;     /* precision 2: 1 (default) the FP32 search in a kernel of its own
-                                before the certificate's, 0 both in one kernel (same
-                                results); with 1, count_block 64 gives the certificate
-                                kernel 640 resident threads (96 registers) */
+    int32_t count_split;     /* precision 2: 1 the FP32 search in a kernel of its own before
+                                the certificate's, 0 both in one kernel; 2 (default) as 1,
+                                and the items the search passes straight to the linear
+                                FP32 scan (no count change below the bound, a mode below
+                                V[0]) take that scan, its check and the mode-count search
+                                on a second, highest-priority stream beside the
+                                certificate. Same results for all three; with 1 or 2,
+                                count_block 64 gives the certificate kernel 640 resident
+                                threads (96 registers) */
 } masw_plan;
 
 /* Copy and validate a model batch into batch-owned device memory and bind it
@@ -253,10 +258,14 @@ int masw_last_scan_ms(const masw_batch* batch, float* ms);
  * scan was graph-replayed. */
 int masw_last_scan_phases(const masw_batch* batch, float* ms);
 
-/* The two parts of ms[0] of masw_last_scan_phases for a plan with precision
- * 2 and count_split 1: ms[0] the FP32 counting search (count_search_kernel),
- * ms[1] its FP64 certificate (count_certify_kernel). MASW_EINVAL for other
- * plans and for a graph-replayed or per-model (masw_dispersion_plain) scan. */
+/* Three device times (ms) of the most recent scan launched without a graph,
+ * for a plan with precision 2 and count_split 1 or 2: ms[0] the FP32
+ * counting search (count_search_kernel), ms[1] its FP64 certificate
+ * (count_certify_kernel), ms[2] with count_split 2 the fallback chain on the
+ * second stream, from the end of the search to its last kernel (it runs
+ * beside the certificate), else 0. ms[0] + ms[1] is the first phase of
+ * masw_last_scan_phases. MASW_EINVAL for other plans and for a graph-replayed
+ * or per-model (masw_dispersion_plain) scan. */
 int masw_last_count_phases(const masw_batch* batch, float* ms);
 
 /* The FP32 screen's first-change index per item (item order, -1 when the

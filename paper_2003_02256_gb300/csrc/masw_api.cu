@@ -82,7 +82,15 @@ struct masw_batch {
     int32_t* d_search = nullptr;
     int32_t* d_unres = nullptr;
     int32_t* d_fallback = nullptr;
-    int32_t* d_counters = nullptr;  // SCAN_COUNTERS
+    int32_t* d_counters = nullptr;  // 2 x SCAN_COUNTERS (scan stream's lists, side stream's)
+    // plan count_split 2: the search's fallback items on a second stream
+    cudaStream_t side = nullptr;
+    int side_prio = 0;
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
+    int32_t* d_nsearch = nullptr;
+    int32_t* d_search2 = nullptr;
+    int32_t* d_unres2 = nullptr;
+    int32_t* d_fallback2 = nullptr;
     // model updates (allocated on first use): staged host arrays, error flag
     double* d_upd = nullptr;
     int32_t* d_upd_err = nullptr;
@@ -104,6 +112,7 @@ struct masw_batch {
     cudaEvent_t phase_ev[3] = {nullptr, nullptr, nullptr};  // after: counting, search, (split) FP32 search
     bool phases_valid = false;
     bool count_phases_valid = false;  // phase_ev[2] recorded (split counting kernels)
+    bool side_phase_valid = false;    // side_fork / side_join recorded (count_split 2)
     float last_ms = 0.f;
 
     DevBatch dev(bool ordered) const {
@@ -315,12 +324,15 @@ static void free_batch(masw_batch* B) {
     if (B->ev1) cudaEventDestroy(B->ev1);
     for (cudaEvent_t e : B->phase_ev)
         if (e) cudaEventDestroy(e);
+    if (B->side_fork) cudaEventDestroy(B->side_fork);
+    if (B->side_join) cudaEventDestroy(B->side_join);
+    if (B->side) cudaStreamDestroy(B->side);
     void* ptrs[] = {B->d_layers, B->d_loff,  B->d_woff,  B->d_nlim,   B->d_k,
                     B->d_item_model, B->d_order_sorted, B->d_order_natural, B->d_grad_off,
                     B->d_counter, B->d_ct, B->d_idx, B->d_status, B->d_croot, B->d_rows, B->d_bs,
                     B->d_dphi, B->d_ce, B->d_misfit, B->d_gb, B->d_gh, B->d_layers32, B->d_layers_df,
                     B->d_n32, B->d_cert, B->d_search, B->d_unres, B->d_fallback, B->d_counters,
-                    B->d_upd, B->d_upd_err,
+                    B->d_nsearch, B->d_search2, B->d_unres2, B->d_fallback2, B->d_upd, B->d_upd_err,
                     B->d_chg_ct, B->d_chg_idx, B->d_chg_status, B->d_chg_delta,
                     B->d_chg_counters, B->d_lk_ct, B->d_lk_idx};
     for (void* p : ptrs)
@@ -341,7 +353,7 @@ static masw_plan default_plan(const masw_batch* B) {
     p.use_graph = 1;
     p.precision = 2;
     p.count_block = 128;
-    p.count_split = 1;
+    p.count_split = 2;
     return p;
 }
 
@@ -350,7 +362,7 @@ static bool plan_ok(const masw_plan& p) {
                p.warps_per_block == 8;
     bool cpl = p.cpl == 1 || p.cpl == 2 || p.cpl == 4;
     bool cb = p.count_block == 64 || p.count_block == 128 || p.count_block == 256;
-    bool cs = p.count_split == 0 || p.count_split == 1;
+    bool cs = p.count_split >= 0 && p.count_split <= 2;
     return wpb && cpl && cb && cs && p.precision >= 0 && p.precision <= 2 && p.blocks_per_sm >= 1 &&
            p.blocks_per_sm <= 32 && p.stage_layers >= 0 &&
            p.stage_layers <= MASW_MAX_LAYERS + 1 &&
@@ -375,10 +387,13 @@ static cudaError_t enqueue_scan(masw_batch* B, const masw_plan& p, cudaStream_t 
                                 bool phase_events = false) {
     if (p.precision >= 1) {
         ScanOut o{B->d_ct, B->d_idx, B->d_status, B->d_cert};
+        ScanSide side{B->side, B->side_prio, B->side_fork, B->side_join,
+                      B->d_nsearch, B->d_search2, B->d_unres2, B->d_fallback2};
         return launch_screen_scan(B->dev(p.ordered != 0), o, to_scan_plan(B, p), B->d_layers32,
                                   B->d_n32, B->d_search, B->d_unres, B->d_fallback, B->d_counters,
                                   p.precision == 2, 0, (int)B->n_items, s,
-                                  phase_events ? B->phase_ev : nullptr);
+                                  phase_events ? B->phase_ev : nullptr,
+                                  p.precision == 2 && p.count_split == 2 ? &side : nullptr);
     }
     if (p.persistent) {
         cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(int32_t), s);
@@ -405,7 +420,8 @@ static int rebuild_graph(masw_batch* B) {
         if (e2 != cudaSuccess) e = e2;
     }
     if (e == cudaSuccess) {
-        e = cudaGraphInstantiate(&B->graph, g, 0);
+        // the side stream's kernels keep their launch priority in the graph
+        e = cudaGraphInstantiateWithFlags(&B->graph, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
     }
     cudaStreamDestroy(cap);
@@ -420,11 +436,13 @@ static int run_scan(masw_batch* B) {
         CK(cudaGraphLaunch(B->graph, B->stream));
         B->phases_valid = false;
         B->count_phases_valid = false;
+        B->side_phase_valid = false;
     } else {
         bool ph = B->plan.precision >= 1;
         CK(enqueue_scan(B, B->plan, B->stream, ph));
         B->phases_valid = ph;
-        B->count_phases_valid = ph && B->plan.precision == 2 && B->plan.count_split == 1;
+        B->count_phases_valid = ph && B->plan.precision == 2 && B->plan.count_split >= 1;
+        B->side_phase_valid = B->count_phases_valid && B->plan.count_split == 2;
     }
     CK(cudaEventRecord(B->ev1, B->stream));
     return MASW_OK;
@@ -563,7 +581,9 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
         dev_alloc(&B->d_layers32, rec32.size()) || dev_alloc(&B->d_layers_df, recdf.size()) ||
         dev_alloc(&B->d_n32, nw) || dev_alloc(&B->d_cert, nw) ||
         dev_alloc(&B->d_search, nw) || dev_alloc(&B->d_unres, nw) || dev_alloc(&B->d_fallback, nw) ||
-        dev_alloc(&B->d_counters, SCAN_COUNTERS)) {
+        dev_alloc(&B->d_counters, 2 * SCAN_COUNTERS) || dev_alloc(&B->d_nsearch, nw) ||
+        dev_alloc(&B->d_search2, nw) || dev_alloc(&B->d_unres2, nw) ||
+        dev_alloc(&B->d_fallback2, nw)) {
         free_batch(B);
         return MASW_ENOMEM;
     }
@@ -587,6 +607,18 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
     if (e == cudaSuccess) e = cudaEventCreate(&B->phase_ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&B->phase_ev[1]);
     if (e == cudaSuccess) e = cudaEventCreate(&B->phase_ev[2]);
+    if (e == cudaSuccess) e = cudaEventCreate(&B->side_fork);
+    if (e == cudaSuccess) e = cudaEventCreate(&B->side_join);
+    if (e == cudaSuccess) {
+        // the side stream at the device's highest priority, so that its few
+        // blocks are dispatched ahead of the certificate's queued ones
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess) {
+            B->side_prio = greatest;
+            e = cudaStreamCreateWithPriority(&B->side, cudaStreamNonBlocking, greatest);
+        }
+    }
     if (e != cudaSuccess) {
         record_cuda_error(e, "batch upload", __LINE__);
         free_batch(B);
@@ -852,12 +884,13 @@ int masw_dispersion_plain(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* s
     ScanPlan sp = to_scan_plan(B, p);
     B->phases_valid = false;  // the per-model launches record no phase events
     B->count_phases_valid = false;
+    B->side_phase_valid = false;
     CK(cudaEventRecord(B->ev0, B->stream));
     for (int32_t m = 0; m < B->n_models; ++m) {
         if (p.precision >= 1)
             CK(launch_screen_scan(d, o, sp, B->d_layers32, B->d_n32, B->d_search, B->d_unres,
                                   B->d_fallback, B->d_counters, p.precision == 2, B->woff[m],
-                                  B->woff[m + 1], B->stream, nullptr));
+                                  B->woff[m + 1], B->stream, nullptr, nullptr));
         else
             CK(launch_scan(d, o, sp, B->d_counter, B->woff[m], B->woff[m + 1], B->stream));
         CK(cudaStreamSynchronize(B->stream));
@@ -882,6 +915,8 @@ int masw_last_count_phases(const masw_batch* B, float* ms) {
     CK(cudaEventSynchronize(B->ev1));
     CK(cudaEventElapsedTime(&ms[0], B->ev0, B->phase_ev[2]));
     CK(cudaEventElapsedTime(&ms[1], B->phase_ev[2], B->phase_ev[0]));
+    ms[2] = 0.f;
+    if (B->side_phase_valid) CK(cudaEventElapsedTime(&ms[2], B->side_fork, B->side_join));
     return MASW_OK;
 }
 
@@ -900,10 +935,10 @@ int masw_last_scan_unresolved(const masw_batch* B, int32_t* n) {
         *n = -1;
         return MASW_OK;
     }
-    int32_t v = 0;
+    int32_t v[2 * SCAN_COUNTERS];
     CK(cudaStreamSynchronize(B->stream));
-    CK(cudaMemcpy(&v, B->d_counters + 5, sizeof(int32_t), cudaMemcpyDeviceToHost));
-    *n = v;
+    CK(cudaMemcpy(v, B->d_counters, sizeof(v), cudaMemcpyDeviceToHost));
+    *n = v[5] + v[SCAN_COUNTERS + 5];
     return MASW_OK;
 }
 
@@ -913,10 +948,10 @@ int masw_last_scan_fallback(const masw_batch* B, int32_t* n) {
         *n = -1;
         return MASW_OK;
     }
-    int32_t v = 0;
+    int32_t v[2 * SCAN_COUNTERS];
     CK(cudaStreamSynchronize(B->stream));
-    CK(cudaMemcpy(&v, B->d_counters + 3, sizeof(int32_t), cudaMemcpyDeviceToHost));
-    *n = v;
+    CK(cudaMemcpy(v, B->d_counters, sizeof(v), cudaMemcpyDeviceToHost));
+    *n = v[3] + v[SCAN_COUNTERS + 3];
     return MASW_OK;
 }
 
@@ -1232,7 +1267,7 @@ int masw_autotune(masw_batch* B, int32_t reps, masw_plan* best) {
     // with the search in the same kernel or in one of its own
     if (!rc && bestp.precision == 2) {
         const masw_plan base = bestp;
-        for (int split : {0, 1}) {
+        for (int split : {0, 1, 2}) {
             for (int cb : {64, 128, 256}) {
                 masw_plan p = base;
                 p.count_block = cb;

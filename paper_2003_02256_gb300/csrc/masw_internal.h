@@ -57,7 +57,8 @@ struct ScanPlan {
     int persistent;       // 1: warps pop items from a queue; 0: one item per warp
     int stage_layers;     // layer records staged in shared memory per warp (0 = read global)
     int count_block = 128;  // threads per block of the counting kernel: 64, 128 or 256
-    int count_split = 0;    // 1: the counting search in a kernel of its own
+    int count_split = 0;    // 1: the counting search in a kernel of its own; 2: as 1, and
+                            // the search's fallback items on a second stream (ScanSide)
     int sms = 0;            // SM count (0: unknown)
 };
 
@@ -65,15 +66,33 @@ struct ScanPlan {
 // 0: linear FP32 screen; 1: counting search with the linear screen as
 // fallback. Both check on the FP64 mode count and search it for the items
 // that fail. n32, search, unresolved, fallback: n_items each; counters:
-// SCAN_COUNTERS ([5]: items that failed their FP64 check).
+// SCAN_COUNTERS per list set ([3]: fallback items, [5]: items that failed
+// their FP64 check).
 constexpr int SCAN_COUNTERS = 7;
 // n32 flag of an index located by the counting search (MASW_SCREEN_COUNTED)
 constexpr int32_t SCREEN_COUNTED = 1 << 30;
+// Plan count_split 2: a second stream for the items the counting search
+// passes straight to the linear FP32 scan. After the search kernel, `fork` on
+// the scan stream releases that stream; its fallback scan, check, mode-count
+// search and re-scan run (at priority `prio`, the stream's) beside the
+// certificate over lists of their own, and the scan stream waits for `join`
+// at the end. nsearch, search, unresolved, fallback: n_items each.
+struct ScanSide {
+    cudaStream_t s;
+    int prio;
+    cudaEvent_t fork, join;
+    int32_t* nsearch;  // the search kernel's index per item (0: passed on)
+    int32_t* search;
+    int32_t* unresolved;
+    int32_t* fallback;
+};
+// counters: 2 x SCAN_COUNTERS (the second set for the side stream's lists).
 cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p,
                                const float* layers32, int32_t* n32, int32_t* search,
                                int32_t* unresolved, int32_t* fallback, int32_t* counters,
                                int counting, int item_begin, int item_end, cudaStream_t s,
-                               cudaEvent_t* phase_ev);  // phase_ev: nullptr or 3 events
+                               cudaEvent_t* phase_ev,  // nullptr or 3 events
+                               const ScanSide* side);  // nullptr: one stream
 
 // Algorithm 1 continued: the first M sign changes per item with their
 // negative-eigenvalue count changes, from the first change `first` (the batch

@@ -49,6 +49,7 @@
 // resolve64_kernel, changes_scan64_kernel) take the plain FP64 element.
 //  fp64_peak_kernel       DFMA throughput microbenchmark (roofline denominator).
 #include <algorithm>
+#include <utility>
 
 #include "masw_adjoint.cuh"
 #include "masw_count.cuh"
@@ -526,13 +527,20 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
 // count_split: the search ran before in count_search_kernel, its index in
 // n32), 640 for B = 64 (96 registers, fewer spills), so that the block size
 // also picks among three register budgets.
-// Search stage alone (count_search_pair): the index goes to n32[item], for
-// count_certify_kernel<B, true>.
+// Search stage alone (count_search_pair): the index goes to nsearch[item],
+// for count_certify_kernel<B, true>. With an early list (plan count_split 2)
+// the items the certificate would only pass on to the linear FP32 scan (no
+// count change inside the pole-free range, a mode below V[0], test routing
+// 1..3) go straight to that list with their start in n32, and nsearch gets 0
+// for them and for models without a scan range (results written here), so
+// that the fallback chain can run on a second stream beside the certificate.
 template <int B>
 __global__ void __launch_bounds__(B) count_search_kernel(DevBatch b,
                                                          const float* __restrict__ layers32,
-                                                         int32_t* __restrict__ n32, int item_begin,
-                                                         int item_end) {
+                                                         int32_t* __restrict__ nsearch,
+                                                         ScanOut o, int32_t* __restrict__ n32,
+                                                         int32_t* early, int32_t* n_early,
+                                                         int item_begin, int item_end) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int item = item_begin + (t >> 1);
     if (item >= item_end) return;  // both lanes of a pair leave together
@@ -542,24 +550,42 @@ __global__ void __launch_bounds__(B) count_search_kernel(DevBatch b,
     const int lo_rec = b.model_loff[m];
     const int N = b.model_loff[m + 1] - lo_rec - 1;
     const int nlim = b.model_nlim[m];
-    if (nlim < 2) return;
+    if (nlim < 2) {
+        if (early && !half) {
+            nsearch[item] = 0;
+            n32[item] = -1;
+            write_result(b, o, item, -1);
+            if (o.cert_counts) o.cert_counts[item] = -1;
+        }
+        return;
+    }
     const float* lay32 = layers32 + (size_t)lo_rec * LAYER_STRIDE32;
     const double k = b.k[item];
     const int npf = pole_free_points_f(lay32, N, (float)k, (float)b.c0, (float)b.dc, nlim);
     const int n = count_search_pair(lay32, N, k, b.c0, b.dc, npf, half, pair);
-    if (!half) n32[item] = n;
+    if (half) return;
+    if (!early || (n >= 1 && route_level(b.route) < 1)) {
+        nsearch[item] = n;
+        return;
+    }
+    // the start certify_pair gives these items (test routing: V[0])
+    nsearch[item] = 0;
+    n32[item] = (route_level(b.route) < 1 && npf >= 1 && n < 0) ? npf : 0;
+    if (o.cert_counts) o.cert_counts[item] = -1;
+    early[atomicAdd(n_early, 1)] = item;
 }
 
 template <int B, bool SPLIT>
 __global__ void __launch_bounds__(B, (B == 256 ? 3 : (B == 64 && SPLIT ? 10 : 896 / B)))
-    count_certify_kernel(DevBatch b, const float* __restrict__ layers32,
-                                                               ScanOut o, int32_t* __restrict__ n32,
-                                                               int32_t* search, int32_t* n_search,
-                                                               int32_t* fallback, int32_t* n_fallback,
-                                                               int item_begin, int item_end) {
+    count_certify_kernel(DevBatch b, const float* __restrict__ layers32, ScanOut o,
+                         int32_t* n32, const int32_t* nsearch, int early, int32_t* search,
+                         int32_t* n_search, int32_t* fallback, int32_t* n_fallback,
+                         int item_begin, int item_end) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int item = item_begin + (t >> 1);
     if (item >= item_end) return;  // both lanes of a pair leave together
+    // (early list: the search kernel has passed the item on, or written it)
+    if (SPLIT && early && nsearch[item] < 1) return;
     const int half = t & 1;
     const unsigned pair = 3u << ((threadIdx.x & 31) & 30);
     const int m = b.item_model[item];
@@ -581,7 +607,7 @@ __global__ void __launch_bounds__(B, (B == 256 ? 3 : (B == 64 && SPLIT ? 10 : 89
     PairCount r;
     if (SPLIT) {
         const int npf = pole_free_points_f(lay32, N, (float)k, (float)b.c0, (float)b.dc, nlim);
-        r = certify_pair(lay32, laydf, lay, N, k, b.c0, b.dc, nlim, npf, n32[item], half, pair);
+        r = certify_pair(lay32, laydf, lay, N, k, b.c0, b.dc, nlim, npf, nsearch[item], half, pair);
     } else {
         r = count_certify_pair(lay32, laydf, lay, N, k, b.c0, b.dc, nlim, half, pair);
     }
@@ -692,32 +718,98 @@ __global__ void __launch_bounds__(256) resolve64_kernel(DevBatch b, ScanOut o,
     }
 }
 
+// Launch with an explicit priority (cudaLaunchAttributePriority, kept as the
+// node's priority when captured into a graph); prio 0 launches plainly.
+template <typename... Arg, typename... Act>
+static cudaError_t launch_prio(void (*kernel)(Arg...), int grid, int block, size_t shm,
+                               cudaStream_t s, int prio, Act&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = shm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = prio;
+    cfg.attrs = at;
+    cfg.numAttrs = prio != 0 ? 1 : 0;  // 0: the stream's own priority
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Act>(args)...);
+}
+
+// The kernels after the screen or the counting kernels, over one set of
+// lists: (counting) the linear FP32 scan of the fallback list and its FP64
+// check, then the mode-count search of the items that failed a check and the
+// FP64 re-scan of the items whose counts failed. phase_ev1: recorded after
+// the search (or nullptr).
+static cudaError_t launch_tail(const DevBatch& b, const ScanOut& o, const ScanPlan& p,
+                               const float* layers32, int32_t* n32, int32_t* search,
+                               int32_t* unresolved, int32_t* fallback, int32_t* counters,
+                               int counting, int n, cudaStream_t s, int prio,
+                               cudaEvent_t phase_ev1) {
+    cudaError_t e;
+    if (counting) {
+        e = launch_prio(fallback32_kernel, std::max(1, std::min(p.blocks, n)), 256,
+                        (size_t)p.stage_layers * LAYER_STRIDE32 * sizeof(float), s, prio, b,
+                        layers32, n32, fallback, counters + 3, counters + 4, p.stage_layers);
+        if (e != cudaSuccess) return e;
+        e = launch_prio(verify64_list_kernel, std::max(1, std::min(p.blocks, (4 * n + 127) / 128)),
+                        128, 0, s, prio, b, o, n32, fallback, counters + 3, search, counters + 5);
+        if (e != cudaSuccess) return e;
+    }
+    // The mode-count search and the FP64 re-scan work through short lists
+    // (0.1 % and none of the ragged batch's items): one warp per block and up
+    // to 8 blocks per SM spread the list over every SM, where blocks of
+    // several warps would stack a list of a thousand items on a few SMs.
+    const int lblocks = std::max(1, std::min(8 * (p.sms > 0 ? p.sms : 152), n));
+    e = launch_prio(first_count64_kernel, lblocks, 32, 0, s, prio, b, o, n32, layers32, search,
+                    counters + 5, counters + 6, unresolved, counters + 1);
+    if (e != cudaSuccess) return e;
+    if (phase_ev1 && (e = cudaEventRecord(phase_ev1, s)) != cudaSuccess) return e;
+    return launch_prio(resolve64_kernel, lblocks, 32, 0, s, prio, b, o, unresolved, counters + 1,
+                       counters + 2);
+}
+
 cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p,
                                const float* layers32, int32_t* n32, int32_t* search,
                                int32_t* unresolved, int32_t* fallback, int32_t* counters,
                                int counting, int item_begin, int item_end, cudaStream_t s,
-                               cudaEvent_t* phase_ev) {
+                               cudaEvent_t* phase_ev, const ScanSide* side) {
     if (item_end <= item_begin) return cudaSuccess;
     // counters: [0] screen queue, [1] unresolved count, [2] resolve queue,
-    // [3] fallback count, [4] fallback queue, [5] search count, [6] search queue
-    cudaError_t e = cudaMemsetAsync(counters, 0, SCAN_COUNTERS * sizeof(int32_t), s);
+    // [3] fallback count, [4] fallback queue, [5] search count, [6] search queue;
+    // then the same for the side stream's lists
+    cudaError_t e = cudaMemsetAsync(counters, 0, 2 * SCAN_COUNTERS * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     int wpb = p.warps_per_block;
     int blocks = p.persistent ? p.blocks : (item_end - item_begin + wpb - 1) / wpb;
     size_t shm = (size_t)wpb * p.stage_layers * LAYER_STRIDE32 * sizeof(float);
     int n = item_end - item_begin;
+    const bool overlap = counting && p.count_split == 2 && side != nullptr;
     if (counting) {
         const int cb = p.count_block;
         const int grid = (2 * n + cb - 1) / cb;
+        int32_t* const side_counters = counters + SCAN_COUNTERS;
+        int32_t* const nsearch = overlap ? side->nsearch : n32;
         if (p.count_split) {
-            count_search_kernel<128><<<(2 * n + 127) / 128, 128, 0, s>>>(b, layers32, n32,
-                                                                         item_begin, item_end);
+            count_search_kernel<128><<<(2 * n + 127) / 128, 128, 0, s>>>(
+                b, layers32, nsearch, o, n32, overlap ? side->fallback : nullptr,
+                overlap ? side_counters + 3 : nullptr, item_begin, item_end);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if (phase_ev && (e = cudaEventRecord(phase_ev[2], s)) != cudaSuccess) return e;
         }
-#define MASW_COUNT_LAUNCH(BS, SPL)                                                             \
-    count_certify_kernel<BS, SPL><<<grid, BS, 0, s>>>(b, layers32, o, n32, search, counters + 5, \
-                                                      fallback, counters + 3, item_begin, item_end)
+        if (overlap) {
+            // the search's fallback items on the side stream, beside the certificate
+            if ((e = cudaEventRecord(side->fork, s)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(side->s, side->fork, 0)) != cudaSuccess) return e;
+            e = launch_tail(b, o, p, layers32, n32, side->search, side->unresolved, side->fallback,
+                            side_counters, 1, n, side->s, side->prio, nullptr);
+            if (e != cudaSuccess) return e;
+            if ((e = cudaEventRecord(side->join, side->s)) != cudaSuccess) return e;
+        }
+#define MASW_COUNT_LAUNCH(BS, SPL)                                                              \
+    count_certify_kernel<BS, SPL><<<grid, BS, 0, s>>>(b, layers32, o, n32, nsearch, overlap ? 1 : 0, \
+                                                      search, counters + 5, fallback, counters + 3, \
+                                                      item_begin, item_end)
         switch (cb * 2 + (p.count_split ? 1 : 0)) {
             case 128: MASW_COUNT_LAUNCH(64, false); break;
             case 129: MASW_COUNT_LAUNCH(64, true); break;
@@ -731,13 +823,6 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
 #undef MASW_COUNT_LAUNCH
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (phase_ev && (e = cudaEventRecord(phase_ev[0], s)) != cudaSuccess) return e;
-        fallback32_kernel<<<std::max(1, std::min(p.blocks, n)), 256,
-                            (size_t)p.stage_layers * LAYER_STRIDE32 * sizeof(float), s>>>(
-            b, layers32, n32, fallback, counters + 3, counters + 4, p.stage_layers);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        verify64_list_kernel<<<std::max(1, std::min(p.blocks, (4 * n + 127) / 128)), 128, 0, s>>>(
-            b, o, n32, fallback, counters + 3, search, counters + 5);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else {
         switch (p.cpl) {
             case 1:
@@ -764,17 +849,12 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
                                                         item_end);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // The mode-count search and the FP64 re-scan work through short lists
-    // (0.1 % and none of the ragged batch's items): one warp per block and up
-    // to 8 blocks per SM spread the list over every SM, where blocks of
-    // several warps would stack a list of a thousand items on a few SMs.
-    const int lblocks = std::max(1, std::min(8 * (p.sms > 0 ? p.sms : 152), n));
-    first_count64_kernel<<<lblocks, 32, 0, s>>>(b, o, n32, layers32, search, counters + 5,
-                                                counters + 6, unresolved, counters + 1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (phase_ev && (e = cudaEventRecord(phase_ev[1], s)) != cudaSuccess) return e;
-    resolve64_kernel<<<lblocks, 32, 0, s>>>(b, o, unresolved, counters + 1, counters + 2);
-    return cudaGetLastError();
+    // the certificate's own failures (with overlap; all fallback items otherwise)
+    e = launch_tail(b, o, p, layers32, n32, search, unresolved, fallback, counters, counting, n, s,
+                    0, phase_ev ? phase_ev[1] : nullptr);
+    if (e != cudaSuccess) return e;
+    if (overlap && (e = cudaStreamWaitEvent(s, side->join, 0)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------------ higher modes

@@ -307,14 +307,15 @@ def last_scan_phases(handle):
 
 
 def last_count_phases(handle):
-    """(FP32 counting search, FP64 certificate) device ms of the last scan
-    (masw_last_count_phases; split counting plan, no graph)."""
+    """(FP32 counting search, FP64 certificate, fallback chain on the second
+    stream or 0) device ms of the last scan (masw_last_count_phases; split
+    counting plan, no graph)."""
     f = load().masw_last_count_phases
     f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]
     f.restype = ctypes.c_int
-    ms = (ctypes.c_float * 2)()
+    ms = (ctypes.c_float * 3)()
     _check(f(ctypes.c_void_p(handle), ms), "masw_last_count_phases")
-    return [ms[0], ms[1]]
+    return [ms[0], ms[1], ms[2]]
 
 
 def last_scan_screen(handle, n32):

@@ -325,7 +325,9 @@ def test_every_plan_and_the_plain_path_give_identical_indices(masw):
                      dict(precision=2, count_split=1), dict(count_split=1, use_graph=1),
                      dict(count_split=1, count_block=64), dict(count_split=1, count_block=256),
                      dict(precision=2, warps_per_block=1, blocks_per_sm=1, count_split=0,
-                          count_block=128)):
+                          count_block=128),
+                     dict(count_split=2, use_graph=0), dict(count_split=2, count_block=64),
+                     dict(count_split=2, count_block=256, use_graph=1)):
             b.set_plan(**plan)
             got = b.dispersion()
             assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2]), plan
@@ -337,18 +339,26 @@ def test_every_plan_and_the_plain_path_give_identical_indices(masw):
 
 def test_scan_phase_timers(masw):
     """masw_last_scan_phases and masw_last_count_phases: the split counting
-    plan times its search and certificate kernels separately, inside the
-    first phase; fused, graph-replayed and per-model scans refuse."""
-    m, g = W.uniform_batch(n_models=64, n_lambda=50)
+    plans time their search and certificate kernels separately, inside the
+    first phase, and count_split 2 also its fallback chain on the second
+    stream; fused, graph-replayed and per-model scans refuse."""
+    m, g = W.ragged_batch(n_models=64, seed=77)
     with masw.Batch(m, g) as b:
-        b.set_plan(precision=2, count_split=1, use_graph=0)
-        b.dispersion()
-        ph = masw.last_scan_phases(b.handle)
-        cp = masw.last_count_phases(b.handle)
-        assert min(ph) >= 0.0 and min(cp) > 0.0
-        assert cp[0] + cp[1] <= ph[0] * 1.001 + 1e-3
+        for split in (1, 2):
+            b.set_plan(precision=2, count_split=split, use_graph=0)
+            b.dispersion()
+            ph = masw.last_scan_phases(b.handle)
+            cp = masw.last_count_phases(b.handle)
+            assert min(ph) >= 0.0 and min(cp[:2]) > 0.0
+            assert cp[0] + cp[1] <= ph[0] * 1.001 + 1e-3
+            if split == 1:
+                assert cp[2] == 0.0
+            else:
+                assert cp[2] > 0.0  # the chain's kernels ran (with or without listed items)
         for plan, plain in ((dict(count_split=0), False), (dict(count_split=1, use_graph=1), False),
-                            (dict(count_split=1, use_graph=0), True)):
+                            (dict(count_split=1, use_graph=0), True),
+                            (dict(count_split=2, use_graph=1), False),
+                            (dict(count_split=2, use_graph=0), True)):
             b.set_plan(**plan)
             b.dispersion(plain=plain)
             with pytest.raises(masw.MaswError):
