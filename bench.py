@@ -384,11 +384,13 @@ def executed_layer_evals(models, idx, st, nlim, cpl):
     return int(np.sum(pts * nl))
 
 
-def counting_evals(models, grid, idx, st, nlim, n32):
+def counting_evals(models, grid, idx, st, nlim, n32, split=True):
     """Per-item evaluations of the counting-search scan (plan precision 2).
-    FP32 layer evaluations of the search: 1 + ceil(log3 npf) steps of two
-    inertia counts for a located item, npf = grid points below the pole-free
-    bound min_i beta_i sqrt(1 + (pi/(k h_i))^2). FP64 layer evaluations of
+    FP32 layer evaluations of the search, npf = grid points below the
+    pole-free bound min_i beta_i sqrt(1 + (pi/(k h_i))^2): split (its own
+    kernel, one thread per item) the top of the range, then ceil(log2 npf)
+    bisection steps when the change lies inside it; fused (a lane pair)
+    1 + ceil(log3 npf) steps of two inertia counts. FP64 layer evaluations of
     the certificate: 2 per counted item. Fallback items: the linear FP32
     scan from its start up to the change, and the three-point FP64 check."""
     counted = (n32 >= 0) & ((n32 & (1 << 30)) != 0)
@@ -404,9 +406,13 @@ def counting_evals(models, grid, idx, st, nlim, n32):
         cb[sl] = np.min(b[None, :-1] * np.sqrt(1.0 + (np.pi / (kk * h[None, :])) ** 2), axis=1)
     lim = nlim[item_model].astype(np.int64)
     npf = np.clip(np.ceil((cb * (1.0 - 1e-4) - grid.c0) / grid.dc), 0, lim).astype(np.int64)
-    steps = np.where(npf >= 2, 1 + np.ceil(np.log(np.maximum(npf, 2)) / np.log(3.0)), 1)
-    search = np.where(npf >= 1, 2 * steps, 0)
     root = np.where(st == 0, idx.astype(np.int64), lim - 1)
+    if split:
+        bis = np.ceil(np.log2(np.maximum(npf, 1)))
+        search = np.where(npf >= 1, 1 + np.where(root < npf, bis, 0), 0)
+    else:
+        steps = np.where(npf >= 2, 1 + np.ceil(np.log(np.maximum(npf, 2)) / np.log(3.0)), 1)
+        search = np.where(npf >= 1, 2 * steps, 0)
     start = np.where(root >= npf, npf, 0)
     linear = np.where(counted, 0, np.maximum(root - start + 1, 0))
     live = lim >= 2
@@ -425,10 +431,10 @@ def counting_roofline(models, grid, idx, st, nlim, n32, phases, peak64, micro, s
     kernel's time when it has one. Also the linear scan's count (Algorithm
     1's (idx + 1)(N + 1) layer-evaluations per item) and how much of it the
     counting search leaves out."""
-    e32, e64, e64_fb, frac_counted = counting_evals(models, grid, idx, st, nlim, n32)
+    split = phases[3] is not None
+    e32, e64, e64_fb, frac_counted = counting_evals(models, grid, idx, st, nlim, n32, split)
     linear = algorithmic_layer_evals(models, idx, st, nlim)
     peak32 = FP32_FFMA_PER_CLK_SM * 2.0 * sms * SM_MAX_MHZ * 1e6
-    split = phases[3] is not None
     t0 = (phases[4] if split else phases[0]) * 1e-3
     t32 = (phases[3] if split else phases[0]) * 1e-3
     achieved = e64 * F_LAYER_FLOPS / t0

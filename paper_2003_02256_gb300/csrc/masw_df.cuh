@@ -559,6 +559,38 @@ __host__ __device__ __forceinline__ void df_record(const double* L, float* out) 
 // values of LayerNum).
 struct LayerNumDD { DF Dh, n00, n01, n11, ce, cf, cg; };
 
+// The element's denominator and numerators before the 1/(rho c^2) and
+// beta^2/c^2 factors of layer_numerators_dd.
+struct ElemDD { DF Dh, A1, D1, B1, E1, F1, G1; };
+
+// The plain forms of masw_device.cuh::layer_numerators in double-float, for
+// a layer whose shear wave is not evanescent (c >= beta_i). Out of line: few
+// layers of a certificate take it, and the hot branch of the element, below
+// the shear speed, then stays compact in the instruction cache.
+static __device__ __noinline__ ElemDD plain_numerators_dd(DF kh, DF r2, DF s2) {
+    const DF kh2 = dmul(kh, kh);
+    const WaveDF Rw = wave_df(kh, kh2, r2);
+    const WaveDF Sw = wave_df(kh, kh2, s2);
+    // both in the series (thin layer): E = 1 and C = 1 + U1, so
+    // E_r E_s - C_r C_s = -(U1_r + U1_s + U1_r U1_s) and C_s - C_r =
+    // U1_s - U1_r, without the cancellation of differences of numbers
+    // near 1 (those would lose digits as 1 / (k h)^2)
+    const bool ser = Rw.series && Sw.series;
+    const DF u = ser ? dneg(dadd(dadd(Rw.U1, Sw.U1), dmul(Rw.U1, Sw.U1)))
+                     : dsub(dmul(Rw.E, Sw.E), dmul(Rw.C, Sw.C));
+    const DF SdSd = dmul(Rw.Sd, Sw.Sd);
+    ElemDD e;
+    e.Dh = dadd(dscale(u, 2.0f), dadd(dmul(Rw.Sm, Sw.Sm), SdSd));
+    e.A1 = dsub(dmul(Rw.C, Sw.Sd), dmul(Sw.C, Rw.Sm));
+    e.D1 = dsub(dmul(Sw.C, Rw.Sd), dmul(Rw.C, Sw.Sm));
+    e.B1 = dneg(dadd(dmul(dadd_f(s2, 3.0f), u),
+                     dadd(dmul(Sw.Sm, dadd(dscale(Rw.Sm, 2.0f), Rw.Sd)), SdSd)));
+    e.E1 = dsub(dmul(Rw.Sm, Sw.E), dmul(Rw.E, Sw.Sd));
+    e.F1 = ser ? dsub(Sw.U1, Rw.U1) : dsub(dmul(Rw.E, Sw.C), dmul(Rw.C, Sw.E));
+    e.G1 = dsub(dmul(Sw.Sm, Rw.E), dmul(Sw.E, Rw.Sd));
+    return e;
+}
+
 // layer_numerators (masw_device.cuh) in double-float: the same quantities as
 // LayerNum, kept as double-floats. R = the record (12 floats); k, c^2 and
 // 1/c^2 as double-floats.
@@ -609,26 +641,14 @@ __device__ __forceinline__ LayerNumDD layer_numerators_dd(const float* __restric
         E1 = dmul(dsub(dS, dmul(om, dmul(Es, hr))), rws);
         G1 = dneg(dmul(dadd_s(dmul(om, dmul(Er, hs)), dS), rwr));
     } else {
-        // the plain forms of masw_device.cuh::layer_numerators
-        const DF kh2 = dmul(kh, kh);
-        const WaveDF Rw = wave_df(kh, kh2, r2);
-        const WaveDF Sw = wave_df(kh, kh2, s2);
-        // both in the series (thin layer): E = 1 and C = 1 + U1, so
-        // E_r E_s - C_r C_s = -(U1_r + U1_s + U1_r U1_s) and C_s - C_r =
-        // U1_s - U1_r, without the cancellation of differences of numbers
-        // near 1 (those would lose digits as 1 / (k h)^2)
-        const bool ser = Rw.series && Sw.series;
-        const DF u = ser ? dneg(dadd(dadd(Rw.U1, Sw.U1), dmul(Rw.U1, Sw.U1)))
-                         : dsub(dmul(Rw.E, Sw.E), dmul(Rw.C, Sw.C));
-        const DF SdSd = dmul(Rw.Sd, Sw.Sd);
-        Dh = dadd(dscale(u, 2.0f), dadd(dmul(Rw.Sm, Sw.Sm), SdSd));
-        A1 = dsub(dmul(Rw.C, Sw.Sd), dmul(Sw.C, Rw.Sm));
-        D1 = dsub(dmul(Sw.C, Rw.Sd), dmul(Rw.C, Sw.Sm));
-        B1 = dneg(dadd(dmul(dadd_f(s2, 3.0f), u),
-                       dadd(dmul(Sw.Sm, dadd(dscale(Rw.Sm, 2.0f), Rw.Sd)), SdSd)));
-        E1 = dsub(dmul(Rw.Sm, Sw.E), dmul(Rw.E, Sw.Sd));
-        F1 = ser ? dsub(Sw.U1, Rw.U1) : dsub(dmul(Rw.E, Sw.C), dmul(Rw.C, Sw.E));
-        G1 = dsub(dmul(Sw.Sm, Rw.E), dmul(Sw.E, Rw.Sd));
+        const ElemDD e = plain_numerators_dd(kh, r2, s2);
+        Dh = e.Dh;
+        A1 = e.A1;
+        D1 = e.D1;
+        B1 = e.B1;
+        E1 = e.E1;
+        F1 = e.F1;
+        G1 = e.G1;
     }
     const DF irc2 = dmul(irho, ic2);  // 1 / (rho c^2)
     return LayerNumDD{dmul(Dh, irc2), A1, dmul(dmul(b2, ic2), B1), D1, E1, F1, G1};

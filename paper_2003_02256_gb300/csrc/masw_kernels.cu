@@ -527,13 +527,15 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
 // count_split: the search ran before in count_search_kernel, its index in
 // n32), 640 for B = 64 (96 registers, fewer spills), so that the block size
 // also picks among three register budgets.
-// Search stage alone (count_search_pair): the index goes to nsearch[item],
-// for count_certify_kernel<B, true>. With an early list (plan count_split 2)
-// the items the certificate would only pass on to the linear FP32 scan (no
-// count change inside the pole-free range, a mode below V[0], test routing
-// 1..3) go straight to that list with their start in n32, and nsearch gets 0
-// for them and for models without a scan range (results written here), so
-// that the fallback chain can run on a second stream beside the certificate.
+// Search stage alone (count_search_single, one thread per item): the index
+// goes to nsearch[item], for count_certify_kernel<B, true>. With an early
+// list (plan count_split 2) the items the certificate would only pass on to
+// the linear FP32 scan (no count change inside the pole-free range, a mode
+// below V[0], test routing 1..3) go straight to that list with their start in
+// n32, and nsearch gets 0 for them and for models without a scan range
+// (results written here), so that the fallback chain can run on a second
+// stream beside the certificate. Natural item order: a warp's 32 items share
+// a model or two and have adjacent wavelengths, so their branches agree.
 template <int B>
 __global__ void __launch_bounds__(B) count_search_kernel(DevBatch b,
                                                          const float* __restrict__ layers32,
@@ -541,17 +543,14 @@ __global__ void __launch_bounds__(B) count_search_kernel(DevBatch b,
                                                          ScanOut o, int32_t* __restrict__ n32,
                                                          int32_t* early, int32_t* n_early,
                                                          int item_begin, int item_end) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int item = item_begin + (t >> 1);
-    if (item >= item_end) return;  // both lanes of a pair leave together
-    const int half = t & 1;
-    const unsigned pair = 3u << ((threadIdx.x & 31) & 30);
+    const int item = item_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= item_end) return;
     const int m = b.item_model[item];
     const int lo_rec = b.model_loff[m];
     const int N = b.model_loff[m + 1] - lo_rec - 1;
     const int nlim = b.model_nlim[m];
     if (nlim < 2) {
-        if (early && !half) {
+        if (early) {
             nsearch[item] = 0;
             n32[item] = -1;
             write_result(b, o, item, -1);
@@ -562,8 +561,7 @@ __global__ void __launch_bounds__(B) count_search_kernel(DevBatch b,
     const float* lay32 = layers32 + (size_t)lo_rec * LAYER_STRIDE32;
     const double k = b.k[item];
     const int npf = pole_free_points_f(lay32, N, (float)k, (float)b.c0, (float)b.dc, nlim);
-    const int n = count_search_pair(lay32, N, k, b.c0, b.dc, npf, half, pair);
-    if (half) return;
+    const int n = count_search_single(lay32, N, k, b.c0, b.dc, npf);
     if (!early || (n >= 1 && route_level(b.route) < 1)) {
         nsearch[item] = n;
         return;
@@ -791,7 +789,7 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
         int32_t* const side_counters = counters + SCAN_COUNTERS;
         int32_t* const nsearch = overlap ? side->nsearch : n32;
         if (p.count_split) {
-            count_search_kernel<128><<<(2 * n + 127) / 128, 128, 0, s>>>(
+            count_search_kernel<128><<<(n + 127) / 128, 128, 0, s>>>(
                 b, layers32, nsearch, o, n32, overlap ? side->fallback : nullptr,
                 overlap ? side_counters + 3 : nullptr, item_begin, item_end);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
