@@ -112,13 +112,16 @@ typedef struct {
     int32_t count_block;     /* precision 2: threads per block of the counting kernel, 64, 128
                                 (default) or 256 (two lanes per item, items of a block
                                 consecutive; launch bounds of 14, 7 or 3 resident blocks) */
-    int32_t count_split;     /* precision 2: 1 the FP32 search in a kernel of its own before
-                                the certificate's, 0 both in one kernel; 2 (default) as 1,
-                                and the items the search passes straight to the linear
-                                FP32 scan (no count change below the bound, a mode below
-                                V[0]) take that scan, its check and the mode-count search
-                                on a second, highest-priority stream beside the
-                                certificate. Same results for all three; with 1 or 2,
+    int32_t count_split;     /* precision 2: 0 the search (a lane pair per item, three-way
+                                splits) and the certificate in one kernel; 1 the search
+                                in a kernel of its own (one thread per item, bisection)
+                                before the certificate's; 2 as 1, and the items the
+                                search passes straight to the linear FP32 scan (no count
+                                change below the bound, a mode below V[0]) take that
+                                scan, its check and the mode-count search on a second,
+                                highest-priority stream beside the certificate. Same
+                                results for all three. Default by batch size: 0 below
+                                131,072 items, 1 below 262,144, else 2. With 1 or 2,
                                 count_block 64 gives the certificate kernel 640 resident
                                 threads (96 registers) */
 } masw_plan;
@@ -400,8 +403,9 @@ int masw_sincos_check(int32_t n, const double* x, double* s_lib, double* c_lib, 
 
 /* The element stiffness of finite layer layer[t] (0-based) of item item[t]'s
  * model at test velocity c[t] > 0, from the FP64 element and from the
- * double-float element of the counting certificate; a diagnostic for testing
- * the latter's accuracy. No paper counterpart. Outputs (host arrays, 7
+ * double-float element of the counting certificate (dd_trig 0) or of the
+ * leaky continuation (dd_trig 1: its trigonometric branch in double-float
+ * too); a diagnostic for testing the latter's accuracy. No paper counterpart. Outputs (host arrays, 7
  * doubles per point): the common denominator and the numerators
  * (D, K11 00, K11 01, K11 11, K12 00, K12 01, K12 11) with K = numerator / D
  * in units of k (the two may scale D and the numerators by different
@@ -409,7 +413,7 @@ int masw_sincos_check(int32_t n, const double* x, double* s_lib, double* c_lib, 
  * item or layer out of range or a non-positive c. Allocates and frees a
  * device buffer of 16 n doubles; synchronises the batch stream. */
 int masw_element_check(masw_batch* batch, int32_t n, const int32_t* item, const int32_t* layer,
-                       const double* c, double* fp64, double* df);
+                       const double* c, int32_t dd_trig, double* fp64, double* df);
 
 /* FP64 fused multiply-add throughput of this GPU in flop/s (2 per DFMA),
  * measured by a dependent-chain microbenchmark on `cuda_stream`. */

@@ -8,9 +8,12 @@ float of v and lo the nearest float of v - hi, from 60-digit mpmath:
   EXP2N_DF[i]  = 2^(-i/256),         i = 0..130
   COSH_DF[n]   = 1/(2n)!,            n = 0..9
   SINH_DF[n]   = 1/(2n+1)!,          n = 0..8
-and the reduction constants of ln 2 / 256 as three floats L1 + L2 + L3 with
+the reduction constants of ln 2 / 256 as three floats L1 + L2 + L3 with
 L1 and L2 rounded to 9 significant bits (so n L1 and n L2 are exact for
-|n| < 2^15) and L3 the nearest float of the rest."""
+|n| < 2^15) and L3 the nearest float of the rest, and those of pi / 2 as
+four floats P1 + P2 + P3 + P4 with P1 and P2 rounded to 12 significant bits
+(j P1 and j P2 exact for 0 <= j < 2^12), P3 the nearest float of the rest
+and P4 the nearest float of what remains, with 2 / pi as a float."""
 import struct
 
 import mpmath as mp
@@ -46,14 +49,20 @@ def tables():
         L2 = round_bits(L - L1, 9)
         L3 = f32(L - L1 - L2)
         inv = f32(256 / mp.log(2))
+        H = mp.pi / 2
+        P1 = round_bits(H, 12)
+        P2 = round_bits(H - P1, 12)
+        P3 = f32(H - P1 - P2)
+        P4 = f32(H - P1 - P2 - mp.mpf(P3))
+        pio2 = (float(P1), float(P2), P3, P4, f32(2 / mp.pi))
         # Taylor coefficients of cosh(x) and sinh(x)/x in u = x^2
         cosh_c = [split(1 / mp.factorial(2 * n)) for n in range(10)]
         sinh_c = [split(1 / mp.factorial(2 * n + 1)) for n in range(9)]
-    return exp2, expm1, exp2n, (float(L1), float(L2), L3), inv, cosh_c, sinh_c
+    return exp2, expm1, exp2n, (float(L1), float(L2), L3), inv, cosh_c, sinh_c, pio2
 
 
 def emit():
-    exp2, expm1, exp2n, (L1, L2, L3), inv, cosh_c, sinh_c = tables()
+    exp2, expm1, exp2n, (L1, L2, L3), inv, cosh_c, sinh_c, pio2 = tables()
     out = []
     def arr(name, vals):
         out.append(f"__device__ const float2 {name}[{len(vals)}] = {{")
@@ -69,6 +78,9 @@ def emit():
     out.append(f"constexpr float DF_LN2_256_2 = {hexf(L2)}f;")
     out.append(f"constexpr float DF_LN2_256_3 = {hexf(L3)}f;")
     out.append(f"constexpr float DF_INV_LN2_256 = {hexf(inv)}f;")
+    for i in range(4):
+        out.append(f"constexpr float DF_PIO2_{i + 1} = {hexf(pio2[i])}f;")
+    out.append(f"constexpr float DF_TWO_OVER_PI = {hexf(pio2[4])}f;")
     return "\n".join(out)
 
 

@@ -353,7 +353,10 @@ static masw_plan default_plan(const masw_batch* B) {
     p.use_graph = 1;
     p.precision = 2;
     p.count_block = 128;
-    p.count_split = 2;
+    // the fused kernel's lane pairs give small batches the shortest chain;
+    // large ones take the split kernels, and from a quarter million items
+    // the search's fallback items on the second stream
+    p.count_split = B->n_items < (1 << 17) ? 0 : B->n_items < (1 << 18) ? 1 : 2;
     return p;
 }
 
@@ -787,7 +790,8 @@ int masw_dispersion_leaky(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* s
     int32_t* lk_status = B->d_lk_idx + nw;
     ScanOut o{B->d_lk_ct, B->d_lk_idx, lk_status};
     CK(launch_leaky(B->dev(B->plan.ordered != 0), to_scan_plan(B, B->plan), B->d_idx,
-                    B->d_status, o, B->d_lk_idx + 2 * nw, B->stream));
+                    B->d_status, o, B->d_lk_idx + 2 * nw, B->plan.precision >= 1 ? 1 : 0,
+                    B->stream));
     bool sync = false;
     int rc;
     if ((rc = copy_out(ct, B->d_lk_ct, nw, B->stream, &sync)) ||
@@ -799,8 +803,9 @@ int masw_dispersion_leaky(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* s
 }
 
 int masw_element_check(masw_batch* B, int32_t n, const int32_t* item, const int32_t* layer,
-                       const double* c, double* fp64, double* df) {
+                       const double* c, int32_t dd_trig, double* fp64, double* df) {
     if (!B || n < 0 || (n > 0 && (!item || !layer || !c || !fp64 || !df))) return MASW_EINVAL;
+    if (dd_trig != 0 && dd_trig != 1) return MASW_EINVAL;
     for (int32_t t = 0; t < n; ++t) {
         if (item[t] < 0 || item[t] >= B->n_items) return MASW_EINVAL;
         const int32_t m = B->item_model[item[t]];
@@ -820,7 +825,7 @@ int masw_element_check(masw_batch* B, int32_t n, const int32_t* item, const int3
     cudaError_t e = cudaMemcpyAsync(d_item, item, n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_layer, layer, n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_c, c, n * sizeof(double), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_element_check(B->dev(false), n, d_item, d_layer, d_c, d_fp, d_df, s);
+    if (e == cudaSuccess) e = launch_element_check(B->dev(false), n, d_item, d_layer, d_c, dd_trig, d_fp, d_df, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(fp64, d_fp, 7 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)

@@ -901,26 +901,18 @@ __device__ __forceinline__ int det_sign(const double* __restrict__ lay, int N, d
 // the pivot is S = Phat / w + M / u = Shat / (u w) with Shat = u Phat + w M, so
 // det S = det Shat / (u w)^2 and sign Re det S = sign Re(det Shat conj(u)^2):
 // no division. Below the shear speed this is det_sign's arithmetic exactly.
-__device__ inline int det_sign_leaky(const double* __restrict__ lay, int N, double k, double c) {
-    double c2 = c * c;
-    const double ic2 = inv_c2(c2);
-    HState st{0.0, 0.0, 0.0, 1.0};
-    int sg = 1;
-    for (int j = 0; j < N; ++j) {
-        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2, ic2);
-        bool ok;
-        double det = schur_layer(st, n, &ok);
-        sg *= sgn(det);
-        if (!ok) return 0;
-    }
-    const double* __restrict__ H = lay + N * LAYER_STRIDE;
+// leaky_halfspace_sign is the last pivot's part of that sign, given the state
+// st after the finite layers (real below the half-space shear speed, q < 1);
+// det_sign_leaky the whole sign over the FP64 element.
+__device__ inline int leaky_halfspace_sign(const double* __restrict__ H, double c2,
+                                           const HState& st) {
     const double q = c2 * H[L_IB2];
     if (q < 1.0) {
         HalfNum hn = halfspace_numerators(H, c2);
         double s00 = fma(hn.den, st.p00, st.w * hn.m00);
         double s01 = fma(hn.den, st.p01, st.w * hn.m01);
         double s11 = fma(hn.den, st.p11, st.w * hn.m11);
-        return sg * sgn(fma(s00, s11, -s01 * s01));
+        return sgn(fma(s00, s11, -s01 * s01));
     }
     const double p = c2 * H[L_IA2];
     const double sig = sqrt(q - 1.0);  // s = i sig
@@ -947,7 +939,22 @@ __device__ inline int det_sign_leaky(const double* __restrict__ lay, int N, doub
     const double t_im = fma(a_re, d_im, a_im * d_re) - 2.0 * b_re * b_im;
     // conj(u)^2 = (u_re^2 - u_im^2, -2 u_re u_im)
     const double v_re = fma(u_re, u_re, -u_im * u_im), v_im = -2.0 * u_re * u_im;
-    return sg * sgn(fma(t_re, v_re, -t_im * v_im));
+    return sgn(fma(t_re, v_re, -t_im * v_im));
+}
+
+__device__ inline int det_sign_leaky(const double* __restrict__ lay, int N, double k, double c) {
+    double c2 = c * c;
+    const double ic2 = inv_c2(c2);
+    HState st{0.0, 0.0, 0.0, 1.0};
+    int sg = 1;
+    for (int j = 0; j < N; ++j) {
+        LayerNum n = layer_numerators(lay + j * LAYER_STRIDE, k, c2, ic2);
+        bool ok;
+        double det = schur_layer(st, n, &ok);
+        sg *= sgn(det);
+        if (!ok) return 0;
+    }
+    return sg * leaky_halfspace_sign(lay + N * LAYER_STRIDE, c2, st);
 }
 
 // Sign of det K (as det_sign: 0 for an exact zero or a failed rescaling) and

@@ -329,6 +329,11 @@ constexpr float DF_LN2_256_1 = 0x1.6300000000000p-9f;
 constexpr float DF_LN2_256_2 = -0x1.bd00000000000p-21f;
 constexpr float DF_LN2_256_3 = -0x1.05c6100000000p-37f;
 constexpr float DF_INV_LN2_256 = 0x1.7154760000000p+8f;
+constexpr float DF_PIO2_1 = 0x1.9220000000000p+0f;
+constexpr float DF_PIO2_2 = -0x1.2ae0000000000p-18f;
+constexpr float DF_PIO2_3 = -0x1.de973e0000000p-31f;
+constexpr float DF_PIO2_4 = 0x1.a626340000000p-58f;
+constexpr float DF_TWO_OVER_PI = 0x1.45f3060000000p-1f;
 
 
 // ------------------------------------------------------------- arithmetic
@@ -504,11 +509,46 @@ __device__ __forceinline__ void dseries(DF u, DF* chm1, DF* sh) {
     *sh = ps;
 }
 
+// sin x and cos x for x >= 0 in double-float. Cody-Waite reduction by the
+// nearest multiple j of pi/2, r = x - j (P1 + P2 + P3 + P4): j P1 and j P2
+// are exact floats for j < 2^12, j P3 an exact product pair, j P4 a rounded
+// float, and the four parts sum to pi/2 within 2^-80, so each step of the
+// reduction adds an error of about 2^-47 |r| and the constant none that
+// matters. Then cos r - 1 and sin r / r from dseries in u = -r^2
+// (|u| <= 0.62), and the quadrant j mod 4. Larger arguments (j >= 2^12,
+// x above 6433) take FP64's sincos, split.
+__device__ __forceinline__ void dsincos(DF x, DF* sn, DF* cs) {
+    const float jf = rintf(__fmul_rn(x.hi, DF_TWO_OVER_PI));
+    if (!(jf < 4096.0f)) {
+        double s, c;
+        sincos(to_double(x), &s, &c);
+        *sn = from_double(s);
+        *cs = from_double(c);
+        return;
+    }
+    DF r = dadd_f(two_sum(x.hi, -__fmul_rn(jf, DF_PIO2_1)), x.lo);
+    r = dadd_f(r, -__fmul_rn(jf, DF_PIO2_2));
+    r = dsub(r, two_prod(jf, DF_PIO2_3));
+    r = dadd_f(r, -__fmul_rn(jf, DF_PIO2_4));
+    DF cm1, sx;
+    dseries(dneg(dmul(r, r)), &cm1, &sx);
+    const DF s_r = dmul(r, sx);
+    const DF c_r = dadd_q(dfc(1.0f), cm1);
+    const int q = ((int)jf) & 3;
+    const DF a = (q & 1) ? c_r : s_r;
+    const DF c = (q & 1) ? s_r : c_r;
+    *sn = (q & 2) ? dneg(a) : a;
+    *cs = ((q + 1) & 2) ? dneg(c) : c;
+}
+
 // U1 = C - 1 (cosh - 1 unscaled) in the series branch, where E = 1.
 struct WaveDF { DF E, C, Sd, Sm, U1; bool series; };
 
 // The scaled even functions of masw_device.cuh::wave_fns in double-float
-// (out of line: called twice per element).
+// (out of line: called twice per element). DDTRIG: the trigonometric branch
+// (k h |w| >= 1, w imaginary) in double-float too (dsincos); otherwise FP64's
+// sincos, split.
+template <bool DDTRIG>
 static __device__ __noinline__ WaveDF wave_df(DF kh, DF kh2, DF w2) {
     const DF u = dmul(kh2, w2);
     WaveDF o;
@@ -532,6 +572,16 @@ static __device__ __noinline__ WaveDF wave_df(DF kh, DF kh2, DF w2) {
         o.C = dscale(dadd_q(dfc(1.0f), E2), 0.5f);
         o.Sd = dmul(t, rw);
         o.Sm = dmul(t, w);
+    } else if (DDTRIG) {  // k h |w| >= 1 with w imaginary
+        const DF nw2 = dneg(w2);
+        const DF rw = drsqrt(nw2);
+        const DF w = dmul(nw2, rw);
+        DF sn, cs;
+        dsincos(dmul(kh, w), &sn, &cs);
+        o.E = dfc(1.0f);
+        o.C = cs;
+        o.Sd = dmul(sn, rw);
+        o.Sm = dneg(dmul(w, sn));
     } else {  // k h |w| >= 1 with w imaginary: FP64 sincos, split
         const double nw2 = -to_double(w2);
         const double rw = rsqrt(nw2);
@@ -567,10 +617,11 @@ struct ElemDD { DF Dh, A1, D1, B1, E1, F1, G1; };
 // a layer whose shear wave is not evanescent (c >= beta_i). Out of line: few
 // layers of a certificate take it, and the hot branch of the element, below
 // the shear speed, then stays compact in the instruction cache.
+template <bool DDTRIG>
 static __device__ __noinline__ ElemDD plain_numerators_dd(DF kh, DF r2, DF s2) {
     const DF kh2 = dmul(kh, kh);
-    const WaveDF Rw = wave_df(kh, kh2, r2);
-    const WaveDF Sw = wave_df(kh, kh2, s2);
+    const WaveDF Rw = wave_df<DDTRIG>(kh, kh2, r2);
+    const WaveDF Sw = wave_df<DDTRIG>(kh, kh2, s2);
     // both in the series (thin layer): E = 1 and C = 1 + U1, so
     // E_r E_s - C_r C_s = -(U1_r + U1_s + U1_r U1_s) and C_s - C_r =
     // U1_s - U1_r, without the cancellation of differences of numbers
@@ -593,7 +644,9 @@ static __device__ __noinline__ ElemDD plain_numerators_dd(DF kh, DF r2, DF s2) {
 
 // layer_numerators (masw_device.cuh) in double-float: the same quantities as
 // LayerNum, kept as double-floats. R = the record (12 floats); k, c^2 and
-// 1/c^2 as double-floats.
+// 1/c^2 as double-floats. DDTRIG as for wave_df (the leaky continuation,
+// where most layers are above their shear speed).
+template <bool DDTRIG = false>
 __device__ __forceinline__ LayerNumDD layer_numerators_dd(const float* __restrict__ R, DF k, DF c2,
                                                           DF ic2) {
     const float4 A = *reinterpret_cast<const float4*>(R);
@@ -641,7 +694,7 @@ __device__ __forceinline__ LayerNumDD layer_numerators_dd(const float* __restric
         E1 = dmul(dsub(dS, dmul(om, dmul(Es, hr))), rws);
         G1 = dneg(dmul(dadd_s(dmul(om, dmul(Er, hs)), dS), rwr));
     } else {
-        const ElemDD e = plain_numerators_dd(kh, r2, s2);
+        const ElemDD e = plain_numerators_dd<DDTRIG>(kh, r2, s2);
         Dh = e.Dh;
         A1 = e.A1;
         D1 = e.D1;
@@ -799,6 +852,36 @@ static __device__ __noinline__ int det_inertia_dd(const float* __restrict__ layd
                                                   const double* __restrict__ lay, int N, double k,
                                                   double c) {
     return det_inertia_t<true>(laydf, lay, N, k, c);
+}
+
+// Sign of Re det K(k, c) for any c > 0 (masw_device.cuh::det_sign_leaky)
+// with each finite layer's element in double-float, trigonometric branch
+// included (layer_numerators_dd<true>): above the half-space shear speed
+// most layers are above their own, and FP64's sincos there set the pace of
+// the FP64 form. The Schur step stays in FP64 (schur_layer; far above the
+// pole-free range the recurrence cancels next to the poles) and so does the
+// complex half-space pivot (leaky_halfspace_sign). 0 for an exact zero or a
+// failed rescaling, as det_sign_leaky. laydf: the N finite layers'
+// double-float records. Out of line: one copy for the continuation kernel.
+static __device__ __noinline__ int det_sign_leaky_df(const float* __restrict__ laydf,
+                                                     const double* __restrict__ lay, int N,
+                                                     double k, double c) {
+    const double c2 = c * c;
+    const DF kd = from_double(k), cd = from_double(c);
+    const DF c2d = dmul(cd, cd);
+    const DF ic2d = drcp(c2d);
+    HState st{0.0, 0.0, 0.0, 1.0};
+    int sg = 1;
+    for (int j = 0; j < N; ++j) {
+        const LayerNumDD nd = layer_numerators_dd<true>(laydf + j * LAYER_STRIDE_DF, kd, c2d, ic2d);
+        const LayerNum n{to_double(nd.Dh), to_double(nd.n00), to_double(nd.n01),
+                         to_double(nd.n11), to_double(nd.ce), to_double(nd.cf),
+                         to_double(nd.cg)};
+        bool ok;
+        sg *= sgn(schur_layer(st, n, &ok));
+        if (!ok) return 0;
+    }
+    return sg * leaky_halfspace_sign(lay + N * LAYER_STRIDE, c2, st);
 }
 
 // Wittrick-Williams mode count of the layered structure below c, split as

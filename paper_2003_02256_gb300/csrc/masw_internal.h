@@ -109,9 +109,10 @@ cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const in
 
 // Leaky continuation: Algorithm 1 over the whole grid with the sign of Re det K
 // (complex half-space block at c >= beta_hs); items the batch scan resolved
-// (status_in 0) keep idx_in; outputs o; counter: 1 (masw_kernels.cu).
+// (status_in 0) keep idx_in; outputs o; counter: 1; dd: the elements in
+// double-float (det_sign_leaky_df), else FP64 (masw_kernels.cu).
 cudaError_t launch_leaky(const DevBatch& b, const ScanPlan& p, const int32_t* idx_in,
-                         const int32_t* status_in, const ScanOut& o, int32_t* counter,
+                         const int32_t* status_in, const ScanOut& o, int32_t* counter, int dd,
                          cudaStream_t s);
 
 cudaError_t launch_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p, int32_t* counter,
@@ -138,7 +139,8 @@ cudaError_t launch_update_beta_h(const DevBatch& b, const double* h, const doubl
                                  double* layers, float* layers32, float* layers_df, int32_t* nlim,
                                  int32_t* err, cudaStream_t s);
 cudaError_t launch_element_check(const DevBatch& b, int n, const int32_t* item, const int32_t* layer,
-                                 const double* c, double* fp64, double* df, cudaStream_t s);
+                                 const double* c, int dd_trig, double* fp64, double* df,
+                                 cudaStream_t s);
 cudaError_t launch_exp_check(int n, const double* x, double* y_lib, double* y_cuda,
                              cudaStream_t s);
 cudaError_t launch_sincos_check(int n, const double* x, double* s_lib, double* c_lib,

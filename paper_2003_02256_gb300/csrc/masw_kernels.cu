@@ -1055,7 +1055,7 @@ template <int G>
 __global__ void __launch_bounds__(256) leaky_scan64_kernel(DevBatch b, ScanOut o,
                                                            const int32_t* __restrict__ idx_in,
                                                            const int32_t* __restrict__ status_in,
-                                                           int32_t* counter) {
+                                                           int32_t* counter, int dd) {
     static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "lanes per item: a power of two");
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
@@ -1076,11 +1076,15 @@ __global__ void __launch_bounds__(256) leaky_scan64_kernel(DevBatch b, ScanOut o
             const int N = b.model_loff[m + 1] - lo - 1;
             const double* lay = b.layers + (size_t)lo * LAYER_STRIDE;
             const double k = b.k[item];
+            const float* laydf = records_df(b, lo);
             const int start = max(b.model_nlim[m], 1);
             int carry = 0;
             for (int base = start - 1; base < b.n_c; base += G) {
                 const int n = base + gl;
-                const int sg = n < b.n_c ? det_sign_leaky(lay, N, k, grid_c(b.c0, b.dc, n)) : 0;
+                const double c = grid_c(b.c0, b.dc, n);
+                const int sg = n >= b.n_c ? 0
+                               : (dd && laydf) ? det_sign_leaky_df(laydf, lay, N, k, c)
+                                               : det_sign_leaky(lay, N, k, c);
                 int ps = __shfl_up_sync(gmask, sg, 1, G);
                 if (gl == 0) ps = carry;
                 const unsigned msk =
@@ -1112,14 +1116,14 @@ __global__ void __launch_bounds__(256) leaky_scan64_kernel(DevBatch b, ScanOut o
 constexpr int LEAKY_LANES = 32;
 
 cudaError_t launch_leaky(const DevBatch& b, const ScanPlan& p, const int32_t* idx_in,
-                         const int32_t* status_in, const ScanOut& o, int32_t* counter,
+                         const int32_t* status_in, const ScanOut& o, int32_t* counter, int dd,
                          cudaStream_t s) {
     if (b.n_items == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     const int wpb = p.warps_per_block;
     leaky_scan64_kernel<LEAKY_LANES><<<std::max(1, std::min(p.blocks, (b.n_items + wpb - 1) / wpb)),
-                                       32 * wpb, 0, s>>>(b, o, idx_in, status_in, counter);
+                                       32 * wpb, 0, s>>>(b, o, idx_in, status_in, counter, dd);
     return cudaGetLastError();
 }
 
@@ -1131,7 +1135,8 @@ cudaError_t launch_leaky(const DevBatch& b, const ScanPlan& p, const int32_t* id
 // point) and the double-float one (df) (tests).
 __global__ void element_check_kernel(DevBatch b, int n, const int32_t* __restrict__ item,
                                      const int32_t* __restrict__ layer,
-                                     const double* __restrict__ c, double* fp64, double* df) {
+                                     const double* __restrict__ c, int dd_trig, double* fp64,
+                                     double* df) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int it = item[t];
@@ -1140,8 +1145,15 @@ __global__ void element_check_kernel(DevBatch b, int n, const int32_t* __restric
     const double cc = c[t], c2 = cc * cc, k = b.k[it];
     const LayerNum a = layer_numerators(b.layers + (size_t)rec * LAYER_STRIDE, k, c2, inv_c2(c2));
     const DF cd = from_double(cc), c2d = dmul(cd, cd);
-    const LayerNum d = layer_numerators_df(b.layers_df + (size_t)rec * LAYER_STRIDE_DF,
-                                           from_double(k), c2d, drcp(c2d));
+    const float* R = b.layers_df + (size_t)rec * LAYER_STRIDE_DF;
+    LayerNum d;
+    if (dd_trig) {
+        const LayerNumDD e = layer_numerators_dd<true>(R, from_double(k), c2d, drcp(c2d));
+        d = LayerNum{to_double(e.Dh), to_double(e.n00), to_double(e.n01), to_double(e.n11),
+                     to_double(e.ce), to_double(e.cf), to_double(e.cg)};
+    } else {
+        d = layer_numerators_df(R, from_double(k), c2d, drcp(c2d));
+    }
     const double va[7] = {a.Dh, a.n00, a.n01, a.n11, a.ce, a.cf, a.cg};
     const double vd[7] = {d.Dh, d.n00, d.n01, d.n11, d.ce, d.cf, d.cg};
     for (int q = 0; q < 7; ++q) {
@@ -1151,9 +1163,10 @@ __global__ void element_check_kernel(DevBatch b, int n, const int32_t* __restric
 }
 
 cudaError_t launch_element_check(const DevBatch& b, int n, const int32_t* item, const int32_t* layer,
-                                 const double* c, double* fp64, double* df, cudaStream_t s) {
+                                 const double* c, int dd_trig, double* fp64, double* df,
+                                 cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    element_check_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, n, item, layer, c, fp64, df);
+    element_check_kernel<<<(n + 127) / 128, 128, 0, s>>>(b, n, item, layer, c, dd_trig, fp64, df);
     return cudaGetLastError();
 }
 

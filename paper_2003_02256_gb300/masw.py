@@ -377,19 +377,21 @@ def sincos_check(x, stream=None):
     return tuple(outs)
 
 
-def element_check(handle, item, layer, c):
+def element_check(handle, item, layer, c, dd_trig=False):
     """(fp64, df): the element's denominator and six numerators (7 per point)
-    from the FP64 element and the double-float one (masw_element_check)."""
+    from the FP64 element and the double-float one (masw_element_check;
+    dd_trig: the leaky continuation's, trigonometric branch in double-float)."""
     item = np.ascontiguousarray(item, dtype=np.int32)
     layer = np.ascontiguousarray(layer, dtype=np.int32)
     c = np.ascontiguousarray(c, dtype=np.float64)
     fp = np.empty((item.size, 7))
     df = np.empty((item.size, 7))
     f = load().masw_element_check
-    f.argtypes = [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 5
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 3 + \
+        [ctypes.c_int32] + [ctypes.c_void_p] * 2
     f.restype = ctypes.c_int
-    _check(f(ctypes.c_void_p(handle), item.size, _ptr(item), _ptr(layer), _ptr(c), _ptr(fp),
-             _ptr(df)), "masw_element_check")
+    _check(f(ctypes.c_void_p(handle), item.size, _ptr(item), _ptr(layer), _ptr(c),
+             int(bool(dd_trig)), _ptr(fp), _ptr(df)), "masw_element_check")
     return fp, df
 
 

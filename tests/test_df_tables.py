@@ -83,3 +83,22 @@ def test_reduction_constants(src):
     # n L1 and n L2 exact in float for |n| < 2^15
     for n in (1, 129, 32132, 32767):
         assert f32(n * L1) == n * L1 and f32(n * L2) == n * L2
+
+
+def test_pi_over_2_reduction_constants(src):
+    """pi/2 = P1 + P2 + P3 + P4 within 2^-80 of it, P1 and P2 of at most 12
+    significant bits (j P1 and j P2 exact floats for 0 <= j < 2^12), P3 and
+    P4 the nearest floats of the successive remainders; 2/pi the nearest
+    float. The double-float sine and cosine reduce by these."""
+    P = [constant(src, f"DF_PIO2_{i}") for i in (1, 2, 3, 4)]
+    for v in P[:2]:
+        m, e = mp.frexp(mp.mpf(v))
+        assert int(abs(m) * 2 ** 12) == abs(m) * 2 ** 12
+    with mp.workdps(60):
+        H = mp.pi / 2
+        assert P[2] == f32(H - P[0] - P[1])
+        assert P[3] == f32(H - P[0] - P[1] - mp.mpf(P[2]))
+        assert abs(sum(mp.mpf(p) for p in P) - H) <= mp.mpf(2) ** -80
+        assert constant(src, "DF_TWO_OVER_PI") == f32(2 / mp.pi)
+    for j in (1, 3, 1000, 4095):
+        assert f32(j * P[0]) == j * P[0] and f32(j * P[1]) == j * P[1]

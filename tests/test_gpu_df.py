@@ -116,3 +116,69 @@ def test_double_float_element_against_50_digits(masw, which):
     assert (err_df <= np.maximum(30 * err_fp, 1e-11)).all()
     if which != "extreme":
         assert err_df.max() <= 1e-11
+
+
+def leaky_points(models, grid, rng, n):
+    """(item, layer, c) with c between the half-space shear speed and the top
+    of the grid: the leaky continuation's points, where most finite layers
+    are above their shear speed (trigonometric branch, arguments k h |s| up
+    to a few hundred)."""
+    item_model = np.repeat(np.arange(models.n_models), models.n_lambda)
+    top = grid.c0 + grid.dc * (grid.n_c - 1)
+    pts = []
+    while len(pts) < n:
+        it = int(rng.integers(models.n_items))
+        h, a, b, r, _ = models.model(item_model[it])
+        if h.size == 0 or b[-1] >= top:
+            continue
+        j = int(rng.integers(h.size))
+        c = float(rng.uniform(b[-1], top))
+        pts.append((it, j, c, h[j], a[j], b[j], r[j], 2 * math.pi / models.lam[it]))
+    return pts
+
+
+@pytest.mark.parametrize("which", ["leaky", "ragged"])
+def test_leaky_double_float_element_against_50_digits(masw, which):
+    """The leaky continuation's element (dd_trig: the trigonometric branch in
+    double-float, dsincos) against 50 digits. There the phase x = k h |w|
+    of a wave reaches several hundred radians, and a double-float phase
+    carries an absolute error of a few units of 2^-48 |x| (k h, w = sqrt(-w2)
+    and their product each round once or twice), which sine and cosine pass
+    on unchanged. Above the shear speeds the element takes its plain forms,
+    which cancel at some points for both forms alike; there the error scales
+    with the unit roundoff, 2^-47 for a double-float product or sum against
+    2^-53, a ratio of 64. Bar, at every point: no worse than the FP64 element
+    by more than a factor 100, or than 1e-11, or than 64 x 2^-48 x the
+    point's largest phase; median 1e-12."""
+    if which == "leaky":
+        m, g = W.leaky_batch(n_models=32)
+    else:
+        m, _ = W.ragged_batch(n_models=32)
+        g = W.Grid(500.0, 0.25, 3001)
+    rng = np.random.default_rng(19)
+    pts = leaky_points(m, g, rng, 300)
+
+    def phase(c, h, a, bb, k):
+        return k * h * max(math.sqrt(max(c * c / (bb * bb) - 1.0, 0.0)),
+                           math.sqrt(max(c * c / (a * a) - 1.0, 0.0)))
+
+    x = np.array([phase(c, h, a, bb, k) for _, _, c, h, a, bb, _, k in pts])
+    assert x.max() > 20.0  # the reduction by pi/2 takes several quadrants
+    with masw.Batch(m, g) as b:
+        fp, df = masw.element_check(b.handle, [p[0] for p in pts], [p[1] for p in pts],
+                                    [p[2] for p in pts], dd_trig=True)
+    err_df, err_fp = [], []
+    for t, (_, _, c, h, a, bb, r, k) in enumerate(pts):
+        ref = reference_entries(h, a, bb, r, k, c)
+        scale = np.abs(ref).max()
+        err_df.append(np.abs(df[t, 1:] / df[t, 0] - ref).max() / scale)
+        err_fp.append(np.abs(fp[t, 1:] / fp[t, 0] - ref).max() / scale)
+    err_df, err_fp = np.array(err_df), np.array(err_fp)
+    w = int(np.argmax(err_df))
+    print(f"{which}: double-float max {err_df.max():.1e} (phase {x[w]:.0f}, FP64 there "
+          f"{err_fp[w]:.1e}) median {np.median(err_df):.1e}; FP64 max {err_fp.max():.1e} "
+          f"median {np.median(err_fp):.1e}; largest phase {x.max():.0f}")
+    assert np.isfinite(err_df).all()
+    assert np.median(err_df) <= 1e-12
+    bar = np.maximum(np.maximum(100 * err_fp, 1e-11), 64 * 2.0 ** -48 * x)
+    assert (err_df <= bar).all(), np.nonzero(err_df > bar)

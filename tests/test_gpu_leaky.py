@@ -140,3 +140,25 @@ def test_invalid_arguments_of_the_new_entry_points(masw):
         assert lib.masw_last_changes_linear(h, ctypes.byref(n)) == 0 and n.value == -1
         ct, idx, st = b.leaky()  # still usable
         assert (st == 0).all()
+
+
+def test_double_float_continuation_equals_the_fp64_one(masw, oracle_lib):
+    """The default plan continues with the element in double-float
+    (det_sign_leaky_df); plan precision 0 with the FP64 element
+    (det_sign_leaky). On the full leaky batch they agree item for item but
+    for sign decisions within rounding of zero: at most 0.01 % of items
+    differ, and where they do, both lie within one grid step of the
+    oracle's index."""
+    m, g = W.leaky_batch()
+    with masw.Batch(m, g) as b:
+        _, idx_dd, st_dd = b.leaky()
+        b.set_plan(precision=0)
+        _, idx64, st64 = b.leaky()
+    assert np.array_equal(st_dd, st64)
+    diff = np.nonzero(idx_dd != idx64)[0]
+    print(f"{diff.size} of {m.n_items} items differ")
+    assert diff.size <= 1e-4 * m.n_items
+    if diff.size:
+        _, o_idx, o_st = oracle_leaky(oracle_lib, m, g, diff)
+        assert (o_st == 0).all()
+        assert (np.abs(idx_dd[diff] - o_idx) <= 1).all() and (np.abs(idx64[diff] - o_idx) <= 1).all()
