@@ -117,6 +117,14 @@ CERTIFY_DRAM_BYTES = {"uniform": (4.459008e6, 1024), "ragged": (10.631168e6, 204
 CERTIFY_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 50.67, "ragged": 53.29}
 SEARCH_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 5.237, "ragged": 5.535}
 ISSUE_PER_CLK_SM = 4
+# FP64-pipe warp instructions per layer-evaluation of the leaky continuation
+# over the double-float element (ncu sm__inst_executed_pipe_fp64.sum of the
+# 256-model leaky batch's launch, 74.85 M, over its 50.68 M layer-evaluations
+# counted as in extra_leaky): the FP64 Schur step, the element's conversions
+# and the complex half-space pivot. ncu's 100 % of the FP64 pipe is 2 thread
+# DFMA per clock per SM, a warp instruction per 16 clocks.
+LEAKY_FP64_WARP_INSTR_PER_LAYER_EVAL = 74.85e6 / 50.68e6
+FP64_WARP_INSTR_PER_CLK_SM = FP64_DFMA_PER_CLK_SM / 32
 # DRAM bytes (read + write) of one scan launch per model, from the ncu capture
 # of the 64-model case (281.6 KB read, 0 written), scaled by the models of a
 # launch; traffic grows with the number of items.
@@ -385,12 +393,41 @@ def executed_layer_evals(models, idx, st, nlim, cpl):
     return int(np.sum(pts * nl))
 
 
+def split_search_evals(models, npf, root, stride=4):
+    """FP32 evaluations per item of the split search (count_search_kernel):
+    every stride-th item of a model and its last bisect the whole pole-free
+    range (the top, then ceil(log2 npf) steps); the others start from the
+    bracket (min(na, nb) - 1, max(na, nb)] of those neighbours' indices and
+    widen it as count_search_bracket does. The located index is taken as the
+    item's first change (root) when it lies inside the range."""
+    ceil_log2 = lambda w: np.ceil(np.log2(np.maximum(w, 1)))
+    n_items = models.n_items
+    woff = np.concatenate([[0], np.cumsum(models.n_lambda)])
+    item_model = np.repeat(np.arange(models.n_models), models.n_lambda)
+    j = np.arange(n_items)
+    first, last = woff[item_model], woff[item_model + 1] - 1
+    loc = np.where(root < npf, root, -1)
+    full = np.where(npf >= 1, 1 + np.where(loc >= 0, ceil_log2(npf), 0), 0)
+    ja = first + ((j - first) // stride) * stride
+    jb = np.minimum(ja + stride, last)
+    anchor = ((j - first) % stride == 0) | (j == last)
+    na, nb = loc[ja], loc[jb]
+    hi = np.minimum(np.maximum(na, nb), npf - 1)
+    lo = np.minimum(np.minimum(na, nb) - 1, hi - 1)
+    above = (loc < 0) | (loc > hi)
+    e_above = np.where(hi == npf - 1, 1, np.where(loc < 0, 2, 2 + ceil_log2(npf - 1 - hi)))
+    e_in = np.where(lo >= 0, 2 + np.where(loc <= lo, ceil_log2(lo + 1), ceil_log2(hi - lo)),
+                    1 + ceil_log2(hi + 1))
+    bracket = np.where(above, e_above, e_in)
+    use_full = anchor | (na < 1) | (nb < 1) | (npf < 1)
+    return np.where(npf >= 1, np.where(use_full, full, bracket), 0)
+
+
 def counting_evals(models, grid, idx, st, nlim, n32, split=True):
     """Per-item evaluations of the counting-search scan (plan precision 2).
     FP32 layer evaluations of the search, npf = grid points below the
     pole-free bound min_i beta_i sqrt(1 + (pi/(k h_i))^2): split (its own
-    kernel, one thread per item) the top of the range, then ceil(log2 npf)
-    bisection steps when the change lies inside it; fused (a lane pair)
+    kernels, one thread per item) as split_search_evals; fused (a lane pair)
     1 + ceil(log3 npf) steps of two inertia counts. FP64 layer evaluations of
     the certificate: 2 per counted item. Fallback items: the linear FP32
     scan from its start up to the change, and the three-point FP64 check."""
@@ -409,8 +446,7 @@ def counting_evals(models, grid, idx, st, nlim, n32, split=True):
     npf = np.clip(np.ceil((cb * (1.0 - 1e-4) - grid.c0) / grid.dc), 0, lim).astype(np.int64)
     root = np.where(st == 0, idx.astype(np.int64), lim - 1)
     if split:
-        bis = np.ceil(np.log2(np.maximum(npf, 1)))
-        search = np.where(npf >= 1, 1 + np.where(root < npf, bis, 0), 0)
+        search = split_search_evals(models, npf, root)
     else:
         steps = np.where(npf >= 2, 1 + np.ceil(np.log(np.maximum(npf, 2)) / np.log(3.0)), 1)
         search = np.where(npf >= 1, 2 * steps, 0)
@@ -702,7 +738,7 @@ def measure(args, torch, masw, workload, n_models, rank, world, with_plain=True)
             "roofline": roofline, "plan": plan.as_dict(), "plain": plain, "e2e": e2e,
             "found_fraction": float(np.mean(st == 0)),
             "launches_per_step": {0: 2, 1: 5,
-                                  2: (6, 7, 11)[plan.count_split]}[plan.precision]}
+                                  2: (6, 8, 12)[plan.count_split]}[plan.precision]}
 
 
 def run_extras(args, masw, torch):
@@ -859,12 +895,14 @@ def extra_higher_modes(masw, torch):
 
 def extra_leaky(masw, torch):
     """Leaky continuation: the whole grid with the sign of Re det K. Besides
-    the host-output rate, an FP64 roofline of the continuation kernel: the
+    the host-output rate, a roofline of the continuation kernel: the
     layer-evaluations the linear scan needs for the items the batch scan
     leaves without a change (from one point below the scan limit to the
-    change, or to the end of the grid) x F_LAYER_FLOPS, over the kernel's
-    device time (CUDA events around the device-output call on the batch
-    stream, less the batch scan's own event time)."""
+    change, or to the end of the grid), over the kernel's device time (CUDA
+    events around the device-output call on the batch stream, less the batch
+    scan's own event time), against the FP64 pipe's ceiling for the kernel's
+    FP64 instructions per layer-evaluation (the element runs in double-float
+    on the FP32 pipe); both in F_LAYER_FLOPS per layer-evaluation."""
     out = {}
     lm, lg = W.leaky_batch()
     n_rec = lm.n_layers.astype(np.int64) + 1
@@ -900,7 +938,10 @@ def extra_leaky(masw, torch):
     evals = float(np.sum(((last - start + 2) * n_rec[item_model])[cont]))
     k_ms = float(np.median(kms))
     achieved = evals * F_LAYER_FLOPS / (k_ms * 1e-3) / 1e12
-    peak = FP64_DFMA_PER_CLK_SM * 2.0 * masw.sm_count() * SM_MAX_MHZ * 1e6 / 1e12
+    sms = masw.sm_count()
+    ceiling = FP64_WARP_INSTR_PER_CLK_SM * sms * SM_MAX_MHZ * 1e6 / LEAKY_FP64_WARP_INSTR_PER_LAYER_EVAL
+    peak = ceiling * F_LAYER_FLOPS / 1e12
+    peak64 = FP64_DFMA_PER_CLK_SM * 2.0 * sms * SM_MAX_MHZ * 1e6 / 1e12
     out["leaky"] = {"workload": lm.meta["workload"] + ", host outputs",
                     "curves_per_s": lm.n_models / min(lms), "ms": 1e3 * min(lms),
                     "batch_scan_ms": float(np.median(lscan)),
@@ -909,8 +950,17 @@ def extra_leaky(masw, torch):
                     "continued_fraction": float(np.mean(cont)),
                     "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved,
                                  "peak": peak, "frac": achieved / peak,
-                                 "kernel": "leaky_scan64_kernel (FP64 pipe)",
-                                 "layer_evals": evals, "flops_per_layer_eval": F_LAYER_FLOPS}}
+                                 "kernel": "leaky_scan64_kernel (element in double-float on the "
+                                           "FP32 pipe; Schur step and half-space pivot on the "
+                                           "FP64 pipe, the bound)",
+                                 "peak_source": "derived: FP64 pipe at 2 DFMA/clk/SM x SMs x "
+                                                "2070 MHz / 32 = warp instructions per second, / "
+                                                f"{LEAKY_FP64_WARP_INSTR_PER_LAYER_EVAL:.3f} FP64 "
+                                                "warp instructions per layer-evaluation (ncu) x "
+                                                "149.1 flops",
+                                 "layer_evals": evals, "layer_evals_per_s": evals / (k_ms * 1e-3),
+                                 "flops_per_layer_eval": F_LAYER_FLOPS,
+                                 "frac_of_fp64_peak": achieved / peak64}}
     return out
 
 

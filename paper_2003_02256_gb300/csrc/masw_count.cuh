@@ -110,6 +110,41 @@ __device__ __forceinline__ int count_search_single(const float* __restrict__ lay
     return hi;
 }
 
+// The search stage for an item whose neighbours at smaller and larger
+// wavelengths of the same model have been searched (indices na, nb; < 1: a
+// neighbour without one, and the item takes count_search_single). A
+// fundamental mode's phase velocity changes little between adjacent
+// wavelengths, so the first nonzero count usually lies in
+// (min(na, nb) - 1, max(na, nb)]: the count at the bracket's ends confirms
+// it, and bisection closes it. When the count at the upper end is 0 the
+// change lies above it (up to the top of the range), when the count at the
+// lower end is nonzero below it: the result is the same first nonzero point
+// of a non-decreasing count, in fewer evaluations when the guess holds.
+__device__ __forceinline__ int count_search_bracket(const float* __restrict__ lay32, int N,
+                                                    double k, double c0, double dc, int npf,
+                                                    int na, int nb) {
+    if (npf < 1) return -1;
+    if (na < 1 || nb < 1) return count_search_single(lay32, N, k, c0, dc, npf);
+    const float kf = (float)k, c0f = (float)c0, dcf = (float)dc;
+    int hi = min(max(na, nb), npf - 1);
+    int lo = min(min(na, nb) - 1, hi - 1);  // >= -1
+    if (inertia_f(lay32, N, kf, fmaf((float)hi, dcf, c0f)) < 1) {
+        if (hi == npf - 1) return -1;  // no change inside the range
+        lo = hi;
+        hi = npf - 1;
+        if (inertia_f(lay32, N, kf, fmaf((float)hi, dcf, c0f)) < 1) return -1;
+    } else if (lo >= 0 && inertia_f(lay32, N, kf, fmaf((float)lo, dcf, c0f)) >= 1) {
+        hi = lo;
+        lo = -1;
+    }
+    while (hi - lo > 1) {
+        const int mid = lo + ((hi - lo) >> 1);
+        if (inertia_f(lay32, N, kf, fmaf((float)mid, dcf, c0f)) >= 1) hi = mid;
+        else lo = mid;
+    }
+    return hi;
+}
+
 // The certificate stage for the search's index n (count_search_pair or
 // count_search_single) in the
 // pole-free range [0, npf). Both lanes of the pair (lane bit 0 = half, `pair`

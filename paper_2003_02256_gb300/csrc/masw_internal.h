@@ -25,7 +25,15 @@ struct DevBatch {
     int32_t n_c;
     int32_t route;  // test routing (masw_set_route): 0 normal, 1..3 force the slower paths,
                     // 4 displaces the FP32-located higher-mode events
+    // the split counting search's two passes (or nullptr: one pass): item ids,
+    // first the n_anchor items searched in full (every SEARCH_STRIDE-th item of
+    // a model and its last), then the others, bracketed by those neighbours
+    const int32_t* search_order = nullptr;
+    int32_t n_anchor = 0;
 };
+
+// Items of a model between two fully searched ones in the split search.
+constexpr int SEARCH_STRIDE = 4;
 
 // The cumulative level 0..3 of a test routing value (route 4 has none).
 __host__ __device__ inline int route_level(int route) { return route <= 3 ? route : 0; }

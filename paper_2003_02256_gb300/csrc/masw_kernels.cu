@@ -527,24 +527,34 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
 // count_split: the search ran before in count_search_kernel, its index in
 // n32), 640 for B = 64 (96 registers, fewer spills), so that the block size
 // also picks among three register budgets.
-// Search stage alone (count_search_single, one thread per item): the index
-// goes to nsearch[item], for count_certify_kernel<B, true>. With an early
-// list (plan count_split 2) the items the certificate would only pass on to
+// Search stage alone (count_search_single or count_search_bracket, one
+// thread per item): the index goes to nsearch[item], for
+// count_certify_kernel<B, true>. With an early list (plan count_split 2) the items the certificate would only pass on to
 // the linear FP32 scan (no count change inside the pole-free range, a mode
 // below V[0], test routing 1..3) go straight to that list with their start in
 // n32, and nsearch gets 0 for them and for models without a scan range
 // (results written here), so that the fallback chain can run on a second
 // stream beside the certificate. Natural item order: a warp's 32 items share
 // a model or two and have adjacent wavelengths, so their branches agree.
-template <int B>
+// PASS 0: the items [item_begin, item_end) in natural order; 1: the anchor
+// items of b.search_order (every SEARCH_STRIDE-th wavelength of a model and
+// its last), each searched in full; 2: the other items, each searched
+// between its two anchors' indices (count_search_bracket), after pass 1.
+template <int B, int PASS>
 __global__ void __launch_bounds__(B) count_search_kernel(DevBatch b,
                                                          const float* __restrict__ layers32,
-                                                         int32_t* __restrict__ nsearch,
-                                                         ScanOut o, int32_t* __restrict__ n32,
+                                                         int32_t* nsearch, ScanOut o, int32_t* n32,
                                                          int32_t* early, int32_t* n_early,
                                                          int item_begin, int item_end) {
-    const int item = item_begin + blockIdx.x * blockDim.x + threadIdx.x;
-    if (item >= item_end) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int item;
+    if (PASS == 0) {
+        item = item_begin + t;
+        if (item >= item_end) return;
+    } else {
+        if (t >= (PASS == 1 ? b.n_anchor : b.n_items - b.n_anchor)) return;
+        item = b.search_order[PASS == 1 ? t : b.n_anchor + t];
+    }
     const int m = b.item_model[item];
     const int lo_rec = b.model_loff[m];
     const int N = b.model_loff[m + 1] - lo_rec - 1;
@@ -561,7 +571,15 @@ __global__ void __launch_bounds__(B) count_search_kernel(DevBatch b,
     const float* lay32 = layers32 + (size_t)lo_rec * LAYER_STRIDE32;
     const double k = b.k[item];
     const int npf = pole_free_points_f(lay32, N, (float)k, (float)b.c0, (float)b.dc, nlim);
-    const int n = count_search_single(lay32, N, k, b.c0, b.dc, npf);
+    int n;
+    if (PASS == 2) {
+        const int w0 = b.model_woff[m], w1 = b.model_woff[m + 1];
+        const int ja = w0 + ((item - w0) / SEARCH_STRIDE) * SEARCH_STRIDE;
+        const int jb = min(ja + SEARCH_STRIDE, w1 - 1);
+        n = count_search_bracket(lay32, N, k, b.c0, b.dc, npf, nsearch[ja], nsearch[jb]);
+    } else {
+        n = count_search_single(lay32, N, k, b.c0, b.dc, npf);
+    }
     if (!early || (n >= 1 && route_level(b.route) < 1)) {
         nsearch[item] = n;
         return;
@@ -789,9 +807,22 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
         int32_t* const side_counters = counters + SCAN_COUNTERS;
         int32_t* const nsearch = overlap ? side->nsearch : n32;
         if (p.count_split) {
-            count_search_kernel<128><<<(n + 127) / 128, 128, 0, s>>>(
-                b, layers32, nsearch, o, n32, overlap ? side->fallback : nullptr,
-                overlap ? side_counters + 3 : nullptr, item_begin, item_end);
+            int32_t* const el = overlap ? side->fallback : nullptr;
+            int32_t* const nel = overlap ? side_counters + 3 : nullptr;
+            if (b.search_order && item_begin == 0 && item_end == b.n_items) {
+                // anchors first, then the items between them
+                const int na = b.n_anchor, nr = b.n_items - b.n_anchor;
+                if (na > 0)
+                    count_search_kernel<128, 1><<<(na + 127) / 128, 128, 0, s>>>(
+                        b, layers32, nsearch, o, n32, el, nel, item_begin, item_end);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                if (nr > 0)
+                    count_search_kernel<128, 2><<<(nr + 127) / 128, 128, 0, s>>>(
+                        b, layers32, nsearch, o, n32, el, nel, item_begin, item_end);
+            } else {
+                count_search_kernel<128, 0><<<(n + 127) / 128, 128, 0, s>>>(
+                    b, layers32, nsearch, o, n32, el, nel, item_begin, item_end);
+            }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if (phase_ev && (e = cudaEventRecord(phase_ev[2], s)) != cudaSuccess) return e;
         }
