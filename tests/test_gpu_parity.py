@@ -603,11 +603,11 @@ def test_extreme_models_two_precision_equals_fp64_scan(masw, oracle_lib, seed):
     with masw.Batch(m, g) as bt:
         bt.set_plan(precision=0)
         ref = bt.dispersion()
-        for p in (1, 2):
-            bt.set_plan(precision=p)
+        for p, split in ((1, 0), (2, 0), (2, 1), (2, 2)):
+            bt.set_plan(precision=p, count_split=split)
             got = bt.dispersion()
-            assert np.array_equal(got[1], ref[1]), (p, np.nonzero(got[1] != ref[1])[0][:10])
-            assert np.array_equal(got[2], ref[2]), p
+            assert np.array_equal(got[1], ref[1]), (p, split, np.nonzero(got[1] != ref[1])[0][:10])
+            assert np.array_equal(got[2], ref[2]), (p, split)
         fb = bt.last_scan_fallback()
     assert (ref[2] == 0).mean() > 0.5 and fb >= 0
     items = np.random.default_rng(seed).choice(oracle_domain(oracle_lib, m), size=48,
@@ -623,8 +623,9 @@ def test_forced_routes_give_the_fp64_scan(masw, route):
     rarely reach: the linear FP32 scan from V[0] (1), the FP64 mode-count
     search after a failed check (2), the FP64 scan from V[0] (3), higher-mode
     events located off by -7..+3 points before their certificate (4). Every
-    plan still reports the pure FP64 scan's indices, on uniform, ragged and
-    extreme models, and the higher modes match too."""
+    plan (the counting plan fused, split and with its second stream) still
+    reports the pure FP64 scan's indices, on uniform, ragged and extreme
+    models, and the higher modes match too."""
     cases = [W.uniform_batch(n_models=32, n_lambda=40), W.ragged_batch(n_models=48),
              W.extreme_batch(n_models=64, seed=W.SEED + 11)]
     for m, g in cases:
@@ -633,10 +634,12 @@ def test_forced_routes_give_the_fp64_scan(masw, route):
             ref = b.dispersion()
             ref_ch = b.changes(3)
             b.set_route(route)
-            for p in (1, 2):
-                b.set_plan(precision=p)
+            # precision 2 in each form: fused, split search, split with the second stream
+            for p, split in ((1, 0), (2, 0), (2, 1), (2, 2)):
+                b.set_plan(precision=p, count_split=split)
                 got = b.dispersion()
-                assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2]), (route, p)
+                assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2]), \
+                    (route, p, split)
             ch = b.changes(3)
             assert all(np.array_equal(x, y) for x, y in zip(ch[1:], ref_ch[1:])), route
             if route == 3:
