@@ -51,6 +51,7 @@ struct masw_batch {
     std::vector<double> lambda, kvec;
     std::vector<int32_t> order_sorted, order_natural;
     std::vector<int32_t> search_order;  // anchors of the split search, then the others
+    std::vector<int32_t> layer_order;   // items by model, models ordered by layer count
     int32_t n_anchor = 0;
     std::vector<int64_t> grad_off;
 
@@ -63,6 +64,7 @@ struct masw_batch {
     int32_t* d_order_sorted = nullptr;
     int32_t* d_order_natural = nullptr;
     int32_t* d_search_order = nullptr;
+    int32_t* d_layer_order = nullptr;
     int64_t* d_grad_off = nullptr;
     int32_t* d_counter = nullptr;
     double* d_ct = nullptr;
@@ -129,6 +131,7 @@ struct masw_batch {
         b.item_model = d_item_model;
         b.order = ordered ? d_order_sorted : d_order_natural;
         b.search_order = d_search_order;
+        b.layer_order = d_layer_order;
         b.n_anchor = n_anchor;
         b.grad_off = d_grad_off;
         b.n_models = n_models;
@@ -334,6 +337,7 @@ static void free_batch(masw_batch* B) {
     if (B->side) cudaStreamDestroy(B->side);
     void* ptrs[] = {B->d_layers, B->d_loff,  B->d_woff,  B->d_nlim,   B->d_k,
                     B->d_item_model, B->d_order_sorted, B->d_order_natural, B->d_search_order,
+                    B->d_layer_order,
                     B->d_grad_off,
                     B->d_counter, B->d_ct, B->d_idx, B->d_status, B->d_croot, B->d_rows, B->d_bs,
                     B->d_dphi, B->d_ce, B->d_misfit, B->d_gb, B->d_gh, B->d_layers32, B->d_layers_df,
@@ -567,17 +571,28 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
     B->order_natural.resize(nw);
     std::iota(B->order_natural.begin(), B->order_natural.end(), 0);
     // the split search: every SEARCH_STRIDE-th wavelength of a model and its
-    // last are searched in full first, the items between them after
+    // last are searched in full first, the items between them after. Both
+    // lists run model by model with the models ordered by their layer count,
+    // so that a warp's items (consecutive wavelengths of one model, or of
+    // models with as many layers) take the same number of layer steps.
+    std::vector<int32_t> by_layers(B->n_models);
+    std::iota(by_layers.begin(), by_layers.end(), 0);
+    std::stable_sort(by_layers.begin(), by_layers.end(),
+                     [&](int32_t a, int32_t b) { return B->n_layers[a] < B->n_layers[b]; });
+    auto anchor = [&](int32_t m, int32_t j) {
+        return (j - B->woff[m]) % SEARCH_STRIDE == 0 || j == B->woff[m + 1] - 1;
+    };
     B->search_order.reserve(nw);
-    for (int32_t m = 0; m < B->n_models; ++m)
+    for (int32_t m : by_layers)
         for (int32_t j = B->woff[m]; j < B->woff[m + 1]; ++j)
-            if ((j - B->woff[m]) % SEARCH_STRIDE == 0 || j == B->woff[m + 1] - 1)
-                B->search_order.push_back(j);
+            if (anchor(m, j)) B->search_order.push_back(j);
     B->n_anchor = (int32_t)B->search_order.size();
-    for (int32_t m = 0; m < B->n_models; ++m)
+    for (int32_t m : by_layers)
         for (int32_t j = B->woff[m]; j < B->woff[m + 1]; ++j)
-            if (!((j - B->woff[m]) % SEARCH_STRIDE == 0 || j == B->woff[m + 1] - 1))
-                B->search_order.push_back(j);
+            if (!anchor(m, j)) B->search_order.push_back(j);
+    B->layer_order.reserve(nw);
+    for (int32_t m : by_layers)
+        for (int32_t j = B->woff[m]; j < B->woff[m + 1]; ++j) B->layer_order.push_back(j);
     B->order_sorted = B->order_natural;
     std::stable_sort(B->order_sorted.begin(), B->order_sorted.end(),
                      [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
@@ -597,7 +612,7 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
         dev_alloc(&B->d_woff, B->n_models + 1) || dev_alloc(&B->d_nlim, B->n_models) ||
         dev_alloc(&B->d_k, nw) || dev_alloc(&B->d_item_model, nw) ||
         dev_alloc(&B->d_order_sorted, nw) || dev_alloc(&B->d_order_natural, nw) ||
-        dev_alloc(&B->d_search_order, nw) ||
+        dev_alloc(&B->d_search_order, nw) || dev_alloc(&B->d_layer_order, nw) ||
         dev_alloc(&B->d_grad_off, nw + 1) || dev_alloc(&B->d_counter, 1) ||
         dev_alloc(&B->d_ct, nw) || dev_alloc(&B->d_idx, nw) || dev_alloc(&B->d_status, nw) ||
         dev_alloc(&B->d_layers32, rec32.size()) || dev_alloc(&B->d_layers_df, recdf.size()) ||
@@ -624,6 +639,7 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
     if (e == cudaSuccess) e = up(B->d_order_sorted, B->order_sorted.data(), nw * 4);
     if (e == cudaSuccess) e = up(B->d_order_natural, B->order_natural.data(), nw * 4);
     if (e == cudaSuccess) e = up(B->d_search_order, B->search_order.data(), nw * 4);
+    if (e == cudaSuccess) e = up(B->d_layer_order, B->layer_order.data(), nw * 4);
     if (e == cudaSuccess) e = up(B->d_grad_off, B->grad_off.data(), (nw + 1) * 8);
     if (e == cudaSuccess) e = cudaEventCreate(&B->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&B->ev1);

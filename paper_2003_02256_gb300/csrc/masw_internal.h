@@ -30,6 +30,9 @@ struct DevBatch {
     // a model and its last), then the others, bracketed by those neighbours
     const int32_t* search_order = nullptr;
     int32_t n_anchor = 0;
+    // all items, model by model with the models ordered by layer count (the
+    // split certificate's order over a whole batch), or nullptr
+    const int32_t* layer_order = nullptr;
 };
 
 // Items of a model between two fully searched ones in the split search.

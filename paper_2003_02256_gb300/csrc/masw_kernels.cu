@@ -598,8 +598,12 @@ __global__ void __launch_bounds__(B, (B == 256 ? 3 : (B == 64 && SPLIT ? 10 : 89
                          int32_t* n_search, int32_t* fallback, int32_t* n_fallback,
                          int item_begin, int item_end) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int item = item_begin + (t >> 1);
+    int item = item_begin + (t >> 1);
     if (item >= item_end) return;  // both lanes of a pair leave together
+    // a whole batch in the order by layer count (a warp's pairs, one model's
+    // or like models' items, walk the same number of layers)
+    if (SPLIT && b.layer_order && item_begin == 0 && item_end == b.n_items)
+        item = b.layer_order[item];
     // (early list: the search kernel has passed the item on, or written it)
     if (SPLIT && early && nsearch[item] < 1) return;
     const int half = t & 1;
