@@ -103,19 +103,19 @@ SM_MAX_MHZ = 2070.0
 # read once, the outputs stay in L2. Scaled by the models of a launch; None
 # where no capture of the current kernel exists.
 # uniform: 4.46 MB for the 1024-model launch of count_certify_kernel<128,
-# true>; ragged: 10.63 MB for the launch over the first 2048 models (429,978
+# true>; ragged: 12.46 MB for the launch over the first 2048 models (429,978
 # items), scaled by the models to the 8192-model launch (its algorithmic
 # bytes -- records, wavenumbers, item tables, the search's indices -- are
 # 4.024 times the 2048-model launch's).
-CERTIFY_DRAM_BYTES = {"uniform": (4.459008e6, 1024), "ragged": (10.631168e6, 2048)}
+CERTIFY_DRAM_BYTES = {"uniform": (4.459008e6, 1024), "ragged": (12.464128e6, 2048)}
 # Warp instructions a kernel issues per layer-evaluation (ncu
 # smsp__inst_executed.sum of one launch / its layer-evaluations counted as in
 # counting_evals), by workload (ragged: the 2048-model launch): the
 # certificate kernel per certificate layer-evaluation, the search kernel per
 # FP32 one. A kernel's ceiling is the SM's issue rate, ISSUE_PER_CLK_SM warp
 # instructions per clock, over this count.
-CERTIFY_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 50.67, "ragged": 53.29}
-SEARCH_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 5.237, "ragged": 5.535}
+CERTIFY_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 50.82, "ragged": 52.59}
+SEARCH_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 6.48, "ragged": 6.43}
 ISSUE_PER_CLK_SM = 4
 # FP64-pipe warp instructions per layer-evaluation of the leaky continuation
 # over the double-float element (ncu sm__inst_executed_pipe_fp64.sum of the

@@ -590,9 +590,12 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
     for (int32_t m : by_layers)
         for (int32_t j = B->woff[m]; j < B->woff[m + 1]; ++j)
             if (!anchor(m, j)) B->search_order.push_back(j);
-    B->layer_order.reserve(nw);
-    for (int32_t m : by_layers)
-        for (int32_t j = B->woff[m]; j < B->woff[m + 1]; ++j) B->layer_order.push_back(j);
+    // (left out when the models come in that order already)
+    if (!std::is_sorted(B->n_layers.begin(), B->n_layers.end())) {
+        B->layer_order.reserve(nw);
+        for (int32_t m : by_layers)
+            for (int32_t j = B->woff[m]; j < B->woff[m + 1]; ++j) B->layer_order.push_back(j);
+    }
     B->order_sorted = B->order_natural;
     std::stable_sort(B->order_sorted.begin(), B->order_sorted.end(),
                      [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
@@ -612,7 +615,8 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
         dev_alloc(&B->d_woff, B->n_models + 1) || dev_alloc(&B->d_nlim, B->n_models) ||
         dev_alloc(&B->d_k, nw) || dev_alloc(&B->d_item_model, nw) ||
         dev_alloc(&B->d_order_sorted, nw) || dev_alloc(&B->d_order_natural, nw) ||
-        dev_alloc(&B->d_search_order, nw) || dev_alloc(&B->d_layer_order, nw) ||
+        dev_alloc(&B->d_search_order, nw) ||
+        (!B->layer_order.empty() && dev_alloc(&B->d_layer_order, nw)) ||
         dev_alloc(&B->d_grad_off, nw + 1) || dev_alloc(&B->d_counter, 1) ||
         dev_alloc(&B->d_ct, nw) || dev_alloc(&B->d_idx, nw) || dev_alloc(&B->d_status, nw) ||
         dev_alloc(&B->d_layers32, rec32.size()) || dev_alloc(&B->d_layers_df, recdf.size()) ||
@@ -639,7 +643,8 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
     if (e == cudaSuccess) e = up(B->d_order_sorted, B->order_sorted.data(), nw * 4);
     if (e == cudaSuccess) e = up(B->d_order_natural, B->order_natural.data(), nw * 4);
     if (e == cudaSuccess) e = up(B->d_search_order, B->search_order.data(), nw * 4);
-    if (e == cudaSuccess) e = up(B->d_layer_order, B->layer_order.data(), nw * 4);
+    if (e == cudaSuccess && B->d_layer_order)
+        e = up(B->d_layer_order, B->layer_order.data(), nw * 4);
     if (e == cudaSuccess) e = up(B->d_grad_off, B->grad_off.data(), (nw + 1) * 8);
     if (e == cudaSuccess) e = cudaEventCreate(&B->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&B->ev1);
