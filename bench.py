@@ -1025,7 +1025,7 @@ def extra_noalloc(masw, torch):
                         "noalloc_ms": t_na, "noalloc_curves_per_s": m.n_models / (t_na * 1e-3),
                         "dispersion_ms": t_b, "dispersion_curves_per_s": m.n_models / (t_b * 1e-3),
                         "identical_indices": same,
-                        "noalloc_plan": "plain FP64 scan, one warp per item, natural order"}}
+                        "noalloc_plan": "counting plan, fused search and certificate"}}
 
 
 def plain_per_request(masw, reqs, arrival_s, grid, limit_s=10.0):

@@ -524,8 +524,9 @@ int masw_server_run_trace(masw_server* server, int32_t n_requests, const int32_t
  * allocation after start-up), so masw_model_batch_create, which allocates a
  * device copy of the batch, is not open to them. This call allocates nothing,
  * neither on the device nor on the host: everything derived from the inputs
- * (layer records, offsets, scan limits, wavenumbers, item order and the
- * work-queue counter) goes to one fixed array of MASW_NOALLOC_SCRATCH_BYTES
+ * (layer records in FP64, FP32 and double-float, offsets, scan limits,
+ * wavenumbers, item order, the counting search's per-item lists and
+ * counters) goes to one fixed array of MASW_NOALLOC_SCRATCH_BYTES (5.3 MiB)
  * in device memory that every GPU loading the library holds until exit.
  *  - models: like masw_model_batch_create (host or device arrays, mem_space);
  *    grid as there. Every input array must lie in the space mem_space
@@ -533,9 +534,9 @@ int masw_server_run_trace(masw_server* server, int32_t n_requests, const int32_t
  *    MASW_HOST); a mixed call returns MASW_EINVAL before any copy or launch.
  *    ct, ct_idx, status: DEVICE buffers of sum(n_lambda) entries, same
  *    meaning as masw_dispersion; results equal its results.
- *  - It runs the plain FP64 scan (one warp per item, 32 test velocities per
- *    chunk, items in their natural order), not masw_dispersion's default
- *    counting plan: the same indices, at the FP64 scan's lower throughput.
+ *  - It runs masw_dispersion's default counting plan in the form that plan
+ *    takes for batches of this size (the fused search and certificate, then
+ *    the fallback chain), with the same indices.
  *  - Limits: n_models <= MASW_NOALLOC_MAX_MODELS, sum(N_m + 1) <=
  *    MASW_NOALLOC_MAX_RECORDS, sum(n_lambda) <= MASW_NOALLOC_MAX_ITEMS;
  *    beyond them the call returns MASW_ETOOBIG and touches nothing.
@@ -552,7 +553,7 @@ int masw_server_run_trace(masw_server* server, int32_t n_requests, const int32_t
 #define MASW_NOALLOC_MAX_MODELS 1024
 #define MASW_NOALLOC_MAX_RECORDS 16384
 #define MASW_NOALLOC_MAX_ITEMS 65536
-#define MASW_NOALLOC_SCRATCH_BYTES 3159040
+#define MASW_NOALLOC_SCRATCH_BYTES 5518592
 int masw_dispersion_noalloc(const masw_models_desc* models, const masw_grid* grid,
                             void* cuda_stream, double* ct, int32_t* ct_idx, int32_t* status);
 

@@ -6,10 +6,12 @@
 // services that forbid allocation after start-up, and embedders that only
 // hand out pre-allocated buffers. masw_model_batch_create does allocate
 // (it owns a device copy of the batch). This entry point instead keeps
-// everything it derives from the inputs -- layer records, offsets, scan
-// limits, wavenumbers, the item order and the work-queue counter -- in one
-// file-scope device array of fixed size, and writes the results straight
-// into the caller's output buffers.
+// everything it derives from the inputs -- layer records (FP64, FP32 and
+// double-float), offsets, scan limits, wavenumbers, the item order, the
+// counting search's per-item lists and their counters -- in one file-scope
+// device array of fixed size, and writes the results straight into the
+// caller's output buffers. It runs the batch path's default counting plan in
+// its fused form (the form that plan takes for batches of this size).
 //
 // The array lives for the whole process on every device that loads the
 // library. Host code must not hand its symbol to a kernel (on the host the
@@ -22,7 +24,9 @@
 
 #include "../../include/masw.h"
 #include "masw_device.cuh"
+#include "masw_df.cuh"
 #include "masw_internal.h"
+#include "masw_screen.cuh"
 
 using namespace masw;
 
@@ -44,7 +48,14 @@ constexpr size_t OFF_NLIM = align256(OFF_WOFF + SZ_MODELS1_I32);
 constexpr size_t OFF_STAGE = align256(OFF_NLIM + SZ_MODELS1_I32);  // host inputs: h, alpha, beta, rho
 constexpr size_t SZ_STAGE_LAYERS = (size_t)MASW_NOALLOC_MAX_RECORDS * sizeof(double);
 constexpr size_t OFF_STAGE_LAMBDA = align256(OFF_STAGE + 4 * SZ_STAGE_LAYERS);
-constexpr size_t OFF_COUNTER = align256(OFF_STAGE_LAMBDA + SZ_K);
+constexpr size_t OFF_REC32 = align256(OFF_STAGE_LAMBDA + SZ_K);
+constexpr size_t SZ_REC32 = (size_t)MASW_NOALLOC_MAX_RECORDS * LAYER_STRIDE32 * sizeof(float);
+constexpr size_t OFF_RECDF = align256(OFF_REC32 + SZ_REC32);
+constexpr size_t SZ_RECDF = (size_t)MASW_NOALLOC_MAX_RECORDS * LAYER_STRIDE_DF * sizeof(float);
+constexpr size_t OFF_N32 = align256(OFF_RECDF + SZ_RECDF);  // then search, re-scan, fallback lists
+constexpr size_t OFF_LISTS = align256(OFF_N32 + SZ_ITEMS_I32);
+constexpr size_t OFF_SCAN_COUNTERS = align256(OFF_LISTS + 3 * SZ_ITEMS_I32);
+constexpr size_t OFF_COUNTER = align256(OFF_SCAN_COUNTERS + 2 * SCAN_COUNTERS * sizeof(int32_t));
 constexpr size_t OFF_ERROR = OFF_COUNTER + 64;
 constexpr size_t SCRATCH_BYTES = align256(OFF_ERROR + 64);
 static_assert(SCRATCH_BYTES == MASW_NOALLOC_SCRATCH_BYTES, "scratch size must match masw.h");
@@ -115,9 +126,10 @@ __global__ void noalloc_prep_kernel(int n_models, const int32_t* __restrict__ lo
                                     const int32_t* __restrict__ woff, const double* __restrict__ h,
                                     const double* __restrict__ alpha, const double* __restrict__ beta,
                                     const double* __restrict__ rho, const double* __restrict__ lam,
-                                    masw_grid grid, double* records, double* kvec,
-                                    int32_t* item_model, int32_t* order, int32_t* nlim,
-                                    int32_t* counter, int32_t* err) {
+                                    masw_grid grid, double* records, float* records32,
+                                    float* records_df, double* kvec, int32_t* item_model,
+                                    int32_t* order, int32_t* nlim, int32_t* counter,
+                                    int32_t* err) {
     const int n_rec = loff[n_models];
     const int n_items = woff[n_models];
     const int stride = gridDim.x * blockDim.x;
@@ -143,6 +155,21 @@ __global__ void noalloc_prep_kernel(int n_models, const int32_t* __restrict__ lo
             L[L_BETA] = b;
             L[L_RATIO] = a / b;
             L[L_IRHO] = 1.0 / r;
+        }
+        // the FP32 records of the search (stiffnesses over the half-space's
+        // shear modulus) and the certificate's double-float records
+        const double mref = records[(size_t)(rec0 + N) * LAYER_STRIDE + L_MU];
+        for (int i = 0; i <= N; ++i) {
+            const double* L = records + (size_t)(rec0 + i) * LAYER_STRIDE;
+            float* F = records32 + (size_t)(rec0 + i) * LAYER_STRIDE32;
+            for (int q = 0; q < LAYER_STRIDE32; ++q) F[q] = 0.0f;
+            F[F_H] = (float)L[L_H];
+            F[F_MU] = (float)(L[L_MU] / mref);
+            F[F_RHO] = (float)(L[L_RHO] / mref);
+            F[F_IA2] = (float)L[L_IA2];
+            F[F_IB2] = (float)L[L_IB2];
+            F[F_DIB] = (float)(L[L_IB2] - L[L_IA2]);
+            df_record(L, records_df + (size_t)(rec0 + i) * LAYER_STRIDE_DF);
         }
         // grid points with V[n] < beta of the half-space
         double bhs = beta[rec0 + N];
@@ -219,6 +246,11 @@ extern "C" int masw_dispersion_noalloc(const masw_models_desc* md, const masw_gr
     if (rec - M > 0 && !md->h) return MASW_EINVAL;
 
     double* records = (double*)(base + OFF_RECORDS);
+    float* records32 = (float*)(base + OFF_REC32);
+    float* records_df = (float*)(base + OFF_RECDF);
+    int32_t* n32 = (int32_t*)(base + OFF_N32);
+    int32_t* lists = (int32_t*)(base + OFF_LISTS);
+    int32_t* scan_counters = (int32_t*)(base + OFF_SCAN_COUNTERS);
     double* kvec = (double*)(base + OFF_K);
     int32_t* item_model = (int32_t*)(base + OFF_ITEM_MODEL);
     int32_t* order = (int32_t*)(base + OFF_ORDER);
@@ -254,8 +286,8 @@ extern "C" int masw_dispersion_noalloc(const masw_models_desc* md, const masw_gr
         int threads = 128;
         int blocks = (M + threads - 1) / threads;
         noalloc_prep_kernel<<<blocks, threads, 0, s>>>(M, d_loff, d_woff, h, a, b, r, lam, *grid,
-                                                       records, kvec, item_model, order, d_nlim,
-                                                       counter, err);
+                                                       records, records32, records_df, kvec,
+                                                       item_model, order, d_nlim, counter, err);
         e = cudaGetLastError();
     }
     int32_t herr = 0;
@@ -278,7 +310,7 @@ extern "C" int masw_dispersion_noalloc(const masw_models_desc* md, const masw_gr
     }
     DevBatch d;
     d.layers = records;
-    d.layers_df = nullptr;
+    d.layers_df = records_df;
     d.model_loff = d_loff;
     d.model_nlim = d_nlim;
     d.model_woff = d_woff;
@@ -292,14 +324,21 @@ extern "C" int masw_dispersion_noalloc(const masw_models_desc* md, const masw_gr
     d.dc = grid->dc;
     d.n_c = grid->n_c;
     d.route = 0;
+    // the counting plan's fused form: search and certificate in one kernel,
+    // then the fallback chain over the lists in the scratch
     ScanPlan p;
     p.warps_per_block = 8;
-    p.cpl = 1;
-    p.blocks = 3 * sms;
+    p.cpl = 2;
+    p.blocks = 4 * sms;
     p.persistent = 1;
     p.stage_layers = max_n + 1 < 32 ? max_n + 1 : 32;
+    p.count_block = 128;
+    p.count_split = 0;
+    p.sms = sms;
     ScanOut o{ct, ct_idx, status};
-    e = launch_scan(d, o, p, counter, 0, (int)items, s);
+    e = launch_screen_scan(d, o, p, records32, n32, lists, lists + MASW_NOALLOC_MAX_ITEMS,
+                           lists + 2 * MASW_NOALLOC_MAX_ITEMS, scan_counters, 1, 0, (int)items, s,
+                           nullptr, nullptr);
     if (e != cudaSuccess) return MASW_ECUDA;
     return MASW_OK;
 }
