@@ -81,12 +81,18 @@ __device__ __forceinline__ double* slot_records(const SlotView& v, int s) {
 __device__ __forceinline__ float* slot_records32(const SlotView& v, int s) {
     return (float*)(v.region + (size_t)s * v.stride + 2 + (size_t)v.rmax * LAYER_STRIDE);
 }
+// the certificate's double-float records (LAYER_STRIDE_DF floats a record,
+// SLOT_DF doubles)
+constexpr int SLOT_DF = LAYER_STRIDE_DF / 2;
+__device__ __forceinline__ const float* slot_records_df(const SlotView& v, int s) {
+    return (const float*)(v.region + (size_t)s * v.stride + 2 + (size_t)v.rmax * (LAYER_STRIDE + 4));
+}
 __device__ __forceinline__ double* slot_k(const SlotView& v, int s) {
-    return v.region + (size_t)s * v.stride + 2 + (size_t)v.rmax * (LAYER_STRIDE + 4);
+    return v.region + (size_t)s * v.stride + 2 + (size_t)v.rmax * (LAYER_STRIDE + 4 + SLOT_DF);
 }
 __device__ __forceinline__ int32_t* slot_state(const SlotView& v, int s) {
-    return (int32_t*)(v.region + (size_t)s * v.stride + 2 + (size_t)v.rmax * (LAYER_STRIDE + 4) +
-                      v.imax);
+    return (int32_t*)(v.region + (size_t)s * v.stride + 2 +
+                      (size_t)v.rmax * (LAYER_STRIDE + 4 + SLOT_DF) + v.imax);
 }
 
 enum { PH_SCREEN = 0, PH_FP64 = 1 };
@@ -136,10 +142,12 @@ __device__ bool search_or_rescan(SlotView v, int item, int slot, const double* l
     if (p0) {
         P = *p0;
     } else {
-        eval_pair(nullptr, lay, N, k, c0, dc, 0, topp.T < 0 ? nlim - 1 : -1, half, pair, &P, &dummy);
+        eval_pair(slot_records_df(v, slot), lay, N, k, c0, dc, 0, topp.T < 0 ? nlim - 1 : -1, half,
+                  pair, &P, &dummy);
         if (topp.T < 0) topp = dummy;
     }
-    ModeSearch st = mode_search_init(nullptr, lay, N, k, c0, dc, nlim - 1, half, pair, P, topp);
+    ModeSearch st = mode_search_init(slot_records_df(v, slot), lay, N, k, c0, dc, nlim - 1, half,
+                                     pair, P, topp);
     int d = 0;
     const int n = next_change(st, &d);
     const bool bad = st.bad || v.route >= 3;  // (test routing 3: the FP64 scan for every item)
@@ -185,7 +193,8 @@ __global__ void __launch_bounds__(128, 7) serve_count_kernel(SlotView v, const i
     const double* lay = slot_records(v, slot);
     const double k = slot_k(v, slot)[j];
     PairCount r =
-        count_certify_pair(slot_records32(v, slot), nullptr, lay, N, k, c0, dc, nlim, half, pair);
+        count_certify_pair(slot_records32(v, slot), slot_records_df(v, slot), lay, N, k, c0, dc,
+                           nlim, half, pair);
     if (v.route >= 1) r = PairCount{-1, -1, 0};  // test routing: the linear screen from V[0]
     if (r.cert >= 1) {
         if (!half) finish_item(v, item, slot, r.cert, c0, dc);
@@ -321,8 +330,9 @@ __global__ void __launch_bounds__(128) serve_check_kernel(SlotView v,
     const double k = slot_k(v, slot)[j];
     const int n = slot_state(v, slot)[4 * j + 3];  // screen index (-2: none below the limit)
     TPoint p0, pa, pb{-1, -1, 0}, unused;
-    eval_pair(nullptr, lay, N, k, c0, dc, 0, n >= 1 ? n - 1 : nlim - 1, half, pair, &p0, &pa);
-    if (n >= 1) eval_pair(nullptr, lay, N, k, c0, dc, n, -1, half, pair, &pb, &unused);
+    const float* laydf = slot_records_df(v, slot);
+    eval_pair(laydf, lay, N, k, c0, dc, 0, n >= 1 ? n - 1 : nlim - 1, half, pair, &p0, &pa);
+    if (n >= 1) eval_pair(laydf, lay, N, k, c0, dc, n, -1, half, pair, &pb, &unused);
     if (v.route < 2 && mode_count_verified(n, p0.T, pa.T, pb.T)) {
         if (!half) finish_item(v, item, slot, n >= 1 ? n : -1, c0, dc);
         return;
@@ -338,7 +348,7 @@ double now_s() {
 
 int64_t request_bytes(int32_t n_layers, int32_t n_lambda) {
     // records + per-item k, scan state and results
-    return (int64_t)(n_layers + 1) * (LAYER_STRIDE * 8 + LAYER_STRIDE32 * 4) +
+    return (int64_t)(n_layers + 1) * (LAYER_STRIDE * 8 + LAYER_STRIDE32 * 4 + LAYER_STRIDE_DF * 4) +
            (int64_t)n_lambda * (8 + 16 + 16);
 }
 
@@ -591,7 +601,7 @@ int masw_server_create(const masw_grid* grid, const masw_server_config* cfg, voi
     S->stream = (cudaStream_t)cuda_stream;
     S->v.rmax = cfg->max_layers + 1;
     S->v.imax = cfg->max_lambda;
-    S->v.stride = 2 + (int64_t)S->v.rmax * (LAYER_STRIDE + 4) + 3 * (int64_t)S->v.imax;
+    S->v.stride = 2 + (int64_t)S->v.rmax * (LAYER_STRIDE + 4 + SLOT_DF) + 3 * (int64_t)S->v.imax;
     S->v.stride = (S->v.stride + 31) / 32 * 32;  // 256-byte aligned slots
     size_t slots = cfg->max_slots, items = (size_t)cap_items;
     // every slot's block at once, plus descriptors and item ids
@@ -726,7 +736,11 @@ static int server_submit(masw_server* S, int32_t n_layers, const double* h, cons
         F[F_DIB] = (float)(L[L_IB2] - L[L_IA2]);
         F[6] = F[7] = 0.0f;
     }
-    double* kk = rec + (size_t)S->v.rmax * (LAYER_STRIDE + 4);
+    // the certificate's double-float records
+    float* recdf = (float*)(rec + (size_t)S->v.rmax * (LAYER_STRIDE + 4));
+    for (int i = 0; i <= n_layers; ++i)
+        df_record(rec + (size_t)i * LAYER_STRIDE, recdf + (size_t)i * LAYER_STRIDE_DF);
+    double* kk = rec + (size_t)S->v.rmax * (LAYER_STRIDE + 4 + SLOT_DF);
     for (int j = 0; j < n_lambda; ++j) kk[j] = 2.0 * M_PI / lambda[j];
     int32_t* stt = (int32_t*)(kk + S->v.imax);
     std::memset(stt, 0, (size_t)n_lambda * 4 * sizeof(int32_t));
