@@ -117,14 +117,11 @@ CERTIFY_DRAM_BYTES = {"uniform": (4.459008e6, 1024), "ragged": (12.464128e6, 204
 CERTIFY_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 50.82, "ragged": 52.59}
 SEARCH_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 6.48, "ragged": 6.43}
 ISSUE_PER_CLK_SM = 4
-# FP64-pipe warp instructions per layer-evaluation of the leaky continuation
-# over the double-float element (ncu sm__inst_executed_pipe_fp64.sum of the
-# 256-model leaky batch's launch, 74.85 M, over its 50.68 M layer-evaluations
-# counted as in extra_leaky): the FP64 Schur step, the element's conversions
-# and the complex half-space pivot. ncu's 100 % of the FP64 pipe is 2 thread
-# DFMA per clock per SM, a warp instruction per 16 clocks.
-LEAKY_FP64_WARP_INSTR_PER_LAYER_EVAL = 74.85e6 / 50.68e6
-FP64_WARP_INSTR_PER_CLK_SM = FP64_DFMA_PER_CLK_SM / 32
+# Warp instructions per layer-evaluation of the leaky continuation's scan
+# kernel, element and Schur step in double-float (ncu smsp__inst_executed.sum
+# of the 256-model leaky batch's scan launch, 2,242.6 M, over its 50.68 M
+# layer-evaluations counted as in extra_leaky); its FP64 pipe is 31 % busy.
+LEAKY_WARP_INSTR_PER_LAYER_EVAL = 2242.64e6 / 50.68e6
 # DRAM bytes (read + write) of one scan launch per model, from the ncu capture
 # of the 64-model case (281.6 KB read, 0 written), scaled by the models of a
 # launch; traffic grows with the number of items.
@@ -900,9 +897,10 @@ def extra_leaky(masw, torch):
     leaves without a change (from one point below the scan limit to the
     change, or to the end of the grid), over the kernel's device time (CUDA
     events around the device-output call on the batch stream, less the batch
-    scan's own event time), against the FP64 pipe's ceiling for the kernel's
-    FP64 instructions per layer-evaluation (the element runs in double-float
-    on the FP32 pipe); both in F_LAYER_FLOPS per layer-evaluation."""
+    scan's own event time; the FP64 confirmation of each change and the
+    rescans included), against the issue ceiling of the scan kernel's
+    instruction mix (element and Schur step in double-float); both in
+    F_LAYER_FLOPS per layer-evaluation."""
     out = {}
     lm, lg = W.leaky_batch()
     n_rec = lm.n_layers.astype(np.int64) + 1
@@ -939,7 +937,7 @@ def extra_leaky(masw, torch):
     k_ms = float(np.median(kms))
     achieved = evals * F_LAYER_FLOPS / (k_ms * 1e-3) / 1e12
     sms = masw.sm_count()
-    ceiling = FP64_WARP_INSTR_PER_CLK_SM * sms * SM_MAX_MHZ * 1e6 / LEAKY_FP64_WARP_INSTR_PER_LAYER_EVAL
+    ceiling = ISSUE_PER_CLK_SM * sms * SM_MAX_MHZ * 1e6 / LEAKY_WARP_INSTR_PER_LAYER_EVAL
     peak = ceiling * F_LAYER_FLOPS / 1e12
     peak64 = FP64_DFMA_PER_CLK_SM * 2.0 * sms * SM_MAX_MHZ * 1e6 / 1e12
     out["leaky"] = {"workload": lm.meta["workload"] + ", host outputs",
@@ -950,14 +948,15 @@ def extra_leaky(masw, torch):
                     "continued_fraction": float(np.mean(cont)),
                     "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved,
                                  "peak": peak, "frac": achieved / peak,
-                                 "kernel": "leaky_scan64_kernel (element in double-float on the "
-                                           "FP32 pipe; Schur step and half-space pivot on the "
-                                           "FP64 pipe, the bound)",
-                                 "peak_source": "derived: FP64 pipe at 2 DFMA/clk/SM x SMs x "
-                                                "2070 MHz / 32 = warp instructions per second, / "
-                                                f"{LEAKY_FP64_WARP_INSTR_PER_LAYER_EVAL:.3f} FP64 "
-                                                "warp instructions per layer-evaluation (ncu) x "
-                                                "149.1 flops",
+                                 "kernel": "leaky_scan64_kernel (element and Schur step in "
+                                           "double-float on the FP32 pipe, the complex half-space "
+                                           "pivot in FP64), then leaky_check_kernel (the FP64 "
+                                           "step at each change) and the rescans",
+                                 "peak_source": "derived: 4 warp instructions issued/clk/SM x SMs "
+                                                "x 2070 MHz / "
+                                                f"{LEAKY_WARP_INSTR_PER_LAYER_EVAL:.2f} warp "
+                                                "instructions per layer-evaluation (ncu) x 149.1 "
+                                                "flops",
                                  "layer_evals": evals, "layer_evals_per_s": evals / (k_ms * 1e-3),
                                  "flops_per_layer_eval": F_LAYER_FLOPS,
                                  "frac_of_fp64_peak": achieved / peak64}}

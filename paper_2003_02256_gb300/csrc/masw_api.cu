@@ -109,7 +109,7 @@ struct masw_batch {
     bool changes_counted = false;
     // leaky continuation (allocated on first use): per-item outputs, counter
     double* d_lk_ct = nullptr;
-    int32_t* d_lk_idx = nullptr;  // [n_items] idx, then [n_items] status, then counter
+    int32_t* d_lk_idx = nullptr;  // [n_items] idx, [n_items] status, then 2 n_items + 4 of work
     masw_plan plan{};
     int32_t route = 0;  // masw_set_route
     cudaGraphExec_t graph = nullptr;
@@ -823,7 +823,7 @@ int masw_dispersion_leaky(masw_batch* B, double* ct, int32_t* ct_idx, int32_t* s
     if (!B || (out_mem_space != MASW_HOST && out_mem_space != MASW_DEVICE)) return MASW_EINVAL;
     const size_t nw = B->n_items;
     if ((!B->d_lk_ct && dev_alloc(&B->d_lk_ct, std::max<size_t>(nw, 1))) ||
-        (!B->d_lk_idx && dev_alloc(&B->d_lk_idx, 2 * nw + 1)))
+        (!B->d_lk_idx && dev_alloc(&B->d_lk_idx, 4 * nw + 4)))
         return MASW_ENOMEM;
     // below the half-space shear speed: Algorithm 1 with the batch plan
     int rc0 = run_scan(B);

@@ -858,30 +858,55 @@ static __device__ __noinline__ int det_inertia_dd(const float* __restrict__ layd
 // with each finite layer's element in double-float, trigonometric branch
 // included (layer_numerators_dd<true>): above the half-space shear speed
 // most layers are above their own, and FP64's sincos there set the pace of
-// the FP64 form. The Schur step stays in FP64 (schur_layer; far above the
-// pole-free range the recurrence cancels next to the poles) and so does the
-// complex half-space pivot (leaky_halfspace_sign). 0 for an exact zero or a
-// failed rescaling, as det_sign_leaky. laydf: the N finite layers'
-// double-float records. Out of line: one copy for the continuation kernel.
-static __device__ __noinline__ int det_sign_leaky_df(const float* __restrict__ laydf,
-                                                     const double* __restrict__ lay, int N,
-                                                     double k, double c) {
+// the FP64 form. FP64STEP false: the Schur step in double-float too
+// (schur_layer_dd), so the FP64 pipe carries only the complex half-space
+// pivot (leaky_halfspace_sign); true: the Schur step in FP64 (schur_layer).
+// Far above the pole-free range the recurrence cancels next to the poles and
+// the double-float step's sign can differ from the FP64 step's there: the
+// continuation locates with the first and confirms each change with the
+// second. 0 for an exact zero or a failed rescaling, as det_sign_leaky.
+// laydf: the N finite layers' double-float records.
+template <bool FP64STEP>
+__device__ __forceinline__ int det_sign_leaky_t(const float* __restrict__ laydf,
+                                                const double* __restrict__ lay, int N, double k,
+                                                double c) {
     const double c2 = c * c;
     const DF kd = from_double(k), cd = from_double(c);
     const DF c2d = dmul(cd, cd);
     const DF ic2d = drcp(c2d);
+    HStateDD sd{dfc(0.0f), dfc(0.0f), dfc(0.0f), dfc(1.0f)};
     HState st{0.0, 0.0, 0.0, 1.0};
     int sg = 1;
     for (int j = 0; j < N; ++j) {
         const LayerNumDD nd = layer_numerators_dd<true>(laydf + j * LAYER_STRIDE_DF, kd, c2d, ic2d);
-        const LayerNum n{to_double(nd.Dh), to_double(nd.n00), to_double(nd.n01),
-                         to_double(nd.n11), to_double(nd.ce), to_double(nd.cf),
-                         to_double(nd.cg)};
         bool ok;
-        sg *= sgn(schur_layer(st, n, &ok));
+        if (FP64STEP) {
+            const LayerNum n{to_double(nd.Dh), to_double(nd.n00), to_double(nd.n01),
+                             to_double(nd.n11), to_double(nd.ce), to_double(nd.cf),
+                             to_double(nd.cg)};
+            sg *= sgn(schur_layer(st, n, &ok));
+        } else {
+            DF s00;
+            const DF det = schur_layer_dd(sd, nd, &ok, &s00);
+            sg *= det.hi > 0.0f ? 1 : (det.hi < 0.0f ? -1 : 0);
+        }
         if (!ok) return 0;
     }
+    if (!FP64STEP)
+        st = HState{to_double(sd.p00), to_double(sd.p01), to_double(sd.p11), to_double(sd.w)};
     return sg * leaky_halfspace_sign(lay + N * LAYER_STRIDE, c2, st);
+}
+// Out of line, one for each step: the scan kernel holds one, the check
+// kernel the other.
+static __device__ __noinline__ int det_sign_leaky_dd(const float* __restrict__ laydf,
+                                                     const double* __restrict__ lay, int N,
+                                                     double k, double c) {
+    return det_sign_leaky_t<false>(laydf, lay, N, k, c);
+}
+static __device__ __noinline__ int det_sign_leaky_df(const float* __restrict__ laydf,
+                                                     const double* __restrict__ lay, int N,
+                                                     double k, double c) {
+    return det_sign_leaky_t<true>(laydf, lay, N, k, c);
 }
 
 // Wittrick-Williams mode count of the layered structure below c, split as

@@ -120,10 +120,12 @@ cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const in
 
 // Leaky continuation: Algorithm 1 over the whole grid with the sign of Re det K
 // (complex half-space block at c >= beta_hs); items the batch scan resolved
-// (status_in 0) keep idx_in; outputs o; counter: 1; dd: the elements in
-// double-float (det_sign_leaky_df), else FP64 (masw_kernels.cu).
+// (status_in 0) keep idx_in; outputs o; work: 2 n_items + 4; dd: the scan in
+// double-float (det_sign_leaky_df), each change confirmed with the FP64 step
+// and the unconfirmed items scanned again in FP64; else the FP64 scan
+// (masw_kernels.cu).
 cudaError_t launch_leaky(const DevBatch& b, const ScanPlan& p, const int32_t* idx_in,
-                         const int32_t* status_in, const ScanOut& o, int32_t* counter, int dd,
+                         const int32_t* status_in, const ScanOut& o, int32_t* work, int dd,
                          cudaStream_t s);
 
 cudaError_t launch_scan(const DevBatch& b, const ScanOut& o, const ScanPlan& p, int32_t* counter,

@@ -1079,7 +1079,11 @@ cudaError_t launch_changes(const DevBatch& b, const ScanPlan& p, int M, const in
 // test velocities at or above the half-space shear speed included. Below it
 // K is real and this is Algorithm 1 itself, so an item whose batch scan found
 // a change keeps it; the others have the same sign at V[0..nlim-1] and are
-// continued here in FP64 from V[max(nlim, 1) - 1]. A group of G lanes per
+// continued here from V[max(nlim, 1) - 1]: with dd the signs of the element
+// and Schur step in double-float (det_sign_leaky_dd), each located change
+// then confirmed with the FP64 step (leaky_check_kernel) and the items it
+// does not confirm scanned again in FP64 (det_sign_leaky, a list given). A
+// group of G lanes per
 // item (groups pop b.order), G consecutive points per chunk. Smaller groups
 // evaluate fewer points past an item's change, but the lanes of a warp then
 // hold different items at different velocities and their branches (series,
@@ -1090,7 +1094,10 @@ template <int G>
 __global__ void __launch_bounds__(256) leaky_scan64_kernel(DevBatch b, ScanOut o,
                                                            const int32_t* __restrict__ idx_in,
                                                            const int32_t* __restrict__ status_in,
-                                                           int32_t* counter, int dd) {
+                                                           int32_t* counter, int dd,
+                                                           const int32_t* __restrict__ list,
+                                                           const int32_t* __restrict__ n_list,
+                                                           int32_t* check, int32_t* n_check) {
     static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "lanes per item: a power of two");
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
@@ -1100,12 +1107,14 @@ __global__ void __launch_bounds__(256) leaky_scan64_kernel(DevBatch b, ScanOut o
         int t = 0;
         if (gl == 0) t = atomicAdd(counter, 1);
         t = __shfl_sync(gmask, t, 0, G);
-        if (t >= b.n_items) return;  // the whole group leaves together
-        const int item = b.order[t];
+        if (t >= (list ? *n_list : b.n_items)) return;  // the whole group leaves together
+        const int item = list ? list[t] : b.order[t];
         int found = -1;
-        if (status_in[item] == 0) {
+        bool continued = false;
+        if (!list && status_in[item] == 0) {
             found = idx_in[item];
         } else {
+            continued = true;
             const int m = b.item_model[item];
             const int lo = b.model_loff[m];
             const int N = b.model_loff[m + 1] - lo - 1;
@@ -1118,7 +1127,7 @@ __global__ void __launch_bounds__(256) leaky_scan64_kernel(DevBatch b, ScanOut o
                 const int n = base + gl;
                 const double c = grid_c(b.c0, b.dc, n);
                 const int sg = n >= b.n_c ? 0
-                               : (dd && laydf) ? det_sign_leaky_df(laydf, lay, N, k, c)
+                               : (dd && laydf) ? det_sign_leaky_dd(laydf, lay, N, k, c)
                                                : det_sign_leaky(lay, N, k, c);
                 int ps = __shfl_up_sync(gmask, sg, 1, G);
                 if (gl == 0) ps = carry;
@@ -1141,8 +1150,42 @@ __global__ void __launch_bounds__(256) leaky_scan64_kernel(DevBatch b, ScanOut o
                 o.idx[item] = -1;
                 o.status[item] = 1;
             }
+            if (check && continued && found >= 0) check[atomicAdd(n_check, 1)] = item;
         }
         __syncwarp(gmask);
+    }
+}
+
+// The double-float continuation's changes, confirmed with the FP64 Schur
+// step (det_sign_leaky_df): a change at the located index
+// n and none at n - 1 (V[n-2], V[n-1], V[n] on three of four lanes per
+// item). Items without that go to the rescan list (the FP64 scan).
+__global__ void __launch_bounds__(128) leaky_check_kernel(DevBatch b, ScanOut o,
+                                                          const int32_t* __restrict__ list,
+                                                          const int32_t* __restrict__ n_list,
+                                                          int32_t* rescan, int32_t* n_rescan) {
+    const int total = *n_list;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & 3;
+    const int q0 = lane & 28;
+    const unsigned quad = 0xFu << q0;
+    const int stride = (gridDim.x * blockDim.x) >> 2;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 2; t < total; t += stride) {
+        const int item = list[t];
+        const int m = b.item_model[item];
+        const int lo = b.model_loff[m];
+        const int N = b.model_loff[m + 1] - lo - 1;
+        const int start = max(b.model_nlim[m], 1);
+        const int found = o.idx[item];
+        const int pt = found - 2 + sub;
+        const int sg = (sub < 3 && pt >= start - 1)
+                           ? det_sign_leaky_df(records_df(b, lo), b.layers + (size_t)lo * LAYER_STRIDE,
+                                               N, b.k[item], grid_c(b.c0, b.dc, pt))
+                           : 0;
+        const int sa = __shfl_sync(quad, sg, q0), sb = __shfl_sync(quad, sg, q0 + 1);
+        const int sc = __shfl_sync(quad, sg, q0 + 2);
+        if (sub == 0 && !(sb != sc && (found - 2 < start - 1 || sa == sb)))
+            rescan[atomicAdd(n_rescan, 1)] = item;
     }
 }
 
@@ -1151,14 +1194,29 @@ __global__ void __launch_bounds__(256) leaky_scan64_kernel(DevBatch b, ScanOut o
 constexpr int LEAKY_LANES = 32;
 
 cudaError_t launch_leaky(const DevBatch& b, const ScanPlan& p, const int32_t* idx_in,
-                         const int32_t* status_in, const ScanOut& o, int32_t* counter, int dd,
+                         const int32_t* status_in, const ScanOut& o, int32_t* work, int dd,
                          cudaStream_t s) {
     if (b.n_items == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+    // work: the check list, the rescan list (n_items each), then the counters
+    // [0] scan queue, [1] check count, [2] rescan count, [3] rescan queue
+    int32_t* check = work;
+    int32_t* rescan = work + b.n_items;
+    int32_t* cnt = work + 2 * (size_t)b.n_items;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, 4 * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
+    dd = dd && b.layers_df;
     const int wpb = p.warps_per_block;
     leaky_scan64_kernel<LEAKY_LANES><<<std::max(1, std::min(p.blocks, (b.n_items + wpb - 1) / wpb)),
-                                       32 * wpb, 0, s>>>(b, o, idx_in, status_in, counter, dd);
+                                       32 * wpb, 0, s>>>(b, o, idx_in, status_in, cnt, dd, nullptr,
+                                                         nullptr, dd ? check : nullptr, cnt + 1);
+    if ((e = cudaGetLastError()) != cudaSuccess || !dd) return e;
+    const int sms = p.sms > 0 ? p.sms : 152;
+    leaky_check_kernel<<<std::max(1, std::min(4 * sms, (4 * b.n_items + 127) / 128)), 128, 0, s>>>(
+        b, o, check, cnt + 1, rescan, cnt + 2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the few unconfirmed items: the FP64 scan, one warp each, over every SM
+    leaky_scan64_kernel<LEAKY_LANES><<<std::max(1, std::min(8 * sms, b.n_items)), 32, 0, s>>>(
+        b, o, idx_in, status_in, cnt + 3, 0, rescan, cnt + 2, nullptr, nullptr);
     return cudaGetLastError();
 }
 

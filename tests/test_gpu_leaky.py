@@ -143,12 +143,14 @@ def test_invalid_arguments_of_the_new_entry_points(masw):
 
 
 def test_double_float_continuation_equals_the_fp64_one(masw, oracle_lib):
-    """The default plan continues with the element in double-float
-    (det_sign_leaky_df); plan precision 0 with the FP64 element
-    (det_sign_leaky). On the full leaky batch they agree item for item but
-    for sign decisions within rounding of zero: at most 0.01 % of items
-    differ, and where they do, both lie within one grid step of the
-    oracle's index."""
+    """The default plan locates the continued change with the element and
+    the Schur step in double-float (det_sign_leaky_dd), confirms it with the
+    FP64 step at it and the two points below (det_sign_leaky_df) and scans
+    the items it does not confirm again in FP64; plan precision 0 scans with
+    the FP64 element and step (det_sign_leaky). On the full leaky batch they agree item for
+    item but for sign decisions within rounding of zero: at most 0.01 % of
+    items differ, and where they do, both lie within one grid step of the
+    oracle's index (the test prints which of the two equals it)."""
     m, g = W.leaky_batch()
     with masw.Batch(m, g) as b:
         _, idx_dd, st_dd = b.leaky()
@@ -160,5 +162,6 @@ def test_double_float_continuation_equals_the_fp64_one(masw, oracle_lib):
     assert diff.size <= 1e-4 * m.n_items
     if diff.size:
         _, o_idx, o_st = oracle_leaky(oracle_lib, m, g, diff)
+        print("double-float / FP64 / oracle:", list(zip(idx_dd[diff], idx64[diff], o_idx)))
         assert (o_st == 0).all()
         assert (np.abs(idx_dd[diff] - o_idx) <= 1).all() and (np.abs(idx64[diff] - o_idx) <= 1).all()
