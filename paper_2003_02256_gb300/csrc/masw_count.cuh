@@ -1,19 +1,24 @@
 // masw_count.cuh -- counting search with its FP64 certificate for one
-// (model, wavenumber) item, run by a pair of adjacent lanes (plan precision 2
-// of the batch path and the serving tick).
+// (model, wavenumber) item (plan precision 2 of the batch path and the
+// serving tick).
 //
 //  * Search (FP32). Inside the pole-free range [0, npf) of pole_free_points_f
 //    the negative-eigenvalue count of K (inertia_f) is a non-decreasing step
 //    function of the grid index, 0 at c = 0 (Wittrick-Williams below the
-//    lowest clamped-layer mode). The pair evaluates the top of the range and
-//    its midpoint, then splits the bracket in three per step (one point per
-//    lane): about log3(npf) steps instead of Algorithm 1's linear walk. The
-//    first nonzero point goes to the certificate whatever its FP32 parity.
-//  * Certificate (recurrence over double-float elements, det_inertia_dd in
-//    masw_df.cuh: the Schur step in double-float too, the half-space's in
-//    FP64; points above the pole-free range take det_inertia_df, the FP64
-//    step). The count is 0 at V[n-1] (so 0, and
-//    V[0]'s sign, at every point below) and odd at V[n] (the sign differs).
+//    lowest clamped-layer mode). One thread bisects it (count_search_single,
+//    or count_search_bracket from the indices of neighbouring wavelengths),
+//    or a pair of lanes evaluates the top of the range and its midpoint, then
+//    splits the bracket in three per step, one point per lane (the fused
+//    kernel and the serving tick, where the certificate's lanes follow):
+//    about log2(npf), or log3(npf) steps, instead of Algorithm 1's linear
+//    walk. The first nonzero point goes to the certificate whatever its FP32
+//    parity.
+//  * Certificate (a pair of adjacent lanes; the recurrence over
+//    double-float elements, det_inertia_dd in masw_df.cuh: the Schur step in
+//    double-float too, the half-space's in FP64; points above the pole-free
+//    range take det_inertia_df, the FP64 step). The count is 0 at V[n-1] (so
+//    0, and V[0]'s sign, at every point below) and odd at V[n] (the sign
+//    differs).
 //    When the FP32 count was off by one next to the change (count 0 at both
 //    points: the change is higher; nonzero at V[n-1]: lower), the pair takes
 //    one FP64 step of two points in that direction, inside the range. An

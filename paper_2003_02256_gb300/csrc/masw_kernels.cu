@@ -15,11 +15,15 @@
 //                         FP64 check on the Wittrick-Williams mode count.
 //  count_search_kernel,   precision 2 (default): FP32 search on the
 //  count_certify_kernel   negative-eigenvalue count below the pole-free bound
-//                         and its FP64 certificate, a lane pair per item (two
-//                         kernels by default, plan count_split; one fused
-//                         kernel otherwise); the fallback items take
-//                         fallback32_kernel (linear FP32 scan) and
-//                         verify64_list_kernel (the check).
+//                         (one thread per item, bisection, two passes: every
+//                         4th wavelength of a model first, then the others
+//                         from their neighbours' bracket) and its FP64
+//                         certificate, a lane pair per item; for small batches
+//                         both in one kernel (lane pairs, plan count_split).
+//                         The fallback items take fallback32_kernel (linear
+//                         FP32 scan) and verify64_list_kernel (the check), for
+//                         large batches on a second stream beside the
+//                         certificate.
 //  first_count64_kernel   both two-precision plans: items that failed a check,
 //                         search on the mode count from V[0] (FP32-located,
 //                         FP64-certified rises).
@@ -29,7 +33,8 @@
 //                         event certified on the FP64 count;
 //  changes_scan64_kernel  higher modes, FP64 scan at every grid point.
 //  leaky_scan64_kernel    the whole grid with the sign of Re det K (complex
-//                         half-space block above its shear speed).
+//                         half-space block above its shear speed), located in
+//  leaky_check_kernel     double-float and confirmed with the FP64 step.
 // Around the scan:
 //  det_eval_kernel        sign and ln|det K| at arbitrary (item, c) points.
 //  mode_count_kernel      (s, J0) at arbitrary points.
