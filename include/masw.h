@@ -291,8 +291,9 @@ int masw_test_fail_alloc(int32_t k);
  * results must not change. 0: normal. 1: the counting search's items all go to
  * the linear FP32 scan from V[0] (plan precision 2). 2: also, every item fails
  * its three-point FP64 check and takes the FP64 mode-count search. 3: also,
- * every searched item takes the FP64 scan from V[0], and every higher-mode
- * item the FP64 scan at every grid point. 4 (no other routing): each
+ * every searched item takes the FP64 scan from V[0], every higher-mode item
+ * the FP64 scan at every grid point, and every item of the leaky
+ * continuation the FP64 scan after its double-float one. 4 (no other routing): each
  * higher-mode event that the FP32 search locates is displaced by 0, -1, +1,
  * +3 or -7 grid points (by item index mod 5) before its FP64 certificate, so
  * that the search's recovery steps run. Synchronises the batch stream and

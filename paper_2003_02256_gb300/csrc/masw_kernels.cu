@@ -1164,7 +1164,8 @@ __global__ void __launch_bounds__(256) leaky_scan64_kernel(DevBatch b, ScanOut o
 // The double-float continuation's changes, confirmed with the FP64 Schur
 // step (det_sign_leaky_df): a change at the located index
 // n and none at n - 1 (V[n-2], V[n-1], V[n] on three of four lanes per
-// item). Items without that go to the rescan list (the FP64 scan).
+// item). Items without that go to the rescan list (the FP64 scan); test
+// routing 3 sends every item there.
 __global__ void __launch_bounds__(128) leaky_check_kernel(DevBatch b, ScanOut o,
                                                           const int32_t* __restrict__ list,
                                                           const int32_t* __restrict__ n_list,
@@ -1189,7 +1190,8 @@ __global__ void __launch_bounds__(128) leaky_check_kernel(DevBatch b, ScanOut o,
                            : 0;
         const int sa = __shfl_sync(quad, sg, q0), sb = __shfl_sync(quad, sg, q0 + 1);
         const int sc = __shfl_sync(quad, sg, q0 + 2);
-        if (sub == 0 && !(sb != sc && (found - 2 < start - 1 || sa == sb)))
+        // (test routing 3: every item to the rescan)
+        if (sub == 0 && (route_level(b.route) >= 3 || !(sb != sc && (found - 2 < start - 1 || sa == sb))))
             rescan[atomicAdd(n_rescan, 1)] = item;
     }
 }

@@ -165,3 +165,19 @@ def test_double_float_continuation_equals_the_fp64_one(masw, oracle_lib):
         print("double-float / FP64 / oracle:", list(zip(idx_dd[diff], idx64[diff], o_idx)))
         assert (o_st == 0).all()
         assert (np.abs(idx_dd[diff] - o_idx) <= 1).all() and (np.abs(idx64[diff] - o_idx) <= 1).all()
+
+
+def test_forced_rescan_gives_the_fp64_continuation(masw):
+    """Test routing 3 sends every continued item, after its double-float scan
+    and check, to the FP64 rescan: the results are the FP64 continuation's
+    (plan precision 0), so the rescan path runs whatever the check finds."""
+    m, g = W.leaky_batch(n_models=64, n_lambda=40)
+    with masw.Batch(m, g) as b:
+        b.set_plan(precision=0)
+        ref = b.leaky()
+        b.set_plan(precision=2)
+        b.set_route(3)
+        got = b.leaky()
+        b.set_route(0)
+    assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
+    assert (ref[2] == 0).mean() > 0.9
