@@ -517,15 +517,17 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
 }
 
 
-// Counting search and its FP64 certificate (plan precision 2) fused in one
-// kernel, two lanes per item (count_certify_pair; natural item order: a
-// warp's 16 items share a model and have adjacent wavelengths, so their
-// branches agree). Fusing lets warps in the FP32 search and warps in the FP64
-// certificate share an SM: the two use different pipes. Items whose change
-// lies above the pole-free range, at V[0], or behind an even FP64 count go to
-// the fallback list (linear FP32 scan and mode-count check); uncertified items
-// go to the FP64 mode-count search. Certified items keep SCREEN_COUNTED in
-// n32. B threads per block (plan count_block: 64, 128 or 256), each block's
+// The counting search's FP64 certificate (plan precision 2), two lanes per
+// item (certify_pair; natural item order, or by layer count over a whole
+// batch: a warp's 16 items share a model and have adjacent wavelengths, so
+// their branches agree), with the search in the same kernel (count_search_pair,
+// small batches) or before it (SPLIT: its index in nsearch). Items whose
+// change lies above the pole-free range or at V[0] go to the fallback list
+// (linear FP32 scan and mode-count check); the certificate's own failures
+// (the counts around the located point, or an even count with no odd one
+// found above it) take the mode-count search from V[0] in this kernel
+// (pair_mode_search), and those whose FP64 counts fail there the FP64
+// re-scan list. Certified items keep SCREEN_COUNTED in n32. B threads per block (plan count_block: 64, 128 or 256), each block's
 // B/2 items consecutive, so its warps share the records of one or two models
 // in L1; the launch bounds ask for 896 resident threads per SM (at most 73
 // registers a thread) for B = 64 and 128, and 768 for 256; with SPLIT (plan
@@ -596,12 +598,33 @@ __global__ void __launch_bounds__(B) count_search_kernel(DevBatch b,
     early[atomicAdd(n_early, 1)] = item;
 }
 
+// Algorithm 1's first change of one item as the first odd jump of the FP64
+// mode count T = s + 2 J0 above V[0], by a pair of lanes: T at V[0] and
+// V[top], then next_change_f32 (masw_modes.cuh), each rise of T located on
+// its FP32 value and certified on the FP64 count. *bad: the FP64 counts
+// failed (rescaling, or T not monotone at the evaluated points). Out of line:
+// first_count64_kernel runs it for listed items, the certificate for its own
+// few failures.
+static __device__ __noinline__ int pair_mode_search(const float* laydf, const double* lay,
+                                                    const float* lay32, int N, double k,
+                                                    double c0, double dc, int top, int half,
+                                                    unsigned pair, bool* bad) {
+    TPoint p0, ptop;
+    eval_pair(laydf, lay, N, k, c0, dc, 0, top, half, pair, &p0, &ptop);
+    ModeSearch st = mode_search_init(laydf, lay, N, k, c0, dc, top, half, pair, p0, ptop);
+    int d = 0;
+    const int res = next_change_f32(st, lay32, &d);
+    *bad = st.bad;
+    return res;
+}
+
 template <int B, bool SPLIT>
 __global__ void __launch_bounds__(B, (B == 256 ? 3 : (B == 64 && SPLIT ? 10 : 896 / B)))
     count_certify_kernel(DevBatch b, const float* __restrict__ layers32, ScanOut o,
                          int32_t* n32, const int32_t* nsearch, int early, int32_t* search,
                          int32_t* n_search, int32_t* fallback, int32_t* n_fallback,
-                         int item_begin, int item_end) {
+                         int32_t* unresolved, int32_t* n_unresolved, int item_begin,
+                         int item_end) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     int item = item_begin + (t >> 1);
     if (item >= item_end) return;  // both lanes of a pair leave together
@@ -629,12 +652,28 @@ __global__ void __launch_bounds__(B, (B == 256 ? 3 : (B == 64 && SPLIT ? 10 : 89
     const float* laydf = b.layers_df ? b.layers_df + (size_t)lo_rec * LAYER_STRIDE_DF : nullptr;
     const float* lay32 = layers32 + (size_t)lo_rec * LAYER_STRIDE32;
     const double k = b.k[item];
-    PairCount r;
-    if (SPLIT) {
-        const int npf = pole_free_points_f(lay32, N, (float)k, (float)b.c0, (float)b.dc, nlim);
-        r = certify_pair(lay32, laydf, lay, N, k, b.c0, b.dc, nlim, npf, nsearch[item], half, pair);
-    } else {
-        r = count_certify_pair(lay32, laydf, lay, N, k, b.c0, b.dc, nlim, half, pair);
+    const int npf = pole_free_points_f(lay32, N, (float)k, (float)b.c0, (float)b.dc, nlim);
+    const int ns = SPLIT ? nsearch[item] : count_search_pair(lay32, N, k, b.c0, b.dc, npf, half, pair);
+    const PairCount r = certify_pair(lay32, laydf, lay, N, k, b.c0, b.dc, nlim, npf, ns, half, pair);
+    // the certificate's own failures (the FP64 counts around the located
+    // point fail, or two modes inside one interval with no odd count found
+    // above them): the mode-count search from V[0] right here, by this pair,
+    // while the kernel's other blocks run, where the fallback chain after the
+    // kernel would take three more launches in a row
+    if (route_level(b.route) < 1 && r.cert < 1 && (r.n >= 1 || (r.start >= 1 && r.start < npf))) {
+        bool bad;
+        const int res = pair_mode_search(laydf, lay, lay32, N, k, b.c0, b.dc, nlim - 1, half, pair,
+                                         &bad);
+        if (half) return;
+        if (o.cert_counts) o.cert_counts[item] = -1;
+        if (bad) {  // the FP64 scan from V[0]
+            n32[item] = 0;
+            unresolved[atomicAdd(n_unresolved, 1)] = item;
+        } else {
+            n32[item] = res;
+            write_result(b, o, item, res);
+        }
+        return;
     }
     if (half) return;
     if (o.cert_counts) o.cert_counts[item] = route_level(b.route) >= 1 ? -1 : r.counts;
@@ -689,13 +728,11 @@ __global__ void __launch_bounds__(32) first_count64_kernel(DevBatch b, ScanOut o
         const float* laydf = records_df(b, l0);
         const double k = b.k[item];
         const int top = b.model_nlim[m] - 1;  // >= 1 for listed items
-        TPoint p0, ptop;
-        eval_pair(laydf, lay, N, k, b.c0, b.dc, 0, top, half, pair, &p0, &ptop);
-        ModeSearch st = mode_search_init(laydf, lay, N, k, b.c0, b.dc, top, half, pair, p0, ptop);
-        int d = 0;
-        const int res = next_change_f32(st, layers32 + (size_t)l0 * LAYER_STRIDE32, &d);
+        bool bad;
+        const int res = pair_mode_search(laydf, lay, layers32 + (size_t)l0 * LAYER_STRIDE32, N, k,
+                                         b.c0, b.dc, top, half, pair, &bad);
         if (!half) {
-            if (st.bad || route_level(b.route) >= 3) {  // (test routing 3: every item to the FP64 scan)
+            if (bad || route_level(b.route) >= 3) {  // (test routing 3: every item to the FP64 scan)
                 n32[item] = 0;
                 unresolved[atomicAdd(n_unresolved, 1)] = item;
             } else {
@@ -847,7 +884,7 @@ cudaError_t launch_screen_scan(const DevBatch& b, const ScanOut& o, const ScanPl
 #define MASW_COUNT_LAUNCH(BS, SPL)                                                              \
     count_certify_kernel<BS, SPL><<<grid, BS, 0, s>>>(b, layers32, o, n32, nsearch, overlap ? 1 : 0, \
                                                       search, counters + 5, fallback, counters + 3, \
-                                                      item_begin, item_end)
+                                                      unresolved, counters + 1, item_begin, item_end)
         switch (cb * 2 + (p.count_split ? 1 : 0)) {
             case 128: MASW_COUNT_LAUNCH(64, false); break;
             case 129: MASW_COUNT_LAUNCH(64, true); break;
