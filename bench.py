@@ -99,23 +99,24 @@ FP64_DFMA_PER_CLK_SM = 2.0
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one count_certify launch, from ncu captures
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the full workload, as
-# (bytes, models of that launch); the records, wavenumbers and item tables are
-# read once, the outputs stay in L2. Scaled by the models of a launch; None
+# (bytes, models of that launch); the records, wavenumbers, item tables and
+# the search's indices are read once. Scaled by the models of a launch; None
 # where no capture of the current kernel exists.
-# uniform: 4.46 MB for the 1024-model launch of count_certify_kernel<128,
-# true>; ragged: 12.46 MB for the launch over the first 2048 models (429,978
-# items), scaled by the models to the 8192-model launch (its algorithmic
-# bytes -- records, wavenumbers, item tables, the search's indices -- are
-# 4.024 times the 2048-model launch's).
-CERTIFY_DRAM_BYTES = {"uniform": (4.459008e6, 1024), "ragged": (12.464128e6, 2048)}
+# uniform: 5.27 MB for the 1024-model launch of count_certify_kernel<128,
+# true> (most of its outputs stay in L2); ragged: 75.79 MB for the
+# 8192-model launch (48.25 MB read, 27.54 MB written: its 1.74 M items'
+# outputs leave L2).
+CERTIFY_DRAM_BYTES = {"uniform": (5.267968e6, 1024), "ragged": (75.7888e6, 8192)}
 # Warp instructions a kernel issues per layer-evaluation (ncu
-# smsp__inst_executed.sum of one launch / its layer-evaluations counted as in
-# counting_evals), by workload (ragged: the 2048-model launch): the
-# certificate kernel per certificate layer-evaluation, the search kernel per
-# FP32 one. A kernel's ceiling is the SM's issue rate, ISSUE_PER_CLK_SM warp
+# smsp__inst_executed.sum of one full-workload launch / its layer-evaluations
+# counted as in counting_evals), by workload: the certificate kernel per
+# certificate layer-evaluation, the search kernels (both passes) per FP32
+# one. A kernel's ceiling is the SM's issue rate, ISSUE_PER_CLK_SM warp
 # instructions per clock, over this count.
-CERTIFY_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 50.82, "ragged": 52.59}
-SEARCH_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 6.48, "ragged": 6.43}
+CERTIFY_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 51.25, "ragged": 52.97}
+# the split search's anchor stride (SEARCH_STRIDE in csrc/masw_internal.h)
+SEARCH_STRIDE = 6
+SEARCH_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 6.41, "ragged": 6.27}
 ISSUE_PER_CLK_SM = 4
 # Warp instructions per layer-evaluation of the leaky continuation's scan
 # kernel, element and Schur step in double-float (ncu smsp__inst_executed.sum
@@ -390,13 +391,14 @@ def executed_layer_evals(models, idx, st, nlim, cpl):
     return int(np.sum(pts * nl))
 
 
-def split_search_evals(models, npf, root, stride=4):
+def split_search_evals(models, npf, root, stride=None):
     """FP32 evaluations per item of the split search (count_search_kernel):
     every stride-th item of a model and its last bisect the whole pole-free
     range (the top, then ceil(log2 npf) steps); the others start from the
     bracket (min(na, nb) - 1, max(na, nb)] of those neighbours' indices and
     widen it as count_search_bracket does. The located index is taken as the
     item's first change (root) when it lies inside the range."""
+    stride = stride or SEARCH_STRIDE
     ceil_log2 = lambda w: np.ceil(np.log2(np.maximum(w, 1)))
     n_items = models.n_items
     woff = np.concatenate([[0], np.cumsum(models.n_lambda)])

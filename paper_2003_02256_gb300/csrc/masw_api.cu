@@ -15,6 +15,7 @@
 // plus lazily allocated buffers for roots, gradient rows and misfits, model
 // updates, the higher modes and the leaky continuation.
 #include <algorithm>
+#include <functional>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -572,13 +573,15 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
     std::iota(B->order_natural.begin(), B->order_natural.end(), 0);
     // the split search: every SEARCH_STRIDE-th wavelength of a model and its
     // last are searched in full first, the items between them after. Both
-    // lists run model by model with the models ordered by their layer count,
-    // so that a warp's items (consecutive wavelengths of one model, or of
-    // models with as many layers) take the same number of layer steps.
+    // lists run model by model, so that a warp's items (consecutive
+    // wavelengths of one model, or of models with as many layers) take the
+    // same number of layer steps, the models with the most layers first: the
+    // longest threads start in the first wave, and the last waves, with the
+    // shortest, end closer together.
     std::vector<int32_t> by_layers(B->n_models);
     std::iota(by_layers.begin(), by_layers.end(), 0);
     std::stable_sort(by_layers.begin(), by_layers.end(),
-                     [&](int32_t a, int32_t b) { return B->n_layers[a] < B->n_layers[b]; });
+                     [&](int32_t a, int32_t b) { return B->n_layers[a] > B->n_layers[b]; });
     auto anchor = [&](int32_t m, int32_t j) {
         return (j - B->woff[m]) % SEARCH_STRIDE == 0 || j == B->woff[m + 1] - 1;
     };
@@ -590,9 +593,14 @@ int masw_model_batch_create(const masw_models_desc* md, const masw_grid* grid, v
     for (int32_t m : by_layers)
         for (int32_t j = B->woff[m]; j < B->woff[m + 1]; ++j)
             if (!anchor(m, j)) B->search_order.push_back(j);
-    // (left out when the models come in that order already)
+    // The certificate's order: model by model, the fewest layers first
+    // (measured a little faster there than the other way round, beside the
+    // second stream's chain). Left out when the models come in that order
+    // already.
     if (!std::is_sorted(B->n_layers.begin(), B->n_layers.end())) {
         B->layer_order.reserve(nw);
+        std::stable_sort(by_layers.begin(), by_layers.end(),
+                         [&](int32_t a, int32_t b) { return B->n_layers[a] < B->n_layers[b]; });
         for (int32_t m : by_layers)
             for (int32_t j = B->woff[m]; j < B->woff[m + 1]; ++j) B->layer_order.push_back(j);
     }

@@ -26,17 +26,18 @@ struct DevBatch {
     int32_t route;  // test routing (masw_set_route): 0 normal, 1..3 force the slower paths,
                     // 4 displaces the FP32-located higher-mode events
     // the split counting search's two passes (or nullptr: one pass): item ids,
-    // first the n_anchor items searched in full (every SEARCH_STRIDE-th item of
-    // a model and its last), then the others, bracketed by those neighbours
+    // model by model from the most layers down, first the n_anchor items
+    // searched in full (every SEARCH_STRIDE-th item of a model and its last),
+    // then the others, bracketed by those neighbours
     const int32_t* search_order = nullptr;
     int32_t n_anchor = 0;
-    // all items, model by model with the models ordered by layer count (the
-    // split certificate's order over a whole batch), or nullptr
+    // all items, model by model from the fewest layers up (the split
+    // certificate's order over a whole batch), or nullptr
     const int32_t* layer_order = nullptr;
 };
 
 // Items of a model between two fully searched ones in the split search.
-constexpr int SEARCH_STRIDE = 4;
+constexpr int SEARCH_STRIDE = 6;
 
 // The cumulative level 0..3 of a test routing value (route 4 has none).
 __host__ __device__ inline int route_level(int route) { return route <= 3 ? route : 0; }

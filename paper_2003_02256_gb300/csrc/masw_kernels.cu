@@ -16,7 +16,7 @@
 //  count_search_kernel,   precision 2 (default): FP32 search on the
 //  count_certify_kernel   negative-eigenvalue count below the pole-free bound
 //                         (one thread per item, bisection, two passes: every
-//                         4th wavelength of a model first, then the others
+//                         6th wavelength of a model first, then the others
 //                         from their neighbours' bracket) and its FP64
 //                         certificate, a lane pair per item; for small batches
 //                         both in one kernel (lane pairs, plan count_split).
