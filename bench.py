@@ -103,20 +103,20 @@ SM_MAX_MHZ = 2070.0
 # the search's indices are read once. Scaled by the models of a launch; None
 # where no capture of the current kernel exists.
 # uniform: 5.27 MB for the 1024-model launch of count_certify_kernel<128,
-# true> (most of its outputs stay in L2); ragged: 75.79 MB for the
-# 8192-model launch (48.25 MB read, 27.54 MB written: its 1.74 M items'
-# outputs leave L2).
-CERTIFY_DRAM_BYTES = {"uniform": (5.267968e6, 1024), "ragged": (75.7888e6, 8192)}
+# true> (most of its outputs stay in L2); ragged: 59.90 MB for the
+# 8192-model launch of count_certify_kernel<256, true> (47.86 MB read,
+# 12.04 MB written by the end of the launch).
+CERTIFY_DRAM_BYTES = {"uniform": (5.27488e6, 1024), "ragged": (59.904e6, 8192)}
 # Warp instructions a kernel issues per layer-evaluation (ncu
 # smsp__inst_executed.sum of one full-workload launch / its layer-evaluations
 # counted as in counting_evals), by workload: the certificate kernel per
 # certificate layer-evaluation, the search kernels (both passes) per FP32
 # one. A kernel's ceiling is the SM's issue rate, ISSUE_PER_CLK_SM warp
 # instructions per clock, over this count.
-CERTIFY_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 51.25, "ragged": 52.97}
+CERTIFY_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 51.25, "ragged": 52.72}
 # the split search's anchor stride (SEARCH_STRIDE in csrc/masw_internal.h)
 SEARCH_STRIDE = 6
-SEARCH_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 6.41, "ragged": 6.27}
+SEARCH_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 8.22, "ragged": 7.92}
 ISSUE_PER_CLK_SM = 4
 # Warp instructions per layer-evaluation of the leaky continuation's scan
 # kernel, element and Schur step in double-float (ncu smsp__inst_executed.sum
@@ -391,35 +391,73 @@ def executed_layer_evals(models, idx, st, nlim, cpl):
     return int(np.sum(pts * nl))
 
 
+def _bisect_evals(lo, hi, r, active):
+    """Evaluations of the bisection of (lo, hi] (count 0 at lo, nonzero at
+    hi) down to the first nonzero point r, item by item (numpy arrays)."""
+    ev = np.zeros_like(lo)
+    lo, hi = lo.copy(), hi.copy()
+    act = active & (hi - lo > 1)
+    while act.any():
+        mid = lo + ((hi - lo) >> 1)
+        ev += act
+        up = mid >= r
+        hi = np.where(act & up, mid, hi)
+        lo = np.where(act & ~up, mid, lo)
+        act &= hi - lo > 1
+    return ev
+
+
 def split_search_evals(models, npf, root, stride=None):
-    """FP32 evaluations per item of the split search (count_search_kernel):
-    every stride-th item of a model and its last bisect the whole pole-free
-    range (the top, then ceil(log2 npf) steps); the others start from the
-    bracket (min(na, nb) - 1, max(na, nb)] of those neighbours' indices and
-    widen it as count_search_bracket does. The located index is taken as the
-    item's first change (root) when it lies inside the range."""
+    """FP32 evaluations per item of the split search (count_search_kernel),
+    simulated step by step on a count that turns nonzero at the item's first
+    change (root, when it lies inside the pole-free range): every stride-th
+    item of a model and its last evaluate the top of the range and bisect it
+    (count_search_single); the others start from the guess interpolated
+    between those neighbours' indices, step away from it by 1, 2, 4, ...
+    points until the change is bracketed, and bisect the bracket
+    (count_search_guess)."""
     stride = stride or SEARCH_STRIDE
-    ceil_log2 = lambda w: np.ceil(np.log2(np.maximum(w, 1)))
     n_items = models.n_items
     woff = np.concatenate([[0], np.cumsum(models.n_lambda)])
     item_model = np.repeat(np.arange(models.n_models), models.n_lambda)
     j = np.arange(n_items)
     first, last = woff[item_model], woff[item_model + 1] - 1
-    loc = np.where(root < npf, root, -1)
-    full = np.where(npf >= 1, 1 + np.where(loc >= 0, ceil_log2(npf), 0), 0)
+    npf = np.asarray(npf, dtype=np.int64)
+    r = np.where(root < npf, root, -1).astype(np.int64)
+    has = npf >= 1
+    # single: the top, then bisection of (-1, npf - 1] when it is nonzero
+    full = has.astype(np.int64) + _bisect_evals(np.full(n_items, -1, np.int64), npf - 1, r,
+                                                has & (r >= 0))
     ja = first + ((j - first) // stride) * stride
     jb = np.minimum(ja + stride, last)
     anchor = ((j - first) % stride == 0) | (j == last)
-    na, nb = loc[ja], loc[jb]
-    hi = np.minimum(np.maximum(na, nb), npf - 1)
-    lo = np.minimum(np.minimum(na, nb) - 1, hi - 1)
-    above = (loc < 0) | (loc > hi)
-    e_above = np.where(hi == npf - 1, 1, np.where(loc < 0, 2, 2 + ceil_log2(npf - 1 - hi)))
-    e_in = np.where(lo >= 0, 2 + np.where(loc <= lo, ceil_log2(lo + 1), ceil_log2(hi - lo)),
-                    1 + ceil_log2(hi + 1))
-    bracket = np.where(above, e_above, e_in)
-    use_full = anchor | (na < 1) | (nb < 1) | (npf < 1)
-    return np.where(npf >= 1, np.where(use_full, full, bracket), 0)
+    na, nb = r[ja], r[jb]
+    guess = has & ~anchor & (na >= 1) & (nb >= 1)
+    t = (j - ja) / np.maximum(jb - ja, 1)
+    g = np.clip(np.rint(na + (nb - na) * t).astype(np.int64), 0, np.maximum(npf - 1, 0))
+    ev = guess.astype(np.int64)
+    down = guess & (r >= 0) & (r <= g)
+    up = guess & ~down
+    lo = np.where(down, -1, g)
+    hi = np.where(down, g, -1)
+    step = 1
+    act_d = down & (hi > 0)
+    act_u = up & (lo < npf - 1)
+    while act_d.any() or act_u.any():
+        pd = np.maximum(hi - step, 0)
+        pu = np.minimum(lo + step, npf - 1)
+        ev += act_d | act_u
+        zero_d = pd < r  # count 0 at pd: the bracket's lower end
+        lo = np.where(act_d & zero_d, pd, lo)
+        hi = np.where(act_d & ~zero_d, pd, hi)
+        act_d &= ~zero_d & (hi > 0)
+        hit_u = (r >= 0) & (pu >= r)
+        hi = np.where(act_u & hit_u, pu, hi)
+        lo = np.where(act_u & ~hit_u, pu, lo)
+        act_u &= ~hit_u & (lo < npf - 1)
+        step *= 2
+    ev += _bisect_evals(lo, hi, r, guess & (hi >= 0))
+    return np.where(has, np.where(guess, ev, full), 0)
 
 
 def counting_evals(models, grid, idx, st, nlim, n32, split=True):

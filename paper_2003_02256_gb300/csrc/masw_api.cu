@@ -363,11 +363,14 @@ static masw_plan default_plan(const masw_batch* B) {
     p.stage_layers = std::min(B->max_layers + 1, 32);
     p.use_graph = 1;
     p.precision = 2;
-    p.count_block = 128;
     // the fused kernel's lane pairs give small batches the shortest chain;
     // large ones take the split kernels, and from a quarter million items
     // the search's fallback items on the second stream
     p.count_split = B->n_items < (1 << 17) ? 0 : B->n_items < (1 << 18) ? 1 : 2;
+    // beside the second stream's chain the certificate runs in blocks of 256
+    // (768 resident threads per SM, against 896 in blocks of 128: measured
+    // faster there, the chain ending sooner), else of 128
+    p.count_block = p.count_split == 2 ? 256 : 128;
     return p;
 }
 

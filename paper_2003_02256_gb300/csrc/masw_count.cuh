@@ -6,7 +6,8 @@
 //    the negative-eigenvalue count of K (inertia_f) is a non-decreasing step
 //    function of the grid index, 0 at c = 0 (Wittrick-Williams below the
 //    lowest clamped-layer mode). One thread bisects it (count_search_single,
-//    or count_search_bracket from the indices of neighbouring wavelengths),
+//    or count_search_guess from a guess interpolated between the indices of
+//    neighbouring wavelengths),
 //    or a pair of lanes evaluates the top of the range and its midpoint, then
 //    splits the bracket in three per step, one point per lane (the fused
 //    kernel and the serving tick, where the certificate's lanes follow):
@@ -115,32 +116,48 @@ __device__ __forceinline__ int count_search_single(const float* __restrict__ lay
     return hi;
 }
 
-// The search stage for an item whose neighbours at smaller and larger
-// wavelengths of the same model have been searched (indices na, nb; < 1: a
-// neighbour without one, and the item takes count_search_single). A
-// fundamental mode's phase velocity changes little between adjacent
-// wavelengths, so the first nonzero count usually lies in
-// (min(na, nb) - 1, max(na, nb)]: the count at the bracket's ends confirms
-// it, and bisection closes it. When the count at the upper end is 0 the
-// change lies above it (up to the top of the range), when the count at the
-// lower end is nonzero below it: the result is the same first nonzero point
-// of a non-decreasing count, in fewer evaluations when the guess holds.
-__device__ __forceinline__ int count_search_bracket(const float* __restrict__ lay32, int N,
-                                                    double k, double c0, double dc, int npf,
-                                                    int na, int nb) {
+// The search stage for an item between two searched wavelengths of its
+// model (indices na at item ja, nb at item jb > ja; < 1: a neighbour without
+// one, and the item takes count_search_single). The guess g interpolates the
+// neighbours' indices at the item's place between them (a fundamental mode's
+// phase velocity varies smoothly along log-spaced wavelengths). The count at
+// g says on which side the change lies; steps of 1, 2, 4, ... from g away
+// in that direction bracket it, and bisection closes the bracket: 2
+// evaluations when the guess is within one point, about 2 log2(e) + 2 for
+// an error of e points. The result is the same first nonzero point of a
+// non-decreasing count in [0, npf), or -1.
+__device__ __forceinline__ int count_search_guess(const float* __restrict__ lay32, int N,
+                                                  double k, double c0, double dc, int npf,
+                                                  int na, int nb, int num, int den) {
     if (npf < 1) return -1;
     if (na < 1 || nb < 1) return count_search_single(lay32, N, k, c0, dc, npf);
     const float kf = (float)k, c0f = (float)c0, dcf = (float)dc;
-    int hi = min(max(na, nb), npf - 1);
-    int lo = min(min(na, nb) - 1, hi - 1);  // >= -1
-    if (inertia_f(lay32, N, kf, fmaf((float)hi, dcf, c0f)) < 1) {
-        if (hi == npf - 1) return -1;  // no change inside the range
-        lo = hi;
-        hi = npf - 1;
-        if (inertia_f(lay32, N, kf, fmaf((float)hi, dcf, c0f)) < 1) return -1;
-    } else if (lo >= 0 && inertia_f(lay32, N, kf, fmaf((float)lo, dcf, c0f)) >= 1) {
-        hi = lo;
+    const int g = min(max(__float2int_rn((float)na + (float)(nb - na) * (float)num / (float)den), 0),
+                      npf - 1);
+    int lo, hi;  // count 0 at lo (c = 0 when lo = -1), nonzero at hi
+    if (inertia_f(lay32, N, kf, fmaf((float)g, dcf, c0f)) >= 1) {
+        hi = g;
         lo = -1;
+        for (int step = 1; hi > 0; step *= 2) {
+            const int p = max(hi - step, 0);
+            if (inertia_f(lay32, N, kf, fmaf((float)p, dcf, c0f)) < 1) {
+                lo = p;
+                break;
+            }
+            hi = p;
+        }
+    } else {
+        lo = g;
+        hi = -1;
+        for (int step = 1; lo < npf - 1; step *= 2) {
+            const int p = min(lo + step, npf - 1);
+            if (inertia_f(lay32, N, kf, fmaf((float)p, dcf, c0f)) >= 1) {
+                hi = p;
+                break;
+            }
+            lo = p;
+        }
+        if (hi < 0) return -1;  // no change inside the range
     }
     while (hi - lo > 1) {
         const int mid = lo + ((hi - lo) >> 1);

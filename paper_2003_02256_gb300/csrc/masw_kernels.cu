@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
 // count_split: the search ran before in count_search_kernel, its index in
 // n32), 640 for B = 64 (96 registers, fewer spills), so that the block size
 // also picks among three register budgets.
-// Search stage alone (count_search_single or count_search_bracket, one
+// Search stage alone (count_search_single or count_search_guess, one
 // thread per item): the index goes to nsearch[item], for
 // count_certify_kernel<B, true>. With an early list (plan count_split 2) the items the certificate would only pass on to
 // the linear FP32 scan (no count change inside the pole-free range, a mode
@@ -546,7 +546,8 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
 // PASS 0: the items [item_begin, item_end) in natural order; 1: the anchor
 // items of b.search_order (every SEARCH_STRIDE-th wavelength of a model and
 // its last), each searched in full; 2: the other items, each searched
-// between its two anchors' indices (count_search_bracket), after pass 1.
+// from a guess between its two anchors' indices (count_search_guess),
+// after pass 1.
 template <int B, int PASS>
 __global__ void __launch_bounds__(B) count_search_kernel(DevBatch b,
                                                          const float* __restrict__ layers32,
@@ -583,7 +584,8 @@ __global__ void __launch_bounds__(B) count_search_kernel(DevBatch b,
         const int w0 = b.model_woff[m], w1 = b.model_woff[m + 1];
         const int ja = w0 + ((item - w0) / SEARCH_STRIDE) * SEARCH_STRIDE;
         const int jb = min(ja + SEARCH_STRIDE, w1 - 1);
-        n = count_search_bracket(lay32, N, k, b.c0, b.dc, npf, nsearch[ja], nsearch[jb]);
+        n = count_search_guess(lay32, N, k, b.c0, b.dc, npf, nsearch[ja], nsearch[jb], item - ja,
+                               max(jb - ja, 1));
     } else {
         n = count_search_single(lay32, N, k, b.c0, b.dc, npf);
     }
