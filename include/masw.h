@@ -111,7 +111,7 @@ typedef struct {
                                 outside the bound take the linear screen of 1. Default: 2 */
     int32_t count_block;     /* precision 2: threads per block of the counting kernel, 64, 128
                                 or 256 (two lanes per item, items of a block consecutive;
-                                launch bounds of 14, 7 or 3 resident blocks). Default: 256
+                                launch bounds of 14, 7 or 2 resident blocks). Default: 256
                                 with count_split 2, else 128 */
     int32_t count_split;     /* precision 2: 0 the search (a lane pair per item, three-way
                                 splits) and the certificate in one kernel; 1 the search

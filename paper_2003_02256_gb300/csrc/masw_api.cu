@@ -368,7 +368,7 @@ static masw_plan default_plan(const masw_batch* B) {
     // the search's fallback items on the second stream
     p.count_split = B->n_items < (1 << 17) ? 0 : B->n_items < (1 << 18) ? 1 : 2;
     // beside the second stream's chain the certificate runs in blocks of 256
-    // (768 resident threads per SM, against 896 in blocks of 128: measured
+    // (512 resident threads per SM, against 896 in blocks of 128: measured
     // faster there, the chain ending sooner), else of 128
     p.count_block = p.count_split == 2 ? 256 : 128;
     return p;

@@ -527,13 +527,16 @@ __global__ void __launch_bounds__(256) fallback32_kernel(DevBatch b, const float
 // (the counts around the located point, or an even count with no odd one
 // found above it) take the mode-count search from V[0] in this kernel
 // (pair_mode_search), and those whose FP64 counts fail there the FP64
-// re-scan list. Certified items keep SCREEN_COUNTED in n32. B threads per block (plan count_block: 64, 128 or 256), each block's
-// B/2 items consecutive, so its warps share the records of one or two models
-// in L1; the launch bounds ask for 896 resident threads per SM (at most 73
-// registers a thread) for B = 64 and 128, and 768 for 256; with SPLIT (plan
-// count_split: the search ran before in count_search_kernel, its index in
-// n32), 640 for B = 64 (96 registers, fewer spills), so that the block size
-// also picks among three register budgets.
+// re-scan list. Certified items keep SCREEN_COUNTED in n32. B threads per
+// block (plan count_block: 64, 128 or 256), each block's B/2 items
+// consecutive, so its warps share the records of one or two models in L1;
+// the launch bounds ask for 896 resident threads per SM (at most 73
+// registers a thread) for B = 64 and 128, and 512 for 256 (128 registers, no
+// spills: the default beside the second stream, whose chain then finds room
+// sooner); with SPLIT (plan count_split: the search ran before in
+// count_search_kernel, its index in n32), 640 for B = 64 (96 registers,
+// fewer spills), so that the block size also picks among the register
+// budgets.
 // Search stage alone (count_search_single or count_search_guess, one
 // thread per item): the index goes to nsearch[item], for
 // count_certify_kernel<B, true>. With an early list (plan count_split 2) the items the certificate would only pass on to
@@ -621,7 +624,7 @@ static __device__ __noinline__ int pair_mode_search(const float* laydf, const do
 }
 
 template <int B, bool SPLIT>
-__global__ void __launch_bounds__(B, (B == 256 ? 3 : (B == 64 && SPLIT ? 10 : 896 / B)))
+__global__ void __launch_bounds__(B, (B == 256 ? 2 : (B == 64 && SPLIT ? 10 : 896 / B)))
     count_certify_kernel(DevBatch b, const float* __restrict__ layers32, ScanOut o,
                          int32_t* n32, const int32_t* nsearch, int early, int32_t* search,
                          int32_t* n_search, int32_t* fallback, int32_t* n_fallback,
