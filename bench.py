@@ -103,20 +103,20 @@ SM_MAX_MHZ = 2070.0
 # the search's indices are read once. Scaled by the models of a launch; None
 # where no capture of the current kernel exists.
 # uniform: 5.27 MB for the 1024-model launch of count_certify_kernel<128,
-# true> (most of its outputs stay in L2); ragged: 59.90 MB for the
-# 8192-model launch of count_certify_kernel<256, true> (47.86 MB read,
-# 12.04 MB written by the end of the launch).
-CERTIFY_DRAM_BYTES = {"uniform": (5.27488e6, 1024), "ragged": (59.904e6, 8192)}
+# true> (most of its outputs stay in L2); ragged: 49.51 MB for the
+# 8192-model launch of count_certify_kernel<256, true> (47.71 MB read,
+# 1.80 MB written by the end of the launch).
+CERTIFY_DRAM_BYTES = {"uniform": (5.355264e6, 1024), "ragged": (49.506048e6, 8192)}
 # Warp instructions a kernel issues per layer-evaluation (ncu
 # smsp__inst_executed.sum of one full-workload launch / its layer-evaluations
 # counted as in counting_evals), by workload: the certificate kernel per
 # certificate layer-evaluation, the search kernels (both passes) per FP32
 # one. A kernel's ceiling is the SM's issue rate, ISSUE_PER_CLK_SM warp
 # instructions per clock, over this count.
-CERTIFY_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 51.25, "ragged": 52.72}
+CERTIFY_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 51.25, "ragged": 51.95}
 # the split search's anchor stride (SEARCH_STRIDE in csrc/masw_internal.h)
 SEARCH_STRIDE = 6
-SEARCH_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 8.22, "ragged": 7.92}
+SEARCH_WARP_INSTR_PER_LAYER_EVAL = {"uniform": 8.61, "ragged": 8.21}
 ISSUE_PER_CLK_SM = 4
 # Warp instructions per layer-evaluation of the leaky continuation's scan
 # kernel, element and Schur step in double-float (ncu smsp__inst_executed.sum
@@ -412,10 +412,10 @@ def split_search_evals(models, npf, root, stride=None):
     simulated step by step on a count that turns nonzero at the item's first
     change (root, when it lies inside the pole-free range): every stride-th
     item of a model and its last evaluate the top of the range and bisect it
-    (count_search_single); the others start from the guess interpolated
-    between those neighbours' indices, step away from it by 1, 2, 4, ...
-    points until the change is bracketed, and bisect the bracket
-    (count_search_guess)."""
+    (count_search_single); the others start from the guess of search_guess
+    (the line through those neighbours' indices, rounded down from a quarter
+    point below it), step away from it by 1, 2, 4, ... points until the
+    change is bracketed, and bisect the bracket (count_search_guess)."""
     stride = stride or SEARCH_STRIDE
     n_items = models.n_items
     woff = np.concatenate([[0], np.cumsum(models.n_lambda)])
@@ -433,8 +433,8 @@ def split_search_evals(models, npf, root, stride=None):
     anchor = ((j - first) % stride == 0) | (j == last)
     na, nb = r[ja], r[jb]
     guess = has & ~anchor & (na >= 1) & (nb >= 1)
-    t = (j - ja) / np.maximum(jb - ja, 1)
-    g = np.clip(np.rint(na + (nb - na) * t).astype(np.int64), 0, np.maximum(npf - 1, 0))
+    lin = na + (nb - na) * (j - ja) / np.maximum(jb - ja, 1)
+    g = np.clip(np.floor(lin - 0.25).astype(np.int64), 0, np.maximum(npf - 1, 0))
     ev = guess.astype(np.int64)
     down = guess & (r >= 0) & (r <= g)
     up = guess & ~down

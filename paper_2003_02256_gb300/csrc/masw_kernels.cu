@@ -587,8 +587,10 @@ __global__ void __launch_bounds__(B) count_search_kernel(DevBatch b,
         const int w0 = b.model_woff[m], w1 = b.model_woff[m + 1];
         const int ja = w0 + ((item - w0) / SEARCH_STRIDE) * SEARCH_STRIDE;
         const int jb = min(ja + SEARCH_STRIDE, w1 - 1);
-        n = count_search_guess(lay32, N, k, b.c0, b.dc, npf, nsearch[ja], nsearch[jb], item - ja,
-                               max(jb - ja, 1));
+        const int na = nsearch[ja], nb = nsearch[jb];
+        const int guess = (na >= 1 && nb >= 1) ? max(search_guess(na, nb, item - ja, jb - ja), 0)
+                                               : -1;
+        n = count_search_guess(lay32, N, k, b.c0, b.dc, npf, guess);
     } else {
         n = count_search_single(lay32, N, k, b.c0, b.dc, npf);
     }

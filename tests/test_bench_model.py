@@ -1,5 +1,6 @@
 """The benchmark's evaluation model follows the library's split search (CPU
 only): its anchor stride is the one the kernels are built with."""
+import math
 import os
 import re
 
@@ -31,13 +32,13 @@ def _single(npf, r):
     return ev
 
 
-def _guess(npf, r, na, nb, num, den):
-    # count_search_guess, item by item
+def _guess(npf, r, na, nb, x, d):
+    # search_guess and count_search_guess, item by item
     if npf < 1:
         return 0
     if na < 1 or nb < 1:
         return _single(npf, r)
-    g = min(max(int(round(na + (nb - na) * num / den)), 0), npf - 1)
+    g = min(max(math.floor(na + (nb - na) * x / d - 0.25), 0), npf - 1)
     ev = 1
     if g >= r:
         hi, lo, step = g, -1, 1
