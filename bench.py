@@ -411,8 +411,8 @@ def split_search_evals(models, npf, root, stride=None):
     """FP32 evaluations per item of the split search (count_search_kernel),
     simulated step by step on a count that turns nonzero at the item's first
     change (root, when it lies inside the pole-free range): every stride-th
-    item of a model and its last evaluate the top of the range and bisect it
-    (count_search_single); the others start from the guess of search_guess
+    item of a model and its last bisect the range, evaluating its top only
+    when the bisection ends there (count_search_single); the others start from the guess of search_guess
     (the line through those neighbours' indices, rounded down from a quarter
     point below it), step away from it by 1, 2, 4, ... points until the
     change is bracketed, and bisect the bracket (count_search_guess)."""
@@ -425,9 +425,10 @@ def split_search_evals(models, npf, root, stride=None):
     npf = np.asarray(npf, dtype=np.int64)
     r = np.where(root < npf, root, -1).astype(np.int64)
     has = npf >= 1
-    # single: the top, then bisection of (-1, npf - 1] when it is nonzero
-    full = has.astype(np.int64) + _bisect_evals(np.full(n_items, -1, np.int64), npf - 1, r,
-                                                has & (r >= 0))
+    # single: bisection of (-1, npf - 1], the top evaluated when it ends there
+    r_none = np.where(r >= 0, r, np.iinfo(np.int64).max)
+    full = (_bisect_evals(np.full(n_items, -1, np.int64), npf - 1, r_none, has)
+            + (has & ((r < 0) | (r == npf - 1))))
     ja = first + ((j - first) // stride) * stride
     jb = np.minimum(ja + stride, last)
     anchor = ((j - first) % stride == 0) | (j == last)

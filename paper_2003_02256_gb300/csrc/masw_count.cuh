@@ -106,13 +106,16 @@ __device__ __forceinline__ int count_search_single(const float* __restrict__ lay
                                                    double k, double c0, double dc, int npf) {
     if (npf < 1) return -1;
     const float kf = (float)k, c0f = (float)c0, dcf = (float)dc;
-    int lo = -1, hi = npf - 1;  // count 0 at lo (c = 0 when lo = -1), nonzero at hi
-    if (inertia_f(lay32, N, kf, fmaf((float)hi, dcf, c0f)) < 1) return -1;
+    // count 0 at lo (c = 0 when lo = -1), nonzero at hi; the top is taken as
+    // nonzero and evaluated only when the bisection ends there (the change
+    // lies inside the range for nearly every item: one evaluation fewer)
+    int lo = -1, hi = npf - 1;
     while (hi - lo > 1) {
         const int mid = lo + ((hi - lo) >> 1);
         if (inertia_f(lay32, N, kf, fmaf((float)mid, dcf, c0f)) >= 1) hi = mid;
         else lo = mid;
     }
+    if (hi == npf - 1 && inertia_f(lay32, N, kf, fmaf((float)hi, dcf, c0f)) < 1) return -1;
     return hi;
 }
 

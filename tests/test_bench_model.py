@@ -19,9 +19,7 @@ def _single(npf, r):
     # count_search_single on a count that turns nonzero at r
     if npf < 1:
         return 0
-    lo, hi, ev = -1, npf - 1, 1
-    if hi < r:
-        return ev
+    lo, hi, ev = -1, npf - 1, 0
     while hi - lo > 1:
         mid = lo + ((hi - lo) >> 1)
         ev += 1
@@ -29,7 +27,7 @@ def _single(npf, r):
             hi = mid
         else:
             lo = mid
-    return ev
+    return ev + (hi == npf - 1)
 
 
 def _guess(npf, r, na, nb, x, d):
