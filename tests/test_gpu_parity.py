@@ -310,6 +310,30 @@ def test_two_precision_scan_equals_the_fp64_scan_at_full_size(masw, which, preci
         assert fallback == -1
 
 
+def test_split_search_with_shuffled_wavelengths_equals_the_fp64_scan(masw):
+    """The second search pass starts from a guess on the line through its
+    anchors' indices. With each model's wavelengths in random order the
+    guesses miss by up to the whole range; the steps away from them and the
+    bisection still give the FP64 scan's index, item for item."""
+    import dataclasses
+
+    m, g = W.ragged_batch(n_models=256, seed=91)
+    rng = np.random.default_rng(5)
+    woff = np.concatenate([[0], np.cumsum(m.n_lambda)])
+    lam = m.lam.copy()
+    for i in range(m.n_models):
+        lam[woff[i]:woff[i + 1]] = rng.permutation(lam[woff[i]:woff[i + 1]])
+    m = dataclasses.replace(m, lam=lam)
+    with masw.Batch(m, g) as b:
+        b.set_plan(precision=0)
+        ct0, idx0, st0 = b.dispersion()
+        for split in (1, 2):
+            b.set_plan(precision=2, count_split=split)
+            ct, idx, st = b.dispersion()
+            assert np.array_equal(idx, idx0) and np.array_equal(st, st0), split
+            assert np.array_equal(ct, ct0, equal_nan=True), split
+
+
 def test_every_plan_and_the_plain_path_give_identical_indices(masw):
     m, g = W.ragged_batch(n_models=64, seed=77)
     with masw.Batch(m, g) as b:
