@@ -17,7 +17,8 @@
 //  count_certify_kernel   negative-eigenvalue count below the pole-free bound
 //                         (one thread per item, bisection, two passes: every
 //                         6th wavelength of a model first, then the others
-//                         from their neighbours' bracket) and its FP64
+//                         from a guess on the line through their neighbours'
+//                         indices) and its FP64
 //                         certificate, a lane pair per item; for small batches
 //                         both in one kernel (lane pairs, plan count_split).
 //                         The fallback items take fallback32_kernel (linear
