@@ -115,7 +115,9 @@ typedef struct {
                                 with count_split 2, else 128 */
     int32_t count_split;     /* precision 2: 0 the search (a lane pair per item, three-way
                                 splits) and the certificate in one kernel; 1 the search
-                                in a kernel of its own (one thread per item, bisection)
+                                in kernels of their own (one thread per item: every 6th
+                                wavelength of a model and its last by bisection, then
+                                the others from a guess between those two indices)
                                 before the certificate's; 2 as 1, and the items the
                                 search passes straight to the linear FP32 scan (no count
                                 change below the bound, a mode below V[0]) take that
