@@ -69,3 +69,17 @@ def test_new_entry_points_reject_bad_arguments_without_the_gpu(lib):
     out = [(d * 2)() for _ in range(4)]
     assert lib.masw_sincos_check(i32(2), x, *out, None) == 1
     assert lib.masw_sincos_check(i32(1), x, None, out[1], out[2], out[3], None) == 1
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """The product path has no CPU fallback: on a machine without a GPU the
+    binding's batch creation fails with the CUDA error instead of computing
+    anything on the host."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2003_02256_gb300 import masw, workloads as W
+
+    m, g = W.uniform_batch(n_models=2, n_layers=3, n_lambda=5)
+    with pytest.raises(masw.MaswError, match="masw_model_batch_create"):
+        masw.Batch(m, g)
